@@ -1,0 +1,262 @@
+"""Python face of the FP64 CPU oracle (soap_oracle.c) plus the Gaussian RV fit.
+
+TEST INFRASTRUCTURE.  Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg
+of ``bench.py`` may import this module.  It shares no code with the CUDA library and never
+calls it.
+
+Functions follow the paper (arXiv 2301.04259):
+  quiet(...)       Alg. 1 (Sect. 2.1): sum over disk cells of I_XY x Doppler-shifted,
+                   re-interpolated local spectrum (Eqs. 6, 9-11).
+  active(...)      Alg. 5 (Sect. 3.3) with Eqs. 1-4 (Sect. 2.1).
+  contrast(...)    Sect. 4.3.1: ratio of two Planck functions.
+  ccf(...)         Sect. 4.1: cross-correlation with a line mask.
+  fit_gaussian(...) Sect. 4.1: RV = mean of a Gaussian fitted to the CCF (least squares,
+                   Levenberg-Marquardt from scipy/MINPACK, used as a library step).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from pathlib import Path
+
+import numpy as np
+
+HERE = Path(__file__).resolve().parent
+SRC = HERE / "soap_oracle.c"
+BUILD = HERE / "_build"
+LIB = BUILD / "liboracle.so"
+
+C_KMS = 299792.458
+
+_lib = None
+
+
+def build(force: bool = False) -> Path:
+    """Compile the oracle with gcc (IEEE FP64, no contraction, OpenMP)."""
+    BUILD.mkdir(exist_ok=True)
+    if LIB.exists() and not force and LIB.stat().st_mtime >= SRC.stat().st_mtime:
+        return LIB
+    tmp = LIB.with_suffix(f".{os.getpid()}.tmp.so")
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+           "-fno-fast-math", str(SRC), "-o", str(tmp), "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, LIB)
+    return LIB
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    build()
+    lib = ctypes.CDLL(str(LIB))
+    d, i32, i64, u32 = ctypes.c_double, ctypes.c_int, ctypes.c_int64, ctypes.c_uint32
+    P = ctypes.c_void_p
+    lib.or_delta.restype = d
+    lib.or_delta.argtypes = [d, d, i64]
+    lib.or_grid.restype = None
+    lib.or_grid.argtypes = [d, d, i64, P]
+    lib.or_cell_geometry.restype = None
+    lib.or_cell_geometry.argtypes = [i32, d, d, d, d, d, i32, P, P, P, P, P]
+    lib.or_shift_interp.restype = d
+    lib.or_shift_interp.argtypes = [P, P, i64, d, d, i64]
+    lib.or_quiet.restype = i32
+    lib.or_quiet.argtypes = [i32, d, d, d, d, d, i32, P, d, d, i64, P, P, i64, P]
+    lib.or_planck_ratio.restype = d
+    lib.or_planck_ratio.argtypes = [d, d, d]
+    lib.or_contrast.restype = None
+    lib.or_contrast.argtypes = [P, i64, d, d, P]
+    lib.or_infomap_grid.restype = i32
+    lib.or_infomap_grid.argtypes = [i32, d, d, i32, P, P, P, d, P]
+    lib.or_active.restype = i32
+    lib.or_active.argtypes = [i32, d, d, d, d, d, i32, P, d, d, i64, d, P, P,
+                              i32, P, P, P, P, P, i32, P, u32, P, i64, P, P]
+    lib.or_ccf.restype = i32
+    lib.or_ccf.argtypes = [P, i32, i64, d, d, P, P, i32, d, d, d, i32, P]
+    lib.or_num_threads.restype = i32
+    lib.or_num_threads.argtypes = []
+    _lib = lib
+    return lib
+
+
+def _p(a):
+    return ctypes.c_void_p(a.ctypes.data) if a is not None else None
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def num_threads() -> int:
+    return int(_load().or_num_threads())
+
+
+# ---------------------------------------------------------------------------------------
+def delta(lambda_start, lambda_end, n_px) -> float:
+    return float(_load().or_delta(lambda_start, lambda_end, n_px))
+
+
+def grid(lambda_start, lambda_end, n_px) -> np.ndarray:
+    out = np.empty(n_px, np.float64)
+    _load().or_grid(lambda_start, lambda_end, n_px, _p(out))
+    return out
+
+
+def cell_geometry(star):
+    """(I, v, mu, bin) on the N x N grid, index j*N+i; invisible cells: I=0, bin=-1."""
+    N = star.grid_n
+    I = np.empty(N * N); v = np.empty(N * N); mu = np.empty(N * N)
+    b = np.empty(N * N, np.int32)
+    muv = _f64(star.mu_values)
+    _load().or_cell_geometry(N, star.vsini_kms, star.incl_deg, star.u1, star.u2,
+                             star.diff_rot_alpha, len(muv), _p(muv), _p(I), _p(v), _p(mu), _p(b))
+    return I, v, mu, b
+
+
+def shift_interp(lam, S, beta, m) -> float:
+    """S Doppler-shifted by beta and re-interpolated at output pixel m (Eqs. 6, 9-11)."""
+    lam = _f64(lam); S = _f64(S)
+    dl = float(np.log(lam[-1] / lam[0]) / (lam.size - 1))
+    return float(_load().or_shift_interp(_p(lam), _p(S), lam.size, dl, beta, int(m)))
+
+
+def _pix(pix, n_px):
+    if pix is None:
+        return None, n_px
+    pix = np.ascontiguousarray(pix, dtype=np.int64)
+    if pix.size and (pix.min() < 0 or pix.max() >= n_px):
+        raise ValueError("pixel index out of range")
+    return pix, pix.size
+
+
+def quiet(star, quiet_local, pix=None) -> np.ndarray:
+    """Integrated quiet spectrum (Alg. 1) at pixels `pix` (all pixels if None)."""
+    q = _f64(quiet_local)
+    assert q.shape == (star.n_mu, star.n_px)
+    pix, ns = _pix(pix, star.n_px)
+    out = np.empty(ns, np.float64)
+    muv = _f64(star.mu_values)
+    rc = _load().or_quiet(star.grid_n, star.vsini_kms, star.incl_deg, star.u1, star.u2,
+                          star.diff_rot_alpha, star.n_mu, _p(muv), star.lambda_start_A,
+                          star.lambda_end_A, star.n_px, _p(q), _p(pix), ns, _p(out))
+    if rc != 0:
+        raise RuntimeError("or_quiet failed")
+    return out
+
+
+EFFECT_TOT, EFFECT_FLUX, EFFECT_BCONV = 1, 2, 4
+
+
+def active(star, quiet_local, active_local, regions, phases, effects=EFFECT_TOT, pix=None,
+           return_delta=False):
+    """Spectra of the active star per phase (Alg. 5, Eqs. 1-4).
+
+    active_local: dict type -> [n_mu, n_px] (1 spot, 2 facula; facula defaults to spot).
+    Returns F [n_eff, n_phases, n_sample] (and Delta F if return_delta)."""
+    q = _f64(quiet_local)
+    spot = _f64(active_local[1])
+    fac = _f64(active_local.get(2, active_local[1]))
+    act = np.ascontiguousarray(np.stack([spot, fac]))
+    nr = len(regions)
+    rtype = np.array([r.type for r in regions], np.int32)
+    lat = _f64([r.lat_deg for r in regions]); lon = _f64([r.lon_deg for r in regions])
+    rad = _f64([r.radius_rstar for r in regions]); tmp = _f64([r.temp_K for r in regions])
+    if nr == 0:
+        rtype = np.zeros(1, np.int32); lat = lon = rad = tmp = np.zeros(1)
+    ph = _f64(phases)
+    pix, ns = _pix(pix, star.n_px)
+    n_eff = bin(effects & 7).count("1")
+    F = np.empty((n_eff, ph.size, ns)); dF = np.empty_like(F) if return_delta else None
+    muv = _f64(star.mu_values)
+    rc = _load().or_active(star.grid_n, star.vsini_kms, star.incl_deg, star.u1, star.u2,
+                           star.diff_rot_alpha, star.n_mu, _p(muv), star.lambda_start_A,
+                           star.lambda_end_A, star.n_px, star.t_quiet_K, _p(q), _p(act), nr,
+                           _p(rtype), _p(lat), _p(lon), _p(rad), _p(tmp), ph.size, _p(ph),
+                           effects, _p(pix), ns, _p(F), _p(dF))
+    if rc != 0:
+        raise RuntimeError("or_active failed")
+    return (F, dF) if return_delta else F
+
+
+def infomap(star, regions, phase) -> np.ndarray:
+    """InfoMap on the N x N grid [j, i]: owning region index, -1 quiet, -2 off-disk."""
+    N = star.grid_n
+    out = np.empty(N * N, np.int32)
+    lat = _f64([r.lat_deg for r in regions] or [0.0]); lon = _f64([r.lon_deg for r in regions] or [0.0])
+    rad = _f64([r.radius_rstar for r in regions] or [0.0])
+    rc = _load().or_infomap_grid(N, star.incl_deg, star.diff_rot_alpha, len(regions), _p(lat),
+                                 _p(lon), _p(rad), float(phase), _p(out))
+    if rc != 0:
+        raise RuntimeError("or_infomap_grid failed")
+    return out.reshape(N, N)
+
+
+def planck_ratio(lambda_A, t_active, t_quiet) -> float:
+    return float(_load().or_planck_ratio(lambda_A, t_active, t_quiet))
+
+
+def contrast(lam, t_active, t_quiet) -> np.ndarray:
+    lam = _f64(lam)
+    out = np.empty_like(lam)
+    _load().or_contrast(_p(lam), lam.size, t_active, t_quiet, _p(out))
+    return out
+
+
+def ccf(F, star_or_range, mask_lambda, mask_weight, width_kms, v_lo, v_step, n_v) -> np.ndarray:
+    """CCF [n_spec, n_v] of spectra F [n_spec, n_px] with the box mask (Sect. 4.1)."""
+    F = _f64(np.atleast_2d(F))
+    if hasattr(star_or_range, "lambda_start_A"):
+        ls, le = star_or_range.lambda_start_A, star_or_range.lambda_end_A
+    else:
+        ls, le = star_or_range
+    ml = _f64(mask_lambda); mw = _f64(mask_weight)
+    out = np.empty((F.shape[0], n_v))
+    _load().or_ccf(_p(F), F.shape[0], F.shape[1], ls, le, _p(ml), _p(mw), ml.size, width_kms,
+                   v_lo, v_step, n_v, _p(out))
+    return out
+
+
+def gaussian(v, A, B, mu, sigma):
+    return A + B * np.exp(-0.5 * ((v - mu) / sigma) ** 2)
+
+
+def fit_initial(v, c):
+    """Starting point of the Gaussian fit: continuum = max, depth at the minimum, width from
+    the area of the dip."""
+    v = np.asarray(v, np.float64); c = np.asarray(c, np.float64)
+    A0 = float(c.max()); k = int(np.argmin(c)); B0 = float(c[k] - A0)
+    dv = float(v[1] - v[0]) if v.size > 1 else 1.0
+    area = float(np.sum(A0 - c) * dv)
+    s0 = area / (abs(B0) * np.sqrt(2 * np.pi)) if B0 != 0 else dv
+    return np.array([A0, B0, float(v[k]), max(s0, dv)])
+
+
+def fit_gaussian(v, c):
+    """Least-squares Gaussian A + B exp(-(v-mu)^2 / 2 sigma^2) to one CCF; returns
+    (A, B, mu, sigma).  RV = mu (Sect. 4.1)."""
+    from scipy.optimize import least_squares
+    v = np.asarray(v, np.float64); c = np.asarray(c, np.float64)
+
+    def res(p):
+        return gaussian(v, *p) - c
+
+    def jac(p):
+        A, B, mu, s = p
+        e = np.exp(-0.5 * ((v - mu) / s) ** 2)
+        return np.stack([np.ones_like(v), e, B * e * (v - mu) / s ** 2,
+                         B * e * (v - mu) ** 2 / s ** 3], axis=1)
+
+    r = least_squares(res, fit_initial(v, c), jac=jac, method="lm", xtol=1e-15, ftol=1e-15,
+                      gtol=1e-15, max_nfev=20000)
+    p = r.x.copy()
+    p[3] = abs(p[3])
+    return p
+
+
+def rv(F, star_or_range, mask_lambda, mask_weight, width_kms, v_lo, v_step, n_v):
+    """RV (km/s) per spectrum: Gaussian centre of the CCF.  Returns (rv, params, ccf)."""
+    c = ccf(F, star_or_range, mask_lambda, mask_weight, width_kms, v_lo, v_step, n_v)
+    v = v_lo + v_step * np.arange(n_v)
+    params = np.array([fit_gaussian(v, row) for row in c])
+    return params[:, 2].copy(), params, c
