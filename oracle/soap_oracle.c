@@ -398,11 +398,16 @@ int or_ccf(const double* F, int n_spec, int64_t n_px, double lambda_start, doubl
                 double uhi = (u0 + atanh(v_hi / OR_C_KMS)) / delta + h;
                 if (ulo < -0.5 || uhi > (double)n_px - 0.5) continue;
                 double uc = (u0 + atanh(v / OR_C_KMS)) / delta;
-                double a = uc - h, b = uc + h;
-                int64_t n0 = (int64_t)floor(a + 0.5), n1 = (int64_t)floor(b + 0.5);
-                for (int64_t n = n0; n <= n1; n++) {
+                /* box edges relative to the pixel below the centre, so that the box keeps its
+                 * width W exactly (edges rounded at the magnitude of uc would not) */
+                double nc = floor(uc);
+                double frac = uc - nc;
+                double a = frac - h, b = frac + h;
+                int64_t i0 = (int64_t)floor(a + 0.5), i1 = (int64_t)floor(b + 0.5);
+                for (int64_t i = i0; i <= i1; i++) {
+                    int64_t n = (int64_t)nc + i;
                     if (n < 0 || n >= n_px) continue;
-                    double lo = fmax(a, (double)n - 0.5), hi = fmin(b, (double)n + 0.5);
+                    double lo = fmax(a, (double)i - 0.5), hi = fmin(b, (double)i + 0.5);
                     if (hi > lo) or_add(&acc, mask_w[l] * f[n] * (hi - lo));
                 }
             }
