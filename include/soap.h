@@ -1,0 +1,235 @@
+/*
+ * soap.h -- C-ABI of the GB300 (sm_103a) stellar-disk integration library (libsoap.so).
+ *
+ * Computes the hot path of SOAP-GPU (Zhao & Dumusque, arXiv 2301.04259): every cell of an
+ * N x N stellar-disk grid takes the local spectrum of its centre-to-limb angle mu, Doppler
+ * shifts it by the cell's projected rotational velocity (Eq. 6), interpolates it back onto
+ * the common wavelength grid (Eqs. 9-11), weights it by limb darkening and sums it over the
+ * disk (Alg. 1 / Alg. 4).  Per rotational phase, the cells covered by spots and faculae
+ * (InfoMap, Alg. 5) contribute the differences of Eqs. 1-3, and Eq. 4 gives the spectrum of
+ * the active star.  Radial velocities come from a line-mask CCF and a Gaussian fit
+ * (Sect. 4.1).
+ *
+ * Conventions shared by every entry point
+ *  - Status: every call returns a soap_status.  On anything but SOAP_OK the outputs are
+ *    unspecified and soap_last_error() (per thread) describes the failure.  No C++
+ *    exception crosses this boundary.
+ *  - Ownership: the caller owns every pointer it passes.  The library copies what it keeps
+ *    (star parameters, local spectra) into memory owned by the context, never frees caller
+ *    memory and never retains caller pointers after a call returns.  The context owns all
+ *    device memory it allocates; soap_free() releases it.
+ *  - Memory space: pointer arguments documented "host or device" come with an `*_on_device`
+ *    flag: 0 = host memory (pageable or pinned), 1 = device memory of the context's GPU.
+ *    Everything else is host memory.
+ *  - Streams: all GPU work of a context is enqueued on its stream (soap_init_star's
+ *    `cuda_stream`, or soap_set_stream(); NULL = the legacy default stream).  Calls whose
+ *    outputs are in device memory return without synchronising: the caller orders later
+ *    work on the same stream or synchronises.  Calls with host outputs synchronise the
+ *    stream before returning.
+ *  - Threads: a context must not be used by two threads at once.  Different contexts are
+ *    independent.
+ *  - Layout: arrays are C row-major; spectra are float64 unless stated otherwise.
+ *
+ * Wavelength grid.  The grid is log-uniform with both ends included:
+ *   lambda_n = lambda_start * exp(n * Delta), n = 0 .. n_px-1,
+ *   Delta = log1p((lambda_end - lambda_start) / lambda_start) / (n_px - 1).
+ * (The paper's Eq. 5 grid is linear; on a log grid a Doppler shift is a uniform translation
+ * in pixel space, which makes the interpolation weight the same for every pixel of a cell.)
+ */
+#ifndef SOAP_H
+#define SOAP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SOAP_OK = 0,
+    SOAP_EINVAL = 1,     /* invalid argument (NULL pointer, size, range, non-finite value) */
+    SOAP_ENOMEM = 2,     /* device or host allocation failed */
+    SOAP_ECUDA = 3,      /* a CUDA runtime call or kernel launch failed */
+    SOAP_ERANGE = 4,     /* a size exceeds a documented limit */
+    SOAP_ETIMEOUT = 5,   /* a bounded device-side wait gave up */
+    SOAP_ESTATE = 6      /* call not valid in the context's state (e.g. no active spectrum) */
+} soap_status;
+
+/* Arithmetic of the disk sum.  SOAP_FP64: FP64 everywhere (outputs float64).
+ * SOAP_FP32: FP64 cell velocities, shifts and weights; FP32 contraction with FP32
+ * accumulation (outputs float32). */
+typedef enum {
+    SOAP_FP64 = 0,
+    SOAP_FP32 = 1
+} soap_precision;
+
+/* Form of the sum over cells (soap_quiet_spectrum). */
+typedef enum {
+    SOAP_FORM_TOEPLITZ = 0,   /* per-mu integer-offset velocity kernels, banded contraction */
+    SOAP_FORM_DIRECT = 1      /* per-cell gather-interpolate-reduce */
+} soap_form;
+
+/* Effects (Eqs. 1-3), OR-able.  Outputs list the requested effects in this order. */
+enum {
+    SOAP_EFFECT_TOT = 1,      /* Eq. 3: S'_quiet - I_ratio S'_active */
+    SOAP_EFFECT_FLUX = 2,     /* Eq. 1: S'_quiet - I_ratio S'_quiet */
+    SOAP_EFFECT_BCONV = 4     /* Eq. 2: S'_quiet - S'_active */
+};
+
+/* Region types (InfoMap values, Sect. 3.3). */
+enum { SOAP_SPOT = 1, SOAP_FACULA = 2 };
+
+/* Limits. */
+#define SOAP_MAX_REGIONS 64         /* regions per soap_active_phases call */
+#define SOAP_MAX_CLASSES 8          /* distinct (type, temperature) pairs per call */
+#define SOAP_MAX_MU 64              /* tabulated mu values */
+#define SOAP_MAX_TAPS 256           /* velocity-kernel taps, 2 ceil(s_max) + 2 */
+
+/* Star (Sect. 2.1, Fig. 0; differential rotation Sect. 3.4).
+ *  grid_n        N of the N x N disk grid, 1 .. 8192.  Cell (i, j) has centre
+ *                x = (2i+1-N)/N, y = (2j+1-N)/N, area (2/N)^2, is visible iff x^2+y^2 < 1,
+ *                mu = sqrt(1 - x^2 - y^2).
+ *  n_mu          number of tabulated mu values (local spectra), 1 .. SOAP_MAX_MU.
+ *  n_px          pixels of the wavelength grid, 2 .. 2^28.
+ *  vsini_kms     projected equatorial velocity, |vsini| < c.  Observer on +z, rotation axis
+ *                (0, sin i, cos i); cells with x > 0 recede (positive velocity = redshift).
+ *  incl_deg      inclination of the rotation axis to the line of sight (0 .. 180).
+ *  u1, u2        quadratic limb darkening I(mu) = 1 - u1 (1-mu) - u2 (1-mu)^2; cell weight
+ *                I = area * I(mu).
+ *  diff_rot_alpha  omega(lat) = omega0 (1 + alpha sin^2 lat) (alpha = omega1/omega0, the
+ *                paper's DIFF_ROT); projected velocity vsini x (1 + alpha sin^2 lat).
+ *  lambda_start_A, lambda_end_A  grid ends (vacuum Angstrom), 0 < start < end.
+ *  t_quiet_K     effective temperature of the quiet photosphere (contrast, Sect. 4.3.1).
+ *  mu_values     host array [n_mu] in (0, 1]; each cell uses the nearest value (ties: lower
+ *                index). */
+typedef struct {
+    int32_t grid_n;
+    int32_t n_mu;
+    int64_t n_px;
+    double vsini_kms;
+    double incl_deg;
+    double u1;
+    double u2;
+    double diff_rot_alpha;
+    double lambda_start_A;
+    double lambda_end_A;
+    double t_quiet_K;
+    const double* mu_values;
+} soap_star_desc;
+
+/* One active region (Sect. 2.1 Localize; Alg. 5): a spherical cap of angular radius
+ * asin(radius_rstar) centred at (lat_deg, lon_deg).  At rotational phase p its longitude is
+ * lon_deg + 360 p (1 + alpha sin^2 lat); longitude 0 at phase 0 faces the observer.  Regions
+ * later in the list overwrite earlier ones in the InfoMap (a spot listed after a facula
+ * inside it keeps its own type).  The contrast is the Planck ratio
+ * B(lambda, temp_K) / B(lambda, t_quiet_K) (Sect. 4.3.1).  radius_rstar in [0, 1]. */
+typedef struct {
+    int32_t type;          /* SOAP_SPOT or SOAP_FACULA */
+    int32_t reserved;      /* must be 0 */
+    double lat_deg;
+    double lon_deg;
+    double radius_rstar;
+    double temp_K;
+} soap_region;
+
+/* Read-only facts about an initialised star. */
+typedef struct {
+    int64_t n_visible;      /* visible cells */
+    int32_t tap_min;        /* smallest velocity-kernel tap offset (pixels) */
+    int32_t n_taps;         /* taps of every velocity kernel */
+    double delta;           /* ln-lambda step of the grid */
+    double total_intensity; /* sum of the cell weights I */
+    int32_t fixed_point_bits; /* kernels are accumulated exactly as integers in units of 2^-bits */
+    int32_t reserved;
+} soap_star_info;
+
+typedef struct soap_ctx soap_ctx;
+
+/* Create a context for one star and upload its quiet local spectra.
+ *  star            star description (host).
+ *  quiet_local     [n_mu][n_px] float64 quiet-photosphere local spectra, host or device.
+ *  quiet_on_device 0 host, 1 device.
+ *  cuda_stream     cudaStream_t to enqueue on (NULL = legacy default stream).
+ *  out             receives the new context; NULL on failure.
+ * Computes the per-cell geometry on the GPU (Sect. 2.1): mu, I, velocity, nearest-mu bin,
+ * pixel shift s = atanh(v/c)/Delta, tap j = ceil(s) and interpolation weight
+ * w = expm1((j - s) Delta) / expm1(Delta) (Eq. 11 on a log grid).  Uses the current CUDA
+ * device.  Errors: SOAP_EINVAL for an invalid description, SOAP_ERANGE when a limit above is
+ * exceeded, SOAP_ENOMEM, SOAP_ECUDA. */
+soap_status soap_init_star(const soap_star_desc* star, const double* quiet_local,
+                           int quiet_on_device, void* cuda_stream, soap_ctx** out);
+
+/* Upload the active-region local spectra of one region type (Sect. 2.1: S_active).
+ *  type          SOAP_SPOT or SOAP_FACULA.  Until a facula spectrum is set, faculae use the
+ *                spot spectrum (as SOAP 2.0 did).
+ *  active_local  [n_mu][n_px] float64, host or device. */
+soap_status soap_set_active_spectrum(soap_ctx* ctx, int32_t type, const double* active_local,
+                                     int on_device);
+
+/* Replace the context's stream (cudaStream_t or NULL). */
+soap_status soap_set_stream(soap_ctx* ctx, void* cuda_stream);
+
+/* Block until all work of the context's stream has finished. */
+soap_status soap_synchronize(soap_ctx* ctx);
+
+/* Fill *out with facts about the star. */
+soap_status soap_get_star_info(const soap_ctx* ctx, soap_star_info* out);
+
+/* Integrated quiet spectrum (Alg. 1 / Alg. 4): F_q[m] = sum_c I_c S'_c[m].
+ *  form       SOAP_FORM_TOEPLITZ or SOAP_FORM_DIRECT (same result up to rounding).
+ *  precision  SOAP_FP64 (out: float64 [n_px]) or SOAP_FP32 (out: float32 [n_px]).
+ *  out        host or device per out_on_device. */
+soap_status soap_quiet_spectrum(soap_ctx* ctx, int32_t form, int32_t precision, void* out,
+                                int out_on_device);
+
+/* Spectra of the active star at each phase (Alg. 5 with Eqs. 1-4).
+ *  regions    host [n_regions], 0 .. SOAP_MAX_REGIONS, order-significant (see soap_region).
+ *  phases     host [n_phases] rotational phases (any real value; 1.0 = one rotation).
+ *  effects    OR of SOAP_EFFECT_* (at least one).
+ *  precision  SOAP_FP64 (float64 output) or SOAP_FP32 (float32 output).
+ *  out        [n_effects][n_phases][n_px], effects in the order TOT, FLUX, BCONV (those
+ *             requested); out[e][p][m] = F_q[m] - Delta F_e[p][m] (Eq. 4).  Host or device.
+ * Errors: SOAP_ESTATE if no active spectrum was set; SOAP_ERANGE if more than
+ * SOAP_MAX_CLASSES distinct (type, temperature) pairs are given. */
+soap_status soap_active_phases(soap_ctx* ctx, const soap_region* regions, int32_t n_regions,
+                               const double* phases, int32_t n_phases, uint32_t effects,
+                               int32_t precision, void* out, int out_on_device);
+
+/* Radial velocities from a line-mask CCF and a Gaussian fit (Sect. 4.1).
+ *  spectra        [n_spec][n_px] on the context's grid, float64 (spectra_f32 = 0) or float32
+ *                 (spectra_f32 = 1); host or device per spectra_on_device.
+ *  mask_lambda    host [n_lines] rest wavelengths (Angstrom); mask_weight host [n_lines].
+ *  mask_width_kms full width W of each mask box in velocity.
+ *  v_lo, v_step, n_v  velocity grid v_k = v_lo + k v_step (km/s), n_v >= 5.
+ * CCF(v) = sum_l w_l sum_n F_n |[n-1/2, n+1/2] intersect box_l(v)| in pixel coordinates
+ * u = ln(lambda/lambda_start)/Delta, box_l(v) centred at (ln(lambda_l/lambda_start) +
+ * atanh(v/c))/Delta with half width W/(2 c Delta); lines whose box leaves the grid anywhere on
+ * the velocity grid are skipped.  The fit minimises sum_k (A + B exp(-(v_k-mu)^2/(2 s^2)) -
+ * CCF_k)^2 by FP64 Levenberg-Marquardt from A = max CCF, B = min - max, mu = v at the
+ * minimum, s from the dip area.
+ *  rv_kms         [n_spec] fitted mu (km/s).
+ *  fit_params     [n_spec][4] (A, B, mu, s), or NULL.
+ *  ccf_out        [n_spec][n_v] float64 CCF, or NULL.
+ *  Outputs are host or device per out_on_device. */
+soap_status soap_rv_ccf(soap_ctx* ctx, const void* spectra, int32_t spectra_f32, int32_t n_spec,
+                        int spectra_on_device, const double* mask_lambda,
+                        const double* mask_weight, int32_t n_lines, double mask_width_kms,
+                        double v_lo, double v_step, int32_t n_v, double* rv_kms,
+                        double* fit_params, double* ccf_out, int out_on_device);
+
+/* Number of kernels this context has launched so far (for launch accounting). */
+soap_status soap_get_launch_count(const soap_ctx* ctx, uint64_t* out);
+
+/* Release the context and all device memory it owns.  NULL is a no-op.  Synchronises the
+ * context's stream first. */
+void soap_free(soap_ctx* ctx);
+
+/* Description of the last failure on the calling thread ("" if none).  The string stays
+ * valid until the next call on this thread. */
+const char* soap_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SOAP_H */

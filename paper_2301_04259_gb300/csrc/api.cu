@@ -1,0 +1,418 @@
+// api.cu -- C-ABI entry points of libsoap: argument validation, context and memory
+// management, host<->device staging.  All arithmetic of the method runs in the kernels of
+// geometry.cu, contract.cu, direct.cu and ccf.cu.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "soap_internal.cuh"
+
+namespace soap {
+
+static thread_local char g_error[1024];
+
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_error, sizeof(g_error), fmt, ap);
+    va_end(ap);
+}
+
+void clear_error() { g_error[0] = '\0'; }
+
+soap_status ensure(DevBuf& b, size_t bytes) {
+    if (bytes <= b.bytes && b.p) return SOAP_OK;
+    if (b.p) {
+        // the old buffer may still be read by queued work on any stream of this device
+        cudaDeviceSynchronize();
+        cudaFree(b.p);
+        b.p = nullptr;
+        b.bytes = 0;
+    }
+    size_t nb = bytes < 256 ? 256 : bytes;
+    cudaError_t e = cudaMalloc(&b.p, nb);
+    if (e != cudaSuccess) {
+        b.p = nullptr;
+        set_error("cudaMalloc(%zu) failed: %s", nb, cudaGetErrorString(e));
+        return SOAP_ENOMEM;
+    }
+    b.bytes = nb;
+    return SOAP_OK;
+}
+
+void release(DevBuf& b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+soap_status ensure_host(HostBuf& b, size_t bytes) {
+    if (bytes <= b.bytes && b.p) return SOAP_OK;
+    if (b.p) cudaFreeHost(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    cudaError_t e = cudaMallocHost(&b.p, bytes);
+    if (e != cudaSuccess) {
+        b.p = nullptr;
+        set_error("cudaMallocHost(%zu) failed: %s", bytes, cudaGetErrorString(e));
+        return SOAP_ENOMEM;
+    }
+    b.bytes = bytes;
+    return SOAP_OK;
+}
+
+void release_host(HostBuf& b) {
+    if (b.p) cudaFreeHost(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+static bool is_finite(double x) { return std::isfinite(x); }
+
+static int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+// Copy n bytes of a caller array into device memory `dst` (async on the context stream).
+static soap_status to_device(soap_ctx* c, void* dst, const void* src, size_t n, int on_device) {
+    SOAP_CUDA(cudaMemcpyAsync(dst, src, n, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                              c->stream));
+    return SOAP_OK;
+}
+
+static void free_ctx_memory(soap_ctx* c) {
+    void* ptrs[] = {c->cell_I, c->cell_w, c->cell_mu, c->cell_j, c->cell_bin, c->flags, c->q64,
+                    c->q32, c->a64[0], c->a32[0], c->a64[1], c->a32[1], c->kq_fixed};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    DevBuf* bufs[] = {&c->stage_in, &c->fq, &c->contrast, &c->kphase, &c->jobs, &c->coefs,
+                      &c->regions, &c->phases, &c->out_stage, &c->partial, &c->ccf_tmp};
+    for (DevBuf* b : bufs) release(*b);
+    release_host(c->host_stage);
+}
+
+// upload [n_mu][n_px] float64 spectra into padded fp64 + fp32 rows
+static soap_status upload_spectra(soap_ctx* c, const double* src, int on_device, double* dst64,
+                                  float* dst32) {
+    size_t bytes = (size_t)c->n_mu * (size_t)c->n_px * sizeof(double);
+    const double* dsrc = src;
+    if (!on_device) {
+        SOAP_TRY(ensure(c->stage_in, bytes));
+        SOAP_TRY(to_device(c, c->stage_in.p, src, bytes, 0));
+        dsrc = c->stage_in.as<double>();
+    }
+    return pad_rows(c, dsrc, dst64, dst32, c->n_mu);
+}
+
+static soap_status check_flags(soap_ctx* c) {
+    unsigned int f = 0;
+    SOAP_CUDA(cudaMemcpyAsync(&f, c->flags, sizeof(f), cudaMemcpyDeviceToHost, c->stream));
+    SOAP_CUDA(cudaStreamSynchronize(c->stream));
+    if (f) {
+        set_error("device status word 0x%x (tap range %d, box range %d, job overflow %d)", f,
+                  !!(f & kFlagTapRange), !!(f & kFlagBoxRange), !!(f & kFlagJobOverflow));
+        return SOAP_ERANGE;
+    }
+    return SOAP_OK;
+}
+
+}  // namespace soap
+
+using namespace soap;
+
+extern "C" {
+
+const char* soap_last_error(void) { return g_error; }
+
+soap_status soap_init_star(const soap_star_desc* s, const double* quiet_local, int quiet_on_device,
+                           void* cuda_stream, soap_ctx** out) {
+    clear_error();
+    if (!out) { set_error("out is NULL"); return SOAP_EINVAL; }
+    *out = nullptr;
+    if (!s || !quiet_local) { set_error("star or quiet_local is NULL"); return SOAP_EINVAL; }
+    if (s->grid_n < 1 || s->grid_n > 8192) { set_error("grid_n=%d outside 1..8192", s->grid_n); return SOAP_EINVAL; }
+    if (s->n_mu < 1 || s->n_mu > SOAP_MAX_MU) { set_error("n_mu=%d outside 1..%d", s->n_mu, SOAP_MAX_MU); return SOAP_ERANGE; }
+    if (s->n_px < 2 || s->n_px > (int64_t(1) << 28)) { set_error("n_px=%lld outside 2..2^28", (long long)s->n_px); return SOAP_EINVAL; }
+    double vals[] = {s->vsini_kms, s->incl_deg, s->u1, s->u2, s->diff_rot_alpha,
+                     s->lambda_start_A, s->lambda_end_A, s->t_quiet_K};
+    for (double v : vals)
+        if (!is_finite(v)) { set_error("non-finite star parameter"); return SOAP_EINVAL; }
+    if (!(s->lambda_start_A > 0) || !(s->lambda_end_A > s->lambda_start_A)) {
+        set_error("need 0 < lambda_start < lambda_end"); return SOAP_EINVAL;
+    }
+    if (s->incl_deg < 0 || s->incl_deg > 180) { set_error("incl_deg outside [0,180]"); return SOAP_EINVAL; }
+    if (!(s->t_quiet_K > 0)) { set_error("t_quiet_K must be > 0"); return SOAP_EINVAL; }
+    if (!s->mu_values) { set_error("mu_values is NULL"); return SOAP_EINVAL; }
+    for (int b = 0; b < s->n_mu; b++)
+        if (!is_finite(s->mu_values[b]) || !(s->mu_values[b] > 0) || s->mu_values[b] > 1) {
+            set_error("mu_values[%d] outside (0,1]", b); return SOAP_EINVAL;
+        }
+    double vfac = std::fmax(1.0, std::fabs(1.0 + s->diff_rot_alpha));
+    double vmax = std::fabs(s->vsini_kms) * vfac;
+    if (!(vmax < kCKms)) { set_error("|v| >= c"); return SOAP_EINVAL; }
+    double delta = std::log1p((s->lambda_end_A - s->lambda_start_A) / s->lambda_start_A) / (double)(s->n_px - 1);
+    if (!(delta > 0) || !is_finite(delta)) { set_error("grid step Delta not positive"); return SOAP_EINVAL; }
+    double smax = std::atanh(vmax / kCKms) / delta;
+    int64_t tmax = (int64_t)std::ceil(smax) + 1, tmin = (int64_t)std::floor(-smax) - 1;
+    if (tmax - tmin + 1 > SOAP_MAX_TAPS) {
+        set_error("velocity kernel needs %lld taps > %d (vsini too large for the pixel size)",
+                  (long long)(tmax - tmin + 1), SOAP_MAX_TAPS);
+        return SOAP_ERANGE;
+    }
+
+    soap_ctx* c = new (std::nothrow) soap_ctx();
+    if (!c) { set_error("out of host memory"); return SOAP_ENOMEM; }
+    cudaGetDevice(&c->device);
+    c->stream = (cudaStream_t)cuda_stream;
+    c->N = s->grid_n; c->n_mu = s->n_mu; c->n_px = s->n_px;
+    c->vsini = s->vsini_kms; c->incl_deg = s->incl_deg; c->u1 = s->u1; c->u2 = s->u2;
+    c->alpha = s->diff_rot_alpha; c->lam_s = s->lambda_start_A; c->lam_e = s->lambda_end_A;
+    c->t_quiet = s->t_quiet_K; c->delta = delta;
+    for (int b = 0; b < s->n_mu; b++) c->mu_values[b] = s->mu_values[b];
+    c->tap_min = (int)tmin;
+    c->n_taps = (int)(tmax - tmin + 1);
+    int64_t need = std::max<int64_t>(tmax, -tmin) + 1;
+    c->pad = round_up(need, 32);
+    c->row_len = round_up(c->n_px + 2 * c->pad, 32);
+    // fixed-point kernels: every partial sum is bounded by sum |I| <= 4 (1 + |u1| + |u2|)
+    double bound = 4.0 * (1.0 + std::fabs(s->u1) + std::fabs(s->u2));
+    c->fx_bits = 61 - (int)std::ceil(std::log2(bound));
+
+    soap_status st = SOAP_OK;
+    size_t NN = (size_t)c->N * c->N;
+    size_t rows = (size_t)c->n_mu * (size_t)c->row_len;
+    cudaError_t e = cudaSuccess;
+#define ALLOC(ptr, bytes) if (e == cudaSuccess) e = cudaMalloc((void**)&(ptr), (bytes))
+    ALLOC(c->cell_I, NN * sizeof(double));
+    ALLOC(c->cell_w, NN * sizeof(double));
+    ALLOC(c->cell_mu, NN * sizeof(double));
+    ALLOC(c->cell_j, NN * sizeof(int32_t));
+    ALLOC(c->cell_bin, NN * sizeof(int32_t));
+    ALLOC(c->flags, sizeof(unsigned int));
+    ALLOC(c->q64, rows * sizeof(double));
+    ALLOC(c->q32, rows * sizeof(float));
+    ALLOC(c->kq_fixed, (size_t)c->n_mu * c->n_taps * sizeof(long long));
+#undef ALLOC
+    if (e != cudaSuccess) {
+        set_error("device allocation failed: %s", cudaGetErrorString(e));
+        free_ctx_memory(c);
+        delete c;
+        return SOAP_ENOMEM;
+    }
+    st = SOAP_OK;
+    if (cudaMemsetAsync(c->flags, 0, sizeof(unsigned int), c->stream) != cudaSuccess) st = SOAP_ECUDA;
+    if (st == SOAP_OK) st = geometry_init(c);
+    if (st == SOAP_OK) st = upload_spectra(c, quiet_local, quiet_on_device, c->q64, c->q32);
+    if (st == SOAP_OK) st = check_flags(c);
+    if (st != SOAP_OK) {
+        cudaStreamSynchronize(c->stream);
+        free_ctx_memory(c);
+        delete c;
+        return st;
+    }
+    *out = c;
+    return SOAP_OK;
+}
+
+soap_status soap_set_active_spectrum(soap_ctx* c, int32_t type, const double* active_local,
+                                     int on_device) {
+    clear_error();
+    if (!c || !active_local) { set_error("ctx or active_local is NULL"); return SOAP_EINVAL; }
+    if (type != SOAP_SPOT && type != SOAP_FACULA) { set_error("type must be SOAP_SPOT or SOAP_FACULA"); return SOAP_EINVAL; }
+    int t = type - 1;
+    size_t rows = (size_t)c->n_mu * (size_t)c->row_len;
+    if (!c->a64[t]) {
+        if (cudaMalloc((void**)&c->a64[t], rows * sizeof(double)) != cudaSuccess ||
+            cudaMalloc((void**)&c->a32[t], rows * sizeof(float)) != cudaSuccess) {
+            set_error("device allocation of active spectra failed");
+            return SOAP_ENOMEM;
+        }
+    }
+    SOAP_TRY(upload_spectra(c, active_local, on_device, c->a64[t], c->a32[t]));
+    c->active_set[t] = true;
+    return SOAP_OK;
+}
+
+soap_status soap_set_stream(soap_ctx* c, void* stream) {
+    clear_error();
+    if (!c) { set_error("ctx is NULL"); return SOAP_EINVAL; }
+    c->stream = (cudaStream_t)stream;
+    return SOAP_OK;
+}
+
+soap_status soap_synchronize(soap_ctx* c) {
+    clear_error();
+    if (!c) { set_error("ctx is NULL"); return SOAP_EINVAL; }
+    SOAP_CUDA(cudaStreamSynchronize(c->stream));
+    return SOAP_OK;
+}
+
+soap_status soap_get_star_info(const soap_ctx* c, soap_star_info* out) {
+    clear_error();
+    if (!c || !out) { set_error("ctx or out is NULL"); return SOAP_EINVAL; }
+    memset(out, 0, sizeof(*out));
+    out->n_visible = c->n_visible;
+    out->tap_min = c->tap_min;
+    out->n_taps = c->n_taps;
+    out->delta = c->delta;
+    out->total_intensity = c->total_I;
+    out->fixed_point_bits = c->fx_bits;
+    return SOAP_OK;
+}
+
+soap_status soap_get_launch_count(const soap_ctx* c, uint64_t* out) {
+    clear_error();
+    if (!c || !out) { set_error("ctx or out is NULL"); return SOAP_EINVAL; }
+    *out = c->launches;
+    return SOAP_OK;
+}
+
+soap_status soap_quiet_spectrum(soap_ctx* c, int32_t form, int32_t precision, void* out,
+                                int out_on_device) {
+    clear_error();
+    if (!c || !out) { set_error("ctx or out is NULL"); return SOAP_EINVAL; }
+    if (form != SOAP_FORM_TOEPLITZ && form != SOAP_FORM_DIRECT) { set_error("unknown form %d", form); return SOAP_EINVAL; }
+    if (precision != SOAP_FP64 && precision != SOAP_FP32) { set_error("unknown precision %d", precision); return SOAP_EINVAL; }
+    size_t esz = precision == SOAP_FP64 ? 8 : 4;
+    size_t bytes = (size_t)c->n_px * esz;
+    void* dst = out;
+    if (!out_on_device) {
+        SOAP_TRY(ensure(c->out_stage, bytes));
+        dst = c->out_stage.p;
+    }
+    if (form == SOAP_FORM_TOEPLITZ) SOAP_TRY(toeplitz_quiet(c, precision, dst));
+    else SOAP_TRY(direct_quiet(c, precision, dst));
+    if (!out_on_device) {
+        SOAP_CUDA(cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, c->stream));
+        SOAP_CUDA(cudaStreamSynchronize(c->stream));
+    }
+    return SOAP_OK;
+}
+
+soap_status soap_active_phases(soap_ctx* c, const soap_region* regions, int32_t n_regions,
+                               const double* phases, int32_t n_phases, uint32_t effects,
+                               int32_t precision, void* out, int out_on_device) {
+    clear_error();
+    if (!c || !out) { set_error("ctx or out is NULL"); return SOAP_EINVAL; }
+    if (n_regions < 0 || n_regions > SOAP_MAX_REGIONS) { set_error("n_regions=%d outside 0..%d", n_regions, SOAP_MAX_REGIONS); return SOAP_ERANGE; }
+    if (n_regions > 0 && !regions) { set_error("regions is NULL"); return SOAP_EINVAL; }
+    if (n_phases < 0) { set_error("n_phases < 0"); return SOAP_EINVAL; }
+    if (n_phases > 0 && !phases) { set_error("phases is NULL"); return SOAP_EINVAL; }
+    if (effects == 0 || (effects & ~7u)) { set_error("effects must be a non-empty OR of SOAP_EFFECT_*"); return SOAP_EINVAL; }
+    if (precision != SOAP_FP64 && precision != SOAP_FP32) { set_error("unknown precision %d", precision); return SOAP_EINVAL; }
+    for (int p = 0; p < n_phases; p++)
+        if (!is_finite(phases[p])) { set_error("phases[%d] not finite", p); return SOAP_EINVAL; }
+    std::vector<RegionDev> rd(n_regions);
+    double ctemp[SOAP_MAX_CLASSES];
+    int ctype[SOAP_MAX_CLASSES];
+    int n_class = 0;
+    for (int r = 0; r < n_regions; r++) {
+        const soap_region& g = regions[r];
+        if (g.type != SOAP_SPOT && g.type != SOAP_FACULA) { set_error("regions[%d].type invalid", r); return SOAP_EINVAL; }
+        if (g.reserved != 0) { set_error("regions[%d].reserved must be 0", r); return SOAP_EINVAL; }
+        if (!is_finite(g.lat_deg) || !is_finite(g.lon_deg) || !is_finite(g.radius_rstar) || !is_finite(g.temp_K)) {
+            set_error("regions[%d] has a non-finite field", r); return SOAP_EINVAL;
+        }
+        if (g.radius_rstar < 0 || g.radius_rstar > 1) { set_error("regions[%d].radius_rstar outside [0,1]", r); return SOAP_EINVAL; }
+        if (!(g.temp_K > 0)) { set_error("regions[%d].temp_K must be > 0", r); return SOAP_EINVAL; }
+        int cl = -1;
+        for (int k = 0; k < n_class; k++)
+            if (ctype[k] == g.type && ctemp[k] == g.temp_K) cl = k;
+        if (cl < 0) {
+            if (n_class == SOAP_MAX_CLASSES) { set_error("more than %d distinct (type, temperature) pairs", SOAP_MAX_CLASSES); return SOAP_ERANGE; }
+            cl = n_class++;
+            ctype[cl] = g.type;
+            ctemp[cl] = g.temp_K;
+        }
+        rd[r] = RegionDev{g.lat_deg, g.lon_deg, g.radius_rstar, g.temp_K, g.type, cl};
+    }
+    for (int k = 0; k < n_class; k++) {
+        bool ok = ctype[k] == SOAP_SPOT ? c->active_set[0] : (c->active_set[1] || c->active_set[0]);
+        if (!ok) { set_error("no active spectrum set for region type %d", ctype[k]); return SOAP_ESTATE; }
+    }
+    int n_eff = __builtin_popcount(effects);
+    size_t esz = precision == SOAP_FP64 ? 8 : 4;
+    size_t bytes = (size_t)n_eff * (size_t)n_phases * (size_t)c->n_px * esz;
+    if (n_phases == 0) return SOAP_OK;
+    void* dst = out;
+    if (!out_on_device) {
+        SOAP_TRY(ensure(c->out_stage, bytes));
+        dst = c->out_stage.p;
+    }
+    SOAP_TRY(toeplitz_active(c, rd.data(), n_regions, ctemp, ctype, n_class, phases, n_phases,
+                             effects, precision, dst));
+    if (!out_on_device) {
+        SOAP_CUDA(cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, c->stream));
+        SOAP_CUDA(cudaStreamSynchronize(c->stream));
+        SOAP_TRY(check_flags(c));
+    }
+    return SOAP_OK;
+}
+
+soap_status soap_rv_ccf(soap_ctx* c, const void* spectra, int32_t spectra_f32, int32_t n_spec,
+                        int spectra_on_device, const double* mask_lambda,
+                        const double* mask_weight, int32_t n_lines, double mask_width_kms,
+                        double v_lo, double v_step, int32_t n_v, double* rv_kms,
+                        double* fit_params, double* ccf_out, int out_on_device) {
+    clear_error();
+    if (!c || !spectra || !mask_lambda || !mask_weight || !rv_kms) {
+        set_error("NULL argument"); return SOAP_EINVAL;
+    }
+    if (n_spec < 0 || n_lines < 1 || n_v < 5 || n_v > 4096) { set_error("need n_spec >= 0, n_lines >= 1, 5 <= n_v <= 4096"); return SOAP_EINVAL; }
+    if (!is_finite(mask_width_kms) || !(mask_width_kms > 0) || !is_finite(v_lo) || !is_finite(v_step) || !(v_step > 0)) {
+        set_error("mask width / velocity grid invalid"); return SOAP_EINVAL;
+    }
+    double v_hi = v_lo + v_step * (n_v - 1);
+    if (!(std::fabs(v_lo) < kCKms) || !(std::fabs(v_hi) < kCKms)) { set_error("velocity grid reaches c"); return SOAP_EINVAL; }
+    double h = mask_width_kms / (2.0 * kCKms * c->delta);
+    if (2.0 * h > 14.0) { set_error("mask box spans more than 14 pixels"); return SOAP_ERANGE; }
+    for (int l = 0; l < n_lines; l++)
+        if (!is_finite(mask_lambda[l]) || !(mask_lambda[l] > 0) || !is_finite(mask_weight[l])) {
+            set_error("mask line %d invalid", l); return SOAP_EINVAL;
+        }
+    if (n_spec == 0) return SOAP_OK;
+    size_t esz = spectra_f32 ? 4 : 8;
+    size_t sbytes = (size_t)n_spec * (size_t)c->n_px * esz;
+    const void* dspec = spectra;
+    if (!spectra_on_device) {
+        SOAP_TRY(ensure(c->stage_in, sbytes));
+        SOAP_CUDA(cudaMemcpyAsync(c->stage_in.p, spectra, sbytes, cudaMemcpyHostToDevice, c->stream));
+        dspec = c->stage_in.p;
+    }
+    double* rv_d = rv_kms;
+    double* fit_d = fit_params;
+    double* ccf_d = ccf_out;
+    size_t o_rv = 0, o_fit = 0, o_ccf = 0, total = 0;
+    if (!out_on_device) {
+        o_rv = 0;
+        o_fit = o_rv + (size_t)n_spec * 8;
+        o_ccf = o_fit + (size_t)n_spec * 32;
+        total = o_ccf + (size_t)n_spec * n_v * 8;
+        SOAP_TRY(ensure(c->out_stage, total));
+        char* base = c->out_stage.as<char>();
+        rv_d = (double*)(base + o_rv);
+        fit_d = (double*)(base + o_fit);
+        ccf_d = (double*)(base + o_ccf);
+    }
+    SOAP_TRY(rv_ccf_run(c, dspec, spectra_f32 ? 1 : 0, n_spec, mask_lambda, mask_weight, n_lines,
+                        mask_width_kms, v_lo, v_step, n_v, rv_d, fit_d, ccf_d));
+    if (!out_on_device) {
+        SOAP_CUDA(cudaMemcpyAsync(rv_kms, rv_d, (size_t)n_spec * 8, cudaMemcpyDeviceToHost, c->stream));
+        if (fit_params)
+            SOAP_CUDA(cudaMemcpyAsync(fit_params, fit_d, (size_t)n_spec * 32, cudaMemcpyDeviceToHost, c->stream));
+        if (ccf_out)
+            SOAP_CUDA(cudaMemcpyAsync(ccf_out, ccf_d, (size_t)n_spec * n_v * 8, cudaMemcpyDeviceToHost, c->stream));
+        SOAP_CUDA(cudaStreamSynchronize(c->stream));
+    }
+    return SOAP_OK;
+}
+
+void soap_free(soap_ctx* c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    free_ctx_memory(c);
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,498 @@
+// contract.cu -- Toeplitz form of the disk sum (quiet star, Alg. 1; active phases, Alg. 5
+// with Eqs. 1-4) and the wavelength-dependent contrast (Sect. 4.3.1).
+//
+// Per phase p and region class (type, temperature) cl, the cells the class owns in the
+// InfoMap add their two-tap kernels into per-mu-bin velocity kernels K[p][cl][b][k] (exact
+// 64-bit fixed point).  With Q = sum_cl K (all active cells) the three effects of Eqs. 1-3,
+// summed over cells and subtracted from the quiet integral (Eq. 4), are
+//   TOT:   F_q - sum_b Q_b * S_q,b + sum_cl C_cl . sum_b K_cl,b * S_a(cl),b
+//   FLUX:  F_q - sum_b Q_b * S_q,b + sum_cl C_cl . sum_b K_cl,b * S_q,b
+//   BCONV: F_q - sum_b Q_b * S_q,b + sum_cl        sum_b K_cl,b * S_a(cl),b
+// where "*" is the banded convolution (K * S)[m] = sum_k K[k] S[m-k] over the kernel's taps
+// and C_cl(lambda) = B(lambda, T_cl) / B(lambda, T_quiet) multiplies on the common grid.
+//
+// A "job" is one (group, mu bin) pair with the union of its non-zero taps over a block of
+// PB consecutive phases; the contraction kernel reads the row of that bin once per tap and
+// reuses it for all PB phases.
+#include <cmath>
+#include <vector>
+
+#include "soap_internal.cuh"
+
+namespace soap {
+
+struct Job {
+    int32_t group;     // 0: all active cells (quiet rows, negative), g >= 1: class g-1
+    int32_t bin;       // mu bin
+    int32_t k_lo;      // first tap offset (pixels)
+    int32_t n_k;       // number of taps
+    int32_t coef_off;  // offset of coefficients [n_k][PB] within the block's coefficient slab
+    int32_t pad0, pad1, pad2;
+};
+
+// ---------------------------------------------------------------------------------------
+// contrast (Sect. 4.3.1): C(lambda) = (exp(hc/lambda k T_q) - 1) / (exp(hc/lambda k T_a) - 1)
+// ---------------------------------------------------------------------------------------
+struct ClassTemps {
+    double t[SOAP_MAX_CLASSES];
+};
+
+__global__ void k_contrast(int64_t n_px, double lam_s, double delta, double t_quiet, int n_class,
+                           ClassTemps temps, double* c64, float* c32) {
+    const double hck = kPlanckH * kLightSI / kBoltzmann * 1e10;   // Angstrom Kelvin
+    for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < n_px;
+         m += (int64_t)gridDim.x * blockDim.x) {
+        double lam = lam_s * exp((double)m * delta);
+        double xq = expm1(hck / (lam * t_quiet));
+        for (int cl = 0; cl < n_class; cl++) {
+            double v = xq / expm1(hck / (lam * temps.t[cl]));
+            c64[cl * n_px + m] = v;
+            c32[cl * n_px + m] = (float)v;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// InfoMap + per-phase velocity kernels (Alg. 5)
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long fx(double v, double scale) {
+    return (unsigned long long)__double2ll_rn(v * scale);
+}
+
+// One block per phase.  Region centre at phase p (observer frame, rotation axis
+// (0, sin i, cos i)): star-frame (cos lat sin L, sin lat, cos lat cos L) with
+// L = lon + 360 p (1 + alpha sin^2 lat), tilted by the inclination.  A visible cell (x, y, mu)
+// belongs to the region iff (x, y, mu) . P >= sqrt(1 - r^2); the last region in list order
+// that contains it owns it.  The membership arithmetic uses explicitly rounded FP64 steps.
+__global__ void k_phase_hist(int N, int n_regions, const RegionDev* regs, const double* phases,
+                             double incl_deg, double alpha, const double* cell_I,
+                             const double* cell_w, const double* cell_mu, const int32_t* cell_j,
+                             const int32_t* cell_bin, int tap_min, int n_taps, int n_mu,
+                             int n_class, double scale, long long* kout, int use_smem,
+                             unsigned int* flags) {
+    __shared__ double sP[SOAP_MAX_REGIONS][3];
+    __shared__ double sCos[SOAP_MAX_REGIONS];
+    __shared__ int sBox[SOAP_MAX_REGIONS][4];
+    __shared__ int sCls[SOAP_MAX_REGIONS];
+    extern __shared__ long long hist_sm[];
+    const int p = blockIdx.x;
+    const int nb = n_class * n_mu * n_taps;
+    long long* hist = use_smem ? hist_sm : kout + (int64_t)p * nb;
+    const double d2r = kPi / 180.0;
+    const double phase = phases[p];
+    if (threadIdx.x < n_regions) {
+        const RegionDev g = regs[threadIdx.x];
+        double lat = __dmul_rn(g.lat_deg, d2r);
+        double sl = sin(lat), cl = cos(lat);
+        double lonp = __dadd_rn(g.lon_deg,
+                                __dmul_rn(__dmul_rn(360.0, phase),
+                                          __dadd_rn(1.0, __dmul_rn(__dmul_rn(alpha, sl), sl))));
+        double lon = __dmul_rn(lonp, d2r);
+        double incl = __dmul_rn(incl_deg, d2r);
+        double si = sin(incl), ci = cos(incl);
+        double px = __dmul_rn(cl, sin(lon)), py = sl, pz = __dmul_rn(cl, cos(lon));
+        double P0 = px;
+        double P1 = __dsub_rn(__dmul_rn(py, si), __dmul_rn(pz, ci));
+        double P2 = __dadd_rn(__dmul_rn(py, ci), __dmul_rn(pz, si));
+        double r = g.radius;
+        sP[threadIdx.x][0] = P0; sP[threadIdx.x][1] = P1; sP[threadIdx.x][2] = P2;
+        sCos[threadIdx.x] = __dsqrt_rn(__dsub_rn(1.0, __dmul_rn(r, r)));
+        sCls[threadIdx.x] = g.cls;
+        // conservative cell box of the cap: angle to an axis +- cap radius
+        double a = asin(fmin(r, 1.0));
+        double bx = acos(fmax(-1.0, fmin(1.0, P0)));
+        double by = acos(fmax(-1.0, fmin(1.0, P1)));
+        double bz = acos(fmax(-1.0, fmin(1.0, P2)));
+        double xhi = cos(fmax(0.0, bx - a)), xlo = cos(fmin(kPi, bx + a));
+        double yhi = cos(fmax(0.0, by - a)), ylo = cos(fmin(kPi, by + a));
+        int i0 = (int)floor((xlo * N + N - 1) * 0.5) - 1, i1 = (int)ceil((xhi * N + N - 1) * 0.5) + 1;
+        int j0 = (int)floor((ylo * N + N - 1) * 0.5) - 1, j1 = (int)ceil((yhi * N + N - 1) * 0.5) + 1;
+        i0 = max(i0, 0); j0 = max(j0, 0); i1 = min(i1, N - 1); j1 = min(j1, N - 1);
+        if (bz - a > 0.5 * kPi + 1e-6) { i1 = i0 - 1; }        // cap entirely on the far side
+        sBox[threadIdx.x][0] = i0; sBox[threadIdx.x][1] = i1;
+        sBox[threadIdx.x][2] = j0; sBox[threadIdx.x][3] = j1;
+    }
+    if (use_smem)
+        for (int t = threadIdx.x; t < nb; t += blockDim.x) hist[t] = 0;
+    __syncthreads();
+    for (int r = 0; r < n_regions; r++) {
+        const int i0 = sBox[r][0], i1 = sBox[r][1], j0 = sBox[r][2], j1 = sBox[r][3];
+        if (i1 < i0 || j1 < j0) continue;
+        const int wdt = i1 - i0 + 1;
+        const int64_t area = (int64_t)wdt * (j1 - j0 + 1);
+        for (int64_t t = threadIdx.x; t < area; t += blockDim.x) {
+            int i = i0 + (int)(t % wdt), jj = j0 + (int)(t / wdt);
+            bool dup = false;                 // visit each cell once: first box that holds it
+            for (int q = 0; q < r; q++)
+                if (i >= sBox[q][0] && i <= sBox[q][1] && jj >= sBox[q][2] && jj <= sBox[q][3]) dup = true;
+            if (dup) continue;
+            int64_t c = (int64_t)jj * N + i;
+            int b = cell_bin[c];
+            if (b < 0) continue;
+            double x = (double)(2 * i + 1 - N) / (double)N;
+            double y = (double)(2 * jj + 1 - N) / (double)N;
+            double mu = cell_mu[c];
+            int owner = -1;
+            for (int q = 0; q < n_regions; q++) {
+                double dot = __dadd_rn(__dadd_rn(__dmul_rn(x, sP[q][0]), __dmul_rn(y, sP[q][1])),
+                                       __dmul_rn(mu, sP[q][2]));
+                if (dot >= sCos[q]) owner = q;
+            }
+            if (owner < 0) continue;
+            int cls = sCls[owner];
+            int kk = cell_j[c] - tap_min;
+            if (kk < 1 || kk >= n_taps) { atomicOr(flags, kFlagTapRange); continue; }
+            double I = cell_I[c], w = cell_w[c];
+            long long* h = hist + ((int64_t)cls * n_mu + b) * n_taps;
+            atomicAdd((unsigned long long*)&h[kk], fx(I * (1.0 - w), scale));
+            atomicAdd((unsigned long long*)&h[kk - 1], fx(I * w, scale));
+        }
+    }
+    if (use_smem) {
+        __syncthreads();
+        long long* dst = kout + (int64_t)p * nb;
+        for (int t = threadIdx.x; t < nb; t += blockDim.x) dst[t] = hist[t];
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// job tables
+// ---------------------------------------------------------------------------------------
+// kfix: [n_phases][n_class][n_mu][n_taps].  mode 0 (quiet): one group, +K of class 0.
+// mode 1 (active): group 0 = -sum_cl K (quiet rows), group g = +K of class g-1.
+// Block pb covers phases pb*PB .. pb*PB+PB-1.  Outputs per block: jobs[max_jobs],
+// gstart[G+1] (job index where each group starts), coefficients [..][n_k][PB] in c64/c32.
+__global__ void k_build_jobs(const long long* kfix, int n_phases, int n_class, int n_mu, int n_taps,
+                             int tap_min, int PB, int mode, double inv_scale, Job* jobs,
+                             int* gstart, double* c64, float* c32, int max_jobs, int max_coef,
+                             unsigned int* flags) {
+    __shared__ int s_lo[(1 + SOAP_MAX_CLASSES) * SOAP_MAX_MU];
+    __shared__ int s_hi[(1 + SOAP_MAX_CLASSES) * SOAP_MAX_MU];
+    __shared__ int s_idx[(1 + SOAP_MAX_CLASSES) * SOAP_MAX_MU];
+    __shared__ int s_off[(1 + SOAP_MAX_CLASSES) * SOAP_MAX_MU];
+    const int pb = blockIdx.x;
+    const int G = mode == 0 ? 1 : 1 + n_class;
+    const int ngb = G * n_mu;
+    const int p0 = pb * PB;
+    const int64_t nb = (int64_t)n_class * n_mu * n_taps;
+    auto value = [&](int g, int b, int p, int kk) -> long long {
+        if (p >= n_phases) return 0;
+        const long long* base = kfix + (int64_t)p * nb;
+        if (mode == 0) return base[(int64_t)b * n_taps + kk];
+        if (g == 0) {
+            long long s = 0;
+            for (int cl = 0; cl < n_class; cl++) s += base[((int64_t)cl * n_mu + b) * n_taps + kk];
+            return -s;
+        }
+        return base[((int64_t)(g - 1) * n_mu + b) * n_taps + kk];
+    };
+    auto nonzero = [&](int g, int b, int p, int kk) -> bool {
+        if (p >= n_phases) return false;
+        const long long* base = kfix + (int64_t)p * nb;
+        if (mode == 0) return base[(int64_t)b * n_taps + kk] != 0;
+        if (g == 0) {
+            for (int cl = 0; cl < n_class; cl++)
+                if (base[((int64_t)cl * n_mu + b) * n_taps + kk] != 0) return true;
+            return false;
+        }
+        return base[((int64_t)(g - 1) * n_mu + b) * n_taps + kk] != 0;
+    };
+    for (int t = threadIdx.x; t < ngb; t += blockDim.x) {
+        int g = t / n_mu, b = t % n_mu;
+        int lo = n_taps, hi = -1;
+        for (int p = p0; p < p0 + PB; p++)
+            for (int kk = 0; kk < n_taps; kk++)
+                if (nonzero(g, b, p, kk)) { lo = min(lo, kk); hi = max(hi, kk); }
+        s_lo[t] = lo; s_hi[t] = hi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int nj = 0, off = 0, g_prev = -1;
+        int* gs = gstart + (int64_t)pb * (G + 1);
+        for (int t = 0; t < ngb; t++) {
+            int g = t / n_mu;
+            while (g_prev < g) { gs[++g_prev] = nj; }
+            if (s_hi[t] < s_lo[t]) { s_idx[t] = -1; continue; }
+            int nk = s_hi[t] - s_lo[t] + 1;
+            if (nj >= max_jobs || off + nk * PB > max_coef) { atomicOr(flags, kFlagJobOverflow); s_idx[t] = -1; continue; }
+            s_idx[t] = nj; s_off[t] = off;
+            Job J;
+            J.group = g; J.bin = t % n_mu; J.k_lo = tap_min + s_lo[t]; J.n_k = nk; J.coef_off = off;
+            J.pad0 = J.pad1 = J.pad2 = 0;
+            jobs[(int64_t)pb * max_jobs + nj] = J;
+            nj++;
+            off += nk * PB;
+        }
+        while (g_prev < G) { gs[++g_prev] = nj; }
+    }
+    __syncthreads();
+    // coefficients [kk][p]
+    for (int t = 0; t < ngb; t++) {
+        if (s_idx[t] < 0) continue;
+        int g = t / n_mu, b = t % n_mu;
+        int nk = s_hi[t] - s_lo[t] + 1;
+        int64_t base = (int64_t)pb * max_coef + s_off[t];
+        for (int e = threadIdx.x; e < nk * PB; e += blockDim.x) {
+            int kk = e / PB, pl = e % PB;
+            double v = (double)value(g, b, p0 + pl, s_lo[t] + kk) * inv_scale;
+            c64[base + e] = v;
+            c32[base + e] = (float)v;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// contraction
+// ---------------------------------------------------------------------------------------
+template <typename T>
+struct Rows {
+    const T* q;         // quiet rows [n_mu][row_len]
+    const T* a[2];      // active rows spot / facula
+};
+
+struct ClassTypes {
+    int t[SOAP_MAX_CLASSES];
+};
+
+struct EffectList {
+    int e[3];
+};
+
+// One thread: R pixels m = m0 + threadIdx.x + r*THREADS, PB phases.  acc holds
+// F_q - (group 0) + folded class terms; tmp accumulates one class before its fold.
+template <typename T, int PB, int R, int THREADS>
+__global__ void __launch_bounds__(THREADS)
+k_contract(int64_t n_px, int64_t row_len, int64_t pad, Rows<T> rows, const Job* __restrict__ jobs,
+           const int* __restrict__ gstart, int G, int max_jobs, const T* __restrict__ coefs,
+           int max_coef, ClassTypes ctype, const T* __restrict__ contrast,
+           const T* __restrict__ fq, int n_phases, EffectList effs, T* __restrict__ out) {
+    const int pb = blockIdx.y;
+    const int eff = effs.e[blockIdx.z];
+    const int64_t mbase = (int64_t)blockIdx.x * THREADS * R + threadIdx.x;
+    int64_t mc[R];
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+        int64_t m = mbase + (int64_t)r * THREADS;
+        mc[r] = pad + (m < n_px ? m : n_px - 1);
+    }
+    T acc[PB][R];
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+        T f0 = fq ? fq[mc[r] - pad] : T(0);
+#pragma unroll
+        for (int p = 0; p < PB; p++) acc[p][r] = f0;
+    }
+    const Job* jb = jobs + (int64_t)pb * max_jobs;
+    const int* gs = gstart + (int64_t)pb * (G + 1);
+    const T* cb = coefs + (int64_t)pb * max_coef;
+
+    // group 0: subtract (active star) or add (quiet star) the quiet-row convolutions
+    for (int jj = gs[0]; jj < gs[1]; jj++) {
+        const Job J = jb[jj];
+        const T* row = rows.q + (int64_t)J.bin * row_len;
+        const T* cf = cb + J.coef_off;
+        for (int kk = 0; kk < J.n_k; kk++) {
+            const int64_t k = J.k_lo + kk;
+            T s[R];
+#pragma unroll
+            for (int r = 0; r < R; r++) s[r] = __ldg(row + mc[r] - k);
+#pragma unroll
+            for (int p = 0; p < PB; p++) {
+                const T cv = cf[kk * PB + p];
+#pragma unroll
+                for (int r = 0; r < R; r++) acc[p][r] = fma(cv, s[r], acc[p][r]);
+            }
+        }
+    }
+    // classes: tmp = sum_b K_cl,b * S, then acc += C_cl . tmp (TOT, FLUX) or tmp (BCONV)
+    for (int g = 1; g < G; g++) {
+        if (gs[g] == gs[g + 1]) continue;
+        const int cl = g - 1;
+        const T* base = eff == SOAP_EFFECT_FLUX ? rows.q : rows.a[ctype.t[cl] == SOAP_FACULA ? 1 : 0];
+        T tmp[PB][R];
+#pragma unroll
+        for (int p = 0; p < PB; p++)
+#pragma unroll
+            for (int r = 0; r < R; r++) tmp[p][r] = T(0);
+        for (int jj = gs[g]; jj < gs[g + 1]; jj++) {
+            const Job J = jb[jj];
+            const T* row = base + (int64_t)J.bin * row_len;
+            const T* cf = cb + J.coef_off;
+            for (int kk = 0; kk < J.n_k; kk++) {
+                const int64_t k = J.k_lo + kk;
+                T s[R];
+#pragma unroll
+                for (int r = 0; r < R; r++) s[r] = __ldg(row + mc[r] - k);
+#pragma unroll
+                for (int p = 0; p < PB; p++) {
+                    const T cv = cf[kk * PB + p];
+#pragma unroll
+                    for (int r = 0; r < R; r++) tmp[p][r] = fma(cv, s[r], tmp[p][r]);
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const T cr = eff == SOAP_EFFECT_BCONV ? T(1) : contrast[(int64_t)cl * n_px + (mc[r] - pad)];
+#pragma unroll
+            for (int p = 0; p < PB; p++) acc[p][r] = fma(cr, tmp[p][r], acc[p][r]);
+        }
+    }
+    // store out[e][p][m]
+    const int64_t plane = (int64_t)n_phases * n_px;
+    T* o = out + (int64_t)blockIdx.z * plane;
+#pragma unroll
+    for (int p = 0; p < PB; p++) {
+        const int ph = pb * PB + p;
+        if (ph >= n_phases) break;
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const int64_t m = mbase + (int64_t)r * THREADS;
+            if (m < n_px) o[(int64_t)ph * n_px + m] = acc[p][r];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------------------
+static int grid_cap(int64_t n, int threads, int cap) {
+    int64_t g = (n + threads - 1) / threads;
+    return (int)(g < 1 ? 1 : (g > cap ? cap : g));
+}
+
+template <typename T, int PB, int R, int THREADS>
+static soap_status launch_contract(soap_ctx* c, int n_blocks, int G, int max_jobs, int max_coef,
+                                   const Job* jobs, const int* gstart, const T* coefs,
+                                   const ClassTypes& ct, const T* contrast, const T* fq,
+                                   int n_phases, const EffectList& el, int n_eff, T* out,
+                                   const T* q, const T* a0, const T* a1) {
+    Rows<T> rows;
+    rows.q = q; rows.a[0] = a0; rows.a[1] = a1;
+    int64_t tiles = (c->n_px + (int64_t)THREADS * R - 1) / ((int64_t)THREADS * R);
+    dim3 grid((unsigned)tiles, (unsigned)n_blocks, (unsigned)n_eff);
+    k_contract<T, PB, R, THREADS><<<grid, THREADS, 0, c->stream>>>(
+        c->n_px, c->row_len, c->pad, rows, jobs, gstart, G, max_jobs, coefs, max_coef, ct,
+        contrast, fq, n_phases, el, out);
+    SOAP_LAUNCHED(c);
+    return SOAP_OK;
+}
+
+// Phase-block sizes and pixels per thread of the two precisions.
+constexpr int kPB64 = 4, kR64 = 2, kT64 = 128;
+constexpr int kPB32 = 8, kR32 = 4, kT32 = 128;
+
+// job + coefficient scratch for a kernel set kfix with n_phases "phases" in blocks of PB
+static soap_status build_jobs(soap_ctx* c, const long long* kfix, int n_phases, int n_class,
+                              int PB, int mode, Job** jobs, int** gstart, double** c64,
+                              float** c32, int* n_blocks, int* G, int* max_jobs, int* max_coef) {
+    *G = mode == 0 ? 1 : 1 + n_class;
+    *n_blocks = (n_phases + PB - 1) / PB;
+    *max_jobs = *G * c->n_mu;
+    *max_coef = *max_jobs * c->n_taps * PB;
+    size_t jb = (size_t)*n_blocks * *max_jobs * sizeof(Job);
+    size_t gb = (size_t)*n_blocks * (*G + 1) * sizeof(int);
+    size_t off_g = (jb + 255) / 256 * 256;
+    SOAP_TRY(ensure(c->jobs, off_g + gb));
+    size_t cb64 = (size_t)*n_blocks * *max_coef * sizeof(double);
+    size_t off32 = (cb64 + 255) / 256 * 256;
+    SOAP_TRY(ensure(c->coefs, off32 + (size_t)*n_blocks * *max_coef * sizeof(float)));
+    *jobs = c->jobs.as<Job>();
+    *gstart = (int*)(c->jobs.as<char>() + off_g);
+    *c64 = c->coefs.as<double>();
+    *c32 = (float*)(c->coefs.as<char>() + off32);
+    double inv_scale = std::ldexp(1.0, -c->fx_bits);
+    k_build_jobs<<<*n_blocks, 128, 0, c->stream>>>(kfix, n_phases, mode == 0 ? 1 : n_class, c->n_mu,
+                                                  c->n_taps, c->tap_min, PB, mode, inv_scale, *jobs,
+                                                  *gstart, *c64, *c32, *max_jobs, *max_coef, c->flags);
+    SOAP_LAUNCHED(c);
+    return SOAP_OK;
+}
+
+soap_status toeplitz_quiet(soap_ctx* c, int precision, void* dst) {
+    Job* jobs; int* gstart; double* c64; float* c32; int nbk, G, mj, mc;
+    SOAP_TRY(build_jobs(c, c->kq_fixed, 1, 1, 1, 0, &jobs, &gstart, &c64, &c32, &nbk, &G, &mj, &mc));
+    ClassTypes ct{};
+    EffectList el{{SOAP_EFFECT_TOT, 0, 0}};
+    if (precision == SOAP_FP64)
+        return launch_contract<double, 1, kR64, kT64>(c, nbk, G, mj, mc, jobs, gstart, c64, ct, nullptr,
+                                                     nullptr, 1, el, 1, (double*)dst, c->q64, nullptr, nullptr);
+    return launch_contract<float, 1, kR32, kT32>(c, nbk, G, mj, mc, jobs, gstart, c32, ct, nullptr,
+                                                nullptr, 1, el, 1, (float*)dst, c->q32, nullptr, nullptr);
+}
+
+soap_status toeplitz_active(soap_ctx* c, const RegionDev* regions_host, int n_regions,
+                            const double* class_temp, const int* class_type, int n_class,
+                            const double* phases_host, int n_phases, uint32_t effects,
+                            int precision, void* dst) {
+    const bool f64 = precision == SOAP_FP64;
+    const size_t esz = f64 ? 8 : 4;
+    const int ncl = n_class > 0 ? n_class : 1;
+    // quiet integral for Eq. 4 in the output precision
+    SOAP_TRY(ensure(c->fq, (size_t)c->n_px * esz));
+    SOAP_TRY(toeplitz_quiet(c, precision, c->fq.p));
+    // contrast per class
+    size_t cbytes = (size_t)ncl * c->n_px;
+    size_t off32 = (cbytes * 8 + 255) / 256 * 256;
+    SOAP_TRY(ensure(c->contrast, off32 + cbytes * 4));
+    double* con64 = c->contrast.as<double>();
+    float* con32 = (float*)(c->contrast.as<char>() + off32);
+    if (n_class > 0) {
+        ClassTemps tt{};
+        for (int k = 0; k < n_class; k++) tt.t[k] = class_temp[k];
+        k_contrast<<<grid_cap(c->n_px, 256, 152 * 8), 256, 0, c->stream>>>(
+            c->n_px, c->lam_s, c->delta, c->t_quiet, n_class, tt, con64, con32);
+        SOAP_LAUNCHED(c);
+    }
+    // regions and phases to the device (pageable copies are staged by the driver at once)
+    size_t rbytes = (size_t)(n_regions > 0 ? n_regions : 1) * sizeof(RegionDev);
+    size_t pbytes = (size_t)n_phases * sizeof(double);
+    SOAP_TRY(ensure(c->regions, rbytes));
+    SOAP_TRY(ensure(c->phases, pbytes));
+    if (n_regions > 0)
+        SOAP_CUDA(cudaMemcpyAsync(c->regions.p, regions_host, (size_t)n_regions * sizeof(RegionDev),
+                                  cudaMemcpyHostToDevice, c->stream));
+    SOAP_CUDA(cudaMemcpyAsync(c->phases.p, phases_host, pbytes, cudaMemcpyHostToDevice, c->stream));
+    // per-phase fixed-point kernels
+    int64_t nb = (int64_t)ncl * c->n_mu * c->n_taps;
+    size_t kbytes = (size_t)n_phases * nb * sizeof(long long);
+    SOAP_TRY(ensure(c->kphase, kbytes));
+    long long* kfix = c->kphase.as<long long>();
+    size_t smem = (size_t)nb * sizeof(long long);
+    int use_smem = smem <= 160 * 1024;
+    if (!use_smem) {
+        SOAP_CUDA(cudaMemsetAsync(kfix, 0, kbytes, c->stream));
+        smem = 0;
+    } else if (smem > 48 * 1024) {
+        SOAP_CUDA(cudaFuncSetAttribute(k_phase_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    }
+    k_phase_hist<<<n_phases, 256, smem, c->stream>>>(
+        c->N, n_regions, c->regions.as<RegionDev>(), c->phases.as<double>(), c->incl_deg, c->alpha,
+        c->cell_I, c->cell_w, c->cell_mu, c->cell_j, c->cell_bin, c->tap_min, c->n_taps, c->n_mu,
+        ncl, std::ldexp(1.0, c->fx_bits), kfix, use_smem, c->flags);
+    SOAP_LAUNCHED(c);
+    // job tables
+    const int PB = f64 ? kPB64 : kPB32;
+    Job* jobs; int* gstart; double* c64; float* c32; int nbk, G, mj, mc;
+    SOAP_TRY(build_jobs(c, kfix, n_phases, ncl, PB, 1, &jobs, &gstart, &c64, &c32, &nbk, &G, &mj, &mc));
+    ClassTypes ct{};
+    for (int k = 0; k < n_class; k++) ct.t[k] = class_type[k];
+    EffectList el{{0, 0, 0}};
+    int n_eff = 0;
+    if (effects & SOAP_EFFECT_TOT) el.e[n_eff++] = SOAP_EFFECT_TOT;
+    if (effects & SOAP_EFFECT_FLUX) el.e[n_eff++] = SOAP_EFFECT_FLUX;
+    if (effects & SOAP_EFFECT_BCONV) el.e[n_eff++] = SOAP_EFFECT_BCONV;
+    const double* a64s = c->active_set[0] ? c->a64[0] : c->a64[1];
+    const double* a64f = c->active_set[1] ? c->a64[1] : c->a64[0];
+    const float* a32s = c->active_set[0] ? c->a32[0] : c->a32[1];
+    const float* a32f = c->active_set[1] ? c->a32[1] : c->a32[0];
+    if (f64)
+        return launch_contract<double, kPB64, kR64, kT64>(c, nbk, G, mj, mc, jobs, gstart, c64, ct, con64,
+                                                         c->fq.as<double>(), n_phases, el, n_eff,
+                                                         (double*)dst, c->q64, a64s, a64f);
+    return launch_contract<float, kPB32, kR32, kT32>(c, nbk, G, mj, mc, jobs, gstart, c32, ct, con32,
+                                                    c->fq.as<float>(), n_phases, el, n_eff,
+                                                    (float*)dst, c->q32, a32s, a32f);
+}
+
+}  // namespace soap

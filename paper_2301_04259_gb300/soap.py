@@ -1,0 +1,239 @@
+"""ctypes binding of libsoap (include/soap.h), with the same names as the C-ABI.
+
+Argument marshalling only: arrays are passed as raw pointers (``torch.Tensor.data_ptr()``
+for CUDA tensors, the numpy buffer for host arrays), every computation runs in the CUDA
+library.  Importing this module loads ``_lib/libsoap.so`` and raises if it has not been built
+(``python -c "import __graft_entry__ as g; g.build()"``): there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+from pathlib import Path
+from typing import Optional, Sequence
+
+import numpy as np
+
+_PKG = Path(__file__).resolve().parent
+LIB_PATH = _PKG / "_lib" / "libsoap.so"
+
+SOAP_OK, SOAP_EINVAL, SOAP_ENOMEM, SOAP_ECUDA, SOAP_ERANGE, SOAP_ETIMEOUT, SOAP_ESTATE = range(7)
+STATUS_NAMES = {0: "SOAP_OK", 1: "SOAP_EINVAL", 2: "SOAP_ENOMEM", 3: "SOAP_ECUDA",
+                4: "SOAP_ERANGE", 5: "SOAP_ETIMEOUT", 6: "SOAP_ESTATE"}
+SOAP_FP64, SOAP_FP32 = 0, 1
+SOAP_FORM_TOEPLITZ, SOAP_FORM_DIRECT = 0, 1
+SOAP_EFFECT_TOT, SOAP_EFFECT_FLUX, SOAP_EFFECT_BCONV = 1, 2, 4
+SOAP_SPOT, SOAP_FACULA = 1, 2
+SOAP_MAX_REGIONS, SOAP_MAX_CLASSES, SOAP_MAX_MU, SOAP_MAX_TAPS = 64, 8, 64, 256
+
+
+class soap_star_desc(ctypes.Structure):
+    _fields_ = [("grid_n", ctypes.c_int32), ("n_mu", ctypes.c_int32), ("n_px", ctypes.c_int64),
+                ("vsini_kms", ctypes.c_double), ("incl_deg", ctypes.c_double),
+                ("u1", ctypes.c_double), ("u2", ctypes.c_double),
+                ("diff_rot_alpha", ctypes.c_double), ("lambda_start_A", ctypes.c_double),
+                ("lambda_end_A", ctypes.c_double), ("t_quiet_K", ctypes.c_double),
+                ("mu_values", ctypes.POINTER(ctypes.c_double))]
+
+
+class soap_region(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("lat_deg", ctypes.c_double), ("lon_deg", ctypes.c_double),
+                ("radius_rstar", ctypes.c_double), ("temp_K", ctypes.c_double)]
+
+
+class soap_star_info(ctypes.Structure):
+    _fields_ = [("n_visible", ctypes.c_int64), ("tap_min", ctypes.c_int32),
+                ("n_taps", ctypes.c_int32), ("delta", ctypes.c_double),
+                ("total_intensity", ctypes.c_double), ("fixed_point_bits", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class SoapError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+def _load():
+    if not LIB_PATH.exists():
+        raise ImportError(f"{LIB_PATH} is not built; run __graft_entry__.build() first")
+    lib = ctypes.CDLL(str(LIB_PATH))
+    P, i32, i64, u32, d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_double
+    sig = {
+        "soap_init_star": (i32, [ctypes.POINTER(soap_star_desc), P, ctypes.c_int, P, ctypes.POINTER(P)]),
+        "soap_set_active_spectrum": (i32, [P, i32, P, ctypes.c_int]),
+        "soap_set_stream": (i32, [P, P]),
+        "soap_synchronize": (i32, [P]),
+        "soap_get_star_info": (i32, [P, ctypes.POINTER(soap_star_info)]),
+        "soap_quiet_spectrum": (i32, [P, i32, i32, P, ctypes.c_int]),
+        "soap_active_phases": (i32, [P, ctypes.POINTER(soap_region), i32, P, i32, u32, i32, P, ctypes.c_int]),
+        "soap_rv_ccf": (i32, [P, P, i32, i32, ctypes.c_int, P, P, i32, d, d, d, i32, P, P, P, ctypes.c_int]),
+        "soap_get_launch_count": (i32, [P, ctypes.POINTER(ctypes.c_uint64)]),
+        "soap_free": (None, [P]),
+        "soap_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+def _check(status: int, where: str):
+    if status != SOAP_OK:
+        raise SoapError(status, where, _lib.soap_last_error().decode())
+
+
+def _ptr(a):
+    """(pointer, on_device) of a torch tensor or numpy array (contiguous)."""
+    if a is None:
+        return None, 0
+    if hasattr(a, "data_ptr") and hasattr(a, "is_cuda"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(a.data_ptr()), int(a.is_cuda)
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return ctypes.c_void_p(a.ctypes.data), 0
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _stream_handle(stream) -> ctypes.c_void_p:
+    if stream is None:
+        return ctypes.c_void_p(None)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+# ---------------------------------------------------------------------------------------
+# entry points (same names as the C-ABI)
+# ---------------------------------------------------------------------------------------
+def star_desc(star) -> soap_star_desc:
+    mus = np.ascontiguousarray(star.mu_values, dtype=np.float64)
+    d = soap_star_desc(grid_n=int(star.grid_n), n_mu=int(mus.size), n_px=int(star.n_px),
+                       vsini_kms=float(star.vsini_kms), incl_deg=float(star.incl_deg),
+                       u1=float(star.u1), u2=float(star.u2),
+                       diff_rot_alpha=float(getattr(star, "diff_rot_alpha", 0.0)),
+                       lambda_start_A=float(star.lambda_start_A), lambda_end_A=float(star.lambda_end_A),
+                       t_quiet_K=float(getattr(star, "t_quiet_K", 5778.0)),
+                       mu_values=mus.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    d._keep = mus
+    return d
+
+
+def soap_init_star(star, quiet_local, stream=None) -> ctypes.c_void_p:
+    """Create a context; quiet_local [n_mu, n_px] float64 (numpy or CUDA tensor)."""
+    d = star_desc(star)
+    ptr, dev = _ptr(quiet_local)
+    out = ctypes.c_void_p()
+    _check(_lib.soap_init_star(ctypes.byref(d), ptr, dev, _stream_handle(stream), ctypes.byref(out)),
+           "soap_init_star")
+    return out
+
+
+def soap_set_active_spectrum(ctx, type_: int, active_local) -> None:
+    ptr, dev = _ptr(active_local)
+    _check(_lib.soap_set_active_spectrum(ctx, int(type_), ptr, dev), "soap_set_active_spectrum")
+
+
+def soap_set_stream(ctx, stream) -> None:
+    _check(_lib.soap_set_stream(ctx, _stream_handle(stream)), "soap_set_stream")
+
+
+def soap_synchronize(ctx) -> None:
+    _check(_lib.soap_synchronize(ctx), "soap_synchronize")
+
+
+def soap_get_star_info(ctx) -> soap_star_info:
+    info = soap_star_info()
+    _check(_lib.soap_get_star_info(ctx, ctypes.byref(info)), "soap_get_star_info")
+    return info
+
+
+def soap_quiet_spectrum(ctx, form: int, precision: int, out) -> None:
+    ptr, dev = _ptr(out)
+    _check(_lib.soap_quiet_spectrum(ctx, int(form), int(precision), ptr, dev), "soap_quiet_spectrum")
+
+
+def regions_array(regions: Sequence) -> ctypes.Array:
+    arr = (soap_region * max(1, len(regions)))()
+    for k, r in enumerate(regions):
+        arr[k] = soap_region(type=int(r.type), reserved=0, lat_deg=float(r.lat_deg),
+                             lon_deg=float(r.lon_deg), radius_rstar=float(r.radius_rstar),
+                             temp_K=float(r.temp_K))
+    return arr
+
+
+def soap_active_phases(ctx, regions: Sequence, phases, effects: int, precision: int, out) -> None:
+    arr = regions_array(regions)
+    ph = np.ascontiguousarray(phases, dtype=np.float64)
+    ptr, dev = _ptr(out)
+    _check(_lib.soap_active_phases(ctx, arr, len(regions), ctypes.c_void_p(ph.ctypes.data), ph.size,
+                                   int(effects), int(precision), ptr, dev), "soap_active_phases")
+
+
+def soap_rv_ccf(ctx, spectra, mask_lambda, mask_weight, mask_width_kms: float, v_lo: float,
+                v_step: float, n_v: int, rv_out, fit_out=None, ccf_out=None) -> None:
+    """spectra [n_spec, n_px] float64/float32; outputs all host (numpy) or all device."""
+    sp, sdev = _ptr(spectra)
+    f32 = int(str(spectra.dtype).endswith("float32"))
+    n_spec = int(spectra.shape[0])
+    ml = np.ascontiguousarray(mask_lambda, dtype=np.float64)
+    mw = np.ascontiguousarray(mask_weight, dtype=np.float64)
+    rp, rdev = _ptr(rv_out)
+    fp, fdev = _ptr(fit_out)
+    cp, cdev = _ptr(ccf_out)
+    if fit_out is not None and fdev != rdev or ccf_out is not None and cdev != rdev:
+        raise ValueError("rv_out, fit_out and ccf_out must all be host or all device")
+    _check(_lib.soap_rv_ccf(ctx, sp, f32, n_spec, sdev, ctypes.c_void_p(ml.ctypes.data),
+                            ctypes.c_void_p(mw.ctypes.data), ml.size, float(mask_width_kms),
+                            float(v_lo), float(v_step), int(n_v), rp, fp, cp, rdev), "soap_rv_ccf")
+
+
+def soap_get_launch_count(ctx) -> int:
+    n = ctypes.c_uint64()
+    _check(_lib.soap_get_launch_count(ctx, ctypes.byref(n)), "soap_get_launch_count")
+    return int(n.value)
+
+
+def soap_free(ctx) -> None:
+    _lib.soap_free(ctx)
+
+
+def soap_last_error() -> str:
+    return _lib.soap_last_error().decode()
+
+
+# ---------------------------------------------------------------------------------------
+# convenience: a context that frees itself
+# ---------------------------------------------------------------------------------------
+class Disk:
+    """Owns one soap context (soap_init_star ... soap_free)."""
+
+    def __init__(self, star, quiet_local, active_local: Optional[dict] = None, stream=None):
+        self.star = star
+        self.ctx = soap_init_star(star, quiet_local, stream)
+        for t, a in (active_local or {}).items():
+            soap_set_active_spectrum(self.ctx, t, a)
+
+    def close(self):
+        if self.ctx:
+            soap_free(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,271 @@
+"""GPU parity: the CUDA library (through its C-ABI) against the FP64 oracle, element by element.
+
+Tolerances (BASELINE: 1e-12 relative flux for the FP64 path, 2e-6 relative flux and 1 cm/s RV
+for the mixed path) are relative to max F_quiet of the oracle.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2301_04259_gb300 import synth
+from paper_2301_04259_gb300.synth import FACULA, SPOT, Region, Star
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 2e-6
+
+
+@pytest.fixture(scope="module")
+def S():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2301_04259_gb300 import soap
+    return soap
+
+
+DEV = "cuda:0"
+
+
+def _t(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def gpu_quiet(S, case, form, prec):
+    dt = torch.float64 if prec == S.SOAP_FP64 else torch.float32
+    with S.Disk(case.star, _t(case.quiet)) as d:
+        out = torch.empty(case.star.n_px, dtype=dt, device=DEV)
+        S.soap_quiet_spectrum(d.ctx, form, prec, out)
+        torch.cuda.synchronize()
+    return out.double().cpu().numpy()
+
+
+def gpu_active(S, case, regions, phases, effects, prec, active=None):
+    dt = torch.float64 if prec == S.SOAP_FP64 else torch.float32
+    n_eff = bin(effects).count("1")
+    act = case.active if active is None else active
+    with S.Disk(case.star, _t(case.quiet), {k: _t(v) for k, v in act.items()}) as d:
+        out = torch.empty((n_eff, len(phases), case.star.n_px), dtype=dt, device=DEV)
+        S.soap_active_phases(d.ctx, regions, phases, effects, prec, out)
+        torch.cuda.synchronize()
+    return out.double().cpu().numpy()
+
+
+def rel(a, b, scale):
+    return float(np.abs(a - b).max() / scale)
+
+
+@pytest.fixture(scope="module")
+def cfg1():
+    return synth.config1(0)
+
+
+@pytest.fixture(scope="module")
+def cfg1_ref(cfg1):
+    q = O.quiet(cfg1.star, cfg1.quiet)
+    F = O.active(cfg1.star, cfg1.quiet, cfg1.active, cfg1.regions, cfg1.phases, effects=7)
+    return q, F
+
+
+# ------------------------------------------------------------------------------------------
+# quiet star
+# ------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("form", [0, 1], ids=["toeplitz", "direct"])
+def test_quiet_config1(S, cfg1, cfg1_ref, form):
+    ref, _ = cfg1_ref
+    g64 = gpu_quiet(S, cfg1, form, S.SOAP_FP64)
+    g32 = gpu_quiet(S, cfg1, form, S.SOAP_FP32)
+    assert rel(g64, ref, ref.max()) <= TOL64
+    assert rel(g32, ref, ref.max()) <= TOL32
+
+
+QUIET_CASES = [
+    # N, n_px, vsini, incl, alpha, n_mu
+    (1, 300, 2.0, 90.0, 0.0, 1),
+    (2, 257, 5.0, 60.0, 0.0, 2),
+    (37, 1031, 8.0, 45.0, -0.18, 5),
+    (64, 2049, 0.0, 90.0, 0.0, 3),
+    (25, 700, 60.0, 30.0, 0.2, 4),
+    (131, 4099, 3.0, 80.0, 0.0, 20),
+]
+
+
+@pytest.mark.parametrize("N,n_px,vsini,incl,alpha,n_mu", QUIET_CASES)
+def test_quiet_ragged_and_edge_cases(S, N, n_px, vsini, incl, alpha, n_mu):
+    case = synth.make_case(N + n_px, name="q", grid_n=N, lambda_start=6000.0, lambda_end=6010.0,
+                           n_px=n_px, mu_values=np.linspace(0.1, 1.0, n_mu), n_lines=15,
+                           depth_law="uniform", sigma_law="angstrom", vsini_kms=vsini,
+                           incl_deg=incl, diff_rot_alpha=alpha, regions=[], n_phases=1)
+    ref = O.quiet(case.star, case.quiet)
+    for form in (0, 1):
+        assert rel(gpu_quiet(S, case, form, S.SOAP_FP64), ref, ref.max()) <= TOL64
+        assert rel(gpu_quiet(S, case, form, S.SOAP_FP32), ref, ref.max()) <= TOL32
+
+
+# ------------------------------------------------------------------------------------------
+# active star
+# ------------------------------------------------------------------------------------------
+def test_active_config1_all_effects(S, cfg1, cfg1_ref):
+    q, ref = cfg1_ref
+    g64 = gpu_active(S, cfg1, cfg1.regions, cfg1.phases, 7, S.SOAP_FP64)
+    g32 = gpu_active(S, cfg1, cfg1.regions, cfg1.phases, 7, S.SOAP_FP32)
+    assert rel(g64, ref, q.max()) <= TOL64
+    assert rel(g32, ref, q.max()) <= TOL32
+    # the residual itself (Delta F = F_q - F), normalised by its own maximum
+    dref = q[None, None] - ref
+    d64 = q[None, None] - g64
+    assert np.abs(d64 - dref).max() <= 1e-10 * np.abs(dref).max()
+
+
+@pytest.fixture(scope="module")
+def complex_case():
+    regs = [Region(FACULA, 25.0, -30.0, 0.3, 6100.0),
+            Region(SPOT, 25.0, -30.0, 0.12, 4800.0),
+            Region(SPOT, -10.0, 60.0, 0.2, 4300.0),
+            Region(FACULA, -12.0, 58.0, 0.25, 6000.0)]
+    c = synth.make_case(17, name="complex", grid_n=57, lambda_start=5000.0, lambda_end=5012.0,
+                        n_px=3001, mu_values=np.linspace(0.05, 1.0, 9), n_lines=40,
+                        depth_law="loguniform", sigma_law="velocity", vsini_kms=6.0,
+                        incl_deg=62.0, diff_rot_alpha=-0.18, regions=regs, n_phases=13)
+    lam = synth.wavelength_grid(5000.0, 5012.0, 3001)
+    rng = np.random.default_rng(4)
+    fac = synth.local_spectra(lam, rng.uniform(5000, 5012, 30), rng.uniform(0.1, 0.5, 30),
+                              np.full(30, 0.05), c.star.mu_values, cb_kms_at_disk_centre=0.1)
+    c.active = {SPOT: c.active[SPOT], FACULA: fac}
+    c.phases = np.linspace(-0.3, 1.4, 13)
+    return c
+
+
+def test_active_complex_regions_classes_and_phases(S, complex_case):
+    c = complex_case
+    q = O.quiet(c.star, c.quiet)
+    ref = O.active(c.star, c.quiet, c.active, c.regions, c.phases, effects=7)
+    g64 = gpu_active(S, c, c.regions, c.phases, 7, S.SOAP_FP64)
+    g32 = gpu_active(S, c, c.regions, c.phases, 7, S.SOAP_FP32)
+    assert rel(g64, ref, q.max()) <= TOL64
+    assert rel(g32, ref, q.max()) <= TOL32
+    # single effects land in the right slot
+    for k, e in enumerate((1, 2, 4)):
+        one = gpu_active(S, c, c.regions, c.phases[:5], e, S.SOAP_FP64)
+        assert rel(one[0], ref[k, :5], q.max()) <= TOL64
+
+
+def test_active_degenerate_cases(S, cfg1, cfg1_ref):
+    q, _ = cfg1_ref
+    ph = np.array([0.0, 0.5, 0.77])
+    # no regions: every phase is the quiet spectrum
+    g = gpu_active(S, cfg1, [], ph, 7, S.SOAP_FP64)
+    assert rel(g, np.broadcast_to(q, g.shape), q.max()) <= TOL64
+    # zero radius
+    g = gpu_active(S, cfg1, [Region(SPOT, 0.0, 0.0, 0.0, 4800.0)], ph, 1, S.SOAP_FP64)
+    assert rel(g, np.broadcast_to(q, g.shape), q.max()) <= TOL64
+    # a region on the far side at phase 0.5 leaves the quiet spectrum
+    g = gpu_active(S, cfg1, [Region(SPOT, 0.0, 0.0, 0.2, 4800.0)], np.array([0.5]), 1, S.SOAP_FP64)
+    assert rel(g[0, 0], q, q.max()) <= TOL64
+    # cap covering the whole disk, one phase
+    regs = [Region(SPOT, 0.0, 0.0, 1.0, 4800.0)]
+    ref = O.active(cfg1.star, cfg1.quiet, cfg1.active, regs, np.array([0.0]), effects=7)
+    g = gpu_active(S, cfg1, regs, np.array([0.0]), 7, S.SOAP_FP64)
+    assert rel(g, ref, q.max()) <= TOL64
+
+
+def test_active_is_deterministic_and_host_output_matches(S, complex_case):
+    c = complex_case
+    a = gpu_active(S, c, c.regions, c.phases, 7, S.SOAP_FP64)
+    b = gpu_active(S, c, c.regions, c.phases, 7, S.SOAP_FP64)
+    assert np.array_equal(a, b)
+    with S.Disk(c.star, c.quiet, c.active) as d:            # host inputs and outputs
+        out = np.empty((3, c.phases.size, c.star.n_px))
+        S.soap_active_phases(d.ctx, c.regions, c.phases, 7, S.SOAP_FP64, out)
+    assert np.array_equal(out, a)
+
+
+def test_state_and_range_errors(S, cfg1):
+    with S.Disk(cfg1.star, _t(cfg1.quiet)) as d:
+        out = torch.empty((1, 2, cfg1.star.n_px), dtype=torch.float64, device=DEV)
+        with pytest.raises(S.SoapError) as e:
+            S.soap_active_phases(d.ctx, cfg1.regions, np.array([0.0, 0.1]), 1, S.SOAP_FP64, out)
+        assert e.value.status == S.SOAP_ESTATE
+        S.soap_set_active_spectrum(d.ctx, SPOT, _t(cfg1.active[SPOT]))
+        regs = [Region(SPOT, 0.0, 0.0, 0.1, 4000.0 + 10 * k) for k in range(9)]
+        with pytest.raises(S.SoapError) as e:
+            S.soap_active_phases(d.ctx, regs, np.array([0.0, 0.1]), 1, S.SOAP_FP64, out)
+        assert e.value.status == S.SOAP_ERANGE
+
+
+# ------------------------------------------------------------------------------------------
+# full size (disk 300x300, 205,800 px, 100 phases) on sampled pixels
+# ------------------------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def cfg2():
+    return synth.config2(0)
+
+
+def _sample_pixels(n_px, seed=0, n=56):
+    rng = np.random.default_rng(seed)
+    edges = [0, 1, 2, 3, n_px - 4, n_px - 3, n_px - 2, n_px - 1]
+    return np.unique(np.concatenate([edges, rng.integers(0, n_px, n)])).astype(np.int64)
+
+
+def test_fullsize_config2_sampled_pixels(S, cfg2):
+    c = cfg2
+    pix = _sample_pixels(c.star.n_px)
+    ref = O.active(c.star, c.quiet, c.active, c.regions, c.phases, effects=1, pix=pix)
+    qref = O.quiet(c.star, c.quiet, pix=pix)
+    g64 = gpu_active(S, c, c.regions, c.phases, 1, S.SOAP_FP64)
+    g32 = gpu_active(S, c, c.regions, c.phases, 1, S.SOAP_FP32)
+    scale = qref.max()
+    assert rel(g64[:, :, pix], ref, scale) <= TOL64
+    assert rel(g32[:, :, pix], ref, scale) <= TOL32
+    # at every pixel: the two precisions agree, and phases with no visible region equal F_q
+    assert np.isfinite(g64).all() and np.isfinite(g32).all()
+    assert np.abs(g32 - g64).max() <= TOL32 * scale
+    gq = gpu_quiet(S, c, 0, S.SOAP_FP64)
+    assert rel(gq[pix], qref, scale) <= TOL64
+    gqd = gpu_quiet(S, c, 1, S.SOAP_FP64)
+    assert rel(gqd, gq, scale) <= TOL64
+
+
+# ------------------------------------------------------------------------------------------
+# CCF and RV (Sect. 4.1)
+# ------------------------------------------------------------------------------------------
+def _gpu_rv(S, case, spectra, lo, step, nv):
+    with S.Disk(case.star, _t(case.quiet)) as d:
+        sp = _t(spectra)
+        n = spectra.shape[0]
+        rv = torch.empty(n, dtype=torch.float64, device=DEV)
+        fit = torch.empty((n, 4), dtype=torch.float64, device=DEV)
+        ccf = torch.empty((n, nv), dtype=torch.float64, device=DEV)
+        S.soap_rv_ccf(d.ctx, sp, case.mask_lambda, case.mask_weight, case.mask_width_kms, lo, step,
+                      nv, rv, fit, ccf)
+        torch.cuda.synchronize()
+    return rv.cpu().numpy(), fit.cpu().numpy(), ccf.cpu().numpy()
+
+
+def test_ccf_and_rv_config1(S, cfg1, cfg1_ref):
+    _, ref = cfg1_ref
+    lo, step, nv = synth.velocity_grid(cfg1.star.vsini_kms)
+    F = ref[0]                                    # oracle spectra as input to both sides
+    rv_o, fit_o, ccf_o = O.rv(F, cfg1.star, cfg1.mask_lambda, cfg1.mask_weight,
+                              cfg1.mask_width_kms, lo, step, nv)
+    rv_g, fit_g, ccf_g = _gpu_rv(S, cfg1, F, lo, step, nv)
+    assert np.abs(ccf_g - ccf_o).max() <= 1e-12 * np.abs(ccf_o).max()
+    assert np.abs(rv_g - rv_o).max() * 1e5 <= 1e-4          # cm/s
+    np.testing.assert_allclose(fit_g, fit_o, rtol=1e-8, atol=1e-10)
+    rv_32, _, ccf_32 = _gpu_rv(S, cfg1, F.astype(np.float32), lo, step, nv)
+    assert np.abs(rv_32 - rv_o).max() * 1e5 <= 1.0
+
+
+def test_ccf_and_rv_fullsize(S, cfg2):
+    c = cfg2
+    lo, step, nv = synth.velocity_grid(c.star.vsini_kms)
+    F = c.quiet[::4]                               # seeded local spectra at full size
+    rv_o, _, ccf_o = O.rv(F, c.star, c.mask_lambda, c.mask_weight, c.mask_width_kms, lo, step, nv)
+    rv_g, _, ccf_g = _gpu_rv(S, c, F, lo, step, nv)
+    assert np.abs(ccf_g - ccf_o).max() <= 1e-12 * np.abs(ccf_o).max()
+    assert np.abs(rv_g - rv_o).max() * 1e5 <= 1e-4
+    rv_32, _, _ = _gpu_rv(S, c, F.astype(np.float32), lo, step, nv)
+    assert np.abs(rv_32 - rv_o).max() * 1e5 <= 1.0
