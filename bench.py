@@ -1,0 +1,365 @@
+#!/usr/bin/env python
+"""Benchmark of the stellar-disk integration (SOAP-GPU hot path, arXiv 2301.04259) on GB300.
+
+Workload: disk 300x300, 3800-6900 A log-uniform at 3 px per R=115000 element (205,800 px),
+20 mu bins, 20k-line synthetic spectra, 1 facula + 2 spots, 100 rotational phases.
+One step = one pass of the whole path over one star: per-cell geometry and quiet velocity
+kernels, local spectra into padded rows, quiet integral, contrast, InfoMap + per-phase
+velocity kernels, Toeplitz contraction with Eqs. 1-4 (total effect) for the 100 phases,
+CCF + Gaussian RV of the 100 spectra.  `value` = active-star spectra/s of the mixed path
+(FP32 contraction, FP64 positions and fit), inputs resident in HBM; `e2e` = the same through
+the C-ABI with host buffers (host->device inputs and device->host spectra + RVs inside the
+timed region).  The FP64 path is timed too.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank integrates its own star (weak scaling, no collective on the path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "active-star spectra/s (300^2 grid, 206k px) and RV error cm/s vs FP64"
+UNIT = "spectra/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--grid", type=int, default=300)
+    ap.add_argument("--n-px", type=int, default=205800)
+    ap.add_argument("--cpu-sample-px", type=int, default=256)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(args, rank):
+    from paper_2301_04259_gb300 import synth
+    if args.n_px == 205800 and args.grid == 300:
+        case = synth.config2(args.seed + rank)
+    else:
+        l1 = 3800.0 * np.exp(np.log(6900.0 / 3800.0) * (args.n_px - 1) / 205799.0)
+        case = synth.config2(args.seed + rank, grid_n=args.grid, n_px=args.n_px, lambda_end=l1)
+    return case
+
+
+# ------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+                except ValueError:
+                    continue
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [r[0] for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[2][k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------------------------------
+# our arm
+# ------------------------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    rank, world, local = dist()
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group(backend="nccl", device_id=torch.device(f"cuda:{local}"))
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    from paper_2301_04259_gb300 import soap as S
+    from paper_2301_04259_gb300 import synth
+
+    case = workload(args, rank)
+    st = case.star
+    P = case.phases.size
+    n_px = st.n_px
+    lo, vstep, nv = synth.velocity_grid(st.vsini_kms)
+    stream = torch.cuda.current_stream()
+    q_dev = torch.from_numpy(case.quiet).to(dev)
+    a_dev = torch.from_numpy(case.active[synth.SPOT]).to(dev)
+    out32 = torch.empty((1, P, n_px), dtype=torch.float32, device=dev)
+    out64 = torch.empty((1, P, n_px), dtype=torch.float64, device=dev)
+    rv32 = torch.empty(P, dtype=torch.float64, device=dev)
+    rv64 = torch.empty(P, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+    ctx = S.soap_init_star(st, q_dev, stream=stream)
+    S.soap_set_active_spectrum(ctx, S.SOAP_SPOT, a_dev)
+
+    def step(prec, out, rv, q=q_dev, a=a_dev):
+        S.soap_update_star(ctx, st)
+        S.soap_set_quiet_spectrum(ctx, q)
+        S.soap_set_active_spectrum(ctx, S.SOAP_SPOT, a)
+        S.soap_active_phases(ctx, case.regions, case.phases, S.SOAP_EFFECT_TOT, prec, out)
+        S.soap_rv_ccf(ctx, out[0], case.mask_lambda, case.mask_weight, case.mask_width_kms,
+                      lo, vstep, nv, rv)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as tdist
+            tdist.barrier()
+
+    def timed(prec, out, rv, K, W, profile=False):
+        for _ in range(W):
+            step(prec, out, rv)
+        torch.cuda.synchronize()
+        S.soap_reset_kernel_times(ctx)
+        S.soap_set_profiling(ctx, profile)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(K)]
+        barrier()
+        torch.cuda.synchronize()
+        l0 = S.soap_get_launch_count(ctx)
+        for k in range(K):
+            flush.fill_(k & 0xFF)                 # evict L2 between steps (not timed)
+            ev[k][0].record(stream)
+            step(prec, out, rv)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        launches = S.soap_get_launch_count(ctx) - l0
+        ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+        timers = {}
+        if profile:
+            for t, name in enumerate(S.TIMERS):
+                tot, n = S.soap_get_kernel_time(ctx, t)
+                timers[name] = (tot, n)
+            S.soap_set_profiling(ctx, False)
+        return ms, launches, timers
+
+    K, W = args.steps, max(3, args.warmup)
+    with ClockSampler(local) as clk:
+        ms32, launches, timers = timed(S.SOAP_FP32, out32, rv32, K, W, profile=True)
+        ms32_plain, launches_plain, _ = timed(S.SOAP_FP32, out32, rv32, K, W)
+        K64 = max(3, K // 4)
+    ms64, _, timers64 = timed(S.SOAP_FP64, out64, rv64, K64, 3, profile=True)
+    clocks = clk.summary()
+    ms_step = ms32_plain
+    # max over ranks
+    if world > 1:
+        import torch.distributed as tdist
+        t = torch.tensor([ms_step, ms64], device=dev, dtype=torch.float64)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        ms_step, ms64 = float(t[0]), float(t[1])
+    value = world * P / (ms_step * 1e-3)
+    value64 = world * P / (ms64 * 1e-3)
+    rv_err = float((rv32 - rv64).abs().max().item() * 1e5)          # cm/s
+
+    # end to end through the C-ABI with host buffers (pinned), copies inside the timed region
+    q_host = torch.from_numpy(case.quiet).pin_memory()
+    a_host = torch.from_numpy(case.active[synth.SPOT]).pin_memory()
+    out_host = torch.empty((1, P, n_px), dtype=torch.float32).pin_memory()
+    rv_host = np.empty(P)
+
+    def step_e2e():
+        S.soap_update_star(ctx, st)
+        S.soap_set_quiet_spectrum(ctx, q_host)
+        S.soap_set_active_spectrum(ctx, S.SOAP_SPOT, a_host)
+        S.soap_active_phases(ctx, case.regions, case.phases, S.SOAP_EFFECT_TOT, S.SOAP_FP32, out_host)
+        S.soap_rv_ccf(ctx, out_host[0], case.mask_lambda, case.mask_weight, case.mask_width_kms,
+                      lo, vstep, nv, rv_host)
+
+    for _ in range(W):
+        step_e2e()
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Ke = max(3, K // 2)
+    for _ in range(Ke):
+        step_e2e()
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / Ke
+    if world > 1:
+        import torch.distributed as tdist
+        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        e2e_ms = float(t[0])
+    # local spectra, mask, phases, regions; soap_rv_ccf reads the host spectra back in
+    h2d = 2 * case.quiet.nbytes + case.mask_lambda.nbytes * 2 + P * 8 + len(case.regions) * 48
+    h2d += P * n_px * 4
+    d2h = P * n_px * 4 + P * 8
+
+    # roofline of the dominant kernel (mixed path)
+    name, (tot, n) = max(timers.items(), key=lambda kv: kv[1][0])
+    per_launch_ms = tot / max(1, n)
+    n_mu = st.n_mu
+    n_class = len({(r.type, r.temp_K) for r in case.regions})
+    bytes_contract = (P * n_px * 4 + 2 * n_mu * n_px * 4 + n_class * n_px * 4 + n_px * 4)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    c_ms, c_n = timers["contract"]
+    c_per = c_ms / max(1, c_n)
+    achieved = bytes_contract / (c_per * 1e-3) / 1e9
+    roofline = {"kernel": "k_contract<float> (Toeplitz contraction, active phases)", "bound": "hbm",
+                "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(achieved / hbm_peak, 4), "traffic": None,
+                "bytes_per_launch": bytes_contract, "ms_per_launch": round(c_per, 5),
+                "peak_source": "measured" if peaks else "fallback",
+                "dominant_kernel": name, "dominant_ms_per_step": round(tot / K, 5)}
+    kernel_ms_per_step = {k: round(v[0] / K, 5) for k, v in timers.items() if v[1]}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(case, args.cpu_sample_px)
+
+    res = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
+           "steps": K, "warmup": W, "ms_per_step": round(ms_step, 5), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic (seeded 20k-line spectra, random-init regions)",
+           "config": {"workload": case.name, "grid": st.grid_n, "n_px": n_px, "n_mu": n_mu,
+                      "phases_per_step": P, "effects": "total (Eq. 3)",
+                      "precision": "FP32 contraction, FP64 positions/weights/fit",
+                      "l2": "flushed between timed steps (256 MB write)",
+                      "parallelism": f"replicas{world}"},
+           "rv_err_cms_vs_fp64": rv_err,
+           "fp64_path": {"value": round(value64, 2), "unit": UNIT, "ms_per_step": round(ms64, 5),
+                         "kernel_ms_per_step": {k: round(v[0] / K64, 5)
+                                                for k, v in timers64.items() if v[1]}},
+           "roofline": roofline, "kernel_ms_per_step": kernel_ms_per_step,
+           "e2e": {"value": round(world * P / (e2e_ms * 1e-3), 2), "unit": UNIT,
+                   "ms_per_step": round(e2e_ms, 4), "h2d_bytes_per_step": int(h2d),
+                   "d2h_bytes_per_step": int(d2h)},
+           "gpu_launches": int(launches_plain), "clocks": clocks}
+    if cpu is not None:
+        res["cpu_baseline"] = cpu
+    S.soap_free(ctx)
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.destroy_process_group()
+
+
+# ------------------------------------------------------------------------------------------
+# CPU oracle (cpu_baseline leg and the reference arm)
+# ------------------------------------------------------------------------------------------
+def oracle_step_seconds(case, n_sample, seed):
+    """Oracle time for one step's worth of work, from a pixel sample of the spectra and two
+    of the RV fits, scaled to all pixels and all phases."""
+    from oracle import oracle as O
+    from paper_2301_04259_gb300 import synth
+    st = case.star
+    rng = np.random.default_rng(seed)
+    pix = np.sort(rng.choice(st.n_px, n_sample, replace=False)).astype(np.int64)
+    t0 = time.perf_counter()
+    O.active(st, case.quiet, case.active, case.regions, case.phases, effects=1, pix=pix)
+    t_spec = (time.perf_counter() - t0) * st.n_px / n_sample
+    lo, vstep, nv = synth.velocity_grid(st.vsini_kms)
+    t0 = time.perf_counter()
+    O.rv(case.quiet[:2], st, case.mask_lambda, case.mask_weight, case.mask_width_kms, lo, vstep, nv)
+    t_rv = (time.perf_counter() - t0) * case.phases.size / 2
+    return t_spec + t_rv
+
+
+def cpu_baseline(case, n_sample):
+    from oracle import oracle as O
+    t = oracle_step_seconds(case, n_sample, 1)
+    P = case.phases.size
+    return {"value": round(P / t, 5), "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"{n_sample} of {case.star.n_px} px for all {P} phases + 2 of {P} CCF/RV fits, "
+                      f"scaled to the full step ({t:.1f} s per {P} spectra)"}
+
+
+def run_reference(args):
+    rank, world, local = dist()
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    case = workload(args, 0)
+    P = case.phases.size
+    n_sample = max(8, args.cpu_sample_px // 4)
+    for k in range(max(0, args.warmup)):
+        oracle_step_seconds(case, 8, 100 + k)
+    times = [oracle_step_seconds(case, n_sample, k) for k in range(args.steps)]
+    t = float(np.mean(times))
+    value = P / t
+    res = {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": UNIT,
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t * 1e3, 2),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": case.name, "grid": case.star.grid_n,
+                                           "n_px": case.star.n_px, "phases_per_step": P},
+           "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": O.num_threads(),
+                            "kind": "oracle",
+                            "sample": f"per step {n_sample} px of all {P} phases + 2 RV fits, scaled"},
+           "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(res), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -132,6 +132,21 @@ typedef struct {
     double temp_K;
 } soap_region;
 
+/* Kernel timers (soap_set_profiling / soap_get_kernel_time). */
+typedef enum {
+    SOAP_TIMER_GEOMETRY = 0,     /* per-cell geometry + quiet velocity kernels */
+    SOAP_TIMER_PAD_ROWS = 1,     /* local spectra -> replicate-padded rows */
+    SOAP_TIMER_CONTRAST = 2,     /* Planck contrast per region class */
+    SOAP_TIMER_PHASE_HIST = 3,   /* InfoMap + per-phase velocity kernels */
+    SOAP_TIMER_JOBS = 4,         /* job tables of the contraction */
+    SOAP_TIMER_CONTRACT = 5,     /* Toeplitz contraction, active phases */
+    SOAP_TIMER_CONTRACT_QUIET = 6, /* Toeplitz contraction, quiet star */
+    SOAP_TIMER_DIRECT = 7,       /* direct-form disk sum (+ split reduction) */
+    SOAP_TIMER_CCF = 8,          /* CCF partial sums + reduction */
+    SOAP_TIMER_FIT = 9,          /* Gaussian fits */
+    SOAP_TIMER_COUNT = 10
+} soap_timer;
+
 /* Read-only facts about an initialised star. */
 typedef struct {
     int64_t n_visible;      /* visible cells */
@@ -159,6 +174,16 @@ typedef struct soap_ctx soap_ctx;
 soap_status soap_init_star(const soap_star_desc* star, const double* quiet_local,
                            int quiet_on_device, void* cuda_stream, soap_ctx** out);
 
+/* Recompute the disk geometry of an existing context for new stellar parameters (vsini,
+ * inclination, limb darkening, differential rotation, t_quiet, mu values).  grid_n, n_mu, n_px
+ * and the wavelength range must equal those of soap_init_star; the new velocity kernels must
+ * fit the padding chosen then (SOAP_ERANGE otherwise: create a new context).  Local spectra are
+ * kept (their nearest-mu assignment follows the new mu values). */
+soap_status soap_update_star(soap_ctx* ctx, const soap_star_desc* star);
+
+/* Replace the quiet local spectra ([n_mu][n_px] float64, host or device). */
+soap_status soap_set_quiet_spectrum(soap_ctx* ctx, const double* quiet_local, int on_device);
+
 /* Upload the active-region local spectra of one region type (Sect. 2.1: S_active).
  *  type          SOAP_SPOT or SOAP_FACULA.  Until a facula spectrum is set, faculae use the
  *                spot spectrum (as SOAP 2.0 did).
@@ -169,11 +194,12 @@ soap_status soap_set_active_spectrum(soap_ctx* ctx, int32_t type, const double* 
 /* Replace the context's stream (cudaStream_t or NULL). */
 soap_status soap_set_stream(soap_ctx* ctx, void* cuda_stream);
 
-/* Block until all work of the context's stream has finished. */
+/* Block until all work of the context's stream has finished; then report any condition the
+ * kernels flagged (SOAP_ERANGE) since the last check. */
 soap_status soap_synchronize(soap_ctx* ctx);
 
 /* Fill *out with facts about the star. */
-soap_status soap_get_star_info(const soap_ctx* ctx, soap_star_info* out);
+soap_status soap_get_star_info(soap_ctx* ctx, soap_star_info* out);
 
 /* Integrated quiet spectrum (Alg. 1 / Alg. 4): F_q[m] = sum_c I_c S'_c[m].
  *  form       SOAP_FORM_TOEPLITZ or SOAP_FORM_DIRECT (same result up to rounding).
@@ -216,6 +242,17 @@ soap_status soap_rv_ccf(soap_ctx* ctx, const void* spectra, int32_t spectra_f32,
                         const double* mask_weight, int32_t n_lines, double mask_width_kms,
                         double v_lo, double v_step, int32_t n_v, double* rv_kms,
                         double* fit_params, double* ccf_out, int out_on_device);
+
+/* Enable (1) or disable (0) per-kernel timing: while enabled, the main kernels of every call
+ * are bracketed by CUDA events on the context's stream. */
+soap_status soap_set_profiling(soap_ctx* ctx, int enabled);
+
+/* Total device time (ms) and number of timed launches of one timer since the last reset.
+ * Synchronises the context's stream.  timer: a soap_timer value. */
+soap_status soap_get_kernel_time(soap_ctx* ctx, int32_t timer, double* total_ms, uint64_t* launches);
+
+/* Zero all timers. */
+soap_status soap_reset_kernel_times(soap_ctx* ctx);
 
 /* Number of kernels this context has launched so far (for launch accounting). */
 soap_status soap_get_launch_count(const soap_ctx* ctx, uint64_t* out);

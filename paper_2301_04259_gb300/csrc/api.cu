@@ -83,7 +83,8 @@ static soap_status to_device(soap_ctx* c, void* dst, const void* src, size_t n, 
 
 static void free_ctx_memory(soap_ctx* c) {
     void* ptrs[] = {c->cell_I, c->cell_w, c->cell_mu, c->cell_j, c->cell_bin, c->flags, c->q64,
-                    c->q32, c->a64[0], c->a32[0], c->a64[1], c->a32[1], c->kq_fixed};
+                    c->q32, c->a64[0], c->a32[0], c->a64[1], c->a32[1], c->kq_fixed,
+                    c->sum_I_fixed};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     DevBuf* bufs[] = {&c->stage_in, &c->fq, &c->contrast, &c->kphase, &c->jobs, &c->coefs,
@@ -110,6 +111,7 @@ static soap_status check_flags(soap_ctx* c) {
     SOAP_CUDA(cudaMemcpyAsync(&f, c->flags, sizeof(f), cudaMemcpyDeviceToHost, c->stream));
     SOAP_CUDA(cudaStreamSynchronize(c->stream));
     if (f) {
+        cudaMemsetAsync(c->flags, 0, sizeof(unsigned int), c->stream);
         set_error("device status word 0x%x (tap range %d, box range %d, job overflow %d)", f,
                   !!(f & kFlagTapRange), !!(f & kFlagBoxRange), !!(f & kFlagJobOverflow));
         return SOAP_ERANGE;
@@ -117,20 +119,62 @@ static soap_status check_flags(soap_ctx* c) {
     return SOAP_OK;
 }
 
-}  // namespace soap
+cudaEvent_t timer_begin(soap_ctx* c) {
+    cudaEvent_t e = nullptr;
+    if (!c->event_pool.empty()) {
+        e = c->event_pool.back();
+        c->event_pool.pop_back();
+    } else if (cudaEventCreate(&e) != cudaSuccess) {
+        return nullptr;
+    }
+    cudaEventRecord(e, c->stream);
+    return e;
+}
 
-using namespace soap;
+void timer_end(soap_ctx* c, int timer, cudaEvent_t begin) {
+    if (!begin) return;
+    cudaEvent_t e = nullptr;
+    if (!c->event_pool.empty()) {
+        e = c->event_pool.back();
+        c->event_pool.pop_back();
+    } else if (cudaEventCreate(&e) != cudaSuccess) {
+        c->event_pool.push_back(begin);
+        return;
+    }
+    cudaEventRecord(e, c->stream);
+    c->pending.push_back({timer, begin, e});
+}
 
-extern "C" {
+static soap_status fold_timers(soap_ctx* c) {
+    if (c->pending.empty()) return SOAP_OK;
+    SOAP_CUDA(cudaStreamSynchronize(c->stream));
+    for (auto& t : c->pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) {
+            c->timer_ms[t.timer] += ms;
+            c->timer_n[t.timer] += 1;
+        }
+        c->event_pool.push_back(t.a);
+        c->event_pool.push_back(t.b);
+    }
+    c->pending.clear();
+    return SOAP_OK;
+}
 
-const char* soap_last_error(void) { return g_error; }
+static void destroy_events(soap_ctx* c) {
+    for (auto& t : c->pending) {
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
+    }
+    c->pending.clear();
+    for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
+    c->event_pool.clear();
+}
 
-soap_status soap_init_star(const soap_star_desc* s, const double* quiet_local, int quiet_on_device,
-                           void* cuda_stream, soap_ctx** out) {
-    clear_error();
-    if (!out) { set_error("out is NULL"); return SOAP_EINVAL; }
-    *out = nullptr;
-    if (!s || !quiet_local) { set_error("star or quiet_local is NULL"); return SOAP_EINVAL; }
+// Validate a star description; fills delta and the tap range.
+static soap_status check_star(const soap_star_desc* s, double* delta_out, int64_t* tmin_out,
+                              int64_t* tmax_out) {
+    if (!s) { set_error("star is NULL"); return SOAP_EINVAL; }
     if (s->grid_n < 1 || s->grid_n > 8192) { set_error("grid_n=%d outside 1..8192", s->grid_n); return SOAP_EINVAL; }
     if (s->n_mu < 1 || s->n_mu > SOAP_MAX_MU) { set_error("n_mu=%d outside 1..%d", s->n_mu, SOAP_MAX_MU); return SOAP_ERANGE; }
     if (s->n_px < 2 || s->n_px > (int64_t(1) << 28)) { set_error("n_px=%lld outside 2..2^28", (long long)s->n_px); return SOAP_EINVAL; }
@@ -154,30 +198,58 @@ soap_status soap_init_star(const soap_star_desc* s, const double* quiet_local, i
     double delta = std::log1p((s->lambda_end_A - s->lambda_start_A) / s->lambda_start_A) / (double)(s->n_px - 1);
     if (!(delta > 0) || !is_finite(delta)) { set_error("grid step Delta not positive"); return SOAP_EINVAL; }
     double smax = std::atanh(vmax / kCKms) / delta;
+    if (!(smax < 1e6)) { set_error("velocity shift too large for the pixel size"); return SOAP_ERANGE; }
     int64_t tmax = (int64_t)std::ceil(smax) + 1, tmin = (int64_t)std::floor(-smax) - 1;
     if (tmax - tmin + 1 > SOAP_MAX_TAPS) {
         set_error("velocity kernel needs %lld taps > %d (vsini too large for the pixel size)",
                   (long long)(tmax - tmin + 1), SOAP_MAX_TAPS);
         return SOAP_ERANGE;
     }
+    *delta_out = delta;
+    *tmin_out = tmin;
+    *tmax_out = tmax;
+    return SOAP_OK;
+}
+
+static void set_star_params(soap_ctx* c, const soap_star_desc* s) {
+    c->vsini = s->vsini_kms; c->incl_deg = s->incl_deg; c->u1 = s->u1; c->u2 = s->u2;
+    c->alpha = s->diff_rot_alpha; c->t_quiet = s->t_quiet_K;
+    for (int b = 0; b < s->n_mu; b++) c->mu_values[b] = s->mu_values[b];
+    // fixed-point kernels: every partial sum is bounded by sum |I| <= 4 (1 + |u1| + |u2|)
+    double bound = 4.0 * (1.0 + std::fabs(s->u1) + std::fabs(s->u2));
+    c->fx_bits = 61 - (int)std::ceil(std::log2(bound));
+}
+
+}  // namespace soap
+
+using namespace soap;
+
+extern "C" {
+
+const char* soap_last_error(void) { return g_error; }
+
+soap_status soap_init_star(const soap_star_desc* s, const double* quiet_local, int quiet_on_device,
+                           void* cuda_stream, soap_ctx** out) {
+    clear_error();
+    if (!out) { set_error("out is NULL"); return SOAP_EINVAL; }
+    *out = nullptr;
+    if (!s || !quiet_local) { set_error("star or quiet_local is NULL"); return SOAP_EINVAL; }
+    double delta = 0;
+    int64_t tmin = 0, tmax = 0;
+    SOAP_TRY(check_star(s, &delta, &tmin, &tmax));
 
     soap_ctx* c = new (std::nothrow) soap_ctx();
     if (!c) { set_error("out of host memory"); return SOAP_ENOMEM; }
     cudaGetDevice(&c->device);
     c->stream = (cudaStream_t)cuda_stream;
     c->N = s->grid_n; c->n_mu = s->n_mu; c->n_px = s->n_px;
-    c->vsini = s->vsini_kms; c->incl_deg = s->incl_deg; c->u1 = s->u1; c->u2 = s->u2;
-    c->alpha = s->diff_rot_alpha; c->lam_s = s->lambda_start_A; c->lam_e = s->lambda_end_A;
-    c->t_quiet = s->t_quiet_K; c->delta = delta;
-    for (int b = 0; b < s->n_mu; b++) c->mu_values[b] = s->mu_values[b];
+    c->lam_s = s->lambda_start_A; c->lam_e = s->lambda_end_A; c->delta = delta;
+    set_star_params(c, s);
     c->tap_min = (int)tmin;
     c->n_taps = (int)(tmax - tmin + 1);
     int64_t need = std::max<int64_t>(tmax, -tmin) + 1;
     c->pad = round_up(need, 32);
     c->row_len = round_up(c->n_px + 2 * c->pad, 32);
-    // fixed-point kernels: every partial sum is bounded by sum |I| <= 4 (1 + |u1| + |u2|)
-    double bound = 4.0 * (1.0 + std::fabs(s->u1) + std::fabs(s->u2));
-    c->fx_bits = 61 - (int)std::ceil(std::log2(bound));
 
     soap_status st = SOAP_OK;
     size_t NN = (size_t)c->N * c->N;
@@ -192,7 +264,8 @@ soap_status soap_init_star(const soap_star_desc* s, const double* quiet_local, i
     ALLOC(c->flags, sizeof(unsigned int));
     ALLOC(c->q64, rows * sizeof(double));
     ALLOC(c->q32, rows * sizeof(float));
-    ALLOC(c->kq_fixed, (size_t)c->n_mu * c->n_taps * sizeof(long long));
+    ALLOC(c->kq_fixed, (size_t)c->n_mu * SOAP_MAX_TAPS * sizeof(long long));
+    ALLOC(c->sum_I_fixed, 2 * sizeof(long long));
 #undef ALLOC
     if (e != cudaSuccess) {
         set_error("device allocation failed: %s", cudaGetErrorString(e));
@@ -212,6 +285,58 @@ soap_status soap_init_star(const soap_star_desc* s, const double* quiet_local, i
         return st;
     }
     *out = c;
+    return SOAP_OK;
+}
+
+soap_status soap_update_star(soap_ctx* c, const soap_star_desc* s) {
+    clear_error();
+    if (!c || !s) { set_error("ctx or star is NULL"); return SOAP_EINVAL; }
+    double delta = 0;
+    int64_t tmin = 0, tmax = 0;
+    SOAP_TRY(check_star(s, &delta, &tmin, &tmax));
+    if (s->grid_n != c->N || s->n_mu != c->n_mu || s->n_px != c->n_px ||
+        s->lambda_start_A != c->lam_s || s->lambda_end_A != c->lam_e) {
+        set_error("soap_update_star cannot change grid_n, n_mu, n_px or the wavelength range");
+        return SOAP_EINVAL;
+    }
+    if (std::max<int64_t>(tmax, -tmin) + 1 > c->pad) {
+        set_error("the new velocity kernels need more row padding than this context has");
+        return SOAP_ERANGE;
+    }
+    set_star_params(c, s);
+    c->tap_min = (int)tmin;
+    c->n_taps = (int)(tmax - tmin + 1);
+    return geometry_init(c);
+}
+
+soap_status soap_set_quiet_spectrum(soap_ctx* c, const double* quiet_local, int on_device) {
+    clear_error();
+    if (!c || !quiet_local) { set_error("ctx or quiet_local is NULL"); return SOAP_EINVAL; }
+    return upload_spectra(c, quiet_local, on_device, c->q64, c->q32);
+}
+
+soap_status soap_set_profiling(soap_ctx* c, int enabled) {
+    clear_error();
+    if (!c) { set_error("ctx is NULL"); return SOAP_EINVAL; }
+    c->profiling = enabled != 0;
+    return SOAP_OK;
+}
+
+soap_status soap_get_kernel_time(soap_ctx* c, int32_t timer, double* total_ms, uint64_t* launches) {
+    clear_error();
+    if (!c || !total_ms || !launches) { set_error("NULL argument"); return SOAP_EINVAL; }
+    if (timer < 0 || timer >= SOAP_TIMER_COUNT) { set_error("unknown timer %d", timer); return SOAP_EINVAL; }
+    SOAP_TRY(fold_timers(c));
+    *total_ms = c->timer_ms[timer];
+    *launches = c->timer_n[timer];
+    return SOAP_OK;
+}
+
+soap_status soap_reset_kernel_times(soap_ctx* c) {
+    clear_error();
+    if (!c) { set_error("ctx is NULL"); return SOAP_EINVAL; }
+    SOAP_TRY(fold_timers(c));
+    for (int k = 0; k < SOAP_TIMER_COUNT; k++) { c->timer_ms[k] = 0; c->timer_n[k] = 0; }
     return SOAP_OK;
 }
 
@@ -244,13 +369,17 @@ soap_status soap_set_stream(soap_ctx* c, void* stream) {
 soap_status soap_synchronize(soap_ctx* c) {
     clear_error();
     if (!c) { set_error("ctx is NULL"); return SOAP_EINVAL; }
-    SOAP_CUDA(cudaStreamSynchronize(c->stream));
-    return SOAP_OK;
+    return check_flags(c);
 }
 
-soap_status soap_get_star_info(const soap_ctx* c, soap_star_info* out) {
+soap_status soap_get_star_info(soap_ctx* c, soap_star_info* out) {
     clear_error();
     if (!c || !out) { set_error("ctx or out is NULL"); return SOAP_EINVAL; }
+    long long h2[2] = {0, 0};
+    SOAP_CUDA(cudaMemcpyAsync(h2, c->sum_I_fixed, sizeof(h2), cudaMemcpyDeviceToHost, c->stream));
+    SOAP_TRY(check_flags(c));
+    c->total_I = std::ldexp((double)h2[0], -c->fx_bits);
+    c->n_visible = h2[1];
     memset(out, 0, sizeof(*out));
     out->n_visible = c->n_visible;
     out->tap_min = c->tap_min;
@@ -411,6 +540,7 @@ soap_status soap_rv_ccf(soap_ctx* c, const void* spectra, int32_t spectra_f32, i
 void soap_free(soap_ctx* c) {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
+    destroy_events(c);
     free_ctx_memory(c);
     delete c;
 }

@@ -234,6 +234,7 @@ soap_status rv_ccf_run(soap_ctx* c, const void* spectra_dev, int f32, int n_spec
     double* d_ccf = ccf_dev ? ccf_dev : (double*)(base + off_c);
     SOAP_CUDA(cudaMemcpyAsync(d_lam, mask_lambda, (size_t)n_lines * 8, cudaMemcpyHostToDevice, c->stream));
     SOAP_CUDA(cudaMemcpyAsync(d_w, mask_weight, (size_t)n_lines * 8, cudaMemcpyHostToDevice, c->stream));
+    cudaEvent_t tb = c->profiling ? timer_begin(c) : nullptr;
     const double h = width_kms / (2.0 * kCKms * c->delta);
     const double v_hi = v_lo + v_step * (n_v - 1);
     k_ccf_lines<<<(n_lines + 255) / 256, 256, 0, c->stream>>>(
@@ -260,10 +261,12 @@ soap_status rv_ccf_run(soap_ctx* c, const void* spectra_dev, int f32, int n_spec
     if (g > 152 * 8) g = 152 * 8;
     k_ccf_reduce<<<g, 256, 0, c->stream>>>(n_chunks, n_spec, n_v, d_part, d_ccf);
     SOAP_LAUNCHED(c);
+    if (c->profiling) timer_end(c, SOAP_TIMER_CCF, tb);
     int warps_per_block = 4;
-    k_gauss_fit<<<(n_spec + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, c->stream>>>(
-        n_spec, n_v, v_lo, v_step, d_ccf, rv_dev, fit_dev);
-    SOAP_LAUNCHED(c);
+    SOAP_TIMED(c, SOAP_TIMER_FIT,
+               k_gauss_fit<<<(n_spec + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0,
+                             c->stream>>>(n_spec, n_v, v_lo, v_step, d_ccf, rv_dev, fit_dev);
+               SOAP_LAUNCHED(c));
     return SOAP_OK;
 }
 

@@ -371,10 +371,11 @@ static soap_status launch_contract(soap_ctx* c, int n_blocks, int G, int max_job
     rows.q = q; rows.a[0] = a0; rows.a[1] = a1;
     int64_t tiles = (c->n_px + (int64_t)THREADS * R - 1) / ((int64_t)THREADS * R);
     dim3 grid((unsigned)tiles, (unsigned)n_blocks, (unsigned)n_eff);
-    k_contract<T, PB, R, THREADS><<<grid, THREADS, 0, c->stream>>>(
-        c->n_px, c->row_len, c->pad, rows, jobs, gstart, G, max_jobs, coefs, max_coef, ct,
-        contrast, fq, n_phases, el, out);
-    SOAP_LAUNCHED(c);
+    SOAP_TIMED(c, fq ? SOAP_TIMER_CONTRACT : SOAP_TIMER_CONTRACT_QUIET,
+               k_contract<T, PB, R, THREADS><<<grid, THREADS, 0, c->stream>>>(
+                   c->n_px, c->row_len, c->pad, rows, jobs, gstart, G, max_jobs, coefs, max_coef, ct,
+                   contrast, fq, n_phases, el, out);
+               SOAP_LAUNCHED(c));
     return SOAP_OK;
 }
 
@@ -402,10 +403,11 @@ static soap_status build_jobs(soap_ctx* c, const long long* kfix, int n_phases, 
     *c64 = c->coefs.as<double>();
     *c32 = (float*)(c->coefs.as<char>() + off32);
     double inv_scale = std::ldexp(1.0, -c->fx_bits);
-    k_build_jobs<<<*n_blocks, 128, 0, c->stream>>>(kfix, n_phases, mode == 0 ? 1 : n_class, c->n_mu,
-                                                  c->n_taps, c->tap_min, PB, mode, inv_scale, *jobs,
-                                                  *gstart, *c64, *c32, *max_jobs, *max_coef, c->flags);
-    SOAP_LAUNCHED(c);
+    SOAP_TIMED(c, SOAP_TIMER_JOBS,
+               k_build_jobs<<<*n_blocks, 128, 0, c->stream>>>(
+                   kfix, n_phases, mode == 0 ? 1 : n_class, c->n_mu, c->n_taps, c->tap_min, PB, mode,
+                   inv_scale, *jobs, *gstart, *c64, *c32, *max_jobs, *max_coef, c->flags);
+               SOAP_LAUNCHED(c));
     return SOAP_OK;
 }
 
@@ -440,9 +442,10 @@ soap_status toeplitz_active(soap_ctx* c, const RegionDev* regions_host, int n_re
     if (n_class > 0) {
         ClassTemps tt{};
         for (int k = 0; k < n_class; k++) tt.t[k] = class_temp[k];
-        k_contrast<<<grid_cap(c->n_px, 256, 152 * 8), 256, 0, c->stream>>>(
-            c->n_px, c->lam_s, c->delta, c->t_quiet, n_class, tt, con64, con32);
-        SOAP_LAUNCHED(c);
+        SOAP_TIMED(c, SOAP_TIMER_CONTRAST,
+                   k_contrast<<<grid_cap(c->n_px, 256, 152 * 8), 256, 0, c->stream>>>(
+                       c->n_px, c->lam_s, c->delta, c->t_quiet, n_class, tt, con64, con32);
+                   SOAP_LAUNCHED(c));
     }
     // regions and phases to the device (pageable copies are staged by the driver at once)
     size_t rbytes = (size_t)(n_regions > 0 ? n_regions : 1) * sizeof(RegionDev);
@@ -466,11 +469,12 @@ soap_status toeplitz_active(soap_ctx* c, const RegionDev* regions_host, int n_re
     } else if (smem > 48 * 1024) {
         SOAP_CUDA(cudaFuncSetAttribute(k_phase_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     }
-    k_phase_hist<<<n_phases, 256, smem, c->stream>>>(
-        c->N, n_regions, c->regions.as<RegionDev>(), c->phases.as<double>(), c->incl_deg, c->alpha,
-        c->cell_I, c->cell_w, c->cell_mu, c->cell_j, c->cell_bin, c->tap_min, c->n_taps, c->n_mu,
-        ncl, std::ldexp(1.0, c->fx_bits), kfix, use_smem, c->flags);
-    SOAP_LAUNCHED(c);
+    SOAP_TIMED(c, SOAP_TIMER_PHASE_HIST,
+               k_phase_hist<<<n_phases, 256, smem, c->stream>>>(
+                   c->N, n_regions, c->regions.as<RegionDev>(), c->phases.as<double>(), c->incl_deg,
+                   c->alpha, c->cell_I, c->cell_w, c->cell_mu, c->cell_j, c->cell_bin, c->tap_min,
+                   c->n_taps, c->n_mu, ncl, std::ldexp(1.0, c->fx_bits), kfix, use_smem, c->flags);
+               SOAP_LAUNCHED(c));
     // job tables
     const int PB = f64 ? kPB64 : kPB32;
     Job* jobs; int* gstart; double* c64; float* c32; int nbk, G, mj, mc;

@@ -91,6 +91,7 @@ static soap_status run_direct(soap_ctx* c, const T* rows, T* dst) {
     per = (per + CHUNK - 1) / CHUNK * CHUNK;
     splits = (NN + per - 1) / per;
     SOAP_TRY(ensure(c->partial, (size_t)splits * c->n_px * sizeof(double)));
+    cudaEvent_t tb = c->profiling ? timer_begin(c) : nullptr;
     dim3 grid((unsigned)tiles, (unsigned)splits);
     k_direct<T, R, THREADS, CHUNK><<<grid, THREADS, 0, c->stream>>>(
         NN, per, c->cell_I, c->cell_w, c->cell_j, c->cell_bin, rows, c->row_len, c->pad, c->n_px,
@@ -100,6 +101,7 @@ static soap_status run_direct(soap_ctx* c, const T* rows, T* dst) {
     if (g > 152 * 8) g = 152 * 8;
     k_reduce_splits<T><<<(unsigned)g, 256, 0, c->stream>>>(c->n_px, (int)splits, c->partial.as<double>(), dst);
     SOAP_LAUNCHED(c);
+    if (c->profiling) timer_end(c, SOAP_TIMER_DIRECT, tb);
     return SOAP_OK;
 }
 

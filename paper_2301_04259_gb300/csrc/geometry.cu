@@ -137,9 +137,10 @@ static int grid_for(int64_t n, int threads, int cap = 152 * 16) {
 
 soap_status pad_rows(soap_ctx* c, const double* src, double* dst64, float* dst32, int rows) {
     int64_t total = (int64_t)rows * c->row_len;
-    k_pad_rows<<<grid_for(total, 256), 256, 0, c->stream>>>(src, c->n_px, c->pad, c->row_len, rows,
-                                                            dst64, dst32);
-    SOAP_LAUNCHED(c);
+    SOAP_TIMED(c, SOAP_TIMER_PAD_ROWS,
+               k_pad_rows<<<grid_for(total, 256), 256, 0, c->stream>>>(src, c->n_px, c->pad, c->row_len,
+                                                                       rows, dst64, dst32);
+               SOAP_LAUNCHED(c));
     return SOAP_OK;
 }
 
@@ -149,6 +150,7 @@ soap_status geometry_init(soap_ctx* c) {
     double incl = c->incl_deg * (kPi / 180.0);
     int64_t NN = (int64_t)c->N * c->N;
     int tap_max = c->tap_min + c->n_taps - 1;
+    cudaEvent_t tb = c->profiling ? timer_begin(c) : nullptr;
     k_cell_geometry<<<grid_for(NN, 256), 256, 0, c->stream>>>(
         c->N, c->vsini, std::sin(incl), std::cos(incl), c->alpha, c->u1, c->u2, c->delta,
         std::expm1(c->delta), c->n_mu, mus, c->tap_min, tap_max, c->cell_I, c->cell_w, c->cell_mu,
@@ -165,17 +167,12 @@ soap_status geometry_init(soap_ctx* c) {
     k_quiet_hist<<<g, 256, smem, c->stream>>>(NN, c->cell_I, c->cell_w, c->cell_j, c->cell_bin,
                                               c->tap_min, c->n_taps, c->n_mu, scale, c->kq_fixed);
     SOAP_LAUNCHED(c);
-    // visible-cell count and total intensity (for soap_get_star_info)
-    SOAP_TRY(ensure(c->partial, 2 * sizeof(long long)));
-    long long* d2 = c->partial.as<long long>();
+    // visible-cell count and total intensity (read by soap_get_star_info)
+    long long* d2 = c->sum_I_fixed;
     SOAP_CUDA(cudaMemsetAsync(d2, 0, 2 * sizeof(long long), c->stream));
     k_sum_intensity<<<grid_for(NN, 256, 152 * 4), 256, 0, c->stream>>>(NN, c->cell_I, c->cell_bin, scale, d2);
     SOAP_LAUNCHED(c);
-    long long h2[2];
-    SOAP_CUDA(cudaMemcpyAsync(h2, d2, sizeof(h2), cudaMemcpyDeviceToHost, c->stream));
-    SOAP_CUDA(cudaStreamSynchronize(c->stream));
-    c->total_I = std::ldexp((double)h2[0], -c->fx_bits);
-    c->n_visible = h2[1];
+    if (c->profiling) timer_end(c, SOAP_TIMER_GEOMETRY, tb);
     return SOAP_OK;
 }
 

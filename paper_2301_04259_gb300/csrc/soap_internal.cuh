@@ -10,6 +10,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <string>
+#include <vector>
 
 #include "soap.h"
 
@@ -40,6 +41,15 @@ void clear_error();
                               __FILE__, __LINE__);                                       \
             return SOAP_ECUDA;                                                           \
         }                                                                                \
+    } while (0)
+
+// Bracket the launches in __VA_ARGS__ with CUDA events when the context is profiling.
+#define SOAP_TIMED(ctx, timer, ...)                                                      \
+    do {                                                                                 \
+        cudaEvent_t a__ = nullptr;                                                       \
+        if ((ctx)->profiling) a__ = ::soap::timer_begin(ctx);                             \
+        __VA_ARGS__;                                                                     \
+        if ((ctx)->profiling) ::soap::timer_end(ctx, timer, a__);                         \
     } while (0)
 
 #define SOAP_LAUNCHED(ctx)                                                               \
@@ -117,6 +127,7 @@ struct soap_ctx {
 
     // quiet velocity kernels, fixed point [n_mu][n_taps]
     long long* kq_fixed = nullptr;
+    long long* sum_I_fixed = nullptr;   // [0] sum of I (fixed point), [1] visible cells
 
     // scratch (grow-only)
     soap::DevBuf stage_in;      // host -> device staging of spectra
@@ -133,9 +144,21 @@ struct soap_ctx {
     soap::HostBuf host_stage;
 
     uint64_t launches = 0;
+
+    // per-kernel timers
+    bool profiling = false;
+    struct TimedLaunch { int timer; cudaEvent_t a, b; };
+    std::vector<TimedLaunch> pending;   // recorded, not yet folded into the totals
+    std::vector<cudaEvent_t> event_pool; // free events
+    double timer_ms[SOAP_TIMER_COUNT] = {};
+    uint64_t timer_n[SOAP_TIMER_COUNT] = {};
 };
 
 namespace soap {
+
+// timers (api.cu)
+cudaEvent_t timer_begin(soap_ctx* c);
+void timer_end(soap_ctx* c, int timer, cudaEvent_t begin);
 
 // ---------------------------------------------------------------------------------------
 // kernels and launchers implemented in the .cu files

@@ -24,6 +24,11 @@ SOAP_FORM_TOEPLITZ, SOAP_FORM_DIRECT = 0, 1
 SOAP_EFFECT_TOT, SOAP_EFFECT_FLUX, SOAP_EFFECT_BCONV = 1, 2, 4
 SOAP_SPOT, SOAP_FACULA = 1, 2
 SOAP_MAX_REGIONS, SOAP_MAX_CLASSES, SOAP_MAX_MU, SOAP_MAX_TAPS = 64, 8, 64, 256
+TIMERS = ("geometry", "pad_rows", "contrast", "phase_hist", "jobs", "contract", "contract_quiet",
+          "direct", "ccf", "fit")
+(SOAP_TIMER_GEOMETRY, SOAP_TIMER_PAD_ROWS, SOAP_TIMER_CONTRAST, SOAP_TIMER_PHASE_HIST,
+ SOAP_TIMER_JOBS, SOAP_TIMER_CONTRACT, SOAP_TIMER_CONTRACT_QUIET, SOAP_TIMER_DIRECT,
+ SOAP_TIMER_CCF, SOAP_TIMER_FIT) = range(10)
 
 
 class soap_star_desc(ctypes.Structure):
@@ -62,6 +67,11 @@ def _load():
     sig = {
         "soap_init_star": (i32, [ctypes.POINTER(soap_star_desc), P, ctypes.c_int, P, ctypes.POINTER(P)]),
         "soap_set_active_spectrum": (i32, [P, i32, P, ctypes.c_int]),
+        "soap_update_star": (i32, [P, ctypes.POINTER(soap_star_desc)]),
+        "soap_set_quiet_spectrum": (i32, [P, P, ctypes.c_int]),
+        "soap_set_profiling": (i32, [P, ctypes.c_int]),
+        "soap_get_kernel_time": (i32, [P, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64)]),
+        "soap_reset_kernel_times": (i32, [P]),
         "soap_set_stream": (i32, [P, P]),
         "soap_synchronize": (i32, [P]),
         "soap_get_star_info": (i32, [P, ctypes.POINTER(soap_star_info)]),
@@ -134,6 +144,33 @@ def soap_init_star(star, quiet_local, stream=None) -> ctypes.c_void_p:
     _check(_lib.soap_init_star(ctypes.byref(d), ptr, dev, _stream_handle(stream), ctypes.byref(out)),
            "soap_init_star")
     return out
+
+
+def soap_update_star(ctx, star) -> None:
+    d = star_desc(star)
+    _check(_lib.soap_update_star(ctx, ctypes.byref(d)), "soap_update_star")
+
+
+def soap_set_quiet_spectrum(ctx, quiet_local) -> None:
+    ptr, dev = _ptr(quiet_local)
+    _check(_lib.soap_set_quiet_spectrum(ctx, ptr, dev), "soap_set_quiet_spectrum")
+
+
+def soap_set_profiling(ctx, enabled: bool) -> None:
+    _check(_lib.soap_set_profiling(ctx, int(bool(enabled))), "soap_set_profiling")
+
+
+def soap_get_kernel_time(ctx, timer: int):
+    """(total device ms, launches) of one timer since the last reset."""
+    ms = ctypes.c_double()
+    n = ctypes.c_uint64()
+    _check(_lib.soap_get_kernel_time(ctx, int(timer), ctypes.byref(ms), ctypes.byref(n)),
+           "soap_get_kernel_time")
+    return float(ms.value), int(n.value)
+
+
+def soap_reset_kernel_times(ctx) -> None:
+    _check(_lib.soap_reset_kernel_times(ctx), "soap_reset_kernel_times")
 
 
 def soap_set_active_spectrum(ctx, type_: int, active_local) -> None:
