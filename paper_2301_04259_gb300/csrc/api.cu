@@ -215,6 +215,9 @@ static void set_star_params(soap_ctx* c, const soap_star_desc* s) {
     c->vsini = s->vsini_kms; c->incl_deg = s->incl_deg; c->u1 = s->u1; c->u2 = s->u2;
     c->alpha = s->diff_rot_alpha; c->t_quiet = s->t_quiet_K;
     for (int b = 0; b < s->n_mu; b++) c->mu_values[b] = s->mu_values[b];
+    c->mu_sorted = 1;
+    for (int b = 1; b < s->n_mu; b++)
+        if (!(s->mu_values[b] - s->mu_values[b - 1] > 1e-9)) c->mu_sorted = 0;
     // fixed-point kernels: every partial sum is bounded by sum |I| <= 4 (1 + |u1| + |u2|)
     double bound = 4.0 * (1.0 + std::fabs(s->u1) + std::fabs(s->u2));
     c->fx_bits = 61 - (int)std::ceil(std::log2(bound));

@@ -11,28 +11,55 @@
 // k_gauss_fit: one warp per spectrum, FP64 Levenberg-Marquardt on
 // A + B exp(-(v - mu)^2 / (2 s^2)).
 #include <cmath>
+#include <type_traits>
+#include <algorithm>
 
 #include "soap_internal.cuh"
 
 namespace soap {
 
-constexpr int kLinesPerChunk = 64;
+constexpr int kLinesPerChunk = 128;      // generic kernel
+constexpr int kWinLines = 32;             // windowed kernel: 32 lines span ~600 px here
+constexpr int kWinMax = 768;              // staged pixels per block (window budget)
+constexpr int kReduceSplit = 8;
 
-__global__ void k_ccf_lines(int n_lines, const double* __restrict__ lam, double lam_s, double delta,
-                            double h, double s_lo, double s_hi, int64_t n_px, double* u0h,
-                            int* valid) {
+// Per line: validity and the box start a0 = u_l - h + 1/2 (pixel n covers [n, n+1) in a0 + s
+// coordinates), split into an integer U_l and an exact fraction f_l in [0, 1).
+__global__ void k_ccf_lines(int n_lines, const double* __restrict__ lam, const double* __restrict__ w,
+                            double lam_s, double delta, double h, double s_lo, double s_hi,
+                            int64_t n_px, int* U, double* f64, float* f32, float* w32, int* valid) {
     for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < n_lines; l += gridDim.x * blockDim.x) {
+        w32[l] = (float)w[l];
         double u = log(lam[l] / lam_s) / delta;
         valid[l] = (u + s_lo - h >= -0.5) && (u + s_hi + h <= (double)n_px - 0.5);
-        u0h[l] = u - h + 0.5;      // box start, shifted so that pixel n covers [n, n+1)
+        double a0 = u - h + 0.5;
+        double fl = floor(a0);
+        U[l] = (int)fl;
+        f64[l] = a0 - fl;
+        f32[l] = (float)(a0 - fl);
     }
 }
 
+// Per velocity: s_k = atanh(v_k / c) / Delta split into an integer S_k and a fraction g_k.
+__global__ void k_ccf_velocities(int n_v, double v_lo, double v_step, double delta, int* S,
+                                 double* g64, float* g32) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_v; k += gridDim.x * blockDim.x) {
+        double s = atanh((v_lo + (double)k * v_step) / kCKms) / delta;
+        double fl = floor(s);
+        S[k] = (int)fl;
+        g64[k] = s - fl;
+        g32[k] = (float)(s - fl);
+    }
+}
+
+// Block = (chunk of lines, block of SB spectra); thread = velocity.  Box start in pixel units:
+// (U_l + S_k) + (f_l + g_k); the fractional part carries the sub-pixel position in T.
 template <typename T, int SB>
-__global__ void k_ccf_partial(int n_lines, const double* __restrict__ u0h, const int* __restrict__ valid,
-                              const double* __restrict__ weight, int n_v, double v_lo, double v_step,
-                              double delta, double box, int64_t n_px, int n_spec,
-                              const T* __restrict__ spectra, double* __restrict__ partial) {
+__global__ void k_ccf_partial(int n_lines, const int* __restrict__ U, const T* __restrict__ f,
+                              const int* __restrict__ valid, const double* __restrict__ weight,
+                              int n_v, const int* __restrict__ S, const T* __restrict__ g,
+                              double box, int64_t n_px, int n_spec, const T* __restrict__ spectra,
+                              double* __restrict__ partial) {
     const int chunk = blockIdx.x;
     const int s0 = blockIdx.y * SB;
     const int l0 = chunk * kLinesPerChunk;
@@ -40,18 +67,19 @@ __global__ void k_ccf_partial(int n_lines, const double* __restrict__ u0h, const
     const int ns = min(SB, n_spec - s0);
     const T boxT = (T)box;
     for (int k = threadIdx.x; k < n_v; k += blockDim.x) {
-        const double sk = atanh((v_lo + (double)k * v_step) / kCKms) / delta;
+        const int Sk = S[k];
+        const T gk = g[k];
         T acc[SB];
 #pragma unroll
         for (int s = 0; s < SB; s++) acc[s] = T(0);
         for (int l = l0; l < l1; l++) {
             if (!valid[l]) continue;
-            const double t = u0h[l] + sk;
-            const double fl = floor(t);
-            const int64_t n0 = (int64_t)fl;
-            const T phi = (T)(t - fl);
+            T fr = f[l] + gk;
+            const int carry = fr >= T(1);
+            const T phi = fr - (T)carry;
+            const int64_t n0 = (int64_t)U[l] + Sk + carry;
             const T wl = (T)weight[l];
-            // overlap with pixel n0 + i: clamp(phi + box - i, 0, 1) for i >= 1, min(1-phi, box) for i = 0
+            // overlap with pixel n0 + i: min(1 - phi, box) for i = 0, clamp(phi + box - i, 0, 1) after
             T ov = fmin(T(1) - phi, boxT);
             int i = 0;
             while (true) {
@@ -59,13 +87,13 @@ __global__ void k_ccf_partial(int n_lines, const double* __restrict__ u0h, const
                 if (n >= n_px) break;                  // rounding at the grid edge only
                 if (n >= 0) {
                     const T cwt = wl * ov;
-                    const T* f = spectra + (int64_t)s0 * n_px + n;
+                    const T* fp = spectra + (int64_t)s0 * n_px + n;
 #pragma unroll
                     for (int s = 0; s < SB; s++)
-                        if (s < ns) acc[s] = fma(cwt, f[(int64_t)s * n_px], acc[s]);
+                        if (s < ns) acc[s] = fma(cwt, __ldg(fp + (int64_t)s * n_px), acc[s]);
                 }
                 i++;
-                T rem = phi + boxT - (T)i;
+                const T rem = phi + boxT - (T)i;
                 if (!(rem > T(0))) break;
                 ov = fmin(rem, T(1));
             }
@@ -75,15 +103,144 @@ __global__ void k_ccf_partial(int n_lines, const double* __restrict__ u0h, const
     }
 }
 
+// Windowed form for masks sorted by wavelength: the block stages the pixels its chunk of
+// lines can reach, for its SB spectra, in shared memory as [pixel][SB] (one 16-byte vector per
+// 4 spectra), so each overlap costs SB/4 vector loads instead of SB scattered global loads.
+// Blocks whose window would not fit fall back to global loads.
+// Windowed form for masks sorted by wavelength.  Block = (group of line chunks, SB spectra);
+// thread = velocity k.  Per chunk the block stages the pixels its lines can reach, for its SB
+// spectra, in shared memory as padded rows [pixel][SB] (one 16-byte vector per VW spectra).
+// For each line the box position (integer pixel + fraction) is computed once and reused for
+// all SB spectra; the box covers at most NB pixels, handled branch-free (zero overlaps add
+// zero).  Chunks whose window does not fit fall back to global loads.
+template <typename T, int SB, int NB>
+__global__ void __launch_bounds__(256)
+k_ccf_window(int n_lines, const int* __restrict__ U, const T* __restrict__ f,
+             const int* __restrict__ valid, const T* __restrict__ wl_, int n_v,
+             const int* __restrict__ S, const T* __restrict__ g, double box, int64_t n_px,
+             int n_spec, const T* __restrict__ spectra, double* __restrict__ partial) {
+    typedef typename std::conditional<sizeof(T) == 4, float4, double2>::type V;
+    constexpr int VW = sizeof(V) / sizeof(T);
+    static_assert(SB % VW == 0, "SB must be a multiple of the vector width");
+    constexpr int ROW = SB + 16 / (int)sizeof(T);         // padded row: consecutive rows on other banks
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ int sB[kWinLines];                        // U_l - n_lo (window-relative base)
+    __shared__ T sF[kWinLines];
+    __shared__ T sW[kWinLines];
+    T* win = reinterpret_cast<T*>(smraw);
+    const int s0 = blockIdx.y * SB;
+    const int ns = min(SB, n_spec - s0);
+    const int n_chunks = (n_lines + kWinLines - 1) / kWinLines;
+    const T boxT = (T)box;
+    const int k = threadIdx.x;
+    const bool active = k < n_v;
+    const int Sk = active ? S[k] : 0;
+    const T gk = active ? g[k] : T(0);
+    T acc[SB];
+#pragma unroll
+    for (int s = 0; s < SB; s++) acc[s] = T(0);
+    for (int chunk = blockIdx.x; chunk < n_chunks; chunk += gridDim.x) {
+        const int l0 = chunk * kWinLines;
+        const int l1 = min(n_lines, l0 + kWinLines);
+        // window [n_lo, n_hi) with a margin on both sides; pixels off the grid stage as 0
+        const int64_t n_lo = (int64_t)U[l0] + S[0] - 2;
+        const int64_t n_hi = (int64_t)U[l1 - 1] + S[n_v - 1] + NB + 2;
+        const int W = (int)(n_hi - n_lo);
+        const bool staged = W >= NB && W <= kWinMax;
+        __syncthreads();                                  // previous chunk done with the window
+        for (int j = threadIdx.x; j < l1 - l0; j += blockDim.x) {
+            const int l = l0 + j;
+            sB[j] = (int)((int64_t)U[l] - n_lo);
+            sF[j] = f[l];
+            sW[j] = valid[l] ? wl_[l] : T(0);             // lines whose box leaves the grid: skipped
+        }
+        if (staged) {
+            // one pixel per thread and step, all SB spectra at once (SB loads in flight)
+            for (int x = threadIdx.x; x < W; x += blockDim.x) {
+                const int64_t pix = n_lo + x;
+                const bool on = pix >= 0 && pix < n_px;
+                T v[SB];
+#pragma unroll
+                for (int s = 0; s < SB; s++)
+                    v[s] = (on && s < ns) ? __ldg(spectra + (int64_t)(s0 + s) * n_px + pix) : T(0);
+                V* dst = reinterpret_cast<V*>(win + x * ROW);
+#pragma unroll
+                for (int q = 0; q < SB / VW; q++) {
+                    V t;
+                    if constexpr (VW == 4) t = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                    else t = make_double2(v[2 * q], v[2 * q + 1]);
+                    dst[q] = t;
+                }
+            }
+        }
+        __syncthreads();
+        if (!active) continue;
+        const int nl = l1 - l0;
+        for (int j = 0; j < nl; j++) {
+            const T wl = sW[j];
+            if (wl == T(0)) continue;
+            const T fr = sF[j] + gk;
+            const bool carry = fr >= T(1);
+            const T phi = carry ? fr - T(1) : fr;
+            const int n = sB[j] + Sk + (carry ? 1 : 0);  // first pixel, window-relative
+            const T end = phi + boxT;                      // box end measured from pixel n
+            if (staged) {
+                const int nc = min(max(n, 0), W - NB);   // always n itself (margins); kept for safety
+#pragma unroll
+                for (int i = 0; i < NB; i++) {
+                    const T lo = i == 0 ? phi : T(i);
+                    const T ov = fmax(fmin(end, T(i + 1)) - lo, T(0));
+                    const T cwt = wl * ov;
+                    const V* src = reinterpret_cast<const V*>(win + (nc + i) * ROW);
+#pragma unroll
+                    for (int q = 0; q < SB / VW; q++) {
+                        const V t = src[q];
+                        if constexpr (VW == 4) {
+                            acc[4 * q] = fma(cwt, t.x, acc[4 * q]);
+                            acc[4 * q + 1] = fma(cwt, t.y, acc[4 * q + 1]);
+                            acc[4 * q + 2] = fma(cwt, t.z, acc[4 * q + 2]);
+                            acc[4 * q + 3] = fma(cwt, t.w, acc[4 * q + 3]);
+                        } else {
+                            acc[2 * q] = fma(cwt, t.x, acc[2 * q]);
+                            acc[2 * q + 1] = fma(cwt, t.y, acc[2 * q + 1]);
+                        }
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < NB; i++) {
+                    const int64_t pix = n_lo + n + i;
+                    if (pix < 0 || pix >= n_px) continue;
+                    const T lo = i == 0 ? phi : T(i);
+                    const T ov = fmax(fmin(end, T(i + 1)) - lo, T(0));
+                    const T cwt = wl * ov;
+                    const T* fp = spectra + (int64_t)s0 * n_px + pix;
+#pragma unroll
+                    for (int s = 0; s < SB; s++)
+                        if (s < ns) acc[s] = fma(cwt, __ldg(fp + (int64_t)s * n_px), acc[s]);
+                }
+            }
+        }
+    }
+    if (active)
+        for (int s = 0; s < ns; s++)
+            partial[((int64_t)blockIdx.x * n_spec + s0 + s) * n_v + k] = (double)acc[s];
+}
+
+// ccf[t] = sum over chunks of partial[c][t], in a fixed order: kReduceSplit lanes take
+// interleaved chunks, then a fixed shuffle tree adds the lanes.
 __global__ void k_ccf_reduce(int n_chunks, int n_spec, int n_v, const double* __restrict__ partial,
                              double* __restrict__ ccf) {
     const int64_t total = (int64_t)n_spec * n_v;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        double s = 0.0;
-        for (int c = 0; c < n_chunks; c++) s += partial[(int64_t)c * total + t];
-        ccf[t] = s;
+    const int sub = threadIdx.x % kReduceSplit;
+    const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kReduceSplit;
+    double s = 0.0;
+    if (t < total) {
+#pragma unroll 4
+        for (int c = sub; c < n_chunks; c += kReduceSplit) s += partial[(int64_t)c * total + t];
     }
+    for (int o = kReduceSplit / 2; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, kReduceSplit);
+    if (sub == 0 && t < total) ccf[t] = s;
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -91,8 +248,33 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// Solve the 4x4 symmetric positive system M x = b by Gaussian elimination with partial
-// pivoting (all lanes do it redundantly).
+// Solve the 4x4 system M x = b by Gaussian elimination with partial pivoting (FP32).
+__device__ bool solve4f(float M[4][4], float b[4], float x[4]) {
+    for (int col = 0; col < 4; col++) {
+        int piv = col;
+        for (int r = col + 1; r < 4; r++)
+            if (fabsf(M[r][col]) > fabsf(M[piv][col])) piv = r;
+        if (!(fabsf(M[piv][col]) > 0.0f)) return false;
+        if (piv != col) {
+            for (int q = 0; q < 4; q++) { float t = M[col][q]; M[col][q] = M[piv][q]; M[piv][q] = t; }
+            float t = b[col]; b[col] = b[piv]; b[piv] = t;
+        }
+        const float inv = 1.0f / M[col][col];
+        for (int r = col + 1; r < 4; r++) {
+            float f = M[r][col] * inv;
+            for (int q = col; q < 4; q++) M[r][q] -= f * M[col][q];
+            b[r] -= f * b[col];
+        }
+    }
+    for (int r = 3; r >= 0; r--) {
+        float s = b[r];
+        for (int q = r + 1; q < 4; q++) s -= M[r][q] * x[q];
+        x[r] = s / M[r][r];
+    }
+    return isfinite(x[0]) && isfinite(x[1]) && isfinite(x[2]) && isfinite(x[3]);
+}
+
+// Solve the 4x4 system M x = b by Gaussian elimination with partial pivoting (FP64).
 __device__ bool solve4(double M[4][4], double b[4], double x[4]) {
     for (int col = 0; col < 4; col++) {
         int piv = col;
@@ -117,97 +299,194 @@ __device__ bool solve4(double M[4][4], double b[4], double x[4]) {
     return true;
 }
 
-__device__ double model_cost(const double* __restrict__ c, int n_v, double v_lo, double v_step,
-                             const double p[4], int lane) {
-    double acc = 0.0;
-    for (int k = lane; k < n_v; k += 32) {
-        double v = v_lo + k * v_step;
-        double z = (v - p[2]) / p[3];
-        double r = p[0] + p[1] * exp(-0.5 * z * z) - c[k];
-        acc += r * r;
+constexpr int kFitThreads = 128;
+constexpr int kFitWarps = kFitThreads / 32;
+constexpr int kFitCache = 4;           // velocities cached in registers per thread
+
+// Column sums of a [kFitThreads][NV] shared table in a fixed order: NV x 8 threads add 16 rows
+// each, then NV threads add the 8 partial sums.  Thread 0 returns the totals in out.
+template <int NV>
+__device__ __forceinline__ void table_sum(const double (&v)[NV], double* tab, double* part,
+                                          double (&out)[NV]) {
+#pragma unroll
+    for (int q = 0; q < NV; q++) tab[threadIdx.x * NV + q] = v[q];
+    __syncthreads();
+    if (threadIdx.x < NV * 8) {
+        const int q = threadIdx.x % NV, seg = threadIdx.x / NV;
+        double s = 0.0;
+        for (int r = seg * (kFitThreads / 8); r < (seg + 1) * (kFitThreads / 8); r++) s += tab[r * NV + q];
+        part[seg * NV + q] = s;
     }
-    return warp_sum(acc);
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double s = 0.0;
+        for (int seg = 0; seg < 8; seg++) s += part[seg * NV + threadIdx.x];
+        part[8 * NV + threadIdx.x] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int q = 0; q < NV; q++) out[q] = part[8 * NV + q];
 }
 
-__global__ void k_gauss_fit(int n_spec, int n_v, double v_lo, double v_step,
-                            const double* __restrict__ ccf, double* rv, double* fit) {
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (warp >= n_spec) return;
-    const double* c = ccf + (int64_t)warp * n_v;
-    // starting point: continuum = max, depth at the (first) minimum, width from the dip area
-    double mx = -INFINITY, mn = INFINITY, sum = 0.0;
-    int kmin = n_v;
-    for (int k = lane; k < n_v; k += 32) {
-        double v = c[k];
-        mx = fmax(mx, v);
-        sum += v;
-        if (v < mn) { mn = v; kmin = k; }
+// One pass over the velocity grid in scaled variables: u = (v - c0)/s0, model
+// a + b exp(-(u - m)^2 / (2 w^2)) against y = CCF / scale.  Sums J^T J (10), J^T r (4), cost.
+__device__ __forceinline__ void fit_pass(const double* __restrict__ y, int n_v, const double* ucache,
+                                         double u0, double du, const double p[4], double* tab,
+                                         double* part, double (&out)[15]) {
+    double acc[15];
+#pragma unroll
+    for (int q = 0; q < 15; q++) acc[q] = 0.0;
+    const double iw = 1.0 / p[3];
+    const double iw2 = iw * iw;
+    int i = 0;
+    for (int k = threadIdx.x; k < n_v; k += kFitThreads, i++) {
+        const double u = i < kFitCache ? ucache[i] : fma((double)k, du, u0);
+        const double d = u - p[2];
+        const double e = exp(-0.5 * d * d * iw2);
+        const double r = fma(p[1], e, p[0]) - y[k];
+        const double t = p[1] * e * d * iw2;
+        const double J[4] = {1.0, e, t, t * d * iw};
+        int q = 0;
+#pragma unroll
+        for (int a = 0; a < 4; a++)
+#pragma unroll
+            for (int b = a; b < 4; b++) { acc[q] = fma(J[a], J[b], acc[q]); q++; }
+#pragma unroll
+        for (int a = 0; a < 4; a++) acc[10 + a] = fma(J[a], r, acc[10 + a]);
+        acc[14] = fma(r, r, acc[14]);
+    }
+    table_sum<15>(acc, tab, part, out);
+}
+
+// One block of 128 threads per spectrum, FP64 throughout.  Start: continuum A = max CCF,
+// B = min - max, mu and sigma from the first two moments of the dip (A - CCF); the model is
+// A + B exp(-(v - mu)^2 / (2 sigma^2)).  The fit runs in scaled variables (CCF / max,
+// (v - mu0) / sigma0) so that the normal equations stay well conditioned.  Levenberg-Marquardt
+// with damping (J^T J + lam diag(J^T J)): each pass evaluates the cost, J^T J and J^T r at the
+// trial point together (fixed-order sums); thread 0 keeps the trial when the cost does not
+// grow (lam shrinks, down to 1e-9) or drops it (lam grows), solves for the next step and
+// broadcasts it.  The fit stops once a step moves every scaled parameter by less than 1e-11
+// (relative for the amplitudes), the damping passes 1e8, or after 100 passes.
+__global__ void __launch_bounds__(kFitThreads) k_gauss_fit(int n_spec, int n_v, double v_lo,
+                                                           double v_step,
+                                                           const double* __restrict__ ccf,
+                                                           double* scratch, double* rv,
+                                                           double* fit) {
+    __shared__ double tab[kFitThreads * 15];
+    __shared__ double part[9 * 15];
+    __shared__ double red[kFitWarps][2];
+    __shared__ double sp[5];
+    __shared__ int sstop;
+    const int spec = blockIdx.x;
+    if (spec >= n_spec) return;
+    const double* c = ccf + (int64_t)spec * n_v;
+    double* y = scratch + (int64_t)spec * n_v;            // scaled CCF
+    // continuum and the dip's moments
+    double mx = -INFINITY, mn = INFINITY;
+    for (int k = threadIdx.x; k < n_v; k += kFitThreads) {
+        mx = fmax(mx, c[k]);
+        mn = fmin(mn, c[k]);
     }
     for (int o = 16; o > 0; o >>= 1) {
         mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        double omn = __shfl_xor_sync(0xffffffffu, mn, o);
-        int okm = __shfl_xor_sync(0xffffffffu, kmin, o);
-        if (omn < mn || (omn == mn && okm < kmin)) { mn = omn; kmin = okm; }
+        mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
     }
-    sum = warp_sum(sum);
-    double p[4];
-    p[0] = mx;
-    p[1] = mn - mx;
-    p[2] = v_lo + kmin * v_step;
-    double area = ((double)n_v * mx - sum) * v_step;
-    double s0 = p[1] != 0.0 ? area / (fabs(p[1]) * sqrt(2.0 * kPi)) : v_step;
-    p[3] = fmax(s0, v_step);
-    double lam = 1e-3;
-    double cost = model_cost(c, n_v, v_lo, v_step, p, lane);
-    for (int it = 0; it < 400; it++) {
-        double jtj[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0}, jtr[4] = {0, 0, 0, 0};
-        for (int k = lane; k < n_v; k += 32) {
-            double v = v_lo + k * v_step;
-            double d = v - p[2];
-            double e = exp(-0.5 * d * d / (p[3] * p[3]));
-            double r = p[0] + p[1] * e - c[k];
-            double J[4] = {1.0, e, p[1] * e * d / (p[3] * p[3]), p[1] * e * d * d / (p[3] * p[3] * p[3])};
-            int q = 0;
-            for (int a = 0; a < 4; a++) {
-                jtr[a] += J[a] * r;
-                for (int b = a; b < 4; b++) jtj[q++] += J[a] * J[b];
-            }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) { red[warp][0] = mx; red[warp][1] = mn; }
+    __syncthreads();
+    mx = red[0][0]; mn = red[0][1];
+    for (int w = 1; w < kFitWarps; w++) { mx = fmax(mx, red[w][0]); mn = fmin(mn, red[w][1]); }
+    const double scale = mx != 0.0 ? fabs(mx) : 1.0;
+    const double iscale = 1.0 / scale;
+    double m3[3] = {0.0, 0.0, 0.0};
+    for (int k = threadIdx.x; k < n_v; k += kFitThreads) {
+        const double v = fma((double)k, v_step, v_lo), d = mx - c[k];
+        y[k] = c[k] * iscale;
+        m3[0] += d; m3[1] += d * v; m3[2] += d * v * v;
+    }
+    double mom[3];
+    table_sum<3>(m3, tab, part, mom);
+    if (threadIdx.x == 0) {
+        double c0 = fma(0.5 * (n_v - 1), v_step, v_lo), s0 = v_step;
+        if (mom[0] > 0.0) {
+            c0 = mom[1] / mom[0];
+            const double var = mom[2] / mom[0] - c0 * c0;
+            s0 = var > 0.0 ? sqrt(var) : v_step;
         }
-        for (int q = 0; q < 10; q++) jtj[q] = warp_sum(jtj[q]);
-        for (int a = 0; a < 4; a++) jtr[a] = warp_sum(jtr[a]);
-        bool accepted = false;
-        double step_rel = 0.0;
-        for (int tries = 0; tries < 40 && !accepted; tries++) {
-            double M[4][4], b[4], dx[4];
-            int q = 0;
-            for (int a = 0; a < 4; a++)
-                for (int bb = a; bb < 4; bb++) { M[a][bb] = M[bb][a] = jtj[q++]; }
-            for (int a = 0; a < 4; a++) { M[a][a] *= (1.0 + lam); b[a] = -jtr[a]; }
-            if (!solve4(M, b, dx)) { lam *= 10.0; continue; }
-            double pn[4] = {p[0] + dx[0], p[1] + dx[1], p[2] + dx[2], p[3] + dx[3]};
-            double cn = model_cost(c, n_v, v_lo, v_step, pn, lane);
-            if (cn <= cost) {
-                step_rel = 0.0;
+        sp[0] = c0;
+        sp[1] = fmax(s0, v_step);
+    }
+    __syncthreads();
+    const double c0 = sp[0], s0 = sp[1];
+    const double u0 = (v_lo - c0) / s0, du = v_step / s0;
+    double ucache[kFitCache];
+    {
+        int i = 0;
+        for (int k = threadIdx.x; k < n_v && i < kFitCache; k += kFitThreads, i++) ucache[i] = fma((double)k, du, u0);
+    }
+    // scaled parameters: a, b, m, w
+    double p[4] = {mx * iscale, (mn - mx) * iscale, 0.0, 1.0};
+    double acc[15];
+    fit_pass(y, n_v, ucache, u0, du, p, tab, part, acc);
+    double jtj[10], jtr[4], cost = 0.0, lam = 1e-3;
+    double pt[4] = {p[0], p[1], p[2], p[3]};
+    bool tiny = false;
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < 10; q++) jtj[q] = acc[q];
+        for (int a = 0; a < 4; a++) jtr[a] = acc[10 + a];
+        cost = acc[14];
+    }
+    for (int it = 0; it < 100; it++) {
+        if (threadIdx.x == 0) {
+            int stop = 0;
+            if (it > 0) {
+                if (acc[14] <= cost) {                // keep the trial point
+                    for (int a = 0; a < 4; a++) p[a] = pt[a];
+                    for (int q = 0; q < 10; q++) jtj[q] = acc[q];
+                    for (int a = 0; a < 4; a++) jtr[a] = acc[10 + a];
+                    cost = acc[14];
+                    lam = fmax(lam * 0.1, 1e-9);
+                    if (tiny) stop = 1;
+                } else {
+                    if (tiny) stop = 1;                 // at the rounding floor of the cost
+                    lam *= 10.0;
+                }
+            }
+            while (!stop) {
+                if (lam > 1e8) { stop = 1; break; }
+                // the step only needs to point downhill: solved in FP32 (the scaled system is
+                // well conditioned); the fixed point J^T r = 0 is still evaluated in FP64
+                float M[4][4], b[4], dxf[4];
+                int q = 0;
                 for (int a = 0; a < 4; a++)
-                    step_rel = fmax(step_rel, fabs(dx[a]) / (fabs(p[a]) + 1e-300));
-                for (int a = 0; a < 4; a++) p[a] = pn[a];
-                cost = cn;
-                lam = fmax(lam * 0.1, 1e-12);
-                accepted = true;
-            } else {
-                lam *= 10.0;
+                    for (int bb = a; bb < 4; bb++) { M[a][bb] = M[bb][a] = (float)jtj[q++]; }
+                for (int a = 0; a < 4; a++) { M[a][a] *= (float)(1.0 + lam); b[a] = (float)(-jtr[a]); }
+                if (!solve4f(M, b, dxf)) { lam *= 10.0; continue; }
+                double dx[4] = {dxf[0], dxf[1], dxf[2], dxf[3]};
+                tiny = fabs(dx[2]) <= 1e-11 && fabs(dx[3]) <= 1e-11 &&
+                       fabs(dx[0]) <= 1e-11 * fabs(p[0]) && fabs(dx[1]) <= 1e-11 * fabs(p[1]);
+                for (int a = 0; a < 4; a++) pt[a] = p[a] + dx[a];
+                break;
             }
+            for (int a = 0; a < 4; a++) sp[a] = stop ? p[a] : pt[a];
+            sstop = stop;
         }
-        if (!accepted || step_rel < 1e-15) break;
+        __syncthreads();
+        const int stop = sstop;
+        const double ptb[4] = {sp[0], sp[1], sp[2], sp[3]};
+        __syncthreads();
+        if (stop) break;
+        fit_pass(y, n_v, ucache, u0, du, ptb, tab, part, acc);
     }
-    if (lane == 0) {
-        rv[warp] = p[2];
+    if (threadIdx.x == 0) {
+        const double mu = fma(p[2], s0, c0);
+        rv[spec] = mu;
         if (fit) {
-            fit[(int64_t)warp * 4 + 0] = p[0];
-            fit[(int64_t)warp * 4 + 1] = p[1];
-            fit[(int64_t)warp * 4 + 2] = p[2];
-            fit[(int64_t)warp * 4 + 3] = fabs(p[3]);
+            fit[(int64_t)spec * 4 + 0] = p[0] * scale;
+            fit[(int64_t)spec * 4 + 1] = p[1] * scale;
+            fit[(int64_t)spec * 4 + 2] = mu;
+            fit[(int64_t)spec * 4 + 3] = fabs(p[3]) * s0;
         }
     }
 }
@@ -216,56 +495,102 @@ soap_status rv_ccf_run(soap_ctx* c, const void* spectra_dev, int f32, int n_spec
                        const double* mask_lambda, const double* mask_weight, int n_lines,
                        double width_kms, double v_lo, double v_step, int n_v, double* rv_dev,
                        double* fit_dev, double* ccf_dev) {
-    const int n_chunks = (n_lines + kLinesPerChunk - 1) / kLinesPerChunk;
-    // scratch: lines (lambda, weight, u0h, valid), partial sums, ccf
-    size_t off_w = (size_t)n_lines * 8;
-    size_t off_u = off_w + (size_t)n_lines * 8;
-    size_t off_v = off_u + (size_t)n_lines * 8;
-    size_t off_p = (off_v + (size_t)n_lines * 4 + 255) / 256 * 256;
-    size_t off_c = off_p + (size_t)n_chunks * n_spec * n_v * 8;
-    size_t total = off_c + (size_t)n_spec * n_v * 8;
+    bool sorted = true;
+    for (int l = 1; l < n_lines; l++)
+        if (mask_lambda[l] < mask_lambda[l - 1]) { sorted = false; break; }
+    // windowed kernel: one velocity per thread (n_v <= 256); blocks walk the chunks
+    const bool windowed = sorted && n_v <= 256 && 2.0 * width_kms / (2.0 * kCKms * c->delta) <= 15.0;
+    const int n_wchunks = (n_lines + kWinLines - 1) / kWinLines;
+    const int n_wgroups = n_wchunks;                    // one chunk of lines per block
+    const int n_chunks = windowed ? n_wgroups : (n_lines + kLinesPerChunk - 1) / kLinesPerChunk;
+    // scratch layout (8-byte aligned pieces, 256-byte aligned blocks)
+    auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+    size_t o_lam = 0;
+    size_t o_w = al(o_lam + (size_t)n_lines * 8);
+    size_t o_U = al(o_w + (size_t)n_lines * 8);
+    size_t o_f64 = al(o_U + (size_t)n_lines * 4);
+    size_t o_f32 = al(o_f64 + (size_t)n_lines * 8);
+    size_t o_w32 = al(o_f32 + (size_t)n_lines * 4);
+    size_t o_valid = al(o_w32 + (size_t)n_lines * 4);
+    size_t o_S = al(o_valid + (size_t)n_lines * 4);
+    size_t o_g64 = al(o_S + (size_t)n_v * 4);
+    size_t o_g32 = al(o_g64 + (size_t)n_v * 8);
+    size_t o_part = al(o_g32 + (size_t)n_v * 4);
+    size_t o_ccf = al(o_part + (size_t)n_chunks * n_spec * n_v * 8);
+    size_t o_y = al(o_ccf + (size_t)n_spec * n_v * 8);
+    size_t total = o_y + (size_t)n_spec * n_v * 8;
     SOAP_TRY(ensure(c->ccf_tmp, total));
     char* base = c->ccf_tmp.as<char>();
-    double* d_lam = (double*)base;
-    double* d_w = (double*)(base + off_w);
-    double* d_u = (double*)(base + off_u);
-    int* d_valid = (int*)(base + off_v);
-    double* d_part = (double*)(base + off_p);
-    double* d_ccf = ccf_dev ? ccf_dev : (double*)(base + off_c);
+    double* d_lam = (double*)(base + o_lam);
+    double* d_w = (double*)(base + o_w);
+    int* d_U = (int*)(base + o_U);
+    double* d_f64 = (double*)(base + o_f64);
+    float* d_f32 = (float*)(base + o_f32);
+    float* d_w32 = (float*)(base + o_w32);
+    int* d_valid = (int*)(base + o_valid);
+    int* d_S = (int*)(base + o_S);
+    double* d_g64 = (double*)(base + o_g64);
+    float* d_g32 = (float*)(base + o_g32);
+    double* d_part = (double*)(base + o_part);
+    double* d_ccf = ccf_dev ? ccf_dev : (double*)(base + o_ccf);
+    double* d_y = (double*)(base + o_y);
     SOAP_CUDA(cudaMemcpyAsync(d_lam, mask_lambda, (size_t)n_lines * 8, cudaMemcpyHostToDevice, c->stream));
     SOAP_CUDA(cudaMemcpyAsync(d_w, mask_weight, (size_t)n_lines * 8, cudaMemcpyHostToDevice, c->stream));
     cudaEvent_t tb = c->profiling ? timer_begin(c) : nullptr;
     const double h = width_kms / (2.0 * kCKms * c->delta);
     const double v_hi = v_lo + v_step * (n_v - 1);
     k_ccf_lines<<<(n_lines + 255) / 256, 256, 0, c->stream>>>(
-        n_lines, d_lam, c->lam_s, c->delta, h, std::atanh(v_lo / kCKms) / c->delta,
-        std::atanh(v_hi / kCKms) / c->delta, c->n_px, d_u, d_valid);
+        n_lines, d_lam, d_w, c->lam_s, c->delta, h, std::atanh(v_lo / kCKms) / c->delta,
+        std::atanh(v_hi / kCKms) / c->delta, c->n_px, d_U, d_f64, d_f32, d_w32, d_valid);
+    SOAP_LAUNCHED(c);
+    k_ccf_velocities<<<(n_v + 127) / 128, 128, 0, c->stream>>>(n_v, v_lo, v_step, c->delta, d_S,
+                                                               d_g64, d_g32);
     SOAP_LAUNCHED(c);
     const int threads = n_v >= 256 ? 256 : ((n_v + 31) / 32) * 32;
-    if (f32) {
+    if (windowed) {
+        const int threads = ((n_v + 31) / 32) * 32;
+        const double box = 2.0 * h;
+        const bool small = box <= 1.0;                   // the box covers at most 2 pixels
+        dim3 grid32((unsigned)n_wgroups, (unsigned)((n_spec + 15) / 16));
+        dim3 grid64((unsigned)n_wgroups, (unsigned)((n_spec + 7) / 8));
+        const size_t smem32 = (size_t)kWinMax * (16 + 4) * 4;
+        const size_t smem64 = (size_t)kWinMax * (8 + 2) * 8;
+#define SOAP_CCF_LAUNCH(T, SB, NB, GRID, SMEM, F, WT, G, SPEC)                                    \
+        do {                                                                                       \
+            SOAP_CUDA(cudaFuncSetAttribute(k_ccf_window<T, SB, NB>,                                \
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM)); \
+            k_ccf_window<T, SB, NB><<<GRID, threads, SMEM, c->stream>>>(                          \
+                n_lines, d_U, F, d_valid, WT, n_v, d_S, G, box, c->n_px, n_spec,                   \
+                (const T*)SPEC, d_part);                                                           \
+        } while (0)
+        if (f32) {
+            if (small) SOAP_CCF_LAUNCH(float, 16, 2, grid32, smem32, d_f32, d_w32, d_g32, spectra_dev);
+            else SOAP_CCF_LAUNCH(float, 16, 16, grid32, smem32, d_f32, d_w32, d_g32, spectra_dev);
+        } else {
+            if (small) SOAP_CCF_LAUNCH(double, 8, 2, grid64, smem64, d_f64, d_w, d_g64, spectra_dev);
+            else SOAP_CCF_LAUNCH(double, 8, 16, grid64, smem64, d_f64, d_w, d_g64, spectra_dev);
+        }
+#undef SOAP_CCF_LAUNCH
+    } else if (f32) {
         constexpr int SB = 16;
         dim3 grid((unsigned)n_chunks, (unsigned)((n_spec + SB - 1) / SB));
         k_ccf_partial<float, SB><<<grid, threads, 0, c->stream>>>(
-            n_lines, d_u, d_valid, d_w, n_v, v_lo, v_step, c->delta, 2.0 * h, c->n_px, n_spec,
+            n_lines, d_U, d_f32, d_valid, d_w, n_v, d_S, d_g32, 2.0 * h, c->n_px, n_spec,
             (const float*)spectra_dev, d_part);
     } else {
         constexpr int SB = 8;
         dim3 grid((unsigned)n_chunks, (unsigned)((n_spec + SB - 1) / SB));
         k_ccf_partial<double, SB><<<grid, threads, 0, c->stream>>>(
-            n_lines, d_u, d_valid, d_w, n_v, v_lo, v_step, c->delta, 2.0 * h, c->n_px, n_spec,
+            n_lines, d_U, d_f64, d_valid, d_w, n_v, d_S, d_g64, 2.0 * h, c->n_px, n_spec,
             (const double*)spectra_dev, d_part);
     }
     SOAP_LAUNCHED(c);
-    int64_t tot = (int64_t)n_spec * n_v;
-    int g = (int)((tot + 255) / 256);
-    if (g > 152 * 8) g = 152 * 8;
-    k_ccf_reduce<<<g, 256, 0, c->stream>>>(n_chunks, n_spec, n_v, d_part, d_ccf);
+    int64_t tot = (int64_t)n_spec * n_v * kReduceSplit;
+    k_ccf_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(n_chunks, n_spec, n_v, d_part, d_ccf);
     SOAP_LAUNCHED(c);
     if (c->profiling) timer_end(c, SOAP_TIMER_CCF, tb);
-    int warps_per_block = 4;
     SOAP_TIMED(c, SOAP_TIMER_FIT,
-               k_gauss_fit<<<(n_spec + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0,
-                             c->stream>>>(n_spec, n_v, v_lo, v_step, d_ccf, rv_dev, fit_dev);
+               k_gauss_fit<<<n_spec, kFitThreads, 0, c->stream>>>(n_spec, n_v, v_lo, v_step, d_ccf, d_y, rv_dev, fit_dev);
                SOAP_LAUNCHED(c));
     return SOAP_OK;
 }

@@ -52,6 +52,22 @@ __global__ void k_contrast(int64_t n_px, double lam_s, double delta, double t_qu
     }
 }
 
+// FP32 version for the mixed path (relative error ~1e-7, far inside its 2e-6 tolerance).
+__global__ void k_contrast32(int64_t n_px, double lam_s, double delta, double t_quiet, int n_class,
+                             ClassTemps temps, float* c32) {
+    const double hck = kPlanckH * kLightSI / kBoltzmann * 1e10;
+    const float aq = (float)(hck / (lam_s * t_quiet));
+    float ac[SOAP_MAX_CLASSES];
+    for (int cl = 0; cl < n_class; cl++) ac[cl] = (float)(hck / (lam_s * temps.t[cl]));
+    const float fd = (float)delta;
+    for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < n_px;
+         m += (int64_t)gridDim.x * blockDim.x) {
+        const float inv = expf(-(float)m * fd);            // lambda_s / lambda_m
+        const float xq = expm1f(aq * inv);
+        for (int cl = 0; cl < n_class; cl++) c32[cl * n_px + m] = xq / expm1f(ac[cl] * inv);
+    }
+}
+
 // ---------------------------------------------------------------------------------------
 // InfoMap + per-phase velocity kernels (Alg. 5)
 // ---------------------------------------------------------------------------------------
@@ -59,11 +75,15 @@ __device__ __forceinline__ unsigned long long fx(double v, double scale) {
     return (unsigned long long)__double2ll_rn(v * scale);
 }
 
-// One block per phase.  Region centre at phase p (observer frame, rotation axis
+// Blocks (phase p, split).  Region centre at phase p (observer frame, rotation axis
 // (0, sin i, cos i)): star-frame (cos lat sin L, sin lat, cos lat cos L) with
 // L = lon + 360 p (1 + alpha sin^2 lat), tilted by the inclination.  A visible cell (x, y, mu)
 // belongs to the region iff (x, y, mu) . P >= sqrt(1 - r^2); the last region in list order
-// that contains it owns it.  The membership arithmetic uses explicitly rounded FP64 steps.
+// that contains it owns it.  An FP32 test decides cells farther than 2e-6 from the edge (its
+// error is below 1e-6); the others are decided by the explicitly rounded FP64 sequence.
+// Each block accumulates its cells in shared memory and adds its integers to the phase's
+// kernels with 64-bit atomics (integer addition is associative: the result is exact and
+// independent of order).
 __global__ void k_phase_hist(int N, int n_regions, const RegionDev* regs, const double* phases,
                              double incl_deg, double alpha, const double* cell_I,
                              const double* cell_w, const double* cell_mu, const int32_t* cell_j,
@@ -72,12 +92,16 @@ __global__ void k_phase_hist(int N, int n_regions, const RegionDev* regs, const 
                              unsigned int* flags) {
     __shared__ double sP[SOAP_MAX_REGIONS][3];
     __shared__ double sCos[SOAP_MAX_REGIONS];
+    __shared__ float sPf[SOAP_MAX_REGIONS][3];
+    __shared__ float sCosf[SOAP_MAX_REGIONS];
     __shared__ int sBox[SOAP_MAX_REGIONS][4];
     __shared__ int sCls[SOAP_MAX_REGIONS];
     extern __shared__ long long hist_sm[];
     const int p = blockIdx.x;
+    const int split = blockIdx.y, n_split = gridDim.y;
     const int nb = n_class * n_mu * n_taps;
-    long long* hist = use_smem ? hist_sm : kout + (int64_t)p * nb;
+    long long* gdst = kout + (int64_t)p * nb;
+    long long* hist = use_smem ? hist_sm : gdst;
     const double d2r = kPi / 180.0;
     const double phase = phases[p];
     if (threadIdx.x < n_regions) {
@@ -95,8 +119,11 @@ __global__ void k_phase_hist(int N, int n_regions, const RegionDev* regs, const 
         double P1 = __dsub_rn(__dmul_rn(py, si), __dmul_rn(pz, ci));
         double P2 = __dadd_rn(__dmul_rn(py, ci), __dmul_rn(pz, si));
         double r = g.radius;
+        double cr = __dsqrt_rn(__dsub_rn(1.0, __dmul_rn(r, r)));
         sP[threadIdx.x][0] = P0; sP[threadIdx.x][1] = P1; sP[threadIdx.x][2] = P2;
-        sCos[threadIdx.x] = __dsqrt_rn(__dsub_rn(1.0, __dmul_rn(r, r)));
+        sPf[threadIdx.x][0] = (float)P0; sPf[threadIdx.x][1] = (float)P1; sPf[threadIdx.x][2] = (float)P2;
+        sCos[threadIdx.x] = cr;
+        sCosf[threadIdx.x] = (float)cr;
         sCls[threadIdx.x] = g.cls;
         // conservative cell box of the cap: angle to an axis +- cap radius
         double a = asin(fmin(r, 1.0));
@@ -115,12 +142,14 @@ __global__ void k_phase_hist(int N, int n_regions, const RegionDev* regs, const 
     if (use_smem)
         for (int t = threadIdx.x; t < nb; t += blockDim.x) hist[t] = 0;
     __syncthreads();
+    const float invN = 1.0f / (float)N;
     for (int r = 0; r < n_regions; r++) {
         const int i0 = sBox[r][0], i1 = sBox[r][1], j0 = sBox[r][2], j1 = sBox[r][3];
         if (i1 < i0 || j1 < j0) continue;
         const int wdt = i1 - i0 + 1;
         const int64_t area = (int64_t)wdt * (j1 - j0 + 1);
-        for (int64_t t = threadIdx.x; t < area; t += blockDim.x) {
+        for (int64_t t = (int64_t)split * blockDim.x + threadIdx.x; t < area;
+             t += (int64_t)n_split * blockDim.x) {
             int i = i0 + (int)(t % wdt), jj = j0 + (int)(t / wdt);
             bool dup = false;                 // visit each cell once: first box that holds it
             for (int q = 0; q < r; q++)
@@ -129,14 +158,23 @@ __global__ void k_phase_hist(int N, int n_regions, const RegionDev* regs, const 
             int64_t c = (int64_t)jj * N + i;
             int b = cell_bin[c];
             if (b < 0) continue;
-            double x = (double)(2 * i + 1 - N) / (double)N;
-            double y = (double)(2 * jj + 1 - N) / (double)N;
-            double mu = cell_mu[c];
+            const double mu = cell_mu[c];
+            const float xf = (float)(2 * i + 1 - N) * invN, yf = (float)(2 * jj + 1 - N) * invN;
+            const float muf = (float)mu;
             int owner = -1;
             for (int q = 0; q < n_regions; q++) {
-                double dot = __dadd_rn(__dadd_rn(__dmul_rn(x, sP[q][0]), __dmul_rn(y, sP[q][1])),
-                                       __dmul_rn(mu, sP[q][2]));
-                if (dot >= sCos[q]) owner = q;
+                const float df = fmaf(xf, sPf[q][0], fmaf(yf, sPf[q][1], muf * sPf[q][2]));
+                bool in;
+                if (df > sCosf[q] + 2e-6f) in = true;
+                else if (df < sCosf[q] - 2e-6f) in = false;
+                else {
+                    double x = (double)(2 * i + 1 - N) / (double)N;
+                    double y = (double)(2 * jj + 1 - N) / (double)N;
+                    double dot = __dadd_rn(__dadd_rn(__dmul_rn(x, sP[q][0]), __dmul_rn(y, sP[q][1])),
+                                           __dmul_rn(mu, sP[q][2]));
+                    in = dot >= sCos[q];
+                }
+                if (in) owner = q;
             }
             if (owner < 0) continue;
             int cls = sCls[owner];
@@ -150,8 +188,8 @@ __global__ void k_phase_hist(int N, int n_regions, const RegionDev* regs, const 
     }
     if (use_smem) {
         __syncthreads();
-        long long* dst = kout + (int64_t)p * nb;
-        for (int t = threadIdx.x; t < nb; t += blockDim.x) dst[t] = hist[t];
+        for (int t = threadIdx.x; t < nb; t += blockDim.x)
+            if (hist[t]) atomicAdd((unsigned long long*)&gdst[t], (unsigned long long)hist[t]);
     }
 }
 
@@ -162,47 +200,53 @@ __global__ void k_phase_hist(int N, int n_regions, const RegionDev* regs, const 
 // mode 1 (active): group 0 = -sum_cl K (quiet rows), group g = +K of class g-1.
 // Block pb covers phases pb*PB .. pb*PB+PB-1.  Outputs per block: jobs[max_jobs],
 // gstart[G+1] (job index where each group starts), coefficients [..][n_k][PB] in c64/c32.
-__global__ void k_build_jobs(const long long* kfix, int n_phases, int n_class, int n_mu, int n_taps,
-                             int tap_min, int PB, int mode, double inv_scale, Job* jobs,
+__global__ void k_build_jobs(const long long* __restrict__ kfix, int n_phases, int n_class, int n_mu,
+                             int n_taps, int tap_min, int PB, int mode, double inv_scale, Job* jobs,
                              int* gstart, double* c64, float* c32, int max_jobs, int max_coef,
-                             unsigned int* flags) {
+                             int use_smem, unsigned int* flags) {
     __shared__ int s_lo[(1 + SOAP_MAX_CLASSES) * SOAP_MAX_MU];
     __shared__ int s_hi[(1 + SOAP_MAX_CLASSES) * SOAP_MAX_MU];
     __shared__ int s_idx[(1 + SOAP_MAX_CLASSES) * SOAP_MAX_MU];
     __shared__ int s_off[(1 + SOAP_MAX_CLASSES) * SOAP_MAX_MU];
+    extern __shared__ long long s_k[];
     const int pb = blockIdx.x;
     const int G = mode == 0 ? 1 : 1 + n_class;
     const int ngb = G * n_mu;
     const int p0 = pb * PB;
+    const int np = min(PB, n_phases - p0);
     const int64_t nb = (int64_t)n_class * n_mu * n_taps;
-    auto value = [&](int g, int b, int p, int kk) -> long long {
-        if (p >= n_phases) return 0;
-        const long long* base = kfix + (int64_t)p * nb;
-        if (mode == 0) return base[(int64_t)b * n_taps + kk];
-        if (g == 0) {
+    // the block's slice of kernels, [np][n_class][n_mu][n_taps], staged with coalesced loads
+    const long long* src = kfix + (int64_t)p0 * nb;
+    const long long* K = src;
+    if (use_smem) {
+        for (int64_t t = threadIdx.x; t < (int64_t)np * nb; t += blockDim.x) s_k[t] = src[t];
+        __syncthreads();
+        K = s_k;
+    }
+    auto value = [&](int g, int b, int pl, int kk) -> long long {
+        if (pl >= np) return 0;
+        const long long* base = K + (int64_t)pl * nb;
+        if (g == 0 && mode == 1) {
             long long s = 0;
             for (int cl = 0; cl < n_class; cl++) s += base[((int64_t)cl * n_mu + b) * n_taps + kk];
             return -s;
         }
-        return base[((int64_t)(g - 1) * n_mu + b) * n_taps + kk];
-    };
-    auto nonzero = [&](int g, int b, int p, int kk) -> bool {
-        if (p >= n_phases) return false;
-        const long long* base = kfix + (int64_t)p * nb;
-        if (mode == 0) return base[(int64_t)b * n_taps + kk] != 0;
-        if (g == 0) {
-            for (int cl = 0; cl < n_class; cl++)
-                if (base[((int64_t)cl * n_mu + b) * n_taps + kk] != 0) return true;
-            return false;
-        }
-        return base[((int64_t)(g - 1) * n_mu + b) * n_taps + kk] != 0;
+        const int cl = mode == 0 ? 0 : g - 1;
+        return base[((int64_t)cl * n_mu + b) * n_taps + kk];
     };
     for (int t = threadIdx.x; t < ngb; t += blockDim.x) {
         int g = t / n_mu, b = t % n_mu;
         int lo = n_taps, hi = -1;
-        for (int p = p0; p < p0 + PB; p++)
-            for (int kk = 0; kk < n_taps; kk++)
-                if (nonzero(g, b, p, kk)) { lo = min(lo, kk); hi = max(hi, kk); }
+        for (int pl = 0; pl < np; pl++) {
+            const long long* base = K + (int64_t)pl * nb;
+            const int c0 = (mode == 0 || g == 0) ? 0 : g - 1;
+            const int c1 = (mode == 1 && g == 0) ? n_class : c0 + 1;
+            for (int cl = c0; cl < c1; cl++) {
+                const long long* row = base + ((int64_t)cl * n_mu + b) * n_taps;
+                for (int kk = 0; kk < n_taps; kk++)
+                    if (row[kk] != 0) { lo = min(lo, kk); hi = max(hi, kk); }
+            }
+        }
         s_lo[t] = lo; s_hi[t] = hi;
     }
     __syncthreads();
@@ -226,15 +270,16 @@ __global__ void k_build_jobs(const long long* kfix, int n_phases, int n_class, i
         while (g_prev < G) { gs[++g_prev] = nj; }
     }
     __syncthreads();
-    // coefficients [kk][p]
-    for (int t = 0; t < ngb; t++) {
+    // coefficients [kk][p]: one warp per job
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int t = warp; t < ngb; t += nw) {
         if (s_idx[t] < 0) continue;
         int g = t / n_mu, b = t % n_mu;
         int nk = s_hi[t] - s_lo[t] + 1;
         int64_t base = (int64_t)pb * max_coef + s_off[t];
-        for (int e = threadIdx.x; e < nk * PB; e += blockDim.x) {
+        for (int e = lane; e < nk * PB; e += 32) {
             int kk = e / PB, pl = e % PB;
-            double v = (double)value(g, b, p0 + pl, s_lo[t] + kk) * inv_scale;
+            double v = (double)value(g, b, pl, s_lo[t] + kk) * inv_scale;
             c64[base + e] = v;
             c32[base + e] = (float)v;
         }
@@ -403,10 +448,16 @@ static soap_status build_jobs(soap_ctx* c, const long long* kfix, int n_phases, 
     *c64 = c->coefs.as<double>();
     *c32 = (float*)(c->coefs.as<char>() + off32);
     double inv_scale = std::ldexp(1.0, -c->fx_bits);
+    const int ncl = mode == 0 ? 1 : n_class;
+    size_t smem = (size_t)PB * ncl * c->n_mu * c->n_taps * sizeof(long long);
+    int use_smem = smem <= 96 * 1024;
+    if (!use_smem) smem = 0;
+    else if (smem > 48 * 1024)
+        SOAP_CUDA(cudaFuncSetAttribute(k_build_jobs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     SOAP_TIMED(c, SOAP_TIMER_JOBS,
-               k_build_jobs<<<*n_blocks, 128, 0, c->stream>>>(
-                   kfix, n_phases, mode == 0 ? 1 : n_class, c->n_mu, c->n_taps, c->tap_min, PB, mode,
-                   inv_scale, *jobs, *gstart, *c64, *c32, *max_jobs, *max_coef, c->flags);
+               k_build_jobs<<<*n_blocks, 256, smem, c->stream>>>(
+                   kfix, n_phases, ncl, c->n_mu, c->n_taps, c->tap_min, PB, mode, inv_scale, *jobs,
+                   *gstart, *c64, *c32, *max_jobs, *max_coef, use_smem, c->flags);
                SOAP_LAUNCHED(c));
     return SOAP_OK;
 }
@@ -417,10 +468,10 @@ soap_status toeplitz_quiet(soap_ctx* c, int precision, void* dst) {
     ClassTypes ct{};
     EffectList el{{SOAP_EFFECT_TOT, 0, 0}};
     if (precision == SOAP_FP64)
-        return launch_contract<double, 1, kR64, kT64>(c, nbk, G, mj, mc, jobs, gstart, c64, ct, nullptr,
-                                                     nullptr, 1, el, 1, (double*)dst, c->q64, nullptr, nullptr);
-    return launch_contract<float, 1, kR32, kT32>(c, nbk, G, mj, mc, jobs, gstart, c32, ct, nullptr,
-                                                nullptr, 1, el, 1, (float*)dst, c->q32, nullptr, nullptr);
+        return launch_contract<double, 1, 1, 128>(c, nbk, G, mj, mc, jobs, gstart, c64, ct, nullptr,
+                                                 nullptr, 1, el, 1, (double*)dst, c->q64, nullptr, nullptr);
+    return launch_contract<float, 1, 1, 128>(c, nbk, G, mj, mc, jobs, gstart, c32, ct, nullptr,
+                                            nullptr, 1, el, 1, (float*)dst, c->q32, nullptr, nullptr);
 }
 
 soap_status toeplitz_active(soap_ctx* c, const RegionDev* regions_host, int n_regions,
@@ -442,10 +493,16 @@ soap_status toeplitz_active(soap_ctx* c, const RegionDev* regions_host, int n_re
     if (n_class > 0) {
         ClassTemps tt{};
         for (int k = 0; k < n_class; k++) tt.t[k] = class_temp[k];
-        SOAP_TIMED(c, SOAP_TIMER_CONTRAST,
-                   k_contrast<<<grid_cap(c->n_px, 256, 152 * 8), 256, 0, c->stream>>>(
-                       c->n_px, c->lam_s, c->delta, c->t_quiet, n_class, tt, con64, con32);
-                   SOAP_LAUNCHED(c));
+        if (f64)
+            SOAP_TIMED(c, SOAP_TIMER_CONTRAST,
+                       k_contrast<<<grid_cap(c->n_px, 256, 152 * 8), 256, 0, c->stream>>>(
+                           c->n_px, c->lam_s, c->delta, c->t_quiet, n_class, tt, con64, con32);
+                       SOAP_LAUNCHED(c));
+        else
+            SOAP_TIMED(c, SOAP_TIMER_CONTRAST,
+                       k_contrast32<<<grid_cap(c->n_px, 256, 152 * 8), 256, 0, c->stream>>>(
+                           c->n_px, c->lam_s, c->delta, c->t_quiet, n_class, tt, con32);
+                       SOAP_LAUNCHED(c));
     }
     // regions and phases to the device (pageable copies are staged by the driver at once)
     size_t rbytes = (size_t)(n_regions > 0 ? n_regions : 1) * sizeof(RegionDev);
@@ -463,14 +520,17 @@ soap_status toeplitz_active(soap_ctx* c, const RegionDev* regions_host, int n_re
     long long* kfix = c->kphase.as<long long>();
     size_t smem = (size_t)nb * sizeof(long long);
     int use_smem = smem <= 160 * 1024;
+    SOAP_CUDA(cudaMemsetAsync(kfix, 0, kbytes, c->stream));
     if (!use_smem) {
-        SOAP_CUDA(cudaMemsetAsync(kfix, 0, kbytes, c->stream));
         smem = 0;
     } else if (smem > 48 * 1024) {
         SOAP_CUDA(cudaFuncSetAttribute(k_phase_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     }
+    // split each phase over several blocks so that all SMs take part
+    const int n_split = (int)std::max<int64_t>(1, std::min<int64_t>(8, (4 * 152 + n_phases - 1) / n_phases));
+    dim3 hgrid((unsigned)n_phases, (unsigned)n_split);
     SOAP_TIMED(c, SOAP_TIMER_PHASE_HIST,
-               k_phase_hist<<<n_phases, 256, smem, c->stream>>>(
+               k_phase_hist<<<hgrid, 256, smem, c->stream>>>(
                    c->N, n_regions, c->regions.as<RegionDev>(), c->phases.as<double>(), c->incl_deg,
                    c->alpha, c->cell_I, c->cell_w, c->cell_mu, c->cell_j, c->cell_bin, c->tap_min,
                    c->n_taps, c->n_mu, ncl, std::ldexp(1.0, c->fx_bits), kfix, use_smem, c->flags);

@@ -22,9 +22,44 @@ struct MuTable {
     double v[SOAP_MAX_MU];
 };
 
+// atanh(x) = x + x^3/3 + x^5/5 + x^7/7 + ...; for |x| <= 1e-3 the omitted terms are below
+// 1e-24 of x (GB300 FP64 is slow: four FMAs instead of a general atanh).
+__device__ __forceinline__ double atanh_small(double x) {
+    const double x2 = x * x;
+    return fma(x * x2, fma(x2, fma(x2, 1.0 / 7.0, 1.0 / 5.0), 1.0 / 3.0), x);
+}
+
+// expm1(e) = e + e^2/2 + e^3/6 + ...; for |e| <= 1e-3 terms beyond e^6 are below 1e-21 of e.
+__device__ __forceinline__ double expm1_small(double e) {
+    return fma(e * e, fma(e, fma(e, fma(e, fma(e, 1.0 / 720.0, 1.0 / 120.0), 1.0 / 24.0), 1.0 / 6.0), 0.5), e);
+}
+
+// Nearest tabulated mu, ties to the lower index, as the first minimum of |mu - mu_b| in FP64.
+// For a strictly increasing table the minimum lies next to the insertion point, so only a
+// window around it is scanned (same answer as the full scan).
+__device__ __forceinline__ int nearest_mu(double mu, int n_mu, const MuTable& mus, int sorted) {
+    int b0 = 0, b1 = n_mu - 1;
+    if (sorted) {
+        int lo = 0, hi = n_mu;                  // first index with mu_b >= mu
+        while (lo < hi) {
+            int mid = (lo + hi) >> 1;
+            if (mus.v[mid] < mu) lo = mid + 1; else hi = mid;
+        }
+        b0 = max(0, lo - 2);
+        b1 = min(n_mu - 1, lo + 1);
+    }
+    int best = b0;
+    double bd = fabs(__dsub_rn(mu, mus.v[b0]));
+    for (int b = b0 + 1; b <= b1; b++) {
+        double d = fabs(__dsub_rn(mu, mus.v[b]));
+        if (d < bd) { bd = d; best = b; }
+    }
+    return best;
+}
+
 __global__ void k_cell_geometry(int N, double vsini, double sin_i, double cos_i, double alpha,
                                 double u1, double u2, double delta, double expm1_delta,
-                                int n_mu, MuTable mus, int tap_min, int tap_max, double* cell_I,
+                                int n_mu, MuTable mus, int mu_sorted, int tap_min, int tap_max, double* cell_I,
                                 double* cell_w, double* cell_mu, int32_t* cell_j,
                                 int32_t* cell_bin, unsigned int* flags) {
     int64_t NN = (int64_t)N * N;
@@ -39,23 +74,19 @@ __global__ void k_cell_geometry(int N, double vsini, double sin_i, double cos_i,
             continue;
         }
         double mu = __dsqrt_rn(__dsub_rn(1.0, r2));
-        // nearest tabulated mu, ties to the lower index
-        int best = 0;
-        double bd = fabs(__dsub_rn(mu, mus.v[0]));
-        for (int b = 1; b < n_mu; b++) {
-            double d = fabs(__dsub_rn(mu, mus.v[b]));
-            if (d < bd) { bd = d; best = b; }
-        }
+        const int best = nearest_mu(mu, n_mu, mus, mu_sorted);
         double area = (2.0 / (double)N) * (2.0 / (double)N);
         double om = 1.0 - mu;
         double I = area * (1.0 - u1 * om - u2 * om * om);          // quadratic limb darkening
         double slat = y * sin_i + mu * cos_i;                        // sin(latitude) of the cell
         double v = vsini * x * (1.0 + alpha * slat * slat);          // x > 0 recedes
-        double ab = atanh(v / kCKms);                                // ln D
+        const double beta = v / kCKms;
+        double ab = fabs(beta) <= 1e-3 ? atanh_small(beta) : atanh(beta);    // ln D
         double s = ab / delta;
         double jd = ceil(s);
         int jt = (int)jd;
-        double w = expm1(fma(jd, delta, -ab)) / expm1_delta;
+        const double e = fma(jd, delta, -ab);                        // (j - s) Delta
+        double w = (delta <= 1e-3 ? expm1_small(e) : expm1(e)) / expm1_delta;
         if (jt - 1 < tap_min || jt > tap_max) {
             atomicOr(flags, kFlagTapRange);
             jt = jt < tap_min + 1 ? tap_min + 1 : tap_max;
@@ -114,17 +145,19 @@ __global__ void k_sum_intensity(int64_t NN, const double* cell_I, const int32_t*
 // Replicate-padded rows: dst[r][pad + n] = src[r][n]; left pad = src[r][0]; right pad =
 // src[r][n_px-1].  Reading dst at pad + m - k for any tap k reproduces the clamped index
 // min(max(m - k, 0), n_px - 1) of the interpolation's edge rule.
-__global__ void k_pad_rows(const double* src, int64_t n_px, int64_t pad, int64_t row_len, int rows,
-                           double* dst64, float* dst32) {
-    int64_t total = (int64_t)rows * row_len;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        int64_t r = t / row_len, e = t % row_len;
+__global__ void k_pad_rows(const double* __restrict__ src, int64_t n_px, int64_t pad, int64_t row_len,
+                           double* __restrict__ dst64, float* __restrict__ dst32) {
+    const int64_t r = blockIdx.y;
+    const double* s = src + r * n_px;
+    double* d64 = dst64 + r * row_len;
+    float* d32 = dst32 + r * row_len;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < row_len;
+         e += (int64_t)gridDim.x * blockDim.x) {
         int64_t n = e - pad;
         n = n < 0 ? 0 : (n >= n_px ? n_px - 1 : n);
-        double v = src[r * n_px + n];
-        dst64[t] = v;
-        dst32[t] = (float)v;
+        double v = __ldg(s + n);
+        d64[e] = v;
+        d32[e] = (float)v;
     }
 }
 
@@ -136,10 +169,9 @@ static int grid_for(int64_t n, int threads, int cap = 152 * 16) {
 }
 
 soap_status pad_rows(soap_ctx* c, const double* src, double* dst64, float* dst32, int rows) {
-    int64_t total = (int64_t)rows * c->row_len;
+    dim3 grid((unsigned)grid_for(c->row_len, 256, 64), (unsigned)rows);
     SOAP_TIMED(c, SOAP_TIMER_PAD_ROWS,
-               k_pad_rows<<<grid_for(total, 256), 256, 0, c->stream>>>(src, c->n_px, c->pad, c->row_len,
-                                                                       rows, dst64, dst32);
+               k_pad_rows<<<grid, 256, 0, c->stream>>>(src, c->n_px, c->pad, c->row_len, dst64, dst32);
                SOAP_LAUNCHED(c));
     return SOAP_OK;
 }
@@ -153,7 +185,7 @@ soap_status geometry_init(soap_ctx* c) {
     cudaEvent_t tb = c->profiling ? timer_begin(c) : nullptr;
     k_cell_geometry<<<grid_for(NN, 256), 256, 0, c->stream>>>(
         c->N, c->vsini, std::sin(incl), std::cos(incl), c->alpha, c->u1, c->u2, c->delta,
-        std::expm1(c->delta), c->n_mu, mus, c->tap_min, tap_max, c->cell_I, c->cell_w, c->cell_mu,
+        std::expm1(c->delta), c->n_mu, mus, c->mu_sorted, c->tap_min, tap_max, c->cell_I, c->cell_w, c->cell_mu,
         c->cell_j, c->cell_bin, c->flags);
     SOAP_LAUNCHED(c);
     // quiet kernels (exact integer sums)

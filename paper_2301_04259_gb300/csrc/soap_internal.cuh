@@ -100,6 +100,7 @@ struct soap_ctx {
     double vsini = 0, incl_deg = 0, u1 = 0, u2 = 0, alpha = 0;
     double lam_s = 0, lam_e = 0, t_quiet = 0, delta = 0;
     double mu_values[SOAP_MAX_MU] = {};
+    int mu_sorted = 0;      // mu_values strictly increasing (fast nearest-mu search)
 
     // velocity kernels: taps k = tap_min .. tap_min + n_taps - 1; padded rows
     int tap_min = 0;

@@ -259,6 +259,22 @@ def test_ccf_and_rv_config1(S, cfg1, cfg1_ref):
     assert np.abs(rv_32 - rv_o).max() * 1e5 <= 1.0
 
 
+def test_ccf_unsorted_mask_matches_sorted(S, cfg1, cfg1_ref):
+    """The windowed kernel (mask sorted by wavelength) and the generic one (any order) agree."""
+    _, ref = cfg1_ref
+    lo, step, nv = synth.velocity_grid(cfg1.star.vsini_kms)
+    F = ref[0, :7]
+    rv_a, _, ccf_a = _gpu_rv(S, cfg1, F, lo, step, nv)
+    perm = np.random.default_rng(5).permutation(cfg1.mask_lambda.size)
+    c2 = synth.config1(0)
+    c2.mask_lambda, c2.mask_weight = cfg1.mask_lambda[perm].copy(), cfg1.mask_weight[perm].copy()
+    rv_b, _, ccf_b = _gpu_rv(S, c2, F, lo, step, nv)
+    assert np.abs(ccf_a - ccf_b).max() <= 1e-13 * np.abs(ccf_a).max()
+    assert np.abs(rv_a - rv_b).max() * 1e5 <= 1e-4
+    rv_c, _, ccf_c = _gpu_rv(S, c2, F.astype(np.float32), lo, step, nv)
+    assert np.abs(rv_c - rv_a).max() * 1e5 <= 1.0
+
+
 def test_ccf_and_rv_fullsize(S, cfg2):
     c = cfg2
     lo, step, nv = synth.velocity_grid(c.star.vsini_kms)
