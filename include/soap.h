@@ -254,6 +254,36 @@ soap_status soap_get_kernel_time(soap_ctx* ctx, int32_t timer, double* total_ms,
 /* Zero all timers. */
 soap_status soap_reset_kernel_times(soap_ctx* ctx);
 
+/* Allocation-free CCF + RV fit, without a context.  The paper has no counterpart: this entry
+ * point exists for callers that may not allocate device memory once running (an application
+ * that gives the whole GPU to its own memory pool at start-up, a real-time pipeline where an
+ * allocation -- which can synchronise the device -- is not allowed after initialisation, or a
+ * plug-in that only receives buffers from its host).  It computes what soap_rv_ccf computes
+ * (same CCF definition, same fit) on caller buffers only and calls no cudaMalloc, cudaFree or
+ * other allocating routine.
+ *  Grid: lambda_start_A, lambda_end_A, n_px as in soap_star_desc.
+ *  spectra      DEVICE [n_spec][n_px], float64 (spectra_f32 = 0) or float32 (1).
+ *  mask_lambda, mask_weight  DEVICE [n_lines] (any order).
+ *  rv_kms       DEVICE [n_spec]; fit_params DEVICE [n_spec][4] or NULL; ccf_out DEVICE
+ *               [n_spec][n_v] or NULL.
+ *  cuda_stream  stream to enqueue on (NULL = legacy default stream); returns without
+ *               synchronising.
+ * Scratch: one fixed 16 MiB device array inside the library, which every GPU that loads the
+ * library keeps until the process exits.  A call needs
+ *   24 n_lines + 16 n_v + 8 n_spec n_v (ceil(n_lines / 128) + 2) bytes (plus alignment);
+ * larger requests are rejected with SOAP_ERANGE and a message giving both sizes.  The first
+ * call on each device looks up the array's device address (cudaGetSymbolAddress); make that
+ * first call before any stream capture.  All calls share the one array and it keeps the last
+ * call's contents (every element a call reads is written earlier in that call): calls whose
+ * GPU work can overlap -- on different streams, or from different threads -- race on it and
+ * must be serialised by the caller. */
+soap_status soap_rv_ccf_static(double lambda_start_A, double lambda_end_A, int64_t n_px,
+                               const void* spectra, int32_t spectra_f32, int32_t n_spec,
+                               const double* mask_lambda, const double* mask_weight,
+                               int32_t n_lines, double mask_width_kms, double v_lo, double v_step,
+                               int32_t n_v, double* rv_kms, double* fit_params, double* ccf_out,
+                               void* cuda_stream);
+
 /* Number of kernels this context has launched so far (for launch accounting). */
 soap_status soap_get_launch_count(const soap_ctx* ctx, uint64_t* out);
 

@@ -596,3 +596,136 @@ soap_status rv_ccf_run(soap_ctx* c, const void* spectra_dev, int f32, int n_spec
 }
 
 }  // namespace soap
+
+// ---------------------------------------------------------------------------------------
+// Allocation-free variant of the CCF + RV fit (soap_rv_ccf_static in soap.h)
+// ---------------------------------------------------------------------------------------
+// Some callers may not allocate device memory once they are running: applications that
+// hand every byte of the GPU to their own pool at start-up, real-time pipelines where an
+// allocation (which can synchronise the device) is not allowed after initialisation, or
+// plug-ins that only receive buffers from their host.  For them this entry point works on
+// caller buffers only; its scratch is the fixed array below, which every GPU that loads the
+// library holds until the process exits.
+namespace soap {
+
+constexpr size_t kStaticScratchBytes = size_t(16) << 20;      // 16 MiB
+static __device__ __align__(256) unsigned char g_rv_scratch[kStaticScratchBytes];
+
+constexpr int kStaticMaxDevices = 64;
+static void* g_rv_scratch_ptr[kStaticMaxDevices];              // device address per device
+static bool g_rv_scratch_ready[kStaticMaxDevices];
+
+// Device address of g_rv_scratch on the current device, looked up once per device.  In host
+// code g_rv_scratch is only a host-side handle, so the address must come from the runtime.
+static soap_status static_scratch(void** out) {
+    int dev = 0;
+    SOAP_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kStaticMaxDevices) {
+        set_error("device %d beyond the %d devices soap_rv_ccf_static supports", dev, kStaticMaxDevices);
+        return SOAP_ERANGE;
+    }
+    if (!g_rv_scratch_ready[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_rv_scratch);
+        if (e != cudaSuccess || !p) {
+            set_error("cudaGetSymbolAddress(g_rv_scratch) failed: %s", cudaGetErrorString(e));
+            return SOAP_ECUDA;
+        }
+        g_rv_scratch_ptr[dev] = p;
+        g_rv_scratch_ready[dev] = true;
+    }
+    *out = g_rv_scratch_ptr[dev];
+    return SOAP_OK;
+}
+
+}  // namespace soap
+
+extern "C" soap_status soap_rv_ccf_static(double lambda_start_A, double lambda_end_A, int64_t n_px,
+                                          const void* spectra, int32_t spectra_f32, int32_t n_spec,
+                                          const double* mask_lambda, const double* mask_weight,
+                                          int32_t n_lines, double mask_width_kms, double v_lo,
+                                          double v_step, int32_t n_v, double* rv_kms,
+                                          double* fit_params, double* ccf_out, void* cuda_stream) {
+    using namespace soap;
+    clear_error();
+    if (!spectra || !mask_lambda || !mask_weight || !rv_kms) { set_error("NULL argument"); return SOAP_EINVAL; }
+    if (!(lambda_start_A > 0) || !(lambda_end_A > lambda_start_A) || !std::isfinite(lambda_end_A) ||
+        n_px < 2 || n_px > (int64_t(1) << 28)) {
+        set_error("invalid wavelength grid"); return SOAP_EINVAL;
+    }
+    if (n_spec < 0 || n_lines < 1 || n_v < 5 || n_v > 4096) { set_error("need n_spec >= 0, n_lines >= 1, 5 <= n_v <= 4096"); return SOAP_EINVAL; }
+    if (!std::isfinite(mask_width_kms) || !(mask_width_kms > 0) || !std::isfinite(v_lo) ||
+        !std::isfinite(v_step) || !(v_step > 0)) {
+        set_error("mask width / velocity grid invalid"); return SOAP_EINVAL;
+    }
+    const double v_hi = v_lo + v_step * (n_v - 1);
+    if (!(std::fabs(v_lo) < kCKms) || !(std::fabs(v_hi) < kCKms)) { set_error("velocity grid reaches c"); return SOAP_EINVAL; }
+    const double delta = std::log1p((lambda_end_A - lambda_start_A) / lambda_start_A) / (double)(n_px - 1);
+    const double h = mask_width_kms / (2.0 * kCKms * delta);
+    if (2.0 * h > 14.0) { set_error("mask box spans more than 14 pixels"); return SOAP_ERANGE; }
+    if (n_spec == 0) return SOAP_OK;
+    // scratch layout, as in rv_ccf_run (generic line order kernel)
+    const int n_chunks = (n_lines + kLinesPerChunk - 1) / kLinesPerChunk;
+    auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+    size_t o_U = 0;
+    size_t o_f64 = al(o_U + (size_t)n_lines * 4);
+    size_t o_f32 = al(o_f64 + (size_t)n_lines * 8);
+    size_t o_w32 = al(o_f32 + (size_t)n_lines * 4);
+    size_t o_valid = al(o_w32 + (size_t)n_lines * 4);
+    size_t o_S = al(o_valid + (size_t)n_lines * 4);
+    size_t o_g64 = al(o_S + (size_t)n_v * 4);
+    size_t o_g32 = al(o_g64 + (size_t)n_v * 8);
+    size_t o_part = al(o_g32 + (size_t)n_v * 4);
+    size_t o_ccf = al(o_part + (size_t)n_chunks * n_spec * n_v * 8);
+    size_t o_y = al(o_ccf + (size_t)n_spec * n_v * 8);
+    size_t total = o_y + (size_t)n_spec * n_v * 8;
+    if (total > kStaticScratchBytes) {
+        set_error("soap_rv_ccf_static needs %zu bytes of scratch for %d lines x %d spectra x %d velocities; "
+                  "its fixed scratch holds %zu (use fewer spectra per call, or soap_rv_ccf)",
+                  total, n_lines, n_spec, n_v, kStaticScratchBytes);
+        return SOAP_ERANGE;
+    }
+    void* sp = nullptr;
+    SOAP_TRY(static_scratch(&sp));
+    char* base = static_cast<char*>(sp);
+    int* d_U = (int*)(base + o_U);
+    double* d_f64 = (double*)(base + o_f64);
+    float* d_f32 = (float*)(base + o_f32);
+    float* d_w32 = (float*)(base + o_w32);
+    int* d_valid = (int*)(base + o_valid);
+    int* d_S = (int*)(base + o_S);
+    double* d_g64 = (double*)(base + o_g64);
+    float* d_g32 = (float*)(base + o_g32);
+    double* d_part = (double*)(base + o_part);
+    double* d_ccf = ccf_out ? ccf_out : (double*)(base + o_ccf);
+    double* d_y = (double*)(base + o_y);
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+    // every scratch element read below is written earlier in this call: nothing needs clearing
+    k_ccf_lines<<<(n_lines + 255) / 256, 256, 0, stream>>>(
+        n_lines, mask_lambda, mask_weight, lambda_start_A, delta, h, std::atanh(v_lo / kCKms) / delta,
+        std::atanh(v_hi / kCKms) / delta, n_px, d_U, d_f64, d_f32, d_w32, d_valid);
+    SOAP_CUDA(cudaGetLastError());
+    k_ccf_velocities<<<(n_v + 127) / 128, 128, 0, stream>>>(n_v, v_lo, v_step, delta, d_S, d_g64, d_g32);
+    SOAP_CUDA(cudaGetLastError());
+    const int threads = n_v >= 256 ? 256 : ((n_v + 31) / 32) * 32;
+    if (spectra_f32) {
+        constexpr int SB = 16;
+        dim3 grid((unsigned)n_chunks, (unsigned)((n_spec + SB - 1) / SB));
+        k_ccf_partial<float, SB><<<grid, threads, 0, stream>>>(
+            n_lines, d_U, d_f32, d_valid, mask_weight, n_v, d_S, d_g32, 2.0 * h, n_px, n_spec,
+            (const float*)spectra, d_part);
+    } else {
+        constexpr int SB = 8;
+        dim3 grid((unsigned)n_chunks, (unsigned)((n_spec + SB - 1) / SB));
+        k_ccf_partial<double, SB><<<grid, threads, 0, stream>>>(
+            n_lines, d_U, d_f64, d_valid, mask_weight, n_v, d_S, d_g64, 2.0 * h, n_px, n_spec,
+            (const double*)spectra, d_part);
+    }
+    SOAP_CUDA(cudaGetLastError());
+    int64_t tot = (int64_t)n_spec * n_v * kReduceSplit;
+    k_ccf_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, stream>>>(n_chunks, n_spec, n_v, d_part, d_ccf);
+    SOAP_CUDA(cudaGetLastError());
+    k_gauss_fit<<<n_spec, kFitThreads, 0, stream>>>(n_spec, n_v, v_lo, v_step, d_ccf, d_y, rv_kms, fit_params);
+    SOAP_CUDA(cudaGetLastError());
+    return SOAP_OK;
+}

@@ -79,6 +79,7 @@ def _load():
         "soap_active_phases": (i32, [P, ctypes.POINTER(soap_region), i32, P, i32, u32, i32, P, ctypes.c_int]),
         "soap_rv_ccf": (i32, [P, P, i32, i32, ctypes.c_int, P, P, i32, d, d, d, i32, P, P, P, ctypes.c_int]),
         "soap_get_launch_count": (i32, [P, ctypes.POINTER(ctypes.c_uint64)]),
+        "soap_rv_ccf_static": (i32, [d, d, i64, P, i32, i32, P, P, i32, d, d, d, i32, P, P, P, P]),
         "soap_free": (None, [P]),
         "soap_last_error": (ctypes.c_char_p, []),
     }
@@ -230,6 +231,28 @@ def soap_rv_ccf(ctx, spectra, mask_lambda, mask_weight, mask_width_kms: float, v
     _check(_lib.soap_rv_ccf(ctx, sp, f32, n_spec, sdev, ctypes.c_void_p(ml.ctypes.data),
                             ctypes.c_void_p(mw.ctypes.data), ml.size, float(mask_width_kms),
                             float(v_lo), float(v_step), int(n_v), rp, fp, cp, rdev), "soap_rv_ccf")
+
+
+def soap_rv_ccf_static(lambda_start_A: float, lambda_end_A: float, n_px: int, spectra,
+                       mask_lambda, mask_weight, mask_width_kms: float, v_lo: float,
+                       v_step: float, n_v: int, rv_out, fit_out=None, ccf_out=None,
+                       stream=None) -> None:
+    """Allocation-free CCF + RV fit (no context); every array must be a CUDA tensor."""
+    arrays = [spectra, mask_lambda, mask_weight, rv_out] + [a for a in (fit_out, ccf_out) if a is not None]
+    for a in arrays:
+        if not (hasattr(a, "is_cuda") and a.is_cuda):
+            raise ValueError("soap_rv_ccf_static takes device arrays only")
+    sp, _ = _ptr(spectra)
+    f32 = int(str(spectra.dtype).endswith("float32"))
+    ml, _ = _ptr(mask_lambda)
+    mw, _ = _ptr(mask_weight)
+    rp, _ = _ptr(rv_out)
+    fp, _ = _ptr(fit_out)
+    cp, _ = _ptr(ccf_out)
+    _check(_lib.soap_rv_ccf_static(float(lambda_start_A), float(lambda_end_A), int(n_px), sp, f32,
+                                   int(spectra.shape[0]), ml, mw, int(mask_lambda.shape[0]),
+                                   float(mask_width_kms), float(v_lo), float(v_step), int(n_v),
+                                   rp, fp, cp, _stream_handle(stream)), "soap_rv_ccf_static")
 
 
 def soap_get_launch_count(ctx) -> int:
