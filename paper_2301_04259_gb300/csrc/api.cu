@@ -82,13 +82,14 @@ static soap_status to_device(soap_ctx* c, void* dst, const void* src, size_t n, 
 }
 
 static void free_ctx_memory(soap_ctx* c) {
-    void* ptrs[] = {c->cell_I, c->cell_w, c->cell_mu, c->cell_j, c->cell_bin, c->flags, c->q64,
+    void* ptrs[] = {c->cell_I, c->cell_w, c->cell_mu, c->cell_j, c->cell_bin, c->cell_mu32,
+                    c->cell_k0, c->cell_k1, c->flags, c->q64,
                     c->q32, c->a64[0], c->a32[0], c->a64[1], c->a32[1], c->kq_fixed,
                     c->sum_I_fixed};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     DevBuf* bufs[] = {&c->stage_in, &c->fq, &c->contrast, &c->kphase, &c->jobs, &c->coefs,
-                      &c->regions, &c->phases, &c->out_stage, &c->partial, &c->ccf_tmp};
+                      &c->regions, &c->region_geo, &c->phases, &c->out_stage, &c->partial, &c->ccf_tmp};
     for (DevBuf* b : bufs) release(*b);
     release_host(c->host_stage);
 }
@@ -264,6 +265,9 @@ soap_status soap_init_star(const soap_star_desc* s, const double* quiet_local, i
     ALLOC(c->cell_mu, NN * sizeof(double));
     ALLOC(c->cell_j, NN * sizeof(int32_t));
     ALLOC(c->cell_bin, NN * sizeof(int32_t));
+    ALLOC(c->cell_mu32, NN * sizeof(float));
+    ALLOC(c->cell_k0, NN * sizeof(long long));
+    ALLOC(c->cell_k1, NN * sizeof(long long));
     ALLOC(c->flags, sizeof(unsigned int));
     ALLOC(c->q64, rows * sizeof(double));
     ALLOC(c->q32, rows * sizeof(float));

@@ -53,18 +53,16 @@ __global__ void k_contrast(int64_t n_px, double lam_s, double delta, double t_qu
 }
 
 // FP32 version for the mixed path (relative error ~1e-7, far inside its 2e-6 tolerance).
-__global__ void k_contrast32(int64_t n_px, double lam_s, double delta, double t_quiet, int n_class,
-                             ClassTemps temps, float* c32) {
-    const double hck = kPlanckH * kLightSI / kBoltzmann * 1e10;
-    const float aq = (float)(hck / (lam_s * t_quiet));
-    float ac[SOAP_MAX_CLASSES];
-    for (int cl = 0; cl < n_class; cl++) ac[cl] = (float)(hck / (lam_s * temps.t[cl]));
-    const float fd = (float)delta;
+struct ClassConsts {
+    float a[SOAP_MAX_CLASSES];       // h c / (lambda_s k T_class)
+};
+
+__global__ void k_contrast32(int64_t n_px, float aq, float fd, int n_class, ClassConsts ac, float* c32) {
     for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < n_px;
          m += (int64_t)gridDim.x * blockDim.x) {
         const float inv = expf(-(float)m * fd);            // lambda_s / lambda_m
         const float xq = expm1f(aq * inv);
-        for (int cl = 0; cl < n_class; cl++) c32[cl * n_px + m] = xq / expm1f(ac[cl] * inv);
+        for (int cl = 0; cl < n_class; cl++) c32[cl * n_px + m] = xq / expm1f(ac.a[cl] * inv);
     }
 }
 
@@ -75,115 +73,123 @@ __device__ __forceinline__ unsigned long long fx(double v, double scale) {
     return (unsigned long long)__double2ll_rn(v * scale);
 }
 
-// Blocks (phase p, split).  Region centre at phase p (observer frame, rotation axis
-// (0, sin i, cos i)): star-frame (cos lat sin L, sin lat, cos lat cos L) with
-// L = lon + 360 p (1 + alpha sin^2 lat), tilted by the inclination.  A visible cell (x, y, mu)
-// belongs to the region iff (x, y, mu) . P >= sqrt(1 - r^2); the last region in list order
-// that contains it owns it.  An FP32 test decides cells farther than 2e-6 from the edge (its
-// error is below 1e-6); the others are decided by the explicitly rounded FP64 sequence.
-// Each block accumulates its cells in shared memory and adds its integers to the phase's
-// kernels with 64-bit atomics (integer addition is associative: the result is exact and
-// independent of order).
-__global__ void k_phase_hist(int N, int n_regions, const RegionDev* regs, const double* phases,
-                             double incl_deg, double alpha, const double* cell_I,
-                             const double* cell_w, const double* cell_mu, const int32_t* cell_j,
-                             const int32_t* cell_bin, int tap_min, int n_taps, int n_mu,
-                             int n_class, double scale, long long* kout, int use_smem,
-                             unsigned int* flags) {
-    __shared__ double sP[SOAP_MAX_REGIONS][3];
-    __shared__ double sCos[SOAP_MAX_REGIONS];
-    __shared__ float sPf[SOAP_MAX_REGIONS][3];
-    __shared__ float sCosf[SOAP_MAX_REGIONS];
-    __shared__ int sBox[SOAP_MAX_REGIONS][4];
-    __shared__ int sCls[SOAP_MAX_REGIONS];
+// Region centre, cap and cell box per (phase, region), computed once (FP64 trigonometry).
+struct RegionGeo {
+    double P[3];       // unit vector of the cap centre, observer frame
+    double cosr;       // cos of the cap's angular radius, sqrt(1 - r^2)
+    float Pf[3];
+    float cosrf;
+    int box[4];        // i0, i1, j0, j1 (empty if i1 < i0)
+    int cls;
+    int pad;
+};
+
+// Region centre at phase p (observer frame, rotation axis (0, sin i, cos i)): star-frame
+// (cos lat sin L, sin lat, cos lat cos L) with L = lon + 360 p (1 + alpha sin^2 lat), tilted by
+// the inclination; written with explicitly rounded FP64 steps.  The cell box is conservative:
+// the cap reaches axis angles within +-asin(r) of the centre's.
+__global__ void k_region_geo(int N, int n_regions, int n_phases, const RegionDev* regs,
+                             const double* phases, double incl_deg, double alpha, RegionGeo* out) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_phases * n_regions) return;
+    const int p = t / n_regions, q = t % n_regions;
+    const double d2r = kPi / 180.0;
+    const RegionDev g = regs[q];
+    const double phase = phases[p];
+    double lat = __dmul_rn(g.lat_deg, d2r);
+    double sl = sin(lat), cl = cos(lat);
+    double lonp = __dadd_rn(g.lon_deg, __dmul_rn(__dmul_rn(360.0, phase),
+                                                 __dadd_rn(1.0, __dmul_rn(__dmul_rn(alpha, sl), sl))));
+    double lon = __dmul_rn(lonp, d2r);
+    double incl = __dmul_rn(incl_deg, d2r);
+    double si = sin(incl), ci = cos(incl);
+    double px = __dmul_rn(cl, sin(lon)), py = sl, pz = __dmul_rn(cl, cos(lon));
+    RegionGeo o;
+    o.P[0] = px;
+    o.P[1] = __dsub_rn(__dmul_rn(py, si), __dmul_rn(pz, ci));
+    o.P[2] = __dadd_rn(__dmul_rn(py, ci), __dmul_rn(pz, si));
+    const double r = g.radius;
+    o.cosr = __dsqrt_rn(__dsub_rn(1.0, __dmul_rn(r, r)));
+    for (int k = 0; k < 3; k++) o.Pf[k] = (float)o.P[k];
+    o.cosrf = (float)o.cosr;
+    o.cls = g.cls;
+    o.pad = 0;
+    const double a = asin(fmin(r, 1.0));
+    const double bx = acos(fmax(-1.0, fmin(1.0, o.P[0])));
+    const double by = acos(fmax(-1.0, fmin(1.0, o.P[1])));
+    const double bz = acos(fmax(-1.0, fmin(1.0, o.P[2])));
+    const double xhi = cos(fmax(0.0, bx - a)), xlo = cos(fmin(kPi, bx + a));
+    const double yhi = cos(fmax(0.0, by - a)), ylo = cos(fmin(kPi, by + a));
+    int i0 = (int)floor((xlo * N + N - 1) * 0.5) - 1, i1 = (int)ceil((xhi * N + N - 1) * 0.5) + 1;
+    int j0 = (int)floor((ylo * N + N - 1) * 0.5) - 1, j1 = (int)ceil((yhi * N + N - 1) * 0.5) + 1;
+    i0 = max(i0, 0); j0 = max(j0, 0); i1 = min(i1, N - 1); j1 = min(j1, N - 1);
+    if (bz - a > 0.5 * kPi + 1e-6) i1 = i0 - 1;          // cap entirely on the far side
+    o.box[0] = i0; o.box[1] = i1; o.box[2] = j0; o.box[3] = j1;
+    out[t] = o;
+}
+
+// Blocks (phase p, split).  A visible cell (x, y, mu) belongs to a region iff
+// (x, y, mu) . P >= sqrt(1 - r^2); the last region in list order that contains it owns it.  An
+// FP32 test decides cells farther than 2e-6 from the edge (its error is below 1e-6); the others
+// are decided by the explicitly rounded FP64 sequence.  Owned cells add their precomputed
+// fixed-point contributions to the block's shared-memory kernels, which are then added to the
+// phase's kernels with 64-bit atomics (exact, order-independent).
+__global__ void k_phase_hist(int N, int n_regions, const RegionGeo* __restrict__ geo,
+                             const double* __restrict__ cell_mu, const float* __restrict__ cell_mu32,
+                             const int32_t* __restrict__ cell_j, const int32_t* __restrict__ cell_bin,
+                             const long long* __restrict__ cell_k0, const long long* __restrict__ cell_k1,
+                             int tap_min, int n_taps, int n_mu, int n_class, long long* kout,
+                             int use_smem, unsigned int* flags) {
+    __shared__ RegionGeo sg[SOAP_MAX_REGIONS];
     extern __shared__ long long hist_sm[];
     const int p = blockIdx.x;
     const int split = blockIdx.y, n_split = gridDim.y;
     const int nb = n_class * n_mu * n_taps;
     long long* gdst = kout + (int64_t)p * nb;
     long long* hist = use_smem ? hist_sm : gdst;
-    const double d2r = kPi / 180.0;
-    const double phase = phases[p];
-    if (threadIdx.x < n_regions) {
-        const RegionDev g = regs[threadIdx.x];
-        double lat = __dmul_rn(g.lat_deg, d2r);
-        double sl = sin(lat), cl = cos(lat);
-        double lonp = __dadd_rn(g.lon_deg,
-                                __dmul_rn(__dmul_rn(360.0, phase),
-                                          __dadd_rn(1.0, __dmul_rn(__dmul_rn(alpha, sl), sl))));
-        double lon = __dmul_rn(lonp, d2r);
-        double incl = __dmul_rn(incl_deg, d2r);
-        double si = sin(incl), ci = cos(incl);
-        double px = __dmul_rn(cl, sin(lon)), py = sl, pz = __dmul_rn(cl, cos(lon));
-        double P0 = px;
-        double P1 = __dsub_rn(__dmul_rn(py, si), __dmul_rn(pz, ci));
-        double P2 = __dadd_rn(__dmul_rn(py, ci), __dmul_rn(pz, si));
-        double r = g.radius;
-        double cr = __dsqrt_rn(__dsub_rn(1.0, __dmul_rn(r, r)));
-        sP[threadIdx.x][0] = P0; sP[threadIdx.x][1] = P1; sP[threadIdx.x][2] = P2;
-        sPf[threadIdx.x][0] = (float)P0; sPf[threadIdx.x][1] = (float)P1; sPf[threadIdx.x][2] = (float)P2;
-        sCos[threadIdx.x] = cr;
-        sCosf[threadIdx.x] = (float)cr;
-        sCls[threadIdx.x] = g.cls;
-        // conservative cell box of the cap: angle to an axis +- cap radius
-        double a = asin(fmin(r, 1.0));
-        double bx = acos(fmax(-1.0, fmin(1.0, P0)));
-        double by = acos(fmax(-1.0, fmin(1.0, P1)));
-        double bz = acos(fmax(-1.0, fmin(1.0, P2)));
-        double xhi = cos(fmax(0.0, bx - a)), xlo = cos(fmin(kPi, bx + a));
-        double yhi = cos(fmax(0.0, by - a)), ylo = cos(fmin(kPi, by + a));
-        int i0 = (int)floor((xlo * N + N - 1) * 0.5) - 1, i1 = (int)ceil((xhi * N + N - 1) * 0.5) + 1;
-        int j0 = (int)floor((ylo * N + N - 1) * 0.5) - 1, j1 = (int)ceil((yhi * N + N - 1) * 0.5) + 1;
-        i0 = max(i0, 0); j0 = max(j0, 0); i1 = min(i1, N - 1); j1 = min(j1, N - 1);
-        if (bz - a > 0.5 * kPi + 1e-6) { i1 = i0 - 1; }        // cap entirely on the far side
-        sBox[threadIdx.x][0] = i0; sBox[threadIdx.x][1] = i1;
-        sBox[threadIdx.x][2] = j0; sBox[threadIdx.x][3] = j1;
-    }
+    if (threadIdx.x < n_regions) sg[threadIdx.x] = geo[(int64_t)p * n_regions + threadIdx.x];
     if (use_smem)
         for (int t = threadIdx.x; t < nb; t += blockDim.x) hist[t] = 0;
     __syncthreads();
     const float invN = 1.0f / (float)N;
     for (int r = 0; r < n_regions; r++) {
-        const int i0 = sBox[r][0], i1 = sBox[r][1], j0 = sBox[r][2], j1 = sBox[r][3];
+        const int i0 = sg[r].box[0], i1 = sg[r].box[1], j0 = sg[r].box[2], j1 = sg[r].box[3];
         if (i1 < i0 || j1 < j0) continue;
         const int wdt = i1 - i0 + 1;
         const int64_t area = (int64_t)wdt * (j1 - j0 + 1);
         for (int64_t t = (int64_t)split * blockDim.x + threadIdx.x; t < area;
              t += (int64_t)n_split * blockDim.x) {
-            int i = i0 + (int)(t % wdt), jj = j0 + (int)(t / wdt);
+            const int i = i0 + (int)(t % wdt), jj = j0 + (int)(t / wdt);
             bool dup = false;                 // visit each cell once: first box that holds it
             for (int q = 0; q < r; q++)
-                if (i >= sBox[q][0] && i <= sBox[q][1] && jj >= sBox[q][2] && jj <= sBox[q][3]) dup = true;
+                if (i >= sg[q].box[0] && i <= sg[q].box[1] && jj >= sg[q].box[2] && jj <= sg[q].box[3]) dup = true;
             if (dup) continue;
-            int64_t c = (int64_t)jj * N + i;
-            int b = cell_bin[c];
+            const int64_t c = (int64_t)jj * N + i;
+            const int b = cell_bin[c];
             if (b < 0) continue;
-            const double mu = cell_mu[c];
             const float xf = (float)(2 * i + 1 - N) * invN, yf = (float)(2 * jj + 1 - N) * invN;
-            const float muf = (float)mu;
+            const float muf = cell_mu32[c];
             int owner = -1;
             for (int q = 0; q < n_regions; q++) {
-                const float df = fmaf(xf, sPf[q][0], fmaf(yf, sPf[q][1], muf * sPf[q][2]));
+                const float df = fmaf(xf, sg[q].Pf[0], fmaf(yf, sg[q].Pf[1], muf * sg[q].Pf[2]));
                 bool in;
-                if (df > sCosf[q] + 2e-6f) in = true;
-                else if (df < sCosf[q] - 2e-6f) in = false;
+                if (df > sg[q].cosrf + 2e-6f) in = true;
+                else if (df < sg[q].cosrf - 2e-6f) in = false;
                 else {
-                    double x = (double)(2 * i + 1 - N) / (double)N;
-                    double y = (double)(2 * jj + 1 - N) / (double)N;
-                    double dot = __dadd_rn(__dadd_rn(__dmul_rn(x, sP[q][0]), __dmul_rn(y, sP[q][1])),
-                                           __dmul_rn(mu, sP[q][2]));
-                    in = dot >= sCos[q];
+                    const double x = (double)(2 * i + 1 - N) / (double)N;
+                    const double y = (double)(2 * jj + 1 - N) / (double)N;
+                    const double dot = __dadd_rn(__dadd_rn(__dmul_rn(x, sg[q].P[0]), __dmul_rn(y, sg[q].P[1])),
+                                                 __dmul_rn(cell_mu[c], sg[q].P[2]));
+                    in = dot >= sg[q].cosr;
                 }
                 if (in) owner = q;
             }
             if (owner < 0) continue;
-            int cls = sCls[owner];
-            int kk = cell_j[c] - tap_min;
+            const int kk = cell_j[c] - tap_min;
             if (kk < 1 || kk >= n_taps) { atomicOr(flags, kFlagTapRange); continue; }
-            double I = cell_I[c], w = cell_w[c];
-            long long* h = hist + ((int64_t)cls * n_mu + b) * n_taps;
-            atomicAdd((unsigned long long*)&h[kk], fx(I * (1.0 - w), scale));
-            atomicAdd((unsigned long long*)&h[kk - 1], fx(I * w, scale));
+            long long* h = hist + ((int64_t)sg[owner].cls * n_mu + b) * n_taps;
+            atomicAdd((unsigned long long*)&h[kk], (unsigned long long)cell_k0[c]);
+            atomicAdd((unsigned long long*)&h[kk - 1], (unsigned long long)cell_k1[c]);
         }
     }
     if (use_smem) {
@@ -219,7 +225,20 @@ __global__ void k_build_jobs(const long long* __restrict__ kfix, int n_phases, i
     const long long* src = kfix + (int64_t)p0 * nb;
     const long long* K = src;
     if (use_smem) {
-        for (int64_t t = threadIdx.x; t < (int64_t)np * nb; t += blockDim.x) s_k[t] = src[t];
+        const int64_t n_el = (int64_t)np * nb;
+        for (int64_t t0 = threadIdx.x; t0 < n_el; t0 += 8 * (int64_t)blockDim.x) {
+            long long v[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                const int64_t t = t0 + (int64_t)u * blockDim.x;
+                v[u] = t < n_el ? src[t] : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                const int64_t t = t0 + (int64_t)u * blockDim.x;
+                if (t < n_el) s_k[t] = v[u];
+            }
+        }
         __syncthreads();
         K = s_k;
     }
@@ -336,6 +355,7 @@ k_contract(int64_t n_px, int64_t row_len, int64_t pad, Rows<T> rows, const Job* 
         const Job J = jb[jj];
         const T* row = rows.q + (int64_t)J.bin * row_len;
         const T* cf = cb + J.coef_off;
+#pragma unroll 4
         for (int kk = 0; kk < J.n_k; kk++) {
             const int64_t k = J.k_lo + kk;
             T s[R];
@@ -363,6 +383,7 @@ k_contract(int64_t n_px, int64_t row_len, int64_t pad, Rows<T> rows, const Job* 
             const Job J = jb[jj];
             const T* row = base + (int64_t)J.bin * row_len;
             const T* cf = cb + J.coef_off;
+#pragma unroll 4
             for (int kk = 0; kk < J.n_k; kk++) {
                 const int64_t k = J.k_lo + kk;
                 T s[R];
@@ -492,7 +513,12 @@ soap_status toeplitz_active(soap_ctx* c, const RegionDev* regions_host, int n_re
     float* con32 = (float*)(c->contrast.as<char>() + off32);
     if (n_class > 0) {
         ClassTemps tt{};
-        for (int k = 0; k < n_class; k++) tt.t[k] = class_temp[k];
+        ClassConsts cc{};
+        const double hck = kPlanckH * kLightSI / kBoltzmann * 1e10;
+        for (int k = 0; k < n_class; k++) {
+            tt.t[k] = class_temp[k];
+            cc.a[k] = (float)(hck / (c->lam_s * class_temp[k]));
+        }
         if (f64)
             SOAP_TIMED(c, SOAP_TIMER_CONTRAST,
                        k_contrast<<<grid_cap(c->n_px, 256, 152 * 8), 256, 0, c->stream>>>(
@@ -501,7 +527,7 @@ soap_status toeplitz_active(soap_ctx* c, const RegionDev* regions_host, int n_re
         else
             SOAP_TIMED(c, SOAP_TIMER_CONTRAST,
                        k_contrast32<<<grid_cap(c->n_px, 256, 152 * 8), 256, 0, c->stream>>>(
-                           c->n_px, c->lam_s, c->delta, c->t_quiet, n_class, tt, con32);
+                           c->n_px, (float)(hck / (c->lam_s * c->t_quiet)), (float)c->delta, n_class, cc, con32);
                        SOAP_LAUNCHED(c));
     }
     // regions and phases to the device (pageable copies are staged by the driver at once)
@@ -526,14 +552,23 @@ soap_status toeplitz_active(soap_ctx* c, const RegionDev* regions_host, int n_re
     } else if (smem > 48 * 1024) {
         SOAP_CUDA(cudaFuncSetAttribute(k_phase_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     }
+    // region centres and boxes per (phase, region)
+    SOAP_TRY(ensure(c->region_geo, (size_t)n_phases * (n_regions > 0 ? n_regions : 1) * sizeof(RegionGeo)));
+    if (n_regions > 0) {
+        const int nt = n_phases * n_regions;
+        k_region_geo<<<(nt + 127) / 128, 128, 0, c->stream>>>(
+            c->N, n_regions, n_phases, c->regions.as<RegionDev>(), c->phases.as<double>(), c->incl_deg,
+            c->alpha, c->region_geo.as<RegionGeo>());
+        SOAP_LAUNCHED(c);
+    }
     // split each phase over several blocks so that all SMs take part
     const int n_split = (int)std::max<int64_t>(1, std::min<int64_t>(8, (4 * 152 + n_phases - 1) / n_phases));
     dim3 hgrid((unsigned)n_phases, (unsigned)n_split);
     SOAP_TIMED(c, SOAP_TIMER_PHASE_HIST,
                k_phase_hist<<<hgrid, 256, smem, c->stream>>>(
-                   c->N, n_regions, c->regions.as<RegionDev>(), c->phases.as<double>(), c->incl_deg,
-                   c->alpha, c->cell_I, c->cell_w, c->cell_mu, c->cell_j, c->cell_bin, c->tap_min,
-                   c->n_taps, c->n_mu, ncl, std::ldexp(1.0, c->fx_bits), kfix, use_smem, c->flags);
+                   c->N, n_regions, c->region_geo.as<RegionGeo>(), c->cell_mu, c->cell_mu32, c->cell_j,
+                   c->cell_bin, c->cell_k0, c->cell_k1, c->tap_min, c->n_taps, c->n_mu, ncl, kfix,
+                   use_smem, c->flags);
                SOAP_LAUNCHED(c));
     // job tables
     const int PB = f64 ? kPB64 : kPB32;

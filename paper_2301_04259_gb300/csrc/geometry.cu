@@ -57,89 +57,75 @@ __device__ __forceinline__ int nearest_mu(double mu, int n_mu, const MuTable& mu
     return best;
 }
 
-__global__ void k_cell_geometry(int N, double vsini, double sin_i, double cos_i, double alpha,
-                                double u1, double u2, double delta, double expm1_delta,
-                                int n_mu, MuTable mus, int mu_sorted, int tap_min, int tap_max, double* cell_I,
-                                double* cell_w, double* cell_mu, int32_t* cell_j,
-                                int32_t* cell_bin, unsigned int* flags) {
-    int64_t NN = (int64_t)N * N;
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < NN;
-         c += (int64_t)gridDim.x * blockDim.x) {
-        int i = (int)(c % N), j = (int)(c / N);
-        double x = (double)(2 * i + 1 - N) / (double)N;
-        double y = (double)(2 * j + 1 - N) / (double)N;
-        double r2 = __dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y));
-        if (!(r2 < 1.0)) {
-            cell_I[c] = 0.0; cell_w[c] = 0.0; cell_mu[c] = 0.0; cell_j[c] = 0; cell_bin[c] = -1;
-            continue;
-        }
-        double mu = __dsqrt_rn(__dsub_rn(1.0, r2));
-        const int best = nearest_mu(mu, n_mu, mus, mu_sorted);
-        double area = (2.0 / (double)N) * (2.0 / (double)N);
-        double om = 1.0 - mu;
-        double I = area * (1.0 - u1 * om - u2 * om * om);          // quadratic limb darkening
-        double slat = y * sin_i + mu * cos_i;                        // sin(latitude) of the cell
-        double v = vsini * x * (1.0 + alpha * slat * slat);          // x > 0 recedes
-        const double beta = v / kCKms;
-        double ab = fabs(beta) <= 1e-3 ? atanh_small(beta) : atanh(beta);    // ln D
-        double s = ab / delta;
-        double jd = ceil(s);
-        int jt = (int)jd;
-        const double e = fma(jd, delta, -ab);                        // (j - s) Delta
-        double w = (delta <= 1e-3 ? expm1_small(e) : expm1(e)) / expm1_delta;
-        if (jt - 1 < tap_min || jt > tap_max) {
-            atomicOr(flags, kFlagTapRange);
-            jt = jt < tap_min + 1 ? tap_min + 1 : tap_max;
-        }
-        cell_I[c] = I; cell_w[c] = w; cell_mu[c] = mu; cell_j[c] = jt; cell_bin[c] = best;
-    }
-}
-
-// Fixed-point conversion: contributions are accumulated as 64-bit integers so that sums
-// are exact and independent of the order the GPU happens to add them in.
-__device__ __forceinline__ unsigned long long to_fixed(double v, double scale) {
-    return (unsigned long long)__double2ll_rn(v * scale);
-}
-
-// quiet velocity kernels K_b[k] = sum_{c in bin b} I_c [(1-w_c) d(k, j_c) + w_c d(k, j_c - 1)]
-__global__ void k_quiet_hist(int64_t NN, const double* cell_I, const double* cell_w,
-                             const int32_t* cell_j, const int32_t* cell_bin, int tap_min,
-                             int n_taps, int n_mu, double scale, long long* kout) {
-    extern __shared__ long long hist[];
-    int nb = n_mu * n_taps;
+// One block per (row j, 128 columns).  Besides the geometry it stores, per cell, the two
+// fixed-point contributions fx(I (1-w)) and fx(I w) of its two-tap kernel (reused by every
+// phase), an FP32 copy of mu (for the FP32 membership pre-test), and adds the cell to the quiet
+// velocity kernels (shared-memory 64-bit integer sums, then one atomic per non-zero bin) and
+// to the total intensity.  Integer sums are exact, so the result does not depend on order.
+__global__ void __launch_bounds__(128)
+k_geometry(int N, double vsini, double sin_i, double cos_i, double alpha, double u1, double u2,
+           double inv_c, double inv_delta, double delta, double inv_expm1_delta, int n_mu,
+           MuTable mus, int mu_sorted, int tap_min, int tap_max, int n_taps, double scale,
+           double* cell_I, double* cell_w, double* cell_mu, float* cell_mu32, int32_t* cell_j,
+           int32_t* cell_bin, long long* cell_k0, long long* cell_k1, long long* kq_fixed,
+           long long* sum2, unsigned int* flags) {
+    extern __shared__ long long hist[];                  // [n_mu][n_taps]
+    __shared__ double sy;
+    const int nb = n_mu * n_taps;
     for (int t = threadIdx.x; t < nb; t += blockDim.x) hist[t] = 0;
+    const int j = blockIdx.y;
+    if (threadIdx.x == 0) sy = (double)(2 * j + 1 - N) / (double)N;
     __syncthreads();
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < NN;
-         c += (int64_t)gridDim.x * blockDim.x) {
-        int b = cell_bin[c];
-        if (b < 0) continue;
-        double I = cell_I[c], w = cell_w[c];
-        int kk = cell_j[c] - tap_min;
-        atomicAdd((unsigned long long*)&hist[b * n_taps + kk], to_fixed(I * (1.0 - w), scale));
-        atomicAdd((unsigned long long*)&hist[b * n_taps + kk - 1], to_fixed(I * w, scale));
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long sumI = 0, cnt = 0;
+    if (i < N) {
+        const int64_t c = (int64_t)j * N + i;
+        const double x = (double)(2 * i + 1 - N) / (double)N;
+        const double y = sy;
+        const double r2 = __dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y));
+        if (!(r2 < 1.0)) {
+            cell_I[c] = 0.0; cell_w[c] = 0.0; cell_mu[c] = 0.0; cell_mu32[c] = 0.0f;
+            cell_j[c] = 0; cell_bin[c] = -1; cell_k0[c] = 0; cell_k1[c] = 0;
+        } else {
+            const double mu = __dsqrt_rn(__dsub_rn(1.0, r2));
+            const int best = nearest_mu(mu, n_mu, mus, mu_sorted);
+            const double area = (2.0 / (double)N) * (2.0 / (double)N);
+            const double om = 1.0 - mu;
+            const double I = area * (1.0 - u1 * om - u2 * om * om);      // quadratic limb darkening
+            const double slat = y * sin_i + mu * cos_i;                    // sin(latitude) of the cell
+            const double v = vsini * x * (1.0 + alpha * slat * slat);      // x > 0 recedes
+            const double beta = v * inv_c;
+            const double ab = fabs(beta) <= 1e-3 ? atanh_small(beta) : atanh(beta);   // ln D
+            const double jd = ceil(ab * inv_delta);                        // j = ceil(s), s = ln D / Delta
+            int jt = (int)jd;
+            const double e = fma(jd, delta, -ab);                          // (j - s) Delta
+            const double w = (delta <= 1e-3 ? expm1_small(e) : expm1(e)) * inv_expm1_delta;
+            if (jt - 1 < tap_min || jt > tap_max) {
+                atomicOr(flags, kFlagTapRange);
+                jt = jt < tap_min + 1 ? tap_min + 1 : tap_max;
+            }
+            const long long k0 = __double2ll_rn(I * (1.0 - w) * scale);
+            const long long k1 = __double2ll_rn(I * w * scale);
+            cell_I[c] = I; cell_w[c] = w; cell_mu[c] = mu; cell_mu32[c] = (float)mu;
+            cell_j[c] = jt; cell_bin[c] = best; cell_k0[c] = k0; cell_k1[c] = k1;
+            const int kk = jt - tap_min;
+            atomicAdd((unsigned long long*)&hist[best * n_taps + kk], (unsigned long long)k0);
+            atomicAdd((unsigned long long*)&hist[best * n_taps + kk - 1], (unsigned long long)k1);
+            sumI = (unsigned long long)__double2ll_rn(I * scale);
+            cnt = 1;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        sumI += __shfl_down_sync(0xffffffffu, sumI, o);
+        cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+    }
+    if ((threadIdx.x & 31) == 0 && cnt) {
+        atomicAdd((unsigned long long*)&sum2[0], sumI);
+        atomicAdd((unsigned long long*)&sum2[1], cnt);
     }
     __syncthreads();
     for (int t = threadIdx.x; t < nb; t += blockDim.x)
-        if (hist[t]) atomicAdd((unsigned long long*)&kout[t], (unsigned long long)hist[t]);
-}
-
-__global__ void k_sum_intensity(int64_t NN, const double* cell_I, const int32_t* cell_bin,
-                                double scale, long long* out2) {
-    unsigned long long acc = 0, cnt = 0;
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < NN;
-         c += (int64_t)gridDim.x * blockDim.x) {
-        if (cell_bin[c] < 0) continue;
-        acc += to_fixed(cell_I[c], scale);
-        cnt += 1;
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        acc += __shfl_down_sync(0xffffffffu, acc, o);
-        cnt += __shfl_down_sync(0xffffffffu, cnt, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        atomicAdd((unsigned long long*)&out2[0], acc);
-        atomicAdd((unsigned long long*)&out2[1], cnt);
-    }
+        if (hist[t]) atomicAdd((unsigned long long*)&kq_fixed[t], (unsigned long long)hist[t]);
 }
 
 // Replicate-padded rows: dst[r][pad + n] = src[r][n]; left pad = src[r][0]; right pad =
@@ -180,29 +166,21 @@ soap_status geometry_init(soap_ctx* c) {
     MuTable mus{};
     for (int b = 0; b < c->n_mu; b++) mus.v[b] = c->mu_values[b];
     double incl = c->incl_deg * (kPi / 180.0);
-    int64_t NN = (int64_t)c->N * c->N;
     int tap_max = c->tap_min + c->n_taps - 1;
-    cudaEvent_t tb = c->profiling ? timer_begin(c) : nullptr;
-    k_cell_geometry<<<grid_for(NN, 256), 256, 0, c->stream>>>(
-        c->N, c->vsini, std::sin(incl), std::cos(incl), c->alpha, c->u1, c->u2, c->delta,
-        std::expm1(c->delta), c->n_mu, mus, c->mu_sorted, c->tap_min, tap_max, c->cell_I, c->cell_w, c->cell_mu,
-        c->cell_j, c->cell_bin, c->flags);
-    SOAP_LAUNCHED(c);
-    // quiet kernels (exact integer sums)
     size_t nb = (size_t)c->n_mu * c->n_taps;
+    const double scale = std::ldexp(1.0, c->fx_bits);
+    cudaEvent_t tb = c->profiling ? timer_begin(c) : nullptr;
     SOAP_CUDA(cudaMemsetAsync(c->kq_fixed, 0, nb * sizeof(long long), c->stream));
+    SOAP_CUDA(cudaMemsetAsync(c->sum_I_fixed, 0, 2 * sizeof(long long), c->stream));
     size_t smem = nb * sizeof(long long);
     if (smem > 48 * 1024)
-        SOAP_CUDA(cudaFuncSetAttribute(k_quiet_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    double scale = std::ldexp(1.0, c->fx_bits);
-    int g = grid_for(NN, 256, 152 * 2);
-    k_quiet_hist<<<g, 256, smem, c->stream>>>(NN, c->cell_I, c->cell_w, c->cell_j, c->cell_bin,
-                                              c->tap_min, c->n_taps, c->n_mu, scale, c->kq_fixed);
-    SOAP_LAUNCHED(c);
-    // visible-cell count and total intensity (read by soap_get_star_info)
-    long long* d2 = c->sum_I_fixed;
-    SOAP_CUDA(cudaMemsetAsync(d2, 0, 2 * sizeof(long long), c->stream));
-    k_sum_intensity<<<grid_for(NN, 256, 152 * 4), 256, 0, c->stream>>>(NN, c->cell_I, c->cell_bin, scale, d2);
+        SOAP_CUDA(cudaFuncSetAttribute(k_geometry, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid((unsigned)((c->N + 127) / 128), (unsigned)c->N);
+    k_geometry<<<grid, 128, smem, c->stream>>>(
+        c->N, c->vsini, std::sin(incl), std::cos(incl), c->alpha, c->u1, c->u2, 1.0 / kCKms,
+        1.0 / c->delta, c->delta, 1.0 / std::expm1(c->delta), c->n_mu, mus, c->mu_sorted, c->tap_min,
+        tap_max, c->n_taps, scale, c->cell_I, c->cell_w, c->cell_mu, c->cell_mu32, c->cell_j,
+        c->cell_bin, c->cell_k0, c->cell_k1, c->kq_fixed, c->sum_I_fixed, c->flags);
     SOAP_LAUNCHED(c);
     if (c->profiling) timer_end(c, SOAP_TIMER_GEOMETRY, tb);
     return SOAP_OK;

@@ -117,6 +117,9 @@ struct soap_ctx {
     double* cell_mu = nullptr;     // mu (0 off disk)
     int32_t* cell_j = nullptr;     // tap j = ceil(s)
     int32_t* cell_bin = nullptr;   // nearest-mu bin, -1 off disk
+    float* cell_mu32 = nullptr;    // mu in FP32 (membership pre-test)
+    long long* cell_k0 = nullptr;  // fixed-point I (1 - w), tap j
+    long long* cell_k1 = nullptr;  // fixed-point I w, tap j - 1
     unsigned int* flags = nullptr; // device status word
 
     // local spectra, padded rows [n_mu][row_len]; element n at [pad + n]
@@ -138,6 +141,7 @@ struct soap_ctx {
     soap::DevBuf jobs;          // job tables
     soap::DevBuf coefs;         // job coefficients (fp64 and fp32)
     soap::DevBuf regions;       // region parameters
+    soap::DevBuf region_geo;    // region centres and boxes per (phase, region)
     soap::DevBuf phases;
     soap::DevBuf out_stage;     // device output when the caller wants host output
     soap::DevBuf partial;       // direct-form and CCF partial sums
