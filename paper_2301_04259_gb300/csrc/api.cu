@@ -85,10 +85,10 @@ static void free_ctx_memory(soap_ctx* c) {
     void* ptrs[] = {c->cell_I, c->cell_w, c->cell_mu, c->cell_j, c->cell_bin, c->cell_mu32,
                     c->cell_k0, c->cell_k1, c->flags, c->q64,
                     c->q32, c->a64[0], c->a32[0], c->a64[1], c->a32[1], c->kq_fixed,
-                    c->sum_I_fixed};
+                    c->sum_I_fixed, c->qjobs, c->qc64, c->qc32, c->geo_counter};
     for (void* p : ptrs)
         if (p) cudaFree(p);
-    DevBuf* bufs[] = {&c->stage_in, &c->fq, &c->contrast, &c->kphase, &c->jobs, &c->coefs,
+    DevBuf* bufs[] = {&c->stage_in, &c->fq, &c->contrast, &c->kphase, &c->jobs, &c->coefs, &c->job_counters,
                       &c->regions, &c->region_geo, &c->phases, &c->out_stage, &c->partial, &c->ccf_tmp};
     for (DevBuf* b : bufs) release(*b);
     release_host(c->host_stage);
@@ -273,6 +273,10 @@ soap_status soap_init_star(const soap_star_desc* s, const double* quiet_local, i
     ALLOC(c->q32, rows * sizeof(float));
     ALLOC(c->kq_fixed, (size_t)c->n_mu * SOAP_MAX_TAPS * sizeof(long long));
     ALLOC(c->sum_I_fixed, 2 * sizeof(long long));
+    ALLOC(c->qjobs, (size_t)c->n_mu * 32 + 16);
+    ALLOC(c->qc64, (size_t)c->n_mu * SOAP_MAX_TAPS * sizeof(double));
+    ALLOC(c->qc32, (size_t)c->n_mu * SOAP_MAX_TAPS * sizeof(float));
+    ALLOC(c->geo_counter, sizeof(int));
 #undef ALLOC
     if (e != cudaSuccess) {
         set_error("device allocation failed: %s", cudaGetErrorString(e));

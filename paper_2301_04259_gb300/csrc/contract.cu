@@ -21,14 +21,6 @@
 
 namespace soap {
 
-struct Job {
-    int32_t group;     // 0: all active cells (quiet rows, negative), g >= 1: class g-1
-    int32_t bin;       // mu bin
-    int32_t k_lo;      // first tap offset (pixels)
-    int32_t n_k;       // number of taps
-    int32_t coef_off;  // offset of coefficients [n_k][PB] within the block's coefficient slab
-    int32_t pad0, pad1, pad2;
-};
 
 // ---------------------------------------------------------------------------------------
 // contrast (Sect. 4.3.1): C(lambda) = (exp(hc/lambda k T_q) - 1) / (exp(hc/lambda k T_a) - 1)
@@ -65,6 +57,7 @@ __global__ void k_contrast32(int64_t n_px, float aq, float fd, int n_class, Clas
         for (int cl = 0; cl < n_class; cl++) c32[cl * n_px + m] = xq / expm1f(ac.a[cl] * inv);
     }
 }
+
 
 // ---------------------------------------------------------------------------------------
 // InfoMap + per-phase velocity kernels (Alg. 5)
@@ -139,7 +132,9 @@ __global__ void k_phase_hist(int N, int n_regions, const RegionGeo* __restrict__
                              const int32_t* __restrict__ cell_j, const int32_t* __restrict__ cell_bin,
                              const long long* __restrict__ cell_k0, const long long* __restrict__ cell_k1,
                              int tap_min, int n_taps, int n_mu, int n_class, long long* kout,
-                             int use_smem, unsigned int* flags) {
+                             int use_smem, int PB, double inv_scale, Job* jobs, int* gstart,
+                             double* c64, float* c32, int max_jobs, int max_coef, int* counters,
+                             int jobs_smem, unsigned int* flags) {
     __shared__ RegionGeo sg[SOAP_MAX_REGIONS];
     extern __shared__ long long hist_sm[];
     const int p = blockIdx.x;
@@ -197,111 +192,22 @@ __global__ void k_phase_hist(int N, int n_regions, const RegionGeo* __restrict__
         for (int t = threadIdx.x; t < nb; t += blockDim.x)
             if (hist[t]) atomicAdd((unsigned long long*)&gdst[t], (unsigned long long)hist[t]);
     }
-}
-
-// ---------------------------------------------------------------------------------------
-// job tables
-// ---------------------------------------------------------------------------------------
-// kfix: [n_phases][n_class][n_mu][n_taps].  mode 0 (quiet): one group, +K of class 0.
-// mode 1 (active): group 0 = -sum_cl K (quiet rows), group g = +K of class g-1.
-// Block pb covers phases pb*PB .. pb*PB+PB-1.  Outputs per block: jobs[max_jobs],
-// gstart[G+1] (job index where each group starts), coefficients [..][n_k][PB] in c64/c32.
-__global__ void k_build_jobs(const long long* __restrict__ kfix, int n_phases, int n_class, int n_mu,
-                             int n_taps, int tap_min, int PB, int mode, double inv_scale, Job* jobs,
-                             int* gstart, double* c64, float* c32, int max_jobs, int max_coef,
-                             int use_smem, unsigned int* flags) {
-    __shared__ int s_lo[(1 + SOAP_MAX_CLASSES) * SOAP_MAX_MU];
-    __shared__ int s_hi[(1 + SOAP_MAX_CLASSES) * SOAP_MAX_MU];
-    __shared__ int s_idx[(1 + SOAP_MAX_CLASSES) * SOAP_MAX_MU];
-    __shared__ int s_off[(1 + SOAP_MAX_CLASSES) * SOAP_MAX_MU];
-    extern __shared__ long long s_k[];
-    const int pb = blockIdx.x;
-    const int G = mode == 0 ? 1 : 1 + n_class;
-    const int ngb = G * n_mu;
-    const int p0 = pb * PB;
-    const int np = min(PB, n_phases - p0);
-    const int64_t nb = (int64_t)n_class * n_mu * n_taps;
-    // the block's slice of kernels, [np][n_class][n_mu][n_taps], staged with coalesced loads
-    const long long* src = kfix + (int64_t)p0 * nb;
-    const long long* K = src;
-    if (use_smem) {
-        const int64_t n_el = (int64_t)np * nb;
-        for (int64_t t0 = threadIdx.x; t0 < n_el; t0 += 8 * (int64_t)blockDim.x) {
-            long long v[8];
-#pragma unroll
-            for (int u = 0; u < 8; u++) {
-                const int64_t t = t0 + (int64_t)u * blockDim.x;
-                v[u] = t < n_el ? src[t] : 0;
-            }
-#pragma unroll
-            for (int u = 0; u < 8; u++) {
-                const int64_t t = t0 + (int64_t)u * blockDim.x;
-                if (t < n_el) s_k[t] = v[u];
-            }
-        }
-        __syncthreads();
-        K = s_k;
-    }
-    auto value = [&](int g, int b, int pl, int kk) -> long long {
-        if (pl >= np) return 0;
-        const long long* base = K + (int64_t)pl * nb;
-        if (g == 0 && mode == 1) {
-            long long s = 0;
-            for (int cl = 0; cl < n_class; cl++) s += base[((int64_t)cl * n_mu + b) * n_taps + kk];
-            return -s;
-        }
-        const int cl = mode == 0 ? 0 : g - 1;
-        return base[((int64_t)cl * n_mu + b) * n_taps + kk];
-    };
-    for (int t = threadIdx.x; t < ngb; t += blockDim.x) {
-        int g = t / n_mu, b = t % n_mu;
-        int lo = n_taps, hi = -1;
-        for (int pl = 0; pl < np; pl++) {
-            const long long* base = K + (int64_t)pl * nb;
-            const int c0 = (mode == 0 || g == 0) ? 0 : g - 1;
-            const int c1 = (mode == 1 && g == 0) ? n_class : c0 + 1;
-            for (int cl = c0; cl < c1; cl++) {
-                const long long* row = base + ((int64_t)cl * n_mu + b) * n_taps;
-                for (int kk = 0; kk < n_taps; kk++)
-                    if (row[kk] != 0) { lo = min(lo, kk); hi = max(hi, kk); }
-            }
-        }
-        s_lo[t] = lo; s_hi[t] = hi;
-    }
+    // The last block to finish among those feeding a phase block builds its job table
+    // (counter ticket after a memory fence: every other block's sums are visible by then).
+    __shared__ int s_last;
+    __threadfence();
     __syncthreads();
+    const int pbk = p / PB;
     if (threadIdx.x == 0) {
-        int nj = 0, off = 0, g_prev = -1;
-        int* gs = gstart + (int64_t)pb * (G + 1);
-        for (int t = 0; t < ngb; t++) {
-            int g = t / n_mu;
-            while (g_prev < g) { gs[++g_prev] = nj; }
-            if (s_hi[t] < s_lo[t]) { s_idx[t] = -1; continue; }
-            int nk = s_hi[t] - s_lo[t] + 1;
-            if (nj >= max_jobs || off + nk * PB > max_coef) { atomicOr(flags, kFlagJobOverflow); s_idx[t] = -1; continue; }
-            s_idx[t] = nj; s_off[t] = off;
-            Job J;
-            J.group = g; J.bin = t % n_mu; J.k_lo = tap_min + s_lo[t]; J.n_k = nk; J.coef_off = off;
-            J.pad0 = J.pad1 = J.pad2 = 0;
-            jobs[(int64_t)pb * max_jobs + nj] = J;
-            nj++;
-            off += nk * PB;
-        }
-        while (g_prev < G) { gs[++g_prev] = nj; }
+        const int np_pb = min(PB, (int)gridDim.x - pbk * PB);
+        const int t = atomicAdd(&counters[pbk], 1);
+        s_last = t == np_pb * n_split - 1;
     }
     __syncthreads();
-    // coefficients [kk][p]: one warp per job
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int t = warp; t < ngb; t += nw) {
-        if (s_idx[t] < 0) continue;
-        int g = t / n_mu, b = t % n_mu;
-        int nk = s_hi[t] - s_lo[t] + 1;
-        int64_t base = (int64_t)pb * max_coef + s_off[t];
-        for (int e = lane; e < nk * PB; e += 32) {
-            int kk = e / PB, pl = e % PB;
-            double v = (double)value(g, b, pl, s_lo[t] + kk) * inv_scale;
-            c64[base + e] = v;
-            c32[base + e] = (float)v;
-        }
+    if (s_last) {
+        __threadfence();
+        build_jobs_dev(kout, pbk, (int)gridDim.x, n_class, n_mu, n_taps, tap_min, PB, 1, inv_scale, jobs,
+                       gstart, c64, c32, max_jobs, max_coef, jobs_smem ? hist_sm : nullptr, flags);
     }
 }
 
@@ -321,6 +227,28 @@ struct ClassTypes {
 struct EffectList {
     int e[3];
 };
+
+// PB coefficients of one tap (16-byte vector loads when PB allows; coefficient slabs are
+// 256-byte aligned and every job's block is a multiple of PB elements).
+template <typename T, int PB>
+__device__ __forceinline__ void load_coefs(const T* __restrict__ src, T (&cv)[PB]) {
+    if constexpr (sizeof(T) == 4 && PB % 4 == 0) {
+#pragma unroll
+        for (int q = 0; q < PB / 4; q++) {
+            const float4 t = __ldg(reinterpret_cast<const float4*>(src) + q);
+            cv[4 * q] = t.x; cv[4 * q + 1] = t.y; cv[4 * q + 2] = t.z; cv[4 * q + 3] = t.w;
+        }
+    } else if constexpr (sizeof(T) == 8 && PB % 2 == 0) {
+#pragma unroll
+        for (int q = 0; q < PB / 2; q++) {
+            const double2 t = __ldg(reinterpret_cast<const double2*>(src) + q);
+            cv[2 * q] = t.x; cv[2 * q + 1] = t.y;
+        }
+    } else {
+#pragma unroll
+        for (int p = 0; p < PB; p++) cv[p] = __ldg(src + p);
+    }
+}
 
 // One thread: R pixels m = m0 + threadIdx.x + r*THREADS, PB phases.  acc holds
 // F_q - (group 0) + folded class terms; tmp accumulates one class before its fold.
@@ -361,12 +289,12 @@ k_contract(int64_t n_px, int64_t row_len, int64_t pad, Rows<T> rows, const Job* 
             T s[R];
 #pragma unroll
             for (int r = 0; r < R; r++) s[r] = __ldg(row + mc[r] - k);
+            T cv[PB];
+            load_coefs<T, PB>(cf + kk * PB, cv);
 #pragma unroll
-            for (int p = 0; p < PB; p++) {
-                const T cv = cf[kk * PB + p];
+            for (int p = 0; p < PB; p++)
 #pragma unroll
-                for (int r = 0; r < R; r++) acc[p][r] = fma(cv, s[r], acc[p][r]);
-            }
+                for (int r = 0; r < R; r++) acc[p][r] = fma(cv[p], s[r], acc[p][r]);
         }
     }
     // classes: tmp = sum_b K_cl,b * S, then acc += C_cl . tmp (TOT, FLUX) or tmp (BCONV)
@@ -389,12 +317,12 @@ k_contract(int64_t n_px, int64_t row_len, int64_t pad, Rows<T> rows, const Job* 
                 T s[R];
 #pragma unroll
                 for (int r = 0; r < R; r++) s[r] = __ldg(row + mc[r] - k);
+                T cv[PB];
+                load_coefs<T, PB>(cf + kk * PB, cv);
 #pragma unroll
-                for (int p = 0; p < PB; p++) {
-                    const T cv = cf[kk * PB + p];
+                for (int p = 0; p < PB; p++)
 #pragma unroll
-                    for (int r = 0; r < R; r++) tmp[p][r] = fma(cv, s[r], tmp[p][r]);
-                }
+                    for (int r = 0; r < R; r++) tmp[p][r] = fma(cv[p], s[r], tmp[p][r]);
             }
         }
 #pragma unroll
@@ -450,9 +378,9 @@ constexpr int kPB64 = 4, kR64 = 2, kT64 = 128;
 constexpr int kPB32 = 8, kR32 = 4, kT32 = 128;
 
 // job + coefficient scratch for a kernel set kfix with n_phases "phases" in blocks of PB
-static soap_status build_jobs(soap_ctx* c, const long long* kfix, int n_phases, int n_class,
-                              int PB, int mode, Job** jobs, int** gstart, double** c64,
-                              float** c32, int* n_blocks, int* G, int* max_jobs, int* max_coef) {
+static soap_status job_buffers(soap_ctx* c, int n_phases, int n_class, int PB, int mode, Job** jobs,
+                               int** gstart, double** c64, float** c32, int* n_blocks, int* G,
+                               int* max_jobs, int* max_coef) {
     *G = mode == 0 ? 1 : 1 + n_class;
     *n_blocks = (n_phases + PB - 1) / PB;
     *max_jobs = *G * c->n_mu;
@@ -468,24 +396,16 @@ static soap_status build_jobs(soap_ctx* c, const long long* kfix, int n_phases, 
     *gstart = (int*)(c->jobs.as<char>() + off_g);
     *c64 = c->coefs.as<double>();
     *c32 = (float*)(c->coefs.as<char>() + off32);
-    double inv_scale = std::ldexp(1.0, -c->fx_bits);
-    const int ncl = mode == 0 ? 1 : n_class;
-    size_t smem = (size_t)PB * ncl * c->n_mu * c->n_taps * sizeof(long long);
-    int use_smem = smem <= 96 * 1024;
-    if (!use_smem) smem = 0;
-    else if (smem > 48 * 1024)
-        SOAP_CUDA(cudaFuncSetAttribute(k_build_jobs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    SOAP_TIMED(c, SOAP_TIMER_JOBS,
-               k_build_jobs<<<*n_blocks, 256, smem, c->stream>>>(
-                   kfix, n_phases, ncl, c->n_mu, c->n_taps, c->tap_min, PB, mode, inv_scale, *jobs,
-                   *gstart, *c64, *c32, *max_jobs, *max_coef, use_smem, c->flags);
-               SOAP_LAUNCHED(c));
     return SOAP_OK;
 }
 
 soap_status toeplitz_quiet(soap_ctx* c, int precision, void* dst) {
-    Job* jobs; int* gstart; double* c64; float* c32; int nbk, G, mj, mc;
-    SOAP_TRY(build_jobs(c, c->kq_fixed, 1, 1, 1, 0, &jobs, &gstart, &c64, &c32, &nbk, &G, &mj, &mc));
+    // job table built by the geometry kernel
+    Job* jobs = c->qjobs;
+    int* gstart = reinterpret_cast<int*>(c->qjobs + c->n_mu);
+    double* c64 = c->qc64;
+    float* c32 = c->qc32;
+    const int nbk = 1, G = 1, mj = c->n_mu, mc = c->n_mu * SOAP_MAX_TAPS;
     ClassTypes ct{};
     EffectList el{{SOAP_EFFECT_TOT, 0, 0}};
     if (precision == SOAP_FP64)
@@ -544,14 +464,20 @@ soap_status toeplitz_active(soap_ctx* c, const RegionDev* regions_host, int n_re
     size_t kbytes = (size_t)n_phases * nb * sizeof(long long);
     SOAP_TRY(ensure(c->kphase, kbytes));
     long long* kfix = c->kphase.as<long long>();
-    size_t smem = (size_t)nb * sizeof(long long);
-    int use_smem = smem <= 160 * 1024;
+    // job tables are built by the last block of each phase block (fused into k_phase_hist)
+    const int PB = f64 ? kPB64 : kPB32;
+    Job* jobs; int* gstart; double* c64; float* c32; int nbk, G, mj, mc;
+    SOAP_TRY(job_buffers(c, n_phases, ncl, PB, 1, &jobs, &gstart, &c64, &c32, &nbk, &G, &mj, &mc));
+    SOAP_TRY(ensure(c->job_counters, (size_t)nbk * sizeof(int)));
+    SOAP_CUDA(cudaMemsetAsync(c->job_counters.p, 0, (size_t)nbk * sizeof(int), c->stream));
+    const size_t hist_bytes = (size_t)nb * sizeof(long long);
+    const size_t kslice_bytes = (size_t)PB * nb * sizeof(long long);
+    const int use_smem = hist_bytes <= 160 * 1024;
+    const int jobs_smem = kslice_bytes <= 96 * 1024;
+    size_t smem = std::max(use_smem ? hist_bytes : (size_t)0, jobs_smem ? kslice_bytes : (size_t)0);
     SOAP_CUDA(cudaMemsetAsync(kfix, 0, kbytes, c->stream));
-    if (!use_smem) {
-        smem = 0;
-    } else if (smem > 48 * 1024) {
+    if (smem > 48 * 1024)
         SOAP_CUDA(cudaFuncSetAttribute(k_phase_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    }
     // region centres and boxes per (phase, region)
     SOAP_TRY(ensure(c->region_geo, (size_t)n_phases * (n_regions > 0 ? n_regions : 1) * sizeof(RegionGeo)));
     if (n_regions > 0) {
@@ -568,12 +494,9 @@ soap_status toeplitz_active(soap_ctx* c, const RegionDev* regions_host, int n_re
                k_phase_hist<<<hgrid, 256, smem, c->stream>>>(
                    c->N, n_regions, c->region_geo.as<RegionGeo>(), c->cell_mu, c->cell_mu32, c->cell_j,
                    c->cell_bin, c->cell_k0, c->cell_k1, c->tap_min, c->n_taps, c->n_mu, ncl, kfix,
-                   use_smem, c->flags);
+                   use_smem, PB, std::ldexp(1.0, -c->fx_bits), jobs, gstart, c64, c32, mj, mc,
+                   c->job_counters.as<int>(), jobs_smem, c->flags);
                SOAP_LAUNCHED(c));
-    // job tables
-    const int PB = f64 ? kPB64 : kPB32;
-    Job* jobs; int* gstart; double* c64; float* c32; int nbk, G, mj, mc;
-    SOAP_TRY(build_jobs(c, kfix, n_phases, ncl, PB, 1, &jobs, &gstart, &c64, &c32, &nbk, &G, &mj, &mc));
     ClassTypes ct{};
     for (int k = 0; k < n_class; k++) ct.t[k] = class_type[k];
     EffectList el{{0, 0, 0}};

@@ -68,7 +68,8 @@ k_geometry(int N, double vsini, double sin_i, double cos_i, double alpha, double
            MuTable mus, int mu_sorted, int tap_min, int tap_max, int n_taps, double scale,
            double* cell_I, double* cell_w, double* cell_mu, float* cell_mu32, int32_t* cell_j,
            int32_t* cell_bin, long long* cell_k0, long long* cell_k1, long long* kq_fixed,
-           long long* sum2, unsigned int* flags) {
+           long long* sum2, Job* qjobs, int* qgstart, double* qc64, float* qc32, int q_max_coef,
+           int* counter, unsigned int* flags) {
     extern __shared__ long long hist[];                  // [n_mu][n_taps]
     __shared__ double sy;
     const int nb = n_mu * n_taps;
@@ -126,6 +127,20 @@ k_geometry(int N, double vsini, double sin_i, double cos_i, double alpha, double
     __syncthreads();
     for (int t = threadIdx.x; t < nb; t += blockDim.x)
         if (hist[t]) atomicAdd((unsigned long long*)&kq_fixed[t], (unsigned long long)hist[t]);
+    // the last block to finish builds the quiet job table (one "phase", one group)
+    __shared__ int s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int t = atomicAdd(counter, 1);
+        s_last = t == (int)(gridDim.x * gridDim.y) - 1;
+    }
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        build_jobs_dev(kq_fixed, 0, 1, 1, n_mu, n_taps, tap_min, 1, 0, 1.0 / scale, qjobs, qgstart, qc64,
+                       qc32, n_mu, q_max_coef, hist, flags);
+    }
 }
 
 // Replicate-padded rows: dst[r][pad + n] = src[r][n]; left pad = src[r][0]; right pad =
@@ -172,6 +187,7 @@ soap_status geometry_init(soap_ctx* c) {
     cudaEvent_t tb = c->profiling ? timer_begin(c) : nullptr;
     SOAP_CUDA(cudaMemsetAsync(c->kq_fixed, 0, nb * sizeof(long long), c->stream));
     SOAP_CUDA(cudaMemsetAsync(c->sum_I_fixed, 0, 2 * sizeof(long long), c->stream));
+    SOAP_CUDA(cudaMemsetAsync(c->geo_counter, 0, sizeof(int), c->stream));
     size_t smem = nb * sizeof(long long);
     if (smem > 48 * 1024)
         SOAP_CUDA(cudaFuncSetAttribute(k_geometry, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -180,7 +196,9 @@ soap_status geometry_init(soap_ctx* c) {
         c->N, c->vsini, std::sin(incl), std::cos(incl), c->alpha, c->u1, c->u2, 1.0 / kCKms,
         1.0 / c->delta, c->delta, 1.0 / std::expm1(c->delta), c->n_mu, mus, c->mu_sorted, c->tap_min,
         tap_max, c->n_taps, scale, c->cell_I, c->cell_w, c->cell_mu, c->cell_mu32, c->cell_j,
-        c->cell_bin, c->cell_k0, c->cell_k1, c->kq_fixed, c->sum_I_fixed, c->flags);
+        c->cell_bin, c->cell_k0, c->cell_k1, c->kq_fixed, c->sum_I_fixed, c->qjobs,
+        reinterpret_cast<int*>(c->qjobs + c->n_mu), c->qc64, c->qc32, c->n_mu * SOAP_MAX_TAPS,
+        c->geo_counter, c->flags);
     SOAP_LAUNCHED(c);
     if (c->profiling) timer_end(c, SOAP_TIMER_GEOMETRY, tb);
     return SOAP_OK;

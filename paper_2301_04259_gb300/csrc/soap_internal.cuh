@@ -87,6 +87,8 @@ enum DeviceFlag : unsigned int {
     kFlagJobOverflow = 4u      // a job table would overflow its capacity
 };
 
+struct Job;
+
 }  // namespace soap
 
 struct soap_ctx {
@@ -132,6 +134,11 @@ struct soap_ctx {
     // quiet velocity kernels, fixed point [n_mu][n_taps]
     long long* kq_fixed = nullptr;
     long long* sum_I_fixed = nullptr;   // [0] sum of I (fixed point), [1] visible cells
+    // quiet job table, rebuilt with the geometry: jobs [n_mu] then 2 group starts; coefficients
+    soap::Job* qjobs = nullptr;
+    double* qc64 = nullptr;
+    float* qc32 = nullptr;
+    int* geo_counter = nullptr;
 
     // scratch (grow-only)
     soap::DevBuf stage_in;      // host -> device staging of spectra
@@ -140,6 +147,7 @@ struct soap_ctx {
     soap::DevBuf kphase;        // fixed-point kernels [n_phases][n_class][n_mu][n_taps]
     soap::DevBuf jobs;          // job tables
     soap::DevBuf coefs;         // job coefficients (fp64 and fp32)
+    soap::DevBuf job_counters;  // per phase block: blocks done (fused job tables)
     soap::DevBuf regions;       // region parameters
     soap::DevBuf region_geo;    // region centres and boxes per (phase, region)
     soap::DevBuf phases;
@@ -191,5 +199,135 @@ soap_status rv_ccf_run(soap_ctx* c, const void* spectra_dev, int f32, int n_spec
                        const double* mask_lambda, const double* mask_weight, int n_lines,
                        double width_kms, double v_lo, double v_step, int n_v, double* rv_dev,
                        double* fit_dev, double* ccf_dev);
+
+}  // namespace soap
+
+// ---------------------------------------------------------------------------------------
+// job tables of the Toeplitz contraction (shared by geometry.cu and contract.cu)
+// ---------------------------------------------------------------------------------------
+namespace soap {
+
+struct Job {
+    int32_t group;     // 0: all active cells (quiet rows, negative), g >= 1: class g-1
+    int32_t bin;       // mu bin
+    int32_t k_lo;      // first tap offset (pixels)
+    int32_t n_k;       // number of taps
+    int32_t coef_off;  // offset of coefficients [n_k][PB] within the block's coefficient slab
+    int32_t pad0, pad1, pad2;
+};
+
+// ---------------------------------------------------------------------------------------
+// job tables
+// ---------------------------------------------------------------------------------------
+// kfix: [n_phases][n_class][n_mu][n_taps].  mode 0 (quiet): one group, +K of class 0.
+// mode 1 (active): group 0 = -sum_cl K (quiet rows), group g = +K of class g-1.
+// Block pb covers phases pb*PB .. pb*PB+PB-1.  Outputs per block: jobs[max_jobs],
+// gstart[G+1] (job index where each group starts), coefficients [..][n_k][PB] in c64/c32.
+__device__ __forceinline__ void build_jobs_dev(const long long* __restrict__ kfix, int pb, int n_phases, int n_class,
+                               int n_mu, int n_taps, int tap_min, int PB, int mode, double inv_scale,
+                               Job* jobs, int* gstart, double* c64, float* c32, int max_jobs,
+                               int max_coef, long long* s_k, unsigned int* flags) {
+    __shared__ int s_lo[(1 + SOAP_MAX_CLASSES) * SOAP_MAX_MU];
+    __shared__ int s_hi[(1 + SOAP_MAX_CLASSES) * SOAP_MAX_MU];
+    __shared__ int s_idx[(1 + SOAP_MAX_CLASSES) * SOAP_MAX_MU];
+    __shared__ int s_off[(1 + SOAP_MAX_CLASSES) * SOAP_MAX_MU];
+    const int use_smem = s_k != nullptr;
+    const int G = mode == 0 ? 1 : 1 + n_class;
+    const int ngb = G * n_mu;
+    const int p0 = pb * PB;
+    const int np = min(PB, n_phases - p0);
+    const int64_t nb = (int64_t)n_class * n_mu * n_taps;
+    // the block's slice of kernels, [np][n_class][n_mu][n_taps], staged with coalesced loads
+    const long long* src = kfix + (int64_t)p0 * nb;
+    const long long* K = src;
+    if (use_smem) {
+        const int64_t n_el = (int64_t)np * nb;
+        for (int64_t t0 = threadIdx.x; t0 < n_el; t0 += 8 * (int64_t)blockDim.x) {
+            long long v[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                const int64_t t = t0 + (int64_t)u * blockDim.x;
+                v[u] = t < n_el ? __ldcg(src + t) : 0;      // written by other blocks' atomics
+            }
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                const int64_t t = t0 + (int64_t)u * blockDim.x;
+                if (t < n_el) s_k[t] = v[u];
+            }
+        }
+        __syncthreads();
+        K = s_k;
+    }
+    auto value = [&](int g, int b, int pl, int kk) -> long long {
+        if (pl >= np) return 0;
+        const long long* base = K + (int64_t)pl * nb;
+        if (!use_smem) {
+            if (g == 0 && mode == 1) {
+                long long s = 0;
+                for (int cl = 0; cl < n_class; cl++) s += __ldcg(base + ((int64_t)cl * n_mu + b) * n_taps + kk);
+                return -s;
+            }
+            return __ldcg(base + ((int64_t)(mode == 0 ? 0 : g - 1) * n_mu + b) * n_taps + kk);
+        }
+        if (g == 0 && mode == 1) {
+            long long s = 0;
+            for (int cl = 0; cl < n_class; cl++) s += base[((int64_t)cl * n_mu + b) * n_taps + kk];
+            return -s;
+        }
+        const int cl = mode == 0 ? 0 : g - 1;
+        return base[((int64_t)cl * n_mu + b) * n_taps + kk];
+    };
+    for (int t = threadIdx.x; t < ngb; t += blockDim.x) {
+        int g = t / n_mu, b = t % n_mu;
+        int lo = n_taps, hi = -1;
+        for (int pl = 0; pl < np; pl++) {
+            const long long* base = K + (int64_t)pl * nb;
+            const int c0 = (mode == 0 || g == 0) ? 0 : g - 1;
+            const int c1 = (mode == 1 && g == 0) ? n_class : c0 + 1;
+            for (int cl = c0; cl < c1; cl++) {
+                const long long* row = base + ((int64_t)cl * n_mu + b) * n_taps;
+                for (int kk = 0; kk < n_taps; kk++)
+                    if ((use_smem ? row[kk] : __ldcg(row + kk)) != 0) { lo = min(lo, kk); hi = max(hi, kk); }
+            }
+        }
+        s_lo[t] = lo; s_hi[t] = hi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int nj = 0, off = 0, g_prev = -1;
+        int* gs = gstart + (int64_t)pb * (G + 1);
+        for (int t = 0; t < ngb; t++) {
+            int g = t / n_mu;
+            while (g_prev < g) { gs[++g_prev] = nj; }
+            if (s_hi[t] < s_lo[t]) { s_idx[t] = -1; continue; }
+            int nk = s_hi[t] - s_lo[t] + 1;
+            if (nj >= max_jobs || off + nk * PB > max_coef) { atomicOr(flags, kFlagJobOverflow); s_idx[t] = -1; continue; }
+            s_idx[t] = nj; s_off[t] = off;
+            Job J;
+            J.group = g; J.bin = t % n_mu; J.k_lo = tap_min + s_lo[t]; J.n_k = nk; J.coef_off = off;
+            J.pad0 = J.pad1 = J.pad2 = 0;
+            jobs[(int64_t)pb * max_jobs + nj] = J;
+            nj++;
+            off += nk * PB;
+        }
+        while (g_prev < G) { gs[++g_prev] = nj; }
+    }
+    __syncthreads();
+    // coefficients [kk][p]: one warp per job
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int t = warp; t < ngb; t += nw) {
+        if (s_idx[t] < 0) continue;
+        int g = t / n_mu, b = t % n_mu;
+        int nk = s_hi[t] - s_lo[t] + 1;
+        int64_t base = (int64_t)pb * max_coef + s_off[t];
+        for (int e = lane; e < nk * PB; e += 32) {
+            int kk = e / PB, pl = e % PB;
+            double v = (double)value(g, b, pl, s_lo[t] + kk) * inv_scale;
+            c64[base + e] = v;
+            c32[base + e] = (float)v;
+        }
+    }
+}
+
 
 }  // namespace soap
