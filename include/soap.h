@@ -221,6 +221,64 @@ soap_status soap_active_phases(soap_ctx* ctx, const soap_region* regions, int32_
                                const double* phases, int32_t n_phases, uint32_t effects,
                                int32_t precision, void* out, int out_on_device);
 
+/* One configuration of a batch (soap_active_batch): a star of the context's type (same grid,
+ * mu table, limb darkening, local spectra and wavelength grid) seen with its own projected
+ * velocity and inclination, carrying its own regions at its own phases. */
+typedef struct {
+    double vsini_kms;      /* |vsini_kms| <= the context star's |vsini| (its velocity kernels' range) */
+    double incl_deg;       /* 0 .. 180 */
+    int32_t first_region;  /* regions[first_region .. first_region + n_regions), list order as in */
+    int32_t n_regions;     /*   soap_active_phases; 0 .. SOAP_MAX_REGIONS */
+    int32_t first_phase;   /* phases / output rows [first_phase .. first_phase + n_phases) */
+    int32_t n_phases;
+} soap_batch_item;
+
+/* Spectra of many independent active-star configurations in one call: for every item and
+ * each of its phases, the TOT effect of soap_active_phases (Alg. 5 with Eqs. 3-4) for a star
+ * that differs from the context's only in vsini and inclination.  The paper computes one
+ * configuration per run; batching them, and the schedule below, have no counterpart there.
+ *  items      host [n_items]; every phase index 0 .. n_phases-1 belongs to exactly one item.
+ *  regions    host [n_regions], shared pool that items index into.
+ *  phases     host [n_phases] rotational phases.
+ *  out        float32 [n_phases][n_px]: out[p][m] = F_q,item[m] - Delta F_TOT[p][m], host or
+ *             device per out_on_device.
+ * Arithmetic as SOAP_FP32 (FP64 velocities and shift positions, FP32 contraction and
+ * accumulation); a cell's interpolation weight is held to 32 fractional bits.  Needs
+ * diff_rot_alpha = 0 (a cell's velocity is then vsini x, so one table per item and grid
+ * column replaces per-cell geometry) and at most SOAP_MAX_CLASSES distinct (type, temperature)
+ * pairs over the whole region pool.  Work is cut into (item phase block, pixel tile) units run
+ * by one persistent kernel in decreasing order of estimated cost; the kernel sequence is
+ * captured once per batch shape into a CUDA graph owned by the context and replayed on later
+ * calls with the same shape (soap_set_profiling(ctx, 1) runs it without the graph).  The
+ * variant (phases per block, pixels per thread) is the one soap_batch_set_variant or
+ * soap_batch_autotune chose, else a default.
+ * Errors: SOAP_EINVAL (bad item, phase not covered exactly once, alpha != 0), SOAP_ESTATE (no
+ * active spectrum for a region type), SOAP_ERANGE (class limit, batch too large). */
+soap_status soap_active_batch(soap_ctx* ctx, const soap_batch_item* items, int32_t n_items,
+                              const soap_region* regions, int32_t n_regions, const double* phases,
+                              int32_t n_phases, float* out, int out_on_device);
+
+/* Number of variants of the batched form (valid variants are 0 .. *n - 1). */
+soap_status soap_batch_num_variants(int32_t* n);
+
+/* Phases per block and pixels per thread of a variant; SOAP_ERANGE outside 0 .. n-1. */
+soap_status soap_batch_variant_info(int32_t variant, int32_t* phases_per_block,
+                                    int32_t* px_per_thread);
+
+/* Variant soap_active_batch uses on this context (-1: the default). */
+soap_status soap_batch_set_variant(soap_ctx* ctx, int32_t variant);
+soap_status soap_batch_get_variant(const soap_ctx* ctx, int32_t* variant);
+
+/* Time every variant on the given batch (one untimed run, then `reps` runs timed with CUDA
+ * events on the context's stream), set the fastest on the context and return it.
+ *  out        device float32 [n_phases][n_px] (scratch; holds the last run's result).
+ *  ms         host [n_variants] mean milliseconds per run, or NULL.
+ * Synchronises the context's stream. */
+soap_status soap_batch_autotune(soap_ctx* ctx, const soap_batch_item* items, int32_t n_items,
+                                const soap_region* regions, int32_t n_regions, const double* phases,
+                                int32_t n_phases, float* out, int32_t reps, float* ms,
+                                int32_t* best_variant);
+
 /* Radial velocities from a line-mask CCF and a Gaussian fit (Sect. 4.1).
  *  spectra        [n_spec][n_px] on the context's grid, float64 (spectra_f32 = 0) or float32
  *                 (spectra_f32 = 1); host or device per spectra_on_device.

@@ -548,10 +548,108 @@ soap_status soap_rv_ccf(soap_ctx* c, const void* spectra, int32_t spectra_f32, i
     return SOAP_OK;
 }
 
+soap_status soap_active_batch(soap_ctx* c, const soap_batch_item* items, int32_t n_items,
+                              const soap_region* regions, int32_t n_regions, const double* phases,
+                              int32_t n_phases, float* out, int out_on_device) {
+    clear_error();
+    if (!c || !out) { set_error("ctx or out is NULL"); return SOAP_EINVAL; }
+    if (n_items < 0 || n_regions < 0 || n_phases < 0) { set_error("negative count"); return SOAP_EINVAL; }
+    if ((n_items > 0 && !items) || (n_regions > 0 && !regions) || (n_phases > 0 && !phases)) {
+        set_error("items, regions or phases is NULL"); return SOAP_EINVAL;
+    }
+    const int variant = c->b_variant >= 0 ? c->b_variant : batch_default_variant();
+    const size_t bytes = (size_t)n_phases * (size_t)c->n_px * sizeof(float);
+    float* dst = out;
+    if (!out_on_device && bytes > 0) {
+        SOAP_TRY(ensure(c->out_stage, bytes));
+        dst = c->out_stage.as<float>();
+    }
+    SOAP_TRY(batch_run(c, items, n_items, regions, n_regions, phases, n_phases, variant, dst));
+    if (!out_on_device && bytes > 0) {
+        SOAP_CUDA(cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, c->stream));
+        SOAP_CUDA(cudaStreamSynchronize(c->stream));
+        SOAP_TRY(check_flags(c));
+    }
+    return SOAP_OK;
+}
+
+soap_status soap_batch_num_variants(int32_t* n) {
+    clear_error();
+    if (!n) { set_error("n is NULL"); return SOAP_EINVAL; }
+    *n = batch_num_variants();
+    return SOAP_OK;
+}
+
+soap_status soap_batch_variant_info(int32_t variant, int32_t* phases_per_block, int32_t* px_per_thread) {
+    clear_error();
+    if (!phases_per_block || !px_per_thread) { set_error("NULL argument"); return SOAP_EINVAL; }
+    if (variant < 0 || variant >= batch_num_variants()) { set_error("variant %d outside 0..%d", variant, batch_num_variants() - 1); return SOAP_ERANGE; }
+    int pb = 0, r = 0;
+    batch_variant_info(variant, &pb, &r);
+    *phases_per_block = pb;
+    *px_per_thread = r;
+    return SOAP_OK;
+}
+
+soap_status soap_batch_set_variant(soap_ctx* c, int32_t variant) {
+    clear_error();
+    if (!c) { set_error("ctx is NULL"); return SOAP_EINVAL; }
+    if (variant < -1 || variant >= batch_num_variants()) { set_error("variant %d outside -1..%d", variant, batch_num_variants() - 1); return SOAP_ERANGE; }
+    c->b_variant = variant;
+    return SOAP_OK;
+}
+
+soap_status soap_batch_get_variant(const soap_ctx* c, int32_t* variant) {
+    clear_error();
+    if (!c || !variant) { set_error("NULL argument"); return SOAP_EINVAL; }
+    *variant = c->b_variant;
+    return SOAP_OK;
+}
+
+soap_status soap_batch_autotune(soap_ctx* c, const soap_batch_item* items, int32_t n_items,
+                                const soap_region* regions, int32_t n_regions, const double* phases,
+                                int32_t n_phases, float* out, int32_t reps, float* ms, int32_t* best_variant) {
+    clear_error();
+    if (!c || !out || !best_variant) { set_error("NULL argument"); return SOAP_EINVAL; }
+    if (reps < 1) { set_error("reps must be >= 1"); return SOAP_EINVAL; }
+    const int nv = batch_num_variants();
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    SOAP_CUDA(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); set_error("cudaEventCreate failed"); return SOAP_ECUDA; }
+    soap_status st = SOAP_OK;
+    int best = -1;
+    float best_ms = 0;
+    for (int v = 0; v < nv && st == SOAP_OK; v++) {
+        st = batch_run(c, items, n_items, regions, n_regions, phases, n_phases, v, out);   // capture + warm
+        if (st != SOAP_OK) break;
+        if (cudaEventRecord(e0, c->stream) != cudaSuccess) { st = SOAP_ECUDA; break; }
+        for (int k = 0; k < reps && st == SOAP_OK; k++)
+            st = batch_run(c, items, n_items, regions, n_regions, phases, n_phases, v, out);
+        if (st != SOAP_OK) break;
+        float t = 0;
+        if (cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) {
+            set_error("autotune timing failed"); st = SOAP_ECUDA; break;
+        }
+        t /= (float)reps;
+        if (ms) ms[v] = t;
+        if (best < 0 || t < best_ms) { best = v; best_ms = t; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != SOAP_OK) return st;
+    SOAP_CUDA(cudaStreamSynchronize(c->stream));
+    SOAP_TRY(check_flags(c));
+    c->b_variant = best;
+    *best_variant = best;
+    return SOAP_OK;
+}
+
 void soap_free(soap_ctx* c) {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
     destroy_events(c);
+    batch_release(c);
     free_ctx_memory(c);
     delete c;
 }

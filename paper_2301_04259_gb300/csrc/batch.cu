@@ -1,0 +1,590 @@
+// batch.cu -- batched persistent form: many independent active-region configurations of one
+// star type (shared local spectra, disk grid, limb darkening, mu table), each with its own
+// vsini, inclination, regions and phases, computed by one CUDA-graph launch.
+//
+// Without differential rotation a cell's velocity is vsini x, so a configuration's pixel
+// shifts depend only on the column x of the cell: per configuration, a column table (tap j,
+// weight w as a 32-bit fraction) replaces per-cell geometry, and the quiet velocity kernels
+// come from per-(column, mu bin) intensity sums split by w in exact integer arithmetic.
+//
+// Stages (all on the context's stream, captured once per batch shape into a CUDA graph):
+//  1 k_batch_star     per column: I per cell in fixed point, per-(column, bin) sums
+//  2 k_batch_items    per configuration: column table, quiet kernels, quiet job table
+//  3 k_batch_quiet    quiet spectrum per configuration (Toeplitz contraction)
+//  4 k_batch_regions  region centres / cell boxes per (phase, region)
+//  5 k_batch_hist     InfoMap + per-phase kernels; the last block of each phase block builds
+//                     its job table
+//  6 k_batch_contract persistent: blocks take (phase block, pixel tile) units from an atomic
+//                     ticket, in an order sorted by estimated cost (largest first)
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+#include <vector>
+
+#include "contract_dev.cuh"
+
+namespace soap {
+
+struct BatchItemDev {
+    double vsini, incl_deg;
+    int first_region, n_regions, first_phase, n_phases;
+};
+
+struct PBlockDev {
+    int item, first_phase, np, pad;
+};
+
+// Split an integer intensity into its two taps: k1 = floor(I w), k0 = I - k1 (exact sum).
+__device__ __forceinline__ void split_fx(long long I, unsigned int wfx, long long& k0, long long& k1) {
+    const unsigned long long a = I >= 0 ? (unsigned long long)I : (unsigned long long)(-I);
+    const unsigned long long h = __umul64hi(a, (unsigned long long)wfx << 32);
+    k1 = I >= 0 ? (long long)h : -(long long)h;
+    k0 = I - k1;
+}
+
+// Stage 1: block per column i.  I_fx per cell and IB[i][b] = sum_j I_fx(i, j) [bin = b].
+__global__ void k_batch_star(int N, int n_mu, const double* __restrict__ cell_I,
+                             const int32_t* __restrict__ cell_bin, double scale,
+                             long long* __restrict__ cell_Ifx, long long* __restrict__ IB) {
+    extern __shared__ long long sb[];
+    const int i = blockIdx.x;
+    for (int t = threadIdx.x; t < n_mu; t += blockDim.x) sb[t] = 0;
+    __syncthreads();
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        const int64_t c = (int64_t)j * N + i;
+        const int b = cell_bin[c];
+        long long v = 0;
+        if (b >= 0) {
+            v = __double2ll_rn(cell_I[c] * scale);
+            atomicAdd((unsigned long long*)&sb[b], (unsigned long long)v);
+        }
+        cell_Ifx[c] = v;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < n_mu; t += blockDim.x) IB[(int64_t)i * n_mu + t] = sb[t];
+}
+
+// Stage 2: block per configuration.
+__global__ void k_batch_items(int N, int n_mu, int n_taps, int tap_min, double inv_c, double inv_delta,
+                              double delta, double inv_expm1_delta, const BatchItemDev* __restrict__ items,
+                              const long long* __restrict__ IB, int* __restrict__ colj,
+                              unsigned int* __restrict__ colw, long long* __restrict__ kq,
+                              Job* qjobs, int* qgs, float* qc32, int q_max_coef, double inv_scale,
+                              unsigned int* flags) {
+    extern __shared__ long long hist[];                  // [n_mu][n_taps]
+    const int it = blockIdx.x;
+    const int nb = n_mu * n_taps;
+    const double vsini = items[it].vsini;
+    for (int t = threadIdx.x; t < nb; t += blockDim.x) hist[t] = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const double x = (double)(2 * i + 1 - N) / (double)N;
+        const double beta = vsini * x * inv_c;
+        const double ab = fabs(beta) <= 1e-3 ? atanh_small(beta) : atanh(beta);
+        const double jd = ceil(ab * inv_delta);
+        int jt = (int)jd;
+        const double e = fma(jd, delta, -ab);
+        double w = (delta <= 1e-3 ? expm1_small(e) : expm1(e)) * inv_expm1_delta;
+        w = fmin(fmax(w, 0.0), 1.0);
+        const unsigned int wfx = (unsigned int)fmin(rint(w * 4294967296.0), 4294967295.0);
+        if (jt - 1 < tap_min || jt > tap_min + n_taps - 1) {
+            atomicOr(flags, kFlagTapRange);
+            jt = jt < tap_min + 1 ? tap_min + 1 : tap_min + n_taps - 1;
+        }
+        colj[(int64_t)it * N + i] = jt;
+        colw[(int64_t)it * N + i] = wfx;
+        const int kk = jt - tap_min;
+        for (int b = 0; b < n_mu; b++) {
+            const long long ib = IB[(int64_t)i * n_mu + b];
+            if (ib == 0) continue;
+            long long k0, k1;
+            split_fx(ib, wfx, k0, k1);
+            atomicAdd((unsigned long long*)&hist[b * n_taps + kk], (unsigned long long)k0);
+            atomicAdd((unsigned long long*)&hist[b * n_taps + kk - 1], (unsigned long long)k1);
+        }
+    }
+    __syncthreads();
+    long long* dst = kq + (int64_t)it * nb;
+    for (int t = threadIdx.x; t < nb; t += blockDim.x) dst[t] = hist[t];
+    __threadfence_block();
+    __syncthreads();
+    build_jobs_dev(dst, 0, 1, 1, n_mu, n_taps, tap_min, 1, 0, inv_scale, qjobs + (int64_t)it * n_mu,
+                   qgs + (int64_t)it * 2, nullptr, qc32 + (int64_t)it * q_max_coef, n_mu, q_max_coef,
+                   hist, flags);
+}
+
+// Stage 3: grid (tiles, configurations).
+template <int R, int THREADS>
+__global__ void __launch_bounds__(THREADS)
+k_batch_quiet(int64_t n_px, int64_t row_len, int64_t pad, Rows<float> rows, const Job* __restrict__ qjobs,
+              const int* __restrict__ qgs, int n_mu, const float* __restrict__ qc32, int q_max_coef,
+              float* __restrict__ fq) {
+    const int it = blockIdx.y;
+    ClassTypes ct{};
+    contract_tile<float, 1, R, THREADS>(n_px, row_len, pad, rows, qjobs + (int64_t)it * n_mu,
+                                        qgs + (int64_t)it * 2, 1, qc32 + (int64_t)it * q_max_coef, ct,
+                                        nullptr, nullptr, SOAP_EFFECT_TOT, blockIdx.x, 1,
+                                        fq + (int64_t)it * n_px);
+}
+
+// Stage 4: thread per (phase, region slot).
+__global__ void k_batch_regions(int N, int n_phases, int max_r, const int* __restrict__ phase_item,
+                                const BatchItemDev* __restrict__ items, const RegionDev* __restrict__ regs,
+                                const double* __restrict__ phases, RegionGeo* __restrict__ out) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)n_phases * max_r) return;
+    const int p = (int)(t / max_r), q = (int)(t % max_r);
+    const BatchItemDev it = items[phase_item[p]];
+    if (q >= it.n_regions) return;
+    out[t] = region_geometry(N, regs[it.first_region + q], phases[p], it.incl_deg, 0.0);
+}
+
+// Stage 5: block per phase.  Owned cells add their integer intensity split by their column's
+// weight into the block's kernels (shared memory when they fit, stored whole afterwards; else
+// global atomics into zeroed memory); the last block of a phase block builds its job table.
+__global__ void k_batch_hist(int N, int max_r, const int* __restrict__ phase_item,
+                             const int* __restrict__ phase_block, const BatchItemDev* __restrict__ items,
+                             const PBlockDev* __restrict__ pblocks, const RegionGeo* __restrict__ geo,
+                             const double* __restrict__ cell_mu, const float* __restrict__ cell_mu32,
+                             const int32_t* __restrict__ cell_bin, const long long* __restrict__ cell_Ifx,
+                             const int* __restrict__ colj, const unsigned int* __restrict__ colw,
+                             int tap_min, int n_taps, int n_mu, int n_class, long long* kfix, int use_smem,
+                             int PB, double inv_scale, Job* jobs, int* gstart, float* c32, int max_jobs,
+                             int max_coef, int* counters, int jobs_smem, unsigned int* flags) {
+    __shared__ RegionGeo sg[SOAP_MAX_REGIONS];
+    extern __shared__ long long hist_sm[];
+    const int p = blockIdx.x;
+    const int it = phase_item[p];
+    const int nr = items[it].n_regions;
+    const int nb = n_class * n_mu * n_taps;
+    long long* gdst = kfix + (int64_t)p * nb;
+    long long* hist = use_smem ? hist_sm : gdst;
+    if (threadIdx.x < nr) sg[threadIdx.x] = geo[(int64_t)p * max_r + threadIdx.x];
+    if (use_smem)
+        for (int t = threadIdx.x; t < nb; t += blockDim.x) hist[t] = 0;
+    __syncthreads();
+    const int* cj = colj + (int64_t)it * N;
+    const unsigned int* cw = colw + (int64_t)it * N;
+    for (int r = 0; r < nr; r++) {
+        const int i0 = sg[r].box[0], i1 = sg[r].box[1], j0 = sg[r].box[2], j1 = sg[r].box[3];
+        if (i1 < i0 || j1 < j0) continue;
+        const int wdt = i1 - i0 + 1;
+        const int64_t area = (int64_t)wdt * (j1 - j0 + 1);
+        for (int64_t t = threadIdx.x; t < area; t += blockDim.x) {
+            const int i = i0 + (int)(t % wdt), jj = j0 + (int)(t / wdt);
+            if (in_earlier_box(sg, r, i, jj)) continue;
+            const int64_t c = (int64_t)jj * N + i;
+            const int b = cell_bin[c];
+            if (b < 0) continue;
+            const int owner = cell_owner(sg, nr, N, i, jj, cell_mu32[c], cell_mu, c);
+            if (owner < 0) continue;
+            const int kk = cj[i] - tap_min;
+            if (kk < 1 || kk >= n_taps) { atomicOr(flags, kFlagTapRange); continue; }
+            long long k0, k1;
+            split_fx(cell_Ifx[c], cw[i], k0, k1);
+            long long* h = hist + ((int64_t)sg[owner].cls * n_mu + b) * n_taps;
+            atomicAdd((unsigned long long*)&h[kk], (unsigned long long)k0);
+            atomicAdd((unsigned long long*)&h[kk - 1], (unsigned long long)k1);
+        }
+    }
+    if (use_smem) {
+        __syncthreads();
+        for (int t = threadIdx.x; t < nb; t += blockDim.x) gdst[t] = hist[t];
+    }
+    __shared__ int s_last;
+    __threadfence();
+    __syncthreads();
+    const int pbk = phase_block[p];
+    const PBlockDev pbd = pblocks[pbk];
+    if (threadIdx.x == 0) {
+        const int t = atomicAdd(&counters[pbk], 1);
+        s_last = t == pbd.np - 1;
+    }
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        build_jobs_dev(kfix + (int64_t)pbd.first_phase * nb, 0, pbd.np, n_class, n_mu, n_taps, tap_min, PB, 1,
+                       inv_scale, jobs + (int64_t)pbk * max_jobs, gstart + (int64_t)pbk * (1 + n_class + 1),
+                       nullptr, c32 + (int64_t)pbk * max_coef, max_jobs, max_coef, jobs_smem ? hist_sm : nullptr,
+                       flags);
+    }
+}
+
+// Stage 6: persistent.  Units (phase block, pixel tile) in `order`; blocks take the next unit
+// with an atomic ticket until none is left (no block waits on another).
+template <int PB, int R, int THREADS>
+__global__ void __launch_bounds__(THREADS)
+k_batch_contract(int64_t n_px, int64_t row_len, int64_t pad, Rows<float> rows, const Job* __restrict__ jobs,
+                 const int* __restrict__ gstart, int G, int max_jobs, const float* __restrict__ c32,
+                 int max_coef, ClassTypes ctype, const float* __restrict__ contrast,
+                 const float* __restrict__ fq, const PBlockDev* __restrict__ pblocks,
+                 const int* __restrict__ order, int n_units, int n_tiles, unsigned int* ticket,
+                 float* __restrict__ out) {
+    __shared__ int s_u;
+    while (true) {
+        if (threadIdx.x == 0) s_u = (int)atomicAdd(ticket, 1u);
+        __syncthreads();
+        const int u = s_u;
+        __syncthreads();
+        if (u >= n_units) break;
+        const int unit = order[u];
+        const int pbk = unit / n_tiles, tile = unit % n_tiles;
+        const PBlockDev pb = pblocks[pbk];
+        contract_tile<float, PB, R, THREADS>(n_px, row_len, pad, rows, jobs + (int64_t)pbk * max_jobs,
+                                             gstart + (int64_t)pbk * (G + 1), G, c32 + (int64_t)pbk * max_coef,
+                                             ctype, contrast, fq + (int64_t)pb.item * n_px, SOAP_EFFECT_TOT,
+                                             tile, pb.np, out + (int64_t)pb.first_phase * n_px);
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------------------
+constexpr int kBatchThreads = 128;
+
+// Variants the autotuner chooses from: (phases per block, pixels per thread).
+struct BatchVariant {
+    int PB, R;
+};
+static const BatchVariant kVariants[] = {{4, 2}, {4, 4}, {8, 2}, {8, 4}, {16, 2}, {16, 4}};
+constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
+constexpr int kDefaultVariant = 1;
+
+// Sizes of one batch, fixed by the host preparation and baked into the captured graph.
+struct BatchShape {
+    int n_items, n_phases, max_r, n_pblocks, n_units, n_tiles, variant, n_class;
+    int G, max_jobs, max_coef;
+    int64_t nbk;               // per-phase kernel size n_class * n_mu * n_taps
+    int use_smem, jobs_smem;
+    size_t hist_smem;
+};
+
+template <int PB, int R>
+static soap_status launch_batch_contract(soap_ctx* c, const BatchShape& b, const ClassTypes& ct,
+                                         const float* a0, const float* a1, float* out) {
+    Rows<float> rows;
+    rows.q = c->q32; rows.a[0] = a0; rows.a[1] = a1;
+    int dev = 0, sms = 152, per_sm = 4;
+    SOAP_CUDA(cudaGetDevice(&dev));
+    SOAP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    SOAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_contract<PB, R, kBatchThreads>,
+                                                            kBatchThreads, 0));
+    const int grid = std::max(1, std::min(b.n_units, sms * std::max(1, per_sm)));
+    SOAP_TIMED(c, SOAP_TIMER_CONTRACT,
+               k_batch_contract<PB, R, kBatchThreads><<<grid, kBatchThreads, 0, c->stream>>>(
+                   c->n_px, c->row_len, c->pad, rows, c->b_jobs.as<Job>(), c->b_gstart.as<int>(), b.G,
+                   b.max_jobs, c->b_coefs.as<float>(), b.max_coef, ct, c->b_con.as<float>(), c->b_fq.as<float>(),
+                   c->b_pblocks.as<PBlockDev>(), c->b_order.as<int>(), b.n_units, b.n_tiles,
+                   c->b_ticket.as<unsigned int>(), out);
+               SOAP_LAUNCHED(c));
+    return SOAP_OK;
+}
+
+// Enqueue stages 1-6 on the context's stream for a batch whose inputs are already on the device.
+static soap_status enqueue_batch(soap_ctx* c, const BatchShape& b, const ClassTypes& ct,
+                                 const ClassConsts& cc, float* out) {
+    const int N = c->N;
+    const int q_max_coef = c->n_mu * c->n_taps;
+    const double scale = std::ldexp(1.0, c->fx_bits);
+    const double inv_scale = std::ldexp(1.0, -c->fx_bits);
+    // 1 star
+    k_batch_star<<<N, 128, c->n_mu * sizeof(long long), c->stream>>>(
+        N, c->n_mu, c->cell_I, c->cell_bin, scale, c->b_cellIfx.as<long long>(), c->b_IB.as<long long>());
+    SOAP_LAUNCHED(c);
+    // 2 configurations: column tables, quiet kernels and job tables
+    const size_t smem_q = (size_t)c->n_mu * c->n_taps * sizeof(long long);
+    SOAP_CUDA(cudaFuncSetAttribute(k_batch_items, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_q));
+    k_batch_items<<<b.n_items, 128, smem_q, c->stream>>>(
+        N, c->n_mu, c->n_taps, c->tap_min, 1.0 / kCKms, 1.0 / c->delta, c->delta, 1.0 / std::expm1(c->delta),
+        c->b_items.as<BatchItemDev>(), c->b_IB.as<long long>(), c->b_colj.as<int>(), c->b_colw.as<unsigned int>(),
+        c->b_kq.as<long long>(), c->b_qjobs.as<Job>(), c->b_qgs.as<int>(), c->b_qc32.as<float>(), q_max_coef,
+        inv_scale, c->flags);
+    SOAP_LAUNCHED(c);
+    // 3 quiet spectra
+    {
+        Rows<float> rows;
+        rows.q = c->q32; rows.a[0] = nullptr; rows.a[1] = nullptr;
+        const int64_t TILE = 128 * 4;
+        dim3 grid((unsigned)((c->n_px + TILE - 1) / TILE), (unsigned)b.n_items);
+        SOAP_TIMED(c, SOAP_TIMER_CONTRACT_QUIET,
+                   k_batch_quiet<4, 128><<<grid, 128, 0, c->stream>>>(
+                       c->n_px, c->row_len, c->pad, rows, c->b_qjobs.as<Job>(), c->b_qgs.as<int>(), c->n_mu,
+                       c->b_qc32.as<float>(), q_max_coef, c->b_fq.as<float>());
+                   SOAP_LAUNCHED(c));
+    }
+    // contrast per class
+    if (b.n_class > 0) {
+        const double hck = kPlanckH * kLightSI / kBoltzmann * 1e10;
+        const int64_t g = std::min<int64_t>((c->n_px + 255) / 256, 152 * 8);
+        SOAP_TIMED(c, SOAP_TIMER_CONTRAST,
+                   k_contrast32<<<(unsigned)g, 256, 0, c->stream>>>(c->n_px, (float)(hck / (c->lam_s * c->t_quiet)),
+                                                                   (float)c->delta, b.n_class, cc, c->b_con.as<float>());
+                   SOAP_LAUNCHED(c));
+    }
+    // 4 regions
+    if (b.max_r > 0) {
+        const int64_t nt = (int64_t)b.n_phases * b.max_r;
+        k_batch_regions<<<(unsigned)((nt + 127) / 128), 128, 0, c->stream>>>(
+            N, b.n_phases, b.max_r, c->b_phase_item.as<int>(), c->b_items.as<BatchItemDev>(),
+            c->b_regions.as<RegionDev>(), c->b_phases.as<double>(), c->b_geo.as<RegionGeo>());
+        SOAP_LAUNCHED(c);
+    }
+    // 5 per-phase kernels + job tables
+    if (!b.use_smem)
+        SOAP_CUDA(cudaMemsetAsync(c->b_kfix.p, 0, (size_t)b.n_phases * b.nbk * sizeof(long long), c->stream));
+    SOAP_CUDA(cudaMemsetAsync(c->b_counters.p, 0, (size_t)b.n_pblocks * sizeof(int), c->stream));
+    SOAP_CUDA(cudaFuncSetAttribute(k_batch_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b.hist_smem));
+    SOAP_TIMED(c, SOAP_TIMER_PHASE_HIST,
+               k_batch_hist<<<(unsigned)b.n_phases, 128, b.hist_smem, c->stream>>>(
+                   N, std::max(b.max_r, 1), c->b_phase_item.as<int>(), c->b_phase_block.as<int>(),
+                   c->b_items.as<BatchItemDev>(), c->b_pblocks.as<PBlockDev>(), c->b_geo.as<RegionGeo>(),
+                   c->cell_mu, c->cell_mu32, c->cell_bin, c->b_cellIfx.as<long long>(), c->b_colj.as<int>(),
+                   c->b_colw.as<unsigned int>(), c->tap_min, c->n_taps, c->n_mu, b.n_class,
+                   c->b_kfix.as<long long>(), b.use_smem, kVariants[b.variant].PB, inv_scale, c->b_jobs.as<Job>(),
+                   c->b_gstart.as<int>(), c->b_coefs.as<float>(), b.max_jobs, b.max_coef, c->b_counters.as<int>(),
+                   b.jobs_smem, c->flags);
+               SOAP_LAUNCHED(c));
+    // 6 persistent contraction
+    SOAP_CUDA(cudaMemsetAsync(c->b_ticket.p, 0, sizeof(unsigned int), c->stream));
+    const float* a0 = c->active_set[0] ? c->a32[0] : c->a32[1];
+    const float* a1 = c->active_set[1] ? c->a32[1] : c->a32[0];
+    switch (b.variant) {
+        case 0: return launch_batch_contract<4, 2>(c, b, ct, a0, a1, out);
+        case 1: return launch_batch_contract<4, 4>(c, b, ct, a0, a1, out);
+        case 2: return launch_batch_contract<8, 2>(c, b, ct, a0, a1, out);
+        case 3: return launch_batch_contract<8, 4>(c, b, ct, a0, a1, out);
+        case 4: return launch_batch_contract<16, 2>(c, b, ct, a0, a1, out);
+        default: return launch_batch_contract<16, 4>(c, b, ct, a0, a1, out);
+    }
+}
+
+int batch_num_variants() { return kNumVariants; }
+
+void batch_variant_info(int v, int* pb, int* r) {
+    *pb = kVariants[v].PB;
+    *r = kVariants[v].R;
+}
+
+int batch_default_variant() { return kDefaultVariant; }
+
+void batch_release(soap_ctx* c) {
+    if (c->b_graph_exec) cudaGraphExecDestroy(c->b_graph_exec);
+    c->b_graph_exec = nullptr;
+    c->b_graph_key.clear();
+    DevBuf* bufs[] = {&c->b_items, &c->b_regions, &c->b_phases, &c->b_phase_item, &c->b_phase_block,
+                      &c->b_pblocks, &c->b_order, &c->b_cellIfx, &c->b_IB, &c->b_colj, &c->b_colw, &c->b_kq,
+                      &c->b_qjobs, &c->b_qgs, &c->b_qc32, &c->b_fq, &c->b_con, &c->b_geo, &c->b_kfix,
+                      &c->b_counters, &c->b_jobs, &c->b_gstart, &c->b_coefs, &c->b_ticket};
+    for (DevBuf* b : bufs) release(*b);
+}
+
+// Host preparation (validation, classes, phase blocks, cost-ordered units, uploads), then the
+// graph: captured on the first call with a given shape, replayed on later ones.
+soap_status batch_run(soap_ctx* c, const soap_batch_item* items, int n_items, const soap_region* regions,
+                      int n_regions, const double* phases, int n_phases, int variant, float* out) {
+    if (c->alpha != 0.0) {
+        set_error("the batched form needs a star without differential rotation (diff_rot_alpha = 0)");
+        return SOAP_EINVAL;
+    }
+    if (variant < 0 || variant >= kNumVariants) { set_error("unknown batch variant %d", variant); return SOAP_EINVAL; }
+    const BatchVariant V = kVariants[variant];
+    // classes over all regions, in first-appearance order
+    double ctemp[SOAP_MAX_CLASSES];
+    int ctype[SOAP_MAX_CLASSES];
+    int n_class = 0;
+    std::vector<RegionDev> rd(std::max(1, n_regions));
+    for (int r = 0; r < n_regions; r++) {
+        const soap_region& g = regions[r];
+        if (g.type != SOAP_SPOT && g.type != SOAP_FACULA) { set_error("regions[%d].type invalid", r); return SOAP_EINVAL; }
+        if (g.reserved != 0) { set_error("regions[%d].reserved must be 0", r); return SOAP_EINVAL; }
+        if (!std::isfinite(g.lat_deg) || !std::isfinite(g.lon_deg) || !std::isfinite(g.radius_rstar) ||
+            !std::isfinite(g.temp_K)) {
+            set_error("regions[%d] has a non-finite field", r); return SOAP_EINVAL;
+        }
+        if (g.radius_rstar < 0 || g.radius_rstar > 1) { set_error("regions[%d].radius_rstar outside [0,1]", r); return SOAP_EINVAL; }
+        if (!(g.temp_K > 0)) { set_error("regions[%d].temp_K must be > 0", r); return SOAP_EINVAL; }
+        int cl = -1;
+        for (int k = 0; k < n_class; k++)
+            if (ctype[k] == g.type && ctemp[k] == g.temp_K) cl = k;
+        if (cl < 0) {
+            if (n_class == SOAP_MAX_CLASSES) { set_error("more than %d distinct (type, temperature) pairs", SOAP_MAX_CLASSES); return SOAP_ERANGE; }
+            cl = n_class++;
+            ctype[cl] = g.type;
+            ctemp[cl] = g.temp_K;
+        }
+        rd[r] = RegionDev{g.lat_deg, g.lon_deg, g.radius_rstar, g.temp_K, g.type, cl};
+    }
+    for (int k = 0; k < n_class; k++) {
+        const bool ok = ctype[k] == SOAP_SPOT ? c->active_set[0] : (c->active_set[1] || c->active_set[0]);
+        if (!ok) { set_error("no active spectrum set for region type %d", ctype[k]); return SOAP_ESTATE; }
+    }
+    // configurations, phase ownership, phase blocks and their estimated cost
+    std::vector<BatchItemDev> it(std::max(1, n_items));
+    std::vector<int> phase_item(std::max(1, n_phases), -1), phase_block(std::max(1, n_phases), -1);
+    std::vector<PBlockDev> pbl;
+    std::vector<double> pcost;
+    int max_r = 0;
+    const double vmax = std::fabs(c->vsini);
+    for (int k = 0; k < n_items; k++) {
+        const soap_batch_item& s = items[k];
+        if (!std::isfinite(s.vsini_kms) || std::fabs(s.vsini_kms) > vmax || !std::isfinite(s.incl_deg) ||
+            s.incl_deg < 0 || s.incl_deg > 180) {
+            set_error("items[%d]: need |vsini| <= the star's vsini (%g km/s) and 0 <= incl <= 180", k, vmax);
+            return SOAP_EINVAL;
+        }
+        if (s.n_regions < 0 || s.n_regions > SOAP_MAX_REGIONS || s.first_region < 0 ||
+            (int64_t)s.first_region + s.n_regions > n_regions || s.n_phases < 0 || s.first_phase < 0 ||
+            (int64_t)s.first_phase + s.n_phases > n_phases) {
+            set_error("items[%d]: region or phase range out of bounds", k); return SOAP_EINVAL;
+        }
+        double area = 0;
+        for (int r = 0; r < s.n_regions; r++) {
+            const double rr = regions[s.first_region + r].radius_rstar;
+            area += rr * rr;
+        }
+        for (int p = 0; p < s.n_phases; p++) {
+            const int q = s.first_phase + p;
+            if (phase_item[q] != -1) { set_error("phase %d belongs to two items", q); return SOAP_EINVAL; }
+            if (!std::isfinite(phases[q])) { set_error("phases[%d] not finite", q); return SOAP_EINVAL; }
+            phase_item[q] = k;
+        }
+        for (int p0 = 0; p0 < s.n_phases; p0 += V.PB) {
+            const int np = std::min(V.PB, s.n_phases - p0);
+            for (int p = 0; p < np; p++) phase_block[s.first_phase + p0 + p] = (int)pbl.size();
+            pbl.push_back(PBlockDev{k, s.first_phase + p0, np, 0});
+            // work of one unit ~ phases x (quiet-row taps + active taps); the active part grows
+            // with the spotted area and the velocity spread across it
+            pcost.push_back(np * (1.0 + 40.0 * area * (1.0 + std::fabs(s.vsini_kms))));
+        }
+        max_r = std::max(max_r, s.n_regions);
+        it[k] = BatchItemDev{s.vsini_kms, s.incl_deg, s.first_region, s.n_regions, s.first_phase, s.n_phases};
+    }
+    for (int p = 0; p < n_phases; p++)
+        if (phase_item[p] < 0) { set_error("phase %d belongs to no item", p); return SOAP_EINVAL; }
+    if (n_items == 0 || n_phases == 0) return SOAP_OK;
+    BatchShape b{};
+    b.n_items = n_items;
+    b.n_phases = n_phases;
+    b.max_r = max_r;
+    b.n_pblocks = (int)pbl.size();
+    b.n_tiles = (int)((c->n_px + kBatchThreads * V.R - 1) / (kBatchThreads * V.R));
+    const int64_t n_units64 = (int64_t)b.n_pblocks * b.n_tiles;
+    if (n_units64 > ((int64_t)1 << 31) - 1) { set_error("batch has too many (phase block, tile) units"); return SOAP_ERANGE; }
+    b.n_units = (int)n_units64;
+    b.variant = variant;
+    b.n_class = n_class;
+    b.G = 1 + n_class;
+    b.max_jobs = b.G * c->n_mu;
+    b.max_coef = b.max_jobs * c->n_taps * V.PB;
+    b.nbk = (int64_t)n_class * c->n_mu * c->n_taps;
+    const size_t hist_bytes = (size_t)b.nbk * sizeof(long long);
+    const size_t kslice_bytes = (size_t)V.PB * b.nbk * sizeof(long long);
+    b.use_smem = hist_bytes <= 96 * 1024;
+    b.jobs_smem = kslice_bytes <= 160 * 1024;
+    b.hist_smem = std::max(b.use_smem ? hist_bytes : (size_t)0, b.jobs_smem ? kslice_bytes : (size_t)0);
+    // units (phase block, tile), largest estimated cost first; a block's tiles stay together
+    std::vector<int> border(b.n_pblocks);
+    std::iota(border.begin(), border.end(), 0);
+    std::stable_sort(border.begin(), border.end(), [&](int x, int y) { return pcost[x] > pcost[y]; });
+    std::vector<int> order((size_t)b.n_units);
+    for (int q = 0; q < b.n_pblocks; q++)
+        for (int t = 0; t < b.n_tiles; t++) order[(size_t)q * b.n_tiles + t] = border[q] * b.n_tiles + t;
+    // device buffers (grow-only)
+    const int N = c->N;
+    const int ncl = std::max(1, n_class);
+    SOAP_TRY(ensure(c->b_items, (size_t)n_items * sizeof(BatchItemDev)));
+    SOAP_TRY(ensure(c->b_regions, (size_t)std::max(1, n_regions) * sizeof(RegionDev)));
+    SOAP_TRY(ensure(c->b_phases, (size_t)n_phases * sizeof(double)));
+    SOAP_TRY(ensure(c->b_phase_item, (size_t)n_phases * sizeof(int)));
+    SOAP_TRY(ensure(c->b_phase_block, (size_t)n_phases * sizeof(int)));
+    SOAP_TRY(ensure(c->b_pblocks, (size_t)b.n_pblocks * sizeof(PBlockDev)));
+    SOAP_TRY(ensure(c->b_order, (size_t)b.n_units * sizeof(int)));
+    SOAP_TRY(ensure(c->b_cellIfx, (size_t)N * N * sizeof(long long)));
+    SOAP_TRY(ensure(c->b_IB, (size_t)N * c->n_mu * sizeof(long long)));
+    SOAP_TRY(ensure(c->b_colj, (size_t)n_items * N * sizeof(int)));
+    SOAP_TRY(ensure(c->b_colw, (size_t)n_items * N * sizeof(unsigned int)));
+    SOAP_TRY(ensure(c->b_kq, (size_t)n_items * c->n_mu * c->n_taps * sizeof(long long)));
+    SOAP_TRY(ensure(c->b_qjobs, (size_t)n_items * c->n_mu * sizeof(Job)));
+    SOAP_TRY(ensure(c->b_qgs, (size_t)n_items * 2 * sizeof(int)));
+    SOAP_TRY(ensure(c->b_qc32, (size_t)n_items * c->n_mu * c->n_taps * sizeof(float)));
+    SOAP_TRY(ensure(c->b_fq, (size_t)n_items * c->n_px * sizeof(float)));
+    SOAP_TRY(ensure(c->b_con, (size_t)ncl * c->n_px * sizeof(float)));
+    SOAP_TRY(ensure(c->b_geo, (size_t)n_phases * std::max(1, max_r) * sizeof(RegionGeo)));
+    SOAP_TRY(ensure(c->b_kfix, (size_t)n_phases * std::max<int64_t>(1, b.nbk) * sizeof(long long)));
+    SOAP_TRY(ensure(c->b_counters, (size_t)b.n_pblocks * sizeof(int)));
+    SOAP_TRY(ensure(c->b_jobs, (size_t)b.n_pblocks * b.max_jobs * sizeof(Job)));
+    SOAP_TRY(ensure(c->b_gstart, (size_t)b.n_pblocks * (b.G + 1) * sizeof(int)));
+    SOAP_TRY(ensure(c->b_coefs, (size_t)b.n_pblocks * b.max_coef * sizeof(float)));
+    SOAP_TRY(ensure(c->b_ticket, sizeof(unsigned int)));
+    // inputs (pageable copies: the call returns after the driver has staged them)
+    SOAP_CUDA(cudaMemcpyAsync(c->b_items.p, it.data(), (size_t)n_items * sizeof(BatchItemDev), cudaMemcpyHostToDevice, c->stream));
+    if (n_regions > 0)
+        SOAP_CUDA(cudaMemcpyAsync(c->b_regions.p, rd.data(), (size_t)n_regions * sizeof(RegionDev), cudaMemcpyHostToDevice, c->stream));
+    SOAP_CUDA(cudaMemcpyAsync(c->b_phases.p, phases, (size_t)n_phases * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    SOAP_CUDA(cudaMemcpyAsync(c->b_phase_item.p, phase_item.data(), (size_t)n_phases * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    SOAP_CUDA(cudaMemcpyAsync(c->b_phase_block.p, phase_block.data(), (size_t)n_phases * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    SOAP_CUDA(cudaMemcpyAsync(c->b_pblocks.p, pbl.data(), (size_t)b.n_pblocks * sizeof(PBlockDev), cudaMemcpyHostToDevice, c->stream));
+    SOAP_CUDA(cudaMemcpyAsync(c->b_order.p, order.data(), (size_t)b.n_units * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    ClassTypes ct{};
+    ClassConsts cc{};
+    const double hck = kPlanckH * kLightSI / kBoltzmann * 1e10;
+    for (int k = 0; k < n_class; k++) {
+        ct.t[k] = ctype[k];
+        cc.a[k] = (float)(hck / (c->lam_s * ctemp[k]));
+    }
+    if (c->profiling)      // per-kernel timers need events between the launches: no graph
+        return enqueue_batch(c, b, ct, cc, out);
+    // everything the graph bakes in: sizes, star parameters, class constants and pointers
+    std::vector<uint64_t> key;
+    auto put = [&](uint64_t v) { key.push_back(v); };
+    auto putd = [&](double v) { uint64_t u; memcpy(&u, &v, 8); key.push_back(u); };
+    auto putp = [&](const void* p) { key.push_back((uint64_t)(uintptr_t)p); };
+    put(b.n_items); put(b.n_phases); put(b.max_r); put(b.n_pblocks); put(b.n_units); put(b.n_tiles);
+    put(b.variant); put(b.n_class); put(b.use_smem); put(b.jobs_smem); put(b.hist_smem);
+    put(N); put(c->n_mu); put(c->n_taps); put((uint64_t)c->tap_min); put(c->fx_bits);
+    put(c->n_px); put(c->row_len); put(c->pad);
+    putd(c->delta); putd(c->lam_s); putd(c->t_quiet);
+    for (int k = 0; k < n_class; k++) { put(ct.t[k]); putd(ctemp[k]); }
+    putp(out); putp(c->stream); putp(c->q32); putp(c->a32[0]); putp(c->a32[1]); putp(c->cell_I);
+    putp(c->cell_bin); putp(c->cell_mu); putp(c->cell_mu32); putp(c->flags);
+    const DevBuf* bufs[] = {&c->b_items, &c->b_regions, &c->b_phases, &c->b_phase_item, &c->b_phase_block,
+                            &c->b_pblocks, &c->b_order, &c->b_cellIfx, &c->b_IB, &c->b_colj, &c->b_colw, &c->b_kq,
+                            &c->b_qjobs, &c->b_qgs, &c->b_qc32, &c->b_fq, &c->b_con, &c->b_geo, &c->b_kfix,
+                            &c->b_counters, &c->b_jobs, &c->b_gstart, &c->b_coefs, &c->b_ticket};
+    for (const DevBuf* q : bufs) putp(q->p);
+    if (!c->b_graph_exec || c->b_graph_key != key) {
+        if (c->b_graph_exec) { cudaGraphExecDestroy(c->b_graph_exec); c->b_graph_exec = nullptr; }
+        c->b_graph_key.clear();
+        cudaStream_t cap = nullptr;
+        SOAP_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        const cudaStream_t saved = c->stream;
+        const uint64_t launches0 = c->launches;
+        c->stream = cap;
+        cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        soap_status st = SOAP_OK;
+        cudaGraph_t graph = nullptr;
+        if (e == cudaSuccess) {
+            st = enqueue_batch(c, b, ct, cc, out);
+            const cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+            if (e2 != cudaSuccess && st == SOAP_OK) e = e2;
+        }
+        c->stream = saved;
+        c->b_graph_kernels = c->launches - launches0;
+        c->launches = launches0;
+        if (st == SOAP_OK && e == cudaSuccess) e = cudaGraphInstantiate(&c->b_graph_exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        cudaStreamDestroy(cap);
+        if (st != SOAP_OK) { c->b_graph_exec = nullptr; return st; }
+        if (e != cudaSuccess) {
+            c->b_graph_exec = nullptr;
+            set_error("batch graph capture failed: %s", cudaGetErrorString(e));
+            return SOAP_ECUDA;
+        }
+        c->b_graph_key = key;
+    }
+    SOAP_CUDA(cudaGraphLaunch(c->b_graph_exec, c->stream));
+    c->launches += c->b_graph_kernels;
+    return SOAP_OK;
+}
+
+}  // namespace soap

@@ -17,7 +17,7 @@
 #include <cmath>
 #include <vector>
 
-#include "soap_internal.cuh"
+#include "contract_dev.cuh"
 
 namespace soap {
 
@@ -44,81 +44,16 @@ __global__ void k_contrast(int64_t n_px, double lam_s, double delta, double t_qu
     }
 }
 
-// FP32 version for the mixed path (relative error ~1e-7, far inside its 2e-6 tolerance).
-struct ClassConsts {
-    float a[SOAP_MAX_CLASSES];       // h c / (lambda_s k T_class)
-};
-
-__global__ void k_contrast32(int64_t n_px, float aq, float fd, int n_class, ClassConsts ac, float* c32) {
-    for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < n_px;
-         m += (int64_t)gridDim.x * blockDim.x) {
-        const float inv = expf(-(float)m * fd);            // lambda_s / lambda_m
-        const float xq = expm1f(aq * inv);
-        for (int cl = 0; cl < n_class; cl++) c32[cl * n_px + m] = xq / expm1f(ac.a[cl] * inv);
-    }
-}
-
-
 // ---------------------------------------------------------------------------------------
 // InfoMap + per-phase velocity kernels (Alg. 5)
 // ---------------------------------------------------------------------------------------
-__device__ __forceinline__ unsigned long long fx(double v, double scale) {
-    return (unsigned long long)__double2ll_rn(v * scale);
-}
-
 // Region centre, cap and cell box per (phase, region), computed once (FP64 trigonometry).
-struct RegionGeo {
-    double P[3];       // unit vector of the cap centre, observer frame
-    double cosr;       // cos of the cap's angular radius, sqrt(1 - r^2)
-    float Pf[3];
-    float cosrf;
-    int box[4];        // i0, i1, j0, j1 (empty if i1 < i0)
-    int cls;
-    int pad;
-};
-
-// Region centre at phase p (observer frame, rotation axis (0, sin i, cos i)): star-frame
-// (cos lat sin L, sin lat, cos lat cos L) with L = lon + 360 p (1 + alpha sin^2 lat), tilted by
-// the inclination; written with explicitly rounded FP64 steps.  The cell box is conservative:
-// the cap reaches axis angles within +-asin(r) of the centre's.
 __global__ void k_region_geo(int N, int n_regions, int n_phases, const RegionDev* regs,
                              const double* phases, double incl_deg, double alpha, RegionGeo* out) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n_phases * n_regions) return;
     const int p = t / n_regions, q = t % n_regions;
-    const double d2r = kPi / 180.0;
-    const RegionDev g = regs[q];
-    const double phase = phases[p];
-    double lat = __dmul_rn(g.lat_deg, d2r);
-    double sl = sin(lat), cl = cos(lat);
-    double lonp = __dadd_rn(g.lon_deg, __dmul_rn(__dmul_rn(360.0, phase),
-                                                 __dadd_rn(1.0, __dmul_rn(__dmul_rn(alpha, sl), sl))));
-    double lon = __dmul_rn(lonp, d2r);
-    double incl = __dmul_rn(incl_deg, d2r);
-    double si = sin(incl), ci = cos(incl);
-    double px = __dmul_rn(cl, sin(lon)), py = sl, pz = __dmul_rn(cl, cos(lon));
-    RegionGeo o;
-    o.P[0] = px;
-    o.P[1] = __dsub_rn(__dmul_rn(py, si), __dmul_rn(pz, ci));
-    o.P[2] = __dadd_rn(__dmul_rn(py, ci), __dmul_rn(pz, si));
-    const double r = g.radius;
-    o.cosr = __dsqrt_rn(__dsub_rn(1.0, __dmul_rn(r, r)));
-    for (int k = 0; k < 3; k++) o.Pf[k] = (float)o.P[k];
-    o.cosrf = (float)o.cosr;
-    o.cls = g.cls;
-    o.pad = 0;
-    const double a = asin(fmin(r, 1.0));
-    const double bx = acos(fmax(-1.0, fmin(1.0, o.P[0])));
-    const double by = acos(fmax(-1.0, fmin(1.0, o.P[1])));
-    const double bz = acos(fmax(-1.0, fmin(1.0, o.P[2])));
-    const double xhi = cos(fmax(0.0, bx - a)), xlo = cos(fmin(kPi, bx + a));
-    const double yhi = cos(fmax(0.0, by - a)), ylo = cos(fmin(kPi, by + a));
-    int i0 = (int)floor((xlo * N + N - 1) * 0.5) - 1, i1 = (int)ceil((xhi * N + N - 1) * 0.5) + 1;
-    int j0 = (int)floor((ylo * N + N - 1) * 0.5) - 1, j1 = (int)ceil((yhi * N + N - 1) * 0.5) + 1;
-    i0 = max(i0, 0); j0 = max(j0, 0); i1 = min(i1, N - 1); j1 = min(j1, N - 1);
-    if (bz - a > 0.5 * kPi + 1e-6) i1 = i0 - 1;          // cap entirely on the far side
-    o.box[0] = i0; o.box[1] = i1; o.box[2] = j0; o.box[3] = j1;
-    out[t] = o;
+    out[t] = region_geometry(N, regs[q], phases[p], incl_deg, alpha);
 }
 
 // Blocks (phase p, split).  A visible cell (x, y, mu) belongs to a region iff
@@ -146,7 +81,6 @@ __global__ void k_phase_hist(int N, int n_regions, const RegionGeo* __restrict__
     if (use_smem)
         for (int t = threadIdx.x; t < nb; t += blockDim.x) hist[t] = 0;
     __syncthreads();
-    const float invN = 1.0f / (float)N;
     for (int r = 0; r < n_regions; r++) {
         const int i0 = sg[r].box[0], i1 = sg[r].box[1], j0 = sg[r].box[2], j1 = sg[r].box[3];
         if (i1 < i0 || j1 < j0) continue;
@@ -155,30 +89,11 @@ __global__ void k_phase_hist(int N, int n_regions, const RegionGeo* __restrict__
         for (int64_t t = (int64_t)split * blockDim.x + threadIdx.x; t < area;
              t += (int64_t)n_split * blockDim.x) {
             const int i = i0 + (int)(t % wdt), jj = j0 + (int)(t / wdt);
-            bool dup = false;                 // visit each cell once: first box that holds it
-            for (int q = 0; q < r; q++)
-                if (i >= sg[q].box[0] && i <= sg[q].box[1] && jj >= sg[q].box[2] && jj <= sg[q].box[3]) dup = true;
-            if (dup) continue;
+            if (in_earlier_box(sg, r, i, jj)) continue;
             const int64_t c = (int64_t)jj * N + i;
             const int b = cell_bin[c];
             if (b < 0) continue;
-            const float xf = (float)(2 * i + 1 - N) * invN, yf = (float)(2 * jj + 1 - N) * invN;
-            const float muf = cell_mu32[c];
-            int owner = -1;
-            for (int q = 0; q < n_regions; q++) {
-                const float df = fmaf(xf, sg[q].Pf[0], fmaf(yf, sg[q].Pf[1], muf * sg[q].Pf[2]));
-                bool in;
-                if (df > sg[q].cosrf + 2e-6f) in = true;
-                else if (df < sg[q].cosrf - 2e-6f) in = false;
-                else {
-                    const double x = (double)(2 * i + 1 - N) / (double)N;
-                    const double y = (double)(2 * jj + 1 - N) / (double)N;
-                    const double dot = __dadd_rn(__dadd_rn(__dmul_rn(x, sg[q].P[0]), __dmul_rn(y, sg[q].P[1])),
-                                                 __dmul_rn(cell_mu[c], sg[q].P[2]));
-                    in = dot >= sg[q].cosr;
-                }
-                if (in) owner = q;
-            }
+            const int owner = cell_owner(sg, n_regions, N, i, jj, cell_mu32[c], cell_mu, c);
             if (owner < 0) continue;
             const int kk = cell_j[c] - tap_min;
             if (kk < 1 || kk >= n_taps) { atomicOr(flags, kFlagTapRange); continue; }
@@ -214,44 +129,7 @@ __global__ void k_phase_hist(int N, int n_regions, const RegionGeo* __restrict__
 // ---------------------------------------------------------------------------------------
 // contraction
 // ---------------------------------------------------------------------------------------
-template <typename T>
-struct Rows {
-    const T* q;         // quiet rows [n_mu][row_len]
-    const T* a[2];      // active rows spot / facula
-};
-
-struct ClassTypes {
-    int t[SOAP_MAX_CLASSES];
-};
-
-struct EffectList {
-    int e[3];
-};
-
-// PB coefficients of one tap (16-byte vector loads when PB allows; coefficient slabs are
-// 256-byte aligned and every job's block is a multiple of PB elements).
-template <typename T, int PB>
-__device__ __forceinline__ void load_coefs(const T* __restrict__ src, T (&cv)[PB]) {
-    if constexpr (sizeof(T) == 4 && PB % 4 == 0) {
-#pragma unroll
-        for (int q = 0; q < PB / 4; q++) {
-            const float4 t = __ldg(reinterpret_cast<const float4*>(src) + q);
-            cv[4 * q] = t.x; cv[4 * q + 1] = t.y; cv[4 * q + 2] = t.z; cv[4 * q + 3] = t.w;
-        }
-    } else if constexpr (sizeof(T) == 8 && PB % 2 == 0) {
-#pragma unroll
-        for (int q = 0; q < PB / 2; q++) {
-            const double2 t = __ldg(reinterpret_cast<const double2*>(src) + q);
-            cv[2 * q] = t.x; cv[2 * q + 1] = t.y;
-        }
-    } else {
-#pragma unroll
-        for (int p = 0; p < PB; p++) cv[p] = __ldg(src + p);
-    }
-}
-
-// One thread: R pixels m = m0 + threadIdx.x + r*THREADS, PB phases.  acc holds
-// F_q - (group 0) + folded class terms; tmp accumulates one class before its fold.
+// One block: pixel tile blockIdx.x of phase block blockIdx.y, effect blockIdx.z.
 template <typename T, int PB, int R, int THREADS>
 __global__ void __launch_bounds__(THREADS)
 k_contract(int64_t n_px, int64_t row_len, int64_t pad, Rows<T> rows, const Job* __restrict__ jobs,
@@ -259,92 +137,11 @@ k_contract(int64_t n_px, int64_t row_len, int64_t pad, Rows<T> rows, const Job* 
            int max_coef, ClassTypes ctype, const T* __restrict__ contrast,
            const T* __restrict__ fq, int n_phases, EffectList effs, T* __restrict__ out) {
     const int pb = blockIdx.y;
-    const int eff = effs.e[blockIdx.z];
-    const int64_t mbase = (int64_t)blockIdx.x * THREADS * R + threadIdx.x;
-    int64_t mc[R];
-#pragma unroll
-    for (int r = 0; r < R; r++) {
-        int64_t m = mbase + (int64_t)r * THREADS;
-        mc[r] = pad + (m < n_px ? m : n_px - 1);
-    }
-    T acc[PB][R];
-#pragma unroll
-    for (int r = 0; r < R; r++) {
-        T f0 = fq ? fq[mc[r] - pad] : T(0);
-#pragma unroll
-        for (int p = 0; p < PB; p++) acc[p][r] = f0;
-    }
-    const Job* jb = jobs + (int64_t)pb * max_jobs;
-    const int* gs = gstart + (int64_t)pb * (G + 1);
-    const T* cb = coefs + (int64_t)pb * max_coef;
-
-    // group 0: subtract (active star) or add (quiet star) the quiet-row convolutions
-    for (int jj = gs[0]; jj < gs[1]; jj++) {
-        const Job J = jb[jj];
-        const T* row = rows.q + (int64_t)J.bin * row_len;
-        const T* cf = cb + J.coef_off;
-#pragma unroll 4
-        for (int kk = 0; kk < J.n_k; kk++) {
-            const int64_t k = J.k_lo + kk;
-            T s[R];
-#pragma unroll
-            for (int r = 0; r < R; r++) s[r] = __ldg(row + mc[r] - k);
-            T cv[PB];
-            load_coefs<T, PB>(cf + kk * PB, cv);
-#pragma unroll
-            for (int p = 0; p < PB; p++)
-#pragma unroll
-                for (int r = 0; r < R; r++) acc[p][r] = fma(cv[p], s[r], acc[p][r]);
-        }
-    }
-    // classes: tmp = sum_b K_cl,b * S, then acc += C_cl . tmp (TOT, FLUX) or tmp (BCONV)
-    for (int g = 1; g < G; g++) {
-        if (gs[g] == gs[g + 1]) continue;
-        const int cl = g - 1;
-        const T* base = eff == SOAP_EFFECT_FLUX ? rows.q : rows.a[ctype.t[cl] == SOAP_FACULA ? 1 : 0];
-        T tmp[PB][R];
-#pragma unroll
-        for (int p = 0; p < PB; p++)
-#pragma unroll
-            for (int r = 0; r < R; r++) tmp[p][r] = T(0);
-        for (int jj = gs[g]; jj < gs[g + 1]; jj++) {
-            const Job J = jb[jj];
-            const T* row = base + (int64_t)J.bin * row_len;
-            const T* cf = cb + J.coef_off;
-#pragma unroll 4
-            for (int kk = 0; kk < J.n_k; kk++) {
-                const int64_t k = J.k_lo + kk;
-                T s[R];
-#pragma unroll
-                for (int r = 0; r < R; r++) s[r] = __ldg(row + mc[r] - k);
-                T cv[PB];
-                load_coefs<T, PB>(cf + kk * PB, cv);
-#pragma unroll
-                for (int p = 0; p < PB; p++)
-#pragma unroll
-                    for (int r = 0; r < R; r++) tmp[p][r] = fma(cv[p], s[r], tmp[p][r]);
-            }
-        }
-#pragma unroll
-        for (int r = 0; r < R; r++) {
-            const T cr = eff == SOAP_EFFECT_BCONV ? T(1) : contrast[(int64_t)cl * n_px + (mc[r] - pad)];
-#pragma unroll
-            for (int p = 0; p < PB; p++) acc[p][r] = fma(cr, tmp[p][r], acc[p][r]);
-        }
-    }
-    // store out[e][p][m]
-    const int64_t plane = (int64_t)n_phases * n_px;
-    T* o = out + (int64_t)blockIdx.z * plane;
-#pragma unroll
-    for (int p = 0; p < PB; p++) {
-        const int ph = pb * PB + p;
-        if (ph >= n_phases) break;
-#pragma unroll
-        for (int r = 0; r < R; r++) {
-            const int64_t m = mbase + (int64_t)r * THREADS;
-            if (m < n_px) o[(int64_t)ph * n_px + m] = acc[p][r];
-        }
-    }
+    const int np = min(PB, n_phases - pb * PB);
+    T* out_rows = out + (int64_t)blockIdx.z * n_phases * n_px + (int64_t)pb * PB * n_px;
+    contract_tile<T, PB, R, THREADS>(n_px, row_len, pad, rows, jobs + (int64_t)pb * max_jobs,
+                                     gstart + (int64_t)pb * (G + 1), G, coefs + (int64_t)pb * max_coef,
+                                     ctype, contrast, fq, effs.e[blockIdx.z], blockIdx.x, np, out_rows);
 }
 
 // ---------------------------------------------------------------------------------------

@@ -1,0 +1,242 @@
+// contract_dev.cuh -- device code of the Toeplitz contraction shared by the single-star
+// kernels (contract.cu) and the batched persistent kernel (batch.cu).
+//
+// contract_tile() computes one pixel tile of one block of PB phases:
+//   out[p][m] = F_q[m] - sum_b Q_p,b * S_q,b [m] + sum_cl C_cl[m] sum_b K_p,cl,b * S_a(cl),b [m]
+// (Eqs. 1-4 for the effect `eff`), from a job table (group, mu bin, tap range, coefficients
+// [tap][PB]).  One thread owns R pixels m = m0 + threadIdx.x + r*THREADS; acc holds F_q - group 0
+// + folded class terms, tmp one class before its fold.
+#pragma once
+
+#include "soap_internal.cuh"
+
+namespace soap {
+
+template <typename T>
+struct Rows {
+    const T* q;         // quiet rows [n_mu][row_len]
+    const T* a[2];      // active rows spot / facula
+};
+
+struct ClassTypes {
+    int t[SOAP_MAX_CLASSES];
+};
+
+struct EffectList {
+    int e[3];
+};
+
+// PB coefficients of one tap (16-byte vector loads when PB allows; coefficient slabs are
+// 256-byte aligned and every job's block is a multiple of PB elements).
+template <typename T, int PB>
+__device__ __forceinline__ void load_coefs(const T* __restrict__ src, T (&cv)[PB]) {
+    if constexpr (sizeof(T) == 4 && PB % 4 == 0) {
+#pragma unroll
+        for (int q = 0; q < PB / 4; q++) {
+            const float4 t = __ldg(reinterpret_cast<const float4*>(src) + q);
+            cv[4 * q] = t.x; cv[4 * q + 1] = t.y; cv[4 * q + 2] = t.z; cv[4 * q + 3] = t.w;
+        }
+    } else if constexpr (sizeof(T) == 8 && PB % 2 == 0) {
+#pragma unroll
+        for (int q = 0; q < PB / 2; q++) {
+            const double2 t = __ldg(reinterpret_cast<const double2*>(src) + q);
+            cv[2 * q] = t.x; cv[2 * q + 1] = t.y;
+        }
+    } else {
+#pragma unroll
+        for (int p = 0; p < PB; p++) cv[p] = __ldg(src + p);
+    }
+}
+
+template <typename T, int PB, int R, int THREADS>
+__device__ __forceinline__ void contract_tile(int64_t n_px, int64_t row_len, int64_t pad,
+                                              const Rows<T>& rows, const Job* __restrict__ jb,
+                                              const int* __restrict__ gs, int G,
+                                              const T* __restrict__ cb, const ClassTypes& ctype,
+                                              const T* __restrict__ contrast,
+                                              const T* __restrict__ fq, int eff, int64_t tile,
+                                              int np, T* __restrict__ out_rows) {
+    const int64_t mbase = tile * THREADS * R + threadIdx.x;
+    int64_t mc[R];
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+        int64_t m = mbase + (int64_t)r * THREADS;
+        mc[r] = pad + (m < n_px ? m : n_px - 1);
+    }
+    T acc[PB][R];
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+        T f0 = fq ? fq[mc[r] - pad] : T(0);
+#pragma unroll
+        for (int p = 0; p < PB; p++) acc[p][r] = f0;
+    }
+
+    // group 0: subtract (active star) or add (quiet star) the quiet-row convolutions
+    for (int jj = gs[0]; jj < gs[1]; jj++) {
+        const Job J = jb[jj];
+        const T* row = rows.q + (int64_t)J.bin * row_len;
+        const T* cf = cb + J.coef_off;
+#pragma unroll 4
+        for (int kk = 0; kk < J.n_k; kk++) {
+            const int64_t k = J.k_lo + kk;
+            T s[R];
+#pragma unroll
+            for (int r = 0; r < R; r++) s[r] = __ldg(row + mc[r] - k);
+            T cv[PB];
+            load_coefs<T, PB>(cf + kk * PB, cv);
+#pragma unroll
+            for (int p = 0; p < PB; p++)
+#pragma unroll
+                for (int r = 0; r < R; r++) acc[p][r] = fma(cv[p], s[r], acc[p][r]);
+        }
+    }
+    // classes: tmp = sum_b K_cl,b * S, then acc += C_cl . tmp (TOT, FLUX) or tmp (BCONV)
+    for (int g = 1; g < G; g++) {
+        if (gs[g] == gs[g + 1]) continue;
+        const int cl = g - 1;
+        const T* base = eff == SOAP_EFFECT_FLUX ? rows.q : rows.a[ctype.t[cl] == SOAP_FACULA ? 1 : 0];
+        T tmp[PB][R];
+#pragma unroll
+        for (int p = 0; p < PB; p++)
+#pragma unroll
+            for (int r = 0; r < R; r++) tmp[p][r] = T(0);
+        for (int jj = gs[g]; jj < gs[g + 1]; jj++) {
+            const Job J = jb[jj];
+            const T* row = base + (int64_t)J.bin * row_len;
+            const T* cf = cb + J.coef_off;
+#pragma unroll 4
+            for (int kk = 0; kk < J.n_k; kk++) {
+                const int64_t k = J.k_lo + kk;
+                T s[R];
+#pragma unroll
+                for (int r = 0; r < R; r++) s[r] = __ldg(row + mc[r] - k);
+                T cv[PB];
+                load_coefs<T, PB>(cf + kk * PB, cv);
+#pragma unroll
+                for (int p = 0; p < PB; p++)
+#pragma unroll
+                    for (int r = 0; r < R; r++) tmp[p][r] = fma(cv[p], s[r], tmp[p][r]);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const T cr = eff == SOAP_EFFECT_BCONV ? T(1) : contrast[(int64_t)cl * n_px + (mc[r] - pad)];
+#pragma unroll
+            for (int p = 0; p < PB; p++) acc[p][r] = fma(cr, tmp[p][r], acc[p][r]);
+        }
+    }
+    // store out_rows[p][m]
+#pragma unroll
+    for (int p = 0; p < PB; p++) {
+        if (p >= np) break;
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const int64_t m = mbase + (int64_t)r * THREADS;
+            if (m < n_px) out_rows[(int64_t)p * n_px + m] = acc[p][r];
+        }
+    }
+}
+
+
+// FP32 contrast per class (relative error ~1e-7, inside the mixed path's 2e-6).
+struct ClassConsts {
+    float a[SOAP_MAX_CLASSES];       // h c / (lambda_s k T_class)
+};
+
+static __global__ void k_contrast32(int64_t n_px, float aq, float fd, int n_class, ClassConsts ac, float* c32) {
+    for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < n_px;
+         m += (int64_t)gridDim.x * blockDim.x) {
+        const float inv = expf(-(float)m * fd);            // lambda_s / lambda_m
+        const float xq = expm1f(aq * inv);
+        for (int cl = 0; cl < n_class; cl++) c32[cl * n_px + m] = xq / expm1f(ac.a[cl] * inv);
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// regions (Alg. 5): centre, cap and cell box per (phase, region), and the InfoMap owner
+// ---------------------------------------------------------------------------------------
+struct RegionGeo {
+    double P[3];       // unit vector of the cap centre, observer frame
+    double cosr;       // cos of the cap's angular radius, sqrt(1 - r^2)
+    float Pf[3];
+    float cosrf;
+    int box[4];        // i0, i1, j0, j1 (empty if i1 < i0)
+    int cls;
+    int pad;
+};
+
+// Region centre at `phase` (observer frame, rotation axis (0, sin i, cos i)): star-frame
+// (cos lat sin L, sin lat, cos lat cos L) with L = lon + 360 phase (1 + alpha sin^2 lat), tilted
+// by the inclination; written with explicitly rounded FP64 steps.  The cell box is
+// conservative: the cap reaches axis angles within +-asin(r) of the centre's.
+__device__ __forceinline__ RegionGeo region_geometry(int N, const RegionDev& g, double phase, double incl_deg,
+                                                     double alpha) {
+    const double d2r = kPi / 180.0;
+    const double lat = __dmul_rn(g.lat_deg, d2r);
+    const double sl = sin(lat), cl = cos(lat);
+    const double lonp = __dadd_rn(g.lon_deg, __dmul_rn(__dmul_rn(360.0, phase),
+                                                       __dadd_rn(1.0, __dmul_rn(__dmul_rn(alpha, sl), sl))));
+    const double lon = __dmul_rn(lonp, d2r);
+    const double incl = __dmul_rn(incl_deg, d2r);
+    const double si = sin(incl), ci = cos(incl);
+    const double px = __dmul_rn(cl, sin(lon)), py = sl, pz = __dmul_rn(cl, cos(lon));
+    RegionGeo o;
+    o.P[0] = px;
+    o.P[1] = __dsub_rn(__dmul_rn(py, si), __dmul_rn(pz, ci));
+    o.P[2] = __dadd_rn(__dmul_rn(py, ci), __dmul_rn(pz, si));
+    const double r = g.radius;
+    o.cosr = __dsqrt_rn(__dsub_rn(1.0, __dmul_rn(r, r)));
+    for (int k = 0; k < 3; k++) o.Pf[k] = (float)o.P[k];
+    o.cosrf = (float)o.cosr;
+    o.cls = g.cls;
+    o.pad = 0;
+    const double a = asin(fmin(r, 1.0));
+    const double bx = acos(fmax(-1.0, fmin(1.0, o.P[0])));
+    const double by = acos(fmax(-1.0, fmin(1.0, o.P[1])));
+    const double bz = acos(fmax(-1.0, fmin(1.0, o.P[2])));
+    const double xhi = cos(fmax(0.0, bx - a)), xlo = cos(fmin(kPi, bx + a));
+    const double yhi = cos(fmax(0.0, by - a)), ylo = cos(fmin(kPi, by + a));
+    int i0 = (int)floor((xlo * N + N - 1) * 0.5) - 1, i1 = (int)ceil((xhi * N + N - 1) * 0.5) + 1;
+    int j0 = (int)floor((ylo * N + N - 1) * 0.5) - 1, j1 = (int)ceil((yhi * N + N - 1) * 0.5) + 1;
+    i0 = max(i0, 0); j0 = max(j0, 0); i1 = min(i1, N - 1); j1 = min(j1, N - 1);
+    if (bz - a > 0.5 * kPi + 1e-6) i1 = i0 - 1;          // cap entirely on the far side
+    o.box[0] = i0; o.box[1] = i1; o.box[2] = j0; o.box[3] = j1;
+    return o;
+}
+
+// True when cell (i, j) lies in an earlier region's box (each cell is visited once, from the
+// first box that holds it).
+__device__ __forceinline__ bool in_earlier_box(const RegionGeo* sg, int r, int i, int j) {
+    bool dup = false;
+    for (int q = 0; q < r; q++)
+        if (i >= sg[q].box[0] && i <= sg[q].box[1] && j >= sg[q].box[2] && j <= sg[q].box[3]) dup = true;
+    return dup;
+}
+
+// InfoMap owner of a visible cell: a cell (x, y, mu) belongs to a region iff
+// (x, y, mu) . P >= sqrt(1 - r^2); the last region in list order that contains it owns it
+// (-1: none).  An FP32 test decides cells farther than 2e-6 from the edge (its error is below
+// 1e-6); the others are decided by the explicitly rounded FP64 sequence.
+__device__ __forceinline__ int cell_owner(const RegionGeo* sg, int n_regions, int N, int i, int j, float muf,
+                                          const double* __restrict__ cell_mu, int64_t c) {
+    const float invN = 1.0f / (float)N;
+    const float xf = (float)(2 * i + 1 - N) * invN, yf = (float)(2 * j + 1 - N) * invN;
+    int owner = -1;
+    for (int q = 0; q < n_regions; q++) {
+        const float df = fmaf(xf, sg[q].Pf[0], fmaf(yf, sg[q].Pf[1], muf * sg[q].Pf[2]));
+        bool in;
+        if (df > sg[q].cosrf + 2e-6f) in = true;
+        else if (df < sg[q].cosrf - 2e-6f) in = false;
+        else {
+            const double x = (double)(2 * i + 1 - N) / (double)N;
+            const double y = (double)(2 * j + 1 - N) / (double)N;
+            const double dot = __dadd_rn(__dadd_rn(__dmul_rn(x, sg[q].P[0]), __dmul_rn(y, sg[q].P[1])),
+                                         __dmul_rn(cell_mu[c], sg[q].P[2]));
+            in = dot >= sg[q].cosr;
+        }
+        if (in) owner = q;
+    }
+    return owner;
+}
+
+}  // namespace soap

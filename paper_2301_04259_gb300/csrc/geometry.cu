@@ -22,18 +22,6 @@ struct MuTable {
     double v[SOAP_MAX_MU];
 };
 
-// atanh(x) = x + x^3/3 + x^5/5 + x^7/7 + ...; for |x| <= 1e-3 the omitted terms are below
-// 1e-24 of x (GB300 FP64 is slow: four FMAs instead of a general atanh).
-__device__ __forceinline__ double atanh_small(double x) {
-    const double x2 = x * x;
-    return fma(x * x2, fma(x2, fma(x2, 1.0 / 7.0, 1.0 / 5.0), 1.0 / 3.0), x);
-}
-
-// expm1(e) = e + e^2/2 + e^3/6 + ...; for |e| <= 1e-3 terms beyond e^6 are below 1e-21 of e.
-__device__ __forceinline__ double expm1_small(double e) {
-    return fma(e * e, fma(e, fma(e, fma(e, fma(e, 1.0 / 720.0, 1.0 / 120.0), 1.0 / 24.0), 1.0 / 6.0), 0.5), e);
-}
-
 // Nearest tabulated mu, ties to the lower index, as the first minimum of |mu - mu_b| in FP64.
 // For a strictly increasing table the minimum lies next to the insertion point, so only a
 // window around it is scanned (same answer as the full scan).

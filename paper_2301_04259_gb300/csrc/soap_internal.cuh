@@ -158,6 +158,15 @@ struct soap_ctx {
 
     uint64_t launches = 0;
 
+    // batched form: grow-only buffers, the captured graph and the key of what it baked in
+    soap::DevBuf b_items, b_regions, b_phases, b_phase_item, b_phase_block, b_pblocks, b_order;
+    soap::DevBuf b_cellIfx, b_IB, b_colj, b_colw, b_kq, b_qjobs, b_qgs, b_qc32, b_fq, b_con;
+    soap::DevBuf b_geo, b_kfix, b_counters, b_jobs, b_gstart, b_coefs, b_ticket;
+    cudaGraphExec_t b_graph_exec = nullptr;
+    std::vector<uint64_t> b_graph_key;
+    uint64_t b_graph_kernels = 0;
+    int b_variant = -1;             // chosen by soap_batch_set_variant / the autotuner; -1: default
+
     // per-kernel timers
     bool profiling = false;
     struct TimedLaunch { int timer; cudaEvent_t a, b; };
@@ -195,6 +204,14 @@ soap_status toeplitz_active(soap_ctx* c, const RegionDev* regions_host, int n_re
                             const double* phases_host, int n_phases, uint32_t effects,
                             int precision, void* dst);
 
+// Batched form (batch.cu); variant in 0 .. batch_num_variants() - 1, out [n_phases][n_px] FP32.
+soap_status batch_run(soap_ctx* c, const soap_batch_item* items, int n_items, const soap_region* regions,
+                      int n_regions, const double* phases, int n_phases, int variant, float* out);
+int batch_num_variants();
+int batch_default_variant();
+void batch_variant_info(int v, int* phases_per_block, int* px_per_thread);
+void batch_release(soap_ctx* c);
+
 soap_status rv_ccf_run(soap_ctx* c, const void* spectra_dev, int f32, int n_spec,
                        const double* mask_lambda, const double* mask_weight, int n_lines,
                        double width_kms, double v_lo, double v_step, int n_v, double* rv_dev,
@@ -206,6 +223,19 @@ soap_status rv_ccf_run(soap_ctx* c, const void* spectra_dev, int f32, int n_spec
 // job tables of the Toeplitz contraction (shared by geometry.cu and contract.cu)
 // ---------------------------------------------------------------------------------------
 namespace soap {
+
+// atanh(x) = x + x^3/3 + x^5/5 + x^7/7 + ...; for |x| <= 1e-3 the omitted terms are below
+// 1e-24 of x (GB300 FP64 is slow: four FMAs instead of a general atanh).
+__device__ __forceinline__ double atanh_small(double x) {
+    const double x2 = x * x;
+    return fma(x * x2, fma(x2, fma(x2, 1.0 / 7.0, 1.0 / 5.0), 1.0 / 3.0), x);
+}
+
+// expm1(e) = e + e^2/2 + e^3/6 + ...; for |e| <= 1e-3 terms beyond e^6 are below 1e-21 of e.
+__device__ __forceinline__ double expm1_small(double e) {
+    return fma(e * e, fma(e, fma(e, fma(e, fma(e, 1.0 / 720.0, 1.0 / 120.0), 1.0 / 24.0), 1.0 / 6.0), 0.5), e);
+}
+
 
 struct Job {
     int32_t group;     // 0: all active cells (quiet rows, negative), g >= 1: class g-1
@@ -323,7 +353,7 @@ __device__ __forceinline__ void build_jobs_dev(const long long* __restrict__ kfi
         for (int e = lane; e < nk * PB; e += 32) {
             int kk = e / PB, pl = e % PB;
             double v = (double)value(g, b, pl, s_lo[t] + kk) * inv_scale;
-            c64[base + e] = v;
+            if (c64) c64[base + e] = v;
             c32[base + e] = (float)v;
         }
     }

@@ -46,6 +46,12 @@ class soap_region(ctypes.Structure):
                 ("radius_rstar", ctypes.c_double), ("temp_K", ctypes.c_double)]
 
 
+class soap_batch_item(ctypes.Structure):
+    _fields_ = [("vsini_kms", ctypes.c_double), ("incl_deg", ctypes.c_double),
+                ("first_region", ctypes.c_int32), ("n_regions", ctypes.c_int32),
+                ("first_phase", ctypes.c_int32), ("n_phases", ctypes.c_int32)]
+
+
 class soap_star_info(ctypes.Structure):
     _fields_ = [("n_visible", ctypes.c_int64), ("tap_min", ctypes.c_int32),
                 ("n_taps", ctypes.c_int32), ("delta", ctypes.c_double),
@@ -80,6 +86,14 @@ def _load():
         "soap_rv_ccf": (i32, [P, P, i32, i32, ctypes.c_int, P, P, i32, d, d, d, i32, P, P, P, ctypes.c_int]),
         "soap_get_launch_count": (i32, [P, ctypes.POINTER(ctypes.c_uint64)]),
         "soap_rv_ccf_static": (i32, [d, d, i64, P, i32, i32, P, P, i32, d, d, d, i32, P, P, P, P]),
+        "soap_active_batch": (i32, [P, ctypes.POINTER(soap_batch_item), i32, ctypes.POINTER(soap_region), i32,
+                                    P, i32, P, ctypes.c_int]),
+        "soap_batch_num_variants": (i32, [ctypes.POINTER(i32)]),
+        "soap_batch_variant_info": (i32, [i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
+        "soap_batch_set_variant": (i32, [P, i32]),
+        "soap_batch_get_variant": (i32, [P, ctypes.POINTER(i32)]),
+        "soap_batch_autotune": (i32, [P, ctypes.POINTER(soap_batch_item), i32, ctypes.POINTER(soap_region), i32,
+                                      P, i32, P, i32, P, ctypes.POINTER(i32)]),
         "soap_free": (None, [P]),
         "soap_last_error": (ctypes.c_char_p, []),
     }
@@ -253,6 +267,66 @@ def soap_rv_ccf_static(lambda_start_A: float, lambda_end_A: float, n_px: int, sp
                                    int(spectra.shape[0]), ml, mw, int(mask_lambda.shape[0]),
                                    float(mask_width_kms), float(v_lo), float(v_step), int(n_v),
                                    rp, fp, cp, _stream_handle(stream)), "soap_rv_ccf_static")
+
+
+def batch_items_array(items: Sequence) -> ctypes.Array:
+    """items: (vsini_kms, incl_deg, first_region, n_regions, first_phase, n_phases) tuples."""
+    arr = (soap_batch_item * max(1, len(items)))()
+    for k, t in enumerate(items):
+        v, inc, fr, nr, fp, npp = t
+        arr[k] = soap_batch_item(vsini_kms=float(v), incl_deg=float(inc), first_region=int(fr),
+                                 n_regions=int(nr), first_phase=int(fp), n_phases=int(npp))
+    return arr
+
+
+def soap_active_batch(ctx, items: Sequence, regions: Sequence, phases, out) -> None:
+    """out: float32 [n_phases, n_px], host (numpy) or device (torch)."""
+    ia = batch_items_array(items)
+    ra = regions_array(regions)
+    ph = np.ascontiguousarray(phases, dtype=np.float64)
+    ptr, dev = _ptr(out)
+    _check(_lib.soap_active_batch(ctx, ia, len(items), ra, len(regions), ctypes.c_void_p(ph.ctypes.data),
+                                  ph.size, ptr, dev), "soap_active_batch")
+
+
+def soap_batch_num_variants() -> int:
+    n = ctypes.c_int32()
+    _check(_lib.soap_batch_num_variants(ctypes.byref(n)), "soap_batch_num_variants")
+    return int(n.value)
+
+
+def soap_batch_variant_info(variant: int):
+    """(phases per block, pixels per thread) of a variant."""
+    pb, r = ctypes.c_int32(), ctypes.c_int32()
+    _check(_lib.soap_batch_variant_info(int(variant), ctypes.byref(pb), ctypes.byref(r)),
+           "soap_batch_variant_info")
+    return int(pb.value), int(r.value)
+
+
+def soap_batch_set_variant(ctx, variant: int) -> None:
+    _check(_lib.soap_batch_set_variant(ctx, int(variant)), "soap_batch_set_variant")
+
+
+def soap_batch_get_variant(ctx) -> int:
+    v = ctypes.c_int32()
+    _check(_lib.soap_batch_get_variant(ctx, ctypes.byref(v)), "soap_batch_get_variant")
+    return int(v.value)
+
+
+def soap_batch_autotune(ctx, items: Sequence, regions: Sequence, phases, out, reps: int = 3):
+    """Times every variant (out: device float32 scratch); returns (best, ms per variant)."""
+    ia = batch_items_array(items)
+    ra = regions_array(regions)
+    ph = np.ascontiguousarray(phases, dtype=np.float64)
+    ptr, dev = _ptr(out)
+    if not dev:
+        raise ValueError("soap_batch_autotune needs a device output buffer")
+    ms = np.zeros(soap_batch_num_variants(), dtype=np.float32)
+    best = ctypes.c_int32()
+    _check(_lib.soap_batch_autotune(ctx, ia, len(items), ra, len(regions), ctypes.c_void_p(ph.ctypes.data),
+                                    ph.size, ptr, int(reps), ctypes.c_void_p(ms.ctypes.data),
+                                    ctypes.byref(best)), "soap_batch_autotune")
+    return int(best.value), ms
 
 
 def soap_get_launch_count(ctx) -> int:

@@ -241,6 +241,18 @@ def batch_configs(seed: int, n_configs: int) -> List[BatchConfig]:
     return out
 
 
+def batch_layout(configs: List[BatchConfig]):
+    """Flatten configs into (items, regions, phases): item k = (vsini, incl, first_region,
+    n_regions, first_phase, n_phases); config k's phases are j / n_phases, j = 0 .. n_phases-1
+    (one rotation)."""
+    items, regions, phases = [], [], []
+    for c in configs:
+        items.append((c.vsini_kms, c.incl_deg, len(regions), len(c.regions), len(phases), c.n_phases))
+        regions.extend(c.regions)
+        phases.extend((np.arange(c.n_phases) / c.n_phases).tolist())
+    return items, regions, np.asarray(phases, dtype=np.float64)
+
+
 def batch_spectra(seed: int, *, grid_n: int = 150, n_px: Optional[int] = None,
                   lambda_start: float = 6000.0, lambda_end: float = 6300.0) -> Case:
     """Shared local spectra for the batched workload (6000-6300 A, R=115000 x3 sampling)."""

@@ -69,3 +69,22 @@ def test_null_arguments_are_rejected(lib):
     assert lib._lib.soap_quiet_spectrum(None, 0, 0, None, 0) == lib.SOAP_EINVAL
     assert lib._lib.soap_active_phases(None, None, 0, None, 0, 1, 0, None, 0) == lib.SOAP_EINVAL
     lib._lib.soap_free(None)
+
+
+def test_batch_entry_points_without_a_gpu(lib):
+    assert lib._lib.soap_active_batch(None, None, 0, None, 0, None, 0, None, 0) == lib.SOAP_EINVAL
+    n = lib.soap_batch_num_variants()
+    assert n >= 2
+    seen = set()
+    for v in range(n):
+        pb, r = lib.soap_batch_variant_info(v)
+        assert pb in (1, 2, 4, 8, 16) and r in (1, 2, 4, 8)
+        seen.add((pb, r))
+    assert len(seen) == n                                    # no duplicate variants
+    with pytest.raises(lib.SoapError) as ei:
+        lib.soap_batch_variant_info(n)
+    assert ei.value.status == lib.SOAP_ERANGE
+    assert lib._lib.soap_batch_set_variant(None, 0) == lib.SOAP_EINVAL
+    best = ctypes.c_int32()
+    assert lib._lib.soap_batch_autotune(None, None, 0, None, 0, None, 0, None, 1, None,
+                                        ctypes.byref(best)) == lib.SOAP_EINVAL

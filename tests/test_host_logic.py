@@ -1,0 +1,70 @@
+"""Host-side logic that needs no GPU: the batch layout of the input generators and the
+persisted variant choice of the batched form."""
+import json
+
+import numpy as np
+
+from paper_2301_04259_gb300 import synth, tuning
+from paper_2301_04259_gb300.synth import SPOT, Region
+
+
+def test_batch_layout_covers_every_phase_once():
+    cfgs = synth.batch_configs(3, 50)
+    items, regions, phases = synth.batch_layout(cfgs)
+    assert len(items) == 50 and len(regions) == sum(len(c.regions) for c in cfgs)
+    owner = np.full(phases.size, -1)
+    for k, (v, inc, fr, nr, fp, n) in enumerate(items):
+        assert (v, inc) == (cfgs[k].vsini_kms, cfgs[k].incl_deg)
+        assert regions[fr:fr + nr] == cfgs[k].regions
+        assert n == cfgs[k].n_phases and (owner[fp:fp + n] == -1).all()
+        owner[fp:fp + n] = k
+        np.testing.assert_array_equal(phases[fp:fp + n], np.arange(n) / n)
+    assert (owner >= 0).all()
+
+
+def test_batch_configs_follow_the_stated_distributions():
+    cfgs = synth.batch_configs(0, 4096)
+    v = np.array([c.vsini_kms for c in cfgs])
+    inc = np.array([c.incl_deg for c in cfgs])
+    n_ph = np.array([c.n_phases for c in cfgs])
+    n_sp = np.array([len(c.regions) for c in cfgs])
+    r = np.array([g.radius_rstar for c in cfgs for g in c.regions])
+    lat = np.array([g.lat_deg for c in cfgs for g in c.regions])
+    assert 1 <= v.min() and v.max() <= 10 and 30 <= inc.min() and inc.max() <= 90
+    assert n_ph.min() >= 10 and n_ph.max() <= 200 and abs(n_ph.mean() - 105) < 3
+    assert set(n_sp.tolist()) == {1, 2, 3, 4}
+    assert 0.01 <= r.min() and r.max() <= 0.2 and np.abs(lat).max() <= 60
+    assert all(g.type == SPOT and g.temp_K == 4800.0 for c in cfgs for g in c.regions)
+    assert synth.batch_configs(0, 5)[3].regions == cfgs[3].regions          # seeded
+
+
+def test_variant_choice_is_tuned_once_then_read_back(tmp_path):
+    path = tmp_path / "sub" / "tune.json"
+    calls, chosen = [], []
+    key = tuning.tuning_key(16834, 27, 20, 150, "GPU X")
+
+    def autotune():
+        calls.append(1)
+        return 3, [5.0, 4.0, 3.5, 1.0, 2.0, 9.0]
+
+    e = tuning.choose_variant(key, autotune, chosen.append, 6, path=path)
+    assert e["source"] == "autotune" and e["variant"] == 3 and chosen == [3]
+    assert json.loads(path.read_text())[key]["variant"] == 3
+    e = tuning.choose_variant(key, autotune, chosen.append, 6, path=path)
+    assert e["source"] == "cache" and len(calls) == 1 and chosen == [3, 3]
+    # another shape is tuned separately; a stale entry outside the variant range is retuned
+    key2 = tuning.tuning_key(4096, 27, 20, 150, "GPU X")
+    tuning.choose_variant(key2, lambda: (1, [1.0] * 6), chosen.append, 6, path=path)
+    assert len(json.loads(path.read_text())) == 2
+    e = tuning.choose_variant(key, lambda: (0, [1.0] * 2), chosen.append, 2, path=path)
+    assert e["source"] == "autotune" and e["variant"] == 0
+    e = tuning.choose_variant(key, autotune, chosen.append, 6, path=path, retune=True)
+    assert e["source"] == "autotune" and len(calls) == 2
+
+
+def test_corrupt_tuning_table_is_replaced(tmp_path):
+    path = tmp_path / "tune.json"
+    path.write_text("{not json")
+    chosen = []
+    e = tuning.choose_variant("k", lambda: (2, [3.0, 2.0, 1.0]), chosen.append, 3, path=path)
+    assert e["variant"] == 2 and json.loads(path.read_text()) == {"k": {"variant": 2, "ms": [3.0, 2.0, 1.0]}}
