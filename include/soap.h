@@ -134,11 +134,12 @@ typedef struct {
 
 /* Kernel timers (soap_set_profiling / soap_get_kernel_time). */
 typedef enum {
-    SOAP_TIMER_GEOMETRY = 0,     /* per-cell geometry + quiet velocity kernels */
+    SOAP_TIMER_GEOMETRY = 0,     /* per-cell geometry + quiet velocity kernels (batched form: per-column
+                                    tables and quiet kernels of every configuration) */
     SOAP_TIMER_PAD_ROWS = 1,     /* local spectra -> replicate-padded rows */
     SOAP_TIMER_CONTRAST = 2,     /* Planck contrast per region class */
     SOAP_TIMER_PHASE_HIST = 3,   /* InfoMap + per-phase velocity kernels */
-    SOAP_TIMER_JOBS = 4,         /* job tables (now built inside the geometry and histogram kernels: 0) */
+    SOAP_TIMER_REGIONS = 4,      /* region centres and cell boxes per (phase, region) */
     SOAP_TIMER_CONTRACT = 5,     /* Toeplitz contraction, active phases */
     SOAP_TIMER_CONTRACT_QUIET = 6, /* Toeplitz contraction, quiet star */
     SOAP_TIMER_DIRECT = 7,       /* direct-form disk sum (+ split reduction) */

@@ -85,7 +85,7 @@ static void free_ctx_memory(soap_ctx* c) {
     void* ptrs[] = {c->cell_I, c->cell_w, c->cell_mu, c->cell_j, c->cell_bin, c->cell_mu32,
                     c->cell_k0, c->cell_k1, c->flags, c->q64,
                     c->q32, c->a64[0], c->a32[0], c->a64[1], c->a32[1], c->kq_fixed,
-                    c->sum_I_fixed, c->qjobs, c->qc64, c->qc32, c->geo_counter};
+                    c->sum_I_fixed, c->qtoff, c->qgstart, c->qc64, c->qc32, c->geo_counter};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     DevBuf* bufs[] = {&c->stage_in, &c->fq, &c->contrast, &c->kphase, &c->jobs, &c->coefs, &c->job_counters,
@@ -253,7 +253,8 @@ soap_status soap_init_star(const soap_star_desc* s, const double* quiet_local, i
     c->n_taps = (int)(tmax - tmin + 1);
     int64_t need = std::max<int64_t>(tmax, -tmin) + 1;
     c->pad = round_up(need, 32);
-    c->row_len = round_up(c->n_px + 2 * c->pad, 32);
+    // rows reach past the last tile of any contraction (tiles of up to 1024 pixels)
+    c->row_len = round_up(round_up(c->n_px, 1024) + 2 * c->pad, 32);
 
     soap_status st = SOAP_OK;
     size_t NN = (size_t)c->N * c->N;
@@ -273,7 +274,8 @@ soap_status soap_init_star(const soap_star_desc* s, const double* quiet_local, i
     ALLOC(c->q32, rows * sizeof(float));
     ALLOC(c->kq_fixed, (size_t)c->n_mu * SOAP_MAX_TAPS * sizeof(long long));
     ALLOC(c->sum_I_fixed, 2 * sizeof(long long));
-    ALLOC(c->qjobs, (size_t)c->n_mu * 32 + 16);
+    ALLOC(c->qtoff, (size_t)c->n_mu * SOAP_MAX_TAPS * sizeof(long long));
+    ALLOC(c->qgstart, 2 * sizeof(int));
     ALLOC(c->qc64, (size_t)c->n_mu * SOAP_MAX_TAPS * sizeof(double));
     ALLOC(c->qc32, (size_t)c->n_mu * SOAP_MAX_TAPS * sizeof(float));
     ALLOC(c->geo_counter, sizeof(int));

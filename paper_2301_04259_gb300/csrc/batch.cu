@@ -14,8 +14,8 @@
 //  4 k_batch_regions  region centres / cell boxes per (phase, region)
 //  5 k_batch_hist     InfoMap + per-phase kernels; the last block of each phase block builds
 //                     its job table
-//  6 k_batch_contract persistent: blocks take (phase block, pixel tile) units from an atomic
-//                     ticket, in an order sorted by estimated cost (largest first)
+//  6 k_batch_contract persistent: blocks take phase blocks (all pixel tiles of one) from an
+//                     atomic ticket, in an order sorted by estimated cost (largest first)
 #include <algorithm>
 #include <cmath>
 #include <numeric>
@@ -69,8 +69,8 @@ __global__ void k_batch_items(int N, int n_mu, int n_taps, int tap_min, double i
                               double delta, double inv_expm1_delta, const BatchItemDev* __restrict__ items,
                               const long long* __restrict__ IB, int* __restrict__ colj,
                               unsigned int* __restrict__ colw, long long* __restrict__ kq,
-                              Job* qjobs, int* qgs, float* qc32, int q_max_coef, double inv_scale,
-                              unsigned int* flags) {
+                              long long* qtoff, int* qgs, float* qc32, int q_max_taps, double inv_scale,
+                              int64_t row_len, int64_t pad, unsigned int* flags) {
     extern __shared__ long long hist[];                  // [n_mu][n_taps]
     const int it = blockIdx.x;
     const int nb = n_mu * n_taps;
@@ -108,23 +108,21 @@ __global__ void k_batch_items(int N, int n_mu, int n_taps, int tap_min, double i
     for (int t = threadIdx.x; t < nb; t += blockDim.x) dst[t] = hist[t];
     __threadfence_block();
     __syncthreads();
-    build_jobs_dev(dst, 0, 1, 1, n_mu, n_taps, tap_min, 1, 0, inv_scale, qjobs + (int64_t)it * n_mu,
-                   qgs + (int64_t)it * 2, nullptr, qc32 + (int64_t)it * q_max_coef, n_mu, q_max_coef,
-                   hist, flags);
+    build_taps_dev(dst, 0, 1, 1, n_mu, n_taps, tap_min, 1, 0, inv_scale, row_len, pad,
+                   qtoff + (int64_t)it * q_max_taps, qgs + (int64_t)it * 2, nullptr,
+                   qc32 + (int64_t)it * q_max_taps, q_max_taps, hist, flags);
 }
 
 // Stage 3: grid (tiles, configurations).
 template <int R, int THREADS>
 __global__ void __launch_bounds__(THREADS)
-k_batch_quiet(int64_t n_px, int64_t row_len, int64_t pad, Rows<float> rows, const Job* __restrict__ qjobs,
-              const int* __restrict__ qgs, int n_mu, const float* __restrict__ qc32, int q_max_coef,
-              float* __restrict__ fq) {
+k_batch_quiet(int64_t n_px, Rows<float> rows, const long long* __restrict__ qtoff, const int* __restrict__ qgs,
+              const float* __restrict__ qc32, int q_max_taps, float* __restrict__ fq) {
     const int it = blockIdx.y;
     ClassTypes ct{};
-    contract_tile<float, 1, R, THREADS>(n_px, row_len, pad, rows, qjobs + (int64_t)it * n_mu,
-                                        qgs + (int64_t)it * 2, 1, qc32 + (int64_t)it * q_max_coef, ct,
-                                        nullptr, nullptr, SOAP_EFFECT_TOT, blockIdx.x, 1,
-                                        fq + (int64_t)it * n_px);
+    contract_tile<float, 1, R, THREADS>(n_px, rows, qtoff + (int64_t)it * q_max_taps, qgs + (int64_t)it * 2, 1,
+                                        qc32 + (int64_t)it * q_max_taps, ct, nullptr, nullptr, SOAP_EFFECT_TOT,
+                                        blockIdx.x, 1, fq + (int64_t)it * n_px);
 }
 
 // Stage 4: thread per (phase, region slot).
@@ -149,8 +147,8 @@ __global__ void k_batch_hist(int N, int max_r, const int* __restrict__ phase_ite
                              const int32_t* __restrict__ cell_bin, const long long* __restrict__ cell_Ifx,
                              const int* __restrict__ colj, const unsigned int* __restrict__ colw,
                              int tap_min, int n_taps, int n_mu, int n_class, long long* kfix, int use_smem,
-                             int PB, double inv_scale, Job* jobs, int* gstart, float* c32, int max_jobs,
-                             int max_coef, int* counters, int jobs_smem, unsigned int* flags) {
+                             int PB, double inv_scale, int64_t row_len, int64_t pad, long long* toff, int* gstart,
+                             float* c32, int max_taps, int* counters, int taps_smem, unsigned int* flags) {
     __shared__ RegionGeo sg[SOAP_MAX_REGIONS];
     extern __shared__ long long hist_sm[];
     const int p = blockIdx.x;
@@ -203,23 +201,21 @@ __global__ void k_batch_hist(int N, int max_r, const int* __restrict__ phase_ite
     __syncthreads();
     if (s_last) {
         __threadfence();
-        build_jobs_dev(kfix + (int64_t)pbd.first_phase * nb, 0, pbd.np, n_class, n_mu, n_taps, tap_min, PB, 1,
-                       inv_scale, jobs + (int64_t)pbk * max_jobs, gstart + (int64_t)pbk * (1 + n_class + 1),
-                       nullptr, c32 + (int64_t)pbk * max_coef, max_jobs, max_coef, jobs_smem ? hist_sm : nullptr,
-                       flags);
+        build_taps_dev(kfix + (int64_t)pbd.first_phase * nb, 0, pbd.np, n_class, n_mu, n_taps, tap_min, PB, 1,
+                       inv_scale, row_len, pad, toff + (int64_t)pbk * max_taps, gstart + (int64_t)pbk * (n_class + 2),
+                       nullptr, c32 + (int64_t)pbk * max_taps * PB, max_taps, taps_smem ? hist_sm : nullptr, flags);
     }
 }
 
-// Stage 6: persistent.  Units (phase block, pixel tile) in `order`; blocks take the next unit
-// with an atomic ticket until none is left (no block waits on another).
+// Stage 6: persistent.  A unit is one phase block over all pixel tiles; blocks take the next
+// unit in `order` with an atomic ticket until none is left (no block waits on another).
 template <int PB, int R, int THREADS>
 __global__ void __launch_bounds__(THREADS)
-k_batch_contract(int64_t n_px, int64_t row_len, int64_t pad, Rows<float> rows, const Job* __restrict__ jobs,
-                 const int* __restrict__ gstart, int G, int max_jobs, const float* __restrict__ c32,
-                 int max_coef, ClassTypes ctype, const float* __restrict__ contrast,
-                 const float* __restrict__ fq, const PBlockDev* __restrict__ pblocks,
-                 const int* __restrict__ order, int n_units, int n_tiles, unsigned int* ticket,
-                 float* __restrict__ out) {
+k_batch_contract(int64_t n_px, Rows<float> rows, const long long* __restrict__ toff, const int* __restrict__ gstart,
+                 int G, int max_taps, const float* __restrict__ c32, ClassTypes ctype,
+                 const float* __restrict__ contrast, const float* __restrict__ fq,
+                 const PBlockDev* __restrict__ pblocks, const int* __restrict__ order, int n_units, int n_tiles,
+                 unsigned int* ticket, float* __restrict__ out) {
     __shared__ int s_u;
     while (true) {
         if (threadIdx.x == 0) s_u = (int)atomicAdd(ticket, 1u);
@@ -227,13 +223,16 @@ k_batch_contract(int64_t n_px, int64_t row_len, int64_t pad, Rows<float> rows, c
         const int u = s_u;
         __syncthreads();
         if (u >= n_units) break;
-        const int unit = order[u];
-        const int pbk = unit / n_tiles, tile = unit % n_tiles;
+        const int pbk = order[u];
         const PBlockDev pb = pblocks[pbk];
-        contract_tile<float, PB, R, THREADS>(n_px, row_len, pad, rows, jobs + (int64_t)pbk * max_jobs,
-                                             gstart + (int64_t)pbk * (G + 1), G, c32 + (int64_t)pbk * max_coef,
-                                             ctype, contrast, fq + (int64_t)pb.item * n_px, SOAP_EFFECT_TOT,
-                                             tile, pb.np, out + (int64_t)pb.first_phase * n_px);
+        const long long* tt = toff + (int64_t)pbk * max_taps;
+        const int* gs = gstart + (int64_t)pbk * (G + 1);
+        const float* cb = c32 + (int64_t)pbk * max_taps * PB;
+        const float* fqi = fq + (int64_t)pb.item * n_px;
+        float* orow = out + (int64_t)pb.first_phase * n_px;
+        for (int tile = 0; tile < n_tiles; tile++)
+            contract_tile<float, PB, R, THREADS>(n_px, rows, tt, gs, G, cb, ctype, contrast, fqi, SOAP_EFFECT_TOT,
+                                                 tile, pb.np, orow);
     }
 }
 
@@ -253,9 +252,9 @@ constexpr int kDefaultVariant = 1;
 // Sizes of one batch, fixed by the host preparation and baked into the captured graph.
 struct BatchShape {
     int n_items, n_phases, max_r, n_pblocks, n_units, n_tiles, variant, n_class;
-    int G, max_jobs, max_coef;
+    int G, max_taps;
     int64_t nbk;               // per-phase kernel size n_class * n_mu * n_taps
-    int use_smem, jobs_smem;
+    int use_smem, taps_smem;
     size_t hist_smem;
 };
 
@@ -272,8 +271,8 @@ static soap_status launch_batch_contract(soap_ctx* c, const BatchShape& b, const
     const int grid = std::max(1, std::min(b.n_units, sms * std::max(1, per_sm)));
     SOAP_TIMED(c, SOAP_TIMER_CONTRACT,
                k_batch_contract<PB, R, kBatchThreads><<<grid, kBatchThreads, 0, c->stream>>>(
-                   c->n_px, c->row_len, c->pad, rows, c->b_jobs.as<Job>(), c->b_gstart.as<int>(), b.G,
-                   b.max_jobs, c->b_coefs.as<float>(), b.max_coef, ct, c->b_con.as<float>(), c->b_fq.as<float>(),
+                   c->n_px, rows, c->b_toff.as<long long>(), c->b_gstart.as<int>(), b.G, b.max_taps,
+                   c->b_coefs.as<float>(), ct, c->b_con.as<float>(), c->b_fq.as<float>(),
                    c->b_pblocks.as<PBlockDev>(), c->b_order.as<int>(), b.n_units, b.n_tiles,
                    c->b_ticket.as<unsigned int>(), out);
                SOAP_LAUNCHED(c));
@@ -284,22 +283,25 @@ static soap_status launch_batch_contract(soap_ctx* c, const BatchShape& b, const
 static soap_status enqueue_batch(soap_ctx* c, const BatchShape& b, const ClassTypes& ct,
                                  const ClassConsts& cc, float* out) {
     const int N = c->N;
-    const int q_max_coef = c->n_mu * c->n_taps;
+    const int q_max_taps = c->n_mu * c->n_taps;
     const double scale = std::ldexp(1.0, c->fx_bits);
     const double inv_scale = std::ldexp(1.0, -c->fx_bits);
     // 1 star
-    k_batch_star<<<N, 128, c->n_mu * sizeof(long long), c->stream>>>(
-        N, c->n_mu, c->cell_I, c->cell_bin, scale, c->b_cellIfx.as<long long>(), c->b_IB.as<long long>());
-    SOAP_LAUNCHED(c);
+    SOAP_TIMED(c, SOAP_TIMER_GEOMETRY,
+               k_batch_star<<<N, 128, c->n_mu * sizeof(long long), c->stream>>>(
+                   N, c->n_mu, c->cell_I, c->cell_bin, scale, c->b_cellIfx.as<long long>(), c->b_IB.as<long long>());
+               SOAP_LAUNCHED(c));
     // 2 configurations: column tables, quiet kernels and job tables
     const size_t smem_q = (size_t)c->n_mu * c->n_taps * sizeof(long long);
     SOAP_CUDA(cudaFuncSetAttribute(k_batch_items, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_q));
-    k_batch_items<<<b.n_items, 128, smem_q, c->stream>>>(
-        N, c->n_mu, c->n_taps, c->tap_min, 1.0 / kCKms, 1.0 / c->delta, c->delta, 1.0 / std::expm1(c->delta),
-        c->b_items.as<BatchItemDev>(), c->b_IB.as<long long>(), c->b_colj.as<int>(), c->b_colw.as<unsigned int>(),
-        c->b_kq.as<long long>(), c->b_qjobs.as<Job>(), c->b_qgs.as<int>(), c->b_qc32.as<float>(), q_max_coef,
-        inv_scale, c->flags);
-    SOAP_LAUNCHED(c);
+    SOAP_TIMED(c, SOAP_TIMER_GEOMETRY,
+               k_batch_items<<<b.n_items, 128, smem_q, c->stream>>>(
+                   N, c->n_mu, c->n_taps, c->tap_min, 1.0 / kCKms, 1.0 / c->delta, c->delta,
+                   1.0 / std::expm1(c->delta), c->b_items.as<BatchItemDev>(), c->b_IB.as<long long>(),
+                   c->b_colj.as<int>(), c->b_colw.as<unsigned int>(), c->b_kq.as<long long>(),
+                   c->b_qtoff.as<long long>(), c->b_qgs.as<int>(), c->b_qc32.as<float>(), q_max_taps, inv_scale,
+                   c->row_len, c->pad, c->flags);
+               SOAP_LAUNCHED(c));
     // 3 quiet spectra
     {
         Rows<float> rows;
@@ -308,8 +310,8 @@ static soap_status enqueue_batch(soap_ctx* c, const BatchShape& b, const ClassTy
         dim3 grid((unsigned)((c->n_px + TILE - 1) / TILE), (unsigned)b.n_items);
         SOAP_TIMED(c, SOAP_TIMER_CONTRACT_QUIET,
                    k_batch_quiet<4, 128><<<grid, 128, 0, c->stream>>>(
-                       c->n_px, c->row_len, c->pad, rows, c->b_qjobs.as<Job>(), c->b_qgs.as<int>(), c->n_mu,
-                       c->b_qc32.as<float>(), q_max_coef, c->b_fq.as<float>());
+                       c->n_px, rows, c->b_qtoff.as<long long>(), c->b_qgs.as<int>(), c->b_qc32.as<float>(),
+                       q_max_taps, c->b_fq.as<float>());
                    SOAP_LAUNCHED(c));
     }
     // contrast per class
@@ -324,10 +326,11 @@ static soap_status enqueue_batch(soap_ctx* c, const BatchShape& b, const ClassTy
     // 4 regions
     if (b.max_r > 0) {
         const int64_t nt = (int64_t)b.n_phases * b.max_r;
-        k_batch_regions<<<(unsigned)((nt + 127) / 128), 128, 0, c->stream>>>(
-            N, b.n_phases, b.max_r, c->b_phase_item.as<int>(), c->b_items.as<BatchItemDev>(),
-            c->b_regions.as<RegionDev>(), c->b_phases.as<double>(), c->b_geo.as<RegionGeo>());
-        SOAP_LAUNCHED(c);
+        SOAP_TIMED(c, SOAP_TIMER_REGIONS,
+                   k_batch_regions<<<(unsigned)((nt + 127) / 128), 128, 0, c->stream>>>(
+                       N, b.n_phases, b.max_r, c->b_phase_item.as<int>(), c->b_items.as<BatchItemDev>(),
+                       c->b_regions.as<RegionDev>(), c->b_phases.as<double>(), c->b_geo.as<RegionGeo>());
+                   SOAP_LAUNCHED(c));
     }
     // 5 per-phase kernels + job tables
     if (!b.use_smem)
@@ -340,9 +343,9 @@ static soap_status enqueue_batch(soap_ctx* c, const BatchShape& b, const ClassTy
                    c->b_items.as<BatchItemDev>(), c->b_pblocks.as<PBlockDev>(), c->b_geo.as<RegionGeo>(),
                    c->cell_mu, c->cell_mu32, c->cell_bin, c->b_cellIfx.as<long long>(), c->b_colj.as<int>(),
                    c->b_colw.as<unsigned int>(), c->tap_min, c->n_taps, c->n_mu, b.n_class,
-                   c->b_kfix.as<long long>(), b.use_smem, kVariants[b.variant].PB, inv_scale, c->b_jobs.as<Job>(),
-                   c->b_gstart.as<int>(), c->b_coefs.as<float>(), b.max_jobs, b.max_coef, c->b_counters.as<int>(),
-                   b.jobs_smem, c->flags);
+                   c->b_kfix.as<long long>(), b.use_smem, kVariants[b.variant].PB, inv_scale, c->row_len, c->pad,
+                   c->b_toff.as<long long>(), c->b_gstart.as<int>(), c->b_coefs.as<float>(), b.max_taps,
+                   c->b_counters.as<int>(), b.taps_smem, c->flags);
                SOAP_LAUNCHED(c));
     // 6 persistent contraction
     SOAP_CUDA(cudaMemsetAsync(c->b_ticket.p, 0, sizeof(unsigned int), c->stream));
@@ -373,8 +376,8 @@ void batch_release(soap_ctx* c) {
     c->b_graph_key.clear();
     DevBuf* bufs[] = {&c->b_items, &c->b_regions, &c->b_phases, &c->b_phase_item, &c->b_phase_block,
                       &c->b_pblocks, &c->b_order, &c->b_cellIfx, &c->b_IB, &c->b_colj, &c->b_colw, &c->b_kq,
-                      &c->b_qjobs, &c->b_qgs, &c->b_qc32, &c->b_fq, &c->b_con, &c->b_geo, &c->b_kfix,
-                      &c->b_counters, &c->b_jobs, &c->b_gstart, &c->b_coefs, &c->b_ticket};
+                      &c->b_qtoff, &c->b_qgs, &c->b_qc32, &c->b_fq, &c->b_con, &c->b_geo, &c->b_kfix,
+                      &c->b_counters, &c->b_toff, &c->b_gstart, &c->b_coefs, &c->b_ticket};
     for (DevBuf* b : bufs) release(*b);
 }
 
@@ -468,27 +471,22 @@ soap_status batch_run(soap_ctx* c, const soap_batch_item* items, int n_items, co
     b.max_r = max_r;
     b.n_pblocks = (int)pbl.size();
     b.n_tiles = (int)((c->n_px + kBatchThreads * V.R - 1) / (kBatchThreads * V.R));
-    const int64_t n_units64 = (int64_t)b.n_pblocks * b.n_tiles;
-    if (n_units64 > ((int64_t)1 << 31) - 1) { set_error("batch has too many (phase block, tile) units"); return SOAP_ERANGE; }
-    b.n_units = (int)n_units64;
+    b.n_units = b.n_pblocks;
     b.variant = variant;
     b.n_class = n_class;
     b.G = 1 + n_class;
-    b.max_jobs = b.G * c->n_mu;
-    b.max_coef = b.max_jobs * c->n_taps * V.PB;
+    b.max_taps = b.G * c->n_mu * c->n_taps;
     b.nbk = (int64_t)n_class * c->n_mu * c->n_taps;
     const size_t hist_bytes = (size_t)b.nbk * sizeof(long long);
     const size_t kslice_bytes = (size_t)V.PB * b.nbk * sizeof(long long);
     b.use_smem = hist_bytes <= 96 * 1024;
-    b.jobs_smem = kslice_bytes <= 160 * 1024;
-    b.hist_smem = std::max(b.use_smem ? hist_bytes : (size_t)0, b.jobs_smem ? kslice_bytes : (size_t)0);
-    // units (phase block, tile), largest estimated cost first; a block's tiles stay together
+    b.taps_smem = kslice_bytes <= 160 * 1024;
+    b.hist_smem = std::max(b.use_smem ? hist_bytes : (size_t)0, b.taps_smem ? kslice_bytes : (size_t)0);
+    // units: phase blocks, largest estimated cost first
     std::vector<int> border(b.n_pblocks);
     std::iota(border.begin(), border.end(), 0);
     std::stable_sort(border.begin(), border.end(), [&](int x, int y) { return pcost[x] > pcost[y]; });
-    std::vector<int> order((size_t)b.n_units);
-    for (int q = 0; q < b.n_pblocks; q++)
-        for (int t = 0; t < b.n_tiles; t++) order[(size_t)q * b.n_tiles + t] = border[q] * b.n_tiles + t;
+    const std::vector<int>& order = border;
     // device buffers (grow-only)
     const int N = c->N;
     const int ncl = std::max(1, n_class);
@@ -504,7 +502,7 @@ soap_status batch_run(soap_ctx* c, const soap_batch_item* items, int n_items, co
     SOAP_TRY(ensure(c->b_colj, (size_t)n_items * N * sizeof(int)));
     SOAP_TRY(ensure(c->b_colw, (size_t)n_items * N * sizeof(unsigned int)));
     SOAP_TRY(ensure(c->b_kq, (size_t)n_items * c->n_mu * c->n_taps * sizeof(long long)));
-    SOAP_TRY(ensure(c->b_qjobs, (size_t)n_items * c->n_mu * sizeof(Job)));
+    SOAP_TRY(ensure(c->b_qtoff, (size_t)n_items * c->n_mu * c->n_taps * sizeof(long long)));
     SOAP_TRY(ensure(c->b_qgs, (size_t)n_items * 2 * sizeof(int)));
     SOAP_TRY(ensure(c->b_qc32, (size_t)n_items * c->n_mu * c->n_taps * sizeof(float)));
     SOAP_TRY(ensure(c->b_fq, (size_t)n_items * c->n_px * sizeof(float)));
@@ -512,9 +510,9 @@ soap_status batch_run(soap_ctx* c, const soap_batch_item* items, int n_items, co
     SOAP_TRY(ensure(c->b_geo, (size_t)n_phases * std::max(1, max_r) * sizeof(RegionGeo)));
     SOAP_TRY(ensure(c->b_kfix, (size_t)n_phases * std::max<int64_t>(1, b.nbk) * sizeof(long long)));
     SOAP_TRY(ensure(c->b_counters, (size_t)b.n_pblocks * sizeof(int)));
-    SOAP_TRY(ensure(c->b_jobs, (size_t)b.n_pblocks * b.max_jobs * sizeof(Job)));
+    SOAP_TRY(ensure(c->b_toff, (size_t)b.n_pblocks * b.max_taps * sizeof(long long)));
     SOAP_TRY(ensure(c->b_gstart, (size_t)b.n_pblocks * (b.G + 1) * sizeof(int)));
-    SOAP_TRY(ensure(c->b_coefs, (size_t)b.n_pblocks * b.max_coef * sizeof(float)));
+    SOAP_TRY(ensure(c->b_coefs, (size_t)b.n_pblocks * b.max_taps * V.PB * sizeof(float)));
     SOAP_TRY(ensure(c->b_ticket, sizeof(unsigned int)));
     // inputs (pageable copies: the call returns after the driver has staged them)
     SOAP_CUDA(cudaMemcpyAsync(c->b_items.p, it.data(), (size_t)n_items * sizeof(BatchItemDev), cudaMemcpyHostToDevice, c->stream));
@@ -540,7 +538,7 @@ soap_status batch_run(soap_ctx* c, const soap_batch_item* items, int n_items, co
     auto putd = [&](double v) { uint64_t u; memcpy(&u, &v, 8); key.push_back(u); };
     auto putp = [&](const void* p) { key.push_back((uint64_t)(uintptr_t)p); };
     put(b.n_items); put(b.n_phases); put(b.max_r); put(b.n_pblocks); put(b.n_units); put(b.n_tiles);
-    put(b.variant); put(b.n_class); put(b.use_smem); put(b.jobs_smem); put(b.hist_smem);
+    put(b.variant); put(b.n_class); put(b.use_smem); put(b.taps_smem); put(b.hist_smem);
     put(N); put(c->n_mu); put(c->n_taps); put((uint64_t)c->tap_min); put(c->fx_bits);
     put(c->n_px); put(c->row_len); put(c->pad);
     putd(c->delta); putd(c->lam_s); putd(c->t_quiet);
@@ -549,8 +547,8 @@ soap_status batch_run(soap_ctx* c, const soap_batch_item* items, int n_items, co
     putp(c->cell_bin); putp(c->cell_mu); putp(c->cell_mu32); putp(c->flags);
     const DevBuf* bufs[] = {&c->b_items, &c->b_regions, &c->b_phases, &c->b_phase_item, &c->b_phase_block,
                             &c->b_pblocks, &c->b_order, &c->b_cellIfx, &c->b_IB, &c->b_colj, &c->b_colw, &c->b_kq,
-                            &c->b_qjobs, &c->b_qgs, &c->b_qc32, &c->b_fq, &c->b_con, &c->b_geo, &c->b_kfix,
-                            &c->b_counters, &c->b_jobs, &c->b_gstart, &c->b_coefs, &c->b_ticket};
+                            &c->b_qtoff, &c->b_qgs, &c->b_qc32, &c->b_fq, &c->b_con, &c->b_geo, &c->b_kfix,
+                            &c->b_counters, &c->b_toff, &c->b_gstart, &c->b_coefs, &c->b_ticket};
     for (const DevBuf* q : bufs) putp(q->p);
     if (!c->b_graph_exec || c->b_graph_key != key) {
         if (c->b_graph_exec) { cudaGraphExecDestroy(c->b_graph_exec); c->b_graph_exec = nullptr; }

@@ -11,9 +11,9 @@
 // where "*" is the banded convolution (K * S)[m] = sum_k K[k] S[m-k] over the kernel's taps
 // and C_cl(lambda) = B(lambda, T_cl) / B(lambda, T_quiet) multiplies on the common grid.
 //
-// A "job" is one (group, mu bin) pair with the union of its non-zero taps over a block of
-// PB consecutive phases; the contraction kernel reads the row of that bin once per tap and
-// reuses it for all PB phases.
+// A tap table lists, per (group, mu bin), the range of taps with non-zero kernel values in a
+// block of PB consecutive phases; the contraction kernel reads the shifted row of each tap once
+// and uses it for all PB phases.
 #include <cmath>
 #include <vector>
 
@@ -67,9 +67,9 @@ __global__ void k_phase_hist(int N, int n_regions, const RegionGeo* __restrict__
                              const int32_t* __restrict__ cell_j, const int32_t* __restrict__ cell_bin,
                              const long long* __restrict__ cell_k0, const long long* __restrict__ cell_k1,
                              int tap_min, int n_taps, int n_mu, int n_class, long long* kout,
-                             int use_smem, int PB, double inv_scale, Job* jobs, int* gstart,
-                             double* c64, float* c32, int max_jobs, int max_coef, int* counters,
-                             int jobs_smem, unsigned int* flags) {
+                             int use_smem, int PB, double inv_scale, int64_t row_len, int64_t pad,
+                             long long* toff, int* gstart, double* c64, float* c32, int max_taps,
+                             int* counters, int taps_smem, unsigned int* flags) {
     __shared__ RegionGeo sg[SOAP_MAX_REGIONS];
     extern __shared__ long long hist_sm[];
     const int p = blockIdx.x;
@@ -107,7 +107,7 @@ __global__ void k_phase_hist(int N, int n_regions, const RegionGeo* __restrict__
         for (int t = threadIdx.x; t < nb; t += blockDim.x)
             if (hist[t]) atomicAdd((unsigned long long*)&gdst[t], (unsigned long long)hist[t]);
     }
-    // The last block to finish among those feeding a phase block builds its job table
+    // The last block to finish among those feeding a phase block builds its tap table
     // (counter ticket after a memory fence: every other block's sums are visible by then).
     __shared__ int s_last;
     __threadfence();
@@ -121,8 +121,8 @@ __global__ void k_phase_hist(int N, int n_regions, const RegionGeo* __restrict__
     __syncthreads();
     if (s_last) {
         __threadfence();
-        build_jobs_dev(kout, pbk, (int)gridDim.x, n_class, n_mu, n_taps, tap_min, PB, 1, inv_scale, jobs,
-                       gstart, c64, c32, max_jobs, max_coef, jobs_smem ? hist_sm : nullptr, flags);
+        build_taps_dev(kout, pbk, (int)gridDim.x, n_class, n_mu, n_taps, tap_min, PB, 1, inv_scale, row_len,
+                       pad, toff, gstart, c64, c32, max_taps, taps_smem ? hist_sm : nullptr, flags);
     }
 }
 
@@ -132,16 +132,15 @@ __global__ void k_phase_hist(int N, int n_regions, const RegionGeo* __restrict__
 // One block: pixel tile blockIdx.x of phase block blockIdx.y, effect blockIdx.z.
 template <typename T, int PB, int R, int THREADS>
 __global__ void __launch_bounds__(THREADS)
-k_contract(int64_t n_px, int64_t row_len, int64_t pad, Rows<T> rows, const Job* __restrict__ jobs,
-           const int* __restrict__ gstart, int G, int max_jobs, const T* __restrict__ coefs,
-           int max_coef, ClassTypes ctype, const T* __restrict__ contrast,
+k_contract(int64_t n_px, Rows<T> rows, const long long* __restrict__ toff, const int* __restrict__ gstart,
+           int G, int max_taps, const T* __restrict__ coefs, ClassTypes ctype, const T* __restrict__ contrast,
            const T* __restrict__ fq, int n_phases, EffectList effs, T* __restrict__ out) {
     const int pb = blockIdx.y;
     const int np = min(PB, n_phases - pb * PB);
     T* out_rows = out + (int64_t)blockIdx.z * n_phases * n_px + (int64_t)pb * PB * n_px;
-    contract_tile<T, PB, R, THREADS>(n_px, row_len, pad, rows, jobs + (int64_t)pb * max_jobs,
-                                     gstart + (int64_t)pb * (G + 1), G, coefs + (int64_t)pb * max_coef,
-                                     ctype, contrast, fq, effs.e[blockIdx.z], blockIdx.x, np, out_rows);
+    contract_tile<T, PB, R, THREADS>(n_px, rows, toff + (int64_t)pb * max_taps, gstart + (int64_t)pb * (G + 1), G,
+                                     coefs + (int64_t)pb * max_taps * PB, ctype, contrast, fq,
+                                     effs.e[blockIdx.z], blockIdx.x, np, out_rows);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -153,8 +152,8 @@ static int grid_cap(int64_t n, int threads, int cap) {
 }
 
 template <typename T, int PB, int R, int THREADS>
-static soap_status launch_contract(soap_ctx* c, int n_blocks, int G, int max_jobs, int max_coef,
-                                   const Job* jobs, const int* gstart, const T* coefs,
+static soap_status launch_contract(soap_ctx* c, int n_blocks, int G, int max_taps,
+                                   const long long* toff, const int* gstart, const T* coefs,
                                    const ClassTypes& ct, const T* contrast, const T* fq,
                                    int n_phases, const EffectList& el, int n_eff, T* out,
                                    const T* q, const T* a0, const T* a1) {
@@ -164,8 +163,7 @@ static soap_status launch_contract(soap_ctx* c, int n_blocks, int G, int max_job
     dim3 grid((unsigned)tiles, (unsigned)n_blocks, (unsigned)n_eff);
     SOAP_TIMED(c, fq ? SOAP_TIMER_CONTRACT : SOAP_TIMER_CONTRACT_QUIET,
                k_contract<T, PB, R, THREADS><<<grid, THREADS, 0, c->stream>>>(
-                   c->n_px, c->row_len, c->pad, rows, jobs, gstart, G, max_jobs, coefs, max_coef, ct,
-                   contrast, fq, n_phases, el, out);
+                   c->n_px, rows, toff, gstart, G, max_taps, coefs, ct, contrast, fq, n_phases, el, out);
                SOAP_LAUNCHED(c));
     return SOAP_OK;
 }
@@ -174,22 +172,20 @@ static soap_status launch_contract(soap_ctx* c, int n_blocks, int G, int max_job
 constexpr int kPB64 = 4, kR64 = 2, kT64 = 128;
 constexpr int kPB32 = 8, kR32 = 4, kT32 = 128;
 
-// job + coefficient scratch for a kernel set kfix with n_phases "phases" in blocks of PB
-static soap_status job_buffers(soap_ctx* c, int n_phases, int n_class, int PB, int mode, Job** jobs,
-                               int** gstart, double** c64, float** c32, int* n_blocks, int* G,
-                               int* max_jobs, int* max_coef) {
+// tap-table + coefficient scratch for a kernel set kfix with n_phases "phases" in blocks of PB
+static soap_status tap_buffers(soap_ctx* c, int n_phases, int n_class, int PB, int mode, long long** toff,
+                               int** gstart, double** c64, float** c32, int* n_blocks, int* G, int* max_taps) {
     *G = mode == 0 ? 1 : 1 + n_class;
     *n_blocks = (n_phases + PB - 1) / PB;
-    *max_jobs = *G * c->n_mu;
-    *max_coef = *max_jobs * c->n_taps * PB;
-    size_t jb = (size_t)*n_blocks * *max_jobs * sizeof(Job);
+    *max_taps = *G * c->n_mu * c->n_taps;
+    size_t tb = (size_t)*n_blocks * *max_taps * sizeof(long long);
     size_t gb = (size_t)*n_blocks * (*G + 1) * sizeof(int);
-    size_t off_g = (jb + 255) / 256 * 256;
+    size_t off_g = (tb + 255) / 256 * 256;
     SOAP_TRY(ensure(c->jobs, off_g + gb));
-    size_t cb64 = (size_t)*n_blocks * *max_coef * sizeof(double);
+    size_t cb64 = (size_t)*n_blocks * *max_taps * PB * sizeof(double);
     size_t off32 = (cb64 + 255) / 256 * 256;
-    SOAP_TRY(ensure(c->coefs, off32 + (size_t)*n_blocks * *max_coef * sizeof(float)));
-    *jobs = c->jobs.as<Job>();
+    SOAP_TRY(ensure(c->coefs, off32 + (size_t)*n_blocks * *max_taps * PB * sizeof(float)));
+    *toff = c->jobs.as<long long>();
     *gstart = (int*)(c->jobs.as<char>() + off_g);
     *c64 = c->coefs.as<double>();
     *c32 = (float*)(c->coefs.as<char>() + off32);
@@ -197,18 +193,14 @@ static soap_status job_buffers(soap_ctx* c, int n_phases, int n_class, int PB, i
 }
 
 soap_status toeplitz_quiet(soap_ctx* c, int precision, void* dst) {
-    // job table built by the geometry kernel
-    Job* jobs = c->qjobs;
-    int* gstart = reinterpret_cast<int*>(c->qjobs + c->n_mu);
-    double* c64 = c->qc64;
-    float* c32 = c->qc32;
-    const int nbk = 1, G = 1, mj = c->n_mu, mc = c->n_mu * SOAP_MAX_TAPS;
+    // tap table built by the geometry kernel
+    const int nbk = 1, G = 1, mt = c->n_mu * SOAP_MAX_TAPS;
     ClassTypes ct{};
     EffectList el{{SOAP_EFFECT_TOT, 0, 0}};
     if (precision == SOAP_FP64)
-        return launch_contract<double, 1, 1, 128>(c, nbk, G, mj, mc, jobs, gstart, c64, ct, nullptr,
+        return launch_contract<double, 1, 1, 128>(c, nbk, G, mt, c->qtoff, c->qgstart, c->qc64, ct, nullptr,
                                                  nullptr, 1, el, 1, (double*)dst, c->q64, nullptr, nullptr);
-    return launch_contract<float, 1, 1, 128>(c, nbk, G, mj, mc, jobs, gstart, c32, ct, nullptr,
+    return launch_contract<float, 1, 1, 128>(c, nbk, G, mt, c->qtoff, c->qgstart, c->qc32, ct, nullptr,
                                             nullptr, 1, el, 1, (float*)dst, c->q32, nullptr, nullptr);
 }
 
@@ -261,17 +253,17 @@ soap_status toeplitz_active(soap_ctx* c, const RegionDev* regions_host, int n_re
     size_t kbytes = (size_t)n_phases * nb * sizeof(long long);
     SOAP_TRY(ensure(c->kphase, kbytes));
     long long* kfix = c->kphase.as<long long>();
-    // job tables are built by the last block of each phase block (fused into k_phase_hist)
+    // tap tables are built by the last block of each phase block (fused into k_phase_hist)
     const int PB = f64 ? kPB64 : kPB32;
-    Job* jobs; int* gstart; double* c64; float* c32; int nbk, G, mj, mc;
-    SOAP_TRY(job_buffers(c, n_phases, ncl, PB, 1, &jobs, &gstart, &c64, &c32, &nbk, &G, &mj, &mc));
+    long long* toff; int* gstart; double* c64; float* c32; int nbk, G, mt;
+    SOAP_TRY(tap_buffers(c, n_phases, ncl, PB, 1, &toff, &gstart, &c64, &c32, &nbk, &G, &mt));
     SOAP_TRY(ensure(c->job_counters, (size_t)nbk * sizeof(int)));
     SOAP_CUDA(cudaMemsetAsync(c->job_counters.p, 0, (size_t)nbk * sizeof(int), c->stream));
     const size_t hist_bytes = (size_t)nb * sizeof(long long);
     const size_t kslice_bytes = (size_t)PB * nb * sizeof(long long);
     const int use_smem = hist_bytes <= 160 * 1024;
-    const int jobs_smem = kslice_bytes <= 96 * 1024;
-    size_t smem = std::max(use_smem ? hist_bytes : (size_t)0, jobs_smem ? kslice_bytes : (size_t)0);
+    const int taps_smem = kslice_bytes <= 96 * 1024;
+    size_t smem = std::max(use_smem ? hist_bytes : (size_t)0, taps_smem ? kslice_bytes : (size_t)0);
     SOAP_CUDA(cudaMemsetAsync(kfix, 0, kbytes, c->stream));
     if (smem > 48 * 1024)
         SOAP_CUDA(cudaFuncSetAttribute(k_phase_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -279,10 +271,11 @@ soap_status toeplitz_active(soap_ctx* c, const RegionDev* regions_host, int n_re
     SOAP_TRY(ensure(c->region_geo, (size_t)n_phases * (n_regions > 0 ? n_regions : 1) * sizeof(RegionGeo)));
     if (n_regions > 0) {
         const int nt = n_phases * n_regions;
-        k_region_geo<<<(nt + 127) / 128, 128, 0, c->stream>>>(
-            c->N, n_regions, n_phases, c->regions.as<RegionDev>(), c->phases.as<double>(), c->incl_deg,
-            c->alpha, c->region_geo.as<RegionGeo>());
-        SOAP_LAUNCHED(c);
+        SOAP_TIMED(c, SOAP_TIMER_REGIONS,
+                   k_region_geo<<<(nt + 127) / 128, 128, 0, c->stream>>>(
+                       c->N, n_regions, n_phases, c->regions.as<RegionDev>(), c->phases.as<double>(), c->incl_deg,
+                       c->alpha, c->region_geo.as<RegionGeo>());
+                   SOAP_LAUNCHED(c));
     }
     // split each phase over several blocks so that all SMs take part
     const int n_split = (int)std::max<int64_t>(1, std::min<int64_t>(8, (4 * 152 + n_phases - 1) / n_phases));
@@ -291,8 +284,8 @@ soap_status toeplitz_active(soap_ctx* c, const RegionDev* regions_host, int n_re
                k_phase_hist<<<hgrid, 256, smem, c->stream>>>(
                    c->N, n_regions, c->region_geo.as<RegionGeo>(), c->cell_mu, c->cell_mu32, c->cell_j,
                    c->cell_bin, c->cell_k0, c->cell_k1, c->tap_min, c->n_taps, c->n_mu, ncl, kfix,
-                   use_smem, PB, std::ldexp(1.0, -c->fx_bits), jobs, gstart, c64, c32, mj, mc,
-                   c->job_counters.as<int>(), jobs_smem, c->flags);
+                   use_smem, PB, std::ldexp(1.0, -c->fx_bits), c->row_len, c->pad, toff, gstart, c64, c32,
+                   mt, c->job_counters.as<int>(), taps_smem, c->flags);
                SOAP_LAUNCHED(c));
     ClassTypes ct{};
     for (int k = 0; k < n_class; k++) ct.t[k] = class_type[k];
@@ -306,10 +299,10 @@ soap_status toeplitz_active(soap_ctx* c, const RegionDev* regions_host, int n_re
     const float* a32s = c->active_set[0] ? c->a32[0] : c->a32[1];
     const float* a32f = c->active_set[1] ? c->a32[1] : c->a32[0];
     if (f64)
-        return launch_contract<double, kPB64, kR64, kT64>(c, nbk, G, mj, mc, jobs, gstart, c64, ct, con64,
+        return launch_contract<double, kPB64, kR64, kT64>(c, nbk, G, mt, toff, gstart, c64, ct, con64,
                                                          c->fq.as<double>(), n_phases, el, n_eff,
                                                          (double*)dst, c->q64, a64s, a64f);
-    return launch_contract<float, kPB32, kR32, kT32>(c, nbk, G, mj, mc, jobs, gstart, c32, ct, con32,
+    return launch_contract<float, kPB32, kR32, kT32>(c, nbk, G, mt, toff, gstart, c32, ct, con32,
                                                     c->fq.as<float>(), n_phases, el, n_eff,
                                                     (float*)dst, c->q32, a32s, a32f);
 }

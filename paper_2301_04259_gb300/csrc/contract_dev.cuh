@@ -3,9 +3,9 @@
 //
 // contract_tile() computes one pixel tile of one block of PB phases:
 //   out[p][m] = F_q[m] - sum_b Q_p,b * S_q,b [m] + sum_cl C_cl[m] sum_b K_p,cl,b * S_a(cl),b [m]
-// (Eqs. 1-4 for the effect `eff`), from a job table (group, mu bin, tap range, coefficients
-// [tap][PB]).  One thread owns R pixels m = m0 + threadIdx.x + r*THREADS; acc holds F_q - group 0
-// + folded class terms, tmp one class before its fold.
+// (Eqs. 1-4 for the effect `eff`), from a tap table (group starts, per-tap row offsets,
+// coefficients [tap][PB]).  One thread owns R pixels m = m0 + threadIdx.x + r*THREADS; acc
+// holds F_q - group 0 + folded class terms, tmp one class before its fold.
 #pragma once
 
 #include "soap_internal.cuh"
@@ -49,41 +49,39 @@ __device__ __forceinline__ void load_coefs(const T* __restrict__ src, T (&cv)[PB
 }
 
 template <typename T, int PB, int R, int THREADS>
-__device__ __forceinline__ void contract_tile(int64_t n_px, int64_t row_len, int64_t pad,
-                                              const Rows<T>& rows, const Job* __restrict__ jb,
-                                              const int* __restrict__ gs, int G,
-                                              const T* __restrict__ cb, const ClassTypes& ctype,
-                                              const T* __restrict__ contrast,
-                                              const T* __restrict__ fq, int eff, int64_t tile,
-                                              int np, T* __restrict__ out_rows) {
-    const int64_t mbase = tile * THREADS * R + threadIdx.x;
-    int64_t mc[R];
+__device__ __forceinline__ void contract_tile(int64_t n_px, const Rows<T>& rows, const long long* __restrict__ toff,
+                                              const int* __restrict__ gs, int G, const T* __restrict__ cb,
+                                              const ClassTypes& ctype, const T* __restrict__ contrast,
+                                              const T* __restrict__ fq, int eff, int64_t tile, int np,
+                                              T* __restrict__ out_rows) {
+    // Rows are padded past round_up(n_px, 1024) + max tap, so every tap of every pixel of the
+    // last tile reads inside its row; only the per-pixel inputs below need a clamped index.
+    const int64_t m0 = tile * THREADS * R + threadIdx.x;
+    int64_t mcl[R];
 #pragma unroll
     for (int r = 0; r < R; r++) {
-        int64_t m = mbase + (int64_t)r * THREADS;
-        mc[r] = pad + (m < n_px ? m : n_px - 1);
+        const int64_t m = m0 + (int64_t)r * THREADS;
+        mcl[r] = m < n_px ? m : n_px - 1;
     }
     T acc[PB][R];
 #pragma unroll
     for (int r = 0; r < R; r++) {
-        T f0 = fq ? fq[mc[r] - pad] : T(0);
+        const T f0 = fq ? fq[mcl[r]] : T(0);
 #pragma unroll
         for (int p = 0; p < PB; p++) acc[p][r] = f0;
     }
-
     // group 0: subtract (active star) or add (quiet star) the quiet-row convolutions
-    for (int jj = gs[0]; jj < gs[1]; jj++) {
-        const Job J = jb[jj];
-        const T* row = rows.q + (int64_t)J.bin * row_len;
-        const T* cf = cb + J.coef_off;
+    {
+        const T* base = rows.q + m0;
+        const int t1 = gs[1];
 #pragma unroll 4
-        for (int kk = 0; kk < J.n_k; kk++) {
-            const int64_t k = J.k_lo + kk;
+        for (int t = gs[0]; t < t1; t++) {
+            const T* row = base + __ldg(toff + t);
             T s[R];
 #pragma unroll
-            for (int r = 0; r < R; r++) s[r] = __ldg(row + mc[r] - k);
+            for (int r = 0; r < R; r++) s[r] = __ldg(row + r * THREADS);
             T cv[PB];
-            load_coefs<T, PB>(cf + kk * PB, cv);
+            load_coefs<T, PB>(cb + (int64_t)t * PB, cv);
 #pragma unroll
             for (int p = 0; p < PB; p++)
 #pragma unroll
@@ -92,35 +90,31 @@ __device__ __forceinline__ void contract_tile(int64_t n_px, int64_t row_len, int
     }
     // classes: tmp = sum_b K_cl,b * S, then acc += C_cl . tmp (TOT, FLUX) or tmp (BCONV)
     for (int g = 1; g < G; g++) {
-        if (gs[g] == gs[g + 1]) continue;
+        const int t0 = gs[g], t1 = gs[g + 1];
+        if (t0 == t1) continue;
         const int cl = g - 1;
-        const T* base = eff == SOAP_EFFECT_FLUX ? rows.q : rows.a[ctype.t[cl] == SOAP_FACULA ? 1 : 0];
+        const T* base = (eff == SOAP_EFFECT_FLUX ? rows.q : rows.a[ctype.t[cl] == SOAP_FACULA ? 1 : 0]) + m0;
         T tmp[PB][R];
 #pragma unroll
         for (int p = 0; p < PB; p++)
 #pragma unroll
             for (int r = 0; r < R; r++) tmp[p][r] = T(0);
-        for (int jj = gs[g]; jj < gs[g + 1]; jj++) {
-            const Job J = jb[jj];
-            const T* row = base + (int64_t)J.bin * row_len;
-            const T* cf = cb + J.coef_off;
 #pragma unroll 4
-            for (int kk = 0; kk < J.n_k; kk++) {
-                const int64_t k = J.k_lo + kk;
-                T s[R];
+        for (int t = t0; t < t1; t++) {
+            const T* row = base + __ldg(toff + t);
+            T s[R];
 #pragma unroll
-                for (int r = 0; r < R; r++) s[r] = __ldg(row + mc[r] - k);
-                T cv[PB];
-                load_coefs<T, PB>(cf + kk * PB, cv);
+            for (int r = 0; r < R; r++) s[r] = __ldg(row + r * THREADS);
+            T cv[PB];
+            load_coefs<T, PB>(cb + (int64_t)t * PB, cv);
 #pragma unroll
-                for (int p = 0; p < PB; p++)
+            for (int p = 0; p < PB; p++)
 #pragma unroll
-                    for (int r = 0; r < R; r++) tmp[p][r] = fma(cv[p], s[r], tmp[p][r]);
-            }
+                for (int r = 0; r < R; r++) tmp[p][r] = fma(cv[p], s[r], tmp[p][r]);
         }
 #pragma unroll
         for (int r = 0; r < R; r++) {
-            const T cr = eff == SOAP_EFFECT_BCONV ? T(1) : contrast[(int64_t)cl * n_px + (mc[r] - pad)];
+            const T cr = eff == SOAP_EFFECT_BCONV ? T(1) : contrast[(int64_t)cl * n_px + mcl[r]];
 #pragma unroll
             for (int p = 0; p < PB; p++) acc[p][r] = fma(cr, tmp[p][r], acc[p][r]);
         }
@@ -131,7 +125,7 @@ __device__ __forceinline__ void contract_tile(int64_t n_px, int64_t row_len, int
         if (p >= np) break;
 #pragma unroll
         for (int r = 0; r < R; r++) {
-            const int64_t m = mbase + (int64_t)r * THREADS;
+            const int64_t m = m0 + (int64_t)r * THREADS;
             if (m < n_px) out_rows[(int64_t)p * n_px + m] = acc[p][r];
         }
     }

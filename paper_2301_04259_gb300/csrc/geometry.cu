@@ -56,8 +56,8 @@ k_geometry(int N, double vsini, double sin_i, double cos_i, double alpha, double
            MuTable mus, int mu_sorted, int tap_min, int tap_max, int n_taps, double scale,
            double* cell_I, double* cell_w, double* cell_mu, float* cell_mu32, int32_t* cell_j,
            int32_t* cell_bin, long long* cell_k0, long long* cell_k1, long long* kq_fixed,
-           long long* sum2, Job* qjobs, int* qgstart, double* qc64, float* qc32, int q_max_coef,
-           int* counter, unsigned int* flags) {
+           long long* sum2, long long* qtoff, int* qgstart, double* qc64, float* qc32, int q_max_taps,
+           int64_t row_len, int64_t pad, int* counter, unsigned int* flags) {
     extern __shared__ long long hist[];                  // [n_mu][n_taps]
     __shared__ double sy;
     const int nb = n_mu * n_taps;
@@ -115,7 +115,7 @@ k_geometry(int N, double vsini, double sin_i, double cos_i, double alpha, double
     __syncthreads();
     for (int t = threadIdx.x; t < nb; t += blockDim.x)
         if (hist[t]) atomicAdd((unsigned long long*)&kq_fixed[t], (unsigned long long)hist[t]);
-    // the last block to finish builds the quiet job table (one "phase", one group)
+    // the last block to finish builds the quiet tap table (one "phase", one group)
     __shared__ int s_last;
     __threadfence();
     __syncthreads();
@@ -126,8 +126,8 @@ k_geometry(int N, double vsini, double sin_i, double cos_i, double alpha, double
     __syncthreads();
     if (s_last) {
         __threadfence();
-        build_jobs_dev(kq_fixed, 0, 1, 1, n_mu, n_taps, tap_min, 1, 0, 1.0 / scale, qjobs, qgstart, qc64,
-                       qc32, n_mu, q_max_coef, hist, flags);
+        build_taps_dev(kq_fixed, 0, 1, 1, n_mu, n_taps, tap_min, 1, 0, 1.0 / scale, row_len, pad, qtoff,
+                       qgstart, qc64, qc32, q_max_taps, hist, flags);
     }
 }
 
@@ -184,9 +184,8 @@ soap_status geometry_init(soap_ctx* c) {
         c->N, c->vsini, std::sin(incl), std::cos(incl), c->alpha, c->u1, c->u2, 1.0 / kCKms,
         1.0 / c->delta, c->delta, 1.0 / std::expm1(c->delta), c->n_mu, mus, c->mu_sorted, c->tap_min,
         tap_max, c->n_taps, scale, c->cell_I, c->cell_w, c->cell_mu, c->cell_mu32, c->cell_j,
-        c->cell_bin, c->cell_k0, c->cell_k1, c->kq_fixed, c->sum_I_fixed, c->qjobs,
-        reinterpret_cast<int*>(c->qjobs + c->n_mu), c->qc64, c->qc32, c->n_mu * SOAP_MAX_TAPS,
-        c->geo_counter, c->flags);
+        c->cell_bin, c->cell_k0, c->cell_k1, c->kq_fixed, c->sum_I_fixed, c->qtoff, c->qgstart, c->qc64,
+        c->qc32, c->n_mu * SOAP_MAX_TAPS, c->row_len, c->pad, c->geo_counter, c->flags);
     SOAP_LAUNCHED(c);
     if (c->profiling) timer_end(c, SOAP_TIMER_GEOMETRY, tb);
     return SOAP_OK;

@@ -84,10 +84,8 @@ void release_host(HostBuf& b);
 enum DeviceFlag : unsigned int {
     kFlagTapRange = 1u,        // a cell's tap fell outside the precomputed kernel range
     kFlagBoxRange = 2u,        // a region box index left the grid
-    kFlagJobOverflow = 4u      // a job table would overflow its capacity
+    kFlagJobOverflow = 4u      // a tap table would overflow its capacity
 };
-
-struct Job;
 
 }  // namespace soap
 
@@ -134,8 +132,9 @@ struct soap_ctx {
     // quiet velocity kernels, fixed point [n_mu][n_taps]
     long long* kq_fixed = nullptr;
     long long* sum_I_fixed = nullptr;   // [0] sum of I (fixed point), [1] visible cells
-    // quiet job table, rebuilt with the geometry: jobs [n_mu] then 2 group starts; coefficients
-    soap::Job* qjobs = nullptr;
+    // quiet tap table, rebuilt with the geometry: row offsets, group starts, coefficients
+    long long* qtoff = nullptr;     // [n_mu * SOAP_MAX_TAPS]
+    int* qgstart = nullptr;         // [2]
     double* qc64 = nullptr;
     float* qc32 = nullptr;
     int* geo_counter = nullptr;
@@ -145,9 +144,9 @@ struct soap_ctx {
     soap::DevBuf fq;            // quiet spectrum (fp64 or fp32) for Eq. 4
     soap::DevBuf contrast;      // [n_class][n_px] fp64 + fp32
     soap::DevBuf kphase;        // fixed-point kernels [n_phases][n_class][n_mu][n_taps]
-    soap::DevBuf jobs;          // job tables
-    soap::DevBuf coefs;         // job coefficients (fp64 and fp32)
-    soap::DevBuf job_counters;  // per phase block: blocks done (fused job tables)
+    soap::DevBuf jobs;          // tap tables (row offsets + group starts)
+    soap::DevBuf coefs;         // tap coefficients (fp64 and fp32)
+    soap::DevBuf job_counters;  // per phase block: blocks done (fused tap tables)
     soap::DevBuf regions;       // region parameters
     soap::DevBuf region_geo;    // region centres and boxes per (phase, region)
     soap::DevBuf phases;
@@ -160,8 +159,8 @@ struct soap_ctx {
 
     // batched form: grow-only buffers, the captured graph and the key of what it baked in
     soap::DevBuf b_items, b_regions, b_phases, b_phase_item, b_phase_block, b_pblocks, b_order;
-    soap::DevBuf b_cellIfx, b_IB, b_colj, b_colw, b_kq, b_qjobs, b_qgs, b_qc32, b_fq, b_con;
-    soap::DevBuf b_geo, b_kfix, b_counters, b_jobs, b_gstart, b_coefs, b_ticket;
+    soap::DevBuf b_cellIfx, b_IB, b_colj, b_colw, b_kq, b_qtoff, b_qgs, b_qc32, b_fq, b_con;
+    soap::DevBuf b_geo, b_kfix, b_counters, b_toff, b_gstart, b_coefs, b_ticket;
     cudaGraphExec_t b_graph_exec = nullptr;
     std::vector<uint64_t> b_graph_key;
     uint64_t b_graph_kernels = 0;
@@ -220,7 +219,7 @@ soap_status rv_ccf_run(soap_ctx* c, const void* spectra_dev, int f32, int n_spec
 }  // namespace soap
 
 // ---------------------------------------------------------------------------------------
-// job tables of the Toeplitz contraction (shared by geometry.cu and contract.cu)
+// tap tables of the Toeplitz contraction (shared by geometry.cu, contract.cu and batch.cu)
 // ---------------------------------------------------------------------------------------
 namespace soap {
 
@@ -237,30 +236,31 @@ __device__ __forceinline__ double expm1_small(double e) {
 }
 
 
-struct Job {
-    int32_t group;     // 0: all active cells (quiet rows, negative), g >= 1: class g-1
-    int32_t bin;       // mu bin
-    int32_t k_lo;      // first tap offset (pixels)
-    int32_t n_k;       // number of taps
-    int32_t coef_off;  // offset of coefficients [n_k][PB] within the block's coefficient slab
-    int32_t pad0, pad1, pad2;
-};
-
 // ---------------------------------------------------------------------------------------
-// job tables
+// tap tables of the Toeplitz contraction
 // ---------------------------------------------------------------------------------------
+// A tap table lists, for one block of PB consecutive phases and each (group, mu bin), the taps k
+// from the lowest to the highest with a non-zero kernel value in any of those phases, ordered by
+// group, then bin, then k:
+//   gstart[G+1]   first tap of each group (group 0: quiet rows; group g >= 1: class g-1)
+//   toff[tap]     element offset bin * row_len + pad - k: the row value S_b[m - k] of pixel m
+//                 is rows[toff + m]
+//   coef[tap][PB] kernel value of each phase of the block (0 where a phase has none)
 // kfix: [n_phases][n_class][n_mu][n_taps].  mode 0 (quiet): one group, +K of class 0.
 // mode 1 (active): group 0 = -sum_cl K (quiet rows), group g = +K of class g-1.
-// Block pb covers phases pb*PB .. pb*PB+PB-1.  Outputs per block: jobs[max_jobs],
-// gstart[G+1] (job index where each group starts), coefficients [..][n_k][PB] in c64/c32.
-__device__ __forceinline__ void build_jobs_dev(const long long* __restrict__ kfix, int pb, int n_phases, int n_class,
-                               int n_mu, int n_taps, int tap_min, int PB, int mode, double inv_scale,
-                               Job* jobs, int* gstart, double* c64, float* c32, int max_jobs,
-                               int max_coef, long long* s_k, unsigned int* flags) {
+// Block pb covers phases pb*PB .. pb*PB+PB-1; its outputs start at toff + pb*max_taps,
+// gstart + pb*(G+1) and coef + pb*max_taps*PB.  A table that would exceed max_taps is left
+// empty and flags kFlagJobOverflow.
+__device__ __forceinline__ void build_taps_dev(const long long* __restrict__ kfix, int pb, int n_phases,
+                                               int n_class, int n_mu, int n_taps, int tap_min, int PB, int mode,
+                                               double inv_scale, int64_t row_len, int64_t pad, long long* toff,
+                                               int* gstart, double* c64, float* c32, int max_taps,
+                                               long long* s_k, unsigned int* flags) {
     __shared__ int s_lo[(1 + SOAP_MAX_CLASSES) * SOAP_MAX_MU];
     __shared__ int s_hi[(1 + SOAP_MAX_CLASSES) * SOAP_MAX_MU];
-    __shared__ int s_idx[(1 + SOAP_MAX_CLASSES) * SOAP_MAX_MU];
     __shared__ int s_off[(1 + SOAP_MAX_CLASSES) * SOAP_MAX_MU];
+    __shared__ int s_warp[32];
+    __shared__ int s_total;
     const int use_smem = s_k != nullptr;
     const int G = mode == 0 ? 1 : 1 + n_class;
     const int ngb = G * n_mu;
@@ -288,76 +288,87 @@ __device__ __forceinline__ void build_jobs_dev(const long long* __restrict__ kfi
         __syncthreads();
         K = s_k;
     }
+    auto kval = [&](const long long* q) -> long long { return use_smem ? *q : __ldcg(q); };
     auto value = [&](int g, int b, int pl, int kk) -> long long {
         if (pl >= np) return 0;
         const long long* base = K + (int64_t)pl * nb;
-        if (!use_smem) {
-            if (g == 0 && mode == 1) {
-                long long s = 0;
-                for (int cl = 0; cl < n_class; cl++) s += __ldcg(base + ((int64_t)cl * n_mu + b) * n_taps + kk);
-                return -s;
-            }
-            return __ldcg(base + ((int64_t)(mode == 0 ? 0 : g - 1) * n_mu + b) * n_taps + kk);
-        }
         if (g == 0 && mode == 1) {
             long long s = 0;
-            for (int cl = 0; cl < n_class; cl++) s += base[((int64_t)cl * n_mu + b) * n_taps + kk];
+            for (int cl = 0; cl < n_class; cl++) s += kval(base + ((int64_t)cl * n_mu + b) * n_taps + kk);
             return -s;
         }
         const int cl = mode == 0 ? 0 : g - 1;
-        return base[((int64_t)cl * n_mu + b) * n_taps + kk];
+        return kval(base + ((int64_t)cl * n_mu + b) * n_taps + kk);
     };
+    // tap range of each (group, bin) over the block's phases
     for (int t = threadIdx.x; t < ngb; t += blockDim.x) {
-        int g = t / n_mu, b = t % n_mu;
+        const int g = t / n_mu, b = t % n_mu;
         int lo = n_taps, hi = -1;
+        const int c0 = (mode == 0 || g == 0) ? 0 : g - 1;
+        const int c1 = (mode == 1 && g == 0) ? n_class : c0 + 1;
         for (int pl = 0; pl < np; pl++) {
             const long long* base = K + (int64_t)pl * nb;
-            const int c0 = (mode == 0 || g == 0) ? 0 : g - 1;
-            const int c1 = (mode == 1 && g == 0) ? n_class : c0 + 1;
             for (int cl = c0; cl < c1; cl++) {
                 const long long* row = base + ((int64_t)cl * n_mu + b) * n_taps;
                 for (int kk = 0; kk < n_taps; kk++)
-                    if ((use_smem ? row[kk] : __ldcg(row + kk)) != 0) { lo = min(lo, kk); hi = max(hi, kk); }
+                    if (kval(row + kk) != 0) { lo = min(lo, kk); hi = max(hi, kk); }
             }
         }
         s_lo[t] = lo; s_hi[t] = hi;
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int nj = 0, off = 0, g_prev = -1;
-        int* gs = gstart + (int64_t)pb * (G + 1);
-        for (int t = 0; t < ngb; t++) {
-            int g = t / n_mu;
-            while (g_prev < g) { gs[++g_prev] = nj; }
-            if (s_hi[t] < s_lo[t]) { s_idx[t] = -1; continue; }
-            int nk = s_hi[t] - s_lo[t] + 1;
-            if (nj >= max_jobs || off + nk * PB > max_coef) { atomicOr(flags, kFlagJobOverflow); s_idx[t] = -1; continue; }
-            s_idx[t] = nj; s_off[t] = off;
-            Job J;
-            J.group = g; J.bin = t % n_mu; J.k_lo = tap_min + s_lo[t]; J.n_k = nk; J.coef_off = off;
-            J.pad0 = J.pad1 = J.pad2 = 0;
-            jobs[(int64_t)pb * max_jobs + nj] = J;
-            nj++;
-            off += nk * PB;
-        }
-        while (g_prev < G) { gs[++g_prev] = nj; }
-    }
-    __syncthreads();
-    // coefficients [kk][p]: one warp per job
+    // exclusive prefix sum of the tap counts (warp scans, chunks of blockDim.x)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    if (threadIdx.x == 0) s_total = 0;
+    __syncthreads();
+    for (int c0 = 0; c0 < ngb; c0 += blockDim.x) {
+        const int t = c0 + threadIdx.x;
+        const int nk = (t < ngb && s_hi[t] >= s_lo[t]) ? s_hi[t] - s_lo[t] + 1 : 0;
+        int x = nk;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_warp[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            int w = lane < nw ? s_warp[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            if (lane < nw) s_warp[lane] = w;
+        }
+        __syncthreads();
+        if (t < ngb) s_off[t] = s_total + (warp > 0 ? s_warp[warp - 1] : 0) + x - nk;
+        __syncthreads();
+        if (threadIdx.x == 0) s_total += s_warp[nw - 1];
+        __syncthreads();
+    }
+    const int total = s_total;
+    int* gs = gstart + (int64_t)pb * (G + 1);
+    if (total > max_taps) {
+        if (threadIdx.x == 0) atomicOr(flags, kFlagJobOverflow);
+        for (int g = threadIdx.x; g <= G; g += blockDim.x) gs[g] = 0;
+        return;
+    }
+    for (int g = threadIdx.x; g <= G; g += blockDim.x) gs[g] = g < G ? s_off[g * n_mu] : total;
+    // row offsets and coefficients [tap][PB]: one warp per (group, bin)
     for (int t = warp; t < ngb; t += nw) {
-        if (s_idx[t] < 0) continue;
-        int g = t / n_mu, b = t % n_mu;
-        int nk = s_hi[t] - s_lo[t] + 1;
-        int64_t base = (int64_t)pb * max_coef + s_off[t];
+        if (s_hi[t] < s_lo[t]) continue;
+        const int g = t / n_mu, b = t % n_mu;
+        const int nk = s_hi[t] - s_lo[t] + 1;
+        const int64_t tap0 = (int64_t)pb * max_taps + s_off[t];
+        for (int kk = lane; kk < nk; kk += 32)
+            toff[tap0 + kk] = (int64_t)b * row_len + pad - (tap_min + s_lo[t] + kk);
         for (int e = lane; e < nk * PB; e += 32) {
-            int kk = e / PB, pl = e % PB;
-            double v = (double)value(g, b, pl, s_lo[t] + kk) * inv_scale;
-            if (c64) c64[base + e] = v;
-            c32[base + e] = (float)v;
+            const int kk = e / PB, pl = e % PB;
+            const double v = (double)value(g, b, pl, s_lo[t] + kk) * inv_scale;
+            if (c64) c64[tap0 * PB + e] = v;
+            c32[tap0 * PB + e] = (float)v;
         }
     }
 }
-
 
 }  // namespace soap

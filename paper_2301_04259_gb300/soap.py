@@ -24,10 +24,10 @@ SOAP_FORM_TOEPLITZ, SOAP_FORM_DIRECT = 0, 1
 SOAP_EFFECT_TOT, SOAP_EFFECT_FLUX, SOAP_EFFECT_BCONV = 1, 2, 4
 SOAP_SPOT, SOAP_FACULA = 1, 2
 SOAP_MAX_REGIONS, SOAP_MAX_CLASSES, SOAP_MAX_MU, SOAP_MAX_TAPS = 64, 8, 64, 256
-TIMERS = ("geometry", "pad_rows", "contrast", "phase_hist", "jobs", "contract", "contract_quiet",
+TIMERS = ("geometry", "pad_rows", "contrast", "phase_hist", "regions", "contract", "contract_quiet",
           "direct", "ccf", "fit")
 (SOAP_TIMER_GEOMETRY, SOAP_TIMER_PAD_ROWS, SOAP_TIMER_CONTRAST, SOAP_TIMER_PHASE_HIST,
- SOAP_TIMER_JOBS, SOAP_TIMER_CONTRACT, SOAP_TIMER_CONTRACT_QUIET, SOAP_TIMER_DIRECT,
+ SOAP_TIMER_REGIONS, SOAP_TIMER_CONTRACT, SOAP_TIMER_CONTRACT_QUIET, SOAP_TIMER_DIRECT,
  SOAP_TIMER_CCF, SOAP_TIMER_FIT) = range(10)
 
 
