@@ -343,6 +343,18 @@ soap_status soap_rv_ccf_static(double lambda_start_A, double lambda_end_A, int64
                                int32_t n_v, double* rv_kms, double* fit_params, double* ccf_out,
                                void* cuda_stream);
 
+/* Dense BF16 GEMM on the tensor cores (tcgen05, FP32 accumulation), the building block of the
+ * surrogate network: C[m][n] = act(sum_k A[m][k] B[n][k] + bias[n]).  No counterpart in the
+ * paper.
+ *  A          device BF16 [M][lda], B device BF16 [N][ldb] (K contiguous in both); bases 16-byte
+ *             aligned, lda and ldb multiples of 8 elements, >= K.
+ *  bias       device float [N] or NULL.  activation: 0 none, 1 GELU (exact, erf form).
+ *  C          device float [M][ldc], ldc >= N.
+ * Synchronises the stream; SOAP_ETIMEOUT if a bounded device-side wait gave up. */
+soap_status soap_gemm_bf16_tn(int32_t M, int32_t N, int32_t K, const void* A, int64_t lda,
+                              const void* B, int64_t ldb, const float* bias, int32_t activation,
+                              float* C, int64_t ldc, void* cuda_stream);
+
 /* Number of kernels this context has launched so far (for launch accounting). */
 soap_status soap_get_launch_count(const soap_ctx* ctx, uint64_t* out);
 

@@ -94,6 +94,7 @@ def _load():
         "soap_batch_get_variant": (i32, [P, ctypes.POINTER(i32)]),
         "soap_batch_autotune": (i32, [P, ctypes.POINTER(soap_batch_item), i32, ctypes.POINTER(soap_region), i32,
                                       P, i32, P, i32, P, ctypes.POINTER(i32)]),
+        "soap_gemm_bf16_tn": (i32, [i32, i32, i32, P, i64, P, i64, P, i32, P, i64, P]),
         "soap_free": (None, [P]),
         "soap_last_error": (ctypes.c_char_p, []),
     }
@@ -327,6 +328,23 @@ def soap_batch_autotune(ctx, items: Sequence, regions: Sequence, phases, out, re
                                     ph.size, ptr, int(reps), ctypes.c_void_p(ms.ctypes.data),
                                     ctypes.byref(best)), "soap_batch_autotune")
     return int(best.value), ms
+
+
+def soap_gemm_bf16_tn(A, B, C, bias=None, activation: int = 0, stream=None) -> None:
+    """C[:, :N] = act(A @ B.T + bias) on the tensor cores; A [M, K], B [N, K] bfloat16 CUDA
+    tensors (row-contiguous, possibly column slices of wider ones), C float32 [M, >= N]."""
+    M, K = A.shape
+    N = B.shape[0]
+    if B.shape[1] != K or C.shape[0] != M or C.shape[1] < N:
+        raise ValueError("shape mismatch")
+    for t in (A, B, C):
+        if not t.is_cuda or t.stride(1) != 1:
+            raise ValueError("operands must be CUDA tensors with unit column stride")
+    _check(_lib.soap_gemm_bf16_tn(M, N, K, ctypes.c_void_p(A.data_ptr()), A.stride(0),
+                                  ctypes.c_void_p(B.data_ptr()), B.stride(0),
+                                  ctypes.c_void_p(bias.data_ptr()) if bias is not None else None,
+                                  int(activation), ctypes.c_void_p(C.data_ptr()), C.stride(0),
+                                  _stream_handle(stream)), "soap_gemm_bf16_tn")
 
 
 def soap_get_launch_count(ctx) -> int:
