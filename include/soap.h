@@ -234,6 +234,12 @@ typedef struct {
     int32_t n_phases;
 } soap_batch_item;
 
+/* Output of soap_active_batch. */
+enum {
+    SOAP_BATCH_SPECTRUM = 0,   /* F = F_q - Delta F (Eq. 4) */
+    SOAP_BATCH_RESIDUAL = 1    /* F - F_q = -Delta F: the active regions' change alone */
+};
+
 /* Spectra of many independent active-star configurations in one call: for every item and
  * each of its phases, the TOT effect of soap_active_phases (Alg. 5 with Eqs. 3-4) for a star
  * that differs from the context's only in vsini and inclination.  The paper computes one
@@ -241,23 +247,23 @@ typedef struct {
  *  items      host [n_items]; every phase index 0 .. n_phases-1 belongs to exactly one item.
  *  regions    host [n_regions], shared pool that items index into.
  *  phases     host [n_phases] rotational phases.
- *  out        float32 [n_phases][n_px]: out[p][m] = F_q,item[m] - Delta F_TOT[p][m], host or
- *             device per out_on_device.
+ *  output     SOAP_BATCH_SPECTRUM or SOAP_BATCH_RESIDUAL (skips the quiet spectra).
+ *  out        float32 [n_phases][n_px], row p for phase p, host or device per out_on_device.
  * Arithmetic as SOAP_FP32 (FP64 velocities and shift positions, FP32 contraction and
- * accumulation); a cell's interpolation weight is held to 32 fractional bits.  Needs
- * diff_rot_alpha = 0 (a cell's velocity is then vsini x, so one table per item and grid
- * column replaces per-cell geometry) and at most SOAP_MAX_CLASSES distinct (type, temperature)
- * pairs over the whole region pool.  Work is cut into (item phase block, pixel tile) units run
- * by one persistent kernel in decreasing order of estimated cost; the kernel sequence is
- * captured once per batch shape into a CUDA graph owned by the context and replayed on later
- * calls with the same shape (soap_set_profiling(ctx, 1) runs it without the graph).  The
- * variant (phases per block, pixels per thread) is the one soap_batch_set_variant or
- * soap_batch_autotune chose, else a default.
+ * accumulation); a cell's interpolation weight is held to 32 fractional bits; the contrast
+ * (Sect. 4.3.1) is evaluated per pixel in FP32.  Needs diff_rot_alpha = 0 (a cell's velocity is
+ * then vsini x, so one table per item and grid column replaces per-cell geometry) and at most
+ * SOAP_MAX_CLASSES distinct (type, temperature) pairs within each item.  Work is cut into
+ * phase blocks run by one persistent kernel in decreasing order of estimated cost; the kernel
+ * sequence is captured once per batch shape into a CUDA graph owned by the context and
+ * replayed on later calls with the same shape (soap_set_profiling(ctx, 1) runs it without the
+ * graph).  The variant (phases per block, pixels per thread) is the one soap_batch_set_variant
+ * or soap_batch_autotune chose, else a default.
  * Errors: SOAP_EINVAL (bad item, phase not covered exactly once, alpha != 0), SOAP_ESTATE (no
- * active spectrum for a region type), SOAP_ERANGE (class limit, batch too large). */
+ * active spectrum for a region type), SOAP_ERANGE (class limit). */
 soap_status soap_active_batch(soap_ctx* ctx, const soap_batch_item* items, int32_t n_items,
                               const soap_region* regions, int32_t n_regions, const double* phases,
-                              int32_t n_phases, float* out, int out_on_device);
+                              int32_t n_phases, int32_t output, float* out, int out_on_device);
 
 /* Number of variants of the batched form (valid variants are 0 .. *n - 1). */
 soap_status soap_batch_num_variants(int32_t* n);

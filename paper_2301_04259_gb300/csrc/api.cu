@@ -552,9 +552,10 @@ soap_status soap_rv_ccf(soap_ctx* c, const void* spectra, int32_t spectra_f32, i
 
 soap_status soap_active_batch(soap_ctx* c, const soap_batch_item* items, int32_t n_items,
                               const soap_region* regions, int32_t n_regions, const double* phases,
-                              int32_t n_phases, float* out, int out_on_device) {
+                              int32_t n_phases, int32_t output, float* out, int out_on_device) {
     clear_error();
     if (!c || !out) { set_error("ctx or out is NULL"); return SOAP_EINVAL; }
+    if (output != SOAP_BATCH_SPECTRUM && output != SOAP_BATCH_RESIDUAL) { set_error("unknown output %d", output); return SOAP_EINVAL; }
     if (n_items < 0 || n_regions < 0 || n_phases < 0) { set_error("negative count"); return SOAP_EINVAL; }
     if ((n_items > 0 && !items) || (n_regions > 0 && !regions) || (n_phases > 0 && !phases)) {
         set_error("items, regions or phases is NULL"); return SOAP_EINVAL;
@@ -566,7 +567,8 @@ soap_status soap_active_batch(soap_ctx* c, const soap_batch_item* items, int32_t
         SOAP_TRY(ensure(c->out_stage, bytes));
         dst = c->out_stage.as<float>();
     }
-    SOAP_TRY(batch_run(c, items, n_items, regions, n_regions, phases, n_phases, variant, dst));
+    SOAP_TRY(batch_run(c, items, n_items, regions, n_regions, phases, n_phases, variant,
+                       output == SOAP_BATCH_RESIDUAL, dst));
     if (!out_on_device && bytes > 0) {
         SOAP_CUDA(cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, c->stream));
         SOAP_CUDA(cudaStreamSynchronize(c->stream));
@@ -622,11 +624,11 @@ soap_status soap_batch_autotune(soap_ctx* c, const soap_batch_item* items, int32
     int best = -1;
     float best_ms = 0;
     for (int v = 0; v < nv && st == SOAP_OK; v++) {
-        st = batch_run(c, items, n_items, regions, n_regions, phases, n_phases, v, out);   // capture + warm
+        st = batch_run(c, items, n_items, regions, n_regions, phases, n_phases, v, 0, out);   // capture + warm
         if (st != SOAP_OK) break;
         if (cudaEventRecord(e0, c->stream) != cudaSuccess) { st = SOAP_ECUDA; break; }
         for (int k = 0; k < reps && st == SOAP_OK; k++)
-            st = batch_run(c, items, n_items, regions, n_regions, phases, n_phases, v, out);
+            st = batch_run(c, items, n_items, regions, n_regions, phases, n_phases, v, 0, out);
         if (st != SOAP_OK) break;
         float t = 0;
         if (cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||

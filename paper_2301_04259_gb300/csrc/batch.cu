@@ -28,6 +28,9 @@ namespace soap {
 struct BatchItemDev {
     double vsini, incl_deg;
     int first_region, n_regions, first_phase, n_phases;
+    int n_cls;                           // the item's region classes (type, temperature)
+    int cls_type[SOAP_MAX_CLASSES];
+    float cls_a[SOAP_MAX_CLASSES];       // h c / (lambda_s k T_class)
 };
 
 struct PBlockDev {
@@ -119,9 +122,9 @@ __global__ void __launch_bounds__(THREADS)
 k_batch_quiet(int64_t n_px, Rows<float> rows, const long long* __restrict__ qtoff, const int* __restrict__ qgs,
               const float* __restrict__ qc32, int q_max_taps, float* __restrict__ fq) {
     const int it = blockIdx.y;
-    ClassTypes ct{};
+    const TableContrast<float> con{nullptr, n_px, ClassTypes{}};
     contract_tile<float, 1, R, THREADS>(n_px, rows, qtoff + (int64_t)it * q_max_taps, qgs + (int64_t)it * 2, 1,
-                                        qc32 + (int64_t)it * q_max_taps, ct, nullptr, nullptr, SOAP_EFFECT_TOT,
+                                        qc32 + (int64_t)it * q_max_taps, con, nullptr, SOAP_EFFECT_TOT,
                                         blockIdx.x, 1, fq + (int64_t)it * n_px);
 }
 
@@ -208,14 +211,16 @@ __global__ void k_batch_hist(int N, int max_r, const int* __restrict__ phase_ite
 }
 
 // Stage 6: persistent.  A unit is one phase block over all pixel tiles; blocks take the next
-// unit in `order` with an atomic ticket until none is left (no block waits on another).
+// unit in `order` with an atomic ticket until none is left (no block waits on another).  The
+// contrast of the item's classes is evaluated per pixel (Planck ratio), so items may carry any
+// temperatures.  fq == nullptr: residual output F - F_q.
 template <int PB, int R, int THREADS>
 __global__ void __launch_bounds__(THREADS)
 k_batch_contract(int64_t n_px, Rows<float> rows, const long long* __restrict__ toff, const int* __restrict__ gstart,
-                 int G, int max_taps, const float* __restrict__ c32, ClassTypes ctype,
-                 const float* __restrict__ contrast, const float* __restrict__ fq,
-                 const PBlockDev* __restrict__ pblocks, const int* __restrict__ order, int n_units, int n_tiles,
-                 unsigned int* ticket, float* __restrict__ out) {
+                 int G, int max_taps, const float* __restrict__ c32, const BatchItemDev* __restrict__ items,
+                 float aq, float fd, const float* __restrict__ fq, const PBlockDev* __restrict__ pblocks,
+                 const int* __restrict__ order, int n_units, int n_tiles, unsigned int* ticket,
+                 float* __restrict__ out) {
     __shared__ int s_u;
     while (true) {
         if (threadIdx.x == 0) s_u = (int)atomicAdd(ticket, 1u);
@@ -228,11 +233,12 @@ k_batch_contract(int64_t n_px, Rows<float> rows, const long long* __restrict__ t
         const long long* tt = toff + (int64_t)pbk * max_taps;
         const int* gs = gstart + (int64_t)pbk * (G + 1);
         const float* cb = c32 + (int64_t)pbk * max_taps * PB;
-        const float* fqi = fq + (int64_t)pb.item * n_px;
+        const float* fqi = fq ? fq + (int64_t)pb.item * n_px : nullptr;
         float* orow = out + (int64_t)pb.first_phase * n_px;
+        const PlanckContrast32 con{aq, fd, items[pb.item].cls_type, items[pb.item].cls_a};
         for (int tile = 0; tile < n_tiles; tile++)
-            contract_tile<float, PB, R, THREADS>(n_px, rows, tt, gs, G, cb, ctype, contrast, fqi, SOAP_EFFECT_TOT,
-                                                 tile, pb.np, orow);
+            contract_tile<float, PB, R, THREADS>(n_px, rows, tt, gs, G, cb, con, fqi, SOAP_EFFECT_TOT, tile, pb.np,
+                                                 orow);
     }
 }
 
@@ -251,16 +257,22 @@ constexpr int kDefaultVariant = 1;
 
 // Sizes of one batch, fixed by the host preparation and baked into the captured graph.
 struct BatchShape {
-    int n_items, n_phases, max_r, n_pblocks, n_units, n_tiles, variant, n_class;
+    int n_items, n_phases, max_r, n_pblocks, n_units, n_tiles, variant, n_class, residual;
     int G, max_taps;
     int64_t nbk;               // per-phase kernel size n_class * n_mu * n_taps
     int use_smem, taps_smem;
     size_t hist_smem;
 };
 
+// h c / (lambda_s k T): the Planck exponent at the first grid wavelength.
+static double planck_aq(const soap_ctx* c, double temp) {
+    return kPlanckH * kLightSI / kBoltzmann * 1e10 / (c->lam_s * temp);
+}
+static double planck_aq(const soap_ctx* c) { return planck_aq(c, c->t_quiet); }
+
 template <int PB, int R>
-static soap_status launch_batch_contract(soap_ctx* c, const BatchShape& b, const ClassTypes& ct,
-                                         const float* a0, const float* a1, float* out) {
+static soap_status launch_batch_contract(soap_ctx* c, const BatchShape& b, const float* a0, const float* a1,
+                                         float* out) {
     Rows<float> rows;
     rows.q = c->q32; rows.a[0] = a0; rows.a[1] = a1;
     int dev = 0, sms = 152, per_sm = 4;
@@ -272,16 +284,15 @@ static soap_status launch_batch_contract(soap_ctx* c, const BatchShape& b, const
     SOAP_TIMED(c, SOAP_TIMER_CONTRACT,
                k_batch_contract<PB, R, kBatchThreads><<<grid, kBatchThreads, 0, c->stream>>>(
                    c->n_px, rows, c->b_toff.as<long long>(), c->b_gstart.as<int>(), b.G, b.max_taps,
-                   c->b_coefs.as<float>(), ct, c->b_con.as<float>(), c->b_fq.as<float>(),
-                   c->b_pblocks.as<PBlockDev>(), c->b_order.as<int>(), b.n_units, b.n_tiles,
-                   c->b_ticket.as<unsigned int>(), out);
+                   c->b_coefs.as<float>(), c->b_items.as<BatchItemDev>(), (float)planck_aq(c), (float)c->delta,
+                   b.residual ? nullptr : c->b_fq.as<float>(), c->b_pblocks.as<PBlockDev>(), c->b_order.as<int>(),
+                   b.n_units, b.n_tiles, c->b_ticket.as<unsigned int>(), out);
                SOAP_LAUNCHED(c));
     return SOAP_OK;
 }
 
 // Enqueue stages 1-6 on the context's stream for a batch whose inputs are already on the device.
-static soap_status enqueue_batch(soap_ctx* c, const BatchShape& b, const ClassTypes& ct,
-                                 const ClassConsts& cc, float* out) {
+static soap_status enqueue_batch(soap_ctx* c, const BatchShape& b, float* out) {
     const int N = c->N;
     const int q_max_taps = c->n_mu * c->n_taps;
     const double scale = std::ldexp(1.0, c->fx_bits);
@@ -302,8 +313,8 @@ static soap_status enqueue_batch(soap_ctx* c, const BatchShape& b, const ClassTy
                    c->b_qtoff.as<long long>(), c->b_qgs.as<int>(), c->b_qc32.as<float>(), q_max_taps, inv_scale,
                    c->row_len, c->pad, c->flags);
                SOAP_LAUNCHED(c));
-    // 3 quiet spectra
-    {
+    // 3 quiet spectra (not needed for residual output)
+    if (!b.residual) {
         Rows<float> rows;
         rows.q = c->q32; rows.a[0] = nullptr; rows.a[1] = nullptr;
         const int64_t TILE = 128 * 4;
@@ -312,15 +323,6 @@ static soap_status enqueue_batch(soap_ctx* c, const BatchShape& b, const ClassTy
                    k_batch_quiet<4, 128><<<grid, 128, 0, c->stream>>>(
                        c->n_px, rows, c->b_qtoff.as<long long>(), c->b_qgs.as<int>(), c->b_qc32.as<float>(),
                        q_max_taps, c->b_fq.as<float>());
-                   SOAP_LAUNCHED(c));
-    }
-    // contrast per class
-    if (b.n_class > 0) {
-        const double hck = kPlanckH * kLightSI / kBoltzmann * 1e10;
-        const int64_t g = std::min<int64_t>((c->n_px + 255) / 256, 152 * 8);
-        SOAP_TIMED(c, SOAP_TIMER_CONTRAST,
-                   k_contrast32<<<(unsigned)g, 256, 0, c->stream>>>(c->n_px, (float)(hck / (c->lam_s * c->t_quiet)),
-                                                                   (float)c->delta, b.n_class, cc, c->b_con.as<float>());
                    SOAP_LAUNCHED(c));
     }
     // 4 regions
@@ -352,12 +354,12 @@ static soap_status enqueue_batch(soap_ctx* c, const BatchShape& b, const ClassTy
     const float* a0 = c->active_set[0] ? c->a32[0] : c->a32[1];
     const float* a1 = c->active_set[1] ? c->a32[1] : c->a32[0];
     switch (b.variant) {
-        case 0: return launch_batch_contract<4, 2>(c, b, ct, a0, a1, out);
-        case 1: return launch_batch_contract<4, 4>(c, b, ct, a0, a1, out);
-        case 2: return launch_batch_contract<8, 2>(c, b, ct, a0, a1, out);
-        case 3: return launch_batch_contract<8, 4>(c, b, ct, a0, a1, out);
-        case 4: return launch_batch_contract<16, 2>(c, b, ct, a0, a1, out);
-        default: return launch_batch_contract<16, 4>(c, b, ct, a0, a1, out);
+        case 0: return launch_batch_contract<4, 2>(c, b, a0, a1, out);
+        case 1: return launch_batch_contract<4, 4>(c, b, a0, a1, out);
+        case 2: return launch_batch_contract<8, 2>(c, b, a0, a1, out);
+        case 3: return launch_batch_contract<8, 4>(c, b, a0, a1, out);
+        case 4: return launch_batch_contract<16, 2>(c, b, a0, a1, out);
+        default: return launch_batch_contract<16, 4>(c, b, a0, a1, out);
     }
 }
 
@@ -376,7 +378,7 @@ void batch_release(soap_ctx* c) {
     c->b_graph_key.clear();
     DevBuf* bufs[] = {&c->b_items, &c->b_regions, &c->b_phases, &c->b_phase_item, &c->b_phase_block,
                       &c->b_pblocks, &c->b_order, &c->b_cellIfx, &c->b_IB, &c->b_colj, &c->b_colw, &c->b_kq,
-                      &c->b_qtoff, &c->b_qgs, &c->b_qc32, &c->b_fq, &c->b_con, &c->b_geo, &c->b_kfix,
+                      &c->b_qtoff, &c->b_qgs, &c->b_qc32, &c->b_fq, &c->b_geo, &c->b_kfix,
                       &c->b_counters, &c->b_toff, &c->b_gstart, &c->b_coefs, &c->b_ticket};
     for (DevBuf* b : bufs) release(*b);
 }
@@ -384,18 +386,13 @@ void batch_release(soap_ctx* c) {
 // Host preparation (validation, classes, phase blocks, cost-ordered units, uploads), then the
 // graph: captured on the first call with a given shape, replayed on later ones.
 soap_status batch_run(soap_ctx* c, const soap_batch_item* items, int n_items, const soap_region* regions,
-                      int n_regions, const double* phases, int n_phases, int variant, float* out) {
+                      int n_regions, const double* phases, int n_phases, int variant, int residual, float* out) {
     if (c->alpha != 0.0) {
         set_error("the batched form needs a star without differential rotation (diff_rot_alpha = 0)");
         return SOAP_EINVAL;
     }
     if (variant < 0 || variant >= kNumVariants) { set_error("unknown batch variant %d", variant); return SOAP_EINVAL; }
     const BatchVariant V = kVariants[variant];
-    // classes over all regions, in first-appearance order
-    double ctemp[SOAP_MAX_CLASSES];
-    int ctype[SOAP_MAX_CLASSES];
-    int n_class = 0;
-    std::vector<RegionDev> rd(std::max(1, n_regions));
     for (int r = 0; r < n_regions; r++) {
         const soap_region& g = regions[r];
         if (g.type != SOAP_SPOT && g.type != SOAP_FACULA) { set_error("regions[%d].type invalid", r); return SOAP_EINVAL; }
@@ -406,21 +403,12 @@ soap_status batch_run(soap_ctx* c, const soap_batch_item* items, int n_items, co
         }
         if (g.radius_rstar < 0 || g.radius_rstar > 1) { set_error("regions[%d].radius_rstar outside [0,1]", r); return SOAP_EINVAL; }
         if (!(g.temp_K > 0)) { set_error("regions[%d].temp_K must be > 0", r); return SOAP_EINVAL; }
-        int cl = -1;
-        for (int k = 0; k < n_class; k++)
-            if (ctype[k] == g.type && ctemp[k] == g.temp_K) cl = k;
-        if (cl < 0) {
-            if (n_class == SOAP_MAX_CLASSES) { set_error("more than %d distinct (type, temperature) pairs", SOAP_MAX_CLASSES); return SOAP_ERANGE; }
-            cl = n_class++;
-            ctype[cl] = g.type;
-            ctemp[cl] = g.temp_K;
-        }
-        rd[r] = RegionDev{g.lat_deg, g.lon_deg, g.radius_rstar, g.temp_K, g.type, cl};
     }
-    for (int k = 0; k < n_class; k++) {
-        const bool ok = ctype[k] == SOAP_SPOT ? c->active_set[0] : (c->active_set[1] || c->active_set[0]);
-        if (!ok) { set_error("no active spectrum set for region type %d", ctype[k]); return SOAP_ESTATE; }
-    }
+    // each item's regions are copied with the index of their class (type, temperature) among
+    // the item's classes, in first-appearance order
+    std::vector<RegionDev> rd;
+    int n_class = 0;
+    bool uses[3] = {false, false, false};
     // configurations, phase ownership, phase blocks and their estimated cost
     std::vector<BatchItemDev> it(std::max(1, n_items));
     std::vector<int> phase_item(std::max(1, n_phases), -1), phase_block(std::max(1, n_phases), -1);
@@ -441,10 +429,31 @@ soap_status batch_run(soap_ctx* c, const soap_batch_item* items, int n_items, co
             set_error("items[%d]: region or phase range out of bounds", k); return SOAP_EINVAL;
         }
         double area = 0;
+        BatchItemDev d{};
+        d.vsini = s.vsini_kms; d.incl_deg = s.incl_deg;
+        d.first_region = (int)rd.size(); d.n_regions = s.n_regions;
+        d.first_phase = s.first_phase; d.n_phases = s.n_phases;
+        double ctemp[SOAP_MAX_CLASSES];
         for (int r = 0; r < s.n_regions; r++) {
-            const double rr = regions[s.first_region + r].radius_rstar;
-            area += rr * rr;
+            const soap_region& g = regions[s.first_region + r];
+            area += g.radius_rstar * g.radius_rstar;
+            int cl = -1;
+            for (int q = 0; q < d.n_cls; q++)
+                if (d.cls_type[q] == g.type && ctemp[q] == g.temp_K) cl = q;
+            if (cl < 0) {
+                if (d.n_cls == SOAP_MAX_CLASSES) {
+                    set_error("items[%d]: more than %d distinct (type, temperature) pairs", k, SOAP_MAX_CLASSES);
+                    return SOAP_ERANGE;
+                }
+                cl = d.n_cls++;
+                d.cls_type[cl] = g.type;
+                ctemp[cl] = g.temp_K;
+                d.cls_a[cl] = (float)planck_aq(c, g.temp_K);
+                uses[g.type] = true;
+            }
+            rd.push_back(RegionDev{g.lat_deg, g.lon_deg, g.radius_rstar, g.temp_K, g.type, cl});
         }
+        n_class = std::max(n_class, d.n_cls);
         for (int p = 0; p < s.n_phases; p++) {
             const int q = s.first_phase + p;
             if (phase_item[q] != -1) { set_error("phase %d belongs to two items", q); return SOAP_EINVAL; }
@@ -460,7 +469,11 @@ soap_status batch_run(soap_ctx* c, const soap_batch_item* items, int n_items, co
             pcost.push_back(np * (1.0 + 40.0 * area * (1.0 + std::fabs(s.vsini_kms))));
         }
         max_r = std::max(max_r, s.n_regions);
-        it[k] = BatchItemDev{s.vsini_kms, s.incl_deg, s.first_region, s.n_regions, s.first_phase, s.n_phases};
+        it[k] = d;
+    }
+    if (uses[SOAP_SPOT] && !c->active_set[0]) { set_error("no active spectrum set for spots"); return SOAP_ESTATE; }
+    if (uses[SOAP_FACULA] && !c->active_set[0] && !c->active_set[1]) {
+        set_error("no active spectrum set for faculae"); return SOAP_ESTATE;
     }
     for (int p = 0; p < n_phases; p++)
         if (phase_item[p] < 0) { set_error("phase %d belongs to no item", p); return SOAP_EINVAL; }
@@ -474,6 +487,7 @@ soap_status batch_run(soap_ctx* c, const soap_batch_item* items, int n_items, co
     b.n_units = b.n_pblocks;
     b.variant = variant;
     b.n_class = n_class;
+    b.residual = residual ? 1 : 0;
     b.G = 1 + n_class;
     b.max_taps = b.G * c->n_mu * c->n_taps;
     b.nbk = (int64_t)n_class * c->n_mu * c->n_taps;
@@ -489,9 +503,9 @@ soap_status batch_run(soap_ctx* c, const soap_batch_item* items, int n_items, co
     const std::vector<int>& order = border;
     // device buffers (grow-only)
     const int N = c->N;
-    const int ncl = std::max(1, n_class);
+    const size_t n_rd = std::max<size_t>(1, rd.size());
     SOAP_TRY(ensure(c->b_items, (size_t)n_items * sizeof(BatchItemDev)));
-    SOAP_TRY(ensure(c->b_regions, (size_t)std::max(1, n_regions) * sizeof(RegionDev)));
+    SOAP_TRY(ensure(c->b_regions, n_rd * sizeof(RegionDev)));
     SOAP_TRY(ensure(c->b_phases, (size_t)n_phases * sizeof(double)));
     SOAP_TRY(ensure(c->b_phase_item, (size_t)n_phases * sizeof(int)));
     SOAP_TRY(ensure(c->b_phase_block, (size_t)n_phases * sizeof(int)));
@@ -505,8 +519,7 @@ soap_status batch_run(soap_ctx* c, const soap_batch_item* items, int n_items, co
     SOAP_TRY(ensure(c->b_qtoff, (size_t)n_items * c->n_mu * c->n_taps * sizeof(long long)));
     SOAP_TRY(ensure(c->b_qgs, (size_t)n_items * 2 * sizeof(int)));
     SOAP_TRY(ensure(c->b_qc32, (size_t)n_items * c->n_mu * c->n_taps * sizeof(float)));
-    SOAP_TRY(ensure(c->b_fq, (size_t)n_items * c->n_px * sizeof(float)));
-    SOAP_TRY(ensure(c->b_con, (size_t)ncl * c->n_px * sizeof(float)));
+    if (!residual) SOAP_TRY(ensure(c->b_fq, (size_t)n_items * c->n_px * sizeof(float)));
     SOAP_TRY(ensure(c->b_geo, (size_t)n_phases * std::max(1, max_r) * sizeof(RegionGeo)));
     SOAP_TRY(ensure(c->b_kfix, (size_t)n_phases * std::max<int64_t>(1, b.nbk) * sizeof(long long)));
     SOAP_TRY(ensure(c->b_counters, (size_t)b.n_pblocks * sizeof(int)));
@@ -516,38 +529,30 @@ soap_status batch_run(soap_ctx* c, const soap_batch_item* items, int n_items, co
     SOAP_TRY(ensure(c->b_ticket, sizeof(unsigned int)));
     // inputs (pageable copies: the call returns after the driver has staged them)
     SOAP_CUDA(cudaMemcpyAsync(c->b_items.p, it.data(), (size_t)n_items * sizeof(BatchItemDev), cudaMemcpyHostToDevice, c->stream));
-    if (n_regions > 0)
-        SOAP_CUDA(cudaMemcpyAsync(c->b_regions.p, rd.data(), (size_t)n_regions * sizeof(RegionDev), cudaMemcpyHostToDevice, c->stream));
+    if (!rd.empty())
+        SOAP_CUDA(cudaMemcpyAsync(c->b_regions.p, rd.data(), rd.size() * sizeof(RegionDev), cudaMemcpyHostToDevice, c->stream));
     SOAP_CUDA(cudaMemcpyAsync(c->b_phases.p, phases, (size_t)n_phases * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     SOAP_CUDA(cudaMemcpyAsync(c->b_phase_item.p, phase_item.data(), (size_t)n_phases * sizeof(int), cudaMemcpyHostToDevice, c->stream));
     SOAP_CUDA(cudaMemcpyAsync(c->b_phase_block.p, phase_block.data(), (size_t)n_phases * sizeof(int), cudaMemcpyHostToDevice, c->stream));
     SOAP_CUDA(cudaMemcpyAsync(c->b_pblocks.p, pbl.data(), (size_t)b.n_pblocks * sizeof(PBlockDev), cudaMemcpyHostToDevice, c->stream));
     SOAP_CUDA(cudaMemcpyAsync(c->b_order.p, order.data(), (size_t)b.n_units * sizeof(int), cudaMemcpyHostToDevice, c->stream));
-    ClassTypes ct{};
-    ClassConsts cc{};
-    const double hck = kPlanckH * kLightSI / kBoltzmann * 1e10;
-    for (int k = 0; k < n_class; k++) {
-        ct.t[k] = ctype[k];
-        cc.a[k] = (float)(hck / (c->lam_s * ctemp[k]));
-    }
     if (c->profiling)      // per-kernel timers need events between the launches: no graph
-        return enqueue_batch(c, b, ct, cc, out);
-    // everything the graph bakes in: sizes, star parameters, class constants and pointers
+        return enqueue_batch(c, b, out);
+    // everything the graph bakes in: sizes, star parameters and pointers
     std::vector<uint64_t> key;
     auto put = [&](uint64_t v) { key.push_back(v); };
     auto putd = [&](double v) { uint64_t u; memcpy(&u, &v, 8); key.push_back(u); };
     auto putp = [&](const void* p) { key.push_back((uint64_t)(uintptr_t)p); };
     put(b.n_items); put(b.n_phases); put(b.max_r); put(b.n_pblocks); put(b.n_units); put(b.n_tiles);
-    put(b.variant); put(b.n_class); put(b.use_smem); put(b.taps_smem); put(b.hist_smem);
+    put(b.variant); put(b.n_class); put(b.residual); put(b.use_smem); put(b.taps_smem); put(b.hist_smem);
     put(N); put(c->n_mu); put(c->n_taps); put((uint64_t)c->tap_min); put(c->fx_bits);
     put(c->n_px); put(c->row_len); put(c->pad);
     putd(c->delta); putd(c->lam_s); putd(c->t_quiet);
-    for (int k = 0; k < n_class; k++) { put(ct.t[k]); putd(ctemp[k]); }
     putp(out); putp(c->stream); putp(c->q32); putp(c->a32[0]); putp(c->a32[1]); putp(c->cell_I);
     putp(c->cell_bin); putp(c->cell_mu); putp(c->cell_mu32); putp(c->flags);
     const DevBuf* bufs[] = {&c->b_items, &c->b_regions, &c->b_phases, &c->b_phase_item, &c->b_phase_block,
                             &c->b_pblocks, &c->b_order, &c->b_cellIfx, &c->b_IB, &c->b_colj, &c->b_colw, &c->b_kq,
-                            &c->b_qtoff, &c->b_qgs, &c->b_qc32, &c->b_fq, &c->b_con, &c->b_geo, &c->b_kfix,
+                            &c->b_qtoff, &c->b_qgs, &c->b_qc32, &c->b_fq, &c->b_geo, &c->b_kfix,
                             &c->b_counters, &c->b_toff, &c->b_gstart, &c->b_coefs, &c->b_ticket};
     for (const DevBuf* q : bufs) putp(q->p);
     if (!c->b_graph_exec || c->b_graph_key != key) {
@@ -562,7 +567,7 @@ soap_status batch_run(soap_ctx* c, const soap_batch_item* items, int n_items, co
         soap_status st = SOAP_OK;
         cudaGraph_t graph = nullptr;
         if (e == cudaSuccess) {
-            st = enqueue_batch(c, b, ct, cc, out);
+            st = enqueue_batch(c, b, out);
             const cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
             if (e2 != cudaSuccess && st == SOAP_OK) e = e2;
         }

@@ -138,9 +138,10 @@ k_contract(int64_t n_px, Rows<T> rows, const long long* __restrict__ toff, const
     const int pb = blockIdx.y;
     const int np = min(PB, n_phases - pb * PB);
     T* out_rows = out + (int64_t)blockIdx.z * n_phases * n_px + (int64_t)pb * PB * n_px;
+    const TableContrast<T> con{contrast, n_px, ctype};
     contract_tile<T, PB, R, THREADS>(n_px, rows, toff + (int64_t)pb * max_taps, gstart + (int64_t)pb * (G + 1), G,
-                                     coefs + (int64_t)pb * max_taps * PB, ctype, contrast, fq,
-                                     effs.e[blockIdx.z], blockIdx.x, np, out_rows);
+                                     coefs + (int64_t)pb * max_taps * PB, con, fq, effs.e[blockIdx.z], blockIdx.x,
+                                     np, out_rows);
 }
 
 // ---------------------------------------------------------------------------------------

@@ -48,12 +48,35 @@ __device__ __forceinline__ void load_coefs(const T* __restrict__ src, T (&cv)[PB
     }
 }
 
-template <typename T, int PB, int R, int THREADS>
+// Region classes as the contraction sees them: the type of class cl (which active rows it
+// convolves) and its contrast C_cl at pixel m.  TableContrast reads precomputed rows
+// [n_class][n_px]; PlanckContrast32 evaluates the Planck ratio of Sect. 4.3.1 in FP32 with the
+// same operations as k_contrast32 (so both give the same values).
+template <typename T>
+struct TableContrast {
+    const T* rows;
+    int64_t n_px;
+    ClassTypes ct;
+    __device__ __forceinline__ int type(int cl) const { return ct.t[cl]; }
+    __device__ __forceinline__ T at(int cl, int64_t m) const { return rows[(int64_t)cl * n_px + m]; }
+};
+
+struct PlanckContrast32 {
+    float aq, fd;            // h c / (lambda_s k T_quiet), grid step Delta
+    const int* types;        // [n_class]
+    const float* a;          // [n_class]: h c / (lambda_s k T_class)
+    __device__ __forceinline__ int type(int cl) const { return types[cl]; }
+    __device__ __forceinline__ float at(int cl, int64_t m) const {
+        const float inv = expf(-(float)m * fd);            // lambda_s / lambda_m
+        return expm1f(aq * inv) / expm1f(a[cl] * inv);
+    }
+};
+
+template <typename T, int PB, int R, int THREADS, class Con>
 __device__ __forceinline__ void contract_tile(int64_t n_px, const Rows<T>& rows, const long long* __restrict__ toff,
                                               const int* __restrict__ gs, int G, const T* __restrict__ cb,
-                                              const ClassTypes& ctype, const T* __restrict__ contrast,
-                                              const T* __restrict__ fq, int eff, int64_t tile, int np,
-                                              T* __restrict__ out_rows) {
+                                              const Con& con, const T* __restrict__ fq, int eff, int64_t tile,
+                                              int np, T* __restrict__ out_rows) {
     // Rows are padded past round_up(n_px, 1024) + max tap, so every tap of every pixel of the
     // last tile reads inside its row; only the per-pixel inputs below need a clamped index.
     const int64_t m0 = tile * THREADS * R + threadIdx.x;
@@ -93,7 +116,7 @@ __device__ __forceinline__ void contract_tile(int64_t n_px, const Rows<T>& rows,
         const int t0 = gs[g], t1 = gs[g + 1];
         if (t0 == t1) continue;
         const int cl = g - 1;
-        const T* base = (eff == SOAP_EFFECT_FLUX ? rows.q : rows.a[ctype.t[cl] == SOAP_FACULA ? 1 : 0]) + m0;
+        const T* base = (eff == SOAP_EFFECT_FLUX ? rows.q : rows.a[con.type(cl) == SOAP_FACULA ? 1 : 0]) + m0;
         T tmp[PB][R];
 #pragma unroll
         for (int p = 0; p < PB; p++)
@@ -114,7 +137,7 @@ __device__ __forceinline__ void contract_tile(int64_t n_px, const Rows<T>& rows,
         }
 #pragma unroll
         for (int r = 0; r < R; r++) {
-            const T cr = eff == SOAP_EFFECT_BCONV ? T(1) : contrast[(int64_t)cl * n_px + mcl[r]];
+            const T cr = eff == SOAP_EFFECT_BCONV ? T(1) : con.at(cl, mcl[r]);
 #pragma unroll
             for (int p = 0; p < PB; p++) acc[p][r] = fma(cr, tmp[p][r], acc[p][r]);
         }

@@ -159,7 +159,7 @@ struct soap_ctx {
 
     // batched form: grow-only buffers, the captured graph and the key of what it baked in
     soap::DevBuf b_items, b_regions, b_phases, b_phase_item, b_phase_block, b_pblocks, b_order;
-    soap::DevBuf b_cellIfx, b_IB, b_colj, b_colw, b_kq, b_qtoff, b_qgs, b_qc32, b_fq, b_con;
+    soap::DevBuf b_cellIfx, b_IB, b_colj, b_colw, b_kq, b_qtoff, b_qgs, b_qc32, b_fq;
     soap::DevBuf b_geo, b_kfix, b_counters, b_toff, b_gstart, b_coefs, b_ticket;
     cudaGraphExec_t b_graph_exec = nullptr;
     std::vector<uint64_t> b_graph_key;
@@ -203,9 +203,10 @@ soap_status toeplitz_active(soap_ctx* c, const RegionDev* regions_host, int n_re
                             const double* phases_host, int n_phases, uint32_t effects,
                             int precision, void* dst);
 
-// Batched form (batch.cu); variant in 0 .. batch_num_variants() - 1, out [n_phases][n_px] FP32.
+// Batched form (batch.cu); variant in 0 .. batch_num_variants() - 1, out [n_phases][n_px] FP32
+// (F, or F - F_q when residual).
 soap_status batch_run(soap_ctx* c, const soap_batch_item* items, int n_items, const soap_region* regions,
-                      int n_regions, const double* phases, int n_phases, int variant, float* out);
+                      int n_regions, const double* phases, int n_phases, int variant, int residual, float* out);
 int batch_num_variants();
 int batch_default_variant();
 void batch_variant_info(int v, int* phases_per_block, int* px_per_thread);

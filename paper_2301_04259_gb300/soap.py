@@ -23,6 +23,7 @@ SOAP_FP64, SOAP_FP32 = 0, 1
 SOAP_FORM_TOEPLITZ, SOAP_FORM_DIRECT = 0, 1
 SOAP_EFFECT_TOT, SOAP_EFFECT_FLUX, SOAP_EFFECT_BCONV = 1, 2, 4
 SOAP_SPOT, SOAP_FACULA = 1, 2
+SOAP_BATCH_SPECTRUM, SOAP_BATCH_RESIDUAL = 0, 1
 SOAP_MAX_REGIONS, SOAP_MAX_CLASSES, SOAP_MAX_MU, SOAP_MAX_TAPS = 64, 8, 64, 256
 TIMERS = ("geometry", "pad_rows", "contrast", "phase_hist", "regions", "contract", "contract_quiet",
           "direct", "ccf", "fit")
@@ -87,7 +88,7 @@ def _load():
         "soap_get_launch_count": (i32, [P, ctypes.POINTER(ctypes.c_uint64)]),
         "soap_rv_ccf_static": (i32, [d, d, i64, P, i32, i32, P, P, i32, d, d, d, i32, P, P, P, P]),
         "soap_active_batch": (i32, [P, ctypes.POINTER(soap_batch_item), i32, ctypes.POINTER(soap_region), i32,
-                                    P, i32, P, ctypes.c_int]),
+                                    P, i32, i32, P, ctypes.c_int]),
         "soap_batch_num_variants": (i32, [ctypes.POINTER(i32)]),
         "soap_batch_variant_info": (i32, [i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
         "soap_batch_set_variant": (i32, [P, i32]),
@@ -280,14 +281,16 @@ def batch_items_array(items: Sequence) -> ctypes.Array:
     return arr
 
 
-def soap_active_batch(ctx, items: Sequence, regions: Sequence, phases, out) -> None:
-    """out: float32 [n_phases, n_px], host (numpy) or device (torch)."""
+def soap_active_batch(ctx, items: Sequence, regions: Sequence, phases, out,
+                      output: int = 0) -> None:
+    """out: float32 [n_phases, n_px], host (numpy) or device (torch); output SOAP_BATCH_SPECTRUM
+    (F) or SOAP_BATCH_RESIDUAL (F - F_q)."""
     ia = batch_items_array(items)
     ra = regions_array(regions)
     ph = np.ascontiguousarray(phases, dtype=np.float64)
     ptr, dev = _ptr(out)
     _check(_lib.soap_active_batch(ctx, ia, len(items), ra, len(regions), ctypes.c_void_p(ph.ctypes.data),
-                                  ph.size, ptr, dev), "soap_active_batch")
+                                  ph.size, int(output), ptr, dev), "soap_active_batch")
 
 
 def soap_batch_num_variants() -> int:

@@ -261,3 +261,33 @@ def test_batch_autotune_and_cache(S, small, tmp_path):
         e2 = tuning.tune_batch(d.ctx, small.star, items, regions, phases, out, path=path)
         assert e2["source"] == "cache" and e2["variant"] == e1["variant"]
         assert S.soap_batch_get_variant(d.ctx) == e1["variant"]
+
+
+def test_batch_many_temperatures_and_residual_output(S, small):
+    """More distinct (type, temperature) pairs over the batch than one item may hold: each item
+    against the oracle; the residual output equals the spectrum minus the item's quiet star."""
+    temps = np.linspace(3800.0, 5600.0, 12)
+    cfgs = [synth.BatchConfig(2.0 + 0.5 * k, 40.0 + 4 * k,
+                              [Region(FACULA, -15.0 + 3 * k, 20.0 * k, 0.18, 6000.0 + 10 * k),
+                               Region(SPOT, -15.0 + 3 * k, 20.0 * k, 0.06 + 0.005 * k, t)], 2)
+            for k, t in enumerate(temps)]
+    items, regions, phases = synth.batch_layout(cfgs)
+    quiet_items = [(v, inc, 0, 0, fp, n) for (v, inc, fr, nr, fp, n) in items]
+    n_px = small.star.n_px
+    with _disk(S, small) as d:
+        spec = torch.empty((phases.size, n_px), dtype=torch.float32, device=DEV)
+        res = torch.empty_like(spec)
+        quiet = torch.empty_like(spec)
+        S.soap_active_batch(d.ctx, items, regions, phases, spec, output=S.SOAP_BATCH_SPECTRUM)
+        S.soap_active_batch(d.ctx, items, regions, phases, res, output=S.SOAP_BATCH_RESIDUAL)
+        S.soap_active_batch(d.ctx, quiet_items, [], phases, quiet, output=S.SOAP_BATCH_SPECTRUM)
+        S.soap_synchronize(d.ctx)
+    g = spec.double().cpu().numpy()
+    scale = O.quiet(small.star, small.quiet).max()
+    for cfg, it in zip(cfgs, items):
+        fp, n = it[4], it[5]
+        ref = _oracle_rows(small, cfg, phases[fp:fp + n])
+        assert np.abs(g[fp:fp + n] - ref).max() / scale <= TOL32, cfg
+    diff = (spec.double() - quiet.double() - res.double()).abs().max().item() / scale
+    assert diff <= 1e-6
+    assert res.abs().max().item() > 1e-3 * scale                  # the regions do change the flux
