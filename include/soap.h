@@ -361,6 +361,78 @@ soap_status soap_gemm_bf16_tn(int32_t M, int32_t N, int32_t K, const void* A, in
                               const void* B, int64_t ldb, const float* bias, int32_t activation,
                               float* C, int64_t ldc, void* cuda_stream);
 
+/* ---------------------------------------------------------------------------------------
+ * Learned surrogate (no counterpart in the paper).  A network maps 8 active-region parameters
+ *   x = (spot latitude deg, spot longitude deg, spot radius R*, spot temperature K, phase,
+ *        inclination deg, vsini km/s, facula filling)
+ * to 128 PCA coefficients of the residual spectrum F - F_q (soap_active_batch with
+ * SOAP_BATCH_RESIDUAL) and to log10 of its own RV error in cm/s.  Inputs are scaled linearly to
+ * [-1, 1] from the ranges given at creation; a query outside them, or with a predicted error
+ * above the caller's threshold, is not accepted and belongs to the plain method.
+ * Network: 8 -> 4 x 256 (GELU, erf form) -> 129; BF16 weights and activations as tensor-core
+ * operands with FP32 accumulation; FP32 master weights; Adam (beta 0.9, 0.999, eps 1e-8).
+ * Flat parameter order: W1 [256][8], b1, W2 [256][256], b2, W3, b3, W4, b4, W5 [129][256], b5;
+ * output 128 of the last layer is the RV-error head.
+ * ------------------------------------------------------------------------------------- */
+typedef struct soap_surrogate soap_surrogate;
+
+typedef struct {
+    int32_t n_in;          /* 8 */
+    int32_t hidden;        /* 256 */
+    int32_t n_hidden;      /* 4 */
+    int32_t n_coef;        /* 128 */
+    int32_t batch;         /* training rows per step, a positive multiple of 128 */
+    const float* in_lo;    /* host [n_in] lower ends of the input ranges */
+    const float* in_hi;    /* host [n_in] upper ends */
+} soap_surrogate_desc;
+
+soap_status soap_surrogate_create(const soap_surrogate_desc* desc, void* cuda_stream, soap_surrogate** out);
+soap_status soap_surrogate_num_params(const soap_surrogate* s, int64_t* n);
+/* Host float32 [n_params] in the flat order above; set_params also clears the Adam state. */
+soap_status soap_surrogate_set_params(soap_surrogate* s, const float* flat);
+soap_status soap_surrogate_get_params(soap_surrogate* s, float* flat);
+/* Targets are standardised coefficients: c = y * coef_std + coef_mean (host [n_coef] each). */
+soap_status soap_surrogate_set_scaling(soap_surrogate* s, const float* coef_mean, const float* coef_std);
+/* Loss and gradients of one batch (n = batch rows; x device [n][8] raw inputs, t device [n][129]
+ * targets: standardised coefficients and log10 RV error), L = sum_b sum_j w_j (y - t)^2 / n with
+ * w_out host [129].  loss host, grads host [n_params].  For checking the backward pass. */
+soap_status soap_surrogate_gradients(soap_surrogate* s, const float* x, const float* t, int32_t n,
+                                     const float* w_out, double* loss, float* grads);
+/* Adam over `epochs` passes of shuffled full batches of (x, t) (device, as above; rows beyond
+ * the last full batch of an epoch are skipped).  lr_per_epoch host [epochs]; stage 0 trains
+ * everything except the RV-error head, stage 1 only the head.  loss_per_epoch host [epochs]
+ * or NULL.  One training step is a CUDA graph replayed per batch. */
+soap_status soap_surrogate_train(soap_surrogate* s, const float* x, const float* t, int64_t n, int32_t epochs,
+                                 const float* lr_per_epoch, const float* w_out, int32_t stage, uint64_t seed,
+                                 double* loss_per_epoch);
+/* Network outputs for n queries x (device [n][8]): coefficients in data units (device [n][128]
+ * or NULL), predicted RV error in cm/s (device [n] or NULL) and acceptance (device uint8 [n] or
+ * NULL: 1 if every input is inside its range and the predicted error <= rv_err_max_cms). */
+soap_status soap_surrogate_predict(soap_surrogate* s, const float* x, int64_t n, float rv_err_max_cms,
+                                   float* coef, float* pred_err_cms, uint8_t* accepted);
+/* PCA basis of the residuals: mean device [n_px], basis device [n_coef][n_px] (orthonormal rows). */
+soap_status soap_surrogate_set_basis(soap_surrogate* s, const float* mean, const float* basis, int64_t n_px);
+/* Residual spectra mean + coef . basis for device coef [n][128] into device out [n][n_px]; both
+ * factors split into BF16 high and low parts on the tensor cores (error ~1e-5 of |coef| |basis|). */
+soap_status soap_surrogate_reconstruct(soap_surrogate* s, const float* coef, int64_t n, float* out);
+/* predict + reconstruct: out device [n][n_px] residual spectra for every query (accepted or
+ * not), accepted device uint8 [n] (required), pred_err_cms device [n] or NULL.  The caller
+ * replaces the rows that were not accepted with the plain method's. */
+soap_status soap_surrogate_query(soap_surrogate* s, const float* x, int64_t n, float rv_err_max_cms, float* out,
+                                 float* pred_err_cms, uint8_t* accepted);
+void soap_surrogate_free(soap_surrogate* s);
+
+/* PCA by randomized SVD with n_power power iterations (Halko, Martinsson & Tropp 2011):
+ * X device [n][p] float32 rows, omega device [p][l] a Gaussian test matrix (the caller draws it),
+ * k <= l <= 512 components kept.  mean device [p], basis device [k][p] (orthonormal rows, in
+ * decreasing singular value), sv host [k] singular values of the centred data or NULL.
+ * Synchronises the stream. */
+soap_status soap_pca_fit(const float* X, int64_t n, int64_t p, const float* omega, int32_t l, int32_t k,
+                         int32_t n_power, float* mean, float* basis, double* sv, void* cuda_stream);
+/* coef device [n][k] = (X - mean) basis^T. */
+soap_status soap_pca_project(const float* X, int64_t n, int64_t p, const float* mean, const float* basis,
+                             int32_t k, float* coef, void* cuda_stream);
+
 /* Number of kernels this context has launched so far (for launch accounting). */
 soap_status soap_get_launch_count(const soap_ctx* ctx, uint64_t* out);
 

@@ -53,6 +53,12 @@ class soap_batch_item(ctypes.Structure):
                 ("first_phase", ctypes.c_int32), ("n_phases", ctypes.c_int32)]
 
 
+class soap_surrogate_desc(ctypes.Structure):
+    _fields_ = [("n_in", ctypes.c_int32), ("hidden", ctypes.c_int32), ("n_hidden", ctypes.c_int32),
+                ("n_coef", ctypes.c_int32), ("batch", ctypes.c_int32),
+                ("in_lo", ctypes.POINTER(ctypes.c_float)), ("in_hi", ctypes.POINTER(ctypes.c_float))]
+
+
 class soap_star_info(ctypes.Structure):
     _fields_ = [("n_visible", ctypes.c_int64), ("tap_min", ctypes.c_int32),
                 ("n_taps", ctypes.c_int32), ("delta", ctypes.c_double),
@@ -96,6 +102,20 @@ def _load():
         "soap_batch_autotune": (i32, [P, ctypes.POINTER(soap_batch_item), i32, ctypes.POINTER(soap_region), i32,
                                       P, i32, P, i32, P, ctypes.POINTER(i32)]),
         "soap_gemm_bf16_tn": (i32, [i32, i32, i32, P, i64, P, i64, P, i32, P, i64, P]),
+        "soap_surrogate_create": (i32, [ctypes.POINTER(soap_surrogate_desc), P, ctypes.POINTER(P)]),
+        "soap_surrogate_num_params": (i32, [P, ctypes.POINTER(i64)]),
+        "soap_surrogate_set_params": (i32, [P, P]),
+        "soap_surrogate_get_params": (i32, [P, P]),
+        "soap_surrogate_set_scaling": (i32, [P, P, P]),
+        "soap_surrogate_gradients": (i32, [P, P, P, i32, P, ctypes.POINTER(d), P]),
+        "soap_surrogate_train": (i32, [P, P, P, i64, i32, P, P, i32, ctypes.c_uint64, P]),
+        "soap_surrogate_predict": (i32, [P, P, i64, ctypes.c_float, P, P, P]),
+        "soap_surrogate_set_basis": (i32, [P, P, P, i64]),
+        "soap_surrogate_reconstruct": (i32, [P, P, i64, P]),
+        "soap_surrogate_query": (i32, [P, P, i64, ctypes.c_float, P, P, P]),
+        "soap_surrogate_free": (None, [P]),
+        "soap_pca_fit": (i32, [P, i64, i64, P, i32, i32, i32, P, P, P, P]),
+        "soap_pca_project": (i32, [P, i64, i64, P, P, i32, P, P]),
         "soap_free": (None, [P]),
         "soap_last_error": (ctypes.c_char_p, []),
     }
@@ -362,6 +382,127 @@ def soap_free(ctx) -> None:
 
 def soap_last_error() -> str:
     return _lib.soap_last_error().decode()
+
+
+# ---------------------------------------------------------------------------------------
+# surrogate (device arrays are torch CUDA tensors, host arrays numpy)
+# ---------------------------------------------------------------------------------------
+def _dev(t, dtype=None):
+    if t is None:
+        return None
+    if not (hasattr(t, "is_cuda") and t.is_cuda) or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    if dtype is not None and str(t.dtype) != dtype:
+        raise ValueError(f"expected {dtype}, got {t.dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _host(a, dtype):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, ctypes.c_void_p(a.ctypes.data)
+
+
+def soap_surrogate_create(in_lo, in_hi, batch: int, stream=None, n_in=8, hidden=256, n_hidden=4,
+                          n_coef=128) -> ctypes.c_void_p:
+    lo = np.ascontiguousarray(in_lo, np.float32)
+    hi = np.ascontiguousarray(in_hi, np.float32)
+    d = soap_surrogate_desc(n_in=n_in, hidden=hidden, n_hidden=n_hidden, n_coef=n_coef, batch=int(batch),
+                            in_lo=lo.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                            in_hi=hi.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+    out = ctypes.c_void_p()
+    _check(_lib.soap_surrogate_create(ctypes.byref(d), _stream_handle(stream), ctypes.byref(out)),
+           "soap_surrogate_create")
+    return out
+
+
+def soap_surrogate_num_params(s) -> int:
+    n = ctypes.c_int64()
+    _check(_lib.soap_surrogate_num_params(s, ctypes.byref(n)), "soap_surrogate_num_params")
+    return int(n.value)
+
+
+def soap_surrogate_set_params(s, flat) -> None:
+    a, p = _host(flat, np.float32)
+    _check(_lib.soap_surrogate_set_params(s, p), "soap_surrogate_set_params")
+
+
+def soap_surrogate_get_params(s) -> np.ndarray:
+    out = np.empty(soap_surrogate_num_params(s), np.float32)
+    _check(_lib.soap_surrogate_get_params(s, ctypes.c_void_p(out.ctypes.data)), "soap_surrogate_get_params")
+    return out
+
+
+def soap_surrogate_set_scaling(s, coef_mean, coef_std) -> None:
+    m, pm = _host(coef_mean, np.float32)
+    sd, ps = _host(coef_std, np.float32)
+    _check(_lib.soap_surrogate_set_scaling(s, pm, ps), "soap_surrogate_set_scaling")
+
+
+def soap_surrogate_gradients(s, x, t, w_out):
+    """(loss, flat gradients) of one batch; x [n, 8] and t [n, 129] float32 CUDA tensors."""
+    w, pw = _host(w_out, np.float32)
+    loss = ctypes.c_double()
+    g = np.empty(soap_surrogate_num_params(s), np.float32)
+    _check(_lib.soap_surrogate_gradients(s, _dev(x, "torch.float32"), _dev(t, "torch.float32"), int(x.shape[0]),
+                                         pw, ctypes.byref(loss), ctypes.c_void_p(g.ctypes.data)),
+           "soap_surrogate_gradients")
+    return float(loss.value), g
+
+
+def soap_surrogate_train(s, x, t, epochs: int, lr, w_out, stage: int = 0, seed: int = 0) -> np.ndarray:
+    lr = np.broadcast_to(np.asarray(lr, np.float32), (int(epochs),))
+    lr, plr = _host(lr, np.float32)
+    w, pw = _host(w_out, np.float32)
+    losses = np.zeros(max(1, int(epochs)), np.float64)
+    _check(_lib.soap_surrogate_train(s, _dev(x, "torch.float32"), _dev(t, "torch.float32"), int(x.shape[0]),
+                                     int(epochs), plr, pw, int(stage), ctypes.c_uint64(int(seed)),
+                                     ctypes.c_void_p(losses.ctypes.data)), "soap_surrogate_train")
+    return losses[:int(epochs)]
+
+
+def soap_surrogate_predict(s, x, rv_err_max_cms: float, coef=None, pred_err=None, accepted=None) -> None:
+    _check(_lib.soap_surrogate_predict(s, _dev(x, "torch.float32"), int(x.shape[0]), float(rv_err_max_cms),
+                                       _dev(coef), _dev(pred_err), _dev(accepted)), "soap_surrogate_predict")
+
+
+def soap_surrogate_set_basis(s, mean, basis) -> None:
+    _check(_lib.soap_surrogate_set_basis(s, _dev(mean, "torch.float32"), _dev(basis, "torch.float32"),
+                                         int(mean.shape[0])), "soap_surrogate_set_basis")
+
+
+def soap_surrogate_reconstruct(s, coef, out) -> None:
+    _check(_lib.soap_surrogate_reconstruct(s, _dev(coef, "torch.float32"), int(coef.shape[0]),
+                                           _dev(out, "torch.float32")), "soap_surrogate_reconstruct")
+
+
+def soap_surrogate_query(s, x, rv_err_max_cms: float, out, accepted, pred_err=None) -> None:
+    _check(_lib.soap_surrogate_query(s, _dev(x, "torch.float32"), int(x.shape[0]), float(rv_err_max_cms),
+                                     _dev(out, "torch.float32"), _dev(pred_err), _dev(accepted, "torch.uint8")),
+           "soap_surrogate_query")
+
+
+def soap_surrogate_free(s) -> None:
+    _lib.soap_surrogate_free(s)
+
+
+def soap_pca_fit(X, omega, k: int, n_power: int = 2, stream=None):
+    """(mean [p], basis [k, p], singular values [k]) of the rows of X [n, p] (CUDA float32)."""
+    import torch
+    n, p = X.shape
+    l = omega.shape[1]
+    mean = torch.empty(p, dtype=torch.float32, device=X.device)
+    basis = torch.empty((k, p), dtype=torch.float32, device=X.device)
+    sv = np.zeros(k, np.float64)
+    _check(_lib.soap_pca_fit(_dev(X, "torch.float32"), n, p, _dev(omega, "torch.float32"), int(l), int(k),
+                             int(n_power), _dev(mean), _dev(basis), ctypes.c_void_p(sv.ctypes.data),
+                             _stream_handle(stream)), "soap_pca_fit")
+    return mean, basis, sv
+
+
+def soap_pca_project(X, mean, basis, out, stream=None) -> None:
+    _check(_lib.soap_pca_project(_dev(X, "torch.float32"), X.shape[0], X.shape[1], _dev(mean, "torch.float32"),
+                                 _dev(basis, "torch.float32"), basis.shape[0], _dev(out, "torch.float32"),
+                                 _stream_handle(stream)), "soap_pca_project")
 
 
 # ---------------------------------------------------------------------------------------

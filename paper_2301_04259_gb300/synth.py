@@ -271,3 +271,54 @@ def velocity_grid(vsini_kms: float, step_kms: float = 0.25, margin_kms: float = 
     half = vsini_kms + margin_kms
     n_v = int(np.floor(2 * half / step_kms + 1e-9)) + 1
     return -half, step_kms, n_v
+
+
+# ----------------------------------------------------------------------------------
+# learned surrogate: query parameters, their batch layout, initial weights
+# ----------------------------------------------------------------------------------
+# inputs: spot latitude (deg), spot longitude (deg), spot radius (R*), spot temperature (K),
+# phase, inclination (deg), vsini (km/s), facula filling (facula area / spot area around it)
+SURROGATE_INPUTS = ("lat_deg", "lon_deg", "radius_rstar", "spot_temp_K", "phase", "incl_deg", "vsini_kms",
+                    "facula_filling")
+SURROGATE_LO = np.array([-60.0, 0.0, 0.01, 3800.0, 0.0, 30.0, 1.0, 0.0])
+SURROGATE_HI = np.array([60.0, 360.0, 0.2, 5600.0, 1.0, 90.0, 10.0, 3.0])
+SURROGATE_FACULA_TEMP = 6100.0
+
+
+def surrogate_params(seed: int, n: int) -> np.ndarray:
+    """n query vectors drawn uniformly inside the surrogate's input ranges, float32 [n, 8]."""
+    rng = np.random.default_rng(seed)
+    return (SURROGATE_LO + (SURROGATE_HI - SURROGATE_LO) * rng.uniform(size=(n, 8))).astype(np.float32)
+
+
+def surrogate_layout(params):
+    """(items, regions, phases) of the batched method for query vectors: one item per query with
+    one phase; a facula of area (1 + filling) x the spot's, centred on it and listed first (the
+    spot keeps its cells), when filling > 0, then the spot."""
+    items, regions, phases = [], [], []
+    for k, q in enumerate(np.asarray(params, np.float64)):
+        lat, lon, r, t_spot, ph, inc, vs, fill = q
+        regs = []
+        if fill > 0:
+            regs.append(Region(FACULA, lat, lon, min(1.0, r * np.sqrt(1.0 + fill)), SURROGATE_FACULA_TEMP))
+        regs.append(Region(SPOT, lat, lon, r, t_spot))
+        items.append((vs, inc, len(regions), len(regs), k, 1))
+        regions.extend(regs)
+        phases.append(ph)
+    return items, regions, np.asarray(phases, np.float64)
+
+
+def surrogate_init(seed: int, shapes=((256, 8), (256, 256), (256, 256), (256, 256), (129, 256))) -> np.ndarray:
+    """Initial weights, flat [W1 | b1 | ... ]: normal with variance 2/in (hidden layers) and
+    1/in (output layer), zero biases."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for l, (o, i) in enumerate(shapes):
+        sd = np.sqrt((1.0 if l == len(shapes) - 1 else 2.0) / i)
+        parts += [rng.normal(0.0, sd, o * i), np.zeros(o)]
+    return np.concatenate(parts).astype(np.float32)
+
+
+def gaussian_test_matrix(seed: int, p: int, l: int) -> np.ndarray:
+    """Standard normal test matrix [p, l] (float32) for the randomized PCA."""
+    return np.random.default_rng(seed).standard_normal((p, l)).astype(np.float32)
