@@ -400,8 +400,8 @@ soap_status soap_surrogate_gradients(soap_surrogate* s, const float* x, const fl
                                      const float* w_out, double* loss, float* grads);
 /* Adam over `epochs` passes of shuffled full batches of (x, t) (device, as above; rows beyond
  * the last full batch of an epoch are skipped).  lr_per_epoch host [epochs]; stage 0 trains
- * everything except the RV-error head, stage 1 only the head.  loss_per_epoch host [epochs]
- * or NULL.  One training step is a CUDA graph replayed per batch. */
+ * everything except the RV-error head, stage 1 only the head, stage 2 everything.
+ * loss_per_epoch host [epochs] or NULL.  One training step is a CUDA graph replayed per batch. */
 soap_status soap_surrogate_train(soap_surrogate* s, const float* x, const float* t, int64_t n, int32_t epochs,
                                  const float* lr_per_epoch, const float* w_out, int32_t stage, uint64_t seed,
                                  double* loss_per_epoch);
@@ -410,6 +410,10 @@ soap_status soap_surrogate_train(soap_surrogate* s, const float* x, const float*
  * NULL: 1 if every input is inside its range and the predicted error <= rv_err_max_cms). */
 soap_status soap_surrogate_predict(soap_surrogate* s, const float* x, int64_t n, float rv_err_max_cms,
                                    float* coef, float* pred_err_cms, uint8_t* accepted);
+/* Take the predicted RV error from output n_coef of another network of the same shape and
+ * input ranges (trained with stage 2 on the judged errors), instead of this network's own head;
+ * NULL restores the own head.  The judge must outlive its use. */
+soap_status soap_surrogate_set_judge(soap_surrogate* s, soap_surrogate* judge);
 /* PCA basis of the residuals: mean device [n_px], basis device [n_coef][n_px] (orthonormal rows). */
 soap_status soap_surrogate_set_basis(soap_surrogate* s, const float* mean, const float* basis, int64_t n_px);
 /* Residual spectra mean + coef . basis for device coef [n][128] into device out [n][n_px]; both
@@ -421,6 +425,9 @@ soap_status soap_surrogate_reconstruct(soap_surrogate* s, const float* coef, int
 soap_status soap_surrogate_query(soap_surrogate* s, const float* x, int64_t n, float rv_err_max_cms, float* out,
                                  float* pred_err_cms, uint8_t* accepted);
 void soap_surrogate_free(soap_surrogate* s);
+
+/* y[i] += alpha x[i] for device float arrays of n elements (asynchronous on the stream). */
+soap_status soap_axpy_f32(int64_t n, float alpha, const float* x, float* y, void* cuda_stream);
 
 /* PCA by randomized SVD with n_power power iterations (Halko, Martinsson & Tropp 2011):
  * X device [n][p] float32 rows, omega device [p][l] a Gaussian test matrix (the caller draws it),

@@ -251,9 +251,9 @@ constexpr int kBatchThreads = 128;
 struct BatchVariant {
     int PB, R;
 };
-static const BatchVariant kVariants[] = {{4, 2}, {4, 4}, {8, 2}, {8, 4}, {16, 2}, {16, 4}};
+static const BatchVariant kVariants[] = {{1, 4}, {2, 4}, {4, 2}, {4, 4}, {8, 2}, {8, 4}, {16, 2}, {16, 4}};
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
-constexpr int kDefaultVariant = 1;
+constexpr int kDefaultVariant = 3;
 
 // Sizes of one batch, fixed by the host preparation and baked into the captured graph.
 struct BatchShape {
@@ -354,11 +354,13 @@ static soap_status enqueue_batch(soap_ctx* c, const BatchShape& b, float* out) {
     const float* a0 = c->active_set[0] ? c->a32[0] : c->a32[1];
     const float* a1 = c->active_set[1] ? c->a32[1] : c->a32[0];
     switch (b.variant) {
-        case 0: return launch_batch_contract<4, 2>(c, b, a0, a1, out);
-        case 1: return launch_batch_contract<4, 4>(c, b, a0, a1, out);
-        case 2: return launch_batch_contract<8, 2>(c, b, a0, a1, out);
-        case 3: return launch_batch_contract<8, 4>(c, b, a0, a1, out);
-        case 4: return launch_batch_contract<16, 2>(c, b, a0, a1, out);
+        case 0: return launch_batch_contract<1, 4>(c, b, a0, a1, out);
+        case 1: return launch_batch_contract<2, 4>(c, b, a0, a1, out);
+        case 2: return launch_batch_contract<4, 2>(c, b, a0, a1, out);
+        case 3: return launch_batch_contract<4, 4>(c, b, a0, a1, out);
+        case 4: return launch_batch_contract<8, 2>(c, b, a0, a1, out);
+        case 5: return launch_batch_contract<8, 4>(c, b, a0, a1, out);
+        case 6: return launch_batch_contract<16, 2>(c, b, a0, a1, out);
         default: return launch_batch_contract<16, 4>(c, b, a0, a1, out);
     }
 }

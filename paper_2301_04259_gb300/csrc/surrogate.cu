@@ -90,6 +90,7 @@ struct soap_surrogate {
     int64_t n_px = 0;
     float* mu = nullptr;                      // [n_px]
     bf16* vsplit = nullptr;                   // [n_px][3 n_coef]: V_hi | V_lo | V_hi
+    soap_surrogate* judge = nullptr;          // network whose output n_coef predicts the RV error
 };
 
 namespace soap {
@@ -163,7 +164,7 @@ __global__ void k_bias_grad(BiasJobs jobs, int B) {
 
 // Adam (Kingma & Ba 2015, Algorithm 1) over the flat parameters, then the BF16 copies W and
 // W^T.  mode 0 updates everything except the RV-error head (row n_coef of the last layer and its
-// bias), mode 1 only the head.
+// bias), mode 1 only the head, mode 2 everything.
 __global__ void k_adam(float* __restrict__ P, const float* __restrict__ G, float* __restrict__ M,
                        float* __restrict__ V, int64_t n, const int* __restrict__ d_step, const float* __restrict__ d_lr,
                        float b1, float b2, float eps, int mode, int64_t head_w0, int head_len, int64_t head_b,
@@ -172,8 +173,8 @@ __global__ void k_adam(float* __restrict__ P, const float* __restrict__ G, float
     const float lr = d_lr[0];
     const float c1 = 1.0f - powf(b1, (float)t), c2 = 1.0f - powf(b2, (float)t);
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-        const bool head = (e >= head_w0 && e < head_w0 + head_len) || e == head_b;
-        if (head != (mode == 1)) continue;
+            const bool head = (e >= head_w0 && e < head_w0 + head_len) || e == head_b;
+        if (mode != 2 && head != (mode == 1)) continue;
         const float g = G[e];
         const float m = b1 * M[e] + (1.0f - b1) * g;
         const float v = b2 * V[e] + (1.0f - b2) * g * g;
@@ -227,7 +228,8 @@ __global__ void k_query_in(const float* __restrict__ x, int64_t n, int n_in, con
 
 // Network outputs -> coefficients in data units, predicted RV error (cm/s), acceptance, and the
 // split-BF16 rows [c_hi c_hi c_lo] for the reconstruction GEMM.
-__global__ void k_query_out(const float* __restrict__ Y, int ldy, int64_t n, int n_coef, const float* __restrict__ mean,
+__global__ void k_query_out(const float* __restrict__ Y, int ldy, const float* __restrict__ Yerr, int ldyerr,
+                            int64_t n, int n_coef, const float* __restrict__ mean,
                             const float* __restrict__ sd, float thr_cms, uint8_t* __restrict__ accept,
                             float* __restrict__ pred_err, float* __restrict__ coef_out, bf16* __restrict__ split) {
     const int64_t n_el = n * (n_coef + 1);
@@ -236,7 +238,7 @@ __global__ void k_query_out(const float* __restrict__ Y, int ldy, int64_t n, int
         const int j = (int)(e % (n_coef + 1));
         const float y = Y[r * ldy + j];
         if (j == n_coef) {
-            const float err = exp10f(y);
+            const float err = exp10f(Yerr[r * ldyerr + j]);
             if (pred_err) pred_err[r] = err;
             if (accept) accept[r] = (accept[r] && err <= thr_cms) ? 1 : 0;
             continue;
@@ -346,6 +348,11 @@ static soap_status sgemm(int M, int N, int64_t K, float alpha, const float* A, i
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) { set_error("sgemm launch failed: %s", cudaGetErrorString(e)); return SOAP_ECUDA; }
     return SOAP_OK;
+}
+
+__global__ void k_axpy(int64_t n, float alpha, const float* __restrict__ x, float* __restrict__ y) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        y[e] = fmaf(alpha, x[e], y[e]);
 }
 
 // column means of X [n][p] (FP64 accumulation)
@@ -564,12 +571,27 @@ static soap_status ensure_query(soap_surrogate* s, int rows) {
     return SOAP_OK;
 }
 
+// The judge network (if any) runs on the same scaled inputs, on the main network's stream.
+static soap_status judge_forward(soap_surrogate* s, const bf16* X0, int m) {
+    if (!s->judge) return SOAP_OK;
+    soap_surrogate* j = s->judge;
+    SOAP_TRY(ensure_query(j, s->q_cap));
+    const cudaStream_t saved = j->stream;
+    j->stream = s->stream;
+    const soap_status st = forward(j, X0, m, false, j->qy);
+    j->stream = saved;
+    return st;
+}
+
 static soap_status check(soap_surrogate* s) {
-    unsigned int h = 0;
+    unsigned int h = 0, hj = 0;
     SOAP_CUDA(cudaMemcpyAsync(&h, s->flags, sizeof(h), cudaMemcpyDeviceToHost, s->stream));
+    if (s->judge) SOAP_CUDA(cudaMemcpyAsync(&hj, s->judge->flags, sizeof(hj), cudaMemcpyDeviceToHost, s->stream));
     SOAP_CUDA(cudaStreamSynchronize(s->stream));
+    h |= hj;
     if (h) {
         SOAP_CUDA(cudaMemsetAsync(s->flags, 0, sizeof(unsigned int), s->stream));
+        if (s->judge) SOAP_CUDA(cudaMemsetAsync(s->judge->flags, 0, sizeof(unsigned int), s->stream));
         set_error("a tensor-core kernel gave up waiting (status 0x%x)", h);
         return SOAP_ETIMEOUT;
     }
@@ -742,7 +764,7 @@ soap_status soap_surrogate_train(soap_surrogate* s, const float* x, const float*
                                  double* loss_per_epoch) {
     clear_error();
     if (!s || !x || !t || !lr_per_epoch || !w_out) { set_error("NULL argument"); return SOAP_EINVAL; }
-    if (stage != 0 && stage != 1) { set_error("stage must be 0 (network) or 1 (RV-error head)"); return SOAP_EINVAL; }
+    if (stage < 0 || stage > 2) { set_error("stage must be 0 (all but the RV-error head), 1 (head) or 2 (all)"); return SOAP_EINVAL; }
     const int B = s->batch;
     const int64_t steps64 = n / B;
     if (steps64 < 1 || steps64 > (1 << 24)) { set_error("need at least one full batch of %d rows", B); return SOAP_EINVAL; }
@@ -823,9 +845,11 @@ soap_status soap_surrogate_predict(soap_surrogate* s, const float* x, int64_t n,
         k_query_in<<<grid1(m), 256, 0, s->stream>>>(x + r0 * s->n_in, m, s->n_in, s->d_lohi, X0,
                                                     accepted ? accepted + r0 : nullptr);
         st = forward(s, X0, m, false, s->qy);
+        if (st == SOAP_OK) st = judge_forward(s, X0, m);
         if (st != SOAP_OK) break;
+        const float* ye = s->judge ? s->judge->qy : s->qy;
         k_query_out<<<grid1((int64_t)m * (s->n_coef + 1)), 256, 0, s->stream>>>(
-            s->qy, s->n_out_pad, m, s->n_coef, s->coef_mean, s->coef_std, rv_err_max_cms,
+            s->qy, s->n_out_pad, ye, s->n_out_pad, m, s->n_coef, s->coef_mean, s->coef_std, rv_err_max_cms,
             accepted ? accepted + r0 : nullptr, pred_err_cms ? pred_err_cms + r0 : nullptr,
             coef ? coef + r0 * s->n_coef : nullptr, s->qsplit);
     }
@@ -834,6 +858,20 @@ soap_status soap_surrogate_predict(soap_surrogate* s, const float* x, int64_t n,
     SOAP_CUDA(cudaGetLastError());
     if (st != SOAP_OK) return st;
     return check(s);
+}
+
+soap_status soap_surrogate_set_judge(soap_surrogate* s, soap_surrogate* judge) {
+    clear_error();
+    if (!s) { set_error("NULL argument"); return SOAP_EINVAL; }
+    if (judge == s) { set_error("a network cannot judge itself"); return SOAP_EINVAL; }
+    if (judge) {
+        for (int i = 0; i < s->n_in; i++)
+            if (judge->lo[i] != s->lo[i] || judge->hi[i] != s->hi[i]) {
+                set_error("the judge network must use the same input ranges"); return SOAP_EINVAL;
+            }
+    }
+    s->judge = judge;
+    return SOAP_OK;
 }
 
 soap_status soap_surrogate_set_basis(soap_surrogate* s, const float* mean, const float* basis, int64_t n_px) {
@@ -867,10 +905,12 @@ soap_status soap_surrogate_query(soap_surrogate* s, const float* x, int64_t n, f
         const int m = (int)std::min<int64_t>(chunk, n - r0);
         k_query_in<<<grid1(m), 256, 0, s->stream>>>(x + r0 * s->n_in, m, s->n_in, s->d_lohi, X0, accepted + r0);
         st = forward(s, X0, m, false, s->qy);
+        if (st == SOAP_OK) st = judge_forward(s, X0, m);
         if (st != SOAP_OK) break;
+        const float* ye = s->judge ? s->judge->qy : s->qy;
         k_query_out<<<grid1((int64_t)m * (s->n_coef + 1)), 256, 0, s->stream>>>(
-            s->qy, s->n_out_pad, m, s->n_coef, s->coef_mean, s->coef_std, rv_err_max_cms, accepted + r0,
-            pred_err_cms ? pred_err_cms + r0 : nullptr, nullptr, s->qsplit);
+            s->qy, s->n_out_pad, ye, s->n_out_pad, m, s->n_coef, s->coef_mean, s->coef_std, rv_err_max_cms,
+            accepted + r0, pred_err_cms ? pred_err_cms + r0 : nullptr, nullptr, s->qsplit);
         tc::Epilogue ep{};
         ep.flags = tc::EPI_BIAS | tc::EPI_A32;
         ep.bias = s->mu;
@@ -911,6 +951,15 @@ void soap_surrogate_free(soap_surrogate* s) {
     cudaStreamSynchronize(s->stream);
     free_all(s);
     delete s;
+}
+
+soap_status soap_axpy_f32(int64_t n, float alpha, const float* x, float* y, void* cuda_stream) {
+    clear_error();
+    if (!x || !y || n < 0) { set_error("invalid argument"); return SOAP_EINVAL; }
+    if (n == 0) return SOAP_OK;
+    k_axpy<<<grid1(n), 256, 0, (cudaStream_t)cuda_stream>>>(n, alpha, x, y);
+    SOAP_CUDA(cudaGetLastError());
+    return SOAP_OK;
 }
 
 // ---------------------------------------------------------------------------------------

@@ -111,10 +111,12 @@ def _load():
         "soap_surrogate_train": (i32, [P, P, P, i64, i32, P, P, i32, ctypes.c_uint64, P]),
         "soap_surrogate_predict": (i32, [P, P, i64, ctypes.c_float, P, P, P]),
         "soap_surrogate_set_basis": (i32, [P, P, P, i64]),
+        "soap_surrogate_set_judge": (i32, [P, P]),
         "soap_surrogate_reconstruct": (i32, [P, P, i64, P]),
         "soap_surrogate_query": (i32, [P, P, i64, ctypes.c_float, P, P, P]),
         "soap_surrogate_free": (None, [P]),
         "soap_pca_fit": (i32, [P, i64, i64, P, i32, i32, i32, P, P, P, P]),
+        "soap_axpy_f32": (i32, [i64, ctypes.c_float, P, P, P]),
         "soap_pca_project": (i32, [P, i64, i64, P, P, i32, P, P]),
         "soap_free": (None, [P]),
         "soap_last_error": (ctypes.c_char_p, []),
@@ -313,6 +315,38 @@ def soap_active_batch(ctx, items: Sequence, regions: Sequence, phases, out,
                                   ph.size, int(output), ptr, dev), "soap_active_batch")
 
 
+ITEM_DTYPE = np.dtype([("vsini_kms", "<f8"), ("incl_deg", "<f8"), ("first_region", "<i4"),
+                       ("n_regions", "<i4"), ("first_phase", "<i4"), ("n_phases", "<i4")])
+REGION_DTYPE = np.dtype([("type", "<i4"), ("reserved", "<i4"), ("lat_deg", "<f8"), ("lon_deg", "<f8"),
+                         ("radius_rstar", "<f8"), ("temp_K", "<f8")])
+assert ITEM_DTYPE.itemsize == ctypes.sizeof(soap_batch_item)
+assert REGION_DTYPE.itemsize == ctypes.sizeof(soap_region)
+
+
+def batch_columns_arrays(cols):
+    """Structured item / region arrays (the C layouts) from a dict of numpy columns."""
+    it = np.zeros(len(cols["vsini"]), ITEM_DTYPE)
+    it["vsini_kms"], it["incl_deg"] = cols["vsini"], cols["incl"]
+    it["first_region"], it["n_regions"] = cols["first_region"], cols["n_regions"]
+    it["first_phase"], it["n_phases"] = cols["first_phase"], cols["n_phases"]
+    rg = np.zeros(len(cols["type"]), REGION_DTYPE)
+    rg["type"], rg["lat_deg"], rg["lon_deg"] = cols["type"], cols["lat"], cols["lon"]
+    rg["radius_rstar"], rg["temp_K"] = cols["radius"], cols["temp"]
+    return it, rg, np.ascontiguousarray(cols["phases"], np.float64)
+
+
+def soap_active_batch_arrays(ctx, items, regions, phases, out, output: int = 0) -> None:
+    """soap_active_batch with items / regions given as ITEM_DTYPE / REGION_DTYPE arrays."""
+    items = np.ascontiguousarray(items, ITEM_DTYPE)
+    regions = np.ascontiguousarray(regions, REGION_DTYPE)
+    ph = np.ascontiguousarray(phases, np.float64)
+    ptr, dev = _ptr(out)
+    ip = ctypes.cast(ctypes.c_void_p(items.ctypes.data), ctypes.POINTER(soap_batch_item))
+    rp = ctypes.cast(ctypes.c_void_p(regions.ctypes.data), ctypes.POINTER(soap_region))
+    _check(_lib.soap_active_batch(ctx, ip, len(items), rp, len(regions), ctypes.c_void_p(ph.ctypes.data),
+                                  ph.size, int(output), ptr, dev), "soap_active_batch")
+
+
 def soap_batch_num_variants() -> int:
     n = ctypes.c_int32()
     _check(_lib.soap_batch_num_variants(ctypes.byref(n)), "soap_batch_num_variants")
@@ -465,6 +499,10 @@ def soap_surrogate_predict(s, x, rv_err_max_cms: float, coef=None, pred_err=None
                                        _dev(coef), _dev(pred_err), _dev(accepted)), "soap_surrogate_predict")
 
 
+def soap_surrogate_set_judge(s, judge) -> None:
+    _check(_lib.soap_surrogate_set_judge(s, judge), "soap_surrogate_set_judge")
+
+
 def soap_surrogate_set_basis(s, mean, basis) -> None:
     _check(_lib.soap_surrogate_set_basis(s, _dev(mean, "torch.float32"), _dev(basis, "torch.float32"),
                                          int(mean.shape[0])), "soap_surrogate_set_basis")
@@ -497,6 +535,14 @@ def soap_pca_fit(X, omega, k: int, n_power: int = 2, stream=None):
                              int(n_power), _dev(mean), _dev(basis), ctypes.c_void_p(sv.ctypes.data),
                              _stream_handle(stream)), "soap_pca_fit")
     return mean, basis, sv
+
+
+def soap_axpy_f32(alpha: float, x, y, stream=None) -> None:
+    """y += alpha x (CUDA float32 tensors of equal size)."""
+    if x.numel() != y.numel():
+        raise ValueError("size mismatch")
+    _check(_lib.soap_axpy_f32(int(x.numel()), float(alpha), _dev(x, "torch.float32"), _dev(y, "torch.float32"),
+                              _stream_handle(stream)), "soap_axpy_f32")
 
 
 def soap_pca_project(X, mean, basis, out, stream=None) -> None:

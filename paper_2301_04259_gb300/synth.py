@@ -308,6 +308,33 @@ def surrogate_layout(params):
     return items, regions, np.asarray(phases, np.float64)
 
 
+def surrogate_layout_columns(params):
+    """surrogate_layout() as numpy columns (for many queries): a dict with item columns vsini,
+    incl, first_region, n_regions, first_phase, n_phases, region columns type, lat, lon, radius,
+    temp, and phases."""
+    q = np.asarray(params, np.float64)
+    n = q.shape[0]
+    lat, lon, r, t_spot, ph, inc, vs, fill = (q[:, i] for i in range(8))
+    has_fac = fill > 0
+    n_reg = np.where(has_fac, 2, 1)
+    first = np.concatenate([[0], np.cumsum(n_reg)[:-1]])
+    total = int(n_reg.sum())
+    rtype = np.full(total, SPOT, np.int32)
+    rlat, rlon = np.empty(total), np.empty(total)
+    rrad, rtemp = np.empty(total), np.empty(total)
+    fac_idx = first[has_fac]
+    spot_idx = first + has_fac.astype(np.int64)
+    rtype[fac_idx] = FACULA
+    for idx, sel in ((fac_idx, has_fac), (spot_idx, np.ones(n, bool))):
+        rlat[idx], rlon[idx] = lat[sel], lon[sel]
+    rrad[fac_idx] = np.minimum(1.0, r[has_fac] * np.sqrt(1.0 + fill[has_fac]))
+    rtemp[fac_idx] = SURROGATE_FACULA_TEMP
+    rrad[spot_idx], rtemp[spot_idx] = r, t_spot
+    return dict(vsini=vs, incl=inc, first_region=first.astype(np.int32), n_regions=n_reg.astype(np.int32),
+                first_phase=np.arange(n, dtype=np.int32), n_phases=np.ones(n, np.int32),
+                type=rtype, lat=rlat, lon=rlon, radius=rrad, temp=rtemp, phases=ph.copy())
+
+
 def surrogate_init(seed: int, shapes=((256, 8), (256, 256), (256, 256), (256, 256), (129, 256))) -> np.ndarray:
     """Initial weights, flat [W1 | b1 | ... ]: normal with variance 2/in (hidden layers) and
     1/in (output layer), zero biases."""

@@ -68,3 +68,35 @@ def test_corrupt_tuning_table_is_replaced(tmp_path):
     chosen = []
     e = tuning.choose_variant("k", lambda: (2, [3.0, 2.0, 1.0]), chosen.append, 3, path=path)
     assert e["variant"] == 2 and json.loads(path.read_text()) == {"k": {"variant": 2, "ms": [3.0, 2.0, 1.0]}}
+
+
+def test_vectorised_surrogate_layout_matches_the_per_query_one():
+    from paper_2301_04259_gb300 import soap
+    p = synth.surrogate_params(0, 64)
+    p[3, 7] = 0.0                                       # no facula on one query
+    it, rg, ph = soap.batch_columns_arrays(synth.surrogate_layout_columns(p))
+    items, regs, ph2 = synth.surrogate_layout(p)
+    assert len(it) == len(items) and len(rg) == len(regs)
+    for k, a in enumerate(items):
+        b = it[k]
+        assert a == (b["vsini_kms"], b["incl_deg"], b["first_region"], b["n_regions"], b["first_phase"], b["n_phases"])
+    for k, r in enumerate(regs):
+        b = rg[k]
+        assert (r.type, r.lat_deg, r.lon_deg, r.radius_rstar, r.temp_K) == (
+            b["type"], b["lat_deg"], b["lon_deg"], b["radius_rstar"], b["temp_K"])
+    assert np.array_equal(ph, ph2) and items[3][3] == 1
+
+
+def test_acceptance_threshold_calibration():
+    from paper_2301_04259_gb300.surrogate_pipeline import calibrate_threshold
+    rng = np.random.default_rng(0)
+    err = rng.lognormal(1.5, 1.0, 5000)
+    pred = err * rng.lognormal(0, 0.3, 5000)            # an informative predictor
+    thr = calibrate_threshold(pred, err, limit=10.0, miss=0.01)
+    acc = pred <= thr
+    assert acc.sum() > 100 and (err[acc] > 10).mean() <= 0.01
+    # the next larger threshold would break the bound
+    nxt = np.sort(pred)[np.searchsorted(np.sort(pred), thr, side="right")]
+    acc2 = pred <= nxt
+    assert (err[acc2] > 10).mean() > 0.01 or acc2.sum() == acc.sum()
+    assert calibrate_threshold(np.array([1.0, 2.0]), np.array([50.0, 1.0])) == 0.0
