@@ -45,6 +45,12 @@ def parse():
     ap.add_argument("--n-px", type=int, default=205800)
     ap.add_argument("--cpu-sample-px", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched-form and surrogate measurements (N=1 only)")
+    ap.add_argument("--batch-configs", type=int, default=4096)
+    ap.add_argument("--sur-train", type=int, default=600_000)
+    ap.add_argument("--sur-epochs", type=int, default=150)
+    ap.add_argument("--sur-queries", type=int, default=1_000_000)
     return ap.parse_args()
 
 
@@ -268,6 +274,15 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(case, args.cpu_sample_px)
+    extras = {}
+    if rank == 0 and world == 1 and not args.no_extras:
+        S.soap_free(ctx)
+        ctx = None
+        del out32, out64, flush
+        torch.cuda.empty_cache()
+        extras["batched"] = measure_batched(args, dev, hbm_peak)
+        torch.cuda.empty_cache()
+        extras["surrogate"] = measure_surrogate(args, dev)
 
     res = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
            "steps": K, "warmup": W, "ms_per_step": round(ms_step, 5), "higher_is_better": True,
@@ -289,12 +304,150 @@ def run_ours(args):
            "gpu_launches": int(launches_plain), "clocks": clocks}
     if cpu is not None:
         res["cpu_baseline"] = cpu
-    S.soap_free(ctx)
+    res.update(extras)
+    if ctx is not None:
+        S.soap_free(ctx)
     if rank == 0:
         print(json.dumps(res), flush=True)
     if world > 1:
         import torch.distributed as tdist
         tdist.destroy_process_group()
+
+
+# ------------------------------------------------------------------------------------------
+# batched form and surrogate (N = 1)
+# ------------------------------------------------------------------------------------------
+def _disk(S, case, dev):
+    import torch
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    return S.Disk(case.star, t(case.quiet), {k: t(v) for k, v in case.active.items()})
+
+
+def measure_batched(args, dev, hbm_peak):
+    """4096 independent configurations (disk 150x150, 6000-6300 A at 16,834 px, 10-200 phases,
+    1-4 spots, vsini 1-10 km/s, i 30-90 deg): one autotuned, graph-captured soap_active_batch per
+    step; the 29 GB of output exceed L2, so no flush is needed between steps."""
+    import torch
+    from paper_2301_04259_gb300 import soap as S
+    from paper_2301_04259_gb300 import synth
+    case = synth.batch_spectra(args.seed)
+    cfgs = synth.batch_configs(args.seed + 1, args.batch_configs)
+    items, regions, phases = synth.batch_layout(cfgs)
+    it, rg, ph = S.batch_columns_arrays({
+        "vsini": [c[0] for c in items], "incl": [c[1] for c in items], "first_region": [c[2] for c in items],
+        "n_regions": [c[3] for c in items], "first_phase": [c[4] for c in items],
+        "n_phases": [c[5] for c in items], "type": [r.type for r in regions], "lat": [r.lat_deg for r in regions],
+        "lon": [r.lon_deg for r in regions], "radius": [r.radius_rstar for r in regions],
+        "temp": [r.temp_K for r in regions], "phases": phases})
+    n_px = case.star.n_px
+    out = torch.empty((phases.size, n_px), dtype=torch.float32, device=dev)
+    with _disk(S, case, dev) as d:
+        best, ms_var = S.soap_batch_autotune(d.ctx, items, regions, phases, out, reps=2)
+        stream = torch.cuda.current_stream()
+        for _ in range(3):
+            S.soap_active_batch_arrays(d.ctx, it, rg, ph, out)
+        torch.cuda.synchronize()
+        K = 5
+        l0 = S.soap_get_launch_count(d.ctx)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        for k in range(K):
+            ev[k][0].record(stream)
+            S.soap_active_batch_arrays(d.ctx, it, rg, ph, out)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        launches = (S.soap_get_launch_count(d.ctx) - l0) // K
+        ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+        S.soap_set_profiling(d.ctx, True)
+        S.soap_reset_kernel_times(d.ctx)
+        S.soap_active_batch_arrays(d.ctx, it, rg, ph, out)
+        S.soap_synchronize(d.ctx)
+        kernels = {name: round(S.soap_get_kernel_time(d.ctx, t)[0], 4) for t, name in enumerate(S.TIMERS)
+                   if S.soap_get_kernel_time(d.ctx, t)[1]}
+        S.soap_set_profiling(d.ctx, False)
+        S.soap_synchronize(d.ctx)
+    out_bytes = out.numel() * 4
+    del out
+    c_ms = kernels.get("contract", ms)
+    return {"workload": f"batch{len(cfgs)}_disk150_{n_px}px", "configs": len(cfgs), "spectra": int(phases.size),
+            "ms_per_batch": round(ms, 3), "spectra_per_s": round(phases.size / (ms * 1e-3), 1),
+            "variant": {"index": best, "phases_per_block": S.soap_batch_variant_info(best)[0],
+                        "px_per_thread": S.soap_batch_variant_info(best)[1]},
+            "autotune_ms": [round(float(v), 3) for v in ms_var], "gpu_launches_per_batch": int(launches),
+            "kernel_ms": kernels, "output_bytes": int(out_bytes),
+            "contract_hbm_write_gbs": round(out_bytes / (c_ms * 1e-3) / 1e9, 1),
+            "contract_frac_of_hbm": round(out_bytes / (c_ms * 1e-3) / 1e9 / hbm_peak, 4),
+            "precision": "FP32 contraction, FP64 positions"}
+
+
+def measure_surrogate(args, dev):
+    """Surrogate trained on the batched method's residual spectra; judged accuracy on held-out
+    queries (true RVs from the plain method), and throughput on --sur-queries queries."""
+    import torch
+    from paper_2301_04259_gb300 import soap as S
+    from paper_2301_04259_gb300 import synth
+    from paper_2301_04259_gb300 import surrogate_pipeline as SP
+    case = synth.batch_spectra(args.seed)
+    n_px = case.star.n_px
+    res = {}
+    with _disk(S, case, dev) as d:
+        t0 = time.perf_counter()
+        model = SP.train(d.ctx, case, n_train=args.sur_train, epochs=args.sur_epochs, seed=args.seed,
+                         n_judge=196_608, judge_epochs=60)
+        res["train_wall_s"] = round(time.perf_counter() - t0, 2)
+        res["train"] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in model.log.items()
+                        if k not in ("loss", "head_loss", "rv_sens_cms_per_sd")}
+        res["train"]["final_loss"] = model.log["loss"][-1]
+        xe = synth.surrogate_params(args.seed + 99, 8192)
+        err = SP.judge_errors(d.ctx, case, model, xe)
+        acc = torch.empty(len(xe), dtype=torch.uint8, device=dev)
+        S.soap_surrogate_predict(model.handle, torch.from_numpy(xe).to(dev), model.accept_thr_cms, accepted=acc)
+        a = acc.cpu().numpy().astype(bool)
+        res["judged_heldout"] = {
+            "queries": len(xe), "accepted_frac": round(float(a.mean()), 4),
+            "rv_err_cms_all_median": round(float(np.median(err)), 3),
+            "rv_err_cms_accepted_p50_p95_p99_max": [round(float(np.percentile(err[a], q)), 3) for q in (50, 95, 99, 100)]
+            if a.any() else None,
+            "accepted_over_10cms_frac": round(float((err[a] > SP.RV_ERR_MAX_CMS).mean()), 4) if a.any() else None,
+            "accept_threshold_pred_cms": round(model.accept_thr_cms, 4)}
+        # throughput on n queries in chunks of 65536 (one reused output buffer)
+        nq, ch = args.sur_queries, 65536
+        xq = synth.surrogate_params(args.seed + 123, nq)
+        xqd = torch.from_numpy(xq).to(dev)
+        out = torch.empty((ch, n_px), dtype=torch.float32, device=dev)
+        accq = torch.empty(nq, dtype=torch.uint8, device=dev)
+
+        def t_surrogate():
+            for a0 in range(0, nq, ch):
+                m = min(ch, nq - a0)
+                S.soap_surrogate_query(model.handle, xqd[a0:a0 + m], model.accept_thr_cms, out[:m], accq[a0:a0 + m])
+
+        def t_plain():
+            for a0 in range(0, nq, ch):
+                m = min(ch, nq - a0)
+                SP.plain_residuals(d.ctx, xq[a0:a0 + m], out[:m])
+
+        def t_hybrid():
+            for a0 in range(0, nq, ch):
+                m = min(ch, nq - a0)
+                SP.query(d.ctx, model, xq[a0:a0 + m], out[:m])
+
+        timing = {}
+        for name, fn in (("surrogate", t_surrogate), ("plain", t_plain), ("hybrid", t_hybrid)):
+            fn()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            timing[name] = time.perf_counter() - t0
+        res["queries"] = nq
+        res["queries_per_s"] = {k: round(nq / v, 1) for k, v in timing.items()}
+        res["accepted_frac_queries"] = round(float(accq.float().mean().item()), 4)
+        res["gain_hybrid_vs_plain"] = round(timing["plain"] / timing["hybrid"], 3)
+        res["gain_surrogate_only_vs_plain"] = round(timing["plain"] / timing["surrogate"], 3)
+        res["precision"] = "BF16 weights/activations, FP32 accumulation; split-BF16 reconstruction"
+        res["note"] = "output: residual spectra F - F_q; wall-clock per query set incl. host bookkeeping"
+        model.free()
+    return res
 
 
 # ------------------------------------------------------------------------------------------

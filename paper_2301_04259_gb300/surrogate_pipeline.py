@@ -213,16 +213,28 @@ def judge_errors(ctx, case, model, x, chunk=8192):
     return np.concatenate(out) if out else np.zeros(0)
 
 
-def query(ctx, model, x_dev, x_host, out, thr_cms=None):
-    """Residual spectra of every query into out: the surrogate's where accepted, the plain
-    method's elsewhere.  Returns the acceptance mask (host bool array)."""
+def query(ctx, model, x_host, out, thr_cms=None):
+    """Residual spectra F - F_q of every query into out [n, n_px]: reconstructed from the
+    surrogate where it is accepted, from the plain method elsewhere.  Returns the acceptance mask
+    (host bool array)."""
     torch = _torch()
-    acc = torch.empty(x_dev.shape[0], dtype=torch.uint8, device=x_dev.device)
-    S.soap_surrogate_query(model.handle, x_dev, model.accept_thr_cms if thr_cms is None else thr_cms, out, acc)
+    dev = out.device
+    n = len(x_host)
+    k = model.basis.shape[0]
+    x_dev = torch.from_numpy(np.ascontiguousarray(x_host, np.float32)).to(dev)
+    coef = torch.empty((n, k), dtype=torch.float32, device=dev)
+    acc = torch.empty(n, dtype=torch.uint8, device=dev)
+    thr = model.accept_thr_cms if thr_cms is None else thr_cms
+    S.soap_surrogate_predict(model.handle, x_dev, thr, coef=coef, accepted=acc)
     a = acc.cpu().numpy().astype(bool)
-    rej = np.flatnonzero(~a)
-    if rej.size:
-        tmp = torch.empty((rej.size, out.shape[1]), dtype=torch.float32, device=out.device)
-        plain_residuals(ctx, x_host[rej], tmp)
-        out.index_copy_(0, torch.from_numpy(rej).to(out.device), tmp)
+    ia, ir = np.flatnonzero(a), np.flatnonzero(~a)
+    if ia.size:
+        it = torch.from_numpy(ia).to(dev)
+        tmp = torch.empty((ia.size, out.shape[1]), dtype=torch.float32, device=dev)
+        S.soap_surrogate_reconstruct(model.handle, coef.index_select(0, it), tmp)
+        out.index_copy_(0, it, tmp)
+    if ir.size:
+        tmp = torch.empty((ir.size, out.shape[1]), dtype=torch.float32, device=dev)
+        plain_residuals(ctx, x_host[ir], tmp)
+        out.index_copy_(0, torch.from_numpy(ir).to(dev), tmp)
     return a
