@@ -258,7 +258,8 @@ enum {
  * sequence is captured once per batch shape into a CUDA graph owned by the context and
  * replayed on later calls with the same shape (soap_set_profiling(ctx, 1) runs it without the
  * graph).  The variant (phases per block, pixels per thread) is the one soap_batch_set_variant
- * or soap_batch_autotune chose, else a default.
+ * or soap_batch_autotune chose, else 1 or 2 phases per block when no item has more phases, and
+ * 4 otherwise.
  * Errors: SOAP_EINVAL (bad item, phase not covered exactly once, alpha != 0), SOAP_ESTATE (no
  * active spectrum for a region type), SOAP_ERANGE (class limit). */
 soap_status soap_active_batch(soap_ctx* ctx, const soap_batch_item* items, int32_t n_items,
@@ -272,7 +273,7 @@ soap_status soap_batch_num_variants(int32_t* n);
 soap_status soap_batch_variant_info(int32_t variant, int32_t* phases_per_block,
                                     int32_t* px_per_thread);
 
-/* Variant soap_active_batch uses on this context (-1: the default). */
+/* Variant soap_active_batch uses on this context (-1: chosen from the items' phase counts). */
 soap_status soap_batch_set_variant(soap_ctx* ctx, int32_t variant);
 soap_status soap_batch_get_variant(const soap_ctx* ctx, int32_t* variant);
 

@@ -560,7 +560,13 @@ soap_status soap_active_batch(soap_ctx* c, const soap_batch_item* items, int32_t
     if ((n_items > 0 && !items) || (n_regions > 0 && !regions) || (n_phases > 0 && !phases)) {
         set_error("items, regions or phases is NULL"); return SOAP_EINVAL;
     }
-    const int variant = c->b_variant >= 0 ? c->b_variant : batch_default_variant();
+    int variant = c->b_variant;
+    if (variant < 0) {
+        // no chosen variant: blocks no wider than the items' phase counts (1, 2, else 4 phases)
+        int max_np = 0;
+        for (int k = 0; k < n_items; k++) max_np = std::max(max_np, (int)items[k].n_phases);
+        variant = batch_default_variant(max_np);
+    }
     const size_t bytes = (size_t)n_phases * (size_t)c->n_px * sizeof(float);
     float* dst = out;
     if (!out_on_device && bytes > 0) {

@@ -372,7 +372,11 @@ void batch_variant_info(int v, int* pb, int* r) {
     *r = kVariants[v].R;
 }
 
-int batch_default_variant() { return kDefaultVariant; }
+int batch_default_variant(int max_phases_per_item) {
+    if (max_phases_per_item <= 1) return 0;      // (1, 4)
+    if (max_phases_per_item == 2) return 1;      // (2, 4)
+    return kDefaultVariant;
+}
 
 void batch_release(soap_ctx* c) {
     if (c->b_graph_exec) cudaGraphExecDestroy(c->b_graph_exec);

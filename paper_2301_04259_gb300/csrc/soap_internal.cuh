@@ -208,7 +208,7 @@ soap_status toeplitz_active(soap_ctx* c, const RegionDev* regions_host, int n_re
 soap_status batch_run(soap_ctx* c, const soap_batch_item* items, int n_items, const soap_region* regions,
                       int n_regions, const double* phases, int n_phases, int variant, int residual, float* out);
 int batch_num_variants();
-int batch_default_variant();
+int batch_default_variant(int max_phases_per_item);
 void batch_variant_info(int v, int* phases_per_block, int* px_per_thread);
 void batch_release(soap_ctx* c);
 

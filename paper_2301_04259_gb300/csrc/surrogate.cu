@@ -86,6 +86,7 @@ struct soap_surrogate {
     bf16 *qa = nullptr, *qb = nullptr;        // ping-pong activations [q_cap][256]
     float* qy = nullptr;                      // [q_cap][n_out_pad]
     bf16* qsplit = nullptr;                   // [q_cap][3 n_coef]
+    bf16* qx0 = nullptr;                      // [q_cap][n_in] scaled query inputs
     // basis
     int64_t n_px = 0;
     float* mu = nullptr;                      // [n_px]
@@ -561,12 +562,13 @@ static soap_status alloc(void** p, size_t bytes) {
 static soap_status ensure_query(soap_surrogate* s, int rows) {
     if (rows <= s->q_cap) return SOAP_OK;
     cudaStreamSynchronize(s->stream);
-    cudaFree(s->qa); cudaFree(s->qb); cudaFree(s->qy); cudaFree(s->qsplit);
-    s->qa = s->qb = nullptr; s->qy = nullptr; s->qsplit = nullptr; s->q_cap = 0;
+    cudaFree(s->qa); cudaFree(s->qb); cudaFree(s->qy); cudaFree(s->qsplit); cudaFree(s->qx0);
+    s->qa = s->qb = nullptr; s->qy = nullptr; s->qsplit = nullptr; s->qx0 = nullptr; s->q_cap = 0;
     SOAP_TRY(alloc((void**)&s->qa, (size_t)rows * s->hidden * sizeof(bf16)));
     SOAP_TRY(alloc((void**)&s->qb, (size_t)rows * s->hidden * sizeof(bf16)));
     SOAP_TRY(alloc((void**)&s->qy, (size_t)rows * s->n_out_pad * sizeof(float)));
     SOAP_TRY(alloc((void**)&s->qsplit, (size_t)rows * 3 * s->n_coef * sizeof(bf16)));
+    SOAP_TRY(alloc((void**)&s->qx0, (size_t)rows * s->n_in * sizeof(bf16)));
     s->q_cap = rows;
     return SOAP_OK;
 }
@@ -602,7 +604,7 @@ static void free_all(soap_surrogate* s) {
     if (s->graph) cudaGraphExecDestroy(s->graph);
     void* ptrs[] = {s->P, s->G, s->Mo, s->Vo, s->wbuf, s->d_lohi, s->coef_mean, s->coef_std, s->w_out, s->X0, s->X0T,
                     s->Y, s->T, s->dY, s->dYT, s->perm, s->d_step, s->d_lr, s->d_loss, s->flags, s->qa, s->qb,
-                    s->qy, s->qsplit, s->mu, s->vsplit};
+                    s->qy, s->qsplit, s->qx0, s->mu, s->vsplit};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int l = 0; l < 4; l++) {
@@ -837,8 +839,7 @@ soap_status soap_surrogate_predict(soap_surrogate* s, const float* x, int64_t n,
     if (n <= 0) return SOAP_OK;
     const int chunk = 65536;
     SOAP_TRY(ensure_query(s, (int)std::min<int64_t>(n, chunk)));
-    bf16* X0 = nullptr;
-    SOAP_TRY(alloc((void**)&X0, (size_t)std::min<int64_t>(n, chunk) * s->n_in * sizeof(bf16)));
+    bf16* X0 = s->qx0;
     soap_status st = SOAP_OK;
     for (int64_t r0 = 0; r0 < n && st == SOAP_OK; r0 += chunk) {
         const int m = (int)std::min<int64_t>(chunk, n - r0);
@@ -853,8 +854,6 @@ soap_status soap_surrogate_predict(soap_surrogate* s, const float* x, int64_t n,
             accepted ? accepted + r0 : nullptr, pred_err_cms ? pred_err_cms + r0 : nullptr,
             coef ? coef + r0 * s->n_coef : nullptr, s->qsplit);
     }
-    cudaStreamSynchronize(s->stream);
-    cudaFree(X0);
     SOAP_CUDA(cudaGetLastError());
     if (st != SOAP_OK) return st;
     return check(s);
@@ -898,8 +897,7 @@ soap_status soap_surrogate_query(soap_surrogate* s, const float* x, int64_t n, f
     if (n <= 0) return SOAP_OK;
     const int chunk = 65536;
     SOAP_TRY(ensure_query(s, (int)std::min<int64_t>(n, chunk)));
-    bf16* X0 = nullptr;
-    SOAP_TRY(alloc((void**)&X0, (size_t)std::min<int64_t>(n, chunk) * s->n_in * sizeof(bf16)));
+    bf16* X0 = s->qx0;
     soap_status st = SOAP_OK;
     for (int64_t r0 = 0; r0 < n && st == SOAP_OK; r0 += chunk) {
         const int m = (int)std::min<int64_t>(chunk, n - r0);
@@ -919,8 +917,6 @@ soap_status soap_surrogate_query(soap_surrogate* s, const float* x, int64_t n, f
         st = tc::gemm_tn(s->qsplit, 3 * s->n_coef, s->vsplit, 3 * s->n_coef, m, (int)s->n_px, 3 * s->n_coef, ep,
                          s->stream, s->flags);
     }
-    cudaStreamSynchronize(s->stream);
-    cudaFree(X0);
     if (st != SOAP_OK) return st;
     return check(s);
 }

@@ -213,14 +213,15 @@ def judge_errors(ctx, case, model, x, chunk=8192):
     return np.concatenate(out) if out else np.zeros(0)
 
 
-def query(ctx, model, x_host, out, thr_cms=None):
-    """Residual spectra F - F_q of every query into out [n, n_px]: reconstructed from the
-    surrogate where it is accepted, from the plain method elsewhere.  Returns the acceptance mask
-    (host bool array)."""
+def query(ctx, model, x_host, sink=None, thr_cms=None, chunk=65536):
+    """Answer every query: residual spectra F - F_q reconstructed by the surrogate where it is
+    accepted, computed by the plain method elsewhere, in chunks of `chunk` spectra.  Each chunk
+    is handed to sink(indices, spectra) (host int64 query indices, device [m, n_px]) before the
+    buffer is reused.  Returns the acceptance mask (host bool array)."""
     torch = _torch()
-    dev = out.device
+    dev = model.basis.device
     n = len(x_host)
-    k = model.basis.shape[0]
+    k, n_px = model.basis.shape
     x_dev = torch.from_numpy(np.ascontiguousarray(x_host, np.float32)).to(dev)
     coef = torch.empty((n, k), dtype=torch.float32, device=dev)
     acc = torch.empty(n, dtype=torch.uint8, device=dev)
@@ -228,13 +229,17 @@ def query(ctx, model, x_host, out, thr_cms=None):
     S.soap_surrogate_predict(model.handle, x_dev, thr, coef=coef, accepted=acc)
     a = acc.cpu().numpy().astype(bool)
     ia, ir = np.flatnonzero(a), np.flatnonzero(~a)
+    buf = torch.empty((min(chunk, max(n, 1)), n_px), dtype=torch.float32, device=dev)
     if ia.size:
-        it = torch.from_numpy(ia).to(dev)
-        tmp = torch.empty((ia.size, out.shape[1]), dtype=torch.float32, device=dev)
-        S.soap_surrogate_reconstruct(model.handle, coef.index_select(0, it), tmp)
-        out.index_copy_(0, it, tmp)
-    if ir.size:
-        tmp = torch.empty((ir.size, out.shape[1]), dtype=torch.float32, device=dev)
-        plain_residuals(ctx, x_host[ir], tmp)
-        out.index_copy_(0, torch.from_numpy(ir).to(dev), tmp)
+        ca = coef.index_select(0, torch.from_numpy(ia).to(dev))
+        for c0 in range(0, ia.size, chunk):
+            m = min(chunk, ia.size - c0)
+            S.soap_surrogate_reconstruct(model.handle, ca[c0:c0 + m], buf[:m])
+            if sink:
+                sink(ia[c0:c0 + m], buf[:m])
+    for c0 in range(0, ir.size, chunk):
+        idx = ir[c0:c0 + chunk]
+        plain_residuals(ctx, x_host[idx], buf[:idx.size])
+        if sink:
+            sink(idx, buf[:idx.size])
     return a
