@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--sur-train", type=int, default=600_000)
     ap.add_argument("--sur-epochs", type=int, default=150)
     ap.add_argument("--sur-queries", type=int, default=1_000_000)
+    ap.add_argument("--only", default="all", choices=["all", "batched", "surrogate", "gemm"],
+                    help="run one block alone (for profiling); 'all' is the full benchmark line")
     return ap.parse_args()
 
 
@@ -520,10 +522,67 @@ def run_reference(args):
     print(json.dumps(res), flush=True)
 
 
+def measure_gemm(args, dev, bf16_peak):
+    """The surrogate's reconstruction GEMM alone: 65536 residual spectra of 16,834 px from 128
+    coefficients with BF16 high/low splitting (K = 3 x 128) on the tcgen05 tensor cores."""
+    import torch
+    from paper_2301_04259_gb300 import soap as S
+    from paper_2301_04259_gb300 import synth
+    rng = np.random.default_rng(args.seed)
+    n, p, k = 65536, synth.n_px_for_sampling(6000.0, 6300.0), 128
+    basis = torch.from_numpy(np.linalg.qr(rng.standard_normal((p, k)))[0].T.astype(np.float32)).to(dev).contiguous()
+    mean = torch.zeros(p, dtype=torch.float32, device=dev)
+    coef = torch.from_numpy(rng.standard_normal((n, k)).astype(np.float32)).to(dev)
+    out = torch.empty((n, p), dtype=torch.float32, device=dev)
+    s = S.soap_surrogate_create(synth.SURROGATE_LO, synth.SURROGATE_HI, 128)
+    try:
+        S.soap_surrogate_set_basis(s, mean, basis)
+        for _ in range(3):
+            S.soap_surrogate_reconstruct(s, coef, out)
+        torch.cuda.synchronize()
+        stream = torch.cuda.current_stream()
+        K = max(3, args.steps)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        for a, b in ev:
+            a.record(stream)
+            S.soap_surrogate_reconstruct(s, coef, out)
+            b.record(stream)
+        torch.cuda.synchronize()
+        ms = float(np.median([a.elapsed_time(b) for a, b in ev]))
+    finally:
+        S.soap_surrogate_free(s)
+    flops = 2.0 * n * p * (3 * k)
+    tf = flops / (ms * 1e-3) / 1e12
+    return {"kernel": "k_gemm_tn<256> (tcgen05 BF16, split reconstruction)", "M": n, "N": p, "K": 3 * k,
+            "ms": round(ms, 4), "achieved_tflops": round(tf, 1), "bf16_peak_tflops": bf16_peak,
+            "frac": round(tf / bf16_peak, 4), "output_gbs": round(n * p * 4 / (ms * 1e-3) / 1e9, 1),
+            "note": "includes the split of the coefficient rows (one small kernel per chunk)"}
+
+
+def run_block(args):
+    import torch
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda:0")
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    if args.only == "batched":
+        res = measure_batched(args, dev, float(peaks.get("hbm_gbs", 6800.0)))
+    elif args.only == "surrogate":
+        res = measure_surrogate(args, dev)
+    else:
+        res = measure_gemm(args, dev, float(peaks.get("bf16_tflops", 1900.0)))
+    print(json.dumps({"block": args.only, **res}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.only != "all":
+        run_block(args)
     else:
         run_ours(args)
 

@@ -297,9 +297,11 @@ soap_status soap_batch_autotune(soap_ctx* ctx, const soap_batch_item* items, int
  * u = ln(lambda/lambda_start)/Delta, box_l(v) centred at (ln(lambda_l/lambda_start) +
  * atanh(v/c))/Delta with half width W/(2 c Delta); lines whose box leaves the grid anywhere on
  * the velocity grid are skipped.  The fit minimises sum_k (A + B exp(-(v_k-mu)^2/(2 s^2)) -
- * CCF_k)^2 by FP64 Levenberg-Marquardt (in variables scaled by max CCF and by the dip's
- * moments) from A = max CCF, B = min - max, mu and s = first two moments of the dip max - CCF.
- *  rv_kms         [n_spec] fitted mu (km/s).
+ * CCF_k)^2 by FP64 Levenberg-Marquardt (in variables scaled by max CCF and by the starting
+ * width) from A = max CCF, B = min - max, mu = velocity of the (first) CCF minimum and
+ * s = dip area / (|B| sqrt(2 pi)), at least one velocity step.
+ *  rv_kms         [n_spec] fitted mu (km/s); NaN when the fit leaves the velocity grid (mu
+ *                 outside it or a width larger than it: no dip to fit).
  *  fit_params     [n_spec][4] (A, B, mu, s), or NULL.
  *  ccf_out        [n_spec][n_v] float64 CCF, or NULL.
  *  Outputs are host or device per out_on_device. */

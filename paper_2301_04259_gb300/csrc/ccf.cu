@@ -360,7 +360,7 @@ __device__ __forceinline__ void fit_pass(const double* __restrict__ y, int n_v, 
 }
 
 // One block of 128 threads per spectrum, FP64 throughout.  Start: continuum A = max CCF,
-// B = min - max, mu and sigma from the first two moments of the dip (A - CCF); the model is
+// B = min - max, mu at the (first) minimum and sigma from the dip's area; the model is
 // A + B exp(-(v - mu)^2 / (2 sigma^2)).  The fit runs in scaled variables (CCF / max,
 // (v - mu0) / sigma0) so that the normal equations stay well conditioned.  Levenberg-Marquardt
 // with damping (J^T J + lam diag(J^T J)): each pass evaluates the cost, J^T J and J^T r at the
@@ -382,40 +382,43 @@ __global__ void __launch_bounds__(kFitThreads) k_gauss_fit(int n_spec, int n_v, 
     if (spec >= n_spec) return;
     const double* c = ccf + (int64_t)spec * n_v;
     double* y = scratch + (int64_t)spec * n_v;            // scaled CCF
-    // continuum and the dip's moments
+    // start (as the oracle's): continuum A = max CCF, depth B = min - max at the first
+    // minimum, mu = its velocity, sigma = dip area / (|B| sqrt(2 pi)) (at least one step)
     double mx = -INFINITY, mn = INFINITY;
+    int kmin = n_v;
     for (int k = threadIdx.x; k < n_v; k += kFitThreads) {
         mx = fmax(mx, c[k]);
-        mn = fmin(mn, c[k]);
+        if (c[k] < mn) { mn = c[k]; kmin = k; }
     }
     for (int o = 16; o > 0; o >>= 1) {
         mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        const double mo = __shfl_xor_sync(0xffffffffu, mn, o);
+        const int ko = __shfl_xor_sync(0xffffffffu, kmin, o);
+        if (mo < mn || (mo == mn && ko < kmin)) { mn = mo; kmin = ko; }
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) { red[warp][0] = mx; red[warp][1] = mn; }
+    __shared__ int redk[kFitWarps];
+    if (lane == 0) { red[warp][0] = mx; red[warp][1] = mn; redk[warp] = kmin; }
     __syncthreads();
-    mx = red[0][0]; mn = red[0][1];
-    for (int w = 1; w < kFitWarps; w++) { mx = fmax(mx, red[w][0]); mn = fmin(mn, red[w][1]); }
+    mx = red[0][0]; mn = red[0][1]; kmin = redk[0];
+    for (int w = 1; w < kFitWarps; w++) {
+        mx = fmax(mx, red[w][0]);
+        if (red[w][1] < mn || (red[w][1] == mn && redk[w] < kmin)) { mn = red[w][1]; kmin = redk[w]; }
+    }
     const double scale = mx != 0.0 ? fabs(mx) : 1.0;
     const double iscale = 1.0 / scale;
-    double m3[3] = {0.0, 0.0, 0.0};
+    double m1[1] = {0.0};
     for (int k = threadIdx.x; k < n_v; k += kFitThreads) {
-        const double v = fma((double)k, v_step, v_lo), d = mx - c[k];
         y[k] = c[k] * iscale;
-        m3[0] += d; m3[1] += d * v; m3[2] += d * v * v;
+        m1[0] += mx - c[k];
     }
-    double mom[3];
-    table_sum<3>(m3, tab, part, mom);
+    double area[1];
+    table_sum<1>(m1, tab, part, area);
     if (threadIdx.x == 0) {
-        double c0 = fma(0.5 * (n_v - 1), v_step, v_lo), s0 = v_step;
-        if (mom[0] > 0.0) {
-            c0 = mom[1] / mom[0];
-            const double var = mom[2] / mom[0] - c0 * c0;
-            s0 = var > 0.0 ? sqrt(var) : v_step;
-        }
-        sp[0] = c0;
-        sp[1] = fmax(s0, v_step);
+        const double B0 = mn - mx;
+        const double s = B0 != 0.0 ? area[0] * v_step / (fabs(B0) * 2.5066282746310002) : v_step;
+        sp[0] = fma((double)kmin, v_step, v_lo);
+        sp[1] = fmax(s, v_step);
     }
     __syncthreads();
     const double c0 = sp[0], s0 = sp[1];
@@ -480,7 +483,10 @@ __global__ void __launch_bounds__(kFitThreads) k_gauss_fit(int n_spec, int n_v, 
         fit_pass(y, n_v, ucache, u0, du, ptb, tab, part, acc);
     }
     if (threadIdx.x == 0) {
-        const double mu = fma(p[2], s0, c0);
+        // a fit that leaves the velocity grid (no dip to fit) is reported as NaN
+        const double v_hi = fma((double)(n_v - 1), v_step, v_lo);
+        double mu = fma(p[2], s0, c0);
+        if (!(mu >= v_lo && mu <= v_hi) || !(fabs(p[3]) * s0 <= v_hi - v_lo)) mu = NAN;
         rv[spec] = mu;
         if (fit) {
             fit[(int64_t)spec * 4 + 0] = p[0] * scale;
