@@ -3,7 +3,7 @@
 //   C[m][n] = epilogue( sum_k A[m][k] * B[n][k] )        ("TN": both operands K-contiguous)
 //
 // One CTA computes a 128 x BN tile.  Warp 0 streams 128 x 64 (A) and BN x 64 (B) BF16 tiles
-// into shared memory with TMA (128-byte swizzle) through a STAGES-deep ring of mbarriers;
+// into shared memory with TMA (128-byte swizzle) through a ring of mbarriers (2 to 4 stages);
 // warp 1 owns the tensor-memory accumulator (128 lanes x BN FP32 columns) and issues
 // tcgen05.mma (M = 128, N = BN, K = 16 per instruction) from one thread; warps 2..5 read the
 // accumulator back with tcgen05.ld (one row per thread) and apply the epilogue.
@@ -23,8 +23,10 @@ namespace tc {
 
 constexpr int BM = 128;        // rows per CTA (TMEM lanes)
 constexpr int BK = 64;         // K elements per stage: one 128-byte swizzle atom of BF16
-constexpr int STAGES = 4;
 constexpr int kThreads = 192;
+// Pipeline depth per tile width: two CTAs fit on an SM (shared memory and 512 TMEM columns), so
+// one CTA's loads and MMAs overlap the other's epilogue.
+template <int BN> struct Stages { static constexpr int value = BN >= 256 ? 2 : (BN >= 128 ? 3 : 4); };
 constexpr unsigned int kFlagTimeout = 8u;
 
 // Epilogue: z = acc (+ bias[n]); a = GELU(z) when EPI_GELU, a = z * GELU'(zin[m][n]) when
@@ -146,17 +148,44 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 
 template <int BN>
 struct Smem {
+    static constexpr int STAGES = Stages<BN>::value;
     static constexpr int kA = BM * BK * 2;          // bytes per stage
     static constexpr int kB = BN * BK * 2;
     static constexpr int kStage = kA + kB;
+    static constexpr int kTile = 32 * 33 * 4;       // per epilogue warp: 32 x 32 floats, padded rows
+    static_assert(4 * kTile <= STAGES * kStage, "epilogue tiles reuse the operand ring");
     static constexpr int kBytes = STAGES * kStage + 1024 /* alignment slack */ + 256 /* barriers */;
 };
 
+// Row-major store of a warp's 32 x 32 block through its shared tile: lane r holds row r's 32
+// values; after the transpose, lane j writes column j of each row in turn, so every store
+// instruction covers 32 consecutive elements of one row.
+template <typename T>
+__device__ __forceinline__ void store_rows(float (*tile)[33], const float (&v)[32], int lane, T* base, int64_t ld,
+                                           int m_first, int M, int n_first, int N) {
+#pragma unroll
+    for (int i = 0; i < 32; i++) tile[lane][i] = v[i];
+    __syncwarp();
+    const int n = n_first + lane;
+    if (n < N) {
+#pragma unroll 4
+        for (int r = 0; r < 32; r++) {
+            const int m = m_first + r;
+            if (m >= M) break;
+            const float x = tile[r][lane];
+            if constexpr (sizeof(T) == 4) base[(int64_t)m * ld + n] = x;
+            else base[(int64_t)m * ld + n] = __float2bfloat16_rn(x);
+        }
+    }
+    __syncwarp();
+}
+
 template <int BN>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, 2)
 k_gemm_tn(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b, int M, int N,
           int K, Epilogue ep, unsigned int* flags) {
     static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "tcgen05 N for M = 128");
+    constexpr int STAGES = Smem<BN>::STAGES;
     extern __shared__ unsigned char smem_raw[];
     // 1024-byte aligned operand ring (the swizzle atom), barriers after it
     unsigned char* ring = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
@@ -164,6 +193,9 @@ k_gemm_tn(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUt
     uint64_t* empty = full + STAGES;
     uint64_t* accum = empty + STAGES;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+    // epilogue tiles: the operand ring, free once the accumulator is complete (every copy has
+    // been consumed by an MMA that has finished)
+    float (*tiles)[32][33] = reinterpret_cast<float (*)[32][33]>(ring);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
@@ -231,24 +263,49 @@ k_gemm_tn(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUt
         const bool done = __all_sync(0xffffffffu, mbar_wait(accum, 0, flags));
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (done) {
+            float (*tile)[33] = tiles[warp - 2];
+            const int m_first = m0 + lane_base;
 #pragma unroll 1
             for (int c = 0; c < BN; c += 32) {
+                if (n0 + c >= N) break;
                 float v[32];
                 tmem_ld32(tmem + ((uint32_t)lane_base << 16) + (uint32_t)c, v);
-                if (m < M) {
+                float a[32];
+                if (ep.flags & EPI_DGELU) {
+                    // GELU'(z_in) at this block: staged through the tile so the reads are by row
+                    float zi[32];
+#pragma unroll 4
+                    for (int r = 0; r < 32; r++) {
+                        const int mm = m_first + r, nn = n0 + c + lane;
+                        tile[r][lane] = (mm < M && nn < N) ? ep.zin[(int64_t)mm * ep.ldzin + nn] : 0.0f;
+                    }
+                    __syncwarp();
+#pragma unroll
+                    for (int i = 0; i < 32; i++) zi[i] = tile[lane][i];
+                    __syncwarp();
+#pragma unroll
+                    for (int i = 0; i < 32; i++) {
+                        const float z = (ep.flags & EPI_BIAS) && n0 + c + i < N ? v[i] + ep.bias[n0 + c + i] : v[i];
+                        v[i] = z;
+                        a[i] = z * gelu_grad(zi[i]);
+                    }
+                } else {
 #pragma unroll
                     for (int i = 0; i < 32; i++) {
                         const int n = n0 + c + i;
-                        if (n >= N) break;
-                        float z = v[i];
-                        if (ep.flags & EPI_BIAS) z += ep.bias[n];
-                        float a = z;
-                        if (ep.flags & EPI_GELU) a = gelu(z);
-                        else if (ep.flags & EPI_DGELU) a = z * gelu_grad(ep.zin[(int64_t)m * ep.ldzin + n]);
-                        if (ep.flags & EPI_Z32) ep.c32[(int64_t)m * ep.ldc32 + n] = z;
-                        if (ep.flags & EPI_A32) ep.c32[(int64_t)m * ep.ldc32 + n] = a;
-                        if (ep.flags & EPI_A16) ep.c16[(int64_t)m * ep.ldc16 + n] = __float2bfloat16_rn(a);
-                        if (ep.flags & EPI_A16T) ep.c16t[(int64_t)n * ep.ldc16t + m] = __float2bfloat16_rn(a);
+                        const float z = (ep.flags & EPI_BIAS) && n < N ? v[i] + ep.bias[n] : v[i];
+                        v[i] = z;
+                        a[i] = (ep.flags & EPI_GELU) ? gelu(z) : z;
+                    }
+                }
+                if (ep.flags & EPI_Z32) store_rows(tile, v, lane, ep.c32, ep.ldc32, m_first, M, n0 + c, N);
+                if (ep.flags & EPI_A32) store_rows(tile, a, lane, ep.c32, ep.ldc32, m_first, M, n0 + c, N);
+                if (ep.flags & EPI_A16) store_rows(tile, a, lane, ep.c16, ep.ldc16, m_first, M, n0 + c, N);
+                if ((ep.flags & EPI_A16T) && m < M) {
+#pragma unroll
+                    for (int i = 0; i < 32; i++) {
+                        const int n = n0 + c + i;
+                        if (n < N) ep.c16t[(int64_t)n * ep.ldc16t + m] = __float2bfloat16_rn(a[i]);
                     }
                 }
             }
