@@ -267,7 +267,8 @@ def run_ours(args):
     achieved = bytes_contract / (c_per * 1e-3) / 1e9
     roofline = {"kernel": "k_contract<float> (Toeplitz contraction, active phases)", "bound": "hbm",
                 "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
-                "frac": round(achieved / hbm_peak, 4), "traffic": None,
+                "frac": round(achieved / hbm_peak, 4), "traffic": profiled_traffic(
+                    "k_contract_f32_disk300_205800px.md") if (st.grid_n, n_px) == (300, 205800) else None,
                 "bytes_per_launch": bytes_contract, "ms_per_launch": round(c_per, 5),
                 "peak_source": "measured" if peaks else "fallback",
                 "dominant_kernel": name, "dominant_ms_per_step": round(tot / K, 5)}
@@ -314,6 +315,24 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as tdist
         tdist.destroy_process_group()
+
+
+def profiled_traffic(name):
+    """DRAM bytes read + written per launch from a committed ncu summary (profiles/), or None."""
+    try:
+        text = open(os.path.join(ROOT, "profiles", name)).read()
+    except OSError:
+        return None
+    tot = 0.0
+    for key in ("DRAM read", "DRAM write"):
+        for line in text.splitlines():
+            if line.startswith(f"| {key} |"):
+                val, unit = line.split("|")[2].split()[:2]
+                tot += float(val) * {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}[unit]
+                break
+        else:
+            return None
+    return int(tot)
 
 
 # ------------------------------------------------------------------------------------------

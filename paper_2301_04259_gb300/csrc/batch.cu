@@ -170,9 +170,10 @@ __global__ void k_batch_hist(int N, int max_r, const int* __restrict__ phase_ite
         const int i0 = sg[r].box[0], i1 = sg[r].box[1], j0 = sg[r].box[2], j1 = sg[r].box[3];
         if (i1 < i0 || j1 < j0) continue;
         const int wdt = i1 - i0 + 1;
-        const int64_t area = (int64_t)wdt * (j1 - j0 + 1);
-        for (int64_t t = threadIdx.x; t < area; t += blockDim.x) {
-            const int i = i0 + (int)(t % wdt), jj = j0 + (int)(t / wdt);
+        const int area = wdt * (j1 - j0 + 1);                  // <= N^2 < 2^31
+        for (int t = threadIdx.x; t < area; t += blockDim.x) {
+            const int jr = t / wdt;
+            const int i = i0 + (t - jr * wdt), jj = j0 + jr;
             if (in_earlier_box(sg, r, i, jj)) continue;
             const int64_t c = (int64_t)jj * N + i;
             const int b = cell_bin[c];

@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(256)
 k_ccf_window(int n_lines, const int* __restrict__ U, const T* __restrict__ f,
              const int* __restrict__ valid, const T* __restrict__ wl_, int n_v,
              const int* __restrict__ S, const T* __restrict__ g, double box, int64_t n_px,
-             int n_spec, const T* __restrict__ spectra, double* __restrict__ partial) {
+             int n_spec, const T* __restrict__ spectra, T* __restrict__ partial) {
     typedef typename std::conditional<sizeof(T) == 4, float4, double2>::type V;
     constexpr int VW = sizeof(V) / sizeof(T);
     static_assert(SB % VW == 0, "SB must be a multiple of the vector width");
@@ -224,12 +224,13 @@ k_ccf_window(int n_lines, const int* __restrict__ U, const T* __restrict__ f,
     }
     if (active)
         for (int s = 0; s < ns; s++)
-            partial[((int64_t)blockIdx.x * n_spec + s0 + s) * n_v + k] = (double)acc[s];
+            partial[((int64_t)blockIdx.x * n_spec + s0 + s) * n_v + k] = acc[s];   // FP64 in the reduction
 }
 
 // ccf[t] = sum over chunks of partial[c][t], in a fixed order: kReduceSplit lanes take
 // interleaved chunks, then a fixed shuffle tree adds the lanes.
-__global__ void k_ccf_reduce(int n_chunks, int n_spec, int n_v, const double* __restrict__ partial,
+template <typename TP>
+__global__ void k_ccf_reduce(int n_chunks, int n_spec, int n_v, const TP* __restrict__ partial,
                              double* __restrict__ ccf) {
     const int64_t total = (int64_t)n_spec * n_v;
     const int sub = threadIdx.x % kReduceSplit;
@@ -237,7 +238,7 @@ __global__ void k_ccf_reduce(int n_chunks, int n_spec, int n_v, const double* __
     double s = 0.0;
     if (t < total) {
 #pragma unroll 4
-        for (int c = sub; c < n_chunks; c += kReduceSplit) s += partial[(int64_t)c * total + t];
+        for (int c = sub; c < n_chunks; c += kReduceSplit) s += (double)partial[(int64_t)c * total + t];
     }
     for (int o = kReduceSplit / 2; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, kReduceSplit);
     if (sub == 0 && t < total) ccf[t] = s;
@@ -567,7 +568,7 @@ soap_status rv_ccf_run(soap_ctx* c, const void* spectra_dev, int f32, int n_spec
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM)); \
             k_ccf_window<T, SB, NB><<<GRID, threads, SMEM, c->stream>>>(                          \
                 n_lines, d_U, F, d_valid, WT, n_v, d_S, G, box, c->n_px, n_spec,                   \
-                (const T*)SPEC, d_part);                                                           \
+                (const T*)SPEC, reinterpret_cast<T*>(d_part));                                     \
         } while (0)
         if (f32) {
             if (small) SOAP_CCF_LAUNCH(float, 16, 2, grid32, smem32, d_f32, d_w32, d_g32, spectra_dev);
@@ -592,7 +593,11 @@ soap_status rv_ccf_run(soap_ctx* c, const void* spectra_dev, int f32, int n_spec
     }
     SOAP_LAUNCHED(c);
     int64_t tot = (int64_t)n_spec * n_v * kReduceSplit;
-    k_ccf_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(n_chunks, n_spec, n_v, d_part, d_ccf);
+    if (windowed && f32)      // FP32 partial sums (converted exactly to FP64 here)
+        k_ccf_reduce<float><<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(
+            n_chunks, n_spec, n_v, reinterpret_cast<const float*>(d_part), d_ccf);
+    else
+        k_ccf_reduce<double><<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(n_chunks, n_spec, n_v, d_part, d_ccf);
     SOAP_LAUNCHED(c);
     if (c->profiling) timer_end(c, SOAP_TIMER_CCF, tb);
     SOAP_TIMED(c, SOAP_TIMER_FIT,
@@ -729,7 +734,7 @@ extern "C" soap_status soap_rv_ccf_static(double lambda_start_A, double lambda_e
     }
     SOAP_CUDA(cudaGetLastError());
     int64_t tot = (int64_t)n_spec * n_v * kReduceSplit;
-    k_ccf_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, stream>>>(n_chunks, n_spec, n_v, d_part, d_ccf);
+    k_ccf_reduce<double><<<(unsigned)((tot + 255) / 256), 256, 0, stream>>>(n_chunks, n_spec, n_v, d_part, d_ccf);
     SOAP_CUDA(cudaGetLastError());
     k_gauss_fit<<<n_spec, kFitThreads, 0, stream>>>(n_spec, n_v, v_lo, v_step, d_ccf, d_y, rv_kms, fit_params);
     SOAP_CUDA(cudaGetLastError());

@@ -85,10 +85,10 @@ __global__ void k_phase_hist(int N, int n_regions, const RegionGeo* __restrict__
         const int i0 = sg[r].box[0], i1 = sg[r].box[1], j0 = sg[r].box[2], j1 = sg[r].box[3];
         if (i1 < i0 || j1 < j0) continue;
         const int wdt = i1 - i0 + 1;
-        const int64_t area = (int64_t)wdt * (j1 - j0 + 1);
-        for (int64_t t = (int64_t)split * blockDim.x + threadIdx.x; t < area;
-             t += (int64_t)n_split * blockDim.x) {
-            const int i = i0 + (int)(t % wdt), jj = j0 + (int)(t / wdt);
+        const int area = wdt * (j1 - j0 + 1);                  // <= N^2 < 2^31
+        for (int t = split * (int)blockDim.x + (int)threadIdx.x; t < area; t += n_split * (int)blockDim.x) {
+            const int jr = t / wdt;
+            const int i = i0 + (t - jr * wdt), jj = j0 + jr;
             if (in_earlier_box(sg, r, i, jj)) continue;
             const int64_t c = (int64_t)jj * N + i;
             const int b = cell_bin[c];
