@@ -37,10 +37,13 @@ struct PBlockDev {
     int item, first_phase, np, pad;
 };
 
-// Split an integer intensity into its two taps: k1 = floor(I w), k0 = I - k1 (exact sum).
+// Split an integer intensity into its two taps: k1 = floor(|I| w / 2^32) (sign of I),
+// k0 = I - k1 (exact sum).  With |I| = hi 2^32 + lo, floor(|I| w / 2^32) = hi w + umulhi(lo, w):
+// 32-bit multiplies only.
 __device__ __forceinline__ void split_fx(long long I, unsigned int wfx, long long& k0, long long& k1) {
     const unsigned long long a = I >= 0 ? (unsigned long long)I : (unsigned long long)(-I);
-    const unsigned long long h = __umul64hi(a, (unsigned long long)wfx << 32);
+    const unsigned int hi = (unsigned int)(a >> 32), lo = (unsigned int)a;
+    const unsigned long long h = (unsigned long long)hi * wfx + __umulhi(lo, wfx);
     k1 = I >= 0 ? (long long)h : -(long long)h;
     k0 = I - k1;
 }
@@ -73,7 +76,7 @@ __global__ void k_batch_items(int N, int n_mu, int n_taps, int tap_min, double i
                               const long long* __restrict__ IB, int* __restrict__ colj,
                               unsigned int* __restrict__ colw, long long* __restrict__ kq,
                               long long* qtoff, int* qgs, float* qc32, int q_max_taps, double inv_scale,
-                              int64_t row_len, int64_t pad, unsigned int* flags) {
+                              int fx_bits, int64_t row_len, int64_t pad, unsigned int* flags) {
     extern __shared__ long long hist[];                  // [n_mu][n_taps]
     const int it = blockIdx.x;
     const int nb = n_mu * n_taps;
@@ -111,7 +114,7 @@ __global__ void k_batch_items(int N, int n_mu, int n_taps, int tap_min, double i
     for (int t = threadIdx.x; t < nb; t += blockDim.x) dst[t] = hist[t];
     __threadfence_block();
     __syncthreads();
-    build_taps_dev(dst, 0, 1, 1, n_mu, n_taps, tap_min, 1, 0, inv_scale, row_len, pad,
+    build_taps_dev(dst, 0, 1, 1, n_mu, n_taps, tap_min, 1, 0, inv_scale, fx_bits, row_len, pad,
                    qtoff + (int64_t)it * q_max_taps, qgs + (int64_t)it * 2, nullptr,
                    qc32 + (int64_t)it * q_max_taps, q_max_taps, hist, flags);
 }
@@ -150,7 +153,8 @@ __global__ void k_batch_hist(int N, int max_r, const int* __restrict__ phase_ite
                              const int32_t* __restrict__ cell_bin, const long long* __restrict__ cell_Ifx,
                              const int* __restrict__ colj, const unsigned int* __restrict__ colw,
                              int tap_min, int n_taps, int n_mu, int n_class, long long* kfix, int use_smem,
-                             int PB, double inv_scale, int64_t row_len, int64_t pad, long long* toff, int* gstart,
+                             int PB, double inv_scale, int fx_bits, int64_t row_len, int64_t pad, long long* toff,
+                             int* gstart,
                              float* c32, int max_taps, int* counters, int taps_smem, unsigned int* flags) {
     __shared__ RegionGeo sg[SOAP_MAX_REGIONS];
     extern __shared__ long long hist_sm[];
@@ -166,25 +170,26 @@ __global__ void k_batch_hist(int N, int max_r, const int* __restrict__ phase_ite
     __syncthreads();
     const int* cj = colj + (int64_t)it * N;
     const unsigned int* cw = colw + (int64_t)it * N;
+    const float invN = 1.0f / small_int_to_float(N);
     for (int r = 0; r < nr; r++) {
         const int i0 = sg[r].box[0], i1 = sg[r].box[1], j0 = sg[r].box[2], j1 = sg[r].box[3];
         if (i1 < i0 || j1 < j0) continue;
         const int wdt = i1 - i0 + 1;
         const int area = wdt * (j1 - j0 + 1);                  // <= N^2 < 2^31
-        for (int t = threadIdx.x; t < area; t += blockDim.x) {
-            const int jr = t / wdt;
-            const int i = i0 + (t - jr * wdt), jj = j0 + jr;
+        BoxWalk wk((int)threadIdx.x, (int)blockDim.x, wdt);
+        for (int t = threadIdx.x; t < area; t += blockDim.x, wk.next()) {
+            const int i = i0 + wk.col, jj = j0 + wk.row;
             if (in_earlier_box(sg, r, i, jj)) continue;
-            const int64_t c = (int64_t)jj * N + i;
+            const int c = jj * N + i;                          // N^2 < 2^31
             const int b = cell_bin[c];
             if (b < 0) continue;
-            const int owner = cell_owner(sg, nr, N, i, jj, cell_mu32[c], cell_mu, c);
+            const int owner = cell_owner(sg, nr, N, invN, i, jj, cell_mu32[c], cell_mu, c);
             if (owner < 0) continue;
             const int kk = cj[i] - tap_min;
             if (kk < 1 || kk >= n_taps) { atomicOr(flags, kFlagTapRange); continue; }
             long long k0, k1;
             split_fx(cell_Ifx[c], cw[i], k0, k1);
-            long long* h = hist + ((int64_t)sg[owner].cls * n_mu + b) * n_taps;
+            long long* h = hist + (sg[owner].cls * n_mu + b) * n_taps;
             atomicAdd((unsigned long long*)&h[kk], (unsigned long long)k0);
             atomicAdd((unsigned long long*)&h[kk - 1], (unsigned long long)k1);
         }
@@ -206,7 +211,7 @@ __global__ void k_batch_hist(int N, int max_r, const int* __restrict__ phase_ite
     if (s_last) {
         __threadfence();
         build_taps_dev(kfix + (int64_t)pbd.first_phase * nb, 0, pbd.np, n_class, n_mu, n_taps, tap_min, PB, 1,
-                       inv_scale, row_len, pad, toff + (int64_t)pbk * max_taps, gstart + (int64_t)pbk * (n_class + 2),
+                       inv_scale, fx_bits, row_len, pad, toff + (int64_t)pbk * max_taps, gstart + (int64_t)pbk * (n_class + 2),
                        nullptr, c32 + (int64_t)pbk * max_taps * PB, max_taps, taps_smem ? hist_sm : nullptr, flags);
     }
 }
@@ -312,7 +317,7 @@ static soap_status enqueue_batch(soap_ctx* c, const BatchShape& b, float* out) {
                    1.0 / std::expm1(c->delta), c->b_items.as<BatchItemDev>(), c->b_IB.as<long long>(),
                    c->b_colj.as<int>(), c->b_colw.as<unsigned int>(), c->b_kq.as<long long>(),
                    c->b_qtoff.as<long long>(), c->b_qgs.as<int>(), c->b_qc32.as<float>(), q_max_taps, inv_scale,
-                   c->row_len, c->pad, c->flags);
+                   c->fx_bits, c->row_len, c->pad, c->flags);
                SOAP_LAUNCHED(c));
     // 3 quiet spectra (not needed for residual output)
     if (!b.residual) {
@@ -346,7 +351,8 @@ static soap_status enqueue_batch(soap_ctx* c, const BatchShape& b, float* out) {
                    c->b_items.as<BatchItemDev>(), c->b_pblocks.as<PBlockDev>(), c->b_geo.as<RegionGeo>(),
                    c->cell_mu, c->cell_mu32, c->cell_bin, c->b_cellIfx.as<long long>(), c->b_colj.as<int>(),
                    c->b_colw.as<unsigned int>(), c->tap_min, c->n_taps, c->n_mu, b.n_class,
-                   c->b_kfix.as<long long>(), b.use_smem, kVariants[b.variant].PB, inv_scale, c->row_len, c->pad,
+                   c->b_kfix.as<long long>(), b.use_smem, kVariants[b.variant].PB, inv_scale, c->fx_bits, c->row_len,
+                   c->pad,
                    c->b_toff.as<long long>(), c->b_gstart.as<int>(), c->b_coefs.as<float>(), b.max_taps,
                    c->b_counters.as<int>(), b.taps_smem, c->flags);
                SOAP_LAUNCHED(c));

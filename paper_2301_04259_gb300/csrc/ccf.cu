@@ -156,13 +156,17 @@ k_ccf_window(int n_lines, const int* __restrict__ U, const T* __restrict__ f,
         }
         if (staged) {
             // one pixel per thread and step, all SB spectra at once (SB loads in flight)
+            const T* base = spectra + (int64_t)s0 * n_px + n_lo;
             for (int x = threadIdx.x; x < W; x += blockDim.x) {
                 const int64_t pix = n_lo + x;
                 const bool on = pix >= 0 && pix < n_px;
+                const T* col = base + x;
                 T v[SB];
 #pragma unroll
-                for (int s = 0; s < SB; s++)
-                    v[s] = (on && s < ns) ? __ldg(spectra + (int64_t)(s0 + s) * n_px + pix) : T(0);
+                for (int s = 0; s < SB; s++) {
+                    v[s] = (on && s < ns) ? __ldg(col) : T(0);
+                    col += n_px;
+                }
                 V* dst = reinterpret_cast<V*>(win + x * ROW);
 #pragma unroll
                 for (int q = 0; q < SB / VW; q++) {
@@ -189,7 +193,8 @@ k_ccf_window(int n_lines, const int* __restrict__ U, const T* __restrict__ f,
 #pragma unroll
                 for (int i = 0; i < NB; i++) {
                     const T lo = i == 0 ? phi : T(i);
-                    const T ov = fmax(fmin(end, T(i + 1)) - lo, T(0));
+                    const T hi = end < T(i + 1) ? end : T(i + 1);
+                    const T ov = hi > lo ? hi - lo : T(0);        // overlap of the box with pixel n + i
                     const T cwt = wl * ov;
                     const V* src = reinterpret_cast<const V*>(win + (nc + i) * ROW);
 #pragma unroll

@@ -67,7 +67,7 @@ __global__ void k_phase_hist(int N, int n_regions, const RegionGeo* __restrict__
                              const int32_t* __restrict__ cell_j, const int32_t* __restrict__ cell_bin,
                              const long long* __restrict__ cell_k0, const long long* __restrict__ cell_k1,
                              int tap_min, int n_taps, int n_mu, int n_class, long long* kout,
-                             int use_smem, int PB, double inv_scale, int64_t row_len, int64_t pad,
+                             int use_smem, int PB, double inv_scale, int fx_bits, int64_t row_len, int64_t pad,
                              long long* toff, int* gstart, double* c64, float* c32, int max_taps,
                              int* counters, int taps_smem, unsigned int* flags) {
     __shared__ RegionGeo sg[SOAP_MAX_REGIONS];
@@ -81,23 +81,25 @@ __global__ void k_phase_hist(int N, int n_regions, const RegionGeo* __restrict__
     if (use_smem)
         for (int t = threadIdx.x; t < nb; t += blockDim.x) hist[t] = 0;
     __syncthreads();
+    const float invN = 1.0f / small_int_to_float(N);
     for (int r = 0; r < n_regions; r++) {
         const int i0 = sg[r].box[0], i1 = sg[r].box[1], j0 = sg[r].box[2], j1 = sg[r].box[3];
         if (i1 < i0 || j1 < j0) continue;
         const int wdt = i1 - i0 + 1;
         const int area = wdt * (j1 - j0 + 1);                  // <= N^2 < 2^31
-        for (int t = split * (int)blockDim.x + (int)threadIdx.x; t < area; t += n_split * (int)blockDim.x) {
-            const int jr = t / wdt;
-            const int i = i0 + (t - jr * wdt), jj = j0 + jr;
+        const int t0 = split * (int)blockDim.x + (int)threadIdx.x, step = n_split * (int)blockDim.x;
+        BoxWalk wk(t0, step, wdt);
+        for (int t = t0; t < area; t += step, wk.next()) {
+            const int i = i0 + wk.col, jj = j0 + wk.row;
             if (in_earlier_box(sg, r, i, jj)) continue;
-            const int64_t c = (int64_t)jj * N + i;
+            const int c = jj * N + i;                          // N^2 < 2^31
             const int b = cell_bin[c];
             if (b < 0) continue;
-            const int owner = cell_owner(sg, n_regions, N, i, jj, cell_mu32[c], cell_mu, c);
+            const int owner = cell_owner(sg, n_regions, N, invN, i, jj, cell_mu32[c], cell_mu, c);
             if (owner < 0) continue;
             const int kk = cell_j[c] - tap_min;
             if (kk < 1 || kk >= n_taps) { atomicOr(flags, kFlagTapRange); continue; }
-            long long* h = hist + ((int64_t)sg[owner].cls * n_mu + b) * n_taps;
+            long long* h = hist + (sg[owner].cls * n_mu + b) * n_taps;
             atomicAdd((unsigned long long*)&h[kk], (unsigned long long)cell_k0[c]);
             atomicAdd((unsigned long long*)&h[kk - 1], (unsigned long long)cell_k1[c]);
         }
@@ -121,7 +123,7 @@ __global__ void k_phase_hist(int N, int n_regions, const RegionGeo* __restrict__
     __syncthreads();
     if (s_last) {
         __threadfence();
-        build_taps_dev(kout, pbk, (int)gridDim.x, n_class, n_mu, n_taps, tap_min, PB, 1, inv_scale, row_len,
+        build_taps_dev(kout, pbk, (int)gridDim.x, n_class, n_mu, n_taps, tap_min, PB, 1, inv_scale, fx_bits, row_len,
                        pad, toff, gstart, c64, c32, max_taps, taps_smem ? hist_sm : nullptr, flags);
     }
 }
@@ -285,7 +287,7 @@ soap_status toeplitz_active(soap_ctx* c, const RegionDev* regions_host, int n_re
                k_phase_hist<<<hgrid, 256, smem, c->stream>>>(
                    c->N, n_regions, c->region_geo.as<RegionGeo>(), c->cell_mu, c->cell_mu32, c->cell_j,
                    c->cell_bin, c->cell_k0, c->cell_k1, c->tap_min, c->n_taps, c->n_mu, ncl, kfix,
-                   use_smem, PB, std::ldexp(1.0, -c->fx_bits), c->row_len, c->pad, toff, gstart, c64, c32,
+                   use_smem, PB, std::ldexp(1.0, -c->fx_bits), c->fx_bits, c->row_len, c->pad, toff, gstart, c64, c32,
                    mt, c->job_counters.as<int>(), taps_smem, c->flags);
                SOAP_LAUNCHED(c));
     ClassTypes ct{};

@@ -234,10 +234,30 @@ __device__ __forceinline__ bool in_earlier_box(const RegionGeo* sg, int r, int i
 // (x, y, mu) . P >= sqrt(1 - r^2); the last region in list order that contains it owns it
 // (-1: none).  An FP32 test decides cells farther than 2e-6 from the edge (its error is below
 // 1e-6); the others are decided by the explicitly rounded FP64 sequence.
-__device__ __forceinline__ int cell_owner(const RegionGeo* sg, int n_regions, int N, int i, int j, float muf,
-                                          const double* __restrict__ cell_mu, int64_t c) {
-    const float invN = 1.0f / (float)N;
-    const float xf = (float)(2 * i + 1 - N) * invN, yf = (float)(2 * j + 1 - N) * invN;
+// float(v) for |v| < 2^22 without a conversion instruction: the bits 0x4B400000 + v are the float
+// 2^23 + 2^22 + v exactly, and one subtraction leaves v.
+__device__ __forceinline__ float small_int_to_float(int v) {
+    return __int_as_float(0x4B400000 + v) - 12582912.0f;
+}
+
+// Box cells in the order t = 0, 1, ... (row-major, width w) for a thread that starts at t0 and
+// steps by `step`: the quotient and remainder of the step are taken once, so the walk needs no
+// division per cell.
+struct BoxWalk {
+    int row, col, dq, dr, w;
+    __device__ __forceinline__ BoxWalk(int t0, int step, int width) : w(width) {
+        row = t0 / width; col = t0 - row * width;
+        dq = step / width; dr = step - dq * width;
+    }
+    __device__ __forceinline__ void next() {
+        row += dq; col += dr;
+        if (col >= w) { col -= w; row++; }
+    }
+};
+
+__device__ __forceinline__ int cell_owner(const RegionGeo* sg, int n_regions, int N, float invN, int i, int j,
+                                          float muf, const double* __restrict__ cell_mu, int64_t c) {
+    const float xf = small_int_to_float(2 * i + 1 - N) * invN, yf = small_int_to_float(2 * j + 1 - N) * invN;
     int owner = -1;
     for (int q = 0; q < n_regions; q++) {
         const float df = fmaf(xf, sg[q].Pf[0], fmaf(yf, sg[q].Pf[1], muf * sg[q].Pf[2]));

@@ -57,7 +57,7 @@ k_geometry(int N, double vsini, double sin_i, double cos_i, double alpha, double
            double* cell_I, double* cell_w, double* cell_mu, float* cell_mu32, int32_t* cell_j,
            int32_t* cell_bin, long long* cell_k0, long long* cell_k1, long long* kq_fixed,
            long long* sum2, long long* qtoff, int* qgstart, double* qc64, float* qc32, int q_max_taps,
-           int64_t row_len, int64_t pad, int* counter, unsigned int* flags) {
+           int64_t row_len, int64_t pad, int fx_bits, int* counter, unsigned int* flags) {
     extern __shared__ long long hist[];                  // [n_mu][n_taps]
     __shared__ double sy;
     const int nb = n_mu * n_taps;
@@ -126,7 +126,7 @@ k_geometry(int N, double vsini, double sin_i, double cos_i, double alpha, double
     __syncthreads();
     if (s_last) {
         __threadfence();
-        build_taps_dev(kq_fixed, 0, 1, 1, n_mu, n_taps, tap_min, 1, 0, 1.0 / scale, row_len, pad, qtoff,
+        build_taps_dev(kq_fixed, 0, 1, 1, n_mu, n_taps, tap_min, 1, 0, 1.0 / scale, fx_bits, row_len, pad, qtoff,
                        qgstart, qc64, qc32, q_max_taps, hist, flags);
     }
 }
@@ -185,7 +185,7 @@ soap_status geometry_init(soap_ctx* c) {
         1.0 / c->delta, c->delta, 1.0 / std::expm1(c->delta), c->n_mu, mus, c->mu_sorted, c->tap_min,
         tap_max, c->n_taps, scale, c->cell_I, c->cell_w, c->cell_mu, c->cell_mu32, c->cell_j,
         c->cell_bin, c->cell_k0, c->cell_k1, c->kq_fixed, c->sum_I_fixed, c->qtoff, c->qgstart, c->qc64,
-        c->qc32, c->n_mu * SOAP_MAX_TAPS, c->row_len, c->pad, c->geo_counter, c->flags);
+        c->qc32, c->n_mu * SOAP_MAX_TAPS, c->row_len, c->pad, c->fx_bits, c->geo_counter, c->flags);
     SOAP_LAUNCHED(c);
     if (c->profiling) timer_end(c, SOAP_TIMER_GEOMETRY, tb);
     return SOAP_OK;

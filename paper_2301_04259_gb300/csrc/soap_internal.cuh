@@ -219,6 +219,33 @@ soap_status rv_ccf_run(soap_ctx* c, const void* spectra_dev, int f32, int n_spec
 
 }  // namespace soap
 
+// K * 2^-bits rounded to the nearest float (ties to even) with integer operations only: the
+// fixed-point kernels reach 2^61, and GB300 converts 64-bit integers through its (slow) FP64
+// unit.  Valid for |K| < 2^63 and results in the normal float range.
+__device__ __forceinline__ float fixed_to_float(long long K, int bits) {
+    if (K == 0) return 0.0f;
+    const unsigned int sign = K < 0 ? 0x80000000u : 0u;
+    unsigned long long a = K < 0 ? (unsigned long long)(-K) : (unsigned long long)K;
+    const int e = 63 - __clzll(a);                    // a in [2^e, 2^(e+1))
+    unsigned int m;                                   // 24-bit significand with the hidden bit
+    int ex = e;
+    if (e <= 23) {
+        m = (unsigned int)(a << (23 - e));
+    } else {
+        const int sh = e - 23;
+        const unsigned long long q = a >> sh;
+        const unsigned long long rem = a & ((1ull << sh) - 1ull);
+        const unsigned long long half = 1ull << (sh - 1);
+        m = (unsigned int)q;
+        if (rem > half || (rem == half && (m & 1u))) {
+            m++;
+            if (m == (1u << 24)) { m >>= 1; ex++; }
+        }
+    }
+    const int biased = ex - bits + 127;               // value = m 2^(ex - 23) 2^-bits
+    return __uint_as_float(sign | ((unsigned int)biased << 23) | (m & 0x7FFFFFu));
+}
+
 // ---------------------------------------------------------------------------------------
 // tap tables of the Toeplitz contraction (shared by geometry.cu, contract.cu and batch.cu)
 // ---------------------------------------------------------------------------------------
@@ -237,6 +264,33 @@ __device__ __forceinline__ double expm1_small(double e) {
 }
 
 
+// K * 2^-bits rounded to the nearest float (ties to even) with integer operations only: the
+// fixed-point kernels reach 2^61, and GB300 converts 64-bit integers through its (slow) FP64
+// unit.  Valid for |K| < 2^63 and results in the normal float range.
+__device__ __forceinline__ float fixed_to_float(long long K, int bits) {
+    if (K == 0) return 0.0f;
+    const unsigned int sign = K < 0 ? 0x80000000u : 0u;
+    unsigned long long a = K < 0 ? (unsigned long long)(-K) : (unsigned long long)K;
+    const int e = 63 - __clzll(a);                    // a in [2^e, 2^(e+1))
+    unsigned int m;                                   // 24-bit significand with the hidden bit
+    int ex = e;
+    if (e <= 23) {
+        m = (unsigned int)(a << (23 - e));
+    } else {
+        const int sh = e - 23;
+        const unsigned long long q = a >> sh;
+        const unsigned long long rem = a & ((1ull << sh) - 1ull);
+        const unsigned long long half = 1ull << (sh - 1);
+        m = (unsigned int)q;
+        if (rem > half || (rem == half && (m & 1u))) {
+            m++;
+            if (m == (1u << 24)) { m >>= 1; ex++; }
+        }
+    }
+    const int biased = ex - bits + 127;               // value = m 2^(ex - 23) 2^-bits
+    return __uint_as_float(sign | ((unsigned int)biased << 23) | (m & 0x7FFFFFu));
+}
+
 // ---------------------------------------------------------------------------------------
 // tap tables of the Toeplitz contraction
 // ---------------------------------------------------------------------------------------
@@ -247,14 +301,16 @@ __device__ __forceinline__ double expm1_small(double e) {
 //   toff[tap]     element offset bin * row_len + pad - k: the row value S_b[m - k] of pixel m
 //                 is rows[toff + m]
 //   coef[tap][PB] kernel value of each phase of the block (0 where a phase has none)
-// kfix: [n_phases][n_class][n_mu][n_taps].  mode 0 (quiet): one group, +K of class 0.
-// mode 1 (active): group 0 = -sum_cl K (quiet rows), group g = +K of class g-1.
-// Block pb covers phases pb*PB .. pb*PB+PB-1; its outputs start at toff + pb*max_taps,
+// kfix: [n_phases][n_class][n_mu][n_taps] in units of 2^-fx_bits (inv_scale = 2^-fx_bits).
+// mode 0 (quiet): one group, +K of class 0.  mode 1 (active): group 0 = -sum_cl K (quiet rows),
+// group g = +K of class g-1.  Block pb covers phases pb*PB .. pb*PB+PB-1; its outputs start at
+// toff + pb*max_taps,
 // gstart + pb*(G+1) and coef + pb*max_taps*PB.  A table that would exceed max_taps is left
 // empty and flags kFlagJobOverflow.
 __device__ __forceinline__ void build_taps_dev(const long long* __restrict__ kfix, int pb, int n_phases,
                                                int n_class, int n_mu, int n_taps, int tap_min, int PB, int mode,
-                                               double inv_scale, int64_t row_len, int64_t pad, long long* toff,
+                                               double inv_scale, int fx_bits, int64_t row_len, int64_t pad,
+                                               long long* toff,
                                                int* gstart, double* c64, float* c32, int max_taps,
                                                long long* s_k, unsigned int* flags) {
     __shared__ int s_lo[(1 + SOAP_MAX_CLASSES) * SOAP_MAX_MU];
@@ -365,9 +421,9 @@ __device__ __forceinline__ void build_taps_dev(const long long* __restrict__ kfi
             toff[tap0 + kk] = (int64_t)b * row_len + pad - (tap_min + s_lo[t] + kk);
         for (int e = lane; e < nk * PB; e += 32) {
             const int kk = e / PB, pl = e % PB;
-            const double v = (double)value(g, b, pl, s_lo[t] + kk) * inv_scale;
-            if (c64) c64[tap0 * PB + e] = v;
-            c32[tap0 * PB + e] = (float)v;
+            const long long K = value(g, b, pl, s_lo[t] + kk);
+            if (c64) c64[tap0 * PB + e] = (double)K * inv_scale;
+            c32[tap0 * PB + e] = fixed_to_float(K, fx_bits);
         }
     }
 }
