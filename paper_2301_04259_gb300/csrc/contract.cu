@@ -172,8 +172,15 @@ static soap_status launch_contract(soap_ctx* c, int n_blocks, int G, int max_tap
 }
 
 // Phase-block sizes and pixels per thread of the two precisions.
+// (build-time overrides exist for measuring other tile shapes)
+#ifndef SOAP_PB32
+#define SOAP_PB32 4
+#endif
+#ifndef SOAP_R32
+#define SOAP_R32 4
+#endif
 constexpr int kPB64 = 4, kR64 = 2, kT64 = 128;
-constexpr int kPB32 = 8, kR32 = 4, kT32 = 128;
+constexpr int kPB32 = SOAP_PB32, kR32 = SOAP_R32, kT32 = 128;
 
 // tap-table + coefficient scratch for a kernel set kfix with n_phases "phases" in blocks of PB
 static soap_status tap_buffers(soap_ctx* c, int n_phases, int n_class, int PB, int mode, long long** toff,
