@@ -526,6 +526,52 @@ def test_gaussian_fit_recovers_exact_gaussian():
     np.testing.assert_allclose(got, p, rtol=1e-10, atol=1e-11)
 
 
+def _mp_cost(v, c, p, mp):
+    A, B, mu, s = (mp.mpf(float(x)) for x in p)
+    tot = mp.mpf(0)
+    for vi, ci in zip(v, c):
+        r = A + B * mp.exp(-((mp.mpf(float(vi)) - mu) / s) ** 2 / 2) - mp.mpf(float(ci))
+        tot += r * r
+    return tot
+
+
+@pytest.mark.parametrize("shape", ["flat_bottom", "ccf"])
+def test_gaussian_fit_is_the_least_squares_minimum(shape):
+    """Sect. 4.1: the RV is the centre of the least-squares Gaussian.  On dips far from a
+    Gaussian, the fitted parameters must be a local minimum of the cost at a resolution of
+    1e-10 (relative to the width, or to the continuum for A and B): the cost, evaluated in
+    40-digit arithmetic, may not drop under a move of that size in any parameter.  A fit that
+    stops 2.5e-9 relative short of the minimum (what MINPACK's own stopping rule allowed)
+    fails this on one side."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    v = -22.0 + 0.25 * np.arange(177)
+    if shape == "flat_bottom":
+        c = 1000.0 - 300.0 * np.exp(-np.abs(v - 0.3) ** 3 / 60.0) + 4.0 * np.cos(v / 2.0)
+    else:
+        c = _rotation_ccf(v)
+    p = O.fit_gaussian(v, c)
+    base = _mp_cost(v, c, p, mp)
+    steps = np.array([abs(p[0]), abs(p[0]), p[3], p[3]]) * 1e-10
+    for i in range(4):
+        for sgn in (1.0, -1.0):
+            q = p.copy()
+            q[i] += sgn * steps[i]
+            assert _mp_cost(v, c, q, mp) >= base, (i, sgn)
+
+
+def _rotation_ccf(v):
+    """CCF-like dip: a rotationally broadened line (vsini 2 km/s, linear limb darkening 0.6)
+    convolved with a Gaussian of 2.5 km/s, on a continuum, by direct quadrature."""
+    x = np.linspace(-1.0, 1.0, 4001)
+    prof = (2 * 0.4 * np.sqrt(1 - x ** 2) + 0.5 * np.pi * 0.6 * (1 - x ** 2))
+    prof /= prof.sum()
+    out = np.empty_like(v)
+    for i, vi in enumerate(v):
+        out[i] = 5000.0 - 1800.0 * np.sum(prof * np.exp(-0.5 * ((vi - 2.0 * x - 0.17) / 2.5) ** 2))
+    return out
+
+
 @pytest.mark.parametrize("k", [1, -3])
 def test_integer_pixel_shift_changes_rv_by_c_tanh_k_delta(k):
     """Moving the spectrum by k pixels is a Doppler shift with atanh(v/c) = k Delta.  On a
