@@ -16,7 +16,7 @@
  *   - Sect. 4.1: CCF of the spectrum with a line mask (the RV is then the centre of a
  *     Gaussian fitted to it; the fit is done in oracle.py).
  *
- * Readings where the paper is silent (all listed in the design doc):
+ * Readings where the paper is silent:
  *   - the grid is log-uniform, lambda_n = lambda_s exp(n Delta), both ends included;
  *   - interpolation is a gather: output pixel m takes the shifted interval
  *     lambda'_n <= lambda_m < lambda'_{n+1} (Eqs. 9-10 read as a bracketing); outside the

@@ -280,34 +280,13 @@ __device__ bool solve4f(float M[4][4], float b[4], float x[4]) {
     return isfinite(x[0]) && isfinite(x[1]) && isfinite(x[2]) && isfinite(x[3]);
 }
 
-// Solve the 4x4 system M x = b by Gaussian elimination with partial pivoting (FP64).
-__device__ bool solve4(double M[4][4], double b[4], double x[4]) {
-    for (int col = 0; col < 4; col++) {
-        int piv = col;
-        for (int r = col + 1; r < 4; r++)
-            if (fabs(M[r][col]) > fabs(M[piv][col])) piv = r;
-        if (!(fabs(M[piv][col]) > 0.0)) return false;
-        if (piv != col) {
-            for (int q = 0; q < 4; q++) { double t = M[col][q]; M[col][q] = M[piv][q]; M[piv][q] = t; }
-            double t = b[col]; b[col] = b[piv]; b[piv] = t;
-        }
-        for (int r = col + 1; r < 4; r++) {
-            double f = M[r][col] / M[col][col];
-            for (int q = col; q < 4; q++) M[r][q] -= f * M[col][q];
-            b[r] -= f * b[col];
-        }
-    }
-    for (int r = 3; r >= 0; r--) {
-        double s = b[r];
-        for (int q = r + 1; q < 4; q++) s -= M[r][q] * x[q];
-        x[r] = s / M[r][r];
-    }
-    return true;
-}
-
 constexpr int kFitThreads = 128;
 constexpr int kFitWarps = kFitThreads / 32;
-constexpr int kFitCache = 4;           // velocities cached in registers per thread
+constexpr int kFitCache = 4;            // velocities cached in registers per thread
+constexpr int kFitPassesA = 80;         // FP32 Levenberg-Marquardt passes at most
+constexpr int kFitPassesB = 8;          // Newton passes at most
+constexpr float kFitTolA = 1e-4f;       // scaled step at which the FP32 phase hands over
+constexpr float kFitTolB = 1e-6f;       // scaled Newton step after which one more step is exact
 
 // Column sums of a [kFitThreads][NV] shared table in a fixed order: NV x 8 threads add 16 rows
 // each, then NV threads add the 8 partial sums.  Thread 0 returns the totals in out.
@@ -335,61 +314,156 @@ __device__ __forceinline__ void table_sum(const double (&v)[NV], double* tab, do
         for (int q = 0; q < NV; q++) out[q] = part[8 * NV + q];
 }
 
-// One pass over the velocity grid in scaled variables: u = (v - c0)/s0, model
-// a + b exp(-(u - m)^2 / (2 w^2)) against y = CCF / scale.  Sums J^T J (10), J^T r (4), cost.
-__device__ __forceinline__ void fit_pass(const double* __restrict__ y, int n_v, const double* ucache,
-                                         double u0, double du, const double p[4], double* tab,
-                                         double* part, double (&out)[15]) {
-    double acc[15];
+// Block-wide sums of NF floats and ND doubles that come out bit-identical in every thread: a
+// xor butterfly inside each warp (addition commutes, so every lane ends with the same warp
+// total), one shared row per warp, then the rows added in warp order.  Two buffers alternate,
+// so one barrier per call suffices (a buffer is rewritten only after the next call's barrier).
+constexpr int kSumF = 15, kSumD = 5;
+template <int NF, int ND>
+__device__ __forceinline__ void block_sums(float* f, double* d, float* sf, double* sd, int& buf) {
+    static_assert(NF <= kSumF && ND <= kSumD, "shared rows too short");
 #pragma unroll
-    for (int q = 0; q < 15; q++) acc[q] = 0.0;
-    const double iw = 1.0 / p[3];
-    const double iw2 = iw * iw;
-    int i = 0;
-    for (int k = threadIdx.x; k < n_v; k += kFitThreads, i++) {
-        const double u = i < kFitCache ? ucache[i] : fma((double)k, du, u0);
-        const double d = u - p[2];
-        const double e = exp(-0.5 * d * d * iw2);
-        const double r = fma(p[1], e, p[0]) - y[k];
-        const double t = p[1] * e * d * iw2;
-        const double J[4] = {1.0, e, t, t * d * iw};
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int q = 0; q < NF; q++) f[q] += __shfl_xor_sync(0xffffffffu, f[q], o);
+#pragma unroll
+        for (int q = 0; q < ND; q++) d[q] += __shfl_xor_sync(0xffffffffu, d[q], o);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float* rf = sf + buf * kFitWarps * kSumF;
+    double* rd = sd + buf * kFitWarps * kSumD;
+    if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < NF; q++) rf[warp * kSumF + q] = f[q];
+#pragma unroll
+        for (int q = 0; q < ND; q++) rd[warp * kSumD + q] = d[q];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < NF; q++) {
+        float t = rf[q];
+#pragma unroll
+        for (int w = 1; w < kFitWarps; w++) t += rf[w * kSumF + q];
+        f[q] = t;
+    }
+#pragma unroll
+    for (int q = 0; q < ND; q++) {
+        double t = rd[q];
+#pragma unroll
+        for (int w = 1; w < kFitWarps; w++) t += rd[w * kSumD + q];
+        d[q] = t;
+    }
+    buf ^= 1;
+}
+
+// First phase, FP32: one pass at scaled parameters p = (a, b, m, w) of the model
+// a + b exp(-(u - m)^2 / (2 w^2)) against y.  Returns in every thread the sums J^T J (10, upper
+// triangle by rows), J^T r (4) and r^2.  uc / yc hold this thread's first kFitCache abscissae
+// and ordinates; further points are read from y.
+__device__ __forceinline__ void pass_a(const float p[4], int n_v, const float (&uc)[kFitCache],
+                                       const float (&yc)[kFitCache], const double* __restrict__ y,
+                                       float u0, float du, float* sf, double* sd, int& buf,
+                                       float (&acc)[15]) {
+#pragma unroll
+    for (int q = 0; q < 15; q++) acc[q] = 0.0f;
+    const float iw = 1.0f / p[3];
+    const float iw2 = iw * iw;
+    auto point = [&](float u, float yk) {
+        const float d = u - p[2];
+        const float e = expf(-0.5f * d * d * iw2);
+        const float r = fmaf(p[1], e, p[0]) - yk;
+        const float t = p[1] * e * d * iw2;
+        const float J[4] = {1.0f, e, t, t * d * iw};
         int q = 0;
 #pragma unroll
         for (int a = 0; a < 4; a++)
 #pragma unroll
-            for (int b = a; b < 4; b++) { acc[q] = fma(J[a], J[b], acc[q]); q++; }
+            for (int b = a; b < 4; b++) { acc[q] = fmaf(J[a], J[b], acc[q]); q++; }
 #pragma unroll
-        for (int a = 0; a < 4; a++) acc[10 + a] = fma(J[a], r, acc[10 + a]);
-        acc[14] = fma(r, r, acc[14]);
-    }
-    table_sum<15>(acc, tab, part, out);
+        for (int a = 0; a < 4; a++) acc[10 + a] = fmaf(J[a], r, acc[10 + a]);
+        acc[14] = fmaf(r, r, acc[14]);
+    };
+#pragma unroll
+    for (int i = 0; i < kFitCache; i++)
+        if (threadIdx.x + i * kFitThreads < n_v) point(uc[i], yc[i]);
+    for (int k = threadIdx.x + kFitCache * kFitThreads; k < n_v; k += kFitThreads)
+        point(fmaf((float)k, du, u0), (float)y[k]);
+    block_sums<15, 0>(acc, nullptr, sf, sd, buf);
 }
 
-// One block of 128 threads per spectrum, FP64 throughout.  Start: continuum A = max CCF,
-// B = min - max, mu at the (first) minimum and sigma from the dip's area; the model is
-// A + B exp(-(v - mu)^2 / (2 sigma^2)).  The fit runs in scaled variables (CCF / max,
-// (v - mu0) / sigma0) so that the normal equations stay well conditioned.  Levenberg-Marquardt
-// with damping (J^T J + lam diag(J^T J)): each pass evaluates the cost, J^T J and J^T r at the
-// trial point together (fixed-order sums); thread 0 keeps the trial when the cost does not
-// grow (lam shrinks, down to 1e-9) or drops it (lam grows), solves for the next step and
-// broadcasts it.  The fit stops once a step moves every scaled parameter by less than 1e-11
-// (relative for the amplitudes), the damping passes 1e8, or after 100 passes.
+// Second phase: one Newton pass at p (FP64).  The residuals, the cost and the gradient J^T r
+// are FP64 (they fix where the iteration stops); J^T J (10) and the residual-weighted sums
+// R_j = sum r g d^j, j = 0..4 (g the Gaussian, d = u - m), which enter the Hessian
+// H = J^T J + sum r d2m only as the step's metric, are FP32.  Returns f = (J^T J, R_0..R_4)
+// and g = (J^T r, r^2) in every thread.
+__device__ __forceinline__ void pass_b(const double p[4], int n_v, const double* __restrict__ y,
+                                       double u0, double du, float* sf, double* sd, int& buf,
+                                       float (&f)[15], double (&g)[5]) {
+#pragma unroll
+    for (int q = 0; q < 15; q++) f[q] = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 5; q++) g[q] = 0.0;
+    const double iw = 1.0 / p[3];
+    const double iw2 = iw * iw;
+    const float iwf = (float)iw;
+    for (int k = threadIdx.x; k < n_v; k += kFitThreads) {
+        const double d = fma((double)k, du, u0) - p[2];
+        const double e = exp(-0.5 * d * d * iw2);
+        const double r = fma(p[1], e, p[0]) - y[k];
+        const double t = p[1] * e * d * iw2;
+        g[0] += r;
+        g[1] = fma(e, r, g[1]);
+        g[2] = fma(t, r, g[2]);
+        g[3] = fma(t * d * iw, r, g[3]);
+        g[4] = fma(r, r, g[4]);
+        const float ef = (float)e, df = (float)d, rf = (float)r, tf = (float)t;
+        const float J[4] = {1.0f, ef, tf, tf * df * iwf};
+        int q = 0;
+#pragma unroll
+        for (int a = 0; a < 4; a++)
+#pragma unroll
+            for (int b = a; b < 4; b++) { f[q] = fmaf(J[a], J[b], f[q]); q++; }
+        float w = rf * ef;
+#pragma unroll
+        for (int j = 0; j < 5; j++) { f[10 + j] += w; w *= df; }
+    }
+    block_sums<15, 5>(f, g, sf, sd, buf);
+}
+
+// Upper-triangle index of (a, b), a <= b, in the 10 sums of J^T J.
+__device__ __forceinline__ int tri(int a, int b) { return a * 4 - a * (a - 1) / 2 + (b - a); }
+
+// One block of 128 threads per spectrum.  Start (as the oracle's): continuum A = max CCF,
+// depth B = min - max at the (first) minimum, mu = its velocity, sigma from the dip's area.
+// The fit runs in scaled variables (CCF / max, (v - mu0) / sigma0), model
+// a + b exp(-(u - m)^2 / (2 w^2)), and ends at the least-squares minimum in two phases:
+//  1. Levenberg-Marquardt in FP32 (damping J^T J + lam diag(J^T J)): a trial point is kept
+//     when its cost does not grow (lam / 10, down to 1e-9), else dropped (lam x 10); the phase
+//     ends once a step is below 1e-4 (relative for the amplitudes), lam passes 1e8, or after
+//     kFitPassesA passes.  It only has to land in the basin of the minimum.
+//  2. Newton steps on H = J^T J + sum r d2m with FP64 residuals and gradient: near the minimum
+//     they converge quadratically (Gauss-Newton converges only linearly when, as for a
+//     rotation-broadened CCF, the residuals are large), so once a step is below 1e-6 the
+//     next one would be below rounding and the iteration stops after taking it.  A step is
+//     taken only while it points downhill and the steps shrink; the cost may not grow by more
+//     than 1e-12 relative from one pass to the next (else the previous point is kept).
+// Every thread runs the same iteration on bit-identical sums, so no broadcast is needed.
 __global__ void __launch_bounds__(kFitThreads) k_gauss_fit(int n_spec, int n_v, double v_lo,
                                                            double v_step,
                                                            const double* __restrict__ ccf,
                                                            double* scratch, double* rv,
                                                            double* fit) {
-    __shared__ double tab[kFitThreads * 15];
-    __shared__ double part[9 * 15];
+    __shared__ double tab[kFitThreads];
+    __shared__ double part[9];
     __shared__ double red[kFitWarps][2];
-    __shared__ double sp[5];
-    __shared__ int sstop;
+    __shared__ int redk[kFitWarps];
+    __shared__ double sp[2];
+    __shared__ float sf[2 * kFitWarps * kSumF];
+    __shared__ double sd[2 * kFitWarps * kSumD];
     const int spec = blockIdx.x;
     if (spec >= n_spec) return;
     const double* c = ccf + (int64_t)spec * n_v;
     double* y = scratch + (int64_t)spec * n_v;            // scaled CCF
-    // start (as the oracle's): continuum A = max CCF, depth B = min - max at the first
-    // minimum, mu = its velocity, sigma = dip area / (|B| sqrt(2 pi)) (at least one step)
     double mx = -INFINITY, mn = INFINITY;
     int kmin = n_v;
     for (int k = threadIdx.x; k < n_v; k += kFitThreads) {
@@ -403,7 +477,6 @@ __global__ void __launch_bounds__(kFitThreads) k_gauss_fit(int n_spec, int n_v, 
         if (mo < mn || (mo == mn && ko < kmin)) { mn = mo; kmin = ko; }
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    __shared__ int redk[kFitWarps];
     if (lane == 0) { red[warp][0] = mx; red[warp][1] = mn; redk[warp] = kmin; }
     __syncthreads();
     mx = red[0][0]; mn = red[0][1]; kmin = redk[0];
@@ -429,76 +502,101 @@ __global__ void __launch_bounds__(kFitThreads) k_gauss_fit(int n_spec, int n_v, 
     __syncthreads();
     const double c0 = sp[0], s0 = sp[1];
     const double u0 = (v_lo - c0) / s0, du = v_step / s0;
-    double ucache[kFitCache];
-    {
-        int i = 0;
-        for (int k = threadIdx.x; k < n_v && i < kFitCache; k += kFitThreads, i++) ucache[i] = fma((double)k, du, u0);
+    float uc[kFitCache], yc[kFitCache];
+#pragma unroll
+    for (int i = 0; i < kFitCache; i++) {
+        const int k = threadIdx.x + i * kFitThreads;
+        uc[i] = k < n_v ? (float)fma((double)k, du, u0) : 0.0f;
+        yc[i] = k < n_v ? (float)(c[k] * iscale) : 0.0f;
     }
-    // scaled parameters: a, b, m, w
-    double p[4] = {mx * iscale, (mn - mx) * iscale, 0.0, 1.0};
-    double acc[15];
-    fit_pass(y, n_v, ucache, u0, du, p, tab, part, acc);
-    double jtj[10], jtr[4], cost = 0.0, lam = 1e-3;
-    double pt[4] = {p[0], p[1], p[2], p[3]};
+    int buf = 0;
+
+    // ---- phase 1: FP32 Levenberg-Marquardt ----
+    float p[4] = {(float)(mx * iscale), (float)((mn - mx) * iscale), 0.0f, 1.0f};
+    float pt[4] = {p[0], p[1], p[2], p[3]};
+    float acc[15], jtj[10], jtr[4], cost = 0.0f, lam = 1e-3f;
     bool tiny = false;
-    if (threadIdx.x == 0) {
-        for (int q = 0; q < 10; q++) jtj[q] = acc[q];
-        for (int a = 0; a < 4; a++) jtr[a] = acc[10 + a];
-        cost = acc[14];
-    }
-    for (int it = 0; it < 100; it++) {
-        if (threadIdx.x == 0) {
-            int stop = 0;
-            if (it > 0) {
-                if (acc[14] <= cost) {                // keep the trial point
-                    for (int a = 0; a < 4; a++) p[a] = pt[a];
-                    for (int q = 0; q < 10; q++) jtj[q] = acc[q];
-                    for (int a = 0; a < 4; a++) jtr[a] = acc[10 + a];
-                    cost = acc[14];
-                    lam = fmax(lam * 0.1, 1e-9);
-                    if (tiny) stop = 1;
-                } else {
-                    if (tiny) stop = 1;                 // at the rounding floor of the cost
-                    lam *= 10.0;
-                }
-            }
-            while (!stop) {
-                if (lam > 1e8) { stop = 1; break; }
-                // the step only needs to point downhill: solved in FP32 (the scaled system is
-                // well conditioned); the fixed point J^T r = 0 is still evaluated in FP64
-                float M[4][4], b[4], dxf[4];
-                int q = 0;
-                for (int a = 0; a < 4; a++)
-                    for (int bb = a; bb < 4; bb++) { M[a][bb] = M[bb][a] = (float)jtj[q++]; }
-                for (int a = 0; a < 4; a++) { M[a][a] *= (float)(1.0 + lam); b[a] = (float)(-jtr[a]); }
-                if (!solve4f(M, b, dxf)) { lam *= 10.0; continue; }
-                double dx[4] = {dxf[0], dxf[1], dxf[2], dxf[3]};
-                tiny = fabs(dx[2]) <= 1e-11 && fabs(dx[3]) <= 1e-11 &&
-                       fabs(dx[0]) <= 1e-11 * fabs(p[0]) && fabs(dx[1]) <= 1e-11 * fabs(p[1]);
-                for (int a = 0; a < 4; a++) pt[a] = p[a] + dx[a];
-                break;
-            }
-            for (int a = 0; a < 4; a++) sp[a] = stop ? p[a] : pt[a];
-            sstop = stop;
+    pass_a(p, n_v, uc, yc, y, (float)u0, (float)du, sf, sd, buf, acc);
+    for (int it = 0; it < kFitPassesA; it++) {
+        bool stop = false;
+        if (it == 0 || acc[14] <= cost) {            // keep the trial point
+            for (int a = 0; a < 4; a++) p[a] = pt[a];
+            for (int q = 0; q < 10; q++) jtj[q] = acc[q];
+            for (int a = 0; a < 4; a++) jtr[a] = acc[10 + a];
+            cost = acc[14];
+            if (it > 0) lam = fmaxf(lam * 0.1f, 1e-9f);
+            if (tiny) stop = true;
+        } else {
+            if (tiny) stop = true;
+            lam *= 10.0f;
         }
-        __syncthreads();
-        const int stop = sstop;
-        const double ptb[4] = {sp[0], sp[1], sp[2], sp[3]};
-        __syncthreads();
+        while (!stop) {
+            if (lam > 1e8f) { stop = true; break; }
+            float M[4][4], b[4], dx[4];
+            for (int a = 0; a < 4; a++)
+                for (int bb = a; bb < 4; bb++) M[a][bb] = M[bb][a] = jtj[tri(a, bb)];
+            for (int a = 0; a < 4; a++) { M[a][a] *= 1.0f + lam; b[a] = -jtr[a]; }
+            if (!solve4f(M, b, dx)) { lam *= 10.0f; continue; }
+            tiny = fabsf(dx[2]) <= kFitTolA && fabsf(dx[3]) <= kFitTolA &&
+                   fabsf(dx[0]) <= kFitTolA * fabsf(p[0]) && fabsf(dx[1]) <= kFitTolA * fabsf(p[1]);
+            for (int a = 0; a < 4; a++) pt[a] = p[a] + dx[a];
+            break;
+        }
         if (stop) break;
-        fit_pass(y, n_v, ucache, u0, du, ptb, tab, part, acc);
+        pass_a(pt, n_v, uc, yc, y, (float)u0, (float)du, sf, sd, buf, acc);
     }
+
+    // ---- phase 2: Newton with FP64 residuals ----
+    double pd[4] = {p[0], p[1], p[2], p[3]};
+    double prev[4] = {pd[0], pd[1], pd[2], pd[3]};
+    double cost_prev = INFINITY;
+    float last = INFINITY;
+    for (int it = 0; it < kFitPassesB; it++) {
+        float f[15];
+        double g[5];
+        pass_b(pd, n_v, y, u0, du, sf, sd, buf, f, g);
+        if (!(g[4] <= cost_prev * (1.0 + 1e-12))) {   // the last step did not help: undo it
+            for (int a = 0; a < 4; a++) pd[a] = prev[a];
+            break;
+        }
+        const float b = (float)pd[1], w = (float)pd[3];
+        const float iw = 1.0f / w, iw2 = iw * iw;
+        const float R0 = f[10], R1 = f[11], R2 = f[12], R3 = f[13], R4 = f[14];
+        float M[4][4], rhs[4], dx[4];
+        for (int a = 0; a < 4; a++)
+            for (int bb = a; bb < 4; bb++) M[a][bb] = M[bb][a] = f[tri(a, bb)];
+        M[1][2] += R1 * iw2;
+        M[1][3] += R2 * iw2 * iw;
+        M[2][2] += b * iw2 * (R2 * iw2 - R0);
+        M[2][3] += b * iw2 * iw * (R3 * iw2 - 2.0f * R1);
+        M[3][3] += b * iw2 * iw2 * (R4 * iw2 - 3.0f * R2);
+        M[2][1] = M[1][2];
+        M[3][1] = M[1][3];
+        M[3][2] = M[2][3];
+        for (int a = 0; a < 4; a++) rhs[a] = -(float)g[a];
+        if (!solve4f(M, rhs, dx)) break;
+        if (!(dx[0] * rhs[0] + dx[1] * rhs[1] + dx[2] * rhs[2] + dx[3] * rhs[3] > 0.0f)) break;
+        const float ref = fabsf((float)pd[0]), wref = fabsf(w);
+        const float size = fmaxf(fmaxf(fabsf(dx[0]) / ref, fabsf(dx[1]) / ref),
+                                 fmaxf(fabsf(dx[2]) / wref, fabsf(dx[3]) / wref));
+        if (!(size < last)) break;
+        for (int a = 0; a < 4; a++) { prev[a] = pd[a]; pd[a] += (double)dx[a]; }
+        cost_prev = g[4];
+        last = size;
+        if (size <= kFitTolB) break;
+    }
+
     if (threadIdx.x == 0) {
         // a fit that leaves the velocity grid (no dip to fit) is reported as NaN
         const double v_hi = fma((double)(n_v - 1), v_step, v_lo);
-        double mu = fma(p[2], s0, c0);
-        if (!(mu >= v_lo && mu <= v_hi) || !(fabs(p[3]) * s0 <= v_hi - v_lo)) mu = NAN;
+        double mu = fma(pd[2], s0, c0);
+        if (!(mu >= v_lo && mu <= v_hi) || !(fabs(pd[3]) * s0 <= v_hi - v_lo)) mu = NAN;
         rv[spec] = mu;
         if (fit) {
-            fit[(int64_t)spec * 4 + 0] = p[0] * scale;
-            fit[(int64_t)spec * 4 + 1] = p[1] * scale;
+            fit[(int64_t)spec * 4 + 0] = pd[0] * scale;
+            fit[(int64_t)spec * 4 + 1] = pd[1] * scale;
             fit[(int64_t)spec * 4 + 2] = mu;
-            fit[(int64_t)spec * 4 + 3] = fabs(p[3]) * s0;
+            fit[(int64_t)spec * 4 + 3] = fabs(pd[3]) * s0;
         }
     }
 }

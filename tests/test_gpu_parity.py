@@ -1,6 +1,6 @@
 """GPU parity: the CUDA library (through its C-ABI) against the FP64 oracle, element by element.
 
-Tolerances (BASELINE: 1e-12 relative flux for the FP64 path, 2e-6 relative flux and 1 cm/s RV
+Tolerances (1e-12 relative flux for the FP64 path, 2e-6 relative flux and 1 cm/s RV
 for the mixed path) are relative to max F_quiet of the oracle.
 """
 import numpy as np
@@ -253,7 +253,7 @@ def test_ccf_and_rv_config1(S, cfg1, cfg1_ref):
                               cfg1.mask_width_kms, lo, step, nv)
     rv_g, fit_g, ccf_g = _gpu_rv(S, cfg1, F, lo, step, nv)
     assert np.abs(ccf_g - ccf_o).max() <= 1e-12 * np.abs(ccf_o).max()
-    assert np.abs(rv_g - rv_o).max() * 1e5 <= 1e-4          # cm/s
+    assert np.abs(rv_g - rv_o).max() * 1e5 <= 1e-6          # cm/s
     np.testing.assert_allclose(fit_g, fit_o, rtol=1e-8, atol=1e-10)
     rv_32, _, ccf_32 = _gpu_rv(S, cfg1, F.astype(np.float32), lo, step, nv)
     assert np.abs(rv_32 - rv_o).max() * 1e5 <= 1.0
@@ -270,7 +270,7 @@ def test_ccf_unsorted_mask_matches_sorted(S, cfg1, cfg1_ref):
     c2.mask_lambda, c2.mask_weight = cfg1.mask_lambda[perm].copy(), cfg1.mask_weight[perm].copy()
     rv_b, _, ccf_b = _gpu_rv(S, c2, F, lo, step, nv)
     assert np.abs(ccf_a - ccf_b).max() <= 1e-13 * np.abs(ccf_a).max()
-    assert np.abs(rv_a - rv_b).max() * 1e5 <= 1e-4
+    assert np.abs(rv_a - rv_b).max() * 1e5 <= 1e-6
     rv_c, _, ccf_c = _gpu_rv(S, c2, F.astype(np.float32), lo, step, nv)
     assert np.abs(rv_c - rv_a).max() * 1e5 <= 1.0
 
@@ -282,6 +282,6 @@ def test_ccf_and_rv_fullsize(S, cfg2):
     rv_o, _, ccf_o = O.rv(F, c.star, c.mask_lambda, c.mask_weight, c.mask_width_kms, lo, step, nv)
     rv_g, _, ccf_g = _gpu_rv(S, c, F, lo, step, nv)
     assert np.abs(ccf_g - ccf_o).max() <= 1e-12 * np.abs(ccf_o).max()
-    assert np.abs(rv_g - rv_o).max() * 1e5 <= 1e-4
+    assert np.abs(rv_g - rv_o).max() * 1e5 <= 1e-6
     rv_32, _, _ = _gpu_rv(S, c, F.astype(np.float32), lo, step, nv)
     assert np.abs(rv_32 - rv_o).max() * 1e5 <= 1.0
