@@ -232,6 +232,159 @@ k_ccf_window(int n_lines, const int* __restrict__ U, const T* __restrict__ f,
             partial[((int64_t)blockIdx.x * n_spec + s0 + s) * n_v + k] = acc[s];   // FP64 in the reduction
 }
 
+// Register-tiled form for FP32 spectra and masks sorted by wavelength.  Block = (range of
+// lines, kTileSB spectra); thread = (group of kTileVT consecutive velocities, line lane).  For a
+// line, the boxes of a group's velocities start at a_kk = a_0 + (s_kk - s_k0) pixels from the
+// group's first pixel n0 and, with the host's bound on the group's spread, all lie in the NP
+// pixels n0 .. n0 + NP - 1.  Each of those pixels is read once from the staged window (all
+// kTileSB spectra: four 16-byte loads) and applied to every velocity of the group with its
+// overlap (zero where a box misses the pixel): NP x VT x SB FMAs per line for 4 x NP loads,
+// against 2 x SB FMAs for 2 x 4 loads per velocity when a thread owns one velocity.  The line
+// lanes take alternate lines of each window; their sums are added in lane order at the end.
+// Lines are staged kTileCL at a time in windows of at most kTileWin pixels (a window closes
+// early where the lines spread out), so every line is handled in shared memory.
+constexpr int kTileVT = 4;
+constexpr int kTileSB = 16;
+constexpr int kTileLP = 2;
+constexpr int kTileCL = 16;
+constexpr int kTileWin = 320;
+constexpr int kTileRow = kTileSB + 4;                           // padded row (floats)
+constexpr int kTileRed = kTileVT * kTileSB + 1;                 // lane-sum row (floats, padded)
+constexpr int kTileMaxGroups = kTileWin * kTileRow / kTileRed;  // lane sums reuse the window
+static_assert(kTileLP == 2, "the lane sums below add exactly two lanes");
+
+template <int NP>
+__global__ void __launch_bounds__(256)
+k_ccf_tile(int n_lines, int lines_per_block, const int* __restrict__ U, const float* __restrict__ f,
+           const int* __restrict__ valid, const float* __restrict__ wl_, int n_v,
+           const int* __restrict__ S, const float* __restrict__ g, float box, int64_t n_px,
+           int n_spec, const float* __restrict__ spectra, float* __restrict__ partial) {
+    __shared__ __align__(16) float win[kTileWin * kTileRow];
+    __shared__ int sB[kTileCL];
+    __shared__ float sF[kTileCL];
+    __shared__ float sW[kTileCL];
+    const int NG = (n_v + kTileVT - 1) / kTileVT;
+    const int lane = threadIdx.x / NG;
+    const int gi = threadIdx.x - lane * NG;
+    const bool active = lane < kTileLP;
+    const int k0 = gi * kTileVT;
+    const int s0 = blockIdx.y * kTileSB;
+    const int ns = min(kTileSB, n_spec - s0);
+    const int L0 = blockIdx.x * lines_per_block;
+    const int L1 = min(n_lines, L0 + lines_per_block);
+    int S0 = 0;
+    float g0 = 0.0f;
+    float rel[kTileVT];
+#pragma unroll
+    for (int kk = 0; kk < kTileVT; kk++) rel[kk] = 0.0f;
+    if (active) {
+        S0 = S[k0];
+        g0 = g[k0];
+#pragma unroll
+        for (int kk = 0; kk < kTileVT; kk++) {
+            const int k = min(k0 + kk, n_v - 1);          // past the grid: a copy of the last
+            rel[kk] = (float)(S[k] - S0) + g[k];
+        }
+    }
+    const int Smin = S[0], sweep = S[n_v - 1] - Smin;
+    const int budget = kTileWin - sweep - NP - 5;           // >= 0 (checked by the host)
+    float acc[kTileVT][kTileSB];
+#pragma unroll
+    for (int kk = 0; kk < kTileVT; kk++)
+#pragma unroll
+        for (int s = 0; s < kTileSB; s++) acc[kk][s] = 0.0f;
+    const float* base = spectra + (int64_t)s0 * n_px;
+    for (int j0 = L0; j0 < L1;) {
+        // lines j0 .. j1-1 whose boxes fit one window
+        const int Ub = U[j0];
+        int Umax = Ub, j1 = j0 + 1;
+        while (j1 < L1 && j1 - j0 < kTileCL) {
+            const int u = U[j1];
+            if (u - Ub > budget) break;
+            Umax = max(Umax, u);
+            j1++;
+        }
+        const int64_t n_lo = (int64_t)Ub + Smin - 2;
+        const int W = (Umax - Ub) + sweep + NP + 5;          // <= kTileWin
+        __syncthreads();                                   // the previous window is consumed
+        for (int j = threadIdx.x; j < j1 - j0; j += blockDim.x) {
+            sB[j] = (int)((int64_t)U[j0 + j] - n_lo);
+            sF[j] = f[j0 + j];
+            sW[j] = valid[j0 + j] ? wl_[j0 + j] : 0.0f;     // lines whose box leaves the grid: skipped
+        }
+        for (int x = threadIdx.x; x < W; x += blockDim.x) {
+            const int64_t pix = n_lo + x;
+            const bool on = pix >= 0 && pix < n_px;
+            const float* col = base + pix;                  // spectrum s at col + s n_px (added, not multiplied)
+            float v[kTileSB];
+#pragma unroll
+            for (int s = 0; s < kTileSB; s++) {
+                v[s] = (on && s < ns) ? __ldg(col) : 0.0f;
+                col += n_px;
+            }
+            float4* dst = reinterpret_cast<float4*>(win + x * kTileRow);
+#pragma unroll
+            for (int q = 0; q < kTileSB / 4; q++)
+                dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        }
+        __syncthreads();
+        if (active) {
+            for (int j = lane; j < j1 - j0; j += kTileLP) {
+                const float wl = sW[j];
+                if (wl == 0.0f) continue;
+                const float fl = sF[j];
+                const bool carry = fl + g0 >= 1.0f;
+                const float cf = carry ? 1.0f : 0.0f;
+                const int n0 = sB[j] + S0 + (carry ? 1 : 0);
+                float ov[kTileVT][NP];
+#pragma unroll
+                for (int kk = 0; kk < kTileVT; kk++) {
+                    const float a = (fl + rel[kk]) - cf;     // box start from pixel n0
+                    const float e = a + box;
+#pragma unroll
+                    for (int jj = 0; jj < NP; jj++)
+                        ov[kk][jj] = wl * fmaxf(fminf(e, (float)(jj + 1)) - fmaxf(a, (float)jj), 0.0f);
+                }
+#pragma unroll
+                for (int jj = 0; jj < NP; jj++) {
+                    const float4* src = reinterpret_cast<const float4*>(win + (n0 + jj) * kTileRow);
+                    float t[kTileSB];
+#pragma unroll
+                    for (int q = 0; q < kTileSB / 4; q++) {
+                        const float4 x = src[q];
+                        t[4 * q] = x.x; t[4 * q + 1] = x.y; t[4 * q + 2] = x.z; t[4 * q + 3] = x.w;
+                    }
+#pragma unroll
+                    for (int kk = 0; kk < kTileVT; kk++)
+#pragma unroll
+                        for (int s = 0; s < kTileSB; s++) acc[kk][s] = fmaf(ov[kk][jj], t[s], acc[kk][s]);
+                }
+            }
+        }
+        j0 = j1;
+    }
+    // lane sums in lane order (lane 1 through shared memory), one partial row per block
+    __syncthreads();
+    if (active && lane == 1)
+#pragma unroll
+        for (int kk = 0; kk < kTileVT; kk++)
+#pragma unroll
+            for (int s = 0; s < kTileSB; s++) win[gi * kTileRed + kk * kTileSB + s] = acc[kk][s];
+    __syncthreads();
+    if (active && lane == 0) {
+#pragma unroll
+        for (int kk = 0; kk < kTileVT; kk++) {
+            const int k = k0 + kk;
+            if (k >= n_v) break;
+#pragma unroll
+            for (int s = 0; s < kTileSB; s++)
+                if (s < ns)
+                    partial[((int64_t)blockIdx.x * n_spec + s0 + s) * n_v + k] =
+                        acc[kk][s] + win[gi * kTileRed + kk * kTileSB + s];
+        }
+    }
+}
+
 // ccf[t] = sum over chunks of partial[c][t], in a fixed order: kReduceSplit lanes take
 // interleaved chunks, then a fixed shuffle tree adds the lanes.
 template <typename TP>
@@ -612,7 +765,40 @@ soap_status rv_ccf_run(soap_ctx* c, const void* spectra_dev, int f32, int n_spec
     const bool windowed = sorted && n_v <= 256 && 2.0 * width_kms / (2.0 * kCKms * c->delta) <= 15.0;
     const int n_wchunks = (n_lines + kWinLines - 1) / kWinLines;
     const int n_wgroups = n_wchunks;                    // one chunk of lines per block
-    const int n_chunks = windowed ? n_wgroups : (n_lines + kLinesPerChunk - 1) / kLinesPerChunk;
+    int n_chunks = windowed ? n_wgroups : (n_lines + kLinesPerChunk - 1) / kLinesPerChunk;
+    // register-tiled kernel (FP32, sorted mask): pixels a group of kTileVT velocities can reach
+    // for one line, from the largest spread of kTileVT consecutive box positions
+    int tile_np = 0, tile_blocks = 0, tile_lines = 0;
+    if (f32 && sorted && n_v >= kTileVT) {
+        const double box = width_kms / (kCKms * c->delta);
+        double spread = 0.0;
+        for (int k = 0; k + kTileVT - 1 < n_v; k++)
+            spread = std::max(spread, (std::atanh((v_lo + (k + kTileVT - 1) * v_step) / kCKms) -
+                                       std::atanh((v_lo + k * v_step) / kCKms)) / c->delta);
+        const int np = (int)std::floor(spread + box + 1e-6) + 2;
+        const double sweep = (std::atanh((v_lo + (n_v - 1) * v_step) / kCKms) -
+                              std::atanh(v_lo / kCKms)) / c->delta + 2.0;
+        const int groups = (n_v + kTileVT - 1) / kTileVT;
+        if (np <= 4 && groups <= kTileMaxGroups && groups * kTileLP <= 256 &&
+            sweep + np + 5 + 1 <= kTileWin) {
+            // one full wave: as many blocks as fit on the GPU at once, split evenly over the lines
+            // (a partial second wave would double the time of its SMs)
+            tile_np = std::max(np, 2);
+            const int tthreads = (groups * kTileLP + 31) / 32 * 32;
+            int sms = 0, dev = 0, per_sm = 0;
+            SOAP_CUDA(cudaGetDevice(&dev));
+            SOAP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+            SOAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &per_sm, tile_np == 2 ? k_ccf_tile<2> : tile_np == 3 ? k_ccf_tile<3> : k_ccf_tile<4>,
+                tthreads, 0));
+            const int ys = (n_spec + kTileSB - 1) / kTileSB;
+            const int wave = std::max(1, sms * std::max(per_sm, 1));
+            tile_blocks = std::max(1, std::min(wave >= ys ? wave / ys : 1, (n_lines + 7) / 8));
+            tile_lines = (n_lines + tile_blocks - 1) / tile_blocks;
+            tile_blocks = (n_lines + tile_lines - 1) / tile_lines;
+            n_chunks = tile_blocks;
+        }
+    }
     // scratch layout (8-byte aligned pieces, 256-byte aligned blocks)
     auto al = [](size_t x) { return (x + 255) / 256 * 256; };
     size_t o_lam = 0;
@@ -657,7 +843,20 @@ soap_status rv_ccf_run(soap_ctx* c, const void* spectra_dev, int f32, int n_spec
                                                                d_g64, d_g32);
     SOAP_LAUNCHED(c);
     const int threads = n_v >= 256 ? 256 : ((n_v + 31) / 32) * 32;
-    if (windowed) {
+    if (tile_np) {
+        const int tthreads = ((n_v + kTileVT - 1) / kTileVT * kTileLP + 31) / 32 * 32;
+        dim3 grid((unsigned)tile_blocks, (unsigned)((n_spec + kTileSB - 1) / kTileSB));
+        const float box = (float)(2.0 * h);
+#define SOAP_TILE_LAUNCH(NP)                                                                       \
+        k_ccf_tile<NP><<<grid, tthreads, 0, c->stream>>>(n_lines, tile_lines, d_U, d_f32, d_valid,  \
+                                                         d_w32, n_v, d_S, d_g32, box, c->n_px,     \
+                                                         n_spec, (const float*)spectra_dev,        \
+                                                         reinterpret_cast<float*>(d_part))
+        if (tile_np == 2) SOAP_TILE_LAUNCH(2);
+        else if (tile_np == 3) SOAP_TILE_LAUNCH(3);
+        else SOAP_TILE_LAUNCH(4);
+#undef SOAP_TILE_LAUNCH
+    } else if (windowed) {
         const int threads = ((n_v + 31) / 32) * 32;
         const double box = 2.0 * h;
         const bool small = box <= 1.0;                   // the box covers at most 2 pixels
@@ -696,7 +895,7 @@ soap_status rv_ccf_run(soap_ctx* c, const void* spectra_dev, int f32, int n_spec
     }
     SOAP_LAUNCHED(c);
     int64_t tot = (int64_t)n_spec * n_v * kReduceSplit;
-    if (windowed && f32)      // FP32 partial sums (converted exactly to FP64 here)
+    if ((windowed || tile_np) && f32)      // FP32 partial sums (converted exactly to FP64 here)
         k_ccf_reduce<float><<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(
             n_chunks, n_spec, n_v, reinterpret_cast<const float*>(d_part), d_ccf);
     else

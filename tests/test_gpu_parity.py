@@ -259,6 +259,38 @@ def test_ccf_and_rv_config1(S, cfg1, cfg1_ref):
     assert np.abs(rv_32 - rv_o).max() * 1e5 <= 1.0
 
 
+def _tile_np(c, width, step, nv, lo):
+    """Pixels a group of 4 consecutive velocities can reach for one line (the tiled CCF kernel
+    runs for 2..4): box width plus the largest spread of 4 box positions, + 2."""
+    st = c.star
+    delta = np.log(st.lambda_end_A / st.lambda_start_A) / (st.n_px - 1)
+    s = np.arctanh((lo + step * np.arange(nv)) / 299792.458) / delta
+    return int(np.floor((s[3:] - s[:-3]).max() + width / (299792.458 * delta) + 1e-6)) + 2
+
+
+@pytest.mark.parametrize("width,step,n_spec", [(0.82, 0.25, 17), (0.3, 0.15, 1), (1.6, 0.25, 33),
+                                               (0.82, 0.5, 16)])
+def test_ccf_fp32_sorted_mask_matches_oracle(S, cfg2, width, step, n_spec):
+    """FP32 spectra, mask sorted by wavelength, full-size grid (205,800 px, 12,946 lines): the
+    CCF element by element against the oracle's on the same (FP32-rounded) spectra, for boxes
+    of 0.35 / 0.94 / 1.84 px and velocity steps of 0.15 / 0.25 / 0.5 km/s (2, 3 and 4 pixels per
+    group of 4 velocities), with 1, 16, 17 and 33 spectra (ragged blocks of 16)."""
+    c = cfg2
+    half = c.star.vsini_kms + 20.0
+    nv = int(np.floor(2 * half / step + 1e-9)) + 1
+    lo = -half
+    assert 2 <= _tile_np(c, width, step, nv, lo) <= 4
+    F = np.concatenate([c.quiet, c.quiet[::-1] * 0.97])[:n_spec].astype(np.float32)
+    ccf_o = O.ccf(F.astype(np.float64), c.star, c.mask_lambda, c.mask_weight, width, lo, step, nv)
+    with S.Disk(c.star, _t(c.quiet)) as d:
+        rv = torch.empty(n_spec, dtype=torch.float64, device=DEV)
+        ccf = torch.empty((n_spec, nv), dtype=torch.float64, device=DEV)
+        S.soap_rv_ccf(d.ctx, _t(F), c.mask_lambda, c.mask_weight, width, lo, step, nv, rv, None, ccf)
+        torch.cuda.synchronize()
+    ccf_g = ccf.cpu().numpy()
+    assert np.abs(ccf_g - ccf_o).max() <= 2e-6 * np.abs(ccf_o).max()
+
+
 def test_ccf_unsorted_mask_matches_sorted(S, cfg1, cfg1_ref):
     """The windowed kernel (mask sorted by wavelength) and the generic one (any order) agree."""
     _, ref = cfg1_ref
