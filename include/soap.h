@@ -25,7 +25,10 @@
  *    `cuda_stream`, or soap_set_stream(); NULL = the legacy default stream).  Calls whose
  *    outputs are in device memory return without synchronising: the caller orders later
  *    work on the same stream or synchronises.  Calls with host outputs synchronise the
- *    stream before returning.
+ *    stream before returning, unless the host-transfer pipeline is on
+ *    (soap_set_host_async): then copies from and to host memory run on two streams of the
+ *    context's own, ordered against the compute stream by events, and results reach the host
+ *    only by the next soap_synchronize().
  *  - Threads: a context must not be used by two threads at once.  Different contexts are
  *    independent.
  *  - Layout: arrays are C row-major; spectra are float64 unless stated otherwise.
@@ -195,9 +198,23 @@ soap_status soap_set_active_spectrum(soap_ctx* ctx, int32_t type, const double* 
 /* Replace the context's stream (cudaStream_t or NULL). */
 soap_status soap_set_stream(soap_ctx* ctx, void* cuda_stream);
 
-/* Block until all work of the context's stream has finished; then report any condition the
- * kernels flagged (SOAP_ERANGE) since the last check. */
+/* Block until all work of the context's streams (its compute stream and, once used, its two
+ * host-transfer streams) has finished; then report any condition the kernels flagged
+ * (SOAP_ERANGE) since the last check. */
 soap_status soap_synchronize(soap_ctx* ctx);
+
+/* Host-transfer pipeline on (enabled = 1) or off (0; the default).  While it is on:
+ *  - soap_set_quiet_spectrum / soap_set_active_spectrum with a host source copy it on the
+ *    context's upload stream into a stage of their own (quiet, spot, facula) and return; the
+ *    compute stream waits for that copy only, and the next upload to the same stage waits until
+ *    the compute stream has read the previous one;
+ *  - soap_active_rv with host outputs returns once its work is enqueued; its results are on
+ *    the host after the next soap_synchronize().
+ * So a caller can enqueue step after step and the uploads of one step, the compute of another
+ * and the downloads of a third overlap.  The caller keeps host sources unchanged and host
+ * outputs unread until soap_synchronize(); overlap needs pinned host memory (pageable copies
+ * are correct but block the host).  Turning it off synchronises all streams. */
+soap_status soap_set_host_async(soap_ctx* ctx, int enabled);
 
 /* Fill *out with facts about the star. */
 soap_status soap_get_star_info(soap_ctx* ctx, soap_star_info* out);
@@ -221,6 +238,29 @@ soap_status soap_quiet_spectrum(soap_ctx* ctx, int32_t form, int32_t precision, 
 soap_status soap_active_phases(soap_ctx* ctx, const soap_region* regions, int32_t n_regions,
                                const double* phases, int32_t n_phases, uint32_t effects,
                                int32_t precision, void* out, int out_on_device);
+
+/* Spectra of the active star at each phase and their radial velocities in one call: the
+ * spectra of one effect as soap_active_phases computes them (Alg. 5 with Eqs. 1-4), then the
+ * CCF and Gaussian fit of soap_rv_ccf on those spectra, which stay in device memory between
+ * the two steps.
+ *  regions, n_regions, phases, n_phases, precision   as for soap_active_phases.
+ *  effect       exactly one of SOAP_EFFECT_TOT, SOAP_EFFECT_FLUX, SOAP_EFFECT_BCONV.
+ *  mask_lambda, mask_weight, n_lines, mask_width_kms, v_lo, v_step, n_v   as for soap_rv_ccf.
+ *  spectra_out  [n_phases][n_px] float64 (SOAP_FP64) or float32 (SOAP_FP32), or NULL for RVs
+ *               only.  Host or device per out_on_device.
+ *  rv_kms       [n_phases] fitted line centres (km/s; NaN as in soap_rv_ccf).  Host or device
+ *               per out_on_device.
+ * With host outputs the results are computed into one of two alternating device buffers of
+ * the context; the spectra are copied to the host on the download stream while the CCF runs,
+ * the RVs after the fit.  Without the host-transfer pipeline the call returns when both copies
+ * are done; with it, see soap_set_host_async.
+ * Errors: those of soap_active_phases and soap_rv_ccf; SOAP_EINVAL if effect is not a single
+ * SOAP_EFFECT_* bit. */
+soap_status soap_active_rv(soap_ctx* ctx, const soap_region* regions, int32_t n_regions,
+                           const double* phases, int32_t n_phases, uint32_t effect,
+                           int32_t precision, const double* mask_lambda, const double* mask_weight,
+                           int32_t n_lines, double mask_width_kms, double v_lo, double v_step,
+                           int32_t n_v, void* spectra_out, double* rv_kms, int out_on_device);
 
 /* One configuration of a batch (soap_active_batch): a star of the context's type (same grid,
  * mu table, limb darkening, local spectra and wavelength grid) seen with its own projected
@@ -297,9 +337,11 @@ soap_status soap_batch_autotune(soap_ctx* ctx, const soap_batch_item* items, int
  * u = ln(lambda/lambda_start)/Delta, box_l(v) centred at (ln(lambda_l/lambda_start) +
  * atanh(v/c))/Delta with half width W/(2 c Delta); lines whose box leaves the grid anywhere on
  * the velocity grid are skipped.  The fit minimises sum_k (A + B exp(-(v_k-mu)^2/(2 s^2)) -
- * CCF_k)^2 by FP64 Levenberg-Marquardt (in variables scaled by max CCF and by the starting
- * width) from A = max CCF, B = min - max, mu = velocity of the (first) CCF minimum and
- * s = dip area / (|B| sqrt(2 pi)), at least one velocity step.
+ * CCF_k)^2 (in variables scaled by max CCF and by the starting width) from A = max CCF,
+ * B = min - max, mu = velocity of the (first) CCF minimum and s = dip area / (|B| sqrt(2 pi)),
+ * at least one velocity step: Levenberg-Marquardt in FP32 until its step is below 1e-4, then
+ * Newton steps on the exact Hessian with FP64 residuals and gradient, so that the result is
+ * the least-squares minimum to FP64 rounding.
  *  rv_kms         [n_spec] fitted mu (km/s); NaN when the fit leaves the velocity grid (mu
  *                 outside it or a width larger than it: no dip to fit).
  *  fit_params     [n_spec][4] (A, B, mu, s), or NULL.

@@ -1,6 +1,7 @@
 // api.cu -- C-ABI entry points of libsoap: argument validation, context and memory
 // management, host<->device staging.  All arithmetic of the method runs in the kernels of
 // geometry.cu, contract.cu, direct.cu and ccf.cu.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -70,6 +71,90 @@ void release_host(HostBuf& b) {
     b.bytes = 0;
 }
 
+// Device-side copy of n bytes from mapped pinned host memory (the ring) into device memory.
+// A kernel, not a copy-engine transfer: a small upload on the compute stream must not queue
+// behind a large upload that the copy engine is running for the upload stream.
+__global__ void k_ring_fetch(const unsigned char* __restrict__ src, unsigned char* __restrict__ dst,
+                             size_t n) {
+    const size_t n8 = n / 8;
+    const uint64_t* s8 = reinterpret_cast<const uint64_t*>(src);
+    uint64_t* d8 = reinterpret_cast<uint64_t*>(dst);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n8; i += (size_t)gridDim.x * blockDim.x)
+        d8[i] = s8[i];
+    if (blockIdx.x == 0 && threadIdx.x < n - n8 * 8) dst[n8 * 8 + threadIdx.x] = src[n8 * 8 + threadIdx.x];
+}
+
+soap_status upload_small(soap_ctx* c, void* dst, const void* src, size_t bytes) {
+    if (bytes == 0) return SOAP_OK;
+    PinnedRing& R = c->ring;
+    const size_t need = (bytes + 255) / 256 * 256;
+    if (need > kRingBytes / 4) {                       // large: a plain (pageable) copy
+        SOAP_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->stream));
+        return SOAP_OK;
+    }
+    if (!R.p) {
+        void* h = nullptr;
+        cudaError_t e = cudaMallocHost(&h, kRingBytes);
+        if (e != cudaSuccess) {
+            set_error("cudaMallocHost(%zu) failed: %s", kRingBytes, cudaGetErrorString(e));
+            return SOAP_ENOMEM;
+        }
+        R.p = static_cast<unsigned char*>(h);
+        R.cap = kRingBytes;
+        R.head = 0;
+        void* dp = nullptr;
+        SOAP_CUDA(cudaHostGetDevicePointer(&dp, h, 0));
+        R.dev = static_cast<unsigned char*>(dp);
+    }
+    if (R.head + need > R.cap) R.head = 0;
+    const size_t lo = R.head, hi = R.head + need;
+    // the oldest uses are the ones in the way: wait for those that overlap [lo, hi)
+    size_t done = 0;
+    while (done < R.pending.size() && R.pending[done].lo < hi && R.pending[done].hi > lo) {
+        SOAP_CUDA(cudaEventSynchronize(R.pending[done].ev));
+        R.free_ev.push_back(R.pending[done].ev);
+        done++;
+    }
+    R.pending.erase(R.pending.begin(), R.pending.begin() + (long)done);
+    std::memcpy(R.p + lo, src, bytes);
+    const bool aligned = (reinterpret_cast<uintptr_t>(dst) % 8) == 0;
+    if (aligned) {
+        const size_t n8 = bytes / 8;
+        const unsigned grid = (unsigned)std::min<size_t>((n8 + 255) / 256 + 1, 152 * 4);
+        k_ring_fetch<<<grid, 256, 0, c->stream>>>(R.dev + lo, static_cast<unsigned char*>(dst), bytes);
+        SOAP_CUDA(cudaGetLastError());
+        SOAP_LAUNCHED(c);
+    } else {
+        SOAP_CUDA(cudaMemcpyAsync(dst, R.p + lo, bytes, cudaMemcpyHostToDevice, c->stream));
+    }
+    cudaEvent_t ev = nullptr;
+    if (!R.free_ev.empty()) {
+        ev = R.free_ev.back();
+        R.free_ev.pop_back();
+    } else {
+        SOAP_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    }
+    SOAP_CUDA(cudaEventRecord(ev, c->stream));
+    R.pending.push_back({lo, hi, ev});
+    R.head = hi;
+    return SOAP_OK;
+}
+
+void ring_release(soap_ctx* c) {
+    PinnedRing& R = c->ring;
+    for (auto& u : R.pending) {
+        cudaEventSynchronize(u.ev);
+        cudaEventDestroy(u.ev);
+    }
+    for (cudaEvent_t e : R.free_ev) cudaEventDestroy(e);
+    R.pending.clear();
+    R.free_ev.clear();
+    if (R.p) cudaFreeHost(R.p);
+    R.p = nullptr;
+    R.dev = nullptr;
+    R.cap = R.head = 0;
+}
+
 static bool is_finite(double x) { return std::isfinite(x); }
 
 static int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
@@ -81,6 +166,48 @@ static soap_status to_device(soap_ctx* c, void* dst, const void* src, size_t n, 
     return SOAP_OK;
 }
 
+// Streams and events of the host-transfer pipeline, created on first use.
+static soap_status ensure_pipeline(soap_ctx* c) {
+    if (c->in_stream) return SOAP_OK;
+    SOAP_CUDA(cudaStreamCreateWithFlags(&c->in_stream, cudaStreamNonBlocking));
+    SOAP_CUDA(cudaStreamCreateWithFlags(&c->out_stream, cudaStreamNonBlocking));
+    for (int i = 0; i < 3; i++) {
+        SOAP_CUDA(cudaEventCreateWithFlags(&c->up_filled[i], cudaEventDisableTiming));
+        SOAP_CUDA(cudaEventCreateWithFlags(&c->up_free[i], cudaEventDisableTiming));
+    }
+    for (int i = 0; i < 2; i++) {
+        SOAP_CUDA(cudaEventCreateWithFlags(&c->dn_spec[i], cudaEventDisableTiming));
+        SOAP_CUDA(cudaEventCreateWithFlags(&c->dn_rv[i], cudaEventDisableTiming));
+        SOAP_CUDA(cudaEventCreateWithFlags(&c->dn_free[i], cudaEventDisableTiming));
+    }
+    return SOAP_OK;
+}
+
+static void sync_all(soap_ctx* c) {
+    if (c->in_stream) cudaStreamSynchronize(c->in_stream);
+    cudaStreamSynchronize(c->stream);
+    if (c->out_stream) cudaStreamSynchronize(c->out_stream);
+}
+
+static void destroy_pipeline(soap_ctx* c) {
+    if (!c->in_stream) return;
+    sync_all(c);
+    for (int i = 0; i < 3; i++) {
+        cudaEventDestroy(c->up_filled[i]);
+        cudaEventDestroy(c->up_free[i]);
+        release(c->up_stage[i]);
+    }
+    for (int i = 0; i < 2; i++) {
+        cudaEventDestroy(c->dn_spec[i]);
+        cudaEventDestroy(c->dn_rv[i]);
+        cudaEventDestroy(c->dn_free[i]);
+        release(c->dn_stage[i]);
+    }
+    cudaStreamDestroy(c->in_stream);
+    cudaStreamDestroy(c->out_stream);
+    c->in_stream = c->out_stream = nullptr;
+}
+
 static void free_ctx_memory(soap_ctx* c) {
     void* ptrs[] = {c->cell_I, c->cell_w, c->cell_mu, c->cell_j, c->cell_bin, c->cell_mu32,
                     c->cell_k0, c->cell_k1, c->flags, c->q64,
@@ -89,16 +216,32 @@ static void free_ctx_memory(soap_ctx* c) {
     for (void* p : ptrs)
         if (p) cudaFree(p);
     DevBuf* bufs[] = {&c->stage_in, &c->fq, &c->contrast, &c->kphase, &c->jobs, &c->coefs, &c->job_counters,
-                      &c->regions, &c->region_geo, &c->phases, &c->out_stage, &c->partial, &c->ccf_tmp};
+                      &c->regions, &c->region_geo, &c->phases, &c->out_stage, &c->partial, &c->ccf_tmp,
+                      &c->ccf_tab};
     for (DevBuf* b : bufs) release(*b);
     release_host(c->host_stage);
+    ring_release(c);
 }
 
-// upload [n_mu][n_px] float64 spectra into padded fp64 + fp32 rows
+// upload [n_mu][n_px] float64 spectra into padded fp64 + fp32 rows.  With the host-transfer
+// pipeline on, a host source is copied on in_stream into its own stage (slot: 0 quiet, 1 spot,
+// 2 facula) and the compute stream waits for that copy only.
 static soap_status upload_spectra(soap_ctx* c, const double* src, int on_device, double* dst64,
-                                  float* dst32) {
+                                  float* dst32, int slot) {
     size_t bytes = (size_t)c->n_mu * (size_t)c->n_px * sizeof(double);
     const double* dsrc = src;
+    if (!on_device && c->host_async) {
+        SOAP_TRY(ensure_pipeline(c));
+        soap::DevBuf& st = c->up_stage[slot];
+        SOAP_TRY(ensure(st, bytes));
+        SOAP_CUDA(cudaStreamWaitEvent(c->in_stream, c->up_free[slot], 0));   // last read of the stage
+        SOAP_CUDA(cudaMemcpyAsync(st.p, src, bytes, cudaMemcpyHostToDevice, c->in_stream));
+        SOAP_CUDA(cudaEventRecord(c->up_filled[slot], c->in_stream));
+        SOAP_CUDA(cudaStreamWaitEvent(c->stream, c->up_filled[slot], 0));
+        SOAP_TRY(pad_rows(c, st.as<double>(), dst64, dst32, c->n_mu));
+        SOAP_CUDA(cudaEventRecord(c->up_free[slot], c->stream));
+        return SOAP_OK;
+    }
     if (!on_device) {
         SOAP_TRY(ensure(c->stage_in, bytes));
         SOAP_TRY(to_device(c, c->stage_in.p, src, bytes, 0));
@@ -289,7 +432,7 @@ soap_status soap_init_star(const soap_star_desc* s, const double* quiet_local, i
     st = SOAP_OK;
     if (cudaMemsetAsync(c->flags, 0, sizeof(unsigned int), c->stream) != cudaSuccess) st = SOAP_ECUDA;
     if (st == SOAP_OK) st = geometry_init(c);
-    if (st == SOAP_OK) st = upload_spectra(c, quiet_local, quiet_on_device, c->q64, c->q32);
+    if (st == SOAP_OK) st = upload_spectra(c, quiet_local, quiet_on_device, c->q64, c->q32, 0);
     if (st == SOAP_OK) st = check_flags(c);
     if (st != SOAP_OK) {
         cudaStreamSynchronize(c->stream);
@@ -325,7 +468,7 @@ soap_status soap_update_star(soap_ctx* c, const soap_star_desc* s) {
 soap_status soap_set_quiet_spectrum(soap_ctx* c, const double* quiet_local, int on_device) {
     clear_error();
     if (!c || !quiet_local) { set_error("ctx or quiet_local is NULL"); return SOAP_EINVAL; }
-    return upload_spectra(c, quiet_local, on_device, c->q64, c->q32);
+    return upload_spectra(c, quiet_local, on_device, c->q64, c->q32, 0);
 }
 
 soap_status soap_set_profiling(soap_ctx* c, int enabled) {
@@ -367,7 +510,7 @@ soap_status soap_set_active_spectrum(soap_ctx* c, int32_t type, const double* ac
             return SOAP_ENOMEM;
         }
     }
-    SOAP_TRY(upload_spectra(c, active_local, on_device, c->a64[t], c->a32[t]));
+    SOAP_TRY(upload_spectra(c, active_local, on_device, c->a64[t], c->a32[t], 1 + t));
     c->active_set[t] = true;
     return SOAP_OK;
 }
@@ -382,7 +525,22 @@ soap_status soap_set_stream(soap_ctx* c, void* stream) {
 soap_status soap_synchronize(soap_ctx* c) {
     clear_error();
     if (!c) { set_error("ctx is NULL"); return SOAP_EINVAL; }
-    return check_flags(c);
+    if (c->in_stream) SOAP_CUDA(cudaStreamSynchronize(c->in_stream));
+    SOAP_TRY(check_flags(c));
+    if (c->out_stream) SOAP_CUDA(cudaStreamSynchronize(c->out_stream));
+    return SOAP_OK;
+}
+
+soap_status soap_set_host_async(soap_ctx* c, int enabled) {
+    clear_error();
+    if (!c) { set_error("ctx is NULL"); return SOAP_EINVAL; }
+    if (enabled) {
+        SOAP_TRY(ensure_pipeline(c));
+    } else if (c->host_async) {
+        sync_all(c);
+    }
+    c->host_async = enabled != 0;
+    return SOAP_OK;
 }
 
 soap_status soap_get_star_info(soap_ctx* c, soap_star_info* out) {
@@ -432,11 +590,20 @@ soap_status soap_quiet_spectrum(soap_ctx* c, int32_t form, int32_t precision, vo
     return SOAP_OK;
 }
 
-soap_status soap_active_phases(soap_ctx* c, const soap_region* regions, int32_t n_regions,
-                               const double* phases, int32_t n_phases, uint32_t effects,
-                               int32_t precision, void* out, int out_on_device) {
-    clear_error();
-    if (!c || !out) { set_error("ctx or out is NULL"); return SOAP_EINVAL; }
+}  // extern "C"
+
+// Checks of soap_active_phases / soap_active_rv arguments; the regions in device form and
+// their (type, temperature) classes.
+struct ActiveArgs {
+    std::vector<RegionDev> rd;
+    double ctemp[SOAP_MAX_CLASSES];
+    int ctype[SOAP_MAX_CLASSES];
+    int n_class = 0;
+};
+
+static soap_status check_active(soap_ctx* c, const soap_region* regions, int32_t n_regions,
+                                const double* phases, int32_t n_phases, uint32_t effects,
+                                int32_t precision, ActiveArgs& A) {
     if (n_regions < 0 || n_regions > SOAP_MAX_REGIONS) { set_error("n_regions=%d outside 0..%d", n_regions, SOAP_MAX_REGIONS); return SOAP_ERANGE; }
     if (n_regions > 0 && !regions) { set_error("regions is NULL"); return SOAP_EINVAL; }
     if (n_phases < 0) { set_error("n_phases < 0"); return SOAP_EINVAL; }
@@ -445,10 +612,8 @@ soap_status soap_active_phases(soap_ctx* c, const soap_region* regions, int32_t 
     if (precision != SOAP_FP64 && precision != SOAP_FP32) { set_error("unknown precision %d", precision); return SOAP_EINVAL; }
     for (int p = 0; p < n_phases; p++)
         if (!is_finite(phases[p])) { set_error("phases[%d] not finite", p); return SOAP_EINVAL; }
-    std::vector<RegionDev> rd(n_regions);
-    double ctemp[SOAP_MAX_CLASSES];
-    int ctype[SOAP_MAX_CLASSES];
-    int n_class = 0;
+    A.rd.resize(n_regions);
+    A.n_class = 0;
     for (int r = 0; r < n_regions; r++) {
         const soap_region& g = regions[r];
         if (g.type != SOAP_SPOT && g.type != SOAP_FACULA) { set_error("regions[%d].type invalid", r); return SOAP_EINVAL; }
@@ -459,20 +624,53 @@ soap_status soap_active_phases(soap_ctx* c, const soap_region* regions, int32_t 
         if (g.radius_rstar < 0 || g.radius_rstar > 1) { set_error("regions[%d].radius_rstar outside [0,1]", r); return SOAP_EINVAL; }
         if (!(g.temp_K > 0)) { set_error("regions[%d].temp_K must be > 0", r); return SOAP_EINVAL; }
         int cl = -1;
-        for (int k = 0; k < n_class; k++)
-            if (ctype[k] == g.type && ctemp[k] == g.temp_K) cl = k;
+        for (int k = 0; k < A.n_class; k++)
+            if (A.ctype[k] == g.type && A.ctemp[k] == g.temp_K) cl = k;
         if (cl < 0) {
-            if (n_class == SOAP_MAX_CLASSES) { set_error("more than %d distinct (type, temperature) pairs", SOAP_MAX_CLASSES); return SOAP_ERANGE; }
-            cl = n_class++;
-            ctype[cl] = g.type;
-            ctemp[cl] = g.temp_K;
+            if (A.n_class == SOAP_MAX_CLASSES) { set_error("more than %d distinct (type, temperature) pairs", SOAP_MAX_CLASSES); return SOAP_ERANGE; }
+            cl = A.n_class++;
+            A.ctype[cl] = g.type;
+            A.ctemp[cl] = g.temp_K;
         }
-        rd[r] = RegionDev{g.lat_deg, g.lon_deg, g.radius_rstar, g.temp_K, g.type, cl};
+        A.rd[r] = RegionDev{g.lat_deg, g.lon_deg, g.radius_rstar, g.temp_K, g.type, cl};
     }
-    for (int k = 0; k < n_class; k++) {
-        bool ok = ctype[k] == SOAP_SPOT ? c->active_set[0] : (c->active_set[1] || c->active_set[0]);
-        if (!ok) { set_error("no active spectrum set for region type %d", ctype[k]); return SOAP_ESTATE; }
+    for (int k = 0; k < A.n_class; k++) {
+        bool ok = A.ctype[k] == SOAP_SPOT ? c->active_set[0] : (c->active_set[1] || c->active_set[0]);
+        if (!ok) { set_error("no active spectrum set for region type %d", A.ctype[k]); return SOAP_ESTATE; }
     }
+    return SOAP_OK;
+}
+
+// Checks of the CCF / RV arguments (soap_rv_ccf, soap_active_rv).
+static soap_status check_rv(soap_ctx* c, const double* mask_lambda, const double* mask_weight,
+                            int32_t n_lines, double mask_width_kms, double v_lo, double v_step,
+                            int32_t n_v) {
+    if (!mask_lambda || !mask_weight) { set_error("NULL mask"); return SOAP_EINVAL; }
+    if (n_lines < 1 || n_v < 5 || n_v > 4096) { set_error("need n_lines >= 1, 5 <= n_v <= 4096"); return SOAP_EINVAL; }
+    if (!is_finite(mask_width_kms) || !(mask_width_kms > 0) || !is_finite(v_lo) || !is_finite(v_step) || !(v_step > 0)) {
+        set_error("mask width / velocity grid invalid"); return SOAP_EINVAL;
+    }
+    double v_hi = v_lo + v_step * (n_v - 1);
+    if (!(std::fabs(v_lo) < kCKms) || !(std::fabs(v_hi) < kCKms)) { set_error("velocity grid reaches c"); return SOAP_EINVAL; }
+    double h = mask_width_kms / (2.0 * kCKms * c->delta);
+    if (2.0 * h > 14.0) { set_error("mask box spans more than 14 pixels"); return SOAP_ERANGE; }
+    if (ccf_mask_same(c, mask_lambda, mask_weight, n_lines, mask_width_kms)) return SOAP_OK;   // checked before
+    for (int l = 0; l < n_lines; l++)
+        if (!is_finite(mask_lambda[l]) || !(mask_lambda[l] > 0) || !is_finite(mask_weight[l])) {
+            set_error("mask line %d invalid", l); return SOAP_EINVAL;
+        }
+    return SOAP_OK;
+}
+
+extern "C" {
+
+soap_status soap_active_phases(soap_ctx* c, const soap_region* regions, int32_t n_regions,
+                               const double* phases, int32_t n_phases, uint32_t effects,
+                               int32_t precision, void* out, int out_on_device) {
+    clear_error();
+    if (!c || !out) { set_error("ctx or out is NULL"); return SOAP_EINVAL; }
+    ActiveArgs A;
+    SOAP_TRY(check_active(c, regions, n_regions, phases, n_phases, effects, precision, A));
     int n_eff = __builtin_popcount(effects);
     size_t esz = precision == SOAP_FP64 ? 8 : 4;
     size_t bytes = (size_t)n_eff * (size_t)n_phases * (size_t)c->n_px * esz;
@@ -482,11 +680,69 @@ soap_status soap_active_phases(soap_ctx* c, const soap_region* regions, int32_t 
         SOAP_TRY(ensure(c->out_stage, bytes));
         dst = c->out_stage.p;
     }
-    SOAP_TRY(toeplitz_active(c, rd.data(), n_regions, ctemp, ctype, n_class, phases, n_phases,
+    SOAP_TRY(toeplitz_active(c, A.rd.data(), n_regions, A.ctemp, A.ctype, A.n_class, phases, n_phases,
                              effects, precision, dst));
     if (!out_on_device) {
         SOAP_CUDA(cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, c->stream));
         SOAP_CUDA(cudaStreamSynchronize(c->stream));
+        SOAP_TRY(check_flags(c));
+    }
+    return SOAP_OK;
+}
+
+soap_status soap_active_rv(soap_ctx* c, const soap_region* regions, int32_t n_regions,
+                           const double* phases, int32_t n_phases, uint32_t effect,
+                           int32_t precision, const double* mask_lambda, const double* mask_weight,
+                           int32_t n_lines, double mask_width_kms, double v_lo, double v_step,
+                           int32_t n_v, void* spectra_out, double* rv_kms, int out_on_device) {
+    clear_error();
+    if (!c || !rv_kms) { set_error("ctx or rv_kms is NULL"); return SOAP_EINVAL; }
+    if (effect != SOAP_EFFECT_FLUX && effect != SOAP_EFFECT_BCONV && effect != SOAP_EFFECT_TOT) {
+        set_error("effect must be exactly one of SOAP_EFFECT_*"); return SOAP_EINVAL;
+    }
+    ActiveArgs A;
+    SOAP_TRY(check_active(c, regions, n_regions, phases, n_phases, effect, precision, A));
+    SOAP_TRY(check_rv(c, mask_lambda, mask_weight, n_lines, mask_width_kms, v_lo, v_step, n_v));
+    if (n_phases == 0) return SOAP_OK;
+    const int f32 = precision == SOAP_FP32;
+    const size_t sbytes = (size_t)n_phases * (size_t)c->n_px * (f32 ? 4 : 8);
+    if (out_on_device) {
+        void* sp = spectra_out;
+        if (!sp) {
+            SOAP_TRY(ensure(c->out_stage, sbytes));
+            sp = c->out_stage.p;
+        }
+        SOAP_TRY(toeplitz_active(c, A.rd.data(), n_regions, A.ctemp, A.ctype, A.n_class, phases,
+                                 n_phases, effect, precision, sp));
+        return rv_ccf_run(c, sp, f32, n_phases, mask_lambda, mask_weight, n_lines, mask_width_kms,
+                          v_lo, v_step, n_v, rv_kms, nullptr, nullptr);
+    }
+    // host results: computed into one of two alternating device buffers; the spectra go to the
+    // host on out_stream while the CCF runs, the RVs after the fit
+    SOAP_TRY(ensure_pipeline(c));
+    const int o = c->dn_next;
+    c->dn_next ^= 1;
+    const size_t o_rv = (sbytes + 255) / 256 * 256;
+    soap::DevBuf& d = c->dn_stage[o];
+    SOAP_TRY(ensure(d, o_rv + (size_t)n_phases * 8));
+    void* spec_d = d.p;
+    double* rv_d = reinterpret_cast<double*>(d.as<char>() + o_rv);
+    SOAP_CUDA(cudaStreamWaitEvent(c->stream, c->dn_free[o], 0));        // its last copy out is done
+    SOAP_TRY(toeplitz_active(c, A.rd.data(), n_regions, A.ctemp, A.ctype, A.n_class, phases,
+                             n_phases, effect, precision, spec_d));
+    if (spectra_out) {
+        SOAP_CUDA(cudaEventRecord(c->dn_spec[o], c->stream));
+        SOAP_CUDA(cudaStreamWaitEvent(c->out_stream, c->dn_spec[o], 0));
+        SOAP_CUDA(cudaMemcpyAsync(spectra_out, spec_d, sbytes, cudaMemcpyDeviceToHost, c->out_stream));
+    }
+    SOAP_TRY(rv_ccf_run(c, spec_d, f32, n_phases, mask_lambda, mask_weight, n_lines, mask_width_kms,
+                        v_lo, v_step, n_v, rv_d, nullptr, nullptr));
+    SOAP_CUDA(cudaEventRecord(c->dn_rv[o], c->stream));
+    SOAP_CUDA(cudaStreamWaitEvent(c->out_stream, c->dn_rv[o], 0));
+    SOAP_CUDA(cudaMemcpyAsync(rv_kms, rv_d, (size_t)n_phases * 8, cudaMemcpyDeviceToHost, c->out_stream));
+    SOAP_CUDA(cudaEventRecord(c->dn_free[o], c->out_stream));
+    if (!c->host_async) {
+        SOAP_CUDA(cudaStreamSynchronize(c->out_stream));
         SOAP_TRY(check_flags(c));
     }
     return SOAP_OK;
@@ -501,18 +757,8 @@ soap_status soap_rv_ccf(soap_ctx* c, const void* spectra, int32_t spectra_f32, i
     if (!c || !spectra || !mask_lambda || !mask_weight || !rv_kms) {
         set_error("NULL argument"); return SOAP_EINVAL;
     }
-    if (n_spec < 0 || n_lines < 1 || n_v < 5 || n_v > 4096) { set_error("need n_spec >= 0, n_lines >= 1, 5 <= n_v <= 4096"); return SOAP_EINVAL; }
-    if (!is_finite(mask_width_kms) || !(mask_width_kms > 0) || !is_finite(v_lo) || !is_finite(v_step) || !(v_step > 0)) {
-        set_error("mask width / velocity grid invalid"); return SOAP_EINVAL;
-    }
-    double v_hi = v_lo + v_step * (n_v - 1);
-    if (!(std::fabs(v_lo) < kCKms) || !(std::fabs(v_hi) < kCKms)) { set_error("velocity grid reaches c"); return SOAP_EINVAL; }
-    double h = mask_width_kms / (2.0 * kCKms * c->delta);
-    if (2.0 * h > 14.0) { set_error("mask box spans more than 14 pixels"); return SOAP_ERANGE; }
-    for (int l = 0; l < n_lines; l++)
-        if (!is_finite(mask_lambda[l]) || !(mask_lambda[l] > 0) || !is_finite(mask_weight[l])) {
-            set_error("mask line %d invalid", l); return SOAP_EINVAL;
-        }
+    if (n_spec < 0) { set_error("need n_spec >= 0"); return SOAP_EINVAL; }
+    SOAP_TRY(check_rv(c, mask_lambda, mask_weight, n_lines, mask_width_kms, v_lo, v_step, n_v));
     if (n_spec == 0) return SOAP_OK;
     size_t esz = spectra_f32 ? 4 : 8;
     size_t sbytes = (size_t)n_spec * (size_t)c->n_px * esz;
@@ -657,7 +903,8 @@ soap_status soap_batch_autotune(soap_ctx* c, const soap_batch_item* items, int32
 
 void soap_free(soap_ctx* c) {
     if (!c) return;
-    cudaStreamSynchronize(c->stream);
+    sync_all(c);
+    destroy_pipeline(c);
     destroy_events(c);
     batch_release(c);
     free_ctx_memory(c);

@@ -11,6 +11,7 @@
 // k_gauss_fit: one warp per spectrum, FP64 Levenberg-Marquardt on
 // A + B exp(-(v - mu)^2 / (2 s^2)).
 #include <cmath>
+#include <cstring>
 #include <type_traits>
 #include <algorithm>
 
@@ -754,13 +755,30 @@ __global__ void __launch_bounds__(kFitThreads) k_gauss_fit(int n_spec, int n_v, 
     }
 }
 
+bool ccf_mask_same(const soap_ctx* c, const double* mask_lambda, const double* mask_weight,
+                   int n_lines, double width_kms) {
+    const std::vector<double>& k = c->ccf_mask_key;
+    return k.size() == 2 * (size_t)n_lines + 1 &&
+           std::memcmp(k.data(), mask_lambda, (size_t)n_lines * 8) == 0 &&
+           std::memcmp(k.data() + n_lines, mask_weight, (size_t)n_lines * 8) == 0 &&
+           std::memcmp(k.data() + 2 * (size_t)n_lines, &width_kms, 8) == 0;
+}
+
 soap_status rv_ccf_run(soap_ctx* c, const void* spectra_dev, int f32, int n_spec,
                        const double* mask_lambda, const double* mask_weight, int n_lines,
                        double width_kms, double v_lo, double v_step, int n_v, double* rv_dev,
                        double* fit_dev, double* ccf_dev) {
+    // line and velocity tables: kept while the mask, its width and the velocity grid stay the same
+    const bool same_tab = c->ccf_lines_ok && c->ccf_vel_key[0] == v_lo && c->ccf_vel_key[1] == v_step &&
+                          c->ccf_vel_key[2] == (double)n_v &&
+                          ccf_mask_same(c, mask_lambda, mask_weight, n_lines, width_kms);
     bool sorted = true;
-    for (int l = 1; l < n_lines; l++)
-        if (mask_lambda[l] < mask_lambda[l - 1]) { sorted = false; break; }
+    if (same_tab) {
+        sorted = c->ccf_sorted;
+    } else {
+        for (int l = 1; l < n_lines; l++)
+            if (mask_lambda[l] < mask_lambda[l - 1]) { sorted = false; break; }
+    }
     // windowed kernel: one velocity per thread (n_v <= 256); blocks walk the chunks
     const bool windowed = sorted && n_v <= 256 && 2.0 * width_kms / (2.0 * kCKms * c->delta) <= 15.0;
     const int n_wchunks = (n_lines + kWinLines - 1) / kWinLines;
@@ -799,7 +817,7 @@ soap_status rv_ccf_run(soap_ctx* c, const void* spectra_dev, int f32, int n_spec
             n_chunks = tile_blocks;
         }
     }
-    // scratch layout (8-byte aligned pieces, 256-byte aligned blocks)
+    // table layout (8-byte aligned pieces, 256-byte aligned blocks) and per-call scratch
     auto al = [](size_t x) { return (x + 255) / 256 * 256; };
     size_t o_lam = 0;
     size_t o_w = al(o_lam + (size_t)n_lines * 8);
@@ -811,37 +829,51 @@ soap_status rv_ccf_run(soap_ctx* c, const void* spectra_dev, int f32, int n_spec
     size_t o_S = al(o_valid + (size_t)n_lines * 4);
     size_t o_g64 = al(o_S + (size_t)n_v * 4);
     size_t o_g32 = al(o_g64 + (size_t)n_v * 8);
-    size_t o_part = al(o_g32 + (size_t)n_v * 4);
+    size_t tab_total = o_g32 + (size_t)n_v * 4;
+    size_t o_part = 0;
     size_t o_ccf = al(o_part + (size_t)n_chunks * n_spec * n_v * 8);
     size_t o_y = al(o_ccf + (size_t)n_spec * n_v * 8);
     size_t total = o_y + (size_t)n_spec * n_v * 8;
     SOAP_TRY(ensure(c->ccf_tmp, total));
+    SOAP_TRY(ensure(c->ccf_tab, tab_total));
+    char* tab = c->ccf_tab.as<char>();
     char* base = c->ccf_tmp.as<char>();
-    double* d_lam = (double*)(base + o_lam);
-    double* d_w = (double*)(base + o_w);
-    int* d_U = (int*)(base + o_U);
-    double* d_f64 = (double*)(base + o_f64);
-    float* d_f32 = (float*)(base + o_f32);
-    float* d_w32 = (float*)(base + o_w32);
-    int* d_valid = (int*)(base + o_valid);
-    int* d_S = (int*)(base + o_S);
-    double* d_g64 = (double*)(base + o_g64);
-    float* d_g32 = (float*)(base + o_g32);
+    double* d_lam = (double*)(tab + o_lam);
+    double* d_w = (double*)(tab + o_w);
+    int* d_U = (int*)(tab + o_U);
+    double* d_f64 = (double*)(tab + o_f64);
+    float* d_f32 = (float*)(tab + o_f32);
+    float* d_w32 = (float*)(tab + o_w32);
+    int* d_valid = (int*)(tab + o_valid);
+    int* d_S = (int*)(tab + o_S);
+    double* d_g64 = (double*)(tab + o_g64);
+    float* d_g32 = (float*)(tab + o_g32);
     double* d_part = (double*)(base + o_part);
     double* d_ccf = ccf_dev ? ccf_dev : (double*)(base + o_ccf);
     double* d_y = (double*)(base + o_y);
-    SOAP_CUDA(cudaMemcpyAsync(d_lam, mask_lambda, (size_t)n_lines * 8, cudaMemcpyHostToDevice, c->stream));
-    SOAP_CUDA(cudaMemcpyAsync(d_w, mask_weight, (size_t)n_lines * 8, cudaMemcpyHostToDevice, c->stream));
     cudaEvent_t tb = c->profiling ? timer_begin(c) : nullptr;
     const double h = width_kms / (2.0 * kCKms * c->delta);
     const double v_hi = v_lo + v_step * (n_v - 1);
-    k_ccf_lines<<<(n_lines + 255) / 256, 256, 0, c->stream>>>(
-        n_lines, d_lam, d_w, c->lam_s, c->delta, h, std::atanh(v_lo / kCKms) / c->delta,
-        std::atanh(v_hi / kCKms) / c->delta, c->n_px, d_U, d_f64, d_f32, d_w32, d_valid);
-    SOAP_LAUNCHED(c);
-    k_ccf_velocities<<<(n_v + 127) / 128, 128, 0, c->stream>>>(n_v, v_lo, v_step, c->delta, d_S,
-                                                               d_g64, d_g32);
-    SOAP_LAUNCHED(c);
+    if (!same_tab) {
+        c->ccf_lines_ok = false;
+        SOAP_TRY(upload_small(c, d_lam, mask_lambda, (size_t)n_lines * 8));
+        SOAP_TRY(upload_small(c, d_w, mask_weight, (size_t)n_lines * 8));
+        k_ccf_lines<<<(n_lines + 255) / 256, 256, 0, c->stream>>>(
+            n_lines, d_lam, d_w, c->lam_s, c->delta, h, std::atanh(v_lo / kCKms) / c->delta,
+            std::atanh(v_hi / kCKms) / c->delta, c->n_px, d_U, d_f64, d_f32, d_w32, d_valid);
+        SOAP_LAUNCHED(c);
+        k_ccf_velocities<<<(n_v + 127) / 128, 128, 0, c->stream>>>(n_v, v_lo, v_step, c->delta, d_S,
+                                                                   d_g64, d_g32);
+        SOAP_LAUNCHED(c);
+        c->ccf_mask_key.assign(mask_lambda, mask_lambda + n_lines);
+        c->ccf_mask_key.insert(c->ccf_mask_key.end(), mask_weight, mask_weight + n_lines);
+        c->ccf_mask_key.push_back(width_kms);
+        c->ccf_vel_key[0] = v_lo;
+        c->ccf_vel_key[1] = v_step;
+        c->ccf_vel_key[2] = (double)n_v;
+        c->ccf_sorted = sorted;
+        c->ccf_lines_ok = true;
+    }
     const int threads = n_v >= 256 ? 256 : ((n_v + 31) / 32) * 32;
     if (tile_np) {
         const int tthreads = ((n_v + kTileVT - 1) / kTileVT * kTileLP + 31) / 32 * 32;

@@ -249,15 +249,14 @@ soap_status toeplitz_active(soap_ctx* c, const RegionDev* regions_host, int n_re
                            c->n_px, (float)(hck / (c->lam_s * c->t_quiet)), (float)c->delta, n_class, cc, con32);
                        SOAP_LAUNCHED(c));
     }
-    // regions and phases to the device (pageable copies are staged by the driver at once)
+    // regions and phases to the device (through the pinned ring: no wait for the stream)
     size_t rbytes = (size_t)(n_regions > 0 ? n_regions : 1) * sizeof(RegionDev);
     size_t pbytes = (size_t)n_phases * sizeof(double);
     SOAP_TRY(ensure(c->regions, rbytes));
     SOAP_TRY(ensure(c->phases, pbytes));
     if (n_regions > 0)
-        SOAP_CUDA(cudaMemcpyAsync(c->regions.p, regions_host, (size_t)n_regions * sizeof(RegionDev),
-                                  cudaMemcpyHostToDevice, c->stream));
-    SOAP_CUDA(cudaMemcpyAsync(c->phases.p, phases_host, pbytes, cudaMemcpyHostToDevice, c->stream));
+        SOAP_TRY(upload_small(c, c->regions.p, regions_host, (size_t)n_regions * sizeof(RegionDev)));
+    SOAP_TRY(upload_small(c, c->phases.p, phases_host, pbytes));
     // per-phase fixed-point kernels
     int64_t nb = (int64_t)ncl * c->n_mu * c->n_taps;
     size_t kbytes = (size_t)n_phases * nb * sizeof(long long);

@@ -80,6 +80,22 @@ struct HostBuf {
 soap_status ensure_host(HostBuf& b, size_t bytes);
 void release_host(HostBuf& b);
 
+// Pinned staging ring for small host -> device uploads (regions, phases, masks).  A copy from
+// pageable memory makes the driver wait for the stream before it copies, which would stall a
+// caller that enqueues step after step; through the ring the host only copies into pinned
+// memory and enqueues a small kernel that reads it through its device mapping (no copy engine:
+// a small upload must not queue behind a large one).  Each upload records an event; a range of
+// the ring is rewritten only once the reads that last used it are done.
+struct PinnedRing {
+    unsigned char* p = nullptr;        // host address
+    unsigned char* dev = nullptr;      // the same memory, as the device sees it
+    size_t cap = 0, head = 0;
+    struct Use { size_t lo, hi; cudaEvent_t ev; };
+    std::vector<Use> pending;          // oldest first
+    std::vector<cudaEvent_t> free_ev;
+};
+constexpr size_t kRingBytes = size_t(4) << 20;
+
 // Status word written by kernels (bounds checks that skip an access and record it).
 enum DeviceFlag : unsigned int {
     kFlagTapRange = 1u,        // a cell's tap fell outside the precomputed kernel range
@@ -154,6 +170,27 @@ struct soap_ctx {
     soap::DevBuf partial;       // direct-form and CCF partial sums
     soap::DevBuf ccf_tmp;       // CCF inputs / outputs
     soap::HostBuf host_stage;
+    soap::PinnedRing ring;      // small uploads (see PinnedRing)
+
+    // CCF line and velocity tables, kept while the mask and the velocity grid stay the same
+    soap::DevBuf ccf_tab;
+    std::vector<double> ccf_mask_key;    // mask_lambda, mask_weight, then width
+    double ccf_vel_key[3] = {0, 0, -1};  // v_lo, v_step, n_v
+    bool ccf_lines_ok = false;
+    bool ccf_sorted = false;
+
+    // host-transfer pipeline: uploads from host memory run on in_stream, downloads of host
+    // results on out_stream, ordered against the compute stream by events.  up_* serve the
+    // quiet / spot / facula uploads (filled: copy done; free: pad_rows has read the stage);
+    // dn_* are two alternating device buffers for host results (spec / rv: the spectra /
+    // the RVs are written; free: their copy to the host is done).
+    bool host_async = false;            // calls with host outputs return before the copies end
+    cudaStream_t in_stream = nullptr, out_stream = nullptr;
+    soap::DevBuf up_stage[3];
+    cudaEvent_t up_filled[3] = {}, up_free[3] = {};
+    soap::DevBuf dn_stage[2];
+    cudaEvent_t dn_spec[2] = {}, dn_rv[2] = {}, dn_free[2] = {};
+    int dn_next = 0;
 
     uint64_t launches = 0;
 
@@ -186,6 +223,13 @@ void timer_end(soap_ctx* c, int timer, cudaEvent_t begin);
 // ---------------------------------------------------------------------------------------
 soap_status geometry_init(soap_ctx* c);                          // per-cell geometry + quiet kernels
 soap_status pad_rows(soap_ctx* c, const double* src, double* dst64, float* dst32, int rows);
+// Copy `bytes` of host memory to device memory `dst` on the context stream through the pinned
+// ring (pageable sources are fine; the source may change once the call returns).
+soap_status upload_small(soap_ctx* c, void* dst, const void* src, size_t bytes);
+void ring_release(soap_ctx* c);
+// True when the context's CCF line tables were built from exactly this mask and width.
+bool ccf_mask_same(const soap_ctx* c, const double* mask_lambda, const double* mask_weight,
+                   int n_lines, double width_kms);
 
 // Toeplitz quiet spectrum into dst (fp64 or fp32) on the context's stream.
 soap_status toeplitz_quiet(soap_ctx* c, int precision, void* dst);

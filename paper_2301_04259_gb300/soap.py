@@ -87,6 +87,9 @@ def _load():
         "soap_reset_kernel_times": (i32, [P]),
         "soap_set_stream": (i32, [P, P]),
         "soap_synchronize": (i32, [P]),
+        "soap_set_host_async": (i32, [P, ctypes.c_int]),
+        "soap_active_rv": (i32, [P, ctypes.POINTER(soap_region), i32, P, i32, u32, i32, P, P, i32, d, d, d,
+                                 i32, P, P, ctypes.c_int]),
         "soap_get_star_info": (i32, [P, ctypes.POINTER(soap_star_info)]),
         "soap_quiet_spectrum": (i32, [P, i32, i32, P, ctypes.c_int]),
         "soap_active_phases": (i32, [P, ctypes.POINTER(soap_region), i32, P, i32, u32, i32, P, ctypes.c_int]),
@@ -251,6 +254,29 @@ def soap_active_phases(ctx, regions: Sequence, phases, effects: int, precision: 
     ptr, dev = _ptr(out)
     _check(_lib.soap_active_phases(ctx, arr, len(regions), ctypes.c_void_p(ph.ctypes.data), ph.size,
                                    int(effects), int(precision), ptr, dev), "soap_active_phases")
+
+
+def soap_set_host_async(ctx, enabled: bool) -> None:
+    _check(_lib.soap_set_host_async(ctx, int(bool(enabled))), "soap_set_host_async")
+
+
+def soap_active_rv(ctx, regions: Sequence, phases, effect: int, precision: int, mask_lambda,
+                   mask_weight, mask_width_kms: float, v_lo: float, v_step: float, n_v: int,
+                   spectra_out, rv_out) -> None:
+    """Spectra of one effect and their RVs; spectra_out (or None) and rv_out both host or both
+    device."""
+    arr = regions_array(regions)
+    ph = np.ascontiguousarray(phases, dtype=np.float64)
+    ml = np.ascontiguousarray(mask_lambda, dtype=np.float64)
+    mw = np.ascontiguousarray(mask_weight, dtype=np.float64)
+    rp, rdev = _ptr(rv_out)
+    sp, sdev = _ptr(spectra_out)
+    if spectra_out is not None and sdev != rdev:
+        raise ValueError("spectra_out and rv_out must both be host or both device")
+    _check(_lib.soap_active_rv(ctx, arr, len(regions), ctypes.c_void_p(ph.ctypes.data), ph.size,
+                               int(effect), int(precision), ctypes.c_void_p(ml.ctypes.data),
+                               ctypes.c_void_p(mw.ctypes.data), ml.size, float(mask_width_kms),
+                               float(v_lo), float(v_step), int(n_v), sp, rp, rdev), "soap_active_rv")
 
 
 def soap_rv_ccf(ctx, spectra, mask_lambda, mask_weight, mask_width_kms: float, v_lo: float,

@@ -31,7 +31,7 @@ def lib():
 def test_header_declares_the_boundary():
     names = _declared()
     for n in ("soap_init_star", "soap_quiet_spectrum", "soap_active_phases", "soap_rv_ccf",
-              "soap_free", "soap_last_error"):
+              "soap_active_rv", "soap_set_host_async", "soap_free", "soap_last_error"):
         assert n in names
 
 
@@ -68,6 +68,9 @@ def test_null_arguments_are_rejected(lib):
     assert lib._lib.soap_init_star(None, None, 0, None, ctypes.byref(ctx)) == lib.SOAP_EINVAL
     assert lib._lib.soap_quiet_spectrum(None, 0, 0, None, 0) == lib.SOAP_EINVAL
     assert lib._lib.soap_active_phases(None, None, 0, None, 0, 1, 0, None, 0) == lib.SOAP_EINVAL
+    assert lib._lib.soap_active_rv(None, None, 0, None, 0, 1, 0, None, None, 0, 0.8, -20.0, 0.25, 161,
+                                   None, None, 0) == lib.SOAP_EINVAL
+    assert lib._lib.soap_set_host_async(None, 1) == lib.SOAP_EINVAL
     lib._lib.soap_free(None)
 
 
