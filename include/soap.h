@@ -188,12 +188,22 @@ soap_status soap_update_star(soap_ctx* ctx, const soap_star_desc* star);
 /* Replace the quiet local spectra ([n_mu][n_px] float64, host or device). */
 soap_status soap_set_quiet_spectrum(soap_ctx* ctx, const double* quiet_local, int on_device);
 
+/* The same from float32 local spectra ([n_mu][n_px] float32, host or device), for callers of
+ * the SOAP_FP32 path only: the SOAP_FP32 results are those of float64 spectra rounded to
+ * float32 (which that path reads anyway), at half the upload.  Until float64 spectra are set
+ * again, SOAP_FP64 calls fail with SOAP_ESTATE. */
+soap_status soap_set_quiet_spectrum_f32(soap_ctx* ctx, const float* quiet_local, int on_device);
+
 /* Upload the active-region local spectra of one region type (Sect. 2.1: S_active).
  *  type          SOAP_SPOT or SOAP_FACULA.  Until a facula spectrum is set, faculae use the
  *                spot spectrum (as SOAP 2.0 did).
  *  active_local  [n_mu][n_px] float64, host or device. */
 soap_status soap_set_active_spectrum(soap_ctx* ctx, int32_t type, const double* active_local,
                                      int on_device);
+
+/* The same from float32 active local spectra (see soap_set_quiet_spectrum_f32). */
+soap_status soap_set_active_spectrum_f32(soap_ctx* ctx, int32_t type, const float* active_local,
+                                         int on_device);
 
 /* Replace the context's stream (cudaStream_t or NULL). */
 soap_status soap_set_stream(soap_ctx* ctx, void* cuda_stream);

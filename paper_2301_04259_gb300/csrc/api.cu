@@ -223,13 +223,14 @@ static void free_ctx_memory(soap_ctx* c) {
     ring_release(c);
 }
 
-// upload [n_mu][n_px] float64 spectra into padded fp64 + fp32 rows.  With the host-transfer
-// pipeline on, a host source is copied on in_stream into its own stage (slot: 0 quiet, 1 spot,
-// 2 facula) and the compute stream waits for that copy only.
-static soap_status upload_spectra(soap_ctx* c, const double* src, int on_device, double* dst64,
-                                  float* dst32, int slot) {
-    size_t bytes = (size_t)c->n_mu * (size_t)c->n_px * sizeof(double);
-    const double* dsrc = src;
+// upload [n_mu][n_px] local spectra into padded rows: float64 sources fill the fp64 and fp32
+// rows, float32 sources (f32src) the fp32 rows only.  With the host-transfer pipeline on, a
+// host source is copied on in_stream into its own stage (slot: 0 quiet, 1 spot, 2 facula) and
+// the compute stream waits for that copy only.
+static soap_status upload_spectra(soap_ctx* c, const void* src, int on_device, int f32src,
+                                  double* dst64, float* dst32, int slot) {
+    size_t bytes = (size_t)c->n_mu * (size_t)c->n_px * (f32src ? sizeof(float) : sizeof(double));
+    const void* dsrc = src;
     if (!on_device && c->host_async) {
         SOAP_TRY(ensure_pipeline(c));
         soap::DevBuf& st = c->up_stage[slot];
@@ -238,16 +239,16 @@ static soap_status upload_spectra(soap_ctx* c, const double* src, int on_device,
         SOAP_CUDA(cudaMemcpyAsync(st.p, src, bytes, cudaMemcpyHostToDevice, c->in_stream));
         SOAP_CUDA(cudaEventRecord(c->up_filled[slot], c->in_stream));
         SOAP_CUDA(cudaStreamWaitEvent(c->stream, c->up_filled[slot], 0));
-        SOAP_TRY(pad_rows(c, st.as<double>(), dst64, dst32, c->n_mu));
-        SOAP_CUDA(cudaEventRecord(c->up_free[slot], c->stream));
-        return SOAP_OK;
-    }
-    if (!on_device) {
+        dsrc = st.p;
+    } else if (!on_device) {
         SOAP_TRY(ensure(c->stage_in, bytes));
         SOAP_TRY(to_device(c, c->stage_in.p, src, bytes, 0));
-        dsrc = c->stage_in.as<double>();
+        dsrc = c->stage_in.p;
     }
-    return pad_rows(c, dsrc, dst64, dst32, c->n_mu);
+    if (f32src) SOAP_TRY(pad_rows32(c, static_cast<const float*>(dsrc), dst32, c->n_mu));
+    else SOAP_TRY(pad_rows(c, static_cast<const double*>(dsrc), dst64, dst32, c->n_mu));
+    if (!on_device && c->host_async) SOAP_CUDA(cudaEventRecord(c->up_free[slot], c->stream));
+    return SOAP_OK;
 }
 
 static soap_status check_flags(soap_ctx* c) {
@@ -432,7 +433,8 @@ soap_status soap_init_star(const soap_star_desc* s, const double* quiet_local, i
     st = SOAP_OK;
     if (cudaMemsetAsync(c->flags, 0, sizeof(unsigned int), c->stream) != cudaSuccess) st = SOAP_ECUDA;
     if (st == SOAP_OK) st = geometry_init(c);
-    if (st == SOAP_OK) st = upload_spectra(c, quiet_local, quiet_on_device, c->q64, c->q32, 0);
+    if (st == SOAP_OK) st = upload_spectra(c, quiet_local, quiet_on_device, 0, c->q64, c->q32, 0);
+    c->q64_ok = st == SOAP_OK;
     if (st == SOAP_OK) st = check_flags(c);
     if (st != SOAP_OK) {
         cudaStreamSynchronize(c->stream);
@@ -468,7 +470,16 @@ soap_status soap_update_star(soap_ctx* c, const soap_star_desc* s) {
 soap_status soap_set_quiet_spectrum(soap_ctx* c, const double* quiet_local, int on_device) {
     clear_error();
     if (!c || !quiet_local) { set_error("ctx or quiet_local is NULL"); return SOAP_EINVAL; }
-    return upload_spectra(c, quiet_local, on_device, c->q64, c->q32, 0);
+    SOAP_TRY(upload_spectra(c, quiet_local, on_device, 0, c->q64, c->q32, 0));
+    c->q64_ok = true;
+    return SOAP_OK;
+}
+
+soap_status soap_set_quiet_spectrum_f32(soap_ctx* c, const float* quiet_local, int on_device) {
+    clear_error();
+    if (!c || !quiet_local) { set_error("ctx or quiet_local is NULL"); return SOAP_EINVAL; }
+    c->q64_ok = false;
+    return upload_spectra(c, quiet_local, on_device, 1, nullptr, c->q32, 0);
 }
 
 soap_status soap_set_profiling(soap_ctx* c, int enabled) {
@@ -496,9 +507,8 @@ soap_status soap_reset_kernel_times(soap_ctx* c) {
     return SOAP_OK;
 }
 
-soap_status soap_set_active_spectrum(soap_ctx* c, int32_t type, const double* active_local,
-                                     int on_device) {
-    clear_error();
+static soap_status set_active(soap_ctx* c, int32_t type, const void* active_local, int on_device,
+                              int f32src) {
     if (!c || !active_local) { set_error("ctx or active_local is NULL"); return SOAP_EINVAL; }
     if (type != SOAP_SPOT && type != SOAP_FACULA) { set_error("type must be SOAP_SPOT or SOAP_FACULA"); return SOAP_EINVAL; }
     int t = type - 1;
@@ -510,9 +520,23 @@ soap_status soap_set_active_spectrum(soap_ctx* c, int32_t type, const double* ac
             return SOAP_ENOMEM;
         }
     }
-    SOAP_TRY(upload_spectra(c, active_local, on_device, c->a64[t], c->a32[t], 1 + t));
+    c->a64_ok[t] = false;
+    SOAP_TRY(upload_spectra(c, active_local, on_device, f32src, c->a64[t], c->a32[t], 1 + t));
     c->active_set[t] = true;
+    c->a64_ok[t] = !f32src;
     return SOAP_OK;
+}
+
+soap_status soap_set_active_spectrum(soap_ctx* c, int32_t type, const double* active_local,
+                                     int on_device) {
+    clear_error();
+    return set_active(c, type, active_local, on_device, 0);
+}
+
+soap_status soap_set_active_spectrum_f32(soap_ctx* c, int32_t type, const float* active_local,
+                                         int on_device) {
+    clear_error();
+    return set_active(c, type, active_local, on_device, 1);
 }
 
 soap_status soap_set_stream(soap_ctx* c, void* stream) {
@@ -574,6 +598,10 @@ soap_status soap_quiet_spectrum(soap_ctx* c, int32_t form, int32_t precision, vo
     if (!c || !out) { set_error("ctx or out is NULL"); return SOAP_EINVAL; }
     if (form != SOAP_FORM_TOEPLITZ && form != SOAP_FORM_DIRECT) { set_error("unknown form %d", form); return SOAP_EINVAL; }
     if (precision != SOAP_FP64 && precision != SOAP_FP32) { set_error("unknown precision %d", precision); return SOAP_EINVAL; }
+    if (precision == SOAP_FP64 && !c->q64_ok) {
+        set_error("the FP64 path needs float64 local spectra (the quiet ones were set in float32)");
+        return SOAP_ESTATE;
+    }
     size_t esz = precision == SOAP_FP64 ? 8 : 4;
     size_t bytes = (size_t)c->n_px * esz;
     void* dst = out;
@@ -637,6 +665,11 @@ static soap_status check_active(soap_ctx* c, const soap_region* regions, int32_t
     for (int k = 0; k < A.n_class; k++) {
         bool ok = A.ctype[k] == SOAP_SPOT ? c->active_set[0] : (c->active_set[1] || c->active_set[0]);
         if (!ok) { set_error("no active spectrum set for region type %d", A.ctype[k]); return SOAP_ESTATE; }
+    }
+    if (precision == SOAP_FP64 && (!c->q64_ok || (c->active_set[0] && !c->a64_ok[0]) ||
+                                   (c->active_set[1] && !c->a64_ok[1]))) {
+        set_error("the FP64 path needs float64 local spectra (some were set in float32)");
+        return SOAP_ESTATE;
     }
     return SOAP_OK;
 }

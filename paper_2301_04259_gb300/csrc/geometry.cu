@@ -150,6 +150,20 @@ __global__ void k_pad_rows(const double* __restrict__ src, int64_t n_px, int64_t
     }
 }
 
+// float32 local spectra: the float32 rows only
+__global__ void k_pad_rows32(const float* __restrict__ src, int64_t n_px, int64_t pad, int64_t row_len,
+                             float* __restrict__ dst32) {
+    const int64_t r = blockIdx.y;
+    const float* s = src + r * n_px;
+    float* d32 = dst32 + r * row_len;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < row_len;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t n = e - pad;
+        n = n < 0 ? 0 : (n >= n_px ? n_px - 1 : n);
+        d32[e] = __ldg(s + n);
+    }
+}
+
 static int grid_for(int64_t n, int threads, int cap = 152 * 16) {
     int64_t g = (n + threads - 1) / threads;
     if (g < 1) g = 1;
@@ -161,6 +175,14 @@ soap_status pad_rows(soap_ctx* c, const double* src, double* dst64, float* dst32
     dim3 grid((unsigned)grid_for(c->row_len, 256, 64), (unsigned)rows);
     SOAP_TIMED(c, SOAP_TIMER_PAD_ROWS,
                k_pad_rows<<<grid, 256, 0, c->stream>>>(src, c->n_px, c->pad, c->row_len, dst64, dst32);
+               SOAP_LAUNCHED(c));
+    return SOAP_OK;
+}
+
+soap_status pad_rows32(soap_ctx* c, const float* src, float* dst32, int rows) {
+    dim3 grid((unsigned)grid_for(c->row_len, 256, 64), (unsigned)rows);
+    SOAP_TIMED(c, SOAP_TIMER_PAD_ROWS,
+               k_pad_rows32<<<grid, 256, 0, c->stream>>>(src, c->n_px, c->pad, c->row_len, dst32);
                SOAP_LAUNCHED(c));
     return SOAP_OK;
 }

@@ -144,6 +144,8 @@ struct soap_ctx {
     double* a64[2] = {nullptr, nullptr};   // [0] spot, [1] facula
     float* a32[2] = {nullptr, nullptr};
     bool active_set[2] = {false, false};
+    bool q64_ok = false;                   // float64 rows hold the last quiet upload
+    bool a64_ok[2] = {false, false};       // (a float32 upload fills the float32 rows only)
 
     // quiet velocity kernels, fixed point [n_mu][n_taps]
     long long* kq_fixed = nullptr;
@@ -223,6 +225,7 @@ void timer_end(soap_ctx* c, int timer, cudaEvent_t begin);
 // ---------------------------------------------------------------------------------------
 soap_status geometry_init(soap_ctx* c);                          // per-cell geometry + quiet kernels
 soap_status pad_rows(soap_ctx* c, const double* src, double* dst64, float* dst32, int rows);
+soap_status pad_rows32(soap_ctx* c, const float* src, float* dst32, int rows);
 // Copy `bytes` of host memory to device memory `dst` on the context stream through the pinned
 // ring (pageable sources are fine; the source may change once the call returns).
 soap_status upload_small(soap_ctx* c, void* dst, const void* src, size_t bytes);

@@ -82,6 +82,8 @@ def _load():
         "soap_set_active_spectrum": (i32, [P, i32, P, ctypes.c_int]),
         "soap_update_star": (i32, [P, ctypes.POINTER(soap_star_desc)]),
         "soap_set_quiet_spectrum": (i32, [P, P, ctypes.c_int]),
+        "soap_set_quiet_spectrum_f32": (i32, [P, P, ctypes.c_int]),
+        "soap_set_active_spectrum_f32": (i32, [P, i32, P, ctypes.c_int]),
         "soap_set_profiling": (i32, [P, ctypes.c_int]),
         "soap_get_kernel_time": (i32, [P, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64)]),
         "soap_reset_kernel_times": (i32, [P]),
@@ -193,9 +195,17 @@ def soap_update_star(ctx, star) -> None:
     _check(_lib.soap_update_star(ctx, ctypes.byref(d)), "soap_update_star")
 
 
+def _is_f32(a) -> bool:
+    return str(a.dtype).endswith("float32")
+
+
 def soap_set_quiet_spectrum(ctx, quiet_local) -> None:
+    """float64 local spectra, or float32 ones (SOAP_FP32 path only)."""
     ptr, dev = _ptr(quiet_local)
-    _check(_lib.soap_set_quiet_spectrum(ctx, ptr, dev), "soap_set_quiet_spectrum")
+    if _is_f32(quiet_local):
+        _check(_lib.soap_set_quiet_spectrum_f32(ctx, ptr, dev), "soap_set_quiet_spectrum_f32")
+    else:
+        _check(_lib.soap_set_quiet_spectrum(ctx, ptr, dev), "soap_set_quiet_spectrum")
 
 
 def soap_set_profiling(ctx, enabled: bool) -> None:
@@ -216,8 +226,12 @@ def soap_reset_kernel_times(ctx) -> None:
 
 
 def soap_set_active_spectrum(ctx, type_: int, active_local) -> None:
+    """float64 active local spectra, or float32 ones (SOAP_FP32 path only)."""
     ptr, dev = _ptr(active_local)
-    _check(_lib.soap_set_active_spectrum(ctx, int(type_), ptr, dev), "soap_set_active_spectrum")
+    if _is_f32(active_local):
+        _check(_lib.soap_set_active_spectrum_f32(ctx, int(type_), ptr, dev), "soap_set_active_spectrum_f32")
+    else:
+        _check(_lib.soap_set_active_spectrum(ctx, int(type_), ptr, dev), "soap_set_active_spectrum")
 
 
 def soap_set_stream(ctx, stream) -> None:

@@ -187,3 +187,41 @@ def test_ccf_tables_follow_mask_and_velocity_changes(S, case):
                 rv, ccf = rv_of(d.ctx, m)
                 np.testing.assert_array_equal(ccf, ccf_f)
                 np.testing.assert_array_equal(rv, rv_f)
+
+
+def test_float32_local_spectra_give_the_fp32_path_its_own_results(S, case):
+    """float32 local spectra (host or device, pipelined or not) give the SOAP_FP32 path exactly
+    the results of the float64 ones, which that path rounds to float32 anyway; the FP64 path
+    refuses to run on them until float64 spectra are set again."""
+    c = case
+    lo, step, nv = _grid(c)
+    q32, a32 = c.quiet.astype(np.float32), c.active[synth.SPOT].astype(np.float32)
+    spec_ref, rv_ref = _separate(S, c, c.quiet, c.active[synth.SPOT], c.phases, S.SOAP_FP32,
+                                 S.SOAP_EFFECT_TOT)
+    with S.Disk(c.star, _t(c.quiet), {S.SOAP_SPOT: _t(c.active[synth.SPOT])}) as d:
+        for src, pipelined in ((lambda a: _t(a), False), (_pinned, False), (_pinned, True)):
+            S.soap_set_host_async(d.ctx, pipelined)
+            S.soap_set_quiet_spectrum(d.ctx, src(q32))
+            S.soap_set_active_spectrum(d.ctx, S.SOAP_SPOT, src(a32))
+            spec = torch.empty((len(c.phases), c.star.n_px), dtype=torch.float32).pin_memory()
+            rv = torch.empty(len(c.phases), dtype=torch.float64).pin_memory()
+            S.soap_active_rv(d.ctx, c.regions, c.phases, S.SOAP_EFFECT_TOT, S.SOAP_FP32, c.mask_lambda,
+                             c.mask_weight, c.mask_width_kms, lo, step, nv, spec, rv)
+            S.soap_synchronize(d.ctx)
+            np.testing.assert_array_equal(spec.numpy(), spec_ref)
+            np.testing.assert_array_equal(rv.numpy(), rv_ref)
+        S.soap_set_host_async(d.ctx, False)
+        out64 = torch.empty((1, len(c.phases), c.star.n_px), dtype=torch.float64, device=DEV)
+        with pytest.raises(S.SoapError):
+            S.soap_active_phases(d.ctx, c.regions, c.phases, S.SOAP_EFFECT_TOT, S.SOAP_FP64, out64)
+        with pytest.raises(S.SoapError):
+            S.soap_quiet_spectrum(d.ctx, S.SOAP_FORM_TOEPLITZ, S.SOAP_FP64,
+                                  torch.empty(c.star.n_px, dtype=torch.float64, device=DEV))
+        S.soap_set_quiet_spectrum(d.ctx, _t(c.quiet))
+        with pytest.raises(S.SoapError):                  # the spot spectrum is still float32
+            S.soap_active_phases(d.ctx, c.regions, c.phases, S.SOAP_EFFECT_TOT, S.SOAP_FP64, out64)
+        S.soap_set_active_spectrum(d.ctx, S.SOAP_SPOT, _t(c.active[synth.SPOT]))
+        S.soap_active_phases(d.ctx, c.regions, c.phases, S.SOAP_EFFECT_TOT, S.SOAP_FP64, out64)
+        torch.cuda.synchronize()
+    ref64, _ = _separate(S, c, c.quiet, c.active[synth.SPOT], c.phases, S.SOAP_FP64, S.SOAP_EFFECT_TOT)
+    np.testing.assert_array_equal(out64[0].cpu().numpy(), ref64)
