@@ -157,10 +157,15 @@ def run_ours(args):
     ctx = S.soap_init_star(st, q_dev, stream=stream)
     S.soap_set_active_spectrum(ctx, S.SOAP_SPOT, a_dev)
 
-    def step(prec, out, rv, q=q_dev, a=a_dev):
+    # the FP32 path reads float32 local spectra (bit-identical results to float64 ones rounded
+    # by the library); the FP64 path gets float64 ones
+    q_dev32, a_dev32 = q_dev.float(), a_dev.float()
+
+    def step(prec, out, rv):
+        f32 = prec == S.SOAP_FP32
         S.soap_update_star(ctx, st)
-        S.soap_set_quiet_spectrum(ctx, q)
-        S.soap_set_active_spectrum(ctx, S.SOAP_SPOT, a)
+        S.soap_set_quiet_spectrum(ctx, q_dev32 if f32 else q_dev)
+        S.soap_set_active_spectrum(ctx, S.SOAP_SPOT, a_dev32 if f32 else a_dev)
         S.soap_active_phases(ctx, case.regions, case.phases, S.SOAP_EFFECT_TOT, prec, out)
         S.soap_rv_ccf(ctx, out[0], case.mask_lambda, case.mask_weight, case.mask_width_kms,
                       lo, vstep, nv, rv)
@@ -302,7 +307,7 @@ def run_ours(args):
            "data": "synthetic (seeded 20k-line spectra, random-init regions)",
            "config": {"workload": case.name, "grid": st.grid_n, "n_px": n_px, "n_mu": n_mu,
                       "phases_per_step": P, "effects": "total (Eq. 3)",
-                      "precision": "FP32 contraction, FP64 positions/weights/fit",
+                      "precision": "FP32 local spectra, contraction and CCF; FP64 positions and weights; fit FP32 LM + FP64 Newton",
                       "l2": "flushed between timed steps (256 MB write)",
                       "parallelism": f"replicas{world}"},
            "rv_err_cms_vs_fp64": rv_err,

@@ -212,7 +212,7 @@ static void free_ctx_memory(soap_ctx* c) {
     void* ptrs[] = {c->cell_I, c->cell_w, c->cell_mu, c->cell_j, c->cell_bin, c->cell_mu32,
                     c->cell_k0, c->cell_k1, c->flags, c->q64,
                     c->q32, c->a64[0], c->a32[0], c->a64[1], c->a32[1], c->kq_fixed,
-                    c->sum_I_fixed, c->qtoff, c->qgstart, c->qc64, c->qc32, c->geo_counter};
+                    c->sum_I_fixed, c->qtoff, c->qgstart, c->qc64, c->qc32, c->geo_counter, c->cell_x};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     DevBuf* bufs[] = {&c->stage_in, &c->fq, &c->contrast, &c->kphase, &c->jobs, &c->coefs, &c->job_counters,
@@ -423,6 +423,7 @@ soap_status soap_init_star(const soap_star_desc* s, const double* quiet_local, i
     ALLOC(c->qc64, (size_t)c->n_mu * SOAP_MAX_TAPS * sizeof(double));
     ALLOC(c->qc32, (size_t)c->n_mu * SOAP_MAX_TAPS * sizeof(float));
     ALLOC(c->geo_counter, sizeof(int));
+    ALLOC(c->cell_x, (size_t)c->N * sizeof(double));
 #undef ALLOC
     if (e != cudaSuccess) {
         set_error("device allocation failed: %s", cudaGetErrorString(e));
@@ -432,6 +433,14 @@ soap_status soap_init_star(const soap_star_desc* s, const double* quiet_local, i
     }
     st = SOAP_OK;
     if (cudaMemsetAsync(c->flags, 0, sizeof(unsigned int), c->stream) != cudaSuccess) st = SOAP_ECUDA;
+    {
+        // cell centres (2 i + 1 - N) / N, IEEE-divided here once instead of in every cell
+        std::vector<double> xs((size_t)c->N);
+        for (int i = 0; i < c->N; i++) xs[(size_t)i] = (double)(2 * i + 1 - c->N) / (double)c->N;
+        if (st == SOAP_OK &&
+            cudaMemcpy(c->cell_x, xs.data(), xs.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+            st = SOAP_ECUDA;
+    }
     if (st == SOAP_OK) st = geometry_init(c);
     if (st == SOAP_OK) st = upload_spectra(c, quiet_local, quiet_on_device, 0, c->q64, c->q32, 0);
     c->q64_ok = st == SOAP_OK;

@@ -179,6 +179,9 @@ static soap_status launch_contract(soap_ctx* c, int n_blocks, int G, int max_tap
 #ifndef SOAP_R32
 #define SOAP_R32 4
 #endif
+#ifndef SOAP_QR32
+#define SOAP_QR32 2
+#endif
 constexpr int kPB64 = 4, kR64 = 2, kT64 = 128;
 constexpr int kPB32 = SOAP_PB32, kR32 = SOAP_R32, kT32 = 128;
 
@@ -210,7 +213,7 @@ soap_status toeplitz_quiet(soap_ctx* c, int precision, void* dst) {
     if (precision == SOAP_FP64)
         return launch_contract<double, 1, 1, 128>(c, nbk, G, mt, c->qtoff, c->qgstart, c->qc64, ct, nullptr,
                                                  nullptr, 1, el, 1, (double*)dst, c->q64, nullptr, nullptr);
-    return launch_contract<float, 1, 1, 128>(c, nbk, G, mt, c->qtoff, c->qgstart, c->qc32, ct, nullptr,
+    return launch_contract<float, 1, SOAP_QR32, 128>(c, nbk, G, mt, c->qtoff, c->qgstart, c->qc32, ct, nullptr,
                                             nullptr, 1, el, 1, (float*)dst, c->q32, nullptr, nullptr);
 }
 

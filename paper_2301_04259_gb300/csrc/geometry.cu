@@ -57,20 +57,19 @@ k_geometry(int N, double vsini, double sin_i, double cos_i, double alpha, double
            double* cell_I, double* cell_w, double* cell_mu, float* cell_mu32, int32_t* cell_j,
            int32_t* cell_bin, long long* cell_k0, long long* cell_k1, long long* kq_fixed,
            long long* sum2, long long* qtoff, int* qgstart, double* qc64, float* qc32, int q_max_taps,
-           int64_t row_len, int64_t pad, int fx_bits, int* counter, unsigned int* flags) {
+           int64_t row_len, int64_t pad, int fx_bits, int* counter, unsigned int* flags,
+           const double* __restrict__ cell_x, double area) {
     extern __shared__ long long hist[];                  // [n_mu][n_taps]
-    __shared__ double sy;
     const int nb = n_mu * n_taps;
     for (int t = threadIdx.x; t < nb; t += blockDim.x) hist[t] = 0;
     const int j = blockIdx.y;
-    if (threadIdx.x == 0) sy = (double)(2 * j + 1 - N) / (double)N;
     __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long sumI = 0, cnt = 0;
     if (i < N) {
         const int64_t c = (int64_t)j * N + i;
-        const double x = (double)(2 * i + 1 - N) / (double)N;
-        const double y = sy;
+        const double x = cell_x[i];                                        // (2 i + 1 - N) / N
+        const double y = cell_x[j];
         const double r2 = __dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y));
         if (!(r2 < 1.0)) {
             cell_I[c] = 0.0; cell_w[c] = 0.0; cell_mu[c] = 0.0; cell_mu32[c] = 0.0f;
@@ -78,7 +77,6 @@ k_geometry(int N, double vsini, double sin_i, double cos_i, double alpha, double
         } else {
             const double mu = __dsqrt_rn(__dsub_rn(1.0, r2));
             const int best = nearest_mu(mu, n_mu, mus, mu_sorted);
-            const double area = (2.0 / (double)N) * (2.0 / (double)N);
             const double om = 1.0 - mu;
             const double I = area * (1.0 - u1 * om - u2 * om * om);      // quadratic limb darkening
             const double slat = y * sin_i + mu * cos_i;                    // sin(latitude) of the cell
@@ -134,19 +132,32 @@ k_geometry(int N, double vsini, double sin_i, double cos_i, double alpha, double
 // Replicate-padded rows: dst[r][pad + n] = src[r][n]; left pad = src[r][0]; right pad =
 // src[r][n_px-1].  Reading dst at pad + m - k for any tap k reproduces the clamped index
 // min(max(m - k, 0), n_px - 1) of the interpolation's edge rule.
+// Eight consecutive outputs per thread and step (more loads in flight per thread): 16-byte
+// stores (rows start 256-byte aligned: row_len is a multiple of 32).
+constexpr int kPadE = 8;
+
 __global__ void k_pad_rows(const double* __restrict__ src, int64_t n_px, int64_t pad, int64_t row_len,
                            double* __restrict__ dst64, float* __restrict__ dst32) {
     const int64_t r = blockIdx.y;
     const double* s = src + r * n_px;
-    double* d64 = dst64 + r * row_len;
-    float* d32 = dst32 + r * row_len;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < row_len;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        int64_t n = e - pad;
-        n = n < 0 ? 0 : (n >= n_px ? n_px - 1 : n);
-        double v = __ldg(s + n);
-        d64[e] = v;
-        d32[e] = (float)v;
+    double2* d64 = reinterpret_cast<double2*>(dst64 + r * row_len);
+    float4* d32 = reinterpret_cast<float4*>(dst32 + r * row_len);
+    const int64_t nq = row_len / kPadE;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        double v[kPadE];
+#pragma unroll
+        for (int t = 0; t < kPadE; t++) {
+            int64_t n = kPadE * q + t - pad;
+            n = n < 0 ? 0 : (n >= n_px ? n_px - 1 : n);
+            v[t] = __ldg(s + n);
+        }
+#pragma unroll
+        for (int t = 0; t < kPadE / 2; t++) d64[(kPadE / 2) * q + t] = make_double2(v[2 * t], v[2 * t + 1]);
+#pragma unroll
+        for (int t = 0; t < kPadE / 4; t++)
+            d32[(kPadE / 4) * q + t] = make_float4((float)v[4 * t], (float)v[4 * t + 1], (float)v[4 * t + 2],
+                                                   (float)v[4 * t + 3]);
     }
 }
 
@@ -155,12 +166,20 @@ __global__ void k_pad_rows32(const float* __restrict__ src, int64_t n_px, int64_
                              float* __restrict__ dst32) {
     const int64_t r = blockIdx.y;
     const float* s = src + r * n_px;
-    float* d32 = dst32 + r * row_len;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < row_len;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        int64_t n = e - pad;
-        n = n < 0 ? 0 : (n >= n_px ? n_px - 1 : n);
-        d32[e] = __ldg(s + n);
+    float4* d32 = reinterpret_cast<float4*>(dst32 + r * row_len);
+    const int64_t nq = row_len / kPadE;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        float v[kPadE];
+#pragma unroll
+        for (int t = 0; t < kPadE; t++) {
+            int64_t n = kPadE * q + t - pad;
+            n = n < 0 ? 0 : (n >= n_px ? n_px - 1 : n);
+            v[t] = __ldg(s + n);
+        }
+#pragma unroll
+        for (int t = 0; t < kPadE / 4; t++)
+            d32[(kPadE / 4) * q + t] = make_float4(v[4 * t], v[4 * t + 1], v[4 * t + 2], v[4 * t + 3]);
     }
 }
 
@@ -172,7 +191,7 @@ static int grid_for(int64_t n, int threads, int cap = 152 * 16) {
 }
 
 soap_status pad_rows(soap_ctx* c, const double* src, double* dst64, float* dst32, int rows) {
-    dim3 grid((unsigned)grid_for(c->row_len, 256, 64), (unsigned)rows);
+    dim3 grid((unsigned)grid_for(c->row_len / kPadE, 256, 64), (unsigned)rows);
     SOAP_TIMED(c, SOAP_TIMER_PAD_ROWS,
                k_pad_rows<<<grid, 256, 0, c->stream>>>(src, c->n_px, c->pad, c->row_len, dst64, dst32);
                SOAP_LAUNCHED(c));
@@ -180,7 +199,7 @@ soap_status pad_rows(soap_ctx* c, const double* src, double* dst64, float* dst32
 }
 
 soap_status pad_rows32(soap_ctx* c, const float* src, float* dst32, int rows) {
-    dim3 grid((unsigned)grid_for(c->row_len, 256, 64), (unsigned)rows);
+    dim3 grid((unsigned)grid_for(c->row_len / kPadE, 256, 64), (unsigned)rows);
     SOAP_TIMED(c, SOAP_TIMER_PAD_ROWS,
                k_pad_rows32<<<grid, 256, 0, c->stream>>>(src, c->n_px, c->pad, c->row_len, dst32);
                SOAP_LAUNCHED(c));
@@ -207,7 +226,8 @@ soap_status geometry_init(soap_ctx* c) {
         1.0 / c->delta, c->delta, 1.0 / std::expm1(c->delta), c->n_mu, mus, c->mu_sorted, c->tap_min,
         tap_max, c->n_taps, scale, c->cell_I, c->cell_w, c->cell_mu, c->cell_mu32, c->cell_j,
         c->cell_bin, c->cell_k0, c->cell_k1, c->kq_fixed, c->sum_I_fixed, c->qtoff, c->qgstart, c->qc64,
-        c->qc32, c->n_mu * SOAP_MAX_TAPS, c->row_len, c->pad, c->fx_bits, c->geo_counter, c->flags);
+        c->qc32, c->n_mu * SOAP_MAX_TAPS, c->row_len, c->pad, c->fx_bits, c->geo_counter, c->flags,
+        c->cell_x, (2.0 / (double)c->N) * (2.0 / (double)c->N));
     SOAP_LAUNCHED(c);
     if (c->profiling) timer_end(c, SOAP_TIMER_GEOMETRY, tb);
     return SOAP_OK;

@@ -156,6 +156,7 @@ struct soap_ctx {
     double* qc64 = nullptr;
     float* qc32 = nullptr;
     int* geo_counter = nullptr;
+    double* cell_x = nullptr;          // [N] (2 i + 1 - N) / N, the cell centres' x (and y)
 
     // scratch (grow-only)
     soap::DevBuf stage_in;      // host -> device staging of spectra
