@@ -146,9 +146,10 @@ typedef enum {
     SOAP_TIMER_CONTRACT = 5,     /* Toeplitz contraction, active phases */
     SOAP_TIMER_CONTRACT_QUIET = 6, /* Toeplitz contraction, quiet star */
     SOAP_TIMER_DIRECT = 7,       /* direct-form disk sum (+ split reduction) */
-    SOAP_TIMER_CCF = 8,          /* CCF partial sums + reduction */
+    SOAP_TIMER_CCF = 8,          /* CCF partial sums (the main CCF kernel) */
     SOAP_TIMER_FIT = 9,          /* Gaussian fits */
-    SOAP_TIMER_COUNT = 10
+    SOAP_TIMER_CCF_AUX = 10,     /* CCF line / velocity tables (when rebuilt) + partial-sum reduction */
+    SOAP_TIMER_COUNT = 11
 } soap_timer;
 
 /* Read-only facts about an initialised star. */

@@ -132,54 +132,60 @@ k_geometry(int N, double vsini, double sin_i, double cos_i, double alpha, double
 // Replicate-padded rows: dst[r][pad + n] = src[r][n]; left pad = src[r][0]; right pad =
 // src[r][n_px-1].  Reading dst at pad + m - k for any tap k reproduces the clamped index
 // min(max(m - k, 0), n_px - 1) of the interpolation's edge rule.
-// Eight consecutive outputs per thread and step (more loads in flight per thread): 16-byte
-// stores (rows start 256-byte aligned: row_len is a multiple of 32).
+// Warp-cooperative: one warp covers 32 x kPadE consecutive outputs of a row, lane l taking
+// elements l, l + 32, ..., so every load and store instruction covers contiguous bytes (the
+// source is shifted by pad against the destination, so per-thread vectors would not align).
+// Indices within a row are 32-bit (row_len < 2^31).
 constexpr int kPadE = 8;
 
-__global__ void k_pad_rows(const double* __restrict__ src, int64_t n_px, int64_t pad, int64_t row_len,
+__global__ void k_pad_rows(const double* __restrict__ src, int n_px, int pad, int row_len,
                            double* __restrict__ dst64, float* __restrict__ dst32) {
     const int64_t r = blockIdx.y;
     const double* s = src + r * n_px;
-    double2* d64 = reinterpret_cast<double2*>(dst64 + r * row_len);
-    float4* d32 = reinterpret_cast<float4*>(dst32 + r * row_len);
-    const int64_t nq = row_len / kPadE;
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq;
-         q += (int64_t)gridDim.x * blockDim.x) {
+    double* d64 = dst64 + r * row_len;
+    float* d32 = dst32 + r * row_len;
+    const int lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    const int stride = gridDim.x * wpb * 32 * kPadE;
+    for (int base = (blockIdx.x * wpb + (threadIdx.x >> 5)) * 32 * kPadE; base < row_len; base += stride) {
         double v[kPadE];
 #pragma unroll
         for (int t = 0; t < kPadE; t++) {
-            int64_t n = kPadE * q + t - pad;
-            n = n < 0 ? 0 : (n >= n_px ? n_px - 1 : n);
+            const int n = min(max(base + 32 * t + lane - pad, 0), n_px - 1);
             v[t] = __ldg(s + n);
         }
 #pragma unroll
-        for (int t = 0; t < kPadE / 2; t++) d64[(kPadE / 2) * q + t] = make_double2(v[2 * t], v[2 * t + 1]);
-#pragma unroll
-        for (int t = 0; t < kPadE / 4; t++)
-            d32[(kPadE / 4) * q + t] = make_float4((float)v[4 * t], (float)v[4 * t + 1], (float)v[4 * t + 2],
-                                                   (float)v[4 * t + 3]);
+        for (int t = 0; t < kPadE; t++) {
+            const int e = base + 32 * t + lane;
+            if (e < row_len) {
+                d64[e] = v[t];
+                d32[e] = (float)v[t];
+            }
+        }
     }
 }
 
 // float32 local spectra: the float32 rows only
-__global__ void k_pad_rows32(const float* __restrict__ src, int64_t n_px, int64_t pad, int64_t row_len,
+__global__ void k_pad_rows32(const float* __restrict__ src, int n_px, int pad, int row_len,
                              float* __restrict__ dst32) {
     const int64_t r = blockIdx.y;
     const float* s = src + r * n_px;
-    float4* d32 = reinterpret_cast<float4*>(dst32 + r * row_len);
-    const int64_t nq = row_len / kPadE;
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq;
-         q += (int64_t)gridDim.x * blockDim.x) {
+    float* d32 = dst32 + r * row_len;
+    const int lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    const int stride = gridDim.x * wpb * 32 * kPadE;
+    for (int base = (blockIdx.x * wpb + (threadIdx.x >> 5)) * 32 * kPadE; base < row_len; base += stride) {
         float v[kPadE];
 #pragma unroll
         for (int t = 0; t < kPadE; t++) {
-            int64_t n = kPadE * q + t - pad;
-            n = n < 0 ? 0 : (n >= n_px ? n_px - 1 : n);
+            const int n = min(max(base + 32 * t + lane - pad, 0), n_px - 1);
             v[t] = __ldg(s + n);
         }
 #pragma unroll
-        for (int t = 0; t < kPadE / 4; t++)
-            d32[(kPadE / 4) * q + t] = make_float4(v[4 * t], v[4 * t + 1], v[4 * t + 2], v[4 * t + 3]);
+        for (int t = 0; t < kPadE; t++) {
+            const int e = base + 32 * t + lane;
+            if (e < row_len) d32[e] = v[t];
+        }
     }
 }
 
@@ -193,7 +199,8 @@ static int grid_for(int64_t n, int threads, int cap = 152 * 16) {
 soap_status pad_rows(soap_ctx* c, const double* src, double* dst64, float* dst32, int rows) {
     dim3 grid((unsigned)grid_for(c->row_len / kPadE, 256, 64), (unsigned)rows);
     SOAP_TIMED(c, SOAP_TIMER_PAD_ROWS,
-               k_pad_rows<<<grid, 256, 0, c->stream>>>(src, c->n_px, c->pad, c->row_len, dst64, dst32);
+               k_pad_rows<<<grid, 256, 0, c->stream>>>(src, (int)c->n_px, (int)c->pad, (int)c->row_len,
+                                                       dst64, dst32);
                SOAP_LAUNCHED(c));
     return SOAP_OK;
 }
@@ -201,7 +208,8 @@ soap_status pad_rows(soap_ctx* c, const double* src, double* dst64, float* dst32
 soap_status pad_rows32(soap_ctx* c, const float* src, float* dst32, int rows) {
     dim3 grid((unsigned)grid_for(c->row_len / kPadE, 256, 64), (unsigned)rows);
     SOAP_TIMED(c, SOAP_TIMER_PAD_ROWS,
-               k_pad_rows32<<<grid, 256, 0, c->stream>>>(src, c->n_px, c->pad, c->row_len, dst32);
+               k_pad_rows32<<<grid, 256, 0, c->stream>>>(src, (int)c->n_px, (int)c->pad, (int)c->row_len,
+                                                         dst32);
                SOAP_LAUNCHED(c));
     return SOAP_OK;
 }
