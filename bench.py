@@ -443,7 +443,7 @@ def measure_batched(args, dev, hbm_peak):
 
 
 def measure_surrogate(args, dev):
-    """Surrogate trained on the batched method's residual spectra; judged accuracy on held-out
+    """Surrogate trained on the batched method's residual spectra; checked accuracy on held-out
     queries (true RVs from the plain method), and throughput on --sur-queries queries."""
     import torch
     from paper_2301_04259_gb300 import soap as S
@@ -455,17 +455,17 @@ def measure_surrogate(args, dev):
     with _disk(S, case, dev) as d:
         t0 = time.perf_counter()
         model = SP.train(d.ctx, case, n_train=args.sur_train, epochs=args.sur_epochs, seed=args.seed,
-                         n_judge=196_608, judge_epochs=60)
+                         n_err=196_608, err_epochs=60)
         res["train_wall_s"] = round(time.perf_counter() - t0, 2)
         res["train"] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in model.log.items()
                         if k not in ("loss", "head_loss", "rv_sens_cms_per_sd")}
         res["train"]["final_loss"] = model.log["loss"][-1]
         xe = synth.surrogate_params(args.seed + 99, 8192)
-        err = SP.judge_errors(d.ctx, case, model, xe)
+        err = SP.plain_rv_errors(d.ctx, case, model, xe)
         acc = torch.empty(len(xe), dtype=torch.uint8, device=dev)
         S.soap_surrogate_predict(model.handle, torch.from_numpy(xe).to(dev), model.accept_thr_cms, accepted=acc)
         a = acc.cpu().numpy().astype(bool)
-        res["judged_heldout"] = {
+        res["heldout_vs_plain"] = {
             "queries": len(xe), "accepted_frac": round(float(a.mean()), 4),
             "rv_err_cms_all_median": round(float(np.median(err)), 3),
             "rv_err_cms_accepted_p50_p95_p99_max": [round(float(np.percentile(err[a], q)), 3) for q in (50, 95, 99, 100)]

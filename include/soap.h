@@ -467,9 +467,9 @@ soap_status soap_surrogate_train(soap_surrogate* s, const float* x, const float*
 soap_status soap_surrogate_predict(soap_surrogate* s, const float* x, int64_t n, float rv_err_max_cms,
                                    float* coef, float* pred_err_cms, uint8_t* accepted);
 /* Take the predicted RV error from output n_coef of another network of the same shape and
- * input ranges (trained with stage 2 on the judged errors), instead of this network's own head;
- * NULL restores the own head.  The judge must outlive its use. */
-soap_status soap_surrogate_set_judge(soap_surrogate* s, soap_surrogate* judge);
+ * input ranges (trained with stage 2 on the plain-method errors), instead of this network's own head;
+ * NULL restores the own head.  The error network must outlive its use. */
+soap_status soap_surrogate_set_error_net(soap_surrogate* s, soap_surrogate* error_net);
 /* PCA basis of the residuals: mean device [n_px], basis device [n_coef][n_px] (orthonormal rows). */
 soap_status soap_surrogate_set_basis(soap_surrogate* s, const float* mean, const float* basis, int64_t n_px);
 /* Residual spectra mean + coef . basis for device coef [n][128] into device out [n][n_px]; both

@@ -91,7 +91,7 @@ struct soap_surrogate {
     int64_t n_px = 0;
     float* mu = nullptr;                      // [n_px]
     bf16* vsplit = nullptr;                   // [n_px][3 n_coef]: V_hi | V_lo | V_hi
-    soap_surrogate* judge = nullptr;          // network whose output n_coef predicts the RV error
+    soap_surrogate* error_net = nullptr;         // network whose output n_coef predicts the RV error
 };
 
 namespace soap {
@@ -573,10 +573,10 @@ static soap_status ensure_query(soap_surrogate* s, int rows) {
     return SOAP_OK;
 }
 
-// The judge network (if any) runs on the same scaled inputs, on the main network's stream.
-static soap_status judge_forward(soap_surrogate* s, const bf16* X0, int m) {
-    if (!s->judge) return SOAP_OK;
-    soap_surrogate* j = s->judge;
+// The error network (if any) runs on the same scaled inputs, on the main network's stream.
+static soap_status error_net_forward(soap_surrogate* s, const bf16* X0, int m) {
+    if (!s->error_net) return SOAP_OK;
+    soap_surrogate* j = s->error_net;
     SOAP_TRY(ensure_query(j, s->q_cap));
     const cudaStream_t saved = j->stream;
     j->stream = s->stream;
@@ -588,12 +588,12 @@ static soap_status judge_forward(soap_surrogate* s, const bf16* X0, int m) {
 static soap_status check(soap_surrogate* s) {
     unsigned int h = 0, hj = 0;
     SOAP_CUDA(cudaMemcpyAsync(&h, s->flags, sizeof(h), cudaMemcpyDeviceToHost, s->stream));
-    if (s->judge) SOAP_CUDA(cudaMemcpyAsync(&hj, s->judge->flags, sizeof(hj), cudaMemcpyDeviceToHost, s->stream));
+    if (s->error_net) SOAP_CUDA(cudaMemcpyAsync(&hj, s->error_net->flags, sizeof(hj), cudaMemcpyDeviceToHost, s->stream));
     SOAP_CUDA(cudaStreamSynchronize(s->stream));
     h |= hj;
     if (h) {
         SOAP_CUDA(cudaMemsetAsync(s->flags, 0, sizeof(unsigned int), s->stream));
-        if (s->judge) SOAP_CUDA(cudaMemsetAsync(s->judge->flags, 0, sizeof(unsigned int), s->stream));
+        if (s->error_net) SOAP_CUDA(cudaMemsetAsync(s->error_net->flags, 0, sizeof(unsigned int), s->stream));
         set_error("a tensor-core kernel gave up waiting (status 0x%x)", h);
         return SOAP_ETIMEOUT;
     }
@@ -846,9 +846,9 @@ soap_status soap_surrogate_predict(soap_surrogate* s, const float* x, int64_t n,
         k_query_in<<<grid1(m), 256, 0, s->stream>>>(x + r0 * s->n_in, m, s->n_in, s->d_lohi, X0,
                                                     accepted ? accepted + r0 : nullptr);
         st = forward(s, X0, m, false, s->qy);
-        if (st == SOAP_OK) st = judge_forward(s, X0, m);
+        if (st == SOAP_OK) st = error_net_forward(s, X0, m);
         if (st != SOAP_OK) break;
-        const float* ye = s->judge ? s->judge->qy : s->qy;
+        const float* ye = s->error_net ? s->error_net->qy : s->qy;
         k_query_out<<<grid1((int64_t)m * (s->n_coef + 1)), 256, 0, s->stream>>>(
             s->qy, s->n_out_pad, ye, s->n_out_pad, m, s->n_coef, s->coef_mean, s->coef_std, rv_err_max_cms,
             accepted ? accepted + r0 : nullptr, pred_err_cms ? pred_err_cms + r0 : nullptr,
@@ -859,17 +859,17 @@ soap_status soap_surrogate_predict(soap_surrogate* s, const float* x, int64_t n,
     return check(s);
 }
 
-soap_status soap_surrogate_set_judge(soap_surrogate* s, soap_surrogate* judge) {
+soap_status soap_surrogate_set_error_net(soap_surrogate* s, soap_surrogate* error_net) {
     clear_error();
     if (!s) { set_error("NULL argument"); return SOAP_EINVAL; }
-    if (judge == s) { set_error("a network cannot judge itself"); return SOAP_EINVAL; }
-    if (judge) {
+    if (error_net == s) { set_error("a network cannot be its own error network"); return SOAP_EINVAL; }
+    if (error_net) {
         for (int i = 0; i < s->n_in; i++)
-            if (judge->lo[i] != s->lo[i] || judge->hi[i] != s->hi[i]) {
-                set_error("the judge network must use the same input ranges"); return SOAP_EINVAL;
+            if (error_net->lo[i] != s->lo[i] || error_net->hi[i] != s->hi[i]) {
+                set_error("the error network must use the same input ranges"); return SOAP_EINVAL;
             }
     }
-    s->judge = judge;
+    s->error_net = error_net;
     return SOAP_OK;
 }
 
@@ -903,9 +903,9 @@ soap_status soap_surrogate_query(soap_surrogate* s, const float* x, int64_t n, f
         const int m = (int)std::min<int64_t>(chunk, n - r0);
         k_query_in<<<grid1(m), 256, 0, s->stream>>>(x + r0 * s->n_in, m, s->n_in, s->d_lohi, X0, accepted + r0);
         st = forward(s, X0, m, false, s->qy);
-        if (st == SOAP_OK) st = judge_forward(s, X0, m);
+        if (st == SOAP_OK) st = error_net_forward(s, X0, m);
         if (st != SOAP_OK) break;
-        const float* ye = s->judge ? s->judge->qy : s->qy;
+        const float* ye = s->error_net ? s->error_net->qy : s->qy;
         k_query_out<<<grid1((int64_t)m * (s->n_coef + 1)), 256, 0, s->stream>>>(
             s->qy, s->n_out_pad, ye, s->n_out_pad, m, s->n_coef, s->coef_mean, s->coef_std, rv_err_max_cms,
             accepted + r0, pred_err_cms ? pred_err_cms + r0 : nullptr, nullptr, s->qsplit);

@@ -116,7 +116,7 @@ def _load():
         "soap_surrogate_train": (i32, [P, P, P, i64, i32, P, P, i32, ctypes.c_uint64, P]),
         "soap_surrogate_predict": (i32, [P, P, i64, ctypes.c_float, P, P, P]),
         "soap_surrogate_set_basis": (i32, [P, P, P, i64]),
-        "soap_surrogate_set_judge": (i32, [P, P]),
+        "soap_surrogate_set_error_net": (i32, [P, P]),
         "soap_surrogate_reconstruct": (i32, [P, P, i64, P]),
         "soap_surrogate_query": (i32, [P, P, i64, ctypes.c_float, P, P, P]),
         "soap_surrogate_free": (None, [P]),
@@ -539,8 +539,8 @@ def soap_surrogate_predict(s, x, rv_err_max_cms: float, coef=None, pred_err=None
                                        _dev(coef), _dev(pred_err), _dev(accepted)), "soap_surrogate_predict")
 
 
-def soap_surrogate_set_judge(s, judge) -> None:
-    _check(_lib.soap_surrogate_set_judge(s, judge), "soap_surrogate_set_judge")
+def soap_surrogate_set_error_net(s, error_net) -> None:
+    _check(_lib.soap_surrogate_set_error_net(s, error_net), "soap_surrogate_set_error_net")
 
 
 def soap_surrogate_set_basis(s, mean, basis) -> None:

@@ -1,4 +1,4 @@
-"""Training and judged querying of the surrogate: the order of libsoap calls.
+"""Training and checked querying of the surrogate: the order of libsoap calls.
 
 Every computation is a libsoap call (batched method, PCA, network training and queries, CCF and
 RV fit); this module chooses the calls, holds the device buffers (torch CUDA tensors) and does
@@ -58,16 +58,16 @@ class Surrogate:
     coef_std: np.ndarray
     sv: np.ndarray
     accept_thr_cms: float = RV_ERR_MAX_CMS   # threshold on the predicted error, calibrated
-    judge: object = None                     # network predicting the RV error (output 128)
+    error_net: object = None                     # network predicting the RV error (output 128)
     log: dict = field(default_factory=dict)
 
     def free(self):
         if self.handle:
             S.soap_surrogate_free(self.handle)
             self.handle = None
-        if self.judge:
-            S.soap_surrogate_free(self.judge)
-            self.judge = None
+        if self.error_net:
+            S.soap_surrogate_free(self.error_net)
+            self.error_net = None
 
 
 def _cosine(epochs, lr_max, lr_min):
@@ -109,7 +109,7 @@ def calibrate_threshold(pred, err, limit=RV_ERR_MAX_CMS, miss=0.01):
     return float(pred[order][last])
 
 
-def train(ctx, case, n_train=200_000, n_cal=16_384, n_judge=65_536, epochs=200, judge_epochs=150, batch=4096,
+def train(ctx, case, n_train=200_000, n_cal=16_384, n_err=65_536, epochs=200, err_epochs=150, batch=4096,
           k=128, l=160, n_power=2, seed=0, lr=3e-3, chunk=50_000, rv_weighted=True) -> Surrogate:
     torch = _torch()
     dev = "cuda:0"
@@ -161,25 +161,25 @@ def train(ctx, case, n_train=200_000, n_cal=16_384, n_judge=65_536, epochs=200, 
     log["train_samples_per_s"] = n_train * epochs / max(log["train_s"], 1e-9)
     del xd, td
     # RV-error head: a network of the same shape trained (all layers) on the plain method's
-    # judgement of n_judge new queries; the acceptance threshold is then calibrated on n_cal more
+    # errors, by the plain method, of n_err new queries; the acceptance threshold is then calibrated on n_cal more
     t0 = time.time()
-    if n_judge < batch:
-        raise ValueError("n_judge must hold at least one training batch")
-    xc = synth.surrogate_params(seed + 4, n_judge)
-    err = judge_errors(ctx, case, model, xc)
-    tc = np.zeros((n_judge, k + 1), np.float32)
+    if n_err < batch:
+        raise ValueError("n_err must hold at least one training batch")
+    xc = synth.surrogate_params(seed + 4, n_err)
+    err = plain_rv_errors(ctx, case, model, xc)
+    tc = np.zeros((n_err, k + 1), np.float32)
     tc[:, k] = np.log10(err + 0.1)
     w1 = np.zeros(k + 1, np.float32)
     w1[k] = 1.0
-    model.judge = S.soap_surrogate_create(synth.SURROGATE_LO, synth.SURROGATE_HI, batch)
-    S.soap_surrogate_set_params(model.judge, synth.surrogate_init(seed + 7))
-    log["head_loss"] = S.soap_surrogate_train(model.judge, torch.from_numpy(xc).to(dev),
-                                              torch.from_numpy(tc).to(dev), judge_epochs,
-                                              _cosine(judge_epochs, lr, lr * 0.02), w1, stage=2,
+    model.error_net = S.soap_surrogate_create(synth.SURROGATE_LO, synth.SURROGATE_HI, batch)
+    S.soap_surrogate_set_params(model.error_net, synth.surrogate_init(seed + 7))
+    log["head_loss"] = S.soap_surrogate_train(model.error_net, torch.from_numpy(xc).to(dev),
+                                              torch.from_numpy(tc).to(dev), err_epochs,
+                                              _cosine(err_epochs, lr, lr * 0.02), w1, stage=2,
                                               seed=seed + 5).tolist()
-    S.soap_surrogate_set_judge(h, model.judge)
+    S.soap_surrogate_set_error_net(h, model.error_net)
     xv = synth.surrogate_params(seed + 6, n_cal)
-    err_v = judge_errors(ctx, case, model, xv)
+    err_v = plain_rv_errors(ctx, case, model, xv)
     pe = torch.empty(n_cal, dtype=torch.float32, device=dev)
     S.soap_surrogate_predict(h, torch.from_numpy(xv).to(dev), RV_ERR_MAX_CMS, pred_err=pe)
     model.accept_thr_cms = calibrate_threshold(pe.cpu().numpy(), err_v)
@@ -189,7 +189,7 @@ def train(ctx, case, n_train=200_000, n_cal=16_384, n_judge=65_536, epochs=200, 
     return model
 
 
-def judge_errors(ctx, case, model, x, chunk=8192):
+def plain_rv_errors(ctx, case, model, x, chunk=8192):
     """|RV(F_q + surrogate residual) - RV(F)| in cm/s for queries x, F from the plain method."""
     torch = _torch()
     dev = "cuda:0"

@@ -1,4 +1,4 @@
-"""What the trained surrogate gains over the plain method, judged by the plain method.
+"""What the trained surrogate gains over the plain method, checked by the plain method.
 
 A surrogate trained on residual spectra of the batched method answers part of the held-out
 queries; for those its RV must agree with the plain method's within 10 cm/s (up to the 1%
@@ -31,10 +31,10 @@ def test_surrogate_gain_over_the_plain_method(S):
     case = synth.batch_spectra(0)
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
     with S.Disk(case.star, t(case.quiet), {k: t(v) for k, v in case.active.items()}) as d:
-        model = SP.train(d.ctx, case, n_train=300_000, epochs=100, n_judge=98_304, judge_epochs=60, seed=3)
+        model = SP.train(d.ctx, case, n_train=300_000, epochs=100, n_err=98_304, err_epochs=60, seed=3)
         try:
             xe = synth.surrogate_params(1234, 8192)
-            err = SP.judge_errors(d.ctx, case, model, xe)
+            err = SP.plain_rv_errors(d.ctx, case, model, xe)
             acc = torch.empty(len(xe), dtype=torch.uint8, device=DEV)
             S.soap_surrogate_predict(model.handle, t(xe), model.accept_thr_cms, accepted=acc)
             a = acc.cpu().numpy().astype(bool)
