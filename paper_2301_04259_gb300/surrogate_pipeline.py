@@ -96,14 +96,19 @@ def rv_sensitivity(ctx, case, mean, basis, scale, vsini=5.5, incl=60.0):
     return (rv[:k] - rv[k]) / eps
 
 
-def calibrate_threshold(pred, err, limit=RV_ERR_MAX_CMS, miss=0.01):
+def calibrate_threshold(pred, err, limit=RV_ERR_MAX_CMS, miss=0.01, z=1.645):
     """Largest threshold on the predicted error such that, among the calibration queries it
-    accepts, at most a fraction `miss` has a true error above `limit`."""
+    accepts, the fraction with a true error above `limit` is at most `miss` with one-sided
+    confidence ~95%: the Wilson score upper bound (z = 1.645) of the observed fraction must not
+    exceed `miss`.  (Taking the largest threshold whose observed fraction is <= miss picks the
+    calibration set's luckiest point; new queries then exceed `miss` about half the time.)"""
     order = np.argsort(pred)
-    bad = np.cumsum(err[order] > limit)
-    n_acc = np.arange(1, len(order) + 1)
-    ok = bad <= miss * n_acc
-    if not ok[0]:
+    bad = np.cumsum(err[order] > limit).astype(np.float64)
+    n = np.arange(1, len(order) + 1, dtype=np.float64)
+    p = bad / n
+    ub = (p + z * z / (2 * n) + z * np.sqrt(p * (1 - p) / n + z * z / (4 * n * n))) / (1 + z * z / n)
+    ok = ub <= miss
+    if not ok.any():
         return 0.0
     last = np.flatnonzero(ok)[-1]
     return float(pred[order][last])

@@ -88,15 +88,29 @@ def test_vectorised_surrogate_layout_matches_the_per_query_one():
 
 
 def test_acceptance_threshold_calibration():
+    """The threshold must hold the miss rate on NEW queries: over 40 replications (calibrate on
+    5000 queries, check on 5000 fresh ones) the fresh miss fraction exceeds 1% rarely, while the
+    rule 'largest threshold whose calibration miss fraction is <= 1%' exceeds it about half the
+    time; the calibration set itself stays within 1%."""
     from paper_2301_04259_gb300.surrogate_pipeline import calibrate_threshold
     rng = np.random.default_rng(0)
-    err = rng.lognormal(1.5, 1.0, 5000)
-    pred = err * rng.lognormal(0, 0.3, 5000)            # an informative predictor
-    thr = calibrate_threshold(pred, err, limit=10.0, miss=0.01)
-    acc = pred <= thr
-    assert acc.sum() > 100 and (err[acc] > 10).mean() <= 0.01
-    # the next larger threshold would break the bound
-    nxt = np.sort(pred)[np.searchsorted(np.sort(pred), thr, side="right")]
-    acc2 = pred <= nxt
-    assert (err[acc2] > 10).mean() > 0.01 or acc2.sum() == acc.sum()
+
+    def sample(n):
+        err = rng.lognormal(1.5, 1.0, n)
+        return err * rng.lognormal(0, 0.3, n), err           # an informative predictor
+
+    over, over_naive, acc_frac = 0, 0, []
+    for _ in range(40):
+        pred, err = sample(5000)
+        thr = calibrate_threshold(pred, err, limit=10.0, miss=0.01)
+        acc = pred <= thr
+        assert acc.sum() > 100 and (err[acc] > 10).mean() <= 0.01
+        order = np.argsort(pred)
+        bad = np.cumsum(err[order] > 10) <= 0.01 * np.arange(1, 5001)
+        thr_naive = pred[order][np.flatnonzero(bad)[-1]]
+        p2, e2 = sample(5000)
+        over += (e2[p2 <= thr] > 10).mean() > 0.01
+        over_naive += (e2[p2 <= thr_naive] > 10).mean() > 0.01
+        acc_frac.append((p2 <= thr).mean())
+    assert over <= 6 and over_naive >= 10 and np.mean(acc_frac) > 0.2
     assert calibrate_threshold(np.array([1.0, 2.0]), np.array([50.0, 1.0])) == 0.0
