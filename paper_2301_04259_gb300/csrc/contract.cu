@@ -284,7 +284,7 @@ soap_status toeplitz_active(soap_ctx* c, const RegionDev* regions_host, int n_re
     if (n_regions > 0) {
         const int nt = n_phases * n_regions;
         SOAP_TIMED(c, SOAP_TIMER_REGIONS,
-                   k_region_geo<<<(nt + 127) / 128, 128, 0, c->stream>>>(
+                   k_region_geo<<<(nt + 31) / 32, 32, 0, c->stream>>>(   // FP64 trig: spread over SMs
                        c->N, n_regions, n_phases, c->regions.as<RegionDev>(), c->phases.as<double>(), c->incl_deg,
                        c->alpha, c->region_geo.as<RegionGeo>());
                    SOAP_LAUNCHED(c));

@@ -190,13 +190,16 @@ __device__ __forceinline__ RegionGeo region_geometry(int N, const RegionDev& g, 
                                                      double alpha) {
     const double d2r = kPi / 180.0;
     const double lat = __dmul_rn(g.lat_deg, d2r);
-    const double sl = sin(lat), cl = cos(lat);
+    double sl, cl;
+    sincos(lat, &sl, &cl);
     const double lonp = __dadd_rn(g.lon_deg, __dmul_rn(__dmul_rn(360.0, phase),
                                                        __dadd_rn(1.0, __dmul_rn(__dmul_rn(alpha, sl), sl))));
     const double lon = __dmul_rn(lonp, d2r);
     const double incl = __dmul_rn(incl_deg, d2r);
-    const double si = sin(incl), ci = cos(incl);
-    const double px = __dmul_rn(cl, sin(lon)), py = sl, pz = __dmul_rn(cl, cos(lon));
+    double si, ci, sn, cn;
+    sincos(incl, &si, &ci);
+    sincos(lon, &sn, &cn);
+    const double px = __dmul_rn(cl, sn), py = sl, pz = __dmul_rn(cl, cn);
     RegionGeo o;
     o.P[0] = px;
     o.P[1] = __dsub_rn(__dmul_rn(py, si), __dmul_rn(pz, ci));
@@ -207,16 +210,21 @@ __device__ __forceinline__ RegionGeo region_geometry(int N, const RegionDev& g, 
     o.cosrf = (float)o.cosr;
     o.cls = g.cls;
     o.pad = 0;
-    const double a = asin(fmin(r, 1.0));
-    const double bx = acos(fmax(-1.0, fmin(1.0, o.P[0])));
-    const double by = acos(fmax(-1.0, fmin(1.0, o.P[1])));
-    const double bz = acos(fmax(-1.0, fmin(1.0, o.P[2])));
-    const double xhi = cos(fmax(0.0, bx - a)), xlo = cos(fmin(kPi, bx + a));
-    const double yhi = cos(fmax(0.0, by - a)), ylo = cos(fmin(kPi, by + a));
-    int i0 = (int)floor((xlo * N + N - 1) * 0.5) - 1, i1 = (int)ceil((xhi * N + N - 1) * 0.5) + 1;
-    int j0 = (int)floor((ylo * N + N - 1) * 0.5) - 1, j1 = (int)ceil((yhi * N + N - 1) * 0.5) + 1;
+    // The cell box only bounds the cells the exact membership test visits, so it is computed in
+    // FP32 (FP64 runs at 1/64 rate here): its error (< 1e-6) is far inside the one-cell margin
+    // (2/N), and the far-side cull keeps a 1e-4 rad margin.
+    const float pi_f = 3.14159265358979f;
+    const float af = asinf(fminf((float)r, 1.0f));
+    const float bx = acosf(fmaxf(-1.0f, fminf(1.0f, o.Pf[0])));
+    const float by = acosf(fmaxf(-1.0f, fminf(1.0f, o.Pf[1])));
+    const float bz = acosf(fmaxf(-1.0f, fminf(1.0f, o.Pf[2])));
+    const float xhi = cosf(fmaxf(0.0f, bx - af)), xlo = cosf(fminf(pi_f, bx + af));
+    const float yhi = cosf(fmaxf(0.0f, by - af)), ylo = cosf(fminf(pi_f, by + af));
+    const float Nf = (float)N;
+    int i0 = (int)floorf((xlo * Nf + Nf - 1.0f) * 0.5f) - 1, i1 = (int)ceilf((xhi * Nf + Nf - 1.0f) * 0.5f) + 1;
+    int j0 = (int)floorf((ylo * Nf + Nf - 1.0f) * 0.5f) - 1, j1 = (int)ceilf((yhi * Nf + Nf - 1.0f) * 0.5f) + 1;
     i0 = max(i0, 0); j0 = max(j0, 0); i1 = min(i1, N - 1); j1 = min(j1, N - 1);
-    if (bz - a > 0.5 * kPi + 1e-6) i1 = i0 - 1;          // cap entirely on the far side
+    if (bz - af > 0.5f * pi_f + 1e-4f) i1 = i0 - 1;     // cap entirely on the far side
     o.box[0] = i0; o.box[1] = i1; o.box[2] = j0; o.box[3] = j1;
     return o;
 }
