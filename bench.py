@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--sur-train", type=int, default=600_000)
     ap.add_argument("--sur-epochs", type=int, default=150)
     ap.add_argument("--sur-queries", type=int, default=1_000_000)
-    ap.add_argument("--only", default="all", choices=["all", "batched", "surrogate", "gemm"],
+    ap.add_argument("--only", default="all", choices=["all", "batched", "surrogate", "gemm", "quiet"],
                     help="run one block alone (for profiling); 'all' is the full benchmark line")
     return ap.parse_args()
 
@@ -327,6 +327,8 @@ def run_ours(args):
         extras["batched"] = measure_batched(args, dev, hbm_peak)
         torch.cuda.empty_cache()
         extras["surrogate"] = measure_surrogate(args, dev)
+        torch.cuda.empty_cache()
+        extras["quiet_forms"] = measure_quiet_forms(args, dev)
 
     res = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
            "steps": K, "warmup": W, "ms_per_step": round(ms_step, 5), "higher_is_better": True,
@@ -620,6 +622,57 @@ def measure_gemm(args, dev, bf16_peak):
             "note": "includes the split of the coefficient rows (one small kernel per chunk)"}
 
 
+def measure_quiet_forms(args, dev):
+    """The quiet-star sum (Alg. 1) of the full-size star in its two forms: the direct gather
+    (every visible cell shifts, interpolates and adds its local spectrum: 2 FMA per cell-pixel)
+    and the Toeplitz contraction (per-mu-bin velocity kernels), FP32 and FP64, kernel time from
+    the library's timers (geometry excluded)."""
+    import torch
+    from paper_2301_04259_gb300 import soap as S
+    from paper_2301_04259_gb300 import synth
+    case = workload(args, 0)
+    st = case.star
+    n_px = st.n_px
+    q_dev = torch.from_numpy(case.quiet).to(dev)
+    ctx = S.soap_init_star(st, q_dev)
+    res = {"workload": case.name, "visible_cells": None}
+    try:
+        info = S.soap_get_star_info(ctx)
+        vis = int(getattr(info, "n_visible", 0)) or int(round(np.pi / 4 * st.grid_n ** 2))
+        res["visible_cells"] = vis
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        fp32_tfma = sms * 128 * 2.07e9 / 1e12
+        for form, fname in ((S.SOAP_FORM_DIRECT, "direct"), (S.SOAP_FORM_TOEPLITZ, "toeplitz")):
+            for prec, pname, dt in ((S.SOAP_FP32, "fp32", torch.float32), (S.SOAP_FP64, "fp64", torch.float64)):
+                out = torch.empty(n_px, dtype=dt, device=dev)
+                reps = 2 if (form == S.SOAP_FORM_DIRECT and prec == S.SOAP_FP64) else 5
+                S.soap_quiet_spectrum(ctx, form, prec, out)
+                torch.cuda.synchronize()
+                S.soap_reset_kernel_times(ctx)
+                S.soap_set_profiling(ctx, True)
+                for _ in range(reps):
+                    S.soap_quiet_spectrum(ctx, form, prec, out)
+                torch.cuda.synchronize()
+                timer = S.TIMERS.index("direct" if form == S.SOAP_FORM_DIRECT else "contract_quiet")
+                tot, n = S.soap_get_kernel_time(ctx, timer)
+                S.soap_set_profiling(ctx, False)
+                ms = tot / max(1, n)
+                entry = {"ms": round(ms, 4), "spectra_per_s": round(1e3 / ms, 1)}
+                if form == S.SOAP_FORM_DIRECT:
+                    fma = 2.0 * vis * n_px
+                    entry["cell_px_per_s"] = float(f"{vis * n_px / (ms * 1e-3):.4g}")
+                    if prec == S.SOAP_FP32:
+                        entry["fma_frac_of_fp32_peak"] = round(fma / (ms * 1e-3) / 1e12 / fp32_tfma, 4)
+                    entry["hbm_gbs_algorithmic"] = round((st.n_mu * n_px + n_px) * (4 if prec == S.SOAP_FP32 else 8)
+                                                         / (ms * 1e-3) / 1e9, 1)
+                res[f"{fname}_{pname}"] = entry
+    finally:
+        S.soap_free(ctx)
+    res["note"] = ("direct: 2 FMA per visible cell-pixel, rows read through L1 (HBM is not its limit: the "
+                   "rows are 16.5 MB); toeplitz: the same sum as per-mu-bin banded convolutions")
+    return res
+
+
 def run_block(args):
     import torch
     torch.cuda.set_device(0)
@@ -633,6 +686,8 @@ def run_block(args):
         res = measure_batched(args, dev, float(peaks.get("hbm_gbs", 6800.0)))
     elif args.only == "surrogate":
         res = measure_surrogate(args, dev)
+    elif args.only == "quiet":
+        res = measure_quiet_forms(args, dev)
     else:
         res = measure_gemm(args, dev, float(peaks.get("bf16_tflops", 1900.0)))
     print(json.dumps({"block": args.only, **res}), flush=True)
