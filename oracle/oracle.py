@@ -12,6 +12,9 @@ Functions follow the paper (arXiv 2301.04259):
   ccf(...)         Sect. 4.1: cross-correlation with a line mask.
   fit_gaussian(...) Sect. 4.1: RV = mean of a Gaussian fitted to the CCF (least squares,
                    Levenberg-Marquardt from scipy/MINPACK, used as a library step).
+  lower_resolution(...) Sect. 3.3 after Eq. 4 (Alg. 5): the integrated spectra degraded to an
+                   instrument's resolving power (Gaussian line-spread function; reading in
+                   instrument_kernel).
 """
 from __future__ import annotations
 
@@ -313,3 +316,40 @@ def rv(F, star_or_range, mask_lambda, mask_weight, width_kms, v_lo, v_step, n_v)
     v = v_lo + v_step * np.arange(n_v)
     params = np.array([fit_gaussian(v, row) for row in c])
     return params[:, 2].copy(), params, c
+
+
+# ---------------------------------------------------------------------------------------
+# instrumental resolution (Sect. 3.3, after Eq. 4)
+# ---------------------------------------------------------------------------------------
+def instrument_kernel(resolving_power, delta_px):
+    """Discrete line-spread function of an instrument of resolving power R on the log grid.
+
+    The paper lowers the resolution of each integrated spectrum to the instrument's without
+    giving the method.  Reading: a Gaussian line-spread function of FWHM lambda / R.  On a
+    log-uniform grid that is a constant width in pixels, FWHM = 1 / (R Delta), sigma =
+    FWHM / (2 sqrt(2 ln 2)).  Each tap is the Gaussian's mass over one pixel,
+    g[k] = (erf((k + 1/2) / (sigma sqrt 2)) - erf((k - 1/2) / (sigma sqrt 2))) / 2, for
+    |k| <= K = ceil(6 sigma) + 1, divided by their sum (the spectrum's flux is kept).  Off centre
+    the mass is taken from erfc differences (no cancellation in the tails), and g[-k] = g[k].
+    Returns (g, K) with g[K + k] the weight of a source pixel k pixels away."""
+    import math
+    sigma = 1.0 / (resolving_power * delta_px * 2.0 * math.sqrt(2.0 * math.log(2.0)))
+    K = int(math.ceil(6.0 * sigma)) + 1
+    s2 = sigma * math.sqrt(2.0)
+    half = [math.erf(0.5 / s2)] + [0.5 * (math.erfc((k - 0.5) / s2) - math.erfc((k + 0.5) / s2))
+                                   for k in range(1, K + 1)]
+    g = np.array(half[:0:-1] + half)
+    return g / g.sum(), K
+
+
+def lower_resolution(F, resolving_power, delta_px):
+    """F [..., n_px] convolved with the instrument kernel: out[m] = sum_k g[k] F[m - k], source
+    indices clamped to the grid (the end values repeat, as for the Doppler shifts)."""
+    F = np.asarray(F, np.float64)
+    g, K = instrument_kernel(resolving_power, delta_px)
+    n = F.shape[-1]
+    m = np.arange(n)
+    out = np.zeros_like(F)
+    for k in range(-K, K + 1):
+        out += g[K + k] * F[..., np.clip(m - k, 0, n - 1)]
+    return out

@@ -660,3 +660,70 @@ def test_redshifted_quiet_spectrum_as_spot_gives_nonnegative_cb_rv(rv_case):
                     c.mask_width_kms, lo, st, nv)
     assert np.all((r - r0[0]) * 1e5 >= -1e-3)
     assert (r - r0[0]).max() > 0
+
+
+
+# ---------------------------------------------------------------------------------------
+# instrumental resolution (Sect. 3.3 after Eq. 4)
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("R,delta", [(115000.0, 2.8986e-6), (50000.0, 2.9e-6), (60000.0, 1.0e-5),
+                                     (1.0e6, 2.9e-6)])
+def test_instrument_kernel_is_a_pixel_integrated_gaussian_of_fwhm_lambda_over_r(R, delta):
+    """Taps sum to one and are symmetric; each equals the 50-digit mass of a Gaussian of FWHM
+    1/(R Delta) pixels over its pixel (renormalised over the kept taps).  Where sigma >= 1.2 px
+    the taps' variance is sigma^2 + 1/12 (a Gaussian convolved with a one-pixel box; by Poisson
+    summation the discrete sum differs by terms ~exp(-2 pi^2 sigma^2) < 1e-12, and the truncation
+    at 6 sigma by < 1e-8)."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    g, K = O.instrument_kernel(R, delta)
+    sigma = 1.0 / (R * delta * 2.0 * math.sqrt(2.0 * math.log(2.0)))
+    assert abs(g.sum() - 1.0) < 1e-15
+    np.testing.assert_array_equal(g, g[::-1])
+    k = np.arange(-K, K + 1)
+    if sigma >= 1.2:
+        assert float(np.sum(k * k * g)) == pytest.approx(sigma ** 2 + 1.0 / 12.0, rel=1e-8)
+    s2 = mp.mpf(sigma) * mp.sqrt(2)
+    raw = [(mp.erf((mp.mpf(j) + mp.mpf(0.5)) / s2) - mp.erf((mp.mpf(j) - mp.mpf(0.5)) / s2)) / 2
+           for j in range(-K, K + 1)]
+    tot = mp.fsum(raw)
+    for j in range(2 * K + 1):
+        assert float(raw[j] / tot) == pytest.approx(g[j], rel=1e-13, abs=1e-300)
+
+
+def test_lower_resolution_keeps_flux_centroid_and_adds_variance():
+    """For lines far from the grid ends a discrete convolution with a unit-sum kernel keeps the
+    equivalent width and, with a symmetric kernel, the centroid, and adds the kernel's variance
+    to the line's (exact identities of discrete convolution), whatever the line shape."""
+    rng = np.random.default_rng(3)
+    n = 4001
+    m = np.arange(n, dtype=np.float64)
+    depth = np.zeros(n)
+    for c, w, d in ((1200.3, 3.1, 0.6), (2000.0, 1.2, 0.3), (2890.7, 5.0, 0.45)):
+        depth += d * np.exp(-0.5 * ((m - c) / w) ** 2) * (1 + 0.3 * np.sin(m / 7.0)) ** 2
+    depth += 0.01 * rng.random(n) * ((m > 1500) & (m < 1510))
+    F = 1.0 - depth
+    out = O.lower_resolution(F, 115000.0, 2.8986e-6)
+    g, K = O.instrument_kernel(115000.0, 2.8986e-6)
+    kv = float(np.sum(np.arange(-K, K + 1) ** 2 * g))
+    d_in, d_out = 1.0 - F, 1.0 - out
+    assert d_out.sum() == pytest.approx(d_in.sum(), rel=1e-13)
+    c_in, c_out = (m * d_in).sum() / d_in.sum(), (m * d_out).sum() / d_out.sum()
+    assert c_out == pytest.approx(c_in, abs=1e-9)
+    v_in = ((m - c_in) ** 2 * d_in).sum() / d_in.sum()
+    v_out = ((m - c_out) ** 2 * d_out).sum() / d_out.sum()
+    assert v_out == pytest.approx(v_in + kv, rel=1e-11)
+
+
+def test_lower_resolution_of_a_flat_spectrum_and_at_the_edges():
+    """A flat spectrum stays flat (unit-sum kernel); next to the ends the repeated end values
+    enter: a step at the first pixel is smoothed only inward."""
+    F = np.full((2, 300), 0.75)
+    np.testing.assert_allclose(O.lower_resolution(F, 115000.0, 2.9e-6), F, rtol=0, atol=1e-15)
+    S = np.zeros(300)
+    S[:1] = 1.0
+    out = O.lower_resolution(S, 115000.0, 2.9e-6)
+    g, K = O.instrument_kernel(115000.0, 2.9e-6)
+    # out[m] = sum over k >= m of g[K + k] (the clamped sources of row 0)
+    for mm in range(K + 2):
+        assert out[mm] == pytest.approx(g[K + mm:].sum(), rel=1e-14, abs=1e-17)
