@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--sur-train", type=int, default=600_000)
     ap.add_argument("--sur-epochs", type=int, default=150)
     ap.add_argument("--sur-queries", type=int, default=1_000_000)
-    ap.add_argument("--only", default="all", choices=["all", "batched", "surrogate", "gemm", "quiet"],
+    ap.add_argument("--only", default="all", choices=["all", "batched", "surrogate", "gemm", "quiet", "instrument"],
                     help="run one block alone (for profiling); 'all' is the full benchmark line")
     return ap.parse_args()
 
@@ -329,6 +329,8 @@ def run_ours(args):
         extras["surrogate"] = measure_surrogate(args, dev)
         torch.cuda.empty_cache()
         extras["quiet_forms"] = measure_quiet_forms(args, dev)
+        torch.cuda.empty_cache()
+        extras["instrument"] = measure_instrument(args, dev, hbm_peak)
 
     res = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
            "steps": K, "warmup": W, "ms_per_step": round(ms_step, 5), "higher_is_better": True,
@@ -673,6 +675,42 @@ def measure_quiet_forms(args, dev):
     return res
 
 
+def measure_instrument(args, dev, hbm_peak):
+    """Instrumental resolution lowering (Sect. 3.3 after Eq. 4) of the step's 100 full-size
+    spectra at R = 115000 (FWHM 3 px, 19 taps): kernel time from the library's timer and its
+    HBM roofline (each spectrum read once and written once)."""
+    import torch
+    from paper_2301_04259_gb300 import soap as S
+    case = workload(args, 0)
+    st = case.star
+    P, n_px = case.phases.size, st.n_px
+    ctx = S.soap_init_star(st, torch.from_numpy(case.quiet).to(dev))
+    res = {"workload": case.name, "resolving_power": 115000.0, "spectra": P}
+    try:
+        S.soap_set_instrument_resolution(ctx, 115000.0)
+        for dt, name, esz in ((torch.float32, "fp32", 4), (torch.float64, "fp64", 8)):
+            src = torch.rand((P, n_px), dtype=dt, device=dev)
+            dst = torch.empty_like(src)
+            S.soap_lower_resolution(ctx, src, dst)
+            torch.cuda.synchronize()
+            S.soap_reset_kernel_times(ctx)
+            S.soap_set_profiling(ctx, True)
+            reps = max(3, args.steps)
+            for _ in range(reps):
+                S.soap_lower_resolution(ctx, src, dst)
+            torch.cuda.synchronize()
+            tot, n = S.soap_get_kernel_time(ctx, S.TIMERS.index("lsf"))
+            S.soap_set_profiling(ctx, False)
+            ms = tot / max(1, n)
+            gbs = 2.0 * P * n_px * esz / (ms * 1e-3) / 1e9
+            res[name] = {"ms": round(ms, 4), "hbm_gbs": round(gbs, 1), "frac_of_hbm": round(gbs / hbm_peak, 4)}
+            del src, dst
+    finally:
+        S.soap_free(ctx)
+    res["note"] = "inputs 329/165 MB > L2 (FP64/FP32); timed without an L2 flush between repetitions"
+    return res
+
+
 def run_block(args):
     import torch
     torch.cuda.set_device(0)
@@ -688,6 +726,8 @@ def run_block(args):
         res = measure_surrogate(args, dev)
     elif args.only == "quiet":
         res = measure_quiet_forms(args, dev)
+    elif args.only == "instrument":
+        res = measure_instrument(args, dev, float(peaks.get("hbm_gbs", 6800.0)))
     else:
         res = measure_gemm(args, dev, float(peaks.get("bf16_tflops", 1900.0)))
     print(json.dumps({"block": args.only, **res}), flush=True)

@@ -149,7 +149,8 @@ typedef enum {
     SOAP_TIMER_CCF = 8,          /* CCF partial sums (the main CCF kernel) */
     SOAP_TIMER_FIT = 9,          /* Gaussian fits */
     SOAP_TIMER_CCF_AUX = 10,     /* CCF line / velocity tables (when rebuilt) + partial-sum reduction */
-    SOAP_TIMER_COUNT = 11
+    SOAP_TIMER_LSF = 11,         /* instrumental line-spread function */
+    SOAP_TIMER_COUNT = 12
 } soap_timer;
 
 /* Read-only facts about an initialised star. */
@@ -272,6 +273,24 @@ soap_status soap_active_rv(soap_ctx* ctx, const soap_region* regions, int32_t n_
                            int32_t precision, const double* mask_lambda, const double* mask_weight,
                            int32_t n_lines, double mask_width_kms, double v_lo, double v_step,
                            int32_t n_v, void* spectra_out, double* rv_kms, int out_on_device);
+
+/* Instrumental resolution (Sect. 3.3, after Eq. 4): the integrated spectra are degraded to
+ * an instrument's resolving power R.  The paper does not give the method; the line-spread
+ * function here is a Gaussian of FWHM lambda / R, on the log grid a fixed kernel of 1/(R Delta)
+ * pixels FWHM, one tap per pixel (the Gaussian's mass over it) for |k| <= ceil(6 sigma) + 1,
+ * renormalised to unit sum; out[m] = sum_k g[k] F[clamp(m - k)] (end values repeat).
+ *  resolving_power  R > 0 switches it on for soap_quiet_spectrum, soap_active_phases and
+ *                   soap_active_rv (the CCF then sees the degraded spectra); 0 switches it off
+ *                   (the default).  SOAP_ERANGE if sigma > 800 pixels or the kernel is wider
+ *                   than the grid.
+ * The batched form (soap_active_batch) does not apply it. */
+soap_status soap_set_instrument_resolution(soap_ctx* ctx, double resolving_power);
+
+/* Apply the context's line-spread function to n_spec spectra [n_spec][n_px] (float64, or
+ * float32 with spectra_f32 = 1): in -> out, distinct arrays, both host or both device per
+ * on_device.  SOAP_ESTATE if no resolution is set. */
+soap_status soap_lower_resolution(soap_ctx* ctx, const void* in, void* out, int32_t spectra_f32,
+                                  int32_t n_spec, int on_device);
 
 /* One configuration of a batch (soap_active_batch): a star of the context's type (same grid,
  * mu table, limb darkening, local spectra and wavelength grid) seen with its own projected

@@ -217,7 +217,7 @@ static void free_ctx_memory(soap_ctx* c) {
         if (p) cudaFree(p);
     DevBuf* bufs[] = {&c->stage_in, &c->fq, &c->contrast, &c->kphase, &c->jobs, &c->coefs, &c->job_counters,
                       &c->regions, &c->region_geo, &c->phases, &c->out_stage, &c->partial, &c->ccf_tmp,
-                      &c->ccf_tab};
+                      &c->ccf_tab, &c->lsf_taps, &c->lsf_tmp};
     for (DevBuf* b : bufs) release(*b);
     release_host(c->host_stage);
     ring_release(c);
@@ -618,8 +618,14 @@ soap_status soap_quiet_spectrum(soap_ctx* c, int32_t form, int32_t precision, vo
         SOAP_TRY(ensure(c->out_stage, bytes));
         dst = c->out_stage.p;
     }
-    if (form == SOAP_FORM_TOEPLITZ) SOAP_TRY(toeplitz_quiet(c, precision, dst));
-    else SOAP_TRY(direct_quiet(c, precision, dst));
+    void* raw = dst;                               // before the instrument's line-spread function
+    if (c->lsf_K >= 0) {
+        SOAP_TRY(ensure(c->lsf_tmp, bytes));
+        raw = c->lsf_tmp.p;
+    }
+    if (form == SOAP_FORM_TOEPLITZ) SOAP_TRY(toeplitz_quiet(c, precision, raw));
+    else SOAP_TRY(direct_quiet(c, precision, raw));
+    if (c->lsf_K >= 0) SOAP_TRY(launch_lsf(c, raw, dst, precision == SOAP_FP32, 1));
     if (!out_on_device) {
         SOAP_CUDA(cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, c->stream));
         SOAP_CUDA(cudaStreamSynchronize(c->stream));
@@ -704,7 +710,49 @@ static soap_status check_rv(soap_ctx* c, const double* mask_lambda, const double
     return SOAP_OK;
 }
 
+// Spectra of one effect into dst, through the instrument's line-spread function when one is set.
+static soap_status active_lsf(soap_ctx* c, const ActiveArgs& A, int32_t n_regions, const double* phases,
+                              int32_t n_phases, uint32_t effect, int32_t precision, void* dst, size_t bytes) {
+    void* raw = dst;
+    if (c->lsf_K >= 0) {
+        SOAP_TRY(ensure(c->lsf_tmp, bytes));
+        raw = c->lsf_tmp.p;
+    }
+    SOAP_TRY(toeplitz_active(c, A.rd.data(), n_regions, A.ctemp, A.ctype, A.n_class, phases, n_phases,
+                             effect, precision, raw));
+    if (c->lsf_K >= 0) SOAP_TRY(launch_lsf(c, raw, dst, precision == SOAP_FP32, n_phases));
+    return SOAP_OK;
+}
+
 extern "C" {
+
+soap_status soap_set_instrument_resolution(soap_ctx* c, double resolving_power) {
+    clear_error();
+    if (!c) { set_error("ctx is NULL"); return SOAP_EINVAL; }
+    if (!(resolving_power >= 0) || !std::isfinite(resolving_power)) {
+        set_error("resolving power must be finite and >= 0 (0: off)"); return SOAP_EINVAL;
+    }
+    return set_instrument(c, resolving_power);
+}
+
+soap_status soap_lower_resolution(soap_ctx* c, const void* in, void* out, int32_t spectra_f32,
+                                  int32_t n_spec, int on_device) {
+    clear_error();
+    if (!c || !in || !out) { set_error("NULL argument"); return SOAP_EINVAL; }
+    if (c->lsf_K < 0) { set_error("no instrument resolution set (soap_set_instrument_resolution)"); return SOAP_ESTATE; }
+    if (n_spec < 0) { set_error("n_spec < 0"); return SOAP_EINVAL; }
+    if (in == out) { set_error("in and out must not be the same array"); return SOAP_EINVAL; }
+    if (n_spec == 0) return SOAP_OK;
+    const size_t bytes = (size_t)n_spec * (size_t)c->n_px * (spectra_f32 ? 4 : 8);
+    if (on_device) return launch_lsf(c, in, out, spectra_f32 ? 1 : 0, n_spec);
+    SOAP_TRY(ensure(c->lsf_tmp, bytes));
+    SOAP_TRY(ensure(c->out_stage, bytes));
+    SOAP_CUDA(cudaMemcpyAsync(c->lsf_tmp.p, in, bytes, cudaMemcpyHostToDevice, c->stream));
+    SOAP_TRY(launch_lsf(c, c->lsf_tmp.p, c->out_stage.p, spectra_f32 ? 1 : 0, n_spec));
+    SOAP_CUDA(cudaMemcpyAsync(out, c->out_stage.p, bytes, cudaMemcpyDeviceToHost, c->stream));
+    SOAP_CUDA(cudaStreamSynchronize(c->stream));
+    return SOAP_OK;
+}
 
 soap_status soap_active_phases(soap_ctx* c, const soap_region* regions, int32_t n_regions,
                                const double* phases, int32_t n_phases, uint32_t effects,
@@ -722,8 +770,14 @@ soap_status soap_active_phases(soap_ctx* c, const soap_region* regions, int32_t 
         SOAP_TRY(ensure(c->out_stage, bytes));
         dst = c->out_stage.p;
     }
+    void* raw = dst;                               // before the instrument's line-spread function
+    if (c->lsf_K >= 0) {
+        SOAP_TRY(ensure(c->lsf_tmp, bytes));
+        raw = c->lsf_tmp.p;
+    }
     SOAP_TRY(toeplitz_active(c, A.rd.data(), n_regions, A.ctemp, A.ctype, A.n_class, phases, n_phases,
-                             effects, precision, dst));
+                             effects, precision, raw));
+    if (c->lsf_K >= 0) SOAP_TRY(launch_lsf(c, raw, dst, precision == SOAP_FP32, (int64_t)n_eff * n_phases));
     if (!out_on_device) {
         SOAP_CUDA(cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, c->stream));
         SOAP_CUDA(cudaStreamSynchronize(c->stream));
@@ -754,8 +808,7 @@ soap_status soap_active_rv(soap_ctx* c, const soap_region* regions, int32_t n_re
             SOAP_TRY(ensure(c->out_stage, sbytes));
             sp = c->out_stage.p;
         }
-        SOAP_TRY(toeplitz_active(c, A.rd.data(), n_regions, A.ctemp, A.ctype, A.n_class, phases,
-                                 n_phases, effect, precision, sp));
+        SOAP_TRY(active_lsf(c, A, n_regions, phases, n_phases, effect, precision, sp, sbytes));
         return rv_ccf_run(c, sp, f32, n_phases, mask_lambda, mask_weight, n_lines, mask_width_kms,
                           v_lo, v_step, n_v, rv_kms, nullptr, nullptr);
     }
@@ -770,8 +823,7 @@ soap_status soap_active_rv(soap_ctx* c, const soap_region* regions, int32_t n_re
     void* spec_d = d.p;
     double* rv_d = reinterpret_cast<double*>(d.as<char>() + o_rv);
     SOAP_CUDA(cudaStreamWaitEvent(c->stream, c->dn_free[o], 0));        // its last copy out is done
-    SOAP_TRY(toeplitz_active(c, A.rd.data(), n_regions, A.ctemp, A.ctype, A.n_class, phases,
-                             n_phases, effect, precision, spec_d));
+    SOAP_TRY(active_lsf(c, A, n_regions, phases, n_phases, effect, precision, spec_d, sbytes));
     if (spectra_out) {
         SOAP_CUDA(cudaEventRecord(c->dn_spec[o], c->stream));
         SOAP_CUDA(cudaStreamWaitEvent(c->out_stream, c->dn_spec[o], 0));

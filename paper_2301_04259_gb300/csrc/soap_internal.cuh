@@ -175,6 +175,13 @@ struct soap_ctx {
     soap::HostBuf host_stage;
     soap::PinnedRing ring;      // small uploads (see PinnedRing)
 
+    // instrumental resolution (soap_set_instrument_resolution): taps [2K+1] in f64, then f32 at
+    // lsf_off32; lsf_K < 0 when off; lsf_tmp holds spectra before the line-spread function
+    double lsf_R = 0.0;
+    int lsf_K = -1;
+    size_t lsf_off32 = 0, lsf_offp64 = 0, lsf_offp32 = 0;
+    soap::DevBuf lsf_taps, lsf_tmp;
+
     // CCF line and velocity tables, kept while the mask and the velocity grid stay the same
     soap::DevBuf ccf_tab;
     std::vector<double> ccf_mask_key;    // mask_lambda, mask_weight, then width
@@ -227,6 +234,9 @@ void timer_end(soap_ctx* c, int timer, cudaEvent_t begin);
 soap_status geometry_init(soap_ctx* c);                          // per-cell geometry + quiet kernels
 soap_status pad_rows(soap_ctx* c, const double* src, double* dst64, float* dst32, int rows);
 soap_status pad_rows32(soap_ctx* c, const float* src, float* dst32, int rows);
+// instrumental resolution (instrument.cu)
+soap_status set_instrument(soap_ctx* c, double resolving_power);
+soap_status launch_lsf(soap_ctx* c, const void* in, void* out, int f32, int64_t n_spec);
 // Copy `bytes` of host memory to device memory `dst` on the context stream through the pinned
 // ring (pageable sources are fine; the source may change once the call returns).
 soap_status upload_small(soap_ctx* c, void* dst, const void* src, size_t bytes);

@@ -26,7 +26,7 @@ SOAP_SPOT, SOAP_FACULA = 1, 2
 SOAP_BATCH_SPECTRUM, SOAP_BATCH_RESIDUAL = 0, 1
 SOAP_MAX_REGIONS, SOAP_MAX_CLASSES, SOAP_MAX_MU, SOAP_MAX_TAPS = 64, 8, 64, 256
 TIMERS = ("geometry", "pad_rows", "contrast", "phase_hist", "regions", "contract", "contract_quiet",
-          "direct", "ccf", "fit", "ccf_aux")
+          "direct", "ccf", "fit", "ccf_aux", "lsf")
 (SOAP_TIMER_GEOMETRY, SOAP_TIMER_PAD_ROWS, SOAP_TIMER_CONTRAST, SOAP_TIMER_PHASE_HIST,
  SOAP_TIMER_REGIONS, SOAP_TIMER_CONTRACT, SOAP_TIMER_CONTRACT_QUIET, SOAP_TIMER_DIRECT,
  SOAP_TIMER_CCF, SOAP_TIMER_FIT) = range(10)
@@ -90,6 +90,8 @@ def _load():
         "soap_set_stream": (i32, [P, P]),
         "soap_synchronize": (i32, [P]),
         "soap_set_host_async": (i32, [P, ctypes.c_int]),
+        "soap_set_instrument_resolution": (i32, [P, d]),
+        "soap_lower_resolution": (i32, [P, P, P, i32, i32, ctypes.c_int]),
         "soap_active_rv": (i32, [P, ctypes.POINTER(soap_region), i32, P, i32, u32, i32, P, P, i32, d, d, d,
                                  i32, P, P, ctypes.c_int]),
         "soap_get_star_info": (i32, [P, ctypes.POINTER(soap_star_info)]),
@@ -268,6 +270,22 @@ def soap_active_phases(ctx, regions: Sequence, phases, effects: int, precision: 
     ptr, dev = _ptr(out)
     _check(_lib.soap_active_phases(ctx, arr, len(regions), ctypes.c_void_p(ph.ctypes.data), ph.size,
                                    int(effects), int(precision), ptr, dev), "soap_active_phases")
+
+
+def soap_set_instrument_resolution(ctx, resolving_power: float) -> None:
+    _check(_lib.soap_set_instrument_resolution(ctx, float(resolving_power)), "soap_set_instrument_resolution")
+
+
+def soap_lower_resolution(ctx, spectra, out) -> None:
+    """spectra [n_spec][n_px] (float64 or float32) -> out of the same shape; both host or both device."""
+    ip, idev = _ptr(spectra)
+    op, odev = _ptr(out)
+    if idev != odev:
+        raise ValueError("spectra and out must both be host or both device")
+    f32 = int(_is_f32(spectra))
+    if f32 != int(_is_f32(out)):
+        raise ValueError("spectra and out must have the same dtype")
+    _check(_lib.soap_lower_resolution(ctx, ip, op, f32, int(spectra.shape[0]), idev), "soap_lower_resolution")
 
 
 def soap_set_host_async(ctx, enabled: bool) -> None:
