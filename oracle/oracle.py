@@ -12,6 +12,9 @@ Functions follow the paper (arXiv 2301.04259):
   ccf(...)         Sect. 4.1: cross-correlation with a line mask.
   fit_gaussian(...) Sect. 4.1: RV = mean of a Gaussian fitted to the CCF (least squares,
                    Levenberg-Marquardt from scipy/MINPACK, used as a library step).
+  evolution_area(...), evolution_radius(...)  Sect. 4.2.1: active-region size evolution
+                   (linear growth, linear decay, asymmetric Gaussian); active(..., radii=) takes
+                   per-phase radii.
   lower_resolution(...) Sect. 3.3 after Eq. 4 (Alg. 5): the integrated spectra degraded to an
                    instrument's resolving power (Gaussian line-spread function; reading in
                    instrument_kernel).
@@ -152,11 +155,23 @@ EFFECT_TOT, EFFECT_FLUX, EFFECT_BCONV = 1, 2, 4
 
 
 def active(star, quiet_local, active_local, regions, phases, effects=EFFECT_TOT, pix=None,
-           return_delta=False):
+           return_delta=False, radii=None):
     """Spectra of the active star per phase (Alg. 5, Eqs. 1-4).
 
     active_local: dict type -> [n_mu, n_px] (1 spot, 2 facula; facula defaults to spot).
+    radii: optional [n_phases, n_regions] region radii per phase (evolving regions); each phase
+    is then computed with its own radii.
     Returns F [n_eff, n_phases, n_sample] (and Delta F if return_delta)."""
+    if radii is not None:
+        import dataclasses
+        radii = np.asarray(radii, np.float64)
+        parts = []
+        for p, ph in enumerate(np.atleast_1d(np.asarray(phases, np.float64))):
+            regs = [dataclasses.replace(r, radius_rstar=float(radii[p, q])) for q, r in enumerate(regions)]
+            parts.append(active(star, quiet_local, active_local, regs, [ph], effects, pix, return_delta))
+        if return_delta:
+            return (np.concatenate([a for a, _ in parts], axis=1), np.concatenate([b for _, b in parts], axis=1))
+        return np.concatenate(parts, axis=1)
     q = _f64(quiet_local)
     spot = _f64(active_local[1])
     fac = _f64(active_local.get(2, active_local[1]))
@@ -353,3 +368,40 @@ def lower_resolution(F, resolving_power, delta_px):
     for k in range(-K, K + 1):
         out += g[K + k] * F[..., np.clip(m - k, 0, n - 1)]
     return out
+
+
+# ---------------------------------------------------------------------------------------
+# active-region size evolution (Sect. 4.2.1)
+# ---------------------------------------------------------------------------------------
+EVOLVE_NONE, EVOLVE_LINEAR_GROWTH, EVOLVE_LINEAR_DECAY, EVOLVE_ASYM_GAUSSIAN = 0, 1, 2, 3
+
+
+def evolution_area(law, t, area0_msh=10000.0, rate_msh_per_day=400.0, t_peak_day=0.0,
+                   fwhm_day=10.0, asymmetry=0.09):
+    """Area (millionths of the solar hemisphere, MSH) of an evolving region at time t (days).
+
+    Sect. 4.2.1 names three laws and their parameters; the formulas are this reading's:
+      linear growth:  A = A0 + rate t                  (t >= 0; A0 before)
+      linear decay:   A = max(0, A0 - rate t)          (t >= 0; A0 before)
+      asymmetric Gaussian (Murakozy et al. 2014): A = A0 exp(-(t - t_peak)^2 / (2 s^2)) with
+        s = s_rise before the peak and s_decay after it, s_rise + s_decay = FWHM / sqrt(2 ln 2)
+        (the half-maximum points lie FWHM apart) and (s_decay - s_rise) / (s_decay + s_rise)
+        = asymmetry (> 0: faster growth than decay)."""
+    t = np.asarray(t, np.float64)
+    if law == EVOLVE_LINEAR_GROWTH:
+        return area0_msh + rate_msh_per_day * np.maximum(t, 0.0)
+    if law == EVOLVE_LINEAR_DECAY:
+        return np.maximum(0.0, area0_msh - rate_msh_per_day * np.maximum(t, 0.0))
+    if law == EVOLVE_ASYM_GAUSSIAN:
+        tot = fwhm_day / np.sqrt(2.0 * np.log(2.0))
+        s_rise, s_decay = tot * (1.0 - asymmetry) / 2.0, tot * (1.0 + asymmetry) / 2.0
+        s = np.where(t < t_peak_day, s_rise, s_decay)
+        return area0_msh * np.exp(-0.5 * ((t - t_peak_day) / s) ** 2)
+    raise ValueError("unknown evolution law")
+
+
+def evolution_radius(area_msh):
+    """Region radius (R*) of an area in MSH.  Reading: 10000 MSH = 1% of the visible hemisphere
+    (Sect. 4.2.1), taken as the region's projected area at disk centre, r^2 = A 1e-6 (the same
+    convention as 'a 1% spot' = r 0.1 in Sect. 4.1)."""
+    return np.sqrt(np.asarray(area_msh, np.float64) * 1e-6)

@@ -727,3 +727,40 @@ def test_lower_resolution_of_a_flat_spectrum_and_at_the_edges():
     # out[m] = sum over k >= m of g[K + k] (the clamped sources of row 0)
     for mm in range(K + 2):
         assert out[mm] == pytest.approx(g[K + mm:].sum(), rel=1e-14, abs=1e-17)
+
+
+
+# ---------------------------------------------------------------------------------------
+# active-region evolution (Sect. 4.2.1)
+# ---------------------------------------------------------------------------------------
+def test_evolution_laws_closed_forms():
+    t = np.array([-2.0, 0.0, 1.5, 10.0, 30.0])
+    np.testing.assert_allclose(O.evolution_area(O.EVOLVE_LINEAR_GROWTH, t),
+                               [10000, 10000, 10600, 14000, 22000], rtol=1e-15)
+    np.testing.assert_allclose(O.evolution_area(O.EVOLVE_LINEAR_DECAY, t),
+                               [10000, 10000, 9400, 6000, 0], rtol=1e-15)
+    # asymmetric Gaussian: peak value, half maxima FWHM apart, widths in the asymmetry's ratio
+    tp, fwhm, a = 4.0, 10.0, 0.09
+    A = lambda x: float(O.evolution_area(O.EVOLVE_ASYM_GAUSSIAN, x, t_peak_day=tp, fwhm_day=fwhm, asymmetry=a))
+    assert A(tp) == 10000.0
+    from scipy.optimize import brentq
+    lo = brentq(lambda x: A(x) - 5000.0, tp - 20, tp)
+    hi = brentq(lambda x: A(x) - 5000.0, tp, tp + 20)
+    assert hi - lo == pytest.approx(fwhm, rel=1e-12)
+    assert ((hi - tp) - (tp - lo)) / ((hi - tp) + (tp - lo)) == pytest.approx(a, rel=1e-10)
+    assert O.evolution_radius(10000.0) == pytest.approx(0.1, rel=1e-15)
+
+
+def test_per_phase_radii_reduce_to_fixed_regions(small_case):
+    """Per-phase radii equal to the regions' own radii give the fixed-region spectra; radius 0
+    at a phase gives the quiet spectrum there."""
+    c = small_case
+    phases = c.phases[:4]
+    fixed = O.active(c.star, c.quiet, c.active, c.regions, phases, effects=7)
+    radii = np.array([[r.radius_rstar for r in c.regions]] * len(phases))
+    np.testing.assert_array_equal(O.active(c.star, c.quiet, c.active, c.regions, phases, effects=7, radii=radii),
+                                  fixed)
+    radii[2, :] = 0.0
+    got = O.active(c.star, c.quiet, c.active, c.regions, phases, effects=1, radii=radii)
+    q = O.quiet(c.star, c.quiet)
+    np.testing.assert_allclose(got[0, 2], q, rtol=0, atol=1e-15 * np.abs(q).max())
