@@ -292,6 +292,40 @@ soap_status soap_set_instrument_resolution(soap_ctx* ctx, double resolving_power
 soap_status soap_lower_resolution(soap_ctx* ctx, const void* in, void* out, int32_t spectra_f32,
                                   int32_t n_spec, int on_device);
 
+/* Active-region size evolution (Sect. 4.2.1).  The paper names three laws and their
+ * parameters; the formulas are readings:
+ *  SOAP_EVOLVE_NONE            the region keeps its radius_rstar;
+ *  SOAP_EVOLVE_LINEAR_GROWTH   A(t) = A0 + rate max(t, 0);
+ *  SOAP_EVOLVE_LINEAR_DECAY    A(t) = max(0, A0 - rate max(t, 0));
+ *  SOAP_EVOLVE_ASYM_GAUSSIAN   A(t) = A0 exp(-(t - t_peak)^2 / (2 s^2)) (Murakozy et al. 2014),
+ *                              s = s_rise before the peak, s_decay after it, s_rise + s_decay =
+ *                              fwhm / sqrt(2 ln 2), (s_decay - s_rise) / (s_decay + s_rise) = asymmetry;
+ * A in millionths of the solar hemisphere (MSH), t in days; the radius is sqrt(A 1e-6) stellar
+ * radii (10000 MSH = 1% of the visible hemisphere = a disk-centre region of radius 0.1), at
+ * most 1. */
+enum { SOAP_EVOLVE_NONE = 0, SOAP_EVOLVE_LINEAR_GROWTH = 1, SOAP_EVOLVE_LINEAR_DECAY = 2,
+       SOAP_EVOLVE_ASYM_GAUSSIAN = 3 };
+typedef struct {
+    int32_t law;               /* SOAP_EVOLVE_* */
+    int32_t reserved;          /* 0 */
+    double area0_msh;          /* A0: initial (linear laws) or peak (Gaussian) area, MSH */
+    double rate_msh_per_day;   /* linear laws */
+    double t_peak_day;         /* Gaussian */
+    double fwhm_day;           /* Gaussian, > 0 */
+    double asymmetry;          /* Gaussian, |asymmetry| < 1 */
+} soap_region_evolution;
+
+/* Radii [n_times][n_regions] (host) of evolving regions at times_day[n_times] (host): evo[q]
+ * governs regions[q] (host arrays of n_regions).  Host arithmetic only. */
+soap_status soap_evolve_radii(const soap_region_evolution* evo, const soap_region* regions, int32_t n_regions,
+                              const double* times_day, int32_t n_times, double* radii);
+
+/* soap_active_phases with per-phase region radii: radii host [n_phases][n_regions], each in
+ * [0, 1] (e.g. from soap_evolve_radii at the phases' times); every other argument as there. */
+soap_status soap_active_phases_radii(soap_ctx* ctx, const soap_region* regions, int32_t n_regions,
+                                     const double* phases, int32_t n_phases, const double* radii,
+                                     uint32_t effects, int32_t precision, void* out, int out_on_device);
+
 /* One configuration of a batch (soap_active_batch): a star of the context's type (same grid,
  * mu table, limb darkening, local spectra and wavelength grid) seen with its own projected
  * velocity and inclination, carrying its own regions at its own phases. */

@@ -754,13 +754,19 @@ soap_status soap_lower_resolution(soap_ctx* c, const void* in, void* out, int32_
     return SOAP_OK;
 }
 
-soap_status soap_active_phases(soap_ctx* c, const soap_region* regions, int32_t n_regions,
-                               const double* phases, int32_t n_phases, uint32_t effects,
-                               int32_t precision, void* out, int out_on_device) {
-    clear_error();
+}  // extern "C"
+
+static soap_status active_phases_impl(soap_ctx* c, const soap_region* regions, int32_t n_regions,
+                                      const double* phases, int32_t n_phases, const double* radii,
+                                      uint32_t effects, int32_t precision, void* out, int out_on_device) {
     if (!c || !out) { set_error("ctx or out is NULL"); return SOAP_EINVAL; }
     ActiveArgs A;
     SOAP_TRY(check_active(c, regions, n_regions, phases, n_phases, effects, precision, A));
+    if (radii)
+        for (int64_t i = 0; i < (int64_t)n_phases * n_regions; i++)
+            if (!(radii[i] >= 0.0 && radii[i] <= 1.0)) {
+                set_error("radii[%lld] = %g outside [0, 1]", (long long)i, radii[i]); return SOAP_EINVAL;
+            }
     int n_eff = __builtin_popcount(effects);
     size_t esz = precision == SOAP_FP64 ? 8 : 4;
     size_t bytes = (size_t)n_eff * (size_t)n_phases * (size_t)c->n_px * esz;
@@ -776,7 +782,7 @@ soap_status soap_active_phases(soap_ctx* c, const soap_region* regions, int32_t 
         raw = c->lsf_tmp.p;
     }
     SOAP_TRY(toeplitz_active(c, A.rd.data(), n_regions, A.ctemp, A.ctype, A.n_class, phases, n_phases,
-                             effects, precision, raw));
+                             effects, precision, raw, radii));
     if (c->lsf_K >= 0) SOAP_TRY(launch_lsf(c, raw, dst, precision == SOAP_FP32, (int64_t)n_eff * n_phases));
     if (!out_on_device) {
         SOAP_CUDA(cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, c->stream));
@@ -784,6 +790,71 @@ soap_status soap_active_phases(soap_ctx* c, const soap_region* regions, int32_t 
         SOAP_TRY(check_flags(c));
     }
     return SOAP_OK;
+}
+
+// Area (MSH) of an evolving region at time t (days): the laws and readings of Sect. 4.2.1 as
+// stated in soap.h.
+static double evolution_area(const soap_region_evolution& e, double t) {
+    switch (e.law) {
+        case SOAP_EVOLVE_LINEAR_GROWTH: return e.area0_msh + e.rate_msh_per_day * std::max(t, 0.0);
+        case SOAP_EVOLVE_LINEAR_DECAY: return std::max(0.0, e.area0_msh - e.rate_msh_per_day * std::max(t, 0.0));
+        case SOAP_EVOLVE_ASYM_GAUSSIAN: {
+            const double tot = e.fwhm_day / std::sqrt(2.0 * std::log(2.0));
+            const double s = t < e.t_peak_day ? tot * (1.0 - e.asymmetry) / 2.0 : tot * (1.0 + e.asymmetry) / 2.0;
+            const double u = (t - e.t_peak_day) / s;
+            return e.area0_msh * std::exp(-0.5 * u * u);
+        }
+        default: return -1.0;
+    }
+}
+
+extern "C" {
+
+soap_status soap_evolve_radii(const soap_region_evolution* evo, const soap_region* regions, int32_t n_regions,
+                              const double* times_day, int32_t n_times, double* radii) {
+    clear_error();
+    if (n_regions < 0 || n_times < 0) { set_error("negative count"); return SOAP_EINVAL; }
+    if ((n_regions > 0 && (!evo || !regions)) || (n_times > 0 && !times_day) ||
+        (n_regions > 0 && n_times > 0 && !radii)) {
+        set_error("NULL argument"); return SOAP_EINVAL;
+    }
+    for (int q = 0; q < n_regions; q++) {
+        const soap_region_evolution& e = evo[q];
+        if (e.law < SOAP_EVOLVE_NONE || e.law > SOAP_EVOLVE_ASYM_GAUSSIAN) { set_error("evo[%d].law unknown", q); return SOAP_EINVAL; }
+        if (e.law != SOAP_EVOLVE_NONE &&
+            (!is_finite(e.area0_msh) || e.area0_msh < 0 || !is_finite(e.rate_msh_per_day) ||
+             !is_finite(e.t_peak_day) || (e.law == SOAP_EVOLVE_ASYM_GAUSSIAN &&
+                                           (!(e.fwhm_day > 0) || !(std::fabs(e.asymmetry) < 1.0))))) {
+            set_error("evo[%d] has an invalid parameter", q); return SOAP_EINVAL;
+        }
+    }
+    for (int p = 0; p < n_times; p++) {
+        if (!is_finite(times_day[p])) { set_error("times_day[%d] not finite", p); return SOAP_EINVAL; }
+        for (int q = 0; q < n_regions; q++) {
+            const soap_region_evolution& e = evo[q];
+            double r = regions[q].radius_rstar;
+            if (e.law != SOAP_EVOLVE_NONE) r = std::sqrt(evolution_area(e, times_day[p]) * 1e-6);
+            radii[(int64_t)p * n_regions + q] = std::min(r, 1.0);
+        }
+    }
+    return SOAP_OK;
+}
+
+soap_status soap_active_phases(soap_ctx* c, const soap_region* regions, int32_t n_regions,
+                               const double* phases, int32_t n_phases, uint32_t effects,
+                               int32_t precision, void* out, int out_on_device) {
+    clear_error();
+    return active_phases_impl(c, regions, n_regions, phases, n_phases, nullptr, effects, precision, out,
+                              out_on_device);
+}
+
+soap_status soap_active_phases_radii(soap_ctx* c, const soap_region* regions, int32_t n_regions,
+                                     const double* phases, int32_t n_phases, const double* radii,
+                                     uint32_t effects, int32_t precision, void* out, int out_on_device) {
+    clear_error();
+    if (!radii && n_regions > 0 && n_phases > 0) { set_error("radii is NULL"); return SOAP_EINVAL; }
+    return active_phases_impl(c, regions, n_regions, phases, n_phases, radii, effects, precision, out,
+                              out_on_device);
 }
 
 soap_status soap_active_rv(soap_ctx* c, const soap_region* regions, int32_t n_regions,

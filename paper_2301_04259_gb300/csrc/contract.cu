@@ -48,12 +48,16 @@ __global__ void k_contrast(int64_t n_px, double lam_s, double delta, double t_qu
 // InfoMap + per-phase velocity kernels (Alg. 5)
 // ---------------------------------------------------------------------------------------
 // Region centre, cap and cell box per (phase, region), computed once (FP64 trigonometry).
+// radii (optional, [n_phases][n_regions]): per-phase radii of evolving regions (Sect. 4.2.1).
 __global__ void k_region_geo(int N, int n_regions, int n_phases, const RegionDev* regs,
-                             const double* phases, double incl_deg, double alpha, RegionGeo* out) {
+                             const double* phases, double incl_deg, double alpha,
+                             const double* __restrict__ radii, RegionGeo* out) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n_phases * n_regions) return;
     const int p = t / n_regions, q = t % n_regions;
-    out[t] = region_geometry(N, regs[q], phases[p], incl_deg, alpha);
+    RegionDev g = regs[q];
+    if (radii) g.radius = radii[t];
+    out[t] = region_geometry(N, g, phases[p], incl_deg, alpha);
 }
 
 // Blocks (phase p, split).  A visible cell (x, y, mu) belongs to a region iff
@@ -220,7 +224,8 @@ soap_status toeplitz_quiet(soap_ctx* c, int precision, void* dst) {
 soap_status toeplitz_active(soap_ctx* c, const RegionDev* regions_host, int n_regions,
                             const double* class_temp, const int* class_type, int n_class,
                             const double* phases_host, int n_phases, uint32_t effects,
-                            int precision, void* dst) {
+                            int precision, void* dst,
+                            const double* radii_host) {
     const bool f64 = precision == SOAP_FP64;
     const size_t esz = f64 ? 8 : 4;
     const int ncl = n_class > 0 ? n_class : 1;
@@ -259,6 +264,13 @@ soap_status toeplitz_active(soap_ctx* c, const RegionDev* regions_host, int n_re
     SOAP_TRY(ensure(c->phases, pbytes));
     if (n_regions > 0)
         SOAP_TRY(upload_small(c, c->regions.p, regions_host, (size_t)n_regions * sizeof(RegionDev)));
+    const double* radii_dev = nullptr;
+    if (radii_host && n_regions > 0) {
+        const size_t rb = (size_t)n_phases * n_regions * sizeof(double);
+        SOAP_TRY(ensure(c->radii, rb));
+        SOAP_TRY(upload_small(c, c->radii.p, radii_host, rb));
+        radii_dev = c->radii.as<double>();
+    }
     SOAP_TRY(upload_small(c, c->phases.p, phases_host, pbytes));
     // per-phase fixed-point kernels
     int64_t nb = (int64_t)ncl * c->n_mu * c->n_taps;
@@ -286,7 +298,7 @@ soap_status toeplitz_active(soap_ctx* c, const RegionDev* regions_host, int n_re
         SOAP_TIMED(c, SOAP_TIMER_REGIONS,
                    k_region_geo<<<(nt + 31) / 32, 32, 0, c->stream>>>(   // FP64 trig: spread over SMs
                        c->N, n_regions, n_phases, c->regions.as<RegionDev>(), c->phases.as<double>(), c->incl_deg,
-                       c->alpha, c->region_geo.as<RegionGeo>());
+                       c->alpha, radii_dev, c->region_geo.as<RegionGeo>());
                    SOAP_LAUNCHED(c));
     }
     // split each phase over several blocks so that all SMs take part

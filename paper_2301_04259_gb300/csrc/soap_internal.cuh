@@ -169,6 +169,7 @@ struct soap_ctx {
     soap::DevBuf regions;       // region parameters
     soap::DevBuf region_geo;    // region centres and boxes per (phase, region)
     soap::DevBuf phases;
+    soap::DevBuf radii;         // per-(phase, region) radii of evolving regions
     soap::DevBuf out_stage;     // device output when the caller wants host output
     soap::DevBuf partial;       // direct-form and CCF partial sums
     soap::DevBuf ccf_tmp;       // CCF inputs / outputs
@@ -259,7 +260,8 @@ struct RegionDev {      // one region as the kernels see it
 soap_status toeplitz_active(soap_ctx* c, const RegionDev* regions_host, int n_regions,
                             const double* class_temp, const int* class_type, int n_class,
                             const double* phases_host, int n_phases, uint32_t effects,
-                            int precision, void* dst);
+                            int precision, void* dst,
+                            const double* radii_host = nullptr);
 
 // Batched form (batch.cu); variant in 0 .. batch_num_variants() - 1, out [n_phases][n_px] FP32
 // (F, or F - F_q when residual).

@@ -66,6 +66,15 @@ class soap_star_info(ctypes.Structure):
                 ("reserved", ctypes.c_int32)]
 
 
+class soap_region_evolution(ctypes.Structure):
+    _fields_ = [("law", ctypes.c_int32), ("reserved", ctypes.c_int32), ("area0_msh", ctypes.c_double),
+                ("rate_msh_per_day", ctypes.c_double), ("t_peak_day", ctypes.c_double),
+                ("fwhm_day", ctypes.c_double), ("asymmetry", ctypes.c_double)]
+
+
+SOAP_EVOLVE_NONE, SOAP_EVOLVE_LINEAR_GROWTH, SOAP_EVOLVE_LINEAR_DECAY, SOAP_EVOLVE_ASYM_GAUSSIAN = 0, 1, 2, 3
+
+
 class SoapError(RuntimeError):
     def __init__(self, status: int, where: str, message: str):
         super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {message}")
@@ -90,6 +99,8 @@ def _load():
         "soap_set_stream": (i32, [P, P]),
         "soap_synchronize": (i32, [P]),
         "soap_set_host_async": (i32, [P, ctypes.c_int]),
+        "soap_evolve_radii": (i32, [ctypes.POINTER(soap_region_evolution), ctypes.POINTER(soap_region), i32, P, i32, P]),
+        "soap_active_phases_radii": (i32, [P, ctypes.POINTER(soap_region), i32, P, i32, P, u32, i32, P, ctypes.c_int]),
         "soap_set_instrument_resolution": (i32, [P, d]),
         "soap_lower_resolution": (i32, [P, P, P, i32, i32, ctypes.c_int]),
         "soap_active_rv": (i32, [P, ctypes.POINTER(soap_region), i32, P, i32, u32, i32, P, P, i32, d, d, d,
@@ -286,6 +297,37 @@ def soap_lower_resolution(ctx, spectra, out) -> None:
     if f32 != int(_is_f32(out)):
         raise ValueError("spectra and out must have the same dtype")
     _check(_lib.soap_lower_resolution(ctx, ip, op, f32, int(spectra.shape[0]), idev), "soap_lower_resolution")
+
+
+def soap_evolve_radii(evolutions: Sequence[dict], regions: Sequence, times_day) -> np.ndarray:
+    """Radii [n_times][n_regions] of evolving regions; evolutions[q] is a dict with 'law' and
+    any of area0_msh, rate_msh_per_day, t_peak_day, fwhm_day, asymmetry."""
+    n = len(regions)
+    evo = (soap_region_evolution * max(1, n))()
+    for q, e in enumerate(evolutions):
+        evo[q] = soap_region_evolution(law=int(e.get("law", 0)), reserved=0,
+                                       area0_msh=float(e.get("area0_msh", 10000.0)),
+                                       rate_msh_per_day=float(e.get("rate_msh_per_day", 400.0)),
+                                       t_peak_day=float(e.get("t_peak_day", 0.0)),
+                                       fwhm_day=float(e.get("fwhm_day", 10.0)),
+                                       asymmetry=float(e.get("asymmetry", 0.09)))
+    t = np.ascontiguousarray(times_day, dtype=np.float64)
+    out = np.empty((t.size, n), np.float64)
+    _check(_lib.soap_evolve_radii(evo, regions_array(regions), n, ctypes.c_void_p(t.ctypes.data), t.size,
+                                  ctypes.c_void_p(out.ctypes.data)), "soap_evolve_radii")
+    return out
+
+
+def soap_active_phases_radii(ctx, regions: Sequence, phases, radii, effects: int, precision: int, out) -> None:
+    arr = regions_array(regions)
+    ph = np.ascontiguousarray(phases, dtype=np.float64)
+    rr = np.ascontiguousarray(radii, dtype=np.float64)
+    if rr.shape != (ph.size, len(regions)):
+        raise ValueError("radii must be [n_phases][n_regions]")
+    ptr, dev = _ptr(out)
+    _check(_lib.soap_active_phases_radii(ctx, arr, len(regions), ctypes.c_void_p(ph.ctypes.data), ph.size,
+                                         ctypes.c_void_p(rr.ctypes.data), int(effects), int(precision), ptr, dev),
+           "soap_active_phases_radii")
 
 
 def soap_set_host_async(ctx, enabled: bool) -> None:

@@ -114,3 +114,24 @@ def test_acceptance_threshold_calibration():
         acc_frac.append((p2 <= thr).mean())
     assert over <= 6 and over_naive >= 10 and np.mean(acc_frac) > 0.2
     assert calibrate_threshold(np.array([1.0, 2.0]), np.array([50.0, 1.0])) == 0.0
+
+
+
+def test_library_evolution_radii_equal_the_oracle_laws():
+    """soap_evolve_radii (host code of the library) against the oracle's laws (Sect. 4.2.1)."""
+    from paper_2301_04259_gb300 import _build
+    _build.build()
+    from paper_2301_04259_gb300 import soap as S
+    from paper_2301_04259_gb300.synth import Region, SPOT
+    from oracle import oracle as O
+    regs = [Region(SPOT, 30.0, 180.0, 0.07, 4800.0)] * 4
+    evo = [{"law": 0}, {"law": 1, "area0_msh": 10000.0, "rate_msh_per_day": 400.0},
+           {"law": 2, "area0_msh": 10000.0, "rate_msh_per_day": 400.0},
+           {"law": 3, "area0_msh": 10000.0, "t_peak_day": 12.0, "fwhm_day": 10.0, "asymmetry": 0.09}]
+    t = np.linspace(-5.0, 40.0, 91)
+    r = S.soap_evolve_radii(evo, regs, t)
+    assert r.shape == (91, 4)
+    np.testing.assert_array_equal(r[:, 0], 0.07)
+    np.testing.assert_allclose(r[:, 1], np.minimum(1.0, O.evolution_radius(O.evolution_area(1, t))), rtol=1e-14)
+    np.testing.assert_allclose(r[:, 2], O.evolution_radius(O.evolution_area(2, t)), rtol=1e-14, atol=1e-300)
+    np.testing.assert_allclose(r[:, 3], O.evolution_radius(O.evolution_area(3, t, t_peak_day=12.0)), rtol=1e-13)
