@@ -77,7 +77,7 @@ def _load():
     lib.or_infomap_grid.argtypes = [i32, d, d, i32, P, P, P, d, P]
     lib.or_active.restype = i32
     lib.or_active.argtypes = [i32, d, d, d, d, d, i32, P, d, d, i64, d, P, P,
-                              i32, P, P, P, P, P, i32, P, u32, P, i64, P, P]
+                              i32, P, P, P, P, P, i32, P, u32, P, i64, P, P, i32]
     lib.or_ccf.restype = i32
     lib.or_ccf.argtypes = [P, i32, i64, d, d, P, P, i32, d, d, d, i32, P]
     lib.or_num_threads.restype = i32
@@ -155,12 +155,15 @@ EFFECT_TOT, EFFECT_FLUX, EFFECT_BCONV = 1, 2, 4
 
 
 def active(star, quiet_local, active_local, regions, phases, effects=EFFECT_TOT, pix=None,
-           return_delta=False, radii=None):
+           return_delta=False, radii=None, facula_mu=False):
     """Spectra of the active star per phase (Alg. 5, Eqs. 1-4).
 
     active_local: dict type -> [n_mu, n_px] (1 spot, 2 facula; facula defaults to spot).
     radii: optional [n_phases, n_regions] region radii per phase (evolving regions); each phase
     is then computed with its own radii.
+    facula_mu: facula cells take the temperature T_quiet + dT_f(mu_b) of their mu bin,
+    dT_f(mu) = 250.9 - 407.7 mu + 190.9 mu^2 (SOAP 2.0's limb brightening, Sect. 4.3.1), instead
+    of their region's temperature.
     Returns F [n_eff, n_phases, n_sample] (and Delta F if return_delta)."""
     if radii is not None:
         import dataclasses
@@ -168,7 +171,8 @@ def active(star, quiet_local, active_local, regions, phases, effects=EFFECT_TOT,
         parts = []
         for p, ph in enumerate(np.atleast_1d(np.asarray(phases, np.float64))):
             regs = [dataclasses.replace(r, radius_rstar=float(radii[p, q])) for q, r in enumerate(regions)]
-            parts.append(active(star, quiet_local, active_local, regs, [ph], effects, pix, return_delta))
+            parts.append(active(star, quiet_local, active_local, regs, [ph], effects, pix, return_delta,
+                                facula_mu=facula_mu))
         if return_delta:
             return (np.concatenate([a for a, _ in parts], axis=1), np.concatenate([b for _, b in parts], axis=1))
         return np.concatenate(parts, axis=1)
@@ -191,7 +195,7 @@ def active(star, quiet_local, active_local, regions, phases, effects=EFFECT_TOT,
                            star.diff_rot_alpha, star.n_mu, _p(muv), star.lambda_start_A,
                            star.lambda_end_A, star.n_px, star.t_quiet_K, _p(q), _p(act), nr,
                            _p(rtype), _p(lat), _p(lon), _p(rad), _p(tmp), ph.size, _p(ph),
-                           effects, _p(pix), ns, _p(F), _p(dF))
+                           effects, _p(pix), ns, _p(F), _p(dF), int(bool(facula_mu)))
     if rc != 0:
         raise RuntimeError("or_active failed")
     return (F, dF) if return_delta else F

@@ -314,8 +314,8 @@ int or_active(int N, double vsini, double incl_deg, double u1, double u2, double
               int n_regions, const int32_t* rtype, const double* lat, const double* lon,
               const double* radius, const double* temp, int n_phases, const double* phases,
               uint32_t effects, const int64_t* pix, int64_t n_sample, double* out_F,
-              double* out_dF) {
-    if (n_regions > 64 || n_regions < 0) return -1;
+              double* out_dF, int facula_mu) {
+    if (n_regions > 64 || n_regions < 0 || n_mu > 64) return -1;
     double* lam = (double*)malloc(sizeof(double) * n_px);
     or_grid(lambda_start, lambda_end, n_px, lam);
     double delta = or_delta(lambda_start, lambda_end, n_px);
@@ -342,6 +342,14 @@ int or_active(int N, double vsini, double incl_deg, double u1, double u2, double
         double Fq = or_val(&fq);
         double C[64];
         for (int r = 0; r < n_regions; r++) C[r] = or_planck_ratio(lam[m], temp[r], t_quiet);
+        /* facula limb brightening (Sect. 4.3.1, SOAP 2.0's model): a facula cell of mu bin b has
+         * the temperature T_quiet + dT_f(mu_b), dT_f(mu) = 250.9 - 407.7 mu + 190.9 mu^2 */
+        double Cf[64];
+        if (facula_mu)
+            for (int b = 0; b < n_mu; b++) {
+                double mu = mu_values[b];
+                Cf[b] = or_planck_ratio(lam[m], t_quiet + (250.9 - 407.7 * mu + 190.9 * mu * mu), t_quiet);
+            }
         for (int p = 0; p < n_phases; p++) {
             const int32_t* own = owner + (int64_t)p * d.n;
             or_sum dtot = {0, 0}, dflux = {0, 0}, dbconv = {0, 0};
@@ -353,9 +361,10 @@ int or_active(int N, double vsini, double incl_deg, double u1, double u2, double
                 double sq = or_shift_interp(lam, Sq, n_px, delta, d.beta[c], m);
                 double sa = or_shift_interp(lam, Sa, n_px, delta, d.beta[c], m);
                 double I = d.I[c];
-                or_add(&dflux, I * (sq - C[r] * sq));      /* Eq. 1 */
+                double Cc = (facula_mu && rtype[r] == 2) ? Cf[d.bin[c]] : C[r];
+                or_add(&dflux, I * (sq - Cc * sq));        /* Eq. 1 */
                 or_add(&dbconv, I * (sq - sa));            /* Eq. 2 */
-                or_add(&dtot, I * (sq - C[r] * sa));       /* Eq. 3 */
+                or_add(&dtot, I * (sq - Cc * sa));         /* Eq. 3 */
             }
             for (int e = 0; e < n_eff; e++) {
                 double dF = eff_list[e] == 1 ? or_val(&dtot) : eff_list[e] == 2 ? or_val(&dflux) : or_val(&dbconv);

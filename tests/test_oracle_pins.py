@@ -764,3 +764,40 @@ def test_per_phase_radii_reduce_to_fixed_regions(small_case):
     got = O.active(c.star, c.quiet, c.active, c.regions, phases, effects=1, radii=radii)
     q = O.quiet(c.star, c.quiet)
     np.testing.assert_allclose(got[0, 2], q, rtol=0, atol=1e-15 * np.abs(q).max())
+
+
+
+# ---------------------------------------------------------------------------------------
+# facula limb brightening (Sect. 4.3.1: SOAP 2.0's dT_f(mu))
+# ---------------------------------------------------------------------------------------
+def _dT_f(mu):
+    return 250.9 - 407.7 * mu + 190.9 * mu * mu
+
+
+def test_facula_mu_model_with_one_mu_bin_is_a_facula_at_that_temperature():
+    """With a single tabulated mu every facula cell has dT_f(mu_0): the mu-dependent model must
+    equal the plain model with the facula's temperature set to T_quiet + dT_f(mu_0)."""
+    import dataclasses
+    c = synth.make_case(9, name="fmu1", grid_n=36, lambda_start=6000.0, lambda_end=6010.0, n_px=500,
+                        mu_values=(0.62,), n_lines=10, depth_law="uniform", sigma_law="angstrom",
+                        vsini_kms=3.0, incl_deg=80.0, n_phases=4,
+                        regions=[Region(FACULA, 15.0, 0.0, 0.3, 6100.0), Region(SPOT, 15.0, 5.0, 0.1, 4800.0)])
+    got = O.active(c.star, c.quiet, c.active, c.regions, c.phases, effects=7, facula_mu=True)
+    regs = [dataclasses.replace(c.regions[0], temp_K=c.star.t_quiet_K + _dT_f(0.62)), c.regions[1]]
+    ref = O.active(c.star, c.quiet, c.active, regs, c.phases, effects=7)
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-14 * np.abs(ref).max())
+
+
+def test_facula_mu_model_only_changes_facula_cells(small_case):
+    """Spots are untouched by the facula model, and so is the convective-blueshift effect
+    (Eq. 2 has no contrast); the flux effect of the faculae changes (their temperature now
+    follows dT_f(mu) instead of the region's 6100 K)."""
+    c = small_case
+    spot_only = [r for r in c.regions if r.type == SPOT]
+    a = O.active(c.star, c.quiet, c.active, spot_only, c.phases, effects=7, facula_mu=True)
+    b = O.active(c.star, c.quiet, c.active, spot_only, c.phases, effects=7)
+    np.testing.assert_array_equal(a, b)
+    a = O.active(c.star, c.quiet, c.active, c.regions, c.phases, effects=7, facula_mu=True)
+    b = O.active(c.star, c.quiet, c.active, c.regions, c.phases, effects=7)
+    np.testing.assert_array_equal(a[2], b[2])
+    assert np.abs(a[1] - b[1]).max() > 1e-6 * np.abs(b[1]).max()
