@@ -292,6 +292,14 @@ soap_status soap_set_instrument_resolution(soap_ctx* ctx, double resolving_power
 soap_status soap_lower_resolution(soap_ctx* ctx, const void* in, void* out, int32_t spectra_f32,
                                   int32_t n_spec, int on_device);
 
+/* Facula limb brightening (Sect. 4.3.1: the SOAP 2.0 model the paper quotes).  When enabled,
+ * a facula cell takes the temperature T_quiet + dT_f(mu_b) of its mu bin, dT_f(mu) =
+ * 250.9 - 407.7 mu + 190.9 mu^2 (K), instead of its region's temp_K; the contrast then has one
+ * row per (class, mu bin) and the Toeplitz contraction folds each bin's sum with its own row
+ * (exact: the contrast multiplies on the common grid, Eqs. 1-3).  Off by default.  Applies to
+ * soap_active_phases(_radii) and soap_active_rv; the batched form does not use it. */
+soap_status soap_set_facula_limb_brightening(soap_ctx* ctx, int enabled);
+
 /* Active-region size evolution (Sect. 4.2.1).  The paper names three laws and their
  * parameters; the formulas are readings:
  *  SOAP_EVOLVE_NONE            the region keeps its radius_rstar;

@@ -564,6 +564,13 @@ soap_status soap_synchronize(soap_ctx* c) {
     return SOAP_OK;
 }
 
+soap_status soap_set_facula_limb_brightening(soap_ctx* c, int enabled) {
+    clear_error();
+    if (!c) { set_error("ctx is NULL"); return SOAP_EINVAL; }
+    c->facula_mu = enabled != 0;
+    return SOAP_OK;
+}
+
 soap_status soap_set_host_async(soap_ctx* c, int enabled) {
     clear_error();
     if (!c) { set_error("ctx is NULL"); return SOAP_EINVAL; }

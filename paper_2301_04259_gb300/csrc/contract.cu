@@ -73,7 +73,7 @@ __global__ void k_phase_hist(int N, int n_regions, const RegionGeo* __restrict__
                              int tap_min, int n_taps, int n_mu, int n_class, long long* kout,
                              int use_smem, int PB, double inv_scale, int fx_bits, int64_t row_len, int64_t pad,
                              long long* toff, int* gstart, double* c64, float* c32, int max_taps,
-                             int* counters, int taps_smem, unsigned int* flags) {
+                             int* counters, int taps_smem, unsigned int* flags, int* bstart) {
     __shared__ RegionGeo sg[SOAP_MAX_REGIONS];
     extern __shared__ long long hist_sm[];
     const int p = blockIdx.x;
@@ -128,7 +128,7 @@ __global__ void k_phase_hist(int N, int n_regions, const RegionGeo* __restrict__
     if (s_last) {
         __threadfence();
         build_taps_dev(kout, pbk, (int)gridDim.x, n_class, n_mu, n_taps, tap_min, PB, 1, inv_scale, fx_bits, row_len,
-                       pad, toff, gstart, c64, c32, max_taps, taps_smem ? hist_sm : nullptr, flags);
+                       pad, toff, gstart, c64, c32, max_taps, taps_smem ? hist_sm : nullptr, flags, bstart);
     }
 }
 
@@ -140,14 +140,15 @@ template <typename T, int PB, int R, int THREADS>
 __global__ void __launch_bounds__(THREADS)
 k_contract(int64_t n_px, Rows<T> rows, const long long* __restrict__ toff, const int* __restrict__ gstart,
            int G, int max_taps, const T* __restrict__ coefs, ClassTypes ctype, const T* __restrict__ contrast,
-           const T* __restrict__ fq, int n_phases, EffectList effs, T* __restrict__ out) {
+           const T* __restrict__ fq, int n_phases, EffectList effs, T* __restrict__ out,
+           const int* __restrict__ bstart, int n_mu) {
     const int pb = blockIdx.y;
     const int np = min(PB, n_phases - pb * PB);
     T* out_rows = out + (int64_t)blockIdx.z * n_phases * n_px + (int64_t)pb * PB * n_px;
     const TableContrast<T> con{contrast, n_px, ctype};
     contract_tile<T, PB, R, THREADS>(n_px, rows, toff + (int64_t)pb * max_taps, gstart + (int64_t)pb * (G + 1), G,
                                      coefs + (int64_t)pb * max_taps * PB, con, fq, effs.e[blockIdx.z], blockIdx.x,
-                                     np, out_rows);
+                                     np, out_rows, bstart ? bstart + (int64_t)pb * (G * n_mu + 1) : nullptr, n_mu);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -163,14 +164,15 @@ static soap_status launch_contract(soap_ctx* c, int n_blocks, int G, int max_tap
                                    const long long* toff, const int* gstart, const T* coefs,
                                    const ClassTypes& ct, const T* contrast, const T* fq,
                                    int n_phases, const EffectList& el, int n_eff, T* out,
-                                   const T* q, const T* a0, const T* a1) {
+                                   const T* q, const T* a0, const T* a1, const int* bstart = nullptr) {
     Rows<T> rows;
     rows.q = q; rows.a[0] = a0; rows.a[1] = a1;
     int64_t tiles = (c->n_px + (int64_t)THREADS * R - 1) / ((int64_t)THREADS * R);
     dim3 grid((unsigned)tiles, (unsigned)n_blocks, (unsigned)n_eff);
     SOAP_TIMED(c, fq ? SOAP_TIMER_CONTRACT : SOAP_TIMER_CONTRACT_QUIET,
                k_contract<T, PB, R, THREADS><<<grid, THREADS, 0, c->stream>>>(
-                   c->n_px, rows, toff, gstart, G, max_taps, coefs, ct, contrast, fq, n_phases, el, out);
+                   c->n_px, rows, toff, gstart, G, max_taps, coefs, ct, contrast, fq, n_phases, el, out,
+                   bstart, c->n_mu);
                SOAP_LAUNCHED(c));
     return SOAP_OK;
 }
@@ -191,14 +193,18 @@ constexpr int kPB32 = SOAP_PB32, kR32 = SOAP_R32, kT32 = 128;
 
 // tap-table + coefficient scratch for a kernel set kfix with n_phases "phases" in blocks of PB
 static soap_status tap_buffers(soap_ctx* c, int n_phases, int n_class, int PB, int mode, long long** toff,
-                               int** gstart, double** c64, float** c32, int* n_blocks, int* G, int* max_taps) {
+                               int** gstart, double** c64, float** c32, int* n_blocks, int* G, int* max_taps,
+                               int** bstart = nullptr) {
     *G = mode == 0 ? 1 : 1 + n_class;
     *n_blocks = (n_phases + PB - 1) / PB;
     *max_taps = *G * c->n_mu * c->n_taps;
     size_t tb = (size_t)*n_blocks * *max_taps * sizeof(long long);
     size_t gb = (size_t)*n_blocks * (*G + 1) * sizeof(int);
     size_t off_g = (tb + 255) / 256 * 256;
-    SOAP_TRY(ensure(c->jobs, off_g + gb));
+    size_t off_b = (off_g + gb + 255) / 256 * 256;
+    size_t bb = bstart ? (size_t)*n_blocks * (*G * c->n_mu + 1) * sizeof(int) : 0;
+    SOAP_TRY(ensure(c->jobs, off_b + bb));
+    if (bstart) *bstart = (int*)(c->jobs.as<char>() + off_b);
     size_t cb64 = (size_t)*n_blocks * *max_taps * PB * sizeof(double);
     size_t off32 = (cb64 + 255) / 256 * 256;
     SOAP_TRY(ensure(c->coefs, off32 + (size_t)*n_blocks * *max_taps * PB * sizeof(float)));
@@ -232,13 +238,47 @@ soap_status toeplitz_active(soap_ctx* c, const RegionDev* regions_host, int n_re
     // quiet integral for Eq. 4 in the output precision
     SOAP_TRY(ensure(c->fq, (size_t)c->n_px * esz));
     SOAP_TRY(toeplitz_quiet(c, precision, c->fq.p));
-    // contrast per class
-    size_t cbytes = (size_t)ncl * c->n_px;
+    // contrast per class, or per (class, mu bin) with mu-dependent facula temperatures
+    bool has_fac = false;
+    for (int k = 0; k < n_class; k++) has_fac |= class_type[k] == SOAP_FACULA;
+    const bool per_bin = c->facula_mu && has_fac;
+    const int n_rows = per_bin ? ncl * c->n_mu : ncl;
+    size_t cbytes = (size_t)n_rows * c->n_px;
     size_t off32 = (cbytes * 8 + 255) / 256 * 256;
     SOAP_TRY(ensure(c->contrast, off32 + cbytes * 4));
     double* con64 = c->contrast.as<double>();
     float* con32 = (float*)(c->contrast.as<char>() + off32);
-    if (n_class > 0) {
+    if (per_bin) {
+        // facula rows: T_quiet + dT_f(mu_b), dT_f(mu) = 250.9 - 407.7 mu + 190.9 mu^2 (Sect. 4.3.1,
+        // SOAP 2.0's limb brightening); spot rows repeat the class temperature
+        const double hck = kPlanckH * kLightSI / kBoltzmann * 1e10;
+        std::vector<double> temps((size_t)n_rows);
+        std::vector<float> a32((size_t)n_rows);
+        for (int k = 0; k < n_class; k++)
+            for (int b = 0; b < c->n_mu; b++) {
+                const double mu = c->mu_values[b];
+                const double t = class_type[k] == SOAP_FACULA ? c->t_quiet + (250.9 - 407.7 * mu + 190.9 * mu * mu)
+                                                              : class_temp[k];
+                temps[(size_t)k * c->n_mu + b] = t;
+                a32[(size_t)k * c->n_mu + b] = (float)(hck / (c->lam_s * t));
+            }
+        SOAP_TRY(ensure(c->contrast_t, (size_t)n_rows * (sizeof(double) + sizeof(float)) + 256));
+        double* t_dev = c->contrast_t.as<double>();
+        float* a_dev = reinterpret_cast<float*>(c->contrast_t.as<char>() + ((size_t)n_rows * 8 + 255) / 256 * 256);
+        SOAP_TRY(upload_small(c, t_dev, temps.data(), temps.size() * sizeof(double)));
+        SOAP_TRY(upload_small(c, a_dev, a32.data(), a32.size() * sizeof(float)));
+        dim3 cgrid((unsigned)grid_cap(c->n_px, 256, 152 * 2), (unsigned)std::min(n_rows, 16));
+        if (f64)
+            SOAP_TIMED(c, SOAP_TIMER_CONTRAST,
+                       k_contrast_rows<<<cgrid, 256, 0, c->stream>>>(c->n_px, c->lam_s, c->delta, c->t_quiet, n_rows,
+                                                                     t_dev, con64, con32);
+                       SOAP_LAUNCHED(c));
+        else
+            SOAP_TIMED(c, SOAP_TIMER_CONTRAST,
+                       k_contrast_rows32<<<cgrid, 256, 0, c->stream>>>(
+                           c->n_px, (float)(hck / (c->lam_s * c->t_quiet)), (float)c->delta, n_rows, a_dev, con32);
+                       SOAP_LAUNCHED(c));
+    } else if (n_class > 0) {
         ClassTemps tt{};
         ClassConsts cc{};
         const double hck = kPlanckH * kLightSI / kBoltzmann * 1e10;
@@ -279,8 +319,9 @@ soap_status toeplitz_active(soap_ctx* c, const RegionDev* regions_host, int n_re
     long long* kfix = c->kphase.as<long long>();
     // tap tables are built by the last block of each phase block (fused into k_phase_hist)
     const int PB = f64 ? kPB64 : kPB32;
-    long long* toff; int* gstart; double* c64; float* c32; int nbk, G, mt;
-    SOAP_TRY(tap_buffers(c, n_phases, ncl, PB, 1, &toff, &gstart, &c64, &c32, &nbk, &G, &mt));
+    long long* toff; int* gstart; double* c64; float* c32; int nbk, G, mt; int* bstart = nullptr;
+    SOAP_TRY(tap_buffers(c, n_phases, ncl, PB, 1, &toff, &gstart, &c64, &c32, &nbk, &G, &mt,
+                         per_bin ? &bstart : nullptr));
     SOAP_TRY(ensure(c->job_counters, (size_t)nbk * sizeof(int)));
     SOAP_CUDA(cudaMemsetAsync(c->job_counters.p, 0, (size_t)nbk * sizeof(int), c->stream));
     const size_t hist_bytes = (size_t)nb * sizeof(long long);
@@ -309,7 +350,7 @@ soap_status toeplitz_active(soap_ctx* c, const RegionDev* regions_host, int n_re
                    c->N, n_regions, c->region_geo.as<RegionGeo>(), c->cell_mu, c->cell_mu32, c->cell_j,
                    c->cell_bin, c->cell_k0, c->cell_k1, c->tap_min, c->n_taps, c->n_mu, ncl, kfix,
                    use_smem, PB, std::ldexp(1.0, -c->fx_bits), c->fx_bits, c->row_len, c->pad, toff, gstart, c64, c32,
-                   mt, c->job_counters.as<int>(), taps_smem, c->flags);
+                   mt, c->job_counters.as<int>(), taps_smem, c->flags, bstart);
                SOAP_LAUNCHED(c));
     ClassTypes ct{};
     for (int k = 0; k < n_class; k++) ct.t[k] = class_type[k];
@@ -325,10 +366,10 @@ soap_status toeplitz_active(soap_ctx* c, const RegionDev* regions_host, int n_re
     if (f64)
         return launch_contract<double, kPB64, kR64, kT64>(c, nbk, G, mt, toff, gstart, c64, ct, con64,
                                                          c->fq.as<double>(), n_phases, el, n_eff,
-                                                         (double*)dst, c->q64, a64s, a64f);
+                                                         (double*)dst, c->q64, a64s, a64f, bstart);
     return launch_contract<float, kPB32, kR32, kT32>(c, nbk, G, mt, toff, gstart, c32, ct, con32,
                                                     c->fq.as<float>(), n_phases, el, n_eff,
-                                                    (float*)dst, c->q32, a32s, a32f);
+                                                    (float*)dst, c->q32, a32s, a32f, bstart);
 }
 
 }  // namespace soap

@@ -72,11 +72,15 @@ struct PlanckContrast32 {
     }
 };
 
+// bs (optional): per-(group, mu bin) tap starts [G n_mu + 1]; with it each class is folded
+// per bin, acc += C_(cl n_mu + b)[m] . sum_(taps of bin b) (a contrast row per class and bin:
+// mu-dependent facula temperatures).
 template <typename T, int PB, int R, int THREADS, class Con>
 __device__ __forceinline__ void contract_tile(int64_t n_px, const Rows<T>& rows, const long long* __restrict__ toff,
                                               const int* __restrict__ gs, int G, const T* __restrict__ cb,
                                               const Con& con, const T* __restrict__ fq, int eff, int64_t tile,
-                                              int np, T* __restrict__ out_rows) {
+                                              int np, T* __restrict__ out_rows, const int* __restrict__ bs = nullptr,
+                                              int n_mu = 0) {
     // Rows are padded past round_up(n_px, 1024) + max tap, so every tap of every pixel of the
     // last tile reads inside its row; only the per-pixel inputs below need a clamped index.
     const int64_t m0 = tile * THREADS * R + threadIdx.x;
@@ -110,6 +114,42 @@ __device__ __forceinline__ void contract_tile(int64_t n_px, const Rows<T>& rows,
 #pragma unroll
                 for (int r = 0; r < R; r++) acc[p][r] = fma(cv[p], s[r], acc[p][r]);
         }
+    }
+    // classes with a contrast row per mu bin: fold each bin's sum separately
+    if (bs) {
+        for (int g = 1; g < G; g++) {
+            if (gs[g] == gs[g + 1]) continue;
+            const int cl = g - 1;
+            const T* base = (eff == SOAP_EFFECT_FLUX ? rows.q : rows.a[con.type(cl) == SOAP_FACULA ? 1 : 0]) + m0;
+            for (int b = 0; b < n_mu; b++) {
+                const int t0 = bs[g * n_mu + b], t1 = bs[g * n_mu + b + 1];
+                if (t0 == t1) continue;
+                T tmp[PB][R];
+#pragma unroll
+                for (int p = 0; p < PB; p++)
+#pragma unroll
+                    for (int r = 0; r < R; r++) tmp[p][r] = T(0);
+                for (int t = t0; t < t1; t++) {
+                    const T* row = base + __ldg(toff + t);
+                    T s[R];
+#pragma unroll
+                    for (int r = 0; r < R; r++) s[r] = __ldg(row + r * THREADS);
+                    T cv[PB];
+                    load_coefs<T, PB>(cb + (int64_t)t * PB, cv);
+#pragma unroll
+                    for (int p = 0; p < PB; p++)
+#pragma unroll
+                        for (int r = 0; r < R; r++) tmp[p][r] = fma(cv[p], s[r], tmp[p][r]);
+                }
+#pragma unroll
+                for (int r = 0; r < R; r++) {
+                    const T cr = eff == SOAP_EFFECT_BCONV ? T(1) : con.at(cl * n_mu + b, mcl[r]);
+#pragma unroll
+                    for (int p = 0; p < PB; p++) acc[p][r] = fma(cr, tmp[p][r], acc[p][r]);
+                }
+            }
+        }
+        G = 1;                                             // classes done
     }
     // classes: tmp = sum_b K_cl,b * S, then acc += C_cl . tmp (TOT, FLUX) or tmp (BCONV)
     for (int g = 1; g < G; g++) {
@@ -154,6 +194,35 @@ __device__ __forceinline__ void contract_tile(int64_t n_px, const Rows<T>& rows,
     }
 }
 
+
+// Contrast rows from a device list of temperatures (one row per class and mu bin when facula
+// temperatures depend on mu): FP64 rows (and their FP32 copies).
+static __global__ void k_contrast_rows(int64_t n_px, double lam_s, double delta, double t_quiet, int n_rows,
+                                       const double* __restrict__ temps, double* c64, float* c32) {
+    const double hck = kPlanckH * kLightSI / kBoltzmann * 1e10;   // Angstrom Kelvin
+    for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < n_px;
+         m += (int64_t)gridDim.x * blockDim.x) {
+        const double lam = lam_s * exp((double)m * delta);
+        const double xq = expm1(hck / (lam * t_quiet));
+        for (int k = blockIdx.y; k < n_rows; k += gridDim.y) {
+            const double v = xq / expm1(hck / (lam * temps[k]));
+            c64[(int64_t)k * n_px + m] = v;
+            c32[(int64_t)k * n_px + m] = (float)v;
+        }
+    }
+}
+
+// FP32 rows with the operations of k_contrast32 (a = h c / (lambda_s k T) per row).
+static __global__ void k_contrast_rows32(int64_t n_px, float aq, float fd, int n_rows, const float* __restrict__ a,
+                                         float* c32) {
+    for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < n_px;
+         m += (int64_t)gridDim.x * blockDim.x) {
+        const float inv = expf(-(float)m * fd);            // lambda_s / lambda_m
+        const float xq = expm1f(aq * inv);
+        for (int k = blockIdx.y; k < n_rows; k += gridDim.y)
+            c32[(int64_t)k * n_px + m] = xq / expm1f(a[k] * inv);
+    }
+}
 
 // FP32 contrast per class (relative error ~1e-7, inside the mixed path's 2e-6).
 struct ClassConsts {

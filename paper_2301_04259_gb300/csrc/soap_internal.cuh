@@ -144,6 +144,7 @@ struct soap_ctx {
     double* a64[2] = {nullptr, nullptr};   // [0] spot, [1] facula
     float* a32[2] = {nullptr, nullptr};
     bool active_set[2] = {false, false};
+    bool facula_mu = false;                // facula temperature T_quiet + dT_f(mu) per mu bin
     bool q64_ok = false;                   // float64 rows hold the last quiet upload
     bool a64_ok[2] = {false, false};       // (a float32 upload fills the float32 rows only)
 
@@ -161,7 +162,8 @@ struct soap_ctx {
     // scratch (grow-only)
     soap::DevBuf stage_in;      // host -> device staging of spectra
     soap::DevBuf fq;            // quiet spectrum (fp64 or fp32) for Eq. 4
-    soap::DevBuf contrast;      // [n_class][n_px] fp64 + fp32
+    soap::DevBuf contrast;      // [n_class][n_px] fp64 + fp32 (per (class, mu bin) rows with facula_mu)
+    soap::DevBuf contrast_t;    // per-row temperatures / FP32 constants of the per-bin contrast
     soap::DevBuf kphase;        // fixed-point kernels [n_phases][n_class][n_mu][n_taps]
     soap::DevBuf jobs;          // tap tables (row offsets + group starts)
     soap::DevBuf coefs;         // tap coefficients (fp64 and fp32)
@@ -372,7 +374,7 @@ __device__ __forceinline__ void build_taps_dev(const long long* __restrict__ kfi
                                                double inv_scale, int fx_bits, int64_t row_len, int64_t pad,
                                                long long* toff,
                                                int* gstart, double* c64, float* c32, int max_taps,
-                                               long long* s_k, unsigned int* flags) {
+                                               long long* s_k, unsigned int* flags, int* bstart = nullptr) {
     __shared__ int s_lo[(1 + SOAP_MAX_CLASSES) * SOAP_MAX_MU];
     __shared__ int s_hi[(1 + SOAP_MAX_CLASSES) * SOAP_MAX_MU];
     __shared__ int s_off[(1 + SOAP_MAX_CLASSES) * SOAP_MAX_MU];
@@ -471,6 +473,11 @@ __device__ __forceinline__ void build_taps_dev(const long long* __restrict__ kfi
         return;
     }
     for (int g = threadIdx.x; g <= G; g += blockDim.x) gs[g] = g < G ? s_off[g * n_mu] : total;
+    // per-(group, bin) tap starts, for contractions that fold each bin separately
+    if (bstart) {
+        int* bs = bstart + (int64_t)pb * (ngb + 1);
+        for (int t = threadIdx.x; t <= ngb; t += blockDim.x) bs[t] = t < ngb ? s_off[t] : total;
+    }
     // row offsets and coefficients [tap][PB]: one warp per (group, bin)
     for (int t = warp; t < ngb; t += nw) {
         if (s_hi[t] < s_lo[t]) continue;

@@ -99,6 +99,7 @@ def _load():
         "soap_set_stream": (i32, [P, P]),
         "soap_synchronize": (i32, [P]),
         "soap_set_host_async": (i32, [P, ctypes.c_int]),
+        "soap_set_facula_limb_brightening": (i32, [P, ctypes.c_int]),
         "soap_evolve_radii": (i32, [ctypes.POINTER(soap_region_evolution), ctypes.POINTER(soap_region), i32, P, i32, P]),
         "soap_active_phases_radii": (i32, [P, ctypes.POINTER(soap_region), i32, P, i32, P, u32, i32, P, ctypes.c_int]),
         "soap_set_instrument_resolution": (i32, [P, d]),
@@ -328,6 +329,10 @@ def soap_active_phases_radii(ctx, regions: Sequence, phases, radii, effects: int
     _check(_lib.soap_active_phases_radii(ctx, arr, len(regions), ctypes.c_void_p(ph.ctypes.data), ph.size,
                                          ctypes.c_void_p(rr.ctypes.data), int(effects), int(precision), ptr, dev),
            "soap_active_phases_radii")
+
+
+def soap_set_facula_limb_brightening(ctx, enabled: bool) -> None:
+    _check(_lib.soap_set_facula_limb_brightening(ctx, int(bool(enabled))), "soap_set_facula_limb_brightening")
 
 
 def soap_set_host_async(ctx, enabled: bool) -> None:

@@ -33,7 +33,8 @@ def test_header_declares_the_boundary():
     for n in ("soap_init_star", "soap_quiet_spectrum", "soap_active_phases", "soap_rv_ccf",
               "soap_active_rv", "soap_set_host_async", "soap_set_quiet_spectrum_f32",
               "soap_set_active_spectrum_f32", "soap_set_instrument_resolution", "soap_lower_resolution",
-              "soap_evolve_radii", "soap_active_phases_radii", "soap_free", "soap_last_error"):
+              "soap_evolve_radii", "soap_active_phases_radii", "soap_set_facula_limb_brightening",
+              "soap_free", "soap_last_error"):
         assert n in names
 
 

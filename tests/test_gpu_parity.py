@@ -342,3 +342,31 @@ def test_evolving_regions_match_oracle(S, cfg1, prec):
     tol = TOL64 if prec == "fp64" else TOL32
     q = O.quiet(c.star, c.quiet)
     assert rel(out.double().cpu().numpy(), ref, np.abs(q).max()) <= tol
+
+
+
+@pytest.mark.parametrize("which", ["complex_facula", "config2_sample"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_facula_limb_brightening_matches_oracle(S, complex_case, cfg2, which, prec):
+    """Sect. 4.3.1: faculae at T_quiet + dT_f(mu_b) (one contrast row per class and mu bin, each
+    bin folded separately in the contraction) against the oracle's per-cell model; all effects.
+    The full-size case samples 60 pixels of 3 phases."""
+    p = S.SOAP_FP64 if prec == "fp64" else S.SOAP_FP32
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    tol = TOL64 if prec == "fp64" else TOL32
+    if which == "complex_facula":
+        c, phases, pix = complex_case, complex_case.phases, None
+    else:
+        c, phases = cfg2, cfg2.phases[::40]
+        pix = _sample_pixels(cfg2.star.n_px, seed=3, n=60)
+    ref = O.active(c.star, c.quiet, c.active, c.regions, phases, effects=7, facula_mu=True, pix=pix)
+    q = O.quiet(c.star, c.quiet, pix=pix)
+    with S.Disk(c.star, _t(c.quiet), {k: _t(v) for k, v in c.active.items()}) as d:
+        S.soap_set_facula_limb_brightening(d.ctx, True)
+        out = torch.empty((3, len(phases), c.star.n_px), dtype=dt, device=DEV)
+        S.soap_active_phases(d.ctx, c.regions, phases, 7, p, out)
+        torch.cuda.synchronize()
+    got = out.double().cpu().numpy()
+    if pix is not None:
+        got = got[:, :, pix]
+    assert rel(got, ref, np.abs(q).max()) <= tol
