@@ -160,7 +160,10 @@ k_lsf_gen(const T* __restrict__ in, T* __restrict__ out, int64_t n_px, int K, co
     }
 }
 
-constexpr int kLsfE = 8, kLsfKmax = 12, kLsfThreads = 128;
+#ifndef SOAP_LSF_E
+#define SOAP_LSF_E 8
+#endif
+constexpr int kLsfE = SOAP_LSF_E, kLsfKmax = 12, kLsfThreads = 128;
 
 template <typename T>
 static soap_status launch_lsf_t(soap_ctx* c, const T* in, T* out, int64_t n_spec) {
