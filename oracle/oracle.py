@@ -15,6 +15,9 @@ Functions follow the paper (arXiv 2301.04259):
   evolution_area(...), evolution_radius(...)  Sect. 4.2.1: active-region size evolution
                    (linear growth, linear decay, asymmetric Gaussian); active(..., radii=) takes
                    per-phase radii.
+  inject_bisectors(...) Sect. 4.3 (Convec.model): each point of a normalised local spectrum
+                   moved by the velocity of its normalised depth on a target bisector minus the
+                   original one, then re-sampled on the grid.
   lower_resolution(...) Sect. 3.3 after Eq. 4 (Alg. 5): the integrated spectra degraded to an
                    instrument's resolving power (Gaussian line-spread function; reading in
                    instrument_kernel).
@@ -409,3 +412,41 @@ def evolution_radius(area_msh):
     (Sect. 4.2.1), taken as the region's projected area at disk centre, r^2 = A 1e-6 (the same
     convention as 'a 1% spot' = r 0.1 in Sect. 4.1)."""
     return np.sqrt(np.asarray(area_msh, np.float64) * 1e-6)
+
+
+# ---------------------------------------------------------------------------------------
+# bisector injection (Sect. 4.3, "Convec.model")
+# ---------------------------------------------------------------------------------------
+def inject_bisectors(F, bis_table, orig_table, delta_px):
+    """Local spectra [n_rows, n_px] (normalised: continuum 1) with their line bisectors replaced.
+
+    The paper removes the original bisector and adds the target one per mu by shifting each
+    spectral point according to its normalised depth.  Reading: a point n of depth
+    d = clip(1 - F_n, 0, 1) moves by v = B_row(d) - B_orig(d) (km/s), i.e. to the pixel position
+    u_n = n + atanh(v / c) / Delta on the log grid; the moved points are re-sampled at the pixel
+    centres by linear interpolation in wavelength, as in Eq. 11 (for the bracketing moved points
+    u_n <= m < u_n+1 the weight is (lambda_m - lambda'_n) / (lambda'_n+1 - lambda'_n) =
+    expm1((m - u_n) Delta) / expm1((u_n+1 - u_n) Delta)); the end values repeat outside.
+    Bisectors are tables over
+    n_depth equally spaced depths 0..1 (linear in between): bis_table [n_rows, n_depth],
+    orig_table [n_depth].  The moved positions must stay increasing."""
+    F = np.atleast_2d(np.asarray(F, np.float64))
+    bis = np.atleast_2d(np.asarray(bis_table, np.float64))
+    orig = np.asarray(orig_table, np.float64)
+    nd = orig.size
+    depths = np.linspace(0.0, 1.0, nd)
+    n = np.arange(F.shape[1], dtype=np.float64)
+    out = np.empty_like(F)
+    for r in range(F.shape[0]):
+        d = np.clip(1.0 - F[r], 0.0, 1.0)
+        v = np.interp(d, depths, bis[r]) - np.interp(d, depths, orig)
+        u = n + np.arctanh(v / C_KMS) / delta_px
+        if not np.all(np.diff(u) > 0):
+            raise ValueError("moved positions are not increasing")
+        k = np.searchsorted(u, n, side="right") - 1          # u[k] <= m < u[k+1]
+        inside = (k >= 0) & (k < F.shape[1] - 1)
+        kc = np.clip(k, 0, F.shape[1] - 2)
+        w = np.expm1((n - u[kc]) * delta_px) / np.expm1((u[kc + 1] - u[kc]) * delta_px)
+        val = F[r, kc] + w * (F[r, kc + 1] - F[r, kc])
+        out[r] = np.where(inside, val, np.where(k < 0, F[r, 0], F[r, -1]))
+    return out

@@ -801,3 +801,49 @@ def test_facula_mu_model_only_changes_facula_cells(small_case):
     b = O.active(c.star, c.quiet, c.active, c.regions, c.phases, effects=7)
     np.testing.assert_array_equal(a[2], b[2])
     assert np.abs(a[1] - b[1]).max() > 1e-6 * np.abs(b[1]).max()
+
+
+
+# ---------------------------------------------------------------------------------------
+# bisector injection (Sect. 4.3, Convec.model)
+# ---------------------------------------------------------------------------------------
+def _line_spectrum(n=800, centre=400.3, sigma=12.0, depth=0.7):
+    m = np.arange(n, dtype=np.float64)
+    return 1.0 - depth * np.exp(-0.5 * ((m - centre) / sigma) ** 2)
+
+
+def test_bisector_injection_with_equal_bisectors_is_the_identity():
+    F = np.stack([_line_spectrum(), _line_spectrum(centre=300.0)])
+    tab = np.tile(np.linspace(-0.3, 0.2, 11), (2, 1))
+    np.testing.assert_array_equal(O.inject_bisectors(F, tab, tab[0], 2.9e-6), F)
+
+
+def test_constant_bisector_is_a_doppler_shift():
+    """v(d) = a at every depth moves the whole spectrum by a: the result must equal the oracle's
+    own Doppler shift + Eq. 9-11 interpolation (the C code's shift_interp, written separately),
+    since both interpolate linearly in wavelength."""
+    a = 0.37                                            # km/s
+    delta = O.delta(6000.0, 6010.0, 800)
+    F = _line_spectrum()
+    got = O.inject_bisectors(F, np.full((1, 5), a), np.zeros(5), delta)[0]
+    lam = O.grid(6000.0, 6010.0, 800)
+    beta = math.tanh(math.atanh(a / C_KMS))             # the shift's v/c
+    ref = np.array([O.shift_interp(lam, F, beta, m) for m in range(800)])
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-14)
+
+
+def test_injected_linear_bisector_is_measured_back():
+    """A symmetric line given the bisector v(d) = k d: the output line's bisector (midpoint of
+    the two wing crossings at each flux level, in velocity) follows k d."""
+    delta = 1.0e-6                                      # 0.3 km/s per pixel: a well-sampled line
+    k = 0.4
+    F = _line_spectrum(n=1200, centre=600.0, sigma=20.0, depth=0.8)
+    out = O.inject_bisectors(F, np.array([[0.0, k]]), np.zeros(2), delta)[0]
+    m = np.arange(out.size, dtype=np.float64)
+    c0 = int(np.argmin(out))
+    for level in (0.3, 0.5, 0.7, 0.9):
+        f = 1.0 - level * 0.8                           # flux at normalised depth d = level * 0.8
+        left = np.interp(f, out[:c0 + 1][::-1], m[:c0 + 1][::-1])
+        right = np.interp(f, out[c0:], m[c0:])
+        v_mid = ((left + right) / 2.0 - 600.0) * delta * C_KMS
+        assert v_mid == pytest.approx(k * (1.0 - f), abs=0.01 * k)
