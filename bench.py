@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--sur-train", type=int, default=600_000)
     ap.add_argument("--sur-epochs", type=int, default=150)
     ap.add_argument("--sur-queries", type=int, default=1_000_000)
-    ap.add_argument("--only", default="all", choices=["all", "batched", "surrogate", "gemm", "quiet", "instrument"],
+    ap.add_argument("--only", default="all", choices=["all", "batched", "surrogate", "gemm", "quiet", "instrument", "bisectors"],
                     help="run one block alone (for profiling); 'all' is the full benchmark line")
     return ap.parse_args()
 
@@ -331,6 +331,8 @@ def run_ours(args):
         extras["quiet_forms"] = measure_quiet_forms(args, dev)
         torch.cuda.empty_cache()
         extras["instrument"] = measure_instrument(args, dev, hbm_peak)
+        torch.cuda.empty_cache()
+        extras["bisectors"] = measure_bisectors(args, dev, hbm_peak)
 
     res = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
            "steps": K, "warmup": W, "ms_per_step": round(ms_step, 5), "higher_is_better": True,
@@ -711,6 +713,41 @@ def measure_instrument(args, dev, hbm_peak):
     return res
 
 
+def measure_bisectors(args, dev, hbm_peak):
+    """Bisector injection (Sect. 4.3) into the 20 mu rows of the full-size quiet local spectra
+    (FP64): time per call from CUDA events (one kernel), and the HBM rate of its algorithmic
+    bytes (each row read once and written once)."""
+    import torch
+    from paper_2301_04259_gb300 import soap as S
+    case = workload(args, 0)
+    st = case.star
+    F = torch.from_numpy(case.quiet).to(dev)
+    out = torch.empty_like(F)
+    d = np.linspace(0.0, 1.0, 101)
+    bis = np.tile(0.25 * (d - 1.5 * d * d) + 0.05, (F.shape[0], 1))   # a C-shaped bisector, km/s
+    orig = np.zeros(101)
+    ctx = S.soap_init_star(st, F)
+    try:
+        for _ in range(3):
+            S.soap_inject_bisectors(ctx, F, out, bis, orig)
+        torch.cuda.synchronize()
+        stream = torch.cuda.current_stream()
+        reps = max(3, args.steps)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for a, b in ev:
+            a.record(stream)
+            S.soap_inject_bisectors(ctx, F, out, bis, orig)
+            b.record(stream)
+        torch.cuda.synchronize()
+        ms = float(np.median([a.elapsed_time(b) for a, b in ev]))
+    finally:
+        S.soap_free(ctx)
+    gbs = 2.0 * F.numel() * 8 / (ms * 1e-3) / 1e9
+    return {"workload": case.name, "rows": int(F.shape[0]), "n_px": int(F.shape[1]), "ms": round(ms, 4),
+            "hbm_gbs": round(gbs, 1), "frac_of_hbm": round(gbs / hbm_peak, 4),
+            "note": "FP64; includes the status-word check (one small copy and a stream synchronisation)"}
+
+
 def run_block(args):
     import torch
     torch.cuda.set_device(0)
@@ -728,6 +765,8 @@ def run_block(args):
         res = measure_quiet_forms(args, dev)
     elif args.only == "instrument":
         res = measure_instrument(args, dev, float(peaks.get("hbm_gbs", 6800.0)))
+    elif args.only == "bisectors":
+        res = measure_bisectors(args, dev, float(peaks.get("hbm_gbs", 6800.0)))
     else:
         res = measure_gemm(args, dev, float(peaks.get("bf16_tflops", 1900.0)))
     print(json.dumps({"block": args.only, **res}), flush=True)

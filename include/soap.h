@@ -286,6 +286,23 @@ soap_status soap_active_rv(soap_ctx* ctx, const soap_region* regions, int32_t n_
  * The batched form (soap_active_batch) does not apply it. */
 soap_status soap_set_instrument_resolution(soap_ctx* ctx, double resolving_power);
 
+/* Bisector injection (Sect. 4.3, the paper's Convec.model): normalised local spectra
+ * (continuum 1) get their line bisector replaced, every point moved by the velocity of its
+ * normalised depth.  The paper fits solar bisectors (not available); here the bisectors are
+ * tables: a point of depth d = clip(1 - F, 0, 1) moves by B_row(d) - B_orig(d) km/s, B given at
+ * n_depth equally spaced depths 0..1 and linear in between, i.e. by atanh(v/c)/Delta pixels; the
+ * moved points are re-sampled at the pixel centres linearly in wavelength (Eq. 11), the end
+ * values repeating outside.
+ *  in, out      [n_rows][n_px] float64, distinct, both host or both device per on_device
+ *               (typically the n_mu rows of a quiet or active local spectrum set).
+ *  bis_table    host [n_rows][n_depth] target bisector of each row (km/s).
+ *  orig_table   host [n_depth] the input spectra's own bisector (km/s; zeros when they have none).
+ * Errors: SOAP_ERANGE if |B| exceeds 1e-3 c or moves points by more than 62 pixels, or if the
+ * moved positions of a row are not increasing (checked on the device; the call synchronises). */
+soap_status soap_inject_bisectors(soap_ctx* ctx, const double* in, double* out, int32_t n_rows,
+                                  const double* bis_table, const double* orig_table, int32_t n_depth,
+                                  int on_device);
+
 /* Apply the context's line-spread function to n_spec spectra [n_spec][n_px] (float64, or
  * float32 with spectra_f32 = 1): in -> out, distinct arrays, both host or both device per
  * on_device.  SOAP_ESTATE if no resolution is set. */

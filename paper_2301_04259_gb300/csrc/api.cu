@@ -217,7 +217,7 @@ static void free_ctx_memory(soap_ctx* c) {
         if (p) cudaFree(p);
     DevBuf* bufs[] = {&c->stage_in, &c->fq, &c->contrast, &c->kphase, &c->jobs, &c->coefs, &c->job_counters,
                       &c->regions, &c->region_geo, &c->phases, &c->out_stage, &c->partial, &c->ccf_tmp,
-                      &c->ccf_tab, &c->lsf_taps, &c->lsf_tmp};
+                      &c->ccf_tab, &c->lsf_taps, &c->lsf_tmp, &c->bis_tab};
     for (DevBuf* b : bufs) release(*b);
     release_host(c->host_stage);
     ring_release(c);
@@ -257,8 +257,8 @@ static soap_status check_flags(soap_ctx* c) {
     SOAP_CUDA(cudaStreamSynchronize(c->stream));
     if (f) {
         cudaMemsetAsync(c->flags, 0, sizeof(unsigned int), c->stream);
-        set_error("device status word 0x%x (tap range %d, box range %d, job overflow %d)", f,
-                  !!(f & kFlagTapRange), !!(f & kFlagBoxRange), !!(f & kFlagJobOverflow));
+        set_error("device status word 0x%x (tap range %d, box range %d, job overflow %d, bisector order %d)", f,
+                  !!(f & kFlagTapRange), !!(f & kFlagBoxRange), !!(f & kFlagJobOverflow), !!(f & kFlagOrder));
         return SOAP_ERANGE;
     }
     return SOAP_OK;
@@ -740,6 +740,29 @@ soap_status soap_set_instrument_resolution(soap_ctx* c, double resolving_power) 
         set_error("resolving power must be finite and >= 0 (0: off)"); return SOAP_EINVAL;
     }
     return set_instrument(c, resolving_power);
+}
+
+soap_status soap_inject_bisectors(soap_ctx* c, const double* in, double* out, int32_t n_rows,
+                                  const double* bis_table, const double* orig_table, int32_t n_depth,
+                                  int on_device) {
+    clear_error();
+    if (!c || !in || !out || !bis_table || !orig_table) { set_error("NULL argument"); return SOAP_EINVAL; }
+    if (n_rows < 0 || n_depth < 2) { set_error("need n_rows >= 0 and n_depth >= 2"); return SOAP_EINVAL; }
+    if (in == out) { set_error("in and out must not be the same array"); return SOAP_EINVAL; }
+    if (n_rows == 0) return SOAP_OK;
+    const size_t bytes = (size_t)n_rows * (size_t)c->n_px * sizeof(double);
+    const double* din = in;
+    double* dout = out;
+    if (!on_device) {
+        SOAP_TRY(ensure(c->lsf_tmp, bytes));
+        SOAP_TRY(ensure(c->out_stage, bytes));
+        SOAP_CUDA(cudaMemcpyAsync(c->lsf_tmp.p, in, bytes, cudaMemcpyHostToDevice, c->stream));
+        din = c->lsf_tmp.as<double>();
+        dout = c->out_stage.as<double>();
+    }
+    SOAP_TRY(inject_bisectors(c, din, dout, n_rows, bis_table, orig_table, n_depth));
+    if (!on_device) SOAP_CUDA(cudaMemcpyAsync(out, dout, bytes, cudaMemcpyDeviceToHost, c->stream));
+    return check_flags(c);
 }
 
 soap_status soap_lower_resolution(soap_ctx* c, const void* in, void* out, int32_t spectra_f32,

@@ -100,7 +100,8 @@ constexpr size_t kRingBytes = size_t(4) << 20;
 enum DeviceFlag : unsigned int {
     kFlagTapRange = 1u,        // a cell's tap fell outside the precomputed kernel range
     kFlagBoxRange = 2u,        // a region box index left the grid
-    kFlagJobOverflow = 4u      // a tap table would overflow its capacity
+    kFlagJobOverflow = 4u,     // a tap table would overflow its capacity
+    kFlagOrder = 8u            // bisector injection: moved positions not increasing
 };
 
 }  // namespace soap
@@ -184,6 +185,7 @@ struct soap_ctx {
     int lsf_K = -1;
     size_t lsf_off32 = 0, lsf_offp64 = 0, lsf_offp32 = 0;
     soap::DevBuf lsf_taps, lsf_tmp;
+    soap::DevBuf bis_tab;       // bisector tables of the last injection
 
     // CCF line and velocity tables, kept while the mask and the velocity grid stay the same
     soap::DevBuf ccf_tab;
@@ -240,6 +242,9 @@ soap_status pad_rows32(soap_ctx* c, const float* src, float* dst32, int rows);
 // instrumental resolution (instrument.cu)
 soap_status set_instrument(soap_ctx* c, double resolving_power);
 soap_status launch_lsf(soap_ctx* c, const void* in, void* out, int f32, int64_t n_spec);
+// bisector injection (convection.cu)
+soap_status inject_bisectors(soap_ctx* c, const double* in, double* out, int n_rows, const double* bis_host,
+                             const double* orig_host, int n_d);
 // Copy `bytes` of host memory to device memory `dst` on the context stream through the pinned
 // ring (pageable sources are fine; the source may change once the call returns).
 soap_status upload_small(soap_ctx* c, void* dst, const void* src, size_t bytes);

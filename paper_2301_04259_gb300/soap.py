@@ -99,6 +99,7 @@ def _load():
         "soap_set_stream": (i32, [P, P]),
         "soap_synchronize": (i32, [P]),
         "soap_set_host_async": (i32, [P, ctypes.c_int]),
+        "soap_inject_bisectors": (i32, [P, P, P, i32, P, P, i32, ctypes.c_int]),
         "soap_set_facula_limb_brightening": (i32, [P, ctypes.c_int]),
         "soap_evolve_radii": (i32, [ctypes.POINTER(soap_region_evolution), ctypes.POINTER(soap_region), i32, P, i32, P]),
         "soap_active_phases_radii": (i32, [P, ctypes.POINTER(soap_region), i32, P, i32, P, u32, i32, P, ctypes.c_int]),
@@ -333,6 +334,21 @@ def soap_active_phases_radii(ctx, regions: Sequence, phases, radii, effects: int
 
 def soap_set_facula_limb_brightening(ctx, enabled: bool) -> None:
     _check(_lib.soap_set_facula_limb_brightening(ctx, int(bool(enabled))), "soap_set_facula_limb_brightening")
+
+
+def soap_inject_bisectors(ctx, spectra, out, bis_table, orig_table) -> None:
+    """spectra, out [n_rows][n_px] float64 (both host or both device); bis_table [n_rows][n_depth],
+    orig_table [n_depth] in km/s."""
+    ip, idev = _ptr(spectra)
+    op, odev = _ptr(out)
+    if idev != odev:
+        raise ValueError("spectra and out must both be host or both device")
+    bt = np.ascontiguousarray(bis_table, dtype=np.float64)
+    ot = np.ascontiguousarray(orig_table, dtype=np.float64)
+    if bt.ndim != 2 or bt.shape[0] != spectra.shape[0] or bt.shape[1] != ot.size:
+        raise ValueError("bis_table must be [n_rows][n_depth] with n_depth = len(orig_table)")
+    _check(_lib.soap_inject_bisectors(ctx, ip, op, int(spectra.shape[0]), ctypes.c_void_p(bt.ctypes.data),
+                                      ctypes.c_void_p(ot.ctypes.data), ot.size, idev), "soap_inject_bisectors")
 
 
 def soap_set_host_async(ctx, enabled: bool) -> None:

@@ -34,6 +34,7 @@ def test_header_declares_the_boundary():
               "soap_active_rv", "soap_set_host_async", "soap_set_quiet_spectrum_f32",
               "soap_set_active_spectrum_f32", "soap_set_instrument_resolution", "soap_lower_resolution",
               "soap_evolve_radii", "soap_active_phases_radii", "soap_set_facula_limb_brightening",
+              "soap_inject_bisectors",
               "soap_free", "soap_last_error"):
         assert n in names
 
