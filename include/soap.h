@@ -150,7 +150,8 @@ typedef enum {
     SOAP_TIMER_FIT = 9,          /* Gaussian fits */
     SOAP_TIMER_CCF_AUX = 10,     /* CCF line / velocity tables (when rebuilt) + partial-sum reduction */
     SOAP_TIMER_LSF = 11,         /* instrumental line-spread function */
-    SOAP_TIMER_COUNT = 12
+    SOAP_TIMER_BISECTORS = 12,   /* bisector injection (soap_inject_bisectors, kernel only) */
+    SOAP_TIMER_COUNT = 13
 } soap_timer;
 
 /* Read-only facts about an initialised star. */

@@ -26,7 +26,7 @@ SOAP_SPOT, SOAP_FACULA = 1, 2
 SOAP_BATCH_SPECTRUM, SOAP_BATCH_RESIDUAL = 0, 1
 SOAP_MAX_REGIONS, SOAP_MAX_CLASSES, SOAP_MAX_MU, SOAP_MAX_TAPS = 64, 8, 64, 256
 TIMERS = ("geometry", "pad_rows", "contrast", "phase_hist", "regions", "contract", "contract_quiet",
-          "direct", "ccf", "fit", "ccf_aux", "lsf")
+          "direct", "ccf", "fit", "ccf_aux", "lsf", "bisectors")
 (SOAP_TIMER_GEOMETRY, SOAP_TIMER_PAD_ROWS, SOAP_TIMER_CONTRAST, SOAP_TIMER_PHASE_HIST,
  SOAP_TIMER_REGIONS, SOAP_TIMER_CONTRACT, SOAP_TIMER_CONTRACT_QUIET, SOAP_TIMER_DIRECT,
  SOAP_TIMER_CCF, SOAP_TIMER_FIT) = range(10)

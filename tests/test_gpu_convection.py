@@ -60,6 +60,33 @@ def test_bisector_injection_matches_oracle(S, with_orig, n_d):
     np.testing.assert_array_equal(host, got)
 
 
+def _star(n_px, lam0, lam1):
+    c = synth.config1(0)
+    st = c.star
+    st.n_px = n_px
+    st.lambda_start_A, st.lambda_end_A = lam0, lam1
+    lam = synth.wavelength_grid(lam0, lam1, n_px)
+    rng = np.random.default_rng(n_px)
+    q = synth.local_spectra(lam, rng.uniform(lam0, lam1, 20), rng.uniform(0.1, 0.8, 20),
+                            rng.uniform(0.005, 0.05, 20) * (lam1 - lam0) / 10.0, st.mu_values)
+    return st, q
+
+
+@pytest.mark.parametrize("n_px,lam0,lam1", [(4096, 6000.0, 6010.0), (100, 5000.0, 5100.0), (64, 5000.0, 6000.0)])
+def test_bisector_injection_across_grid_spacings(S, n_px, lam0, lam1):
+    """Fine, medium and coarse log grids (Delta 4e-7, 2e-4, 3e-3): the three expm1 forms of the
+    kernel (series to e^4, series to e^6, library function) against the oracle."""
+    st, q = _star(n_px, lam0, lam1)
+    bis = _tables(q.shape[0], 21, 0.3, 5)
+    orig = _tables(1, 21, 0.1, 6)[0]
+    ref = O.inject_bisectors(q, bis, orig, _delta(st))
+    with S.Disk(st, _t(q)) as d:
+        out = torch.empty(q.shape, dtype=torch.float64, device=DEV)
+        S.soap_inject_bisectors(d.ctx, _t(q), out, bis, orig)
+        torch.cuda.synchronize()
+    assert np.abs(out.cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
 def test_bisector_injection_full_size(S):
     """The 20 mu rows of the full-size quiet and active local spectra (205,800 px)."""
     c = synth.config2(0)
