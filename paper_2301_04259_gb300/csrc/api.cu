@@ -185,6 +185,8 @@ static soap_status ensure_pipeline(soap_ctx* c) {
 
 static void sync_all(soap_ctx* c) {
     if (c->in_stream) cudaStreamSynchronize(c->in_stream);
+    join_geometry(c);
+    if (c->aux) cudaStreamSynchronize(c->aux);
     cudaStreamSynchronize(c->stream);
     if (c->out_stream) cudaStreamSynchronize(c->out_stream);
 }
@@ -221,6 +223,13 @@ static void free_ctx_memory(soap_ctx* c) {
     for (DevBuf* b : bufs) release(*b);
     release_host(c->host_stage);
     ring_release(c);
+    if (c->aux) {
+        cudaStreamSynchronize(c->aux);
+        cudaStreamDestroy(c->aux);
+        c->aux = nullptr;
+    }
+    for (cudaEvent_t* e : {&c->ev_fork, &c->ev_geo, &c->ev_rg, &c->ev_ph})
+        if (*e) { cudaEventDestroy(*e); *e = nullptr; }
 }
 
 // upload [n_mu][n_px] local spectra into padded rows: float64 sources fill the fp64 and fp32
@@ -253,6 +262,7 @@ static soap_status upload_spectra(soap_ctx* c, const void* src, int on_device, i
 
 static soap_status check_flags(soap_ctx* c) {
     unsigned int f = 0;
+    SOAP_TRY(join_geometry(c));
     SOAP_CUDA(cudaMemcpyAsync(&f, c->flags, sizeof(f), cudaMemcpyDeviceToHost, c->stream));
     SOAP_CUDA(cudaStreamSynchronize(c->stream));
     if (f) {
@@ -293,6 +303,7 @@ void timer_end(soap_ctx* c, int timer, cudaEvent_t begin) {
 static soap_status fold_timers(soap_ctx* c) {
     if (c->pending.empty()) return SOAP_OK;
     SOAP_CUDA(cudaStreamSynchronize(c->stream));
+    if (c->aux) SOAP_CUDA(cudaStreamSynchronize(c->aux));
     for (auto& t : c->pending) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) {
@@ -425,6 +436,9 @@ soap_status soap_init_star(const soap_star_desc* s, const double* quiet_local, i
     ALLOC(c->geo_counter, sizeof(int));
     ALLOC(c->cell_x, (size_t)c->N * sizeof(double));
 #undef ALLOC
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking);
+    for (cudaEvent_t* ev : {&c->ev_fork, &c->ev_geo, &c->ev_rg, &c->ev_ph})
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         set_error("device allocation failed: %s", cudaGetErrorString(e));
         free_ctx_memory(c);
@@ -587,6 +601,7 @@ soap_status soap_get_star_info(soap_ctx* c, soap_star_info* out) {
     clear_error();
     if (!c || !out) { set_error("ctx or out is NULL"); return SOAP_EINVAL; }
     long long h2[2] = {0, 0};
+    SOAP_TRY(join_geometry(c));
     SOAP_CUDA(cudaMemcpyAsync(h2, c->sum_I_fixed, sizeof(h2), cudaMemcpyDeviceToHost, c->stream));
     SOAP_TRY(check_flags(c));
     c->total_I = std::ldexp((double)h2[0], -c->fx_bits);

@@ -400,6 +400,7 @@ void batch_release(soap_ctx* c) {
 // graph: captured on the first call with a given shape, replayed on later ones.
 soap_status batch_run(soap_ctx* c, const soap_batch_item* items, int n_items, const soap_region* regions,
                       int n_regions, const double* phases, int n_phases, int variant, int residual, float* out) {
+    SOAP_TRY(join_geometry(c));                        // the cell tables (before any capture)
     if (c->alpha != 0.0) {
         set_error("the batched form needs a star without differential rotation (diff_rot_alpha = 0)");
         return SOAP_EINVAL;

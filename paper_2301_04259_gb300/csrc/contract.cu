@@ -217,6 +217,7 @@ static soap_status tap_buffers(soap_ctx* c, int n_phases, int n_class, int PB, i
 
 soap_status toeplitz_quiet(soap_ctx* c, int precision, void* dst) {
     // tap table built by the geometry kernel
+    SOAP_TRY(join_geometry(c));
     const int nbk = 1, G = 1, mt = c->n_mu * SOAP_MAX_TAPS;
     ClassTypes ct{};
     EffectList el{{SOAP_EFFECT_TOT, 0, 0}};
@@ -235,9 +236,7 @@ soap_status toeplitz_active(soap_ctx* c, const RegionDev* regions_host, int n_re
     const bool f64 = precision == SOAP_FP64;
     const size_t esz = f64 ? 8 : 4;
     const int ncl = n_class > 0 ? n_class : 1;
-    // quiet integral for Eq. 4 in the output precision
     SOAP_TRY(ensure(c->fq, (size_t)c->n_px * esz));
-    SOAP_TRY(toeplitz_quiet(c, precision, c->fq.p));
     // contrast per class, or per (class, mu bin) with mu-dependent facula temperatures
     bool has_fac = false;
     for (int k = 0; k < n_class; k++) has_fac |= class_type[k] == SOAP_FACULA;
@@ -345,13 +344,24 @@ soap_status toeplitz_active(soap_ctx* c, const RegionDev* regions_host, int n_re
     // split each phase over several blocks so that all SMs take part
     const int n_split = (int)std::max<int64_t>(1, std::min<int64_t>(8, (4 * 152 + n_phases - 1) / n_phases));
     dim3 hgrid((unsigned)n_phases, (unsigned)n_split);
-    SOAP_TIMED(c, SOAP_TIMER_PHASE_HIST,
-               k_phase_hist<<<hgrid, 256, smem, c->stream>>>(
-                   c->N, n_regions, c->region_geo.as<RegionGeo>(), c->cell_mu, c->cell_mu32, c->cell_j,
-                   c->cell_bin, c->cell_k0, c->cell_k1, c->tap_min, c->n_taps, c->n_mu, ncl, kfix,
-                   use_smem, PB, std::ldexp(1.0, -c->fx_bits), c->fx_bits, c->row_len, c->pad, toff, gstart, c64, c32,
-                   mt, c->job_counters.as<int>(), taps_smem, c->flags, bstart);
-               SOAP_LAUNCHED(c));
+    // the per-phase kernels run on the auxiliary stream (after the geometry queued there and the
+    // uploads, clears and region boxes above) while the main stream integrates the quiet star
+    SOAP_CUDA(cudaEventRecord(c->ev_rg, c->stream));
+    SOAP_CUDA(cudaStreamWaitEvent(c->aux, c->ev_rg, 0));
+    {
+        OnStream on(c, c->aux);
+        SOAP_TIMED(c, SOAP_TIMER_PHASE_HIST,
+                   k_phase_hist<<<hgrid, 256, smem, c->stream>>>(
+                       c->N, n_regions, c->region_geo.as<RegionGeo>(), c->cell_mu, c->cell_mu32, c->cell_j,
+                       c->cell_bin, c->cell_k0, c->cell_k1, c->tap_min, c->n_taps, c->n_mu, ncl, kfix,
+                       use_smem, PB, std::ldexp(1.0, -c->fx_bits), c->fx_bits, c->row_len, c->pad, toff, gstart, c64,
+                       c32, mt, c->job_counters.as<int>(), taps_smem, c->flags, bstart);
+                   SOAP_LAUNCHED(c));
+        SOAP_CUDA(cudaEventRecord(c->ev_ph, c->stream));
+    }
+    // quiet integral for Eq. 4 in the output precision (joins the geometry), then the tap tables
+    SOAP_TRY(toeplitz_quiet(c, precision, c->fq.p));
+    SOAP_CUDA(cudaStreamWaitEvent(c->stream, c->ev_ph, 0));
     ClassTypes ct{};
     for (int k = 0; k < n_class; k++) ct.t[k] = class_type[k];
     EffectList el{{0, 0, 0}};

@@ -106,6 +106,7 @@ static soap_status run_direct(soap_ctx* c, const T* rows, T* dst) {
 }
 
 soap_status direct_quiet(soap_ctx* c, int precision, void* dst) {
+    SOAP_TRY(join_geometry(c));
     if (precision == SOAP_FP64) return run_direct<double, 2, 256, 128>(c, c->q64, (double*)dst);
     return run_direct<float, 4, 256, 128>(c, c->q32, (float*)dst);
 }

@@ -214,6 +214,10 @@ soap_status pad_rows32(soap_ctx* c, const float* src, float* dst32, int rows) {
     return SOAP_OK;
 }
 
+// The geometry depends only on the star: it runs on the auxiliary stream after everything
+// queued so far on the main stream (which may still read the previous geometry), so that the
+// main stream's next kernels (padded rows, contrast, region boxes) overlap it.  Readers of the
+// cell tables and quiet kernels call join_geometry first.
 soap_status geometry_init(soap_ctx* c) {
     MuTable mus{};
     for (int b = 0; b < c->n_mu; b++) mus.v[b] = c->mu_values[b];
@@ -221,23 +225,37 @@ soap_status geometry_init(soap_ctx* c) {
     int tap_max = c->tap_min + c->n_taps - 1;
     size_t nb = (size_t)c->n_mu * c->n_taps;
     const double scale = std::ldexp(1.0, c->fx_bits);
-    cudaEvent_t tb = c->profiling ? timer_begin(c) : nullptr;
-    SOAP_CUDA(cudaMemsetAsync(c->kq_fixed, 0, nb * sizeof(long long), c->stream));
-    SOAP_CUDA(cudaMemsetAsync(c->sum_I_fixed, 0, 2 * sizeof(long long), c->stream));
-    SOAP_CUDA(cudaMemsetAsync(c->geo_counter, 0, sizeof(int), c->stream));
     size_t smem = nb * sizeof(long long);
     if (smem > 48 * 1024)
         SOAP_CUDA(cudaFuncSetAttribute(k_geometry, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    dim3 grid((unsigned)((c->N + 127) / 128), (unsigned)c->N);
-    k_geometry<<<grid, 128, smem, c->stream>>>(
-        c->N, c->vsini, std::sin(incl), std::cos(incl), c->alpha, c->u1, c->u2, 1.0 / kCKms,
-        1.0 / c->delta, c->delta, 1.0 / std::expm1(c->delta), c->n_mu, mus, c->mu_sorted, c->tap_min,
-        tap_max, c->n_taps, scale, c->cell_I, c->cell_w, c->cell_mu, c->cell_mu32, c->cell_j,
-        c->cell_bin, c->cell_k0, c->cell_k1, c->kq_fixed, c->sum_I_fixed, c->qtoff, c->qgstart, c->qc64,
-        c->qc32, c->n_mu * SOAP_MAX_TAPS, c->row_len, c->pad, c->fx_bits, c->geo_counter, c->flags,
-        c->cell_x, (2.0 / (double)c->N) * (2.0 / (double)c->N));
-    SOAP_LAUNCHED(c);
-    if (c->profiling) timer_end(c, SOAP_TIMER_GEOMETRY, tb);
+    SOAP_CUDA(cudaEventRecord(c->ev_fork, c->stream));
+    SOAP_CUDA(cudaStreamWaitEvent(c->aux, c->ev_fork, 0));
+    {
+        OnStream on(c, c->aux);
+        cudaEvent_t tb = c->profiling ? timer_begin(c) : nullptr;
+        SOAP_CUDA(cudaMemsetAsync(c->kq_fixed, 0, nb * sizeof(long long), c->stream));
+        SOAP_CUDA(cudaMemsetAsync(c->sum_I_fixed, 0, 2 * sizeof(long long), c->stream));
+        SOAP_CUDA(cudaMemsetAsync(c->geo_counter, 0, sizeof(int), c->stream));
+        dim3 grid((unsigned)((c->N + 127) / 128), (unsigned)c->N);
+        k_geometry<<<grid, 128, smem, c->stream>>>(
+            c->N, c->vsini, std::sin(incl), std::cos(incl), c->alpha, c->u1, c->u2, 1.0 / kCKms,
+            1.0 / c->delta, c->delta, 1.0 / std::expm1(c->delta), c->n_mu, mus, c->mu_sorted, c->tap_min,
+            tap_max, c->n_taps, scale, c->cell_I, c->cell_w, c->cell_mu, c->cell_mu32, c->cell_j,
+            c->cell_bin, c->cell_k0, c->cell_k1, c->kq_fixed, c->sum_I_fixed, c->qtoff, c->qgstart, c->qc64,
+            c->qc32, c->n_mu * SOAP_MAX_TAPS, c->row_len, c->pad, c->fx_bits, c->geo_counter, c->flags,
+            c->cell_x, (2.0 / (double)c->N) * (2.0 / (double)c->N));
+        SOAP_LAUNCHED(c);
+        if (c->profiling) timer_end(c, SOAP_TIMER_GEOMETRY, tb);
+        SOAP_CUDA(cudaEventRecord(c->ev_geo, c->stream));
+    }
+    c->geo_pending = true;
+    return SOAP_OK;
+}
+
+soap_status join_geometry(soap_ctx* c) {
+    if (!c->geo_pending) return SOAP_OK;
+    SOAP_CUDA(cudaStreamWaitEvent(c->stream, c->ev_geo, 0));
+    c->geo_pending = false;
     return SOAP_OK;
 }
 

@@ -109,6 +109,13 @@ enum DeviceFlag : unsigned int {
 struct soap_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
+    // auxiliary stream for work that can overlap the main stream: the cell geometry (forked from
+    // the main stream when a star is set or updated, joined by its readers through
+    // join_geometry) and the per-phase kernels (forked after the region boxes, joined before the
+    // contraction).  ev_*: fork point, geometry done, region boxes done, per-phase kernels done.
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_geo = nullptr, ev_rg = nullptr, ev_ph = nullptr;
+    bool geo_pending = false;           // geometry queued on aux, not yet joined by the main stream
 
     // star
     int N = 0;
@@ -236,7 +243,18 @@ void timer_end(soap_ctx* c, int timer, cudaEvent_t begin);
 // ---------------------------------------------------------------------------------------
 // kernels and launchers implemented in the .cu files
 // ---------------------------------------------------------------------------------------
-soap_status geometry_init(soap_ctx* c);                          // per-cell geometry + quiet kernels
+soap_status geometry_init(soap_ctx* c);                          // per-cell geometry + quiet kernels (on aux)
+soap_status join_geometry(soap_ctx* c);                          // main stream waits for a pending geometry
+
+// Launches and timers inside the scope go to stream s instead of the context's main stream.
+struct OnStream {
+    soap_ctx* c;
+    cudaStream_t saved;
+    OnStream(soap_ctx* c_, cudaStream_t s) : c(c_), saved(c_->stream) { c->stream = s; }
+    ~OnStream() { c->stream = saved; }
+    OnStream(const OnStream&) = delete;
+    OnStream& operator=(const OnStream&) = delete;
+};
 soap_status pad_rows(soap_ctx* c, const double* src, double* dst64, float* dst32, int rows);
 soap_status pad_rows32(soap_ctx* c, const float* src, float* dst32, int rows);
 // instrumental resolution (instrument.cu)
