@@ -329,8 +329,7 @@ soap_status toeplitz_active(soap_ctx* c, const RegionDev* regions_host, int n_re
     const int taps_smem = kslice_bytes <= 96 * 1024;
     size_t smem = std::max(use_smem ? hist_bytes : (size_t)0, taps_smem ? kslice_bytes : (size_t)0);
     SOAP_CUDA(cudaMemsetAsync(kfix, 0, kbytes, c->stream));
-    if (smem > 48 * 1024)
-        SOAP_CUDA(cudaFuncSetAttribute(k_phase_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SOAP_TRY(fit_dynamic_smem(k_phase_hist, smem));
     // region centres and boxes per (phase, region)
     SOAP_TRY(ensure(c->region_geo, (size_t)n_phases * (n_regions > 0 ? n_regions : 1) * sizeof(RegionGeo)));
     if (n_regions > 0) {

@@ -226,8 +226,7 @@ soap_status geometry_init(soap_ctx* c) {
     size_t nb = (size_t)c->n_mu * c->n_taps;
     const double scale = std::ldexp(1.0, c->fx_bits);
     size_t smem = nb * sizeof(long long);
-    if (smem > 48 * 1024)
-        SOAP_CUDA(cudaFuncSetAttribute(k_geometry, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SOAP_TRY(fit_dynamic_smem(k_geometry, smem));
     SOAP_CUDA(cudaEventRecord(c->ev_fork, c->stream));
     SOAP_CUDA(cudaStreamWaitEvent(c->aux, c->ev_fork, 0));
     {

@@ -243,6 +243,17 @@ void timer_end(soap_ctx* c, int timer, cudaEvent_t begin);
 // ---------------------------------------------------------------------------------------
 // kernels and launchers implemented in the .cu files
 // ---------------------------------------------------------------------------------------
+// A launch may use 48 KB of shared memory, static and dynamic together, unless the kernel has
+// opted in to more: opt in when the kernel's static part plus `dynamic` exceeds that.
+template <typename Kernel>
+inline soap_status fit_dynamic_smem(Kernel kernel, size_t dynamic) {
+    cudaFuncAttributes a{};
+    SOAP_CUDA(cudaFuncGetAttributes(&a, kernel));
+    if (a.sharedSizeBytes + dynamic > 48 * 1024)
+        SOAP_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dynamic));
+    return SOAP_OK;
+}
+
 soap_status geometry_init(soap_ctx* c);                          // per-cell geometry + quiet kernels (on aux)
 soap_status join_geometry(soap_ctx* c);                          // main stream waits for a pending geometry
 

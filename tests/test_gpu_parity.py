@@ -120,6 +120,18 @@ def test_active_config1_all_effects(S, cfg1, cfg1_ref):
     assert np.abs(d64 - dref).max() <= 1e-10 * np.abs(dref).max()
 
 
+def test_active_wide_velocity_kernels(S):
+    """vsini 8 km/s on the 4096-px grid of config 1: velocity kernels of ~135 taps, so the
+    per-phase kernels need ~47 KB of dynamic shared memory on top of the kernel's static tables
+    (more than the default 48 KB per launch); FP64 and FP32, all three effects."""
+    c = synth.config1(2)
+    c.star.vsini_kms = 8.0
+    q = O.quiet(c.star, c.quiet)
+    ref = O.active(c.star, c.quiet, c.active, c.regions, c.phases, effects=7)
+    assert rel(gpu_active(S, c, c.regions, c.phases, 7, S.SOAP_FP64), ref, q.max()) <= TOL64
+    assert rel(gpu_active(S, c, c.regions, c.phases, 7, S.SOAP_FP32), ref, q.max()) <= TOL32
+
+
 @pytest.fixture(scope="module")
 def complex_case():
     regs = [Region(FACULA, 25.0, -30.0, 0.3, 6100.0),
