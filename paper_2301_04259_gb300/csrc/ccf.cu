@@ -5,11 +5,15 @@
 // half width h = W / (2 c Delta); CCF(v) = sum_l w_l sum_n F_n |pixel n intersect box|.
 // Lines whose box leaves [-1/2, n_px - 1/2] anywhere on the velocity grid are skipped.
 //
-// k_ccf_partial: block = (chunk of 64 mask lines, block of spectra); thread = velocity.  The
-// box position is computed in FP64 (it carries cm/s shifts), the overlaps and products in
-// the spectra's precision; per-chunk partial sums are reduced in FP64 in a fixed order.
-// k_gauss_fit: one warp per spectrum, FP64 Levenberg-Marquardt on
-// A + B exp(-(v - mu)^2 / (2 s^2)).
+// Line and velocity tables (k_ccf_lines, k_ccf_velocities) split each box start into an integer
+// pixel and an exact fraction (FP64: they carry cm/s shifts) and are kept while the mask and the
+// velocity grid are unchanged.  Partial CCF sums per chunk of lines come from one of three
+// kernels: k_ccf_tile (FP32 spectra, mask sorted by wavelength: register tiles of 4 velocities x
+// 16 spectra per thread over staged pixel windows), k_ccf_window (FP64 spectra or boxes too wide
+// for the tiles: staged windows, one velocity per thread) and k_ccf_partial (any line order).
+// k_ccf_reduce adds the partials in a fixed order (FP64, or float pairs with TwoSum); k_gauss_fit
+// fits A + B exp(-(v - mu)^2 / (2 s^2)) per spectrum (one block each: FP32 Levenberg-Marquardt,
+// then Newton steps with FP64 residuals; see its comment).
 #include <cmath>
 #include <cstring>
 #include <type_traits>

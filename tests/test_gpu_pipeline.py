@@ -225,3 +225,22 @@ def test_float32_local_spectra_give_the_fp32_path_its_own_results(S, case):
         torch.cuda.synchronize()
     ref64, _ = _separate(S, c, c.quiet, c.active[synth.SPOT], c.phases, S.SOAP_FP64, S.SOAP_EFFECT_TOT)
     np.testing.assert_array_equal(out64[0].cpu().numpy(), ref64)
+
+
+@pytest.mark.parametrize("n_px", [20000, 20003])
+def test_float32_rows_any_pixel_count(S, n_px):
+    """float32 uploads pad their rows with 16-byte copies when the pixel count allows it (20,000)
+    and element by element otherwise (20,003); either way the FP32 path gets the results of the
+    float64 uploads, bit for bit (spot and facula spectra, all three effects)."""
+    c = synth.config2(3, grid_n=60, n_px=n_px, lambda_start=5000.0, lambda_end=5300.0, n_phases=9)
+    outs = []
+    for dt in (np.float64, np.float32):
+        with S.Disk(c.star, _t(c.quiet)) as d:
+            S.soap_set_quiet_spectrum(d.ctx, _t(c.quiet.astype(dt)))
+            for k, v in c.active.items():
+                S.soap_set_active_spectrum(d.ctx, k, _t(v.astype(dt)))
+            out = torch.empty((3, len(c.phases), n_px), dtype=torch.float32, device=DEV)
+            S.soap_active_phases(d.ctx, c.regions, c.phases, 7, S.SOAP_FP32, out)
+            torch.cuda.synchronize()
+            outs.append(out.cpu().numpy())
+    np.testing.assert_array_equal(outs[0], outs[1])
