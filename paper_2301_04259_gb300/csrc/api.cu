@@ -186,6 +186,7 @@ static soap_status ensure_pipeline(soap_ctx* c) {
 static void sync_all(soap_ctx* c) {
     if (c->in_stream) cudaStreamSynchronize(c->in_stream);
     join_geometry(c);
+    if (c->aux2) cudaStreamSynchronize(c->aux2);
     if (c->aux) cudaStreamSynchronize(c->aux);
     cudaStreamSynchronize(c->stream);
     if (c->out_stream) cudaStreamSynchronize(c->out_stream);
@@ -223,12 +224,13 @@ static void free_ctx_memory(soap_ctx* c) {
     for (DevBuf* b : bufs) release(*b);
     release_host(c->host_stage);
     ring_release(c);
-    if (c->aux) {
-        cudaStreamSynchronize(c->aux);
-        cudaStreamDestroy(c->aux);
-        c->aux = nullptr;
-    }
-    for (cudaEvent_t* e : {&c->ev_fork, &c->ev_geo, &c->ev_rg, &c->ev_ph})
+    for (cudaStream_t* s : {&c->aux, &c->aux2})
+        if (*s) {
+            cudaStreamSynchronize(*s);
+            cudaStreamDestroy(*s);
+            *s = nullptr;
+        }
+    for (cudaEvent_t* e : {&c->ev_fork, &c->ev_geo, &c->ev_rg, &c->ev_ph, &c->ev_main})
         if (*e) { cudaEventDestroy(*e); *e = nullptr; }
 }
 
@@ -303,6 +305,7 @@ void timer_end(soap_ctx* c, int timer, cudaEvent_t begin) {
 static soap_status fold_timers(soap_ctx* c) {
     if (c->pending.empty()) return SOAP_OK;
     SOAP_CUDA(cudaStreamSynchronize(c->stream));
+    if (c->aux2) SOAP_CUDA(cudaStreamSynchronize(c->aux2));
     if (c->aux) SOAP_CUDA(cudaStreamSynchronize(c->aux));
     for (auto& t : c->pending) {
         float ms = 0.f;
@@ -437,7 +440,8 @@ soap_status soap_init_star(const soap_star_desc* s, const double* quiet_local, i
     ALLOC(c->cell_x, (size_t)c->N * sizeof(double));
 #undef ALLOC
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking);
-    for (cudaEvent_t* ev : {&c->ev_fork, &c->ev_geo, &c->ev_rg, &c->ev_ph})
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->aux2, cudaStreamNonBlocking);
+    for (cudaEvent_t* ev : {&c->ev_fork, &c->ev_geo, &c->ev_rg, &c->ev_ph, &c->ev_main})
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         set_error("device allocation failed: %s", cudaGetErrorString(e));

@@ -236,6 +236,9 @@ soap_status toeplitz_active(soap_ctx* c, const RegionDev* regions_host, int n_re
     const bool f64 = precision == SOAP_FP64;
     const size_t esz = f64 ? 8 : 4;
     const int ncl = n_class > 0 ? n_class : 1;
+    // the main stream's position now: the previous call's contraction, the last reader of the
+    // tap tables that this call's per-phase kernels rewrite, is before it
+    SOAP_CUDA(cudaEventRecord(c->ev_main, c->stream));
     SOAP_TRY(ensure(c->fq, (size_t)c->n_px * esz));
     // contrast per class, or per (class, mu bin) with mu-dependent facula temperatures
     bool has_fac = false;
@@ -296,7 +299,11 @@ soap_status toeplitz_active(soap_ctx* c, const RegionDev* regions_host, int n_re
                            c->n_px, (float)(hck / (c->lam_s * c->t_quiet)), (float)c->delta, n_class, cc, con32);
                        SOAP_LAUNCHED(c));
     }
-    // regions and phases to the device (through the pinned ring: no wait for the stream)
+    // regions and phases to the device (through the pinned ring: no wait for the stream), the
+    // clears and the region boxes run on aux2, after the previous call's per-phase kernels (the
+    // last readers of these buffers), overlapping the main stream's padded rows and contrast
+    SOAP_CUDA(cudaStreamWaitEvent(c->aux2, c->ev_ph, 0));
+    OnStream on2(c, c->aux2);
     size_t rbytes = (size_t)(n_regions > 0 ? n_regions : 1) * sizeof(RegionDev);
     size_t pbytes = (size_t)n_phases * sizeof(double);
     SOAP_TRY(ensure(c->regions, rbytes));
@@ -340,13 +347,15 @@ soap_status toeplitz_active(soap_ctx* c, const RegionDev* regions_host, int n_re
                        c->alpha, radii_dev, c->region_geo.as<RegionGeo>());
                    SOAP_LAUNCHED(c));
     }
+    SOAP_CUDA(cudaEventRecord(c->ev_rg, c->stream));
+    c->stream = on2.saved;                                 // back to the main stream
     // split each phase over several blocks so that all SMs take part
     const int n_split = (int)std::max<int64_t>(1, std::min<int64_t>(8, (4 * 152 + n_phases - 1) / n_phases));
     dim3 hgrid((unsigned)n_phases, (unsigned)n_split);
-    // the per-phase kernels run on the auxiliary stream (after the geometry queued there and the
-    // uploads, clears and region boxes above) while the main stream integrates the quiet star
-    SOAP_CUDA(cudaEventRecord(c->ev_rg, c->stream));
+    // the per-phase kernels run on the auxiliary stream (after the geometry queued there, the
+    // region boxes and the previous contraction) while the main stream integrates the quiet star
     SOAP_CUDA(cudaStreamWaitEvent(c->aux, c->ev_rg, 0));
+    SOAP_CUDA(cudaStreamWaitEvent(c->aux, c->ev_main, 0));
     {
         OnStream on(c, c->aux);
         SOAP_TIMED(c, SOAP_TIMER_PHASE_HIST,

@@ -111,10 +111,12 @@ struct soap_ctx {
     cudaStream_t stream = nullptr;
     // auxiliary stream for work that can overlap the main stream: the cell geometry (forked from
     // the main stream when a star is set or updated, joined by its readers through
-    // join_geometry) and the per-phase kernels (forked after the region boxes, joined before the
-    // contraction).  ev_*: fork point, geometry done, region boxes done, per-phase kernels done.
-    cudaStream_t aux = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_geo = nullptr, ev_rg = nullptr, ev_ph = nullptr;
+    // join_geometry) and the per-phase kernels (joined before the contraction); aux2 runs the
+    // region and phase uploads and the region boxes of an active-phase call, after the previous
+    // call's per-phase kernels.  ev_*: fork point, geometry done, region boxes done, per-phase
+    // kernels done, main stream at the start of an active-phase call.
+    cudaStream_t aux = nullptr, aux2 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_geo = nullptr, ev_rg = nullptr, ev_ph = nullptr, ev_main = nullptr;
     bool geo_pending = false;           // geometry queued on aux, not yet joined by the main stream
 
     // star
