@@ -51,7 +51,8 @@ def parse():
     ap.add_argument("--sur-train", type=int, default=600_000)
     ap.add_argument("--sur-epochs", type=int, default=150)
     ap.add_argument("--sur-queries", type=int, default=1_000_000)
-    ap.add_argument("--only", default="all", choices=["all", "batched", "surrogate", "gemm", "quiet", "instrument", "bisectors"],
+    ap.add_argument("--only", default="all", choices=["all", "batched", "surrogate", "gemm", "quiet", "instrument", "bisectors",
+                                                      "tensor"],
                     help="run one block alone (for profiling); 'all' is the full benchmark line")
     return ap.parse_args()
 
@@ -333,6 +334,8 @@ def run_ours(args):
         extras["instrument"] = measure_instrument(args, dev, hbm_peak)
         torch.cuda.empty_cache()
         extras["bisectors"] = measure_bisectors(args, dev, hbm_peak)
+        torch.cuda.empty_cache()
+        extras["tensor_contraction"] = measure_tensor_contraction(args, dev, float(peaks.get("bf16_tflops", 1913.8)))
 
     res = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
            "steps": K, "warmup": W, "ms_per_step": round(ms_step, 5), "higher_is_better": True,
@@ -754,6 +757,55 @@ def measure_bisectors(args, dev, hbm_peak):
             "note": "FP64; call_ms adds the table upload and the status-word check (a stream synchronisation)"}
 
 
+def measure_tensor_contraction(args, dev, bf16_peak):
+    """The active-phase contraction of the headline step in its two forms: SIMT FP32 (per-tap
+    Toeplitz tiles, SOAP_FP32) and tcgen05 BF16 split precision (dense GEMM over pixels x phases x
+    (class, mu bin, tap), SOAP_BF16X3).  Kernel time from the library's timer; for the tensor
+    form the executed tensor work (3 products over the padded GEMM) against the BF16 peak."""
+    import torch
+    from paper_2301_04259_gb300 import soap as S
+    case = workload(args, 0)
+    st = case.star
+    P, n_px = case.phases.size, st.n_px
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    ctx = S.soap_init_star(st, t(case.quiet))
+    res = {"workload": case.name, "phases": P}
+    outs = {}
+    try:
+        for k, v in case.active.items():
+            S.soap_set_active_spectrum(ctx, k, t(v))
+        info = S.soap_get_star_info(ctx)
+        n_class = len({(r.type, r.temp_K) for r in case.regions})
+        for name, prec in (("simt_fp32", S.SOAP_FP32), ("tcgen05_bf16x3", S.SOAP_BF16X3)):
+            out = torch.empty((1, P, n_px), dtype=torch.float32, device=dev)
+            for _ in range(3):
+                S.soap_active_phases(ctx, case.regions, case.phases, S.SOAP_EFFECT_TOT, prec, out)
+            torch.cuda.synchronize()
+            S.soap_reset_kernel_times(ctx)
+            S.soap_set_profiling(ctx, True)
+            for _ in range(max(3, args.steps)):
+                S.soap_active_phases(ctx, case.regions, case.phases, S.SOAP_EFFECT_TOT, prec, out)
+            torch.cuda.synchronize()
+            tot, n = S.soap_get_kernel_time(ctx, S.TIMERS.index("contract"))
+            S.soap_set_profiling(ctx, False)
+            res[name] = {"ms": round(tot / max(1, n), 4)}
+            outs[name] = out
+        k_pad = -(-n_class * st.n_mu * info.n_taps // 64) * 64
+        p_pad = -(-P // 128) * 128
+        m_pad = -(-n_px // 128) * 128
+        flops = 2.0 * 3 * m_pad * p_pad * k_pad
+        ms = res["tcgen05_bf16x3"]["ms"]
+        tf = flops / (ms * 1e-3) / 1e12
+        res["tcgen05_bf16x3"].update({"gemm": [m_pad, p_pad, k_pad], "executed_tflop": round(flops / 1e12, 4),
+                                      "achieved_tflops": round(tf, 1), "frac_of_bf16_peak": round(tf / bf16_peak, 4)})
+        res["max_abs_diff_vs_fp32"] = float((outs["tcgen05_bf16x3"] - outs["simt_fp32"]).abs().max().item())
+    finally:
+        S.soap_free(ctx)
+    res["note"] = ("the dense GEMM executes 3 x k_pad multiply-adds per (phase, pixel); the SIMT kernel visits "
+                   "only the non-zero taps of each block of 4 phases (~50 FMA per phase and pixel)")
+    return res
+
+
 def run_block(args):
     import torch
     torch.cuda.set_device(0)
@@ -773,6 +825,8 @@ def run_block(args):
         res = measure_instrument(args, dev, float(peaks.get("hbm_gbs", 6800.0)))
     elif args.only == "bisectors":
         res = measure_bisectors(args, dev, float(peaks.get("hbm_gbs", 6800.0)))
+    elif args.only == "tensor":
+        res = measure_tensor_contraction(args, dev, float(peaks.get("bf16_tflops", 1913.8)))
     else:
         res = measure_gemm(args, dev, float(peaks.get("bf16_tflops", 1900.0)))
     print(json.dumps({"block": args.only, **res}), flush=True)

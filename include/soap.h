@@ -60,10 +60,15 @@ typedef enum {
 
 /* Arithmetic of the disk sum.  SOAP_FP64: FP64 everywhere (outputs float64).
  * SOAP_FP32: FP64 cell velocities, shifts and weights; FP32 contraction with FP32
- * accumulation (outputs float32). */
+ * accumulation (outputs float32).
+ * SOAP_BF16X3 (active-phase calls only: soap_active_phases(_radii), soap_active_rv): as
+ * SOAP_FP32, but the contraction of Eqs. 1-4 runs on the tensor cores as a GEMM (pixels x
+ * phases x (class, mu bin, tap)) with both operands split into BF16 high and low parts and three
+ * products accumulated in FP32 (outputs float32). */
 typedef enum {
     SOAP_FP64 = 0,
-    SOAP_FP32 = 1
+    SOAP_FP32 = 1,
+    SOAP_BF16X3 = 2
 } soap_precision;
 
 /* Form of the sum over cells (soap_quiet_spectrum). */

@@ -220,7 +220,7 @@ static void free_ctx_memory(soap_ctx* c) {
         if (p) cudaFree(p);
     DevBuf* bufs[] = {&c->stage_in, &c->fq, &c->contrast, &c->kphase, &c->jobs, &c->coefs, &c->job_counters,
                       &c->regions, &c->region_geo, &c->phases, &c->out_stage, &c->partial, &c->ccf_tmp,
-                      &c->ccf_tab, &c->lsf_taps, &c->lsf_tmp, &c->bis_tab};
+                      &c->ccf_tab, &c->lsf_taps, &c->lsf_tmp, &c->bis_tab, &c->tc_coef};
     for (DevBuf* b : bufs) release(*b);
     release_host(c->host_stage);
     ring_release(c);
@@ -269,8 +269,9 @@ static soap_status check_flags(soap_ctx* c) {
     SOAP_CUDA(cudaStreamSynchronize(c->stream));
     if (f) {
         cudaMemsetAsync(c->flags, 0, sizeof(unsigned int), c->stream);
-        set_error("device status word 0x%x (tap range %d, box range %d, job overflow %d, bisector order %d)", f,
-                  !!(f & kFlagTapRange), !!(f & kFlagBoxRange), !!(f & kFlagJobOverflow), !!(f & kFlagOrder));
+        set_error("device status word 0x%x (tap range %d, box range %d, job overflow %d, bisector order %d, "
+                  "tensor-core wait timeout %d)", f, !!(f & kFlagTapRange), !!(f & kFlagBoxRange),
+                  !!(f & kFlagJobOverflow), !!(f & kFlagOrder), !!(f & kFlagTimeout));
         return SOAP_ERANGE;
     }
     return SOAP_OK;
@@ -678,7 +679,10 @@ static soap_status check_active(soap_ctx* c, const soap_region* regions, int32_t
     if (n_phases < 0) { set_error("n_phases < 0"); return SOAP_EINVAL; }
     if (n_phases > 0 && !phases) { set_error("phases is NULL"); return SOAP_EINVAL; }
     if (effects == 0 || (effects & ~7u)) { set_error("effects must be a non-empty OR of SOAP_EFFECT_*"); return SOAP_EINVAL; }
-    if (precision != SOAP_FP64 && precision != SOAP_FP32) { set_error("unknown precision %d", precision); return SOAP_EINVAL; }
+    if (precision != SOAP_FP64 && precision != SOAP_FP32 && precision != SOAP_BF16X3) {
+        set_error("unknown precision %d", precision);
+        return SOAP_EINVAL;
+    }
     for (int p = 0; p < n_phases; p++)
         if (!is_finite(phases[p])) { set_error("phases[%d] not finite", p); return SOAP_EINVAL; }
     A.rd.resize(n_regions);
@@ -746,7 +750,7 @@ static soap_status active_lsf(soap_ctx* c, const ActiveArgs& A, int32_t n_region
     }
     SOAP_TRY(toeplitz_active(c, A.rd.data(), n_regions, A.ctemp, A.ctype, A.n_class, phases, n_phases,
                              effect, precision, raw));
-    if (c->lsf_K >= 0) SOAP_TRY(launch_lsf(c, raw, dst, precision == SOAP_FP32, n_phases));
+    if (c->lsf_K >= 0) SOAP_TRY(launch_lsf(c, raw, dst, precision != SOAP_FP64, n_phases));
     return SOAP_OK;
 }
 
@@ -832,7 +836,7 @@ static soap_status active_phases_impl(soap_ctx* c, const soap_region* regions, i
     }
     SOAP_TRY(toeplitz_active(c, A.rd.data(), n_regions, A.ctemp, A.ctype, A.n_class, phases, n_phases,
                              effects, precision, raw, radii));
-    if (c->lsf_K >= 0) SOAP_TRY(launch_lsf(c, raw, dst, precision == SOAP_FP32, (int64_t)n_eff * n_phases));
+    if (c->lsf_K >= 0) SOAP_TRY(launch_lsf(c, raw, dst, precision != SOAP_FP64, (int64_t)n_eff * n_phases));
     if (!out_on_device) {
         SOAP_CUDA(cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, c->stream));
         SOAP_CUDA(cudaStreamSynchronize(c->stream));
@@ -920,7 +924,7 @@ soap_status soap_active_rv(soap_ctx* c, const soap_region* regions, int32_t n_re
     SOAP_TRY(check_active(c, regions, n_regions, phases, n_phases, effect, precision, A));
     SOAP_TRY(check_rv(c, mask_lambda, mask_weight, n_lines, mask_width_kms, v_lo, v_step, n_v));
     if (n_phases == 0) return SOAP_OK;
-    const int f32 = precision == SOAP_FP32;
+    const int f32 = precision != SOAP_FP64;
     const size_t sbytes = (size_t)n_phases * (size_t)c->n_px * (f32 ? 4 : 8);
     if (out_on_device) {
         void* sp = spectra_out;

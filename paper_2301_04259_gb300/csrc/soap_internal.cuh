@@ -101,7 +101,8 @@ enum DeviceFlag : unsigned int {
     kFlagTapRange = 1u,        // a cell's tap fell outside the precomputed kernel range
     kFlagBoxRange = 2u,        // a region box index left the grid
     kFlagJobOverflow = 4u,     // a tap table would overflow its capacity
-    kFlagOrder = 8u            // bisector injection: moved positions not increasing
+    kFlagOrder = 8u,           // bisector injection: moved positions not increasing
+    kFlagTimeout = 16u         // a tensor-core kernel's bounded barrier wait gave up
 };
 
 }  // namespace soap
@@ -195,6 +196,7 @@ struct soap_ctx {
     size_t lsf_off32 = 0, lsf_offp64 = 0, lsf_offp32 = 0;
     soap::DevBuf lsf_taps, lsf_tmp;
     soap::DevBuf bis_tab;       // bisector tables of the last injection
+    soap::DevBuf tc_coef;       // tensor-core contraction: kernel rows (BF16 hi / lo) + block flags
 
     // CCF line and velocity tables, kept while the mask and the velocity grid stay the same
     soap::DevBuf ccf_tab;
@@ -295,6 +297,11 @@ struct RegionDev {      // one region as the kernels see it
 };
 
 // Active phases (Toeplitz) into dst [n_eff][n_phases][n_px].
+// Active-phase contraction on the tensor cores (SOAP_BF16X3): kfix [n_phases][ncl][n_mu][n_taps]
+// fixed-point kernels, FP32 rows / contrast / F_q of the context; out [n_eff][n_phases][n_px].
+soap_status toeplitz_tc(soap_ctx* c, const long long* kfix, int n_phases, int ncl, const int* class_type,
+                        const float* a_spot, const float* a_fac, const float* con32, bool per_bin,
+                        const int* effects, int n_eff, float* out);
 soap_status toeplitz_active(soap_ctx* c, const RegionDev* regions_host, int n_regions,
                             const double* class_temp, const int* class_type, int n_class,
                             const double* phases_host, int n_phases, uint32_t effects,

@@ -27,7 +27,6 @@ constexpr int kThreads = 192;
 // Pipeline depth per tile width: two CTAs fit on an SM (shared memory and 512 TMEM columns), so
 // one CTA's loads and MMAs overlap the other's epilogue.
 template <int BN> struct Stages { static constexpr int value = BN >= 256 ? 2 : (BN >= 128 ? 3 : 4); };
-constexpr unsigned int kFlagTimeout = 8u;
 
 // Epilogue: z = acc (+ bias[n]); a = GELU(z) when EPI_GELU, a = z * GELU'(zin[m][n]) when
 // EPI_DGELU, else a = z.  Outputs (any subset): c32 <- z (EPI_Z32) or a (EPI_A32), c16 <- bf16(a),

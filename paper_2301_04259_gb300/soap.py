@@ -19,7 +19,7 @@ LIB_PATH = _PKG / "_lib" / "libsoap.so"
 SOAP_OK, SOAP_EINVAL, SOAP_ENOMEM, SOAP_ECUDA, SOAP_ERANGE, SOAP_ETIMEOUT, SOAP_ESTATE = range(7)
 STATUS_NAMES = {0: "SOAP_OK", 1: "SOAP_EINVAL", 2: "SOAP_ENOMEM", 3: "SOAP_ECUDA",
                 4: "SOAP_ERANGE", 5: "SOAP_ETIMEOUT", 6: "SOAP_ESTATE"}
-SOAP_FP64, SOAP_FP32 = 0, 1
+SOAP_FP64, SOAP_FP32, SOAP_BF16X3 = 0, 1, 2
 SOAP_FORM_TOEPLITZ, SOAP_FORM_DIRECT = 0, 1
 SOAP_EFFECT_TOT, SOAP_EFFECT_FLUX, SOAP_EFFECT_BCONV = 1, 2, 4
 SOAP_SPOT, SOAP_FACULA = 1, 2
