@@ -155,7 +155,8 @@ __global__ void k_batch_hist(int N, int max_r, const int* __restrict__ phase_ite
                              int tap_min, int n_taps, int n_mu, int n_class, long long* kfix, int use_smem,
                              int PB, double inv_scale, int fx_bits, int64_t row_len, int64_t pad, long long* toff,
                              int* gstart,
-                             float* c32, int max_taps, int* counters, int taps_smem, unsigned int* flags) {
+                             float* c32, int max_taps, int* counters, int taps_smem, unsigned int* flags,
+                             const double* __restrict__ cell_x) {
     __shared__ RegionGeo sg[SOAP_MAX_REGIONS];
     extern __shared__ long long hist_sm[];
     const int p = blockIdx.x;
@@ -183,7 +184,7 @@ __global__ void k_batch_hist(int N, int max_r, const int* __restrict__ phase_ite
             const int c = jj * N + i;                          // N^2 < 2^31
             const int b = cell_bin[c];
             if (b < 0) continue;
-            const int owner = cell_owner(sg, nr, N, invN, i, jj, cell_mu32[c], cell_mu, c);
+            const int owner = cell_owner(sg, nr, N, invN, i, jj, cell_mu32[c], cell_mu, c, cell_x);
             if (owner < 0) continue;
             const int kk = cj[i] - tap_min;
             if (kk < 1 || kk >= n_taps) { atomicOr(flags, kFlagTapRange); continue; }
@@ -354,7 +355,7 @@ static soap_status enqueue_batch(soap_ctx* c, const BatchShape& b, float* out) {
                    c->b_kfix.as<long long>(), b.use_smem, kVariants[b.variant].PB, inv_scale, c->fx_bits, c->row_len,
                    c->pad,
                    c->b_toff.as<long long>(), c->b_gstart.as<int>(), c->b_coefs.as<float>(), b.max_taps,
-                   c->b_counters.as<int>(), b.taps_smem, c->flags);
+                   c->b_counters.as<int>(), b.taps_smem, c->flags, c->cell_x);
                SOAP_LAUNCHED(c));
     // 6 persistent contraction
     SOAP_CUDA(cudaMemsetAsync(c->b_ticket.p, 0, sizeof(unsigned int), c->stream));
@@ -563,7 +564,7 @@ soap_status batch_run(soap_ctx* c, const soap_batch_item* items, int n_items, co
     put(c->n_px); put(c->row_len); put(c->pad);
     putd(c->delta); putd(c->lam_s); putd(c->t_quiet);
     putp(out); putp(c->stream); putp(c->q32); putp(c->a32[0]); putp(c->a32[1]); putp(c->cell_I);
-    putp(c->cell_bin); putp(c->cell_mu); putp(c->cell_mu32); putp(c->flags);
+    putp(c->cell_bin); putp(c->cell_mu); putp(c->cell_mu32); putp(c->flags); putp(c->cell_x);
     const DevBuf* bufs[] = {&c->b_items, &c->b_regions, &c->b_phases, &c->b_phase_item, &c->b_phase_block,
                             &c->b_pblocks, &c->b_order, &c->b_cellIfx, &c->b_IB, &c->b_colj, &c->b_colw, &c->b_kq,
                             &c->b_qtoff, &c->b_qgs, &c->b_qc32, &c->b_fq, &c->b_geo, &c->b_kfix,

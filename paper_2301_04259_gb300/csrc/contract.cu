@@ -73,7 +73,8 @@ __global__ void k_phase_hist(int N, int n_regions, const RegionGeo* __restrict__
                              int tap_min, int n_taps, int n_mu, int n_class, long long* kout,
                              int use_smem, int PB, double inv_scale, int fx_bits, int64_t row_len, int64_t pad,
                              long long* toff, int* gstart, double* c64, float* c32, int max_taps,
-                             int* counters, int taps_smem, unsigned int* flags, int* bstart) {
+                             int* counters, int taps_smem, unsigned int* flags, int* bstart,
+                             const double* __restrict__ cell_x) {
     __shared__ RegionGeo sg[SOAP_MAX_REGIONS];
     extern __shared__ long long hist_sm[];
     const int p = blockIdx.x;
@@ -99,7 +100,7 @@ __global__ void k_phase_hist(int N, int n_regions, const RegionGeo* __restrict__
             const int c = jj * N + i;                          // N^2 < 2^31
             const int b = cell_bin[c];
             if (b < 0) continue;
-            const int owner = cell_owner(sg, n_regions, N, invN, i, jj, cell_mu32[c], cell_mu, c);
+            const int owner = cell_owner(sg, n_regions, N, invN, i, jj, cell_mu32[c], cell_mu, c, cell_x);
             if (owner < 0) continue;
             const int kk = cell_j[c] - tap_min;
             if (kk < 1 || kk >= n_taps) { atomicOr(flags, kFlagTapRange); continue; }
@@ -363,7 +364,7 @@ soap_status toeplitz_active(soap_ctx* c, const RegionDev* regions_host, int n_re
                        c->N, n_regions, c->region_geo.as<RegionGeo>(), c->cell_mu, c->cell_mu32, c->cell_j,
                        c->cell_bin, c->cell_k0, c->cell_k1, c->tap_min, c->n_taps, c->n_mu, ncl, kfix,
                        use_smem, PB, std::ldexp(1.0, -c->fx_bits), c->fx_bits, c->row_len, c->pad, toff, gstart, c64,
-                       c32, mt, c->job_counters.as<int>(), taps_smem, c->flags, bstart);
+                       c32, mt, c->job_counters.as<int>(), taps_smem, c->flags, bstart, c->cell_x);
                    SOAP_LAUNCHED(c));
         SOAP_CUDA(cudaEventRecord(c->ev_ph, c->stream));
     }

@@ -310,7 +310,8 @@ __device__ __forceinline__ bool in_earlier_box(const RegionGeo* sg, int r, int i
 // InfoMap owner of a visible cell: a cell (x, y, mu) belongs to a region iff
 // (x, y, mu) . P >= sqrt(1 - r^2); the last region in list order that contains it owns it
 // (-1: none).  An FP32 test decides cells farther than 2e-6 from the edge (its error is below
-// 1e-6); the others are decided by the explicitly rounded FP64 sequence.
+// 1e-6); the others are decided by the explicitly rounded FP64 sequence, on the cell centres
+// (2 i + 1 - N) / N of the table cellx (IEEE-divided once, as the oracle divides).
 // float(v) for |v| < 2^22 without a conversion instruction: the bits 0x4B400000 + v are the float
 // 2^23 + 2^22 + v exactly, and one subtraction leaves v.
 __device__ __forceinline__ float small_int_to_float(int v) {
@@ -333,7 +334,8 @@ struct BoxWalk {
 };
 
 __device__ __forceinline__ int cell_owner(const RegionGeo* sg, int n_regions, int N, float invN, int i, int j,
-                                          float muf, const double* __restrict__ cell_mu, int64_t c) {
+                                          float muf, const double* __restrict__ cell_mu, int64_t c,
+                                          const double* __restrict__ cellx) {
     const float xf = small_int_to_float(2 * i + 1 - N) * invN, yf = small_int_to_float(2 * j + 1 - N) * invN;
     int owner = -1;
     for (int q = 0; q < n_regions; q++) {
@@ -342,8 +344,8 @@ __device__ __forceinline__ int cell_owner(const RegionGeo* sg, int n_regions, in
         if (df > sg[q].cosrf + 2e-6f) in = true;
         else if (df < sg[q].cosrf - 2e-6f) in = false;
         else {
-            const double x = (double)(2 * i + 1 - N) / (double)N;
-            const double y = (double)(2 * j + 1 - N) / (double)N;
+            const double x = cellx[i];
+            const double y = cellx[j];
             const double dot = __dadd_rn(__dadd_rn(__dmul_rn(x, sg[q].P[0]), __dmul_rn(y, sg[q].P[1])),
                                          __dmul_rn(cell_mu[c], sg[q].P[2]));
             in = dot >= sg[q].cosr;
