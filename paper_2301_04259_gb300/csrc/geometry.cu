@@ -50,6 +50,10 @@ __device__ __forceinline__ int nearest_mu(double mu, int n_mu, const MuTable& mu
 // phase), an FP32 copy of mu (for the FP32 membership pre-test), and adds the cell to the quiet
 // velocity kernels (shared-memory 64-bit integer sums, then one atomic per non-zero bin) and
 // to the total intensity.  Integer sums are exact, so the result does not depend on order.
+// SERIES: every |beta| and the grid step are at most 1e-3 (decided on the host), so atanh and
+// expm1 are their short series; otherwise the library functions (only one form is compiled into
+// each instance, so no cell evaluates both).
+template <bool SERIES>
 __global__ void __launch_bounds__(128)
 k_geometry(int N, double vsini, double sin_i, double cos_i, double alpha, double u1, double u2,
            double inv_c, double inv_delta, double delta, double inv_expm1_delta, int n_mu,
@@ -82,11 +86,11 @@ k_geometry(int N, double vsini, double sin_i, double cos_i, double alpha, double
             const double slat = y * sin_i + mu * cos_i;                    // sin(latitude) of the cell
             const double v = vsini * x * (1.0 + alpha * slat * slat);      // x > 0 recedes
             const double beta = v * inv_c;
-            const double ab = fabs(beta) <= 1e-3 ? atanh_small(beta) : atanh(beta);   // ln D
+            const double ab = SERIES ? atanh_small(beta) : atanh(beta);    // ln D
             const double jd = ceil(ab * inv_delta);                        // j = ceil(s), s = ln D / Delta
             int jt = (int)jd;
             const double e = fma(jd, delta, -ab);                          // (j - s) Delta
-            const double w = (delta <= 1e-3 ? expm1_small(e) : expm1(e)) * inv_expm1_delta;
+            const double w = (SERIES ? expm1_small(e) : expm1(e)) * inv_expm1_delta;
             if (jt - 1 < tap_min || jt > tap_max) {
                 atomicOr(flags, kFlagTapRange);
                 jt = jt < tap_min + 1 ? tap_min + 1 : tap_max;
@@ -276,7 +280,10 @@ soap_status geometry_init(soap_ctx* c) {
     size_t nb = (size_t)c->n_mu * c->n_taps;
     const double scale = std::ldexp(1.0, c->fx_bits);
     size_t smem = nb * sizeof(long long);
-    SOAP_TRY(fit_dynamic_smem(k_geometry, smem));
+    // largest |beta| = vsini (1 + |alpha|) / c over the disk (|x| < 1, sin^2(latitude) <= 1)
+    const bool series = c->vsini * (1.0 + std::fabs(c->alpha)) / kCKms <= 1e-3 && c->delta <= 1e-3;
+    auto kern = series ? k_geometry<true> : k_geometry<false>;
+    SOAP_TRY(fit_dynamic_smem(kern, smem));
     SOAP_CUDA(cudaEventRecord(c->ev_fork, c->stream));
     SOAP_CUDA(cudaStreamWaitEvent(c->aux, c->ev_fork, 0));
     {
@@ -286,7 +293,7 @@ soap_status geometry_init(soap_ctx* c) {
         SOAP_CUDA(cudaMemsetAsync(c->sum_I_fixed, 0, 2 * sizeof(long long), c->stream));
         SOAP_CUDA(cudaMemsetAsync(c->geo_counter, 0, sizeof(int), c->stream));
         dim3 grid((unsigned)((c->N + 127) / 128), (unsigned)c->N);
-        k_geometry<<<grid, 128, smem, c->stream>>>(
+        kern<<<grid, 128, smem, c->stream>>>(
             c->N, c->vsini, std::sin(incl), std::cos(incl), c->alpha, c->u1, c->u2, 1.0 / kCKms,
             1.0 / c->delta, c->delta, 1.0 / std::expm1(c->delta), c->n_mu, mus, c->mu_sorted, c->tap_min,
             tap_max, c->n_taps, scale, c->cell_I, c->cell_w, c->cell_mu, c->cell_mu32, c->cell_j,

@@ -105,6 +105,20 @@ def test_quiet_ragged_and_edge_cases(S, N, n_px, vsini, incl, alpha, n_mu):
         assert rel(gpu_quiet(S, case, form, S.SOAP_FP32), ref, ref.max()) <= TOL32
 
 
+@pytest.mark.parametrize("lam0,lam1,n_px,vsini", [(5000.0, 6000.0, 64, 2.0), (5000.0, 5500.0, 1000, 400.0)])
+def test_quiet_library_atanh_and_expm1(S, lam0, lam1, n_px, vsini):
+    """A coarse grid (Delta = 2.9e-3) and a 400 km/s rotator (|beta| up to 1.3e-3): the geometry
+    takes the library atanh / expm1 instead of their short series."""
+    case = synth.make_case(n_px, name="q", grid_n=33, lambda_start=lam0, lambda_end=lam1,
+                           n_px=n_px, mu_values=np.linspace(0.1, 1.0, 4), n_lines=15,
+                           depth_law="uniform", sigma_law="angstrom", vsini_kms=vsini,
+                           incl_deg=70.0, diff_rot_alpha=0.0, regions=[], n_phases=1)
+    ref = O.quiet(case.star, case.quiet)
+    for form in (0, 1):
+        assert rel(gpu_quiet(S, case, form, S.SOAP_FP64), ref, ref.max()) <= TOL64
+        assert rel(gpu_quiet(S, case, form, S.SOAP_FP32), ref, ref.max()) <= TOL32
+
+
 # ------------------------------------------------------------------------------------------
 # active star
 # ------------------------------------------------------------------------------------------
