@@ -248,11 +248,14 @@ soap_status soap_quiet_spectrum(soap_ctx* ctx, int32_t form, int32_t precision, 
  *  regions    host [n_regions], 0 .. SOAP_MAX_REGIONS, order-significant (see soap_region).
  *  phases     host [n_phases] rotational phases (any real value; 1.0 = one rotation).
  *  effects    OR of SOAP_EFFECT_* (at least one).
- *  precision  SOAP_FP64 (float64 output) or SOAP_FP32 (float32 output).
+ *  precision  SOAP_FP64 (float64 output), SOAP_FP32 or SOAP_BF16X3 (float32 output).
  *  out        [n_effects][n_phases][n_px], effects in the order TOT, FLUX, BCONV (those
  *             requested); out[e][p][m] = F_q[m] - Delta F_e[p][m] (Eq. 4).  Host or device.
  * Errors: SOAP_ESTATE if no active spectrum was set; SOAP_ERANGE if more than
- * SOAP_MAX_CLASSES distinct (type, temperature) pairs are given. */
+ * SOAP_MAX_CLASSES distinct (type, temperature) pairs are given, or (SOAP_BF16X3) if the
+ * row windows of a 128-pixel tile (3 row sets x n_mu bins x (127 + n_taps) values), the
+ * contrast of the tile and the decode table need more than 227 KB of shared memory;
+ * SOAP_ETIMEOUT if a tensor-core barrier wait gave up (bounded, about a second). */
 soap_status soap_active_phases(soap_ctx* ctx, const soap_region* regions, int32_t n_regions,
                                const double* phases, int32_t n_phases, uint32_t effects,
                                int32_t precision, void* out, int out_on_device);

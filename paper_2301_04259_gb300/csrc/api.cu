@@ -272,7 +272,7 @@ static soap_status check_flags(soap_ctx* c) {
         set_error("device status word 0x%x (tap range %d, box range %d, job overflow %d, bisector order %d, "
                   "tensor-core wait timeout %d)", f, !!(f & kFlagTapRange), !!(f & kFlagBoxRange),
                   !!(f & kFlagJobOverflow), !!(f & kFlagOrder), !!(f & kFlagTimeout));
-        return SOAP_ERANGE;
+        return (f & kFlagTimeout) ? SOAP_ETIMEOUT : SOAP_ERANGE;
     }
     return SOAP_OK;
 }
