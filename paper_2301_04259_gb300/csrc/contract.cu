@@ -136,9 +136,10 @@ __global__ void k_phase_hist(int N, int n_regions, const RegionGeo* __restrict__
 // ---------------------------------------------------------------------------------------
 // contraction
 // ---------------------------------------------------------------------------------------
-// One block: pixel tile blockIdx.x of phase block blockIdx.y, effect blockIdx.z.
+// One block: pixel tile blockIdx.x of phase block blockIdx.y, effect blockIdx.z.  Eight blocks
+// per SM (at most 64 registers with 128 threads) keep the occupancy the tap loads need.
 template <typename T, int PB, int R, int THREADS>
-__global__ void __launch_bounds__(THREADS)
+__global__ void __launch_bounds__(THREADS, THREADS == 128 ? 8 : 1)
 k_contract(int64_t n_px, Rows<T> rows, const long long* __restrict__ toff, const int* __restrict__ gstart,
            int G, int max_taps, const T* __restrict__ coefs, ClassTypes ctype, const T* __restrict__ contrast,
            const T* __restrict__ fq, int n_phases, EffectList effs, T* __restrict__ out,

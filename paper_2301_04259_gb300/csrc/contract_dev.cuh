@@ -90,13 +90,13 @@ __device__ __forceinline__ void contract_tile(int64_t n_px, const Rows<T>& rows,
         const int64_t m = m0 + (int64_t)r * THREADS;
         mcl[r] = m < n_px ? m : n_px - 1;
     }
+    // The tap sums accumulate from zero and F_q is added once at the store: every FMA then
+    // rounds at the scale of the residual, not of the continuum (about 8x finer in FP32).
     T acc[PB][R];
 #pragma unroll
-    for (int r = 0; r < R; r++) {
-        const T f0 = fq ? fq[mcl[r]] : T(0);
+    for (int r = 0; r < R; r++)
 #pragma unroll
-        for (int p = 0; p < PB; p++) acc[p][r] = f0;
-    }
+        for (int p = 0; p < PB; p++) acc[p][r] = T(0);
     // group 0: subtract (active star) or add (quiet star) the quiet-row convolutions
     {
         const T* base = rows.q + m0;
@@ -189,7 +189,7 @@ __device__ __forceinline__ void contract_tile(int64_t n_px, const Rows<T>& rows,
 #pragma unroll
         for (int r = 0; r < R; r++) {
             const int64_t m = m0 + (int64_t)r * THREADS;
-            if (m < n_px) out_rows[(int64_t)p * n_px + m] = acc[p][r];
+            if (m < n_px) out_rows[(int64_t)p * n_px + m] = fq ? fq[mcl[r]] + acc[p][r] : acc[p][r];
         }
     }
 }

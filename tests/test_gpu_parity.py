@@ -198,6 +198,28 @@ def test_active_degenerate_cases(S, cfg1, cfg1_ref):
     assert rel(g, ref, q.max()) <= TOL64
 
 
+def test_active_maximum_sizes(S):
+    """At the library's limits: 64 mu bins, 64 regions (overlapping spots and faculae in list
+    order) of 8 classes (distinct type and temperature), 6 phases; FP64 and FP32."""
+    rng = np.random.default_rng(64)
+    temps = [(SPOT, 3900.0), (SPOT, 4300.0), (SPOT, 4700.0), (SPOT, 5100.0),
+             (FACULA, 5900.0), (FACULA, 6000.0), (FACULA, 6100.0), (FACULA, 6200.0)]
+    regs = []
+    for k in range(64):
+        typ, tk = temps[k % 8]
+        regs.append(Region(typ, float(rng.uniform(-70, 70)), float(rng.uniform(0, 360)),
+                           float(rng.uniform(0.02, 0.25)), tk))
+    c = synth.make_case(640, name="max", grid_n=41, lambda_start=6000.0, lambda_end=6010.0, n_px=1500,
+                        mu_values=(np.arange(64) + 0.5) / 64.0, n_lines=12, depth_law="uniform",
+                        sigma_law="angstrom", vsini_kms=3.0, incl_deg=75.0, diff_rot_alpha=0.0,
+                        regions=regs, n_phases=6)
+    assert c.star.n_mu == S.SOAP_MAX_MU and len(regs) == S.SOAP_MAX_REGIONS
+    q = O.quiet(c.star, c.quiet)
+    ref = O.active(c.star, c.quiet, c.active, regs, c.phases, effects=7)
+    assert rel(gpu_active(S, c, regs, c.phases, 7, S.SOAP_FP64), ref, q.max()) <= TOL64
+    assert rel(gpu_active(S, c, regs, c.phases, 7, S.SOAP_FP32), ref, q.max()) <= TOL32
+
+
 def test_active_is_deterministic_and_host_output_matches(S, complex_case):
     c = complex_case
     a = gpu_active(S, c, c.regions, c.phases, 7, S.SOAP_FP64)
