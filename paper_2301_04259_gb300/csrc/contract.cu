@@ -74,7 +74,7 @@ __global__ void k_phase_hist(int N, int n_regions, const RegionGeo* __restrict__
                              int use_smem, int PB, double inv_scale, int fx_bits, int64_t row_len, int64_t pad,
                              long long* toff, int* gstart, double* c64, float* c32, int max_taps,
                              int* counters, int taps_smem, unsigned int* flags, int* bstart,
-                             const double* __restrict__ cell_x) {
+                             const double* __restrict__ cell_x, int mode) {
     __shared__ RegionGeo sg[SOAP_MAX_REGIONS];
     extern __shared__ long long hist_sm[];
     const int p = blockIdx.x;
@@ -128,7 +128,7 @@ __global__ void k_phase_hist(int N, int n_regions, const RegionGeo* __restrict__
     __syncthreads();
     if (s_last) {
         __threadfence();
-        build_taps_dev(kout, pbk, (int)gridDim.x, n_class, n_mu, n_taps, tap_min, PB, 1, inv_scale, fx_bits, row_len,
+        build_taps_dev(kout, pbk, (int)gridDim.x, n_class, n_mu, n_taps, tap_min, PB, mode, inv_scale, fx_bits, row_len,
                        pad, toff, gstart, c64, c32, max_taps, taps_smem ? hist_sm : nullptr, flags, bstart);
     }
 }
@@ -143,11 +143,17 @@ __global__ void __launch_bounds__(THREADS, THREADS == 128 ? 8 : 1)
 k_contract(int64_t n_px, Rows<T> rows, const long long* __restrict__ toff, const int* __restrict__ gstart,
            int G, int max_taps, const T* __restrict__ coefs, ClassTypes ctype, const T* __restrict__ contrast,
            const T* __restrict__ fq, int n_phases, EffectList effs, T* __restrict__ out,
-           const int* __restrict__ bstart, int n_mu) {
+           const int* __restrict__ bstart, int n_mu, int fold) {
     const int pb = blockIdx.y;
     const int np = min(PB, n_phases - pb * PB);
     T* out_rows = out + (int64_t)blockIdx.z * n_phases * n_px + (int64_t)pb * PB * n_px;
     const TableContrast<T> con{contrast, n_px, ctype};
+    if (fold) {
+        contract_tile_fold<T, PB, R, THREADS>(n_px, rows, toff + (int64_t)pb * max_taps, gstart + (int64_t)pb * (G + 1),
+                                              G, coefs + (int64_t)pb * max_taps * PB, con, fq, effs.e[blockIdx.z],
+                                              blockIdx.x, np, out_rows);
+        return;
+    }
     contract_tile<T, PB, R, THREADS>(n_px, rows, toff + (int64_t)pb * max_taps, gstart + (int64_t)pb * (G + 1), G,
                                      coefs + (int64_t)pb * max_taps * PB, con, fq, effs.e[blockIdx.z], blockIdx.x,
                                      np, out_rows, bstart ? bstart + (int64_t)pb * (G * n_mu + 1) : nullptr, n_mu);
@@ -166,7 +172,8 @@ static soap_status launch_contract(soap_ctx* c, int n_blocks, int G, int max_tap
                                    const long long* toff, const int* gstart, const T* coefs,
                                    const ClassTypes& ct, const T* contrast, const T* fq,
                                    int n_phases, const EffectList& el, int n_eff, T* out,
-                                   const T* q, const T* a0, const T* a1, const int* bstart = nullptr) {
+                                   const T* q, const T* a0, const T* a1, const int* bstart = nullptr,
+                                   int fold = 0) {
     Rows<T> rows;
     rows.q = q; rows.a[0] = a0; rows.a[1] = a1;
     int64_t tiles = (c->n_px + (int64_t)THREADS * R - 1) / ((int64_t)THREADS * R);
@@ -174,7 +181,7 @@ static soap_status launch_contract(soap_ctx* c, int n_blocks, int G, int max_tap
     SOAP_TIMED(c, fq ? SOAP_TIMER_CONTRACT : SOAP_TIMER_CONTRACT_QUIET,
                k_contract<T, PB, R, THREADS><<<grid, THREADS, 0, c->stream>>>(
                    c->n_px, rows, toff, gstart, G, max_taps, coefs, ct, contrast, fq, n_phases, el, out,
-                   bstart, c->n_mu);
+                   bstart, c->n_mu, fold);
                SOAP_LAUNCHED(c));
     return SOAP_OK;
 }
@@ -197,7 +204,7 @@ constexpr int kPB32 = SOAP_PB32, kR32 = SOAP_R32, kT32 = 128;
 static soap_status tap_buffers(soap_ctx* c, int n_phases, int n_class, int PB, int mode, long long** toff,
                                int** gstart, double** c64, float** c32, int* n_blocks, int* G, int* max_taps,
                                int** bstart = nullptr) {
-    *G = mode == 0 ? 1 : 1 + n_class;
+    *G = mode == 0 ? 1 : (mode == 1 ? 1 + n_class : n_class);
     *n_blocks = (n_phases + PB - 1) / PB;
     *max_taps = *G * c->n_mu * c->n_taps;
     size_t tb = (size_t)*n_blocks * *max_taps * sizeof(long long);
@@ -328,7 +335,10 @@ soap_status toeplitz_active(soap_ctx* c, const RegionDev* regions_host, int n_re
     // tap tables are built by the last block of each phase block (fused into k_phase_hist)
     const int PB = f64 ? kPB64 : kPB32;
     long long* toff; int* gstart; double* c64; float* c32; int nbk, G, mt; int* bstart = nullptr;
-    SOAP_TRY(tap_buffers(c, n_phases, ncl, PB, 1, &toff, &gstart, &c64, &c32, &nbk, &G, &mt,
+    // tables without the quiet group (mode 2: the contraction folds the quiet rows into the classes'
+    // operands) unless the contrast has a row per mu bin (mode 1, per-bin folds)
+    const int tmode = per_bin ? 1 : 2;
+    SOAP_TRY(tap_buffers(c, n_phases, ncl, PB, tmode, &toff, &gstart, &c64, &c32, &nbk, &G, &mt,
                          per_bin ? &bstart : nullptr));
     SOAP_TRY(ensure(c->job_counters, (size_t)nbk * sizeof(int)));
     SOAP_CUDA(cudaMemsetAsync(c->job_counters.p, 0, (size_t)nbk * sizeof(int), c->stream));
@@ -365,7 +375,7 @@ soap_status toeplitz_active(soap_ctx* c, const RegionDev* regions_host, int n_re
                        c->N, n_regions, c->region_geo.as<RegionGeo>(), c->cell_mu, c->cell_mu32, c->cell_j,
                        c->cell_bin, c->cell_k0, c->cell_k1, c->tap_min, c->n_taps, c->n_mu, ncl, kfix,
                        use_smem, PB, std::ldexp(1.0, -c->fx_bits), c->fx_bits, c->row_len, c->pad, toff, gstart, c64,
-                       c32, mt, c->job_counters.as<int>(), taps_smem, c->flags, bstart, c->cell_x);
+                       c32, mt, c->job_counters.as<int>(), taps_smem, c->flags, bstart, c->cell_x, tmode);
                    SOAP_LAUNCHED(c));
         SOAP_CUDA(cudaEventRecord(c->ev_ph, c->stream));
     }
@@ -388,10 +398,10 @@ soap_status toeplitz_active(soap_ctx* c, const RegionDev* regions_host, int n_re
     if (f64)
         return launch_contract<double, kPB64, kR64, kT64>(c, nbk, G, mt, toff, gstart, c64, ct, con64,
                                                          c->fq.as<double>(), n_phases, el, n_eff,
-                                                         (double*)dst, c->q64, a64s, a64f, bstart);
+                                                         (double*)dst, c->q64, a64s, a64f, bstart, tmode == 2);
     return launch_contract<float, kPB32, kR32, kT32>(c, nbk, G, mt, toff, gstart, c32, ct, con32,
                                                     c->fq.as<float>(), n_phases, el, n_eff,
-                                                    (float*)dst, c->q32, a32s, a32f, bstart);
+                                                    (float*)dst, c->q32, a32s, a32f, bstart, tmode == 2);
 }
 
 }  // namespace soap

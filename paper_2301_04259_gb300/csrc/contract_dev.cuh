@@ -195,6 +195,68 @@ __device__ __forceinline__ void contract_tile(int64_t n_px, const Rows<T>& rows,
 }
 
 
+// Folded form for tap tables without the quiet group (builder mode 2: group g = class g): the
+// quiet rows enter each class's operand, X_cl[m - k] = Ca_cl[m] S_a(cl)[m - k] + Cq_cl[m] S_q[m - k]
+// with (Ca, Cq) = (C_cl, -1) for the total effect, (0, C_cl - 1) for the flux effect and (1, -1)
+// for the convective blueshift effect, so that out[p][m] = F_q[m] + sum_cl sum_taps K X (the
+// quiet group's kernel is -sum_cl K_cl): one coefficient vector and one FMA per phase and pixel
+// per tap instead of two.  Classes with a contrast row per mu bin keep contract_tile.
+template <typename T, int PB, int R, int THREADS, class Con>
+__device__ __forceinline__ void contract_tile_fold(int64_t n_px, const Rows<T>& rows,
+                                                   const long long* __restrict__ toff, const int* __restrict__ gs,
+                                                   int G, const T* __restrict__ cb, const Con& con,
+                                                   const T* __restrict__ fq, int eff, int64_t tile, int np,
+                                                   T* __restrict__ out_rows) {
+    const int64_t m0 = tile * THREADS * R + threadIdx.x;
+    int64_t mcl[R];
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+        const int64_t m = m0 + (int64_t)r * THREADS;
+        mcl[r] = m < n_px ? m : n_px - 1;
+    }
+    T acc[PB][R];
+#pragma unroll
+    for (int p = 0; p < PB; p++)
+#pragma unroll
+        for (int r = 0; r < R; r++) acc[p][r] = T(0);
+    const T* bq = rows.q + m0;
+    for (int g = 0; g < G; g++) {
+        const int t0 = gs[g], t1 = gs[g + 1];
+        if (t0 == t1) continue;
+        const T* ba = (eff == SOAP_EFFECT_FLUX ? rows.q : rows.a[con.type(g) == SOAP_FACULA ? 1 : 0]) + m0;
+        T ca[R], cq[R];
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const T C = eff == SOAP_EFFECT_BCONV ? T(1) : con.at(g, mcl[r]);
+            ca[r] = eff == SOAP_EFFECT_FLUX ? T(0) : C;
+            cq[r] = eff == SOAP_EFFECT_FLUX ? C - T(1) : T(-1);
+        }
+#pragma unroll 4
+        for (int t = t0; t < t1; t++) {
+            const long long off = __ldg(toff + t);
+            T x[R];
+#pragma unroll
+            for (int r = 0; r < R; r++)
+                x[r] = fma(ca[r], __ldg(ba + off + r * THREADS), cq[r] * __ldg(bq + off + r * THREADS));
+            T cv[PB];
+            load_coefs<T, PB>(cb + (int64_t)t * PB, cv);
+#pragma unroll
+            for (int p = 0; p < PB; p++)
+#pragma unroll
+                for (int r = 0; r < R; r++) acc[p][r] = fma(cv[p], x[r], acc[p][r]);
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < PB; p++) {
+        if (p >= np) break;
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const int64_t m = m0 + (int64_t)r * THREADS;
+            if (m < n_px) out_rows[(int64_t)p * n_px + m] = fq ? fq[mcl[r]] + acc[p][r] : acc[p][r];
+        }
+    }
+}
+
 // Contrast rows from a device list of temperatures (one row per class and mu bin when facula
 // temperatures depend on mu): FP64 rows (and their FP32 copies).
 static __global__ void k_contrast_rows(int64_t n_px, double lam_s, double delta, double t_quiet, int n_rows,

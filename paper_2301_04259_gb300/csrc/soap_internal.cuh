@@ -408,7 +408,8 @@ __device__ __forceinline__ float fixed_to_float(long long K, int bits) {
 //   coef[tap][PB] kernel value of each phase of the block (0 where a phase has none)
 // kfix: [n_phases][n_class][n_mu][n_taps] in units of 2^-fx_bits (inv_scale = 2^-fx_bits).
 // mode 0 (quiet): one group, +K of class 0.  mode 1 (active): group 0 = -sum_cl K (quiet rows),
-// group g = +K of class g-1.  Block pb covers phases pb*PB .. pb*PB+PB-1; its outputs start at
+// group g = +K of class g-1.  mode 2 (active, quiet rows folded into the classes' operands):
+// group g = +K of class g.  Block pb covers phases pb*PB .. pb*PB+PB-1; its outputs start at
 // toff + pb*max_taps,
 // gstart + pb*(G+1) and coef + pb*max_taps*PB.  A table that would exceed max_taps is left
 // empty and flags kFlagJobOverflow.
@@ -424,7 +425,7 @@ __device__ __forceinline__ void build_taps_dev(const long long* __restrict__ kfi
     __shared__ int s_warp[32];
     __shared__ int s_total;
     const int use_smem = s_k != nullptr;
-    const int G = mode == 0 ? 1 : 1 + n_class;
+    const int G = mode == 0 ? 1 : (mode == 1 ? 1 + n_class : n_class);
     const int ngb = G * n_mu;
     const int p0 = pb * PB;
     const int np = min(PB, n_phases - p0);
@@ -459,14 +460,14 @@ __device__ __forceinline__ void build_taps_dev(const long long* __restrict__ kfi
             for (int cl = 0; cl < n_class; cl++) s += kval(base + ((int64_t)cl * n_mu + b) * n_taps + kk);
             return -s;
         }
-        const int cl = mode == 0 ? 0 : g - 1;
+        const int cl = mode == 0 ? 0 : (mode == 1 ? g - 1 : g);
         return kval(base + ((int64_t)cl * n_mu + b) * n_taps + kk);
     };
     // tap range of each (group, bin) over the block's phases
     for (int t = threadIdx.x; t < ngb; t += blockDim.x) {
         const int g = t / n_mu, b = t % n_mu;
         int lo = n_taps, hi = -1;
-        const int c0 = (mode == 0 || g == 0) ? 0 : g - 1;
+        const int c0 = mode == 0 ? 0 : (mode == 2 ? g : (g == 0 ? 0 : g - 1));
         const int c1 = (mode == 1 && g == 0) ? n_class : c0 + 1;
         for (int pl = 0; pl < np; pl++) {
             const long long* base = K + (int64_t)pl * nb;
