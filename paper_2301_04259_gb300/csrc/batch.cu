@@ -211,8 +211,9 @@ __global__ void k_batch_hist(int N, int max_r, const int* __restrict__ phase_ite
     __syncthreads();
     if (s_last) {
         __threadfence();
-        build_taps_dev(kfix + (int64_t)pbd.first_phase * nb, 0, pbd.np, n_class, n_mu, n_taps, tap_min, PB, 1,
-                       inv_scale, fx_bits, row_len, pad, toff + (int64_t)pbk * max_taps, gstart + (int64_t)pbk * (n_class + 2),
+        // tables of the classes only (mode 2): the contraction folds the quiet rows into their operands
+        build_taps_dev(kfix + (int64_t)pbd.first_phase * nb, 0, pbd.np, n_class, n_mu, n_taps, tap_min, PB, 2,
+                       inv_scale, fx_bits, row_len, pad, toff + (int64_t)pbk * max_taps, gstart + (int64_t)pbk * (n_class + 1),
                        nullptr, c32 + (int64_t)pbk * max_taps * PB, max_taps, taps_smem ? hist_sm : nullptr, flags);
     }
 }
@@ -244,8 +245,8 @@ k_batch_contract(int64_t n_px, Rows<float> rows, const long long* __restrict__ t
         float* orow = out + (int64_t)pb.first_phase * n_px;
         const PlanckContrast32 con{aq, fd, items[pb.item].cls_type, items[pb.item].cls_a};
         for (int tile = 0; tile < n_tiles; tile++)
-            contract_tile<float, PB, R, THREADS>(n_px, rows, tt, gs, G, cb, con, fqi, SOAP_EFFECT_TOT, tile, pb.np,
-                                                 orow);
+            contract_tile_fold<float, PB, R, THREADS>(n_px, rows, tt, gs, G, cb, con, fqi, SOAP_EFFECT_TOT, tile,
+                                                      pb.np, orow);
     }
 }
 
@@ -503,8 +504,8 @@ soap_status batch_run(soap_ctx* c, const soap_batch_item* items, int n_items, co
     b.variant = variant;
     b.n_class = n_class;
     b.residual = residual ? 1 : 0;
-    b.G = 1 + n_class;
-    b.max_taps = b.G * c->n_mu * c->n_taps;
+    b.G = n_class;                                     // class groups (quiet rows folded in)
+    b.max_taps = std::max(b.G, 1) * c->n_mu * c->n_taps;
     b.nbk = (int64_t)n_class * c->n_mu * c->n_taps;
     const size_t hist_bytes = (size_t)b.nbk * sizeof(long long);
     const size_t kslice_bytes = (size_t)V.PB * b.nbk * sizeof(long long);
