@@ -799,6 +799,40 @@ def measure_tensor_contraction(args, dev, bf16_peak):
         res["tcgen05_bf16x3"].update({"gemm": [m_pad, p_pad, k_pad], "executed_tflop": round(flops / 1e12, 4),
                                       "achieved_tflops": round(tf, 1), "frac_of_bf16_peak": round(tf / bf16_peak, 4)})
         res["max_abs_diff_vs_fp32"] = float((outs["tcgen05_bf16x3"] - outs["simt_fp32"]).abs().max().item())
+        # the CCF of the same spectra in its two forms (soap_rv_ccf, FP32 spectra in HBM)
+        from paper_2301_04259_gb300 import synth
+        spec = outs["simt_fp32"][0]
+        lo, vstep, nv = synth.velocity_grid(st.vsini_kms)
+        ccf, rvs = {}, {}
+        for name, tcf in (("simt_fp32", False), ("tcgen05_bf16x3", True)):
+            rv = torch.empty(P, dtype=torch.float64, device=dev)
+            call = lambda: S.soap_rv_ccf(ctx, spec, case.mask_lambda, case.mask_weight, case.mask_width_kms,
+                                         lo, vstep, nv, rv, tensor_cores=tcf)
+            for _ in range(3):
+                call()
+            torch.cuda.synchronize()
+            S.soap_reset_kernel_times(ctx)
+            S.soap_set_profiling(ctx, True)
+            for _ in range(max(3, args.steps)):
+                call()
+            torch.cuda.synchronize()
+            tot, n = S.soap_get_kernel_time(ctx, S.TIMERS.index("ccf"))
+            S.soap_set_profiling(ctx, False)
+            ccf[name] = {"ms": round(tot / max(1, n), 4)}
+            rvs[name] = rv.cpu().numpy()
+        # executed tensor work: 3 products over M = 128 spectra, N = velocities rounded up to 16,
+        # K = each pixel chunk rounded up to 64 (one wave of CTAs over the pixels)
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        per = -(-(n_px * -(-P // 128)) // sms)
+        chunk = max(64, -(-per // 64) * 64)
+        k_exec = sum(-(-min(chunk, n_px - p0) // 64) * 64 for p0 in range(0, n_px, chunk))
+        flops = 2.0 * 3 * 128 * (-(-nv // 16) * 16) * k_exec * (-(-P // 128))
+        tf = flops / (ccf["tcgen05_bf16x3"]["ms"] * 1e-3) / 1e12
+        ccf["tcgen05_bf16x3"].update({"gemm": [128 * (-(-P // 128)), -(-nv // 16) * 16, k_exec],
+                                      "executed_tflop": round(flops / 1e12, 4), "achieved_tflops": round(tf, 1),
+                                      "frac_of_bf16_peak": round(tf / bf16_peak, 4)})
+        ccf["max_rv_diff_cm_s"] = float(np.nanmax(np.abs(rvs["tcgen05_bf16x3"] - rvs["simt_fp32"])) * 1e5)
+        res["ccf"] = ccf
     finally:
         S.soap_free(ctx)
     res["note"] = ("the dense GEMM executes 3 x k_pad multiply-adds per (phase, pixel); the SIMT kernel visits "

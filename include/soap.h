@@ -64,7 +64,8 @@ typedef enum {
  * SOAP_BF16X3 (active-phase calls only: soap_active_phases(_radii), soap_active_rv): as
  * SOAP_FP32, but the contraction of Eqs. 1-4 runs on the tensor cores as a GEMM (pixels x
  * phases x (class, mu bin, tap)) with both operands split into BF16 high and low parts and three
- * products accumulated in FP32 (outputs float32). */
+ * products accumulated in FP32 (outputs float32); in soap_active_rv the CCF runs the same way
+ * (as soap_rv_ccf with spectra_f32 = 2). */
 typedef enum {
     SOAP_FP64 = 0,
     SOAP_FP32 = 1,
@@ -427,7 +428,11 @@ soap_status soap_batch_autotune(soap_ctx* ctx, const soap_batch_item* items, int
 
 /* Radial velocities from a line-mask CCF and a Gaussian fit (Sect. 4.1).
  *  spectra        [n_spec][n_px] on the context's grid, float64 (spectra_f32 = 0) or float32
- *                 (spectra_f32 = 1); host or device per spectra_on_device.
+ *                 (spectra_f32 = 1, or 2: float32 with the CCF sum as a tensor-core GEMM over
+ *                 pixels, both operands split into BF16 hi + lo, three products, FP32
+ *                 accumulation; where that form does not apply -- a mask not sorted by
+ *                 wavelength or more than 240 velocities -- 2 computes as 1); host or device
+ *                 per spectra_on_device.  Other values: SOAP_EINVAL.
  *  mask_lambda    host [n_lines] rest wavelengths (Angstrom); mask_weight host [n_lines].
  *  mask_width_kms full width W of each mask box in velocity.
  *  v_lo, v_step, n_v  velocity grid v_k = v_lo + k v_step (km/s), n_v >= 5.

@@ -220,7 +220,7 @@ static void free_ctx_memory(soap_ctx* c) {
         if (p) cudaFree(p);
     DevBuf* bufs[] = {&c->stage_in, &c->fq, &c->contrast, &c->kphase, &c->jobs, &c->coefs, &c->job_counters,
                       &c->regions, &c->region_geo, &c->phases, &c->out_stage, &c->partial, &c->ccf_tmp,
-                      &c->ccf_tab, &c->lsf_taps, &c->lsf_tmp, &c->bis_tab, &c->tc_coef};
+                      &c->ccf_tab, &c->lsf_taps, &c->lsf_tmp, &c->bis_tab, &c->tc_coef, &c->ccf_m};
     for (DevBuf* b : bufs) release(*b);
     release_host(c->host_stage);
     ring_release(c);
@@ -934,7 +934,7 @@ soap_status soap_active_rv(soap_ctx* c, const soap_region* regions, int32_t n_re
         }
         SOAP_TRY(active_lsf(c, A, n_regions, phases, n_phases, effect, precision, sp, sbytes));
         return rv_ccf_run(c, sp, f32, n_phases, mask_lambda, mask_weight, n_lines, mask_width_kms,
-                          v_lo, v_step, n_v, rv_kms, nullptr, nullptr);
+                          v_lo, v_step, n_v, rv_kms, nullptr, nullptr, precision == SOAP_BF16X3);
     }
     // host results: computed into one of two alternating device buffers; the spectra go to the
     // host on out_stream while the CCF runs, the RVs after the fit
@@ -954,7 +954,7 @@ soap_status soap_active_rv(soap_ctx* c, const soap_region* regions, int32_t n_re
         SOAP_CUDA(cudaMemcpyAsync(spectra_out, spec_d, sbytes, cudaMemcpyDeviceToHost, c->out_stream));
     }
     SOAP_TRY(rv_ccf_run(c, spec_d, f32, n_phases, mask_lambda, mask_weight, n_lines, mask_width_kms,
-                        v_lo, v_step, n_v, rv_d, nullptr, nullptr));
+                        v_lo, v_step, n_v, rv_d, nullptr, nullptr, precision == SOAP_BF16X3));
     SOAP_CUDA(cudaEventRecord(c->dn_rv[o], c->stream));
     SOAP_CUDA(cudaStreamWaitEvent(c->out_stream, c->dn_rv[o], 0));
     SOAP_CUDA(cudaMemcpyAsync(rv_kms, rv_d, (size_t)n_phases * 8, cudaMemcpyDeviceToHost, c->out_stream));
@@ -976,6 +976,7 @@ soap_status soap_rv_ccf(soap_ctx* c, const void* spectra, int32_t spectra_f32, i
         set_error("NULL argument"); return SOAP_EINVAL;
     }
     if (n_spec < 0) { set_error("need n_spec >= 0"); return SOAP_EINVAL; }
+    if (spectra_f32 < 0 || spectra_f32 > 2) { set_error("spectra_f32 must be 0, 1 or 2"); return SOAP_EINVAL; }
     SOAP_TRY(check_rv(c, mask_lambda, mask_weight, n_lines, mask_width_kms, v_lo, v_step, n_v));
     if (n_spec == 0) return SOAP_OK;
     size_t esz = spectra_f32 ? 4 : 8;
@@ -1002,7 +1003,7 @@ soap_status soap_rv_ccf(soap_ctx* c, const void* spectra, int32_t spectra_f32, i
         ccf_d = (double*)(base + o_ccf);
     }
     SOAP_TRY(rv_ccf_run(c, dspec, spectra_f32 ? 1 : 0, n_spec, mask_lambda, mask_weight, n_lines,
-                        mask_width_kms, v_lo, v_step, n_v, rv_d, fit_d, ccf_d));
+                        mask_width_kms, v_lo, v_step, n_v, rv_d, fit_d, ccf_d, spectra_f32 == 2));
     if (!out_on_device) {
         SOAP_CUDA(cudaMemcpyAsync(rv_kms, rv_d, (size_t)n_spec * 8, cudaMemcpyDeviceToHost, c->stream));
         if (fit_params)

@@ -804,7 +804,7 @@ bool ccf_mask_same(const soap_ctx* c, const double* mask_lambda, const double* m
 soap_status rv_ccf_run(soap_ctx* c, const void* spectra_dev, int f32, int n_spec,
                        const double* mask_lambda, const double* mask_weight, int n_lines,
                        double width_kms, double v_lo, double v_step, int n_v, double* rv_dev,
-                       double* fit_dev, double* ccf_dev) {
+                       double* fit_dev, double* ccf_dev, int tc) {
     // line and velocity tables: kept while the mask, its width and the velocity grid stay the same
     const bool same_tab = c->ccf_lines_ok && c->ccf_vel_key[0] == v_lo && c->ccf_vel_key[1] == v_step &&
                           c->ccf_vel_key[2] == (double)n_v &&
@@ -854,6 +854,22 @@ soap_status rv_ccf_run(soap_ctx* c, const void* spectra_dev, int f32, int n_spec
             n_chunks = tile_blocks;
         }
     }
+    // tensor-core form (FP32 spectra, sorted mask): pixel chunks of one wave of CTAs
+    int64_t tc_chunk = 0;
+    int tc_smin = 0, tc_smax = 0;
+    if (tc && f32 && sorted && ccf_tc_fits(n_v)) {
+        int sms = 0, dev = 0;
+        SOAP_CUDA(cudaGetDevice(&dev));
+        SOAP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        tc_chunk = ccf_tc_chunk(c->n_px, n_spec, sms);
+        n_chunks = (int)((c->n_px + tc_chunk - 1) / tc_chunk);
+        // range of the velocity shifts' integer parts S_k, one pixel of margin on each side
+        double s_a = std::atanh(v_lo / kCKms) / c->delta;
+        double s_b = std::atanh((v_lo + v_step * (n_v - 1)) / kCKms) / c->delta;
+        tc_smin = (int)std::floor(std::min(s_a, s_b)) - 1;
+        tc_smax = (int)std::floor(std::max(s_a, s_b)) + 1;
+        tile_np = 0;
+    }
     // table layout (8-byte aligned pieces, 256-byte aligned blocks) and per-call scratch
     auto al = [](size_t x) { return (x + 255) / 256 * 256; };
     size_t o_lam = 0;
@@ -893,6 +909,7 @@ soap_status rv_ccf_run(soap_ctx* c, const void* spectra_dev, int f32, int n_spec
     const double v_hi = v_lo + v_step * (n_v - 1);
     if (!same_tab) {
         c->ccf_lines_ok = false;
+        c->ccf_m_ok = false;
         SOAP_TRY(upload_small(c, d_lam, mask_lambda, (size_t)n_lines * 8));
         SOAP_TRY(upload_small(c, d_w, mask_weight, (size_t)n_lines * 8));
         k_ccf_lines<<<(n_lines + 255) / 256, 256, 0, c->stream>>>(
@@ -914,7 +931,10 @@ soap_status rv_ccf_run(soap_ctx* c, const void* spectra_dev, int f32, int n_spec
     if (tb) timer_end(c, SOAP_TIMER_CCF_AUX, tb);
     tb = c->profiling ? timer_begin(c) : nullptr;
     const int threads = n_v >= 256 ? 256 : ((n_v + 31) / 32) * 32;
-    if (tile_np) {
+    if (tc_chunk) {
+        SOAP_TRY(ccf_tc(c, n_lines, d_U, d_f32, d_valid, d_w32, n_v, d_S, d_g32, tc_smin, tc_smax, 2.0 * h,
+                        tc_chunk, n_spec, (const float*)spectra_dev, reinterpret_cast<float*>(d_part)));
+    } else if (tile_np) {
         const int tthreads = ((n_v + kTileVT - 1) / kTileVT * kTileLP + 31) / 32 * 32;
         dim3 grid((unsigned)tile_blocks, (unsigned)((n_spec + kTileSB - 1) / kTileSB));
         const float box = (float)(2.0 * h);
@@ -968,7 +988,7 @@ soap_status rv_ccf_run(soap_ctx* c, const void* spectra_dev, int f32, int n_spec
     if (tb) timer_end(c, SOAP_TIMER_CCF, tb);
     tb = c->profiling ? timer_begin(c) : nullptr;
     int64_t tot = (int64_t)n_spec * n_v * kReduceSplit;
-    if ((windowed || tile_np) && f32)      // FP32 partial sums (converted exactly to FP64 here)
+    if ((windowed || tile_np || tc_chunk) && f32)      // FP32 partial sums (converted exactly to FP64 here)
         k_ccf_reduce<float><<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(
             n_chunks, n_spec, n_v, reinterpret_cast<const float*>(d_part), d_ccf);
     else

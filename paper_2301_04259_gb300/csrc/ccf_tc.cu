@@ -1,0 +1,373 @@
+// ccf_tc.cu -- the line-mask CCF of Sect. 4.1 on the tensor cores (tcgen05), BF16 split
+// precision with FP32 accumulation (SOAP_BF16X3 calls and soap_rv_ccf with spectra_f32 = 2).
+//
+// With A_lk = U_l + f_l + S_k + g_k the start of line l's box at velocity k (pixel n covers
+// [n, n+1) in these coordinates, as in ccf.cu), the CCF is one matrix product
+//   CCF[s][k] = sum_n F[s][n] M[k][n],   M[k][n] = sum_l w_l |[n, n+1) intersect [A_lk, A_lk + box)|,
+// with M = spectra, N = velocities and K = pixels.
+//
+// k_ccf_tc_m builds the mask matrix once per mask and velocity grid (it is kept with the line
+// tables): one CTA per 64-pixel K block, one thread per (velocity, 32-pixel half row), which
+// adds the overlaps of the few lines that reach those pixels (staged in shared memory) in a
+// private FP32 row and stores it split, x = hi + lo with hi = bf16(x), lo = bf16(x - hi), as the
+// 128-byte-swizzle K-major image of the block's shared-memory tile (hi tile, then lo tile).
+// k_ccf_tc: CTA = (chunk of pixels, tile of 128 spectra), 256 threads, one CTA per SM.  Per K
+// block the mask tiles are copied verbatim (cp.async, 16 bytes a thread and copy) and every
+// thread splits 32 pixels of one spectrum (its operand row) into the stage; the copies and loads
+// of block i+1 are issued before block i is split, and one thread issues the 12 MMAs of block i
+// (M = 128, N = velocities rounded up to 16, K = 16; F_hi M_hi + F_hi M_lo + F_lo M_hi) and
+// commits them to the stage's barrier (two stages).  The epilogue writes the chunk's FP32
+// partial CCF, which k_ccf_reduce adds over the chunks in a fixed order.  Every barrier wait is
+// bounded; a timeout sets kFlagTimeout and the CTA stops issuing work.
+#include <cuda_bf16.h>
+#include <climits>
+
+#include "soap_internal.cuh"
+#include "tc_gemm.cuh"
+
+namespace soap {
+
+constexpr int kCcM = 128;                  // spectra per CTA (TMEM lanes)
+constexpr int kCcK = 64;                   // pixels per K block: one 128-byte swizzle row of BF16
+constexpr int kCcThreads = 256;            // two threads per spectrum row
+constexpr int kCcAB = kCcM * kCcK * 2;     // bytes of one half (hi or lo) of the spectra tile, 16 KB
+constexpr int kCcStages = 2;
+constexpr int kCcChunkMax = 2048;          // pixels per CTA at most (bounds the FP32 accumulation)
+// mask-matrix builder
+constexpr int kCcWin = 512;                // lines of a K block staged in shared memory (more: read directly)
+constexpr int kCcMaxV = 256;               // velocities at most (N <= 256)
+
+__host__ __device__ inline int cc_bb(int n_pad) { return n_pad * kCcK * 2; }       // one mask-tile half
+__host__ __device__ inline int cc_stage(int n_pad) { return 2 * kCcAB + 2 * cc_bb(n_pad); }
+__host__ __device__ inline size_t cc_smem(int n_pad) { return (size_t)kCcStages * cc_stage(n_pad) + 1024 + 64; }
+__host__ __device__ inline size_t cc_m_smem() {
+    return (size_t)kCcThreads * 32 * 4 + (size_t)kCcWin * 12 + (size_t)kCcMaxV * 8;
+}
+
+__device__ __forceinline__ void cc_split2(float x0, float x1, uint32_t& hw, uint32_t& lw) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+    const float2 hf = __bfloat1622float2(h);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
+    hw = *reinterpret_cast<const uint32_t*>(&h);
+    lw = *reinterpret_cast<const uint32_t*>(&l);
+}
+
+__device__ __forceinline__ uint32_t cc_sw128(int r, int c) { return (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4)); }
+
+// first line l in [0, n) with U[l] >= key (U non-decreasing)
+__device__ __forceinline__ int cc_lower(const int* __restrict__ U, int n, int64_t key) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if ((int64_t)__ldg(U + mid) < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// the 8 values x[0..7] as one 16-byte chunk of hi and one of lo (shared or global memory)
+__device__ __forceinline__ void cc_put8(unsigned char* hi_tile, unsigned char* lo_tile, uint32_t off,
+                                        const float* x) {
+    uint32_t hw[4], lw[4];
+#pragma unroll
+    for (int e = 0; e < 4; e++) cc_split2(x[2 * e], x[2 * e + 1], hw[e], lw[e]);
+    *reinterpret_cast<uint4*>(hi_tile + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+    *reinterpret_cast<uint4*>(lo_tile + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+}
+
+struct CcMArgs {
+    const int* U;          // [n_lines] integer part of each line's box start (sorted, non-decreasing)
+    const float* f;        // [n_lines] fraction of the box start, [0, 1)
+    const int* valid;      // [n_lines] 0: the box leaves the grid somewhere on the velocity grid
+    const float* w;        // [n_lines] line weights
+    const int* S;          // [n_v] integer part of the velocity shift atanh(v/c)/Delta
+    const float* g;        // [n_v] its fraction, [0, 1)
+    unsigned char* m;      // [n_kb][hi, lo][n_pad x 128 bytes]
+    int n_lines, n_v, n_pad;
+    int lo_off;            // lines with U < p - lo_off cannot reach pixel p at any velocity
+    int hi_off;            // lines with U >= p + hi_off cannot reach pixels below p + kCcK
+    float box;
+};
+
+__global__ void __launch_bounds__(kCcThreads)
+k_ccf_tc_m(const __grid_constant__ CcMArgs g) {
+    extern __shared__ __align__(16) unsigned char cc_m_raw[];
+    float* scratch = reinterpret_cast<float*>(cc_m_raw);                  // element j of thread t at j * 256 + t
+    int* sLU = reinterpret_cast<int*>(scratch + kCcThreads * 32);
+    float* sLF = reinterpret_cast<float*>(sLU + kCcWin);
+    float* sLW = sLF + kCcWin;
+    int* sS = reinterpret_cast<int*>(sLW + kCcWin);
+    float* sG = reinterpret_cast<float*>(sS + kCcMaxV);
+    const int t = threadIdx.x;
+    const int64_t p = (int64_t)blockIdx.x * kCcK;
+    const int la = cc_lower(g.U, g.n_lines, p - g.lo_off);
+    const int lb = max(la, cc_lower(g.U, g.n_lines, p + g.hi_off));
+    const int nl = lb - la;
+    for (int i = t; i < min(nl, kCcWin); i += kCcThreads) {
+        const int l = la + i;
+        sLU[i] = __ldg(g.U + l);
+        sLF[i] = __ldg(g.f + l);
+        sLW[i] = __ldg(g.valid + l) ? __ldg(g.w + l) : 0.0f;       // lines whose box leaves the grid: skipped
+    }
+    for (int k = t; k < g.n_v; k += kCcThreads) {
+        sS[k] = __ldg(g.S + k);
+        sG[k] = __ldg(g.g + k);
+    }
+    __syncthreads();
+    unsigned char* hi = g.m + (size_t)blockIdx.x * 2 * cc_bb(g.n_pad);
+    unsigned char* lo = hi + cc_bb(g.n_pad);
+    float* my = scratch + t;
+    for (int task = t; task < 2 * g.n_pad; task += kCcThreads) {
+        const int k = task >> 1, hb = task & 1;
+        const int64_t q0 = p + 32 * hb;
+#pragma unroll
+        for (int j = 0; j < 32; j++) my[j * kCcThreads] = 0.0f;
+        if (k < g.n_v) {
+            const int Sk = sS[k];
+            const float gk = sG[k];
+            for (int i = 0; i < nl; i++) {
+                int Ul;
+                float fl, wl;
+                if (i < kCcWin) {
+                    Ul = sLU[i]; fl = sLF[i]; wl = sLW[i];
+                } else {                                    // a dense stretch of the mask
+                    const int l = la + i;
+                    Ul = __ldg(g.U + l); fl = __ldg(g.f + l);
+                    wl = __ldg(g.valid + l) ? __ldg(g.w + l) : 0.0f;
+                }
+                // the box starts at base + xf in the pixel units of this row half
+                const int base = (int)((int64_t)Ul + Sk - q0);
+                if (base >= 32) break;                      // so do those of all later lines
+                if (wl == 0.0f) continue;
+                const float xf = fl + gk;                   // in [0, 2)
+                int j = base + (xf >= 1.0f ? 1 : 0);        // pixel holding the box start
+                if (j < 0) j = 0;
+                for (; j < 32; j++) {
+                    const float av = xf - (float)(j - base);       // box start relative to pixel j
+                    if (av + g.box <= 0.0f) break;                 // the box ended before pixel j
+                    my[j * kCcThreads] += wl * (fminf(av + g.box, 1.0f) - fmaxf(av, 0.0f));
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            float x[8];
+#pragma unroll
+            for (int e = 0; e < 8; e++) x[e] = my[(8 * q + e) * kCcThreads];
+            cc_put8(hi, lo, cc_sw128(k, 4 * hb + q), x);
+        }
+    }
+}
+
+struct CcArgs {
+    const unsigned char* m;   // mask tiles from k_ccf_tc_m
+    const float* spectra;     // [n_spec][n_px] FP32
+    float* partial;           // [n_chunks][n_spec][n_v] FP32
+    int64_t n_px;
+    int64_t chunk;            // pixels per chunk (a multiple of kCcK)
+    int n_v, n_pad, n_spec;
+    int vec4;                 // rows are 16-byte aligned: 16-byte loads
+    uint32_t tmem_cols;
+};
+
+__device__ __forceinline__ void cc_cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_u32(dst)), "l"(src) : "memory");
+}
+
+// 32 spectrum values of row frow at pixels pa .. pa+31, zero at and past P1 (or for no row)
+__device__ __forceinline__ void cc_load_row(float (&a)[32], const float* frow, bool row_on, int vec4,
+                                            int64_t pa, int64_t P1) {
+    if (row_on && vec4 && pa + 32 <= P1) {
+        const float4* src = reinterpret_cast<const float4*>(frow + pa);
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            const float4 v = __ldg(src + q);
+            a[4 * q] = v.x; a[4 * q + 1] = v.y; a[4 * q + 2] = v.z; a[4 * q + 3] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < 32; e++) a[e] = (row_on && pa + e < P1) ? __ldg(frow + pa + e) : 0.0f;
+    }
+}
+
+__global__ void __launch_bounds__(kCcThreads, 1)
+k_ccf_tc(const __grid_constant__ CcArgs g, unsigned int* flags) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* ring = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
+    const int stage_bytes = cc_stage(g.n_pad);
+    const int bb = cc_bb(g.n_pad);
+    uint64_t* empty = reinterpret_cast<uint64_t*>(ring + kCcStages * stage_bytes);
+    uint64_t* accum = empty + kCcStages;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+    const int t = threadIdx.x, warp = t >> 5;
+    const int r = t & (kCcM - 1), half = t >> 7;    // spectrum row and which 32 pixels of the block
+    const int64_t P0 = (int64_t)blockIdx.x * g.chunk;
+    const int64_t P1 = P0 + g.chunk < g.n_px ? P0 + g.chunk : g.n_px;
+    const int n_kb = (int)((P1 - P0 + kCcK - 1) / kCcK);
+    const int64_t kb0 = P0 / kCcK;                  // first K block of the chunk in the mask tiles
+    const int s0 = blockIdx.y * kCcM;
+    const bool row_on = s0 + r < g.n_spec;
+    const float* frow = g.spectra + (int64_t)(row_on ? s0 + r : 0) * g.n_px;
+    const int n_copy = 2 * bb / 16;                 // 16-byte pieces of the two mask tiles
+
+    if (t == 0) {
+        for (int s = 0; s < kCcStages; s++) tc::mbar_init(&empty[s], 1);
+        tc::mbar_init(accum, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(tc::smem_u32(tmem_slot)), "r"(g.tmem_cols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    // block 0: mask tiles in flight, spectrum values in registers
+    {
+        const unsigned char* src = g.m + (size_t)kb0 * 2 * bb;
+        for (int i = t; i < n_copy; i += kCcThreads) cc_cp_async16(ring + 2 * kCcAB + 16 * i, src + 16 * i);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+    float a[32];
+    cc_load_row(a, frow, row_on, g.vec4, P0 + 32 * half, P1);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    bool ok = true;
+    for (int kb = 0; kb < n_kb; kb++) {
+        const int s = kb & 1;
+        const bool next = kb + 1 < n_kb;
+        float an[32];
+        if (next) {
+            // block kb+1: its stage is free once the MMAs of block kb-1 are done
+            const int s1 = (kb + 1) & 1;
+            if (kb + 1 >= kCcStages) ok = tc::mbar_wait(&empty[s1], ((kb + 1 - kCcStages) / kCcStages) & 1, flags);
+            if (!__syncthreads_and(ok)) { ok = false; break; }
+            const unsigned char* src = g.m + (size_t)(kb0 + kb + 1) * 2 * bb;
+            unsigned char* dst = ring + s1 * stage_bytes + 2 * kCcAB;
+            for (int i = t; i < n_copy; i += kCcThreads) cc_cp_async16(dst + 16 * i, src + 16 * i);
+            asm volatile("cp.async.commit_group;" ::: "memory");
+            cc_load_row(an, frow, row_on, g.vec4, P0 + (int64_t)(kb + 1) * kCcK + 32 * half, P1);
+        }
+        // block kb: spectrum row r, chunks 4 half .. 4 half + 3 (the stage's last reader, the
+        // MMAs of block kb-2, finished before its mask copies were issued)
+        unsigned char* st = ring + s * stage_bytes;
+#pragma unroll
+        for (int q = 0; q < 4; q++) cc_put8(st, st + kCcAB, cc_sw128(r, 4 * half + q), a + 8 * q);
+        if (next) asm volatile("cp.async.wait_group 1;" ::: "memory");   // block kb's mask tiles landed
+        else asm volatile("cp.async.wait_group 0;" ::: "memory");
+        // the tensor cores read shared memory through the async proxy
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (t == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t ah = tc::smem_u32(st), al = ah + kCcAB, bh = al + kCcAB, bl = bh + (uint32_t)bb;
+            const uint32_t idesc = tc::idesc_bf16(g.n_pad);
+#pragma unroll
+            for (int k = 0; k < kCcK / 16; k++) {
+                tc::mma_bf16(tmem, tc::sdesc(ah + k * 32), tc::sdesc(bh + k * 32), idesc, (kb | k) != 0);
+                tc::mma_bf16(tmem, tc::sdesc(ah + k * 32), tc::sdesc(bl + k * 32), idesc, 1u);
+                tc::mma_bf16(tmem, tc::sdesc(al + k * 32), tc::sdesc(bh + k * 32), idesc, 1u);
+            }
+            tc::mma_commit(&empty[s]);
+        }
+        if (next) {
+#pragma unroll
+            for (int e = 0; e < 32; e++) a[e] = an[e];
+        }
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");     // no copy outlives the CTA
+
+    // accumulator complete (every MMA issued above has finished) before it is read or released
+    if (t == 0) tc::mma_commit(accum);            // n_kb >= 1: at least one block was issued
+    bool done = tc::mbar_wait(accum, 0, flags) && ok;
+    done = __syncthreads_and(done);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (done) {
+        // warp w: TMEM lanes 32 (w & 3) .. +31 (its spectra), column blocks of 32 alternating
+        // between the two warp groups (its velocities)
+        const int lg = warp & 3;
+        const int sp = s0 + 32 * lg + (t & 31);
+#pragma unroll 1
+        for (int c = 32 * (warp >> 2); c < g.n_pad; c += 64) {
+            float v[32];
+            tc::tmem_ld32(tmem + ((uint32_t)(32 * lg) << 16) + (uint32_t)c, v);
+            if (sp < g.n_spec) {
+                float* dst = g.partial + ((int64_t)blockIdx.x * g.n_spec + sp) * g.n_v;
+#pragma unroll
+                for (int i = 0; i < 32; i++)
+                    if (c + i < g.n_v) dst[c + i] = v[i];
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(g.tmem_cols) : "memory");
+    }
+}
+
+bool ccf_tc_fits(int n_v) {
+    const int n_pad = (n_v + 15) / 16 * 16;
+    return n_v >= 1 && n_v <= kCcMaxV && cc_smem(n_pad) <= 227 * 1024;
+}
+
+int64_t ccf_tc_chunk(int64_t n_px, int n_spec, int sms) {
+    const int64_t tiles = (n_spec + kCcM - 1) / kCcM;
+    const int64_t per = (n_px * tiles + sms - 1) / std::max(sms, 1);     // pixels per CTA for one wave
+    const int64_t chunk = (per + kCcK - 1) / kCcK * kCcK;
+    return std::max<int64_t>(kCcK, std::min<int64_t>(chunk, kCcChunkMax));
+}
+
+soap_status ccf_tc(soap_ctx* c, int n_lines, const int* U, const float* f, const int* valid, const float* w,
+                   int n_v, const int* S, const float* g, int s_min, int s_max, double box, int64_t chunk,
+                   int n_spec, const float* spectra, float* partial) {
+    const int n_pad = (n_v + 15) / 16 * 16;
+    if (!c->ccf_m_ok) {
+        // the mask matrix of this mask and velocity grid (kept until either changes)
+        const int64_t n_kb = (c->n_px + kCcK - 1) / kCcK;
+        SOAP_TRY(ensure(c->ccf_m, (size_t)n_kb * 2 * cc_bb(n_pad)));
+        CcMArgs m{};
+        m.U = U;
+        m.f = f;
+        m.valid = valid;
+        m.w = w;
+        m.S = S;
+        m.g = g;
+        m.m = c->ccf_m.as<unsigned char>();
+        m.n_lines = n_lines;
+        m.n_v = n_v;
+        m.n_pad = n_pad;
+        // a line reaches pixels [p, p + 64) at velocity k only if U + S_k < p + 64 and
+        // U + S_k + 2 + box > p (box start U + S_k + f + g with f + g < 2); S_min, S_max carry a margin
+        m.lo_off = s_max + 2 + (int)std::ceil(box) + 1;
+        m.hi_off = kCcK - s_min + 1;
+        m.box = (float)box;
+        SOAP_TRY(fit_dynamic_smem(k_ccf_tc_m, cc_m_smem()));
+        k_ccf_tc_m<<<(unsigned)n_kb, kCcThreads, cc_m_smem(), c->stream>>>(m);
+        SOAP_LAUNCHED(c);
+        c->ccf_m_ok = true;
+    }
+    CcArgs a{};
+    a.m = c->ccf_m.as<unsigned char>();
+    a.spectra = spectra;
+    a.partial = partial;
+    a.n_px = c->n_px;
+    a.chunk = chunk;
+    a.n_v = n_v;
+    a.n_pad = n_pad;
+    a.n_spec = n_spec;
+    a.vec4 = (reinterpret_cast<uintptr_t>(spectra) % 16 == 0 && c->n_px % 4 == 0) ? 1 : 0;
+    uint32_t cols = 32;
+    while ((int)cols < n_pad) cols <<= 1;
+    a.tmem_cols = cols;
+    const size_t smem = cc_smem(n_pad);
+    SOAP_TRY(fit_dynamic_smem(k_ccf_tc, smem));
+    dim3 grid((unsigned)((c->n_px + chunk - 1) / chunk), (unsigned)((n_spec + kCcM - 1) / kCcM));
+    k_ccf_tc<<<grid, kCcThreads, smem, c->stream>>>(a, c->flags);
+    SOAP_LAUNCHED(c);
+    return SOAP_OK;
+}
+
+}  // namespace soap

@@ -204,6 +204,9 @@ struct soap_ctx {
     double ccf_vel_key[3] = {0, 0, -1};  // v_lo, v_step, n_v
     bool ccf_lines_ok = false;
     bool ccf_sorted = false;
+    // tensor-core CCF: the mask matrix as BF16 hi / lo tiles (ccf_tc.cu), kept with the tables
+    soap::DevBuf ccf_m;
+    bool ccf_m_ok = false;
 
     // host-transfer pipeline: uploads from host memory run on in_stream, downloads of host
     // results on out_stream, ordered against the compute stream by events.  up_* serve the
@@ -317,10 +320,17 @@ int batch_default_variant(int max_phases_per_item);
 void batch_variant_info(int v, int* phases_per_block, int* px_per_thread);
 void batch_release(soap_ctx* c);
 
+// tc: FP32 spectra whose CCF may run on the tensor cores (BF16 split, ccf_tc.cu) where that
+// form applies (mask sorted by wavelength, at most 240 velocities)
 soap_status rv_ccf_run(soap_ctx* c, const void* spectra_dev, int f32, int n_spec,
                        const double* mask_lambda, const double* mask_weight, int n_lines,
                        double width_kms, double v_lo, double v_step, int n_v, double* rv_dev,
-                       double* fit_dev, double* ccf_dev);
+                       double* fit_dev, double* ccf_dev, int tc = 0);
+bool ccf_tc_fits(int n_v);
+int64_t ccf_tc_chunk(int64_t n_px, int n_spec, int sms);
+soap_status ccf_tc(soap_ctx* c, int n_lines, const int* U, const float* f, const int* valid, const float* w,
+                   int n_v, const int* S, const float* g, int s_min, int s_max, double box, int64_t chunk,
+                   int n_spec, const float* spectra, float* partial);
 
 }  // namespace soap
 

@@ -375,10 +375,16 @@ def soap_active_rv(ctx, regions: Sequence, phases, effect: int, precision: int, 
 
 
 def soap_rv_ccf(ctx, spectra, mask_lambda, mask_weight, mask_width_kms: float, v_lo: float,
-                v_step: float, n_v: int, rv_out, fit_out=None, ccf_out=None) -> None:
-    """spectra [n_spec, n_px] float64/float32; outputs all host (numpy) or all device."""
+                v_step: float, n_v: int, rv_out, fit_out=None, ccf_out=None,
+                tensor_cores: bool = False) -> None:
+    """spectra [n_spec, n_px] float64/float32; outputs all host (numpy) or all device.
+    tensor_cores: float32 spectra only, the CCF as a BF16-split tcgen05 GEMM (spectra_f32 = 2)."""
     sp, sdev = _ptr(spectra)
     f32 = int(str(spectra.dtype).endswith("float32"))
+    if tensor_cores:
+        if not f32:
+            raise ValueError("tensor_cores needs float32 spectra")
+        f32 = 2
     n_spec = int(spectra.shape[0])
     ml = np.ascontiguousarray(mask_lambda, dtype=np.float64)
     mw = np.ascontiguousarray(mask_weight, dtype=np.float64)
