@@ -233,27 +233,28 @@ k_ccf_tc(const __grid_constant__ CcArgs g, unsigned int* flags) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
 
+    // one K block; the spectrum values of block kb are in cur, those of block kb+1 go to nxt (the
+    // loop below alternates two register sets, so no copy waits for the loads in flight)
     bool ok = true;
-    for (int kb = 0; kb < n_kb; kb++) {
+    auto step = [&](int kb, float (&cur)[32], float (&nxt)[32]) -> bool {
         const int s = kb & 1;
         const bool next = kb + 1 < n_kb;
-        float an[32];
         if (next) {
             // block kb+1: its stage is free once the MMAs of block kb-1 are done
             const int s1 = (kb + 1) & 1;
             if (kb + 1 >= kCcStages) ok = tc::mbar_wait(&empty[s1], ((kb + 1 - kCcStages) / kCcStages) & 1, flags);
-            if (!__syncthreads_and(ok)) { ok = false; break; }
+            if (!__syncthreads_and(ok)) { ok = false; return false; }
             const unsigned char* src = g.m + (size_t)(kb0 + kb + 1) * 2 * bb;
             unsigned char* dst = ring + s1 * stage_bytes + 2 * kCcAB;
             for (int i = t; i < n_copy; i += kCcThreads) cc_cp_async16(dst + 16 * i, src + 16 * i);
             asm volatile("cp.async.commit_group;" ::: "memory");
-            cc_load_row(an, frow, row_on, g.vec4, P0 + (int64_t)(kb + 1) * kCcK + 32 * half, P1);
+            cc_load_row(nxt, frow, row_on, g.vec4, P0 + (int64_t)(kb + 1) * kCcK + 32 * half, P1);
         }
         // block kb: spectrum row r, chunks 4 half .. 4 half + 3 (the stage's last reader, the
         // MMAs of block kb-2, finished before its mask copies were issued)
         unsigned char* st = ring + s * stage_bytes;
 #pragma unroll
-        for (int q = 0; q < 4; q++) cc_put8(st, st + kCcAB, cc_sw128(r, 4 * half + q), a + 8 * q);
+        for (int q = 0; q < 4; q++) cc_put8(st, st + kCcAB, cc_sw128(r, 4 * half + q), cur + 8 * q);
         if (next) asm volatile("cp.async.wait_group 1;" ::: "memory");   // block kb's mask tiles landed
         else asm volatile("cp.async.wait_group 0;" ::: "memory");
         // the tensor cores read shared memory through the async proxy
@@ -271,10 +272,12 @@ k_ccf_tc(const __grid_constant__ CcArgs g, unsigned int* flags) {
             }
             tc::mma_commit(&empty[s]);
         }
-        if (next) {
-#pragma unroll
-            for (int e = 0; e < 32; e++) a[e] = an[e];
-        }
+        return true;
+    };
+    float a1[32];
+    for (int kb = 0; kb < n_kb; kb += 2) {
+        if (!step(kb, a, a1)) break;
+        if (kb + 1 < n_kb && !step(kb + 1, a1, a)) break;
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");     // no copy outlives the CTA
 
