@@ -165,3 +165,19 @@ def test_ccf_tc_dense_mask_stretch(S):
     _, ccf_s = _tc_ccf(S, c, F, c.mask_width_kms, lo, step, nv, tensor_cores=False)
     assert np.abs(ccf_s - ccf_o).max() <= 2e-6 * np.abs(ccf_o).max()
     assert np.abs(ccf_g - ccf_o).max() <= TOL_CCF * np.abs(ccf_o).max()
+
+
+def test_rv_ccf_rejects_unknown_spectra_type(S):
+    """spectra_f32 outside 0, 1, 2 is SOAP_EINVAL before any device work."""
+    import ctypes
+    c = synth.config1(0)
+    lo, step, nv = synth.velocity_grid(c.star.vsini_kms)
+    F = _t(_spectra(c, 2))
+    ml = np.ascontiguousarray(c.mask_lambda)
+    mw = np.ascontiguousarray(c.mask_weight)
+    with S.Disk(c.star, _t(c.quiet)) as d:
+        rv = torch.empty(2, dtype=torch.float64, device=DEV)
+        st = S._lib.soap_rv_ccf(d.ctx, ctypes.c_void_p(F.data_ptr()), 3, 2, 1, ctypes.c_void_p(ml.ctypes.data),
+                                ctypes.c_void_p(mw.ctypes.data), ml.size, float(c.mask_width_kms), float(lo),
+                                float(step), int(nv), ctypes.c_void_p(rv.data_ptr()), None, None, 1)
+    assert st == S.SOAP_EINVAL
