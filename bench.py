@@ -437,6 +437,39 @@ def measure_batched(args, dev, hbm_peak):
                    if S.soap_get_kernel_time(d.ctx, t)[1]}
         S.soap_set_profiling(d.ctx, False)
         S.soap_synchronize(d.ctx)
+        # the same batch with the RV of every spectrum (Sect. 4.1): CCF on one grid -30..30 km/s
+        # (0.25 km/s), each configuration fitted within |v| <= |vsini| + 20 km/s, inside the graph
+        lo, step, nv = synth.velocity_grid(10.0)
+        rv = torch.empty(phases.size, dtype=torch.float64, device=dev)
+        with_rv = {}
+        for form, tcf in (("simt_ccf", False), ("tensor_ccf", True)):
+            S.soap_batch_set_rv(d.ctx, case.mask_lambda, case.mask_weight, case.mask_width_kms, lo, step, nv,
+                                20.0, tcf)
+            for _ in range(2):
+                S.soap_active_batch_arrays(d.ctx, it, rg, ph, out, rv_out=rv)
+            torch.cuda.synchronize()
+            K2 = 3
+            l0 = S.soap_get_launch_count(d.ctx)
+            ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K2)]
+            for k in range(K2):
+                ev2[k][0].record(stream)
+                S.soap_active_batch_arrays(d.ctx, it, rg, ph, out, rv_out=rv)
+                ev2[k][1].record(stream)
+            torch.cuda.synchronize()
+            launches_rv = (S.soap_get_launch_count(d.ctx) - l0) // K2
+            ms_rv = float(np.mean([a.elapsed_time(b) for a, b in ev2]))
+            S.soap_set_profiling(d.ctx, True)
+            S.soap_reset_kernel_times(d.ctx)
+            S.soap_active_batch_arrays(d.ctx, it, rg, ph, out, rv_out=rv)
+            S.soap_synchronize(d.ctx)
+            krv = {name: round(S.soap_get_kernel_time(d.ctx, t)[0], 4) for t, name in enumerate(S.TIMERS)
+                   if name in ("ccf", "ccf_aux", "fit") and S.soap_get_kernel_time(d.ctx, t)[1]}
+            S.soap_set_profiling(d.ctx, False)
+            S.soap_synchronize(d.ctx)
+            r = rv.cpu().numpy()
+            with_rv[form] = {"ms_per_batch": round(ms_rv, 3), "spectra_and_rvs_per_s": round(phases.size / (ms_rv * 1e-3), 1),
+                             "gpu_launches_per_batch": int(launches_rv), "rv_kernel_ms": krv,
+                             "rv_finite_frac": round(float(np.isfinite(r).mean()), 6)}
     out_bytes = out.numel() * 4
     del out
     c_ms = kernels.get("contract", ms)
@@ -446,6 +479,7 @@ def measure_batched(args, dev, hbm_peak):
                         "px_per_thread": S.soap_batch_variant_info(best)[1]},
             "autotune_ms": [round(float(v), 3) for v in ms_var], "gpu_launches_per_batch": int(launches),
             "kernel_ms": kernels, "output_bytes": int(out_bytes),
+            "with_rv": with_rv, "rv_velocity_grid": {"v_lo": lo, "v_step": step, "n_v": nv, "fit_margin_kms": 20.0},
             "contract_hbm_write_gbs": round(out_bytes / (c_ms * 1e-3) / 1e9, 1),
             "contract_frac_of_hbm": round(out_bytes / (c_ms * 1e-3) / 1e9 / hbm_peak, 4),
             "precision": "FP32 contraction, FP64 positions"}

@@ -399,11 +399,36 @@ enum {
  * graph).  The variant (phases per block, pixels per thread) is the one soap_batch_set_variant
  * or soap_batch_autotune chose, else 1 or 2 phases per block when no item has more phases, and
  * 4 otherwise.
+ *  rv_kms     [n_phases] radial velocity of each phase's spectrum (Sect. 4.1: CCF with the mask
+ *             of soap_batch_set_rv and least-squares Gaussian, as soap_rv_ccf on float32 spectra),
+ *             or NULL for spectra only.  Host or device per out_on_device.  Needs
+ *             soap_batch_set_rv (SOAP_ESTATE otherwise) and output = SOAP_BATCH_SPECTRUM (the
+ *             residual rows are not spectra: SOAP_EINVAL).  The CCF, its reduction and the fits
+ *             run inside the same captured graph, on the output rows while they are in device
+ *             memory.
  * Errors: SOAP_EINVAL (bad item, phase not covered exactly once, alpha != 0), SOAP_ESTATE (no
  * active spectrum for a region type), SOAP_ERANGE (class limit). */
 soap_status soap_active_batch(soap_ctx* ctx, const soap_batch_item* items, int32_t n_items,
                               const soap_region* regions, int32_t n_regions, const double* phases,
-                              int32_t n_phases, int32_t output, float* out, int out_on_device);
+                              int32_t n_phases, int32_t output, float* out, double* rv_kms,
+                              int out_on_device);
+
+/* Mask and velocity grid of the batched radial velocities (soap_active_batch with rv_kms).
+ *  mask_lambda, mask_weight, n_lines, mask_width_kms   as for soap_rv_ccf (host, copied).
+ *  v_lo, v_step, n_v   one velocity grid v_k = v_lo + k v_step for every configuration (it must
+ *                      cover the widest one); the CCF is computed on all of it.
+ *  fit_margin_kms      > 0: configuration q fits its CCF only at the grid velocities with
+ *                      |v_k| <= |vsini_q| + fit_margin_kms (at least 5 of them, else SOAP_EINVAL
+ *                      at the batch call), the window a single star of that vsini would use;
+ *                      <= 0: every configuration fits the whole grid.
+ *  tensor_cores        0: the FP32 SIMT CCF; 1: the CCF as a tensor-core GEMM (BF16 hi/lo, as
+ *                      soap_rv_ccf with spectra_f32 = 2) where that form applies.
+ * Lines whose box leaves the wavelength grid anywhere on the velocity grid are skipped (as in
+ * soap_rv_ccf).  Errors: SOAP_EINVAL (as soap_rv_ccf's checks), SOAP_ERANGE (box wider than 14
+ * pixels). */
+soap_status soap_batch_set_rv(soap_ctx* ctx, const double* mask_lambda, const double* mask_weight,
+                              int32_t n_lines, double mask_width_kms, double v_lo, double v_step,
+                              int32_t n_v, double fit_margin_kms, int32_t tensor_cores);
 
 /* Number of variants of the batched form (valid variants are 0 .. *n - 1). */
 soap_status soap_batch_num_variants(int32_t* n);
@@ -431,7 +456,7 @@ soap_status soap_batch_autotune(soap_ctx* ctx, const soap_batch_item* items, int
  *                 (spectra_f32 = 1, or 2: float32 with the CCF sum as a tensor-core GEMM over
  *                 pixels, both operands split into BF16 hi + lo, three products, FP32
  *                 accumulation; where that form does not apply -- a mask not sorted by
- *                 wavelength or more than 240 velocities -- 2 computes as 1); host or device
+ *                 wavelength or more than 256 velocities -- 2 computes as 1); host or device
  *                 per spectra_on_device.  Other values: SOAP_EINVAL.
  *  mask_lambda    host [n_lines] rest wavelengths (Angstrom); mask_weight host [n_lines].
  *  mask_width_kms full width W of each mask box in velocity.
@@ -449,7 +474,10 @@ soap_status soap_batch_autotune(soap_ctx* ctx, const soap_batch_item* items, int
  *                 outside it or a width larger than it: no dip to fit).
  *  fit_params     [n_spec][4] (A, B, mu, s), or NULL.
  *  ccf_out        [n_spec][n_v] float64 CCF, or NULL.
- *  Outputs are host or device per out_on_device. */
+ *  Outputs are host or device per out_on_device.
+ * Errors: SOAP_EINVAL (arguments), SOAP_ETIMEOUT if a tensor-core barrier wait gave up (the CCF
+ * is then incomplete): with host outputs this call reports it, with device outputs the next
+ * soap_synchronize() does. */
 soap_status soap_rv_ccf(soap_ctx* ctx, const void* spectra, int32_t spectra_f32, int32_t n_spec,
                         int spectra_on_device, const double* mask_lambda,
                         const double* mask_weight, int32_t n_lines, double mask_width_kms,
@@ -590,6 +618,12 @@ soap_status soap_pca_project(const float* X, int64_t n, int64_t p, const float* 
 
 /* Number of kernels this context has launched so far (for launch accounting). */
 soap_status soap_get_launch_count(const soap_ctx* ctx, uint64_t* out);
+
+/* For testing error reporting only: mark the context's device status word (stream-ordered) as a
+ * tensor-core kernel does when one of its bounded barrier waits gives up.  The next call that
+ * reads the status word (a call with host outputs, or soap_synchronize) then returns
+ * SOAP_ETIMEOUT and clears it.  No kernel is made to wait or fail. */
+soap_status soap_debug_inject_timeout(soap_ctx* ctx);
 
 /* Release the context and all device memory it owns.  NULL is a no-op.  Synchronises the
  * context's stream first. */

@@ -219,8 +219,8 @@ static void free_ctx_memory(soap_ctx* c) {
     for (void* p : ptrs)
         if (p) cudaFree(p);
     DevBuf* bufs[] = {&c->stage_in, &c->fq, &c->contrast, &c->kphase, &c->jobs, &c->coefs, &c->job_counters,
-                      &c->regions, &c->region_geo, &c->phases, &c->out_stage, &c->partial, &c->ccf_tmp,
-                      &c->ccf_tab, &c->lsf_taps, &c->lsf_tmp, &c->bis_tab, &c->tc_coef, &c->ccf_m};
+                      &c->regions, &c->region_geo, &c->phases, &c->out_stage, &c->partial, &c->ccf.tmp,
+                      &c->ccf.tab, &c->lsf_taps, &c->lsf_tmp, &c->bis_tab, &c->tc_coef, &c->ccf.m};
     for (DevBuf* b : bufs) release(*b);
     release_host(c->host_stage);
     ring_release(c);
@@ -261,6 +261,9 @@ static soap_status upload_spectra(soap_ctx* c, const void* src, int on_device, i
     if (!on_device && c->host_async) SOAP_CUDA(cudaEventRecord(c->up_free[slot], c->stream));
     return SOAP_OK;
 }
+
+// Sets bits in the device status word as a failing kernel would (soap_debug_inject_timeout).
+__global__ void k_raise_status(unsigned int* flags, unsigned int bits) { atomicOr(flags, bits); }
 
 static soap_status check_flags(soap_ctx* c) {
     unsigned int f = 0;
@@ -628,6 +631,14 @@ soap_status soap_get_launch_count(const soap_ctx* c, uint64_t* out) {
     return SOAP_OK;
 }
 
+soap_status soap_debug_inject_timeout(soap_ctx* c) {
+    clear_error();
+    if (!c) { set_error("ctx is NULL"); return SOAP_EINVAL; }
+    k_raise_status<<<1, 1, 0, c->stream>>>(c->flags, kFlagTimeout);
+    SOAP_CUDA(cudaGetLastError());
+    return SOAP_OK;
+}
+
 soap_status soap_quiet_spectrum(soap_ctx* c, int32_t form, int32_t precision, void* out,
                                 int out_on_device) {
     clear_error();
@@ -732,7 +743,7 @@ static soap_status check_rv(soap_ctx* c, const double* mask_lambda, const double
     if (!(std::fabs(v_lo) < kCKms) || !(std::fabs(v_hi) < kCKms)) { set_error("velocity grid reaches c"); return SOAP_EINVAL; }
     double h = mask_width_kms / (2.0 * kCKms * c->delta);
     if (2.0 * h > 14.0) { set_error("mask box spans more than 14 pixels"); return SOAP_ERANGE; }
-    if (ccf_mask_same(c, mask_lambda, mask_weight, n_lines, mask_width_kms)) return SOAP_OK;   // checked before
+    if (ccf_mask_same(c->ccf, mask_lambda, mask_weight, n_lines, mask_width_kms)) return SOAP_OK;   // checked before
     for (int l = 0; l < n_lines; l++)
         if (!is_finite(mask_lambda[l]) || !(mask_lambda[l] > 0) || !is_finite(mask_weight[l])) {
             set_error("mask line %d invalid", l); return SOAP_EINVAL;
@@ -1011,16 +1022,55 @@ soap_status soap_rv_ccf(soap_ctx* c, const void* spectra, int32_t spectra_f32, i
         if (ccf_out)
             SOAP_CUDA(cudaMemcpyAsync(ccf_out, ccf_d, (size_t)n_spec * n_v * 8, cudaMemcpyDeviceToHost, c->stream));
         SOAP_CUDA(cudaStreamSynchronize(c->stream));
+        // a tensor-core wait that gave up left a partial CCF: report it with the results
+        SOAP_TRY(check_flags(c));
     }
+    return SOAP_OK;
+}
+
+soap_status soap_batch_set_rv(soap_ctx* c, const double* mask_lambda, const double* mask_weight,
+                              int32_t n_lines, double mask_width_kms, double v_lo, double v_step,
+                              int32_t n_v, double fit_margin_kms, int32_t tensor_cores) {
+    clear_error();
+    if (!c) { set_error("ctx is NULL"); return SOAP_EINVAL; }
+    if (!is_finite(fit_margin_kms)) { set_error("fit_margin_kms not finite"); return SOAP_EINVAL; }
+    if (tensor_cores != 0 && tensor_cores != 1) { set_error("tensor_cores must be 0 or 1"); return SOAP_EINVAL; }
+    if (!mask_lambda || !mask_weight) { set_error("NULL mask"); return SOAP_EINVAL; }
+    if (n_lines < 1 || n_v < 5 || n_v > 4096) { set_error("need n_lines >= 1, 5 <= n_v <= 4096"); return SOAP_EINVAL; }
+    for (int l = 0; l < n_lines; l++)
+        if (!is_finite(mask_lambda[l]) || !(mask_lambda[l] > 0) || !is_finite(mask_weight[l])) {
+            set_error("mask line %d invalid", l); return SOAP_EINVAL;
+        }
+    if (!is_finite(mask_width_kms) || !(mask_width_kms > 0) || !is_finite(v_lo) || !is_finite(v_step) || !(v_step > 0)) {
+        set_error("mask width / velocity grid invalid"); return SOAP_EINVAL;
+    }
+    const double v_hi = v_lo + v_step * (n_v - 1);
+    if (!(std::fabs(v_lo) < kCKms) || !(std::fabs(v_hi) < kCKms)) { set_error("velocity grid reaches c"); return SOAP_EINVAL; }
+    if (mask_width_kms / (kCKms * c->delta) > 14.0) { set_error("mask box spans more than 14 pixels"); return SOAP_ERANGE; }
+    c->b_rv_lambda.assign(mask_lambda, mask_lambda + n_lines);
+    c->b_rv_weight.assign(mask_weight, mask_weight + n_lines);
+    c->b_rv_width = mask_width_kms;
+    c->b_rv_v_lo = v_lo;
+    c->b_rv_v_step = v_step;
+    c->b_rv_n_v = n_v;
+    c->b_rv_margin = fit_margin_kms;
+    c->b_rv_tc = tensor_cores;
+    c->b_rv_set = true;
     return SOAP_OK;
 }
 
 soap_status soap_active_batch(soap_ctx* c, const soap_batch_item* items, int32_t n_items,
                               const soap_region* regions, int32_t n_regions, const double* phases,
-                              int32_t n_phases, int32_t output, float* out, int out_on_device) {
+                              int32_t n_phases, int32_t output, float* out, double* rv_kms,
+                              int out_on_device) {
     clear_error();
     if (!c || !out) { set_error("ctx or out is NULL"); return SOAP_EINVAL; }
     if (output != SOAP_BATCH_SPECTRUM && output != SOAP_BATCH_RESIDUAL) { set_error("unknown output %d", output); return SOAP_EINVAL; }
+    if (rv_kms && output != SOAP_BATCH_SPECTRUM) {
+        set_error("radial velocities need output = SOAP_BATCH_SPECTRUM (residual rows are not spectra)");
+        return SOAP_EINVAL;
+    }
+    if (rv_kms && !c->b_rv_set) { set_error("no mask for the batched RVs (soap_batch_set_rv)"); return SOAP_ESTATE; }
     if (n_items < 0 || n_regions < 0 || n_phases < 0) { set_error("negative count"); return SOAP_EINVAL; }
     if ((n_items > 0 && !items) || (n_regions > 0 && !regions) || (n_phases > 0 && !phases)) {
         set_error("items, regions or phases is NULL"); return SOAP_EINVAL;
@@ -1033,15 +1083,20 @@ soap_status soap_active_batch(soap_ctx* c, const soap_batch_item* items, int32_t
         variant = batch_default_variant(max_np);
     }
     const size_t bytes = (size_t)n_phases * (size_t)c->n_px * sizeof(float);
+    const size_t rv_off = (bytes + 255) / 256 * 256;
     float* dst = out;
+    double* rv_dst = rv_kms;
     if (!out_on_device && bytes > 0) {
-        SOAP_TRY(ensure(c->out_stage, bytes));
+        SOAP_TRY(ensure(c->out_stage, rv_off + (rv_kms ? (size_t)n_phases * 8 : 0)));
         dst = c->out_stage.as<float>();
+        if (rv_kms) rv_dst = reinterpret_cast<double*>(c->out_stage.as<char>() + rv_off);
     }
     SOAP_TRY(batch_run(c, items, n_items, regions, n_regions, phases, n_phases, variant,
-                       output == SOAP_BATCH_RESIDUAL, dst));
+                       output == SOAP_BATCH_RESIDUAL, dst, rv_dst));
     if (!out_on_device && bytes > 0) {
         SOAP_CUDA(cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, c->stream));
+        if (rv_kms)
+            SOAP_CUDA(cudaMemcpyAsync(rv_kms, rv_dst, (size_t)n_phases * 8, cudaMemcpyDeviceToHost, c->stream));
         SOAP_CUDA(cudaStreamSynchronize(c->stream));
         SOAP_TRY(check_flags(c));
     }

@@ -299,8 +299,9 @@ static soap_status launch_batch_contract(soap_ctx* c, const BatchShape& b, const
     return SOAP_OK;
 }
 
-// Enqueue stages 1-6 on the context's stream for a batch whose inputs are already on the device.
-static soap_status enqueue_batch(soap_ctx* c, const BatchShape& b, float* out) {
+// Enqueue stages 1-6 (and, with rv, 7: CCF, reduction and fits of the output rows) on the
+// context's stream for a batch whose inputs are already on the device.
+static soap_status enqueue_batch(soap_ctx* c, const BatchShape& b, float* out, double* rv, const CcfPlan* rvp) {
     const int N = c->N;
     const int q_max_taps = c->n_mu * c->n_taps;
     const double scale = std::ldexp(1.0, c->fx_bits);
@@ -363,15 +364,18 @@ static soap_status enqueue_batch(soap_ctx* c, const BatchShape& b, float* out) {
     const float* a0 = c->active_set[0] ? c->a32[0] : c->a32[1];
     const float* a1 = c->active_set[1] ? c->a32[1] : c->a32[0];
     switch (b.variant) {
-        case 0: return launch_batch_contract<1, 4>(c, b, a0, a1, out);
-        case 1: return launch_batch_contract<2, 4>(c, b, a0, a1, out);
-        case 2: return launch_batch_contract<4, 2>(c, b, a0, a1, out);
-        case 3: return launch_batch_contract<4, 4>(c, b, a0, a1, out);
-        case 4: return launch_batch_contract<8, 2>(c, b, a0, a1, out);
-        case 5: return launch_batch_contract<8, 4>(c, b, a0, a1, out);
-        case 6: return launch_batch_contract<16, 2>(c, b, a0, a1, out);
-        default: return launch_batch_contract<16, 4>(c, b, a0, a1, out);
+        case 0: SOAP_TRY((launch_batch_contract<1, 4>(c, b, a0, a1, out))); break;
+        case 1: SOAP_TRY((launch_batch_contract<2, 4>(c, b, a0, a1, out))); break;
+        case 2: SOAP_TRY((launch_batch_contract<4, 2>(c, b, a0, a1, out))); break;
+        case 3: SOAP_TRY((launch_batch_contract<4, 4>(c, b, a0, a1, out))); break;
+        case 4: SOAP_TRY((launch_batch_contract<8, 2>(c, b, a0, a1, out))); break;
+        case 5: SOAP_TRY((launch_batch_contract<8, 4>(c, b, a0, a1, out))); break;
+        case 6: SOAP_TRY((launch_batch_contract<16, 2>(c, b, a0, a1, out))); break;
+        default: SOAP_TRY((launch_batch_contract<16, 4>(c, b, a0, a1, out))); break;
     }
+    // 7 radial velocities of the output rows (Sect. 4.1), each fitted in its item's window
+    if (rv) SOAP_TRY(ccf_enqueue(c, c->b_ccf, *rvp, out, rv, nullptr, nullptr, c->b_win.as<int>()));
+    return SOAP_OK;
 }
 
 int batch_num_variants() { return kNumVariants; }
@@ -394,14 +398,18 @@ void batch_release(soap_ctx* c) {
     DevBuf* bufs[] = {&c->b_items, &c->b_regions, &c->b_phases, &c->b_phase_item, &c->b_phase_block,
                       &c->b_pblocks, &c->b_order, &c->b_cellIfx, &c->b_IB, &c->b_colj, &c->b_colw, &c->b_kq,
                       &c->b_qtoff, &c->b_qgs, &c->b_qc32, &c->b_fq, &c->b_geo, &c->b_kfix,
-                      &c->b_counters, &c->b_toff, &c->b_gstart, &c->b_coefs, &c->b_ticket};
+                      &c->b_counters, &c->b_toff, &c->b_gstart, &c->b_coefs, &c->b_ticket,
+                      &c->b_win, &c->b_ccf.tab, &c->b_ccf.tmp, &c->b_ccf.m};
     for (DevBuf* b : bufs) release(*b);
+    c->b_ccf.lines_ok = c->b_ccf.m_ok = false;
+    c->b_ccf.mask_key.clear();
 }
 
 // Host preparation (validation, classes, phase blocks, cost-ordered units, uploads), then the
 // graph: captured on the first call with a given shape, replayed on later ones.
 soap_status batch_run(soap_ctx* c, const soap_batch_item* items, int n_items, const soap_region* regions,
-                      int n_regions, const double* phases, int n_phases, int variant, int residual, float* out) {
+                      int n_regions, const double* phases, int n_phases, int variant, int residual, float* out,
+                      double* rv) {
     SOAP_TRY(join_geometry(c));                        // the cell tables (before any capture)
     if (c->alpha != 0.0) {
         set_error("the batched form needs a star without differential rotation (diff_rot_alpha = 0)");
@@ -493,6 +501,33 @@ soap_status batch_run(soap_ctx* c, const soap_batch_item* items, int n_items, co
     }
     for (int p = 0; p < n_phases; p++)
         if (phase_item[p] < 0) { set_error("phase %d belongs to no item", p); return SOAP_EINVAL; }
+    // fit windows of the RVs: per item the grid velocities with |v| <= |vsini| + margin
+    std::vector<int> win;
+    if (rv) {
+        if (!c->b_rv_set) { set_error("no mask for the batched RVs (soap_batch_set_rv)"); return SOAP_ESTATE; }
+        const int nv = c->b_rv_n_v;
+        win.resize(2 * (size_t)std::max(1, n_phases));
+        for (int k = 0; k < n_items; k++) {
+            int k0 = 0, n = nv;
+            if (c->b_rv_margin > 0) {
+                const double H = std::fabs(items[k].vsini_kms) + c->b_rv_margin;
+                const double a = std::ceil((-H - c->b_rv_v_lo) / c->b_rv_v_step - 1e-9);
+                const double z = std::floor((H - c->b_rv_v_lo) / c->b_rv_v_step + 1e-9);
+                const int lo = (int)std::max(0.0, a), hi = (int)std::min((double)(nv - 1), z);
+                k0 = lo;
+                n = hi - lo + 1;
+            }
+            if (n < 5) {
+                set_error("items[%d]: its fit window (|v| <= |vsini| + %g km/s) holds %d < 5 grid velocities", k,
+                          c->b_rv_margin, std::max(n, 0));
+                return SOAP_EINVAL;
+            }
+            for (int p = 0; p < items[k].n_phases; p++) {
+                win[2 * (size_t)(items[k].first_phase + p)] = k0;
+                win[2 * (size_t)(items[k].first_phase + p) + 1] = n;
+            }
+        }
+    }
     if (n_items == 0 || n_phases == 0) return SOAP_OK;
     BatchShape b{};
     b.n_items = n_items;
@@ -543,6 +578,13 @@ soap_status batch_run(soap_ctx* c, const soap_batch_item* items, int n_items, co
     SOAP_TRY(ensure(c->b_gstart, (size_t)b.n_pblocks * (b.G + 1) * sizeof(int)));
     SOAP_TRY(ensure(c->b_coefs, (size_t)b.n_pblocks * b.max_taps * V.PB * sizeof(float)));
     SOAP_TRY(ensure(c->b_ticket, sizeof(unsigned int)));
+    // RVs: fit windows, CCF tables and scratch (tables built here, before any capture)
+    CcfPlan rvp;
+    if (rv) {
+        SOAP_TRY(ensure(c->b_win, win.size() * sizeof(int)));
+        SOAP_TRY(ccf_prepare(c, c->b_ccf, c->b_rv_lambda.data(), c->b_rv_weight.data(), (int)c->b_rv_lambda.size(),
+                             c->b_rv_width, c->b_rv_v_lo, c->b_rv_v_step, c->b_rv_n_v, n_phases, 1, c->b_rv_tc, rvp));
+    }
     // inputs (pageable copies: the call returns after the driver has staged them)
     SOAP_CUDA(cudaMemcpyAsync(c->b_items.p, it.data(), (size_t)n_items * sizeof(BatchItemDev), cudaMemcpyHostToDevice, c->stream));
     if (!rd.empty())
@@ -552,8 +594,11 @@ soap_status batch_run(soap_ctx* c, const soap_batch_item* items, int n_items, co
     SOAP_CUDA(cudaMemcpyAsync(c->b_phase_block.p, phase_block.data(), (size_t)n_phases * sizeof(int), cudaMemcpyHostToDevice, c->stream));
     SOAP_CUDA(cudaMemcpyAsync(c->b_pblocks.p, pbl.data(), (size_t)b.n_pblocks * sizeof(PBlockDev), cudaMemcpyHostToDevice, c->stream));
     SOAP_CUDA(cudaMemcpyAsync(c->b_order.p, order.data(), (size_t)b.n_units * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    if (rv)
+        SOAP_CUDA(cudaMemcpyAsync(c->b_win.p, win.data(), (size_t)n_phases * 2 * sizeof(int), cudaMemcpyHostToDevice,
+                                  c->stream));
     if (c->profiling)      // per-kernel timers need events between the launches: no graph
-        return enqueue_batch(c, b, out);
+        return enqueue_batch(c, b, out, rv, &rvp);
     // everything the graph bakes in: sizes, star parameters and pointers
     std::vector<uint64_t> key;
     auto put = [&](uint64_t v) { key.push_back(v); };
@@ -571,6 +616,13 @@ soap_status batch_run(soap_ctx* c, const soap_batch_item* items, int n_items, co
                             &c->b_qtoff, &c->b_qgs, &c->b_qc32, &c->b_fq, &c->b_geo, &c->b_kfix,
                             &c->b_counters, &c->b_toff, &c->b_gstart, &c->b_coefs, &c->b_ticket};
     for (const DevBuf* q : bufs) putp(q->p);
+    putp(rv);
+    if (rv) {
+        putp(c->b_win.p); putp(c->b_ccf.tab.p); putp(c->b_ccf.tmp.p); putp(c->b_ccf.m.p);
+        put(rvp.n_lines); put(rvp.n_v); put(rvp.n_chunks); put(rvp.n_wgroups); put(rvp.windowed);
+        put(rvp.tile_np); put(rvp.tile_blocks); put(rvp.tile_lines); put((uint64_t)rvp.tc_chunk);
+        putd(rvp.v_lo); putd(rvp.v_step); putd(rvp.h);
+    }
     if (!c->b_graph_exec || c->b_graph_key != key) {
         if (c->b_graph_exec) { cudaGraphExecDestroy(c->b_graph_exec); c->b_graph_exec = nullptr; }
         c->b_graph_key.clear();
@@ -583,7 +635,7 @@ soap_status batch_run(soap_ctx* c, const soap_batch_item* items, int n_items, co
         soap_status st = SOAP_OK;
         cudaGraph_t graph = nullptr;
         if (e == cudaSuccess) {
-            st = enqueue_batch(c, b, out);
+            st = enqueue_batch(c, b, out, rv, &rvp);
             const cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
             if (e2 != cudaSuccess && st == SOAP_OK) e = e2;
         }

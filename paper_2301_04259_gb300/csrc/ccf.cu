@@ -18,6 +18,8 @@
 #include <cstring>
 #include <type_traits>
 #include <algorithm>
+#include <atomic>
+#include <mutex>
 
 #include "soap_internal.cuh"
 
@@ -639,11 +641,13 @@ __device__ __forceinline__ int tri(int a, int b) { return a * 4 - a * (a - 1) / 
 //     taken only while it points downhill and the steps shrink; the cost may not grow by more
 //     than 1e-12 relative from one pass to the next (else the previous point is kept).
 // Every thread runs the same iteration on bit-identical sums, so no broadcast is needed.
-__global__ void __launch_bounds__(kFitThreads) k_gauss_fit(int n_spec, int n_v, double v_lo,
+// win (nullable): per spectrum, the first velocity index k0 and the number of points n of its
+// fit window; the fit then sees the CCF at v_lo + (k0 + k) v_step, k = 0 .. n-1, only.
+__global__ void __launch_bounds__(kFitThreads) k_gauss_fit(int n_spec, int n_v_grid, double v_lo_grid,
                                                            double v_step,
                                                            const double* __restrict__ ccf,
                                                            double* scratch, double* rv,
-                                                           double* fit) {
+                                                           double* fit, const int* __restrict__ win) {
     __shared__ double tab[kFitThreads];
     __shared__ double part[9];
     __shared__ double red[kFitWarps][2];
@@ -653,8 +657,14 @@ __global__ void __launch_bounds__(kFitThreads) k_gauss_fit(int n_spec, int n_v, 
     __shared__ double sd[2 * kFitWarps * kSumD];
     const int spec = blockIdx.x;
     if (spec >= n_spec) return;
-    const double* c = ccf + (int64_t)spec * n_v;
-    double* y = scratch + (int64_t)spec * n_v;            // scaled CCF
+    int k0 = 0, n_v = n_v_grid;
+    if (win) {
+        k0 = win[2 * spec];
+        n_v = win[2 * spec + 1];
+    }
+    const double v_lo = win ? fma((double)k0, v_step, v_lo_grid) : v_lo_grid;
+    const double* c = ccf + (int64_t)spec * n_v_grid + k0;
+    double* y = scratch + (int64_t)spec * n_v_grid + k0;  // scaled CCF
     double mx = -INFINITY, mn = INFINITY;
     int kmin = n_v;
     for (int k = threadIdx.x; k < n_v; k += kFitThreads) {
@@ -792,38 +802,50 @@ __global__ void __launch_bounds__(kFitThreads) k_gauss_fit(int n_spec, int n_v, 
     }
 }
 
-bool ccf_mask_same(const soap_ctx* c, const double* mask_lambda, const double* mask_weight,
+bool ccf_mask_same(const CcfState& st, const double* mask_lambda, const double* mask_weight,
                    int n_lines, double width_kms) {
-    const std::vector<double>& k = c->ccf_mask_key;
+    const std::vector<double>& k = st.mask_key;
     return k.size() == 2 * (size_t)n_lines + 1 &&
            std::memcmp(k.data(), mask_lambda, (size_t)n_lines * 8) == 0 &&
            std::memcmp(k.data() + n_lines, mask_weight, (size_t)n_lines * 8) == 0 &&
            std::memcmp(k.data() + 2 * (size_t)n_lines, &width_kms, 8) == 0;
 }
 
-soap_status rv_ccf_run(soap_ctx* c, const void* spectra_dev, int f32, int n_spec,
-                       const double* mask_lambda, const double* mask_weight, int n_lines,
-                       double width_kms, double v_lo, double v_step, int n_v, double* rv_dev,
-                       double* fit_dev, double* ccf_dev, int tc) {
+soap_status ccf_prepare(soap_ctx* c, CcfState& st, const double* mask_lambda, const double* mask_weight,
+                        int n_lines, double width_kms, double v_lo, double v_step, int n_v, int n_spec,
+                        int f32, int tc, CcfPlan& p) {
     // line and velocity tables: kept while the mask, its width and the velocity grid stay the same
-    const bool same_tab = c->ccf_lines_ok && c->ccf_vel_key[0] == v_lo && c->ccf_vel_key[1] == v_step &&
-                          c->ccf_vel_key[2] == (double)n_v &&
-                          ccf_mask_same(c, mask_lambda, mask_weight, n_lines, width_kms);
+    const bool same_tab = st.lines_ok && st.vel_key[0] == v_lo && st.vel_key[1] == v_step &&
+                          st.vel_key[2] == (double)n_v &&
+                          ccf_mask_same(st, mask_lambda, mask_weight, n_lines, width_kms);
     bool sorted = true;
     if (same_tab) {
-        sorted = c->ccf_sorted;
+        sorted = st.sorted;
     } else {
         for (int l = 1; l < n_lines; l++)
             if (mask_lambda[l] < mask_lambda[l - 1]) { sorted = false; break; }
     }
+    if ((int64_t)(n_spec + kTileSB - 1) / kTileSB > 65535) {
+        set_error("%d spectra in one CCF call; at most %d", n_spec, 65535 * kTileSB);
+        return SOAP_ERANGE;
+    }
+    p = CcfPlan{};
+    p.n_spec = n_spec;
+    p.n_lines = n_lines;
+    p.n_v = n_v;
+    p.f32 = f32;
+    p.v_lo = v_lo;
+    p.v_step = v_step;
+    p.h = width_kms / (2.0 * kCKms * c->delta);
     // windowed kernel: one velocity per thread (n_v <= 256); blocks walk the chunks
-    const bool windowed = sorted && n_v <= 256 && 2.0 * width_kms / (2.0 * kCKms * c->delta) <= 15.0;
-    const int n_wchunks = (n_lines + kWinLines - 1) / kWinLines;
-    const int n_wgroups = n_wchunks;                    // one chunk of lines per block
-    int n_chunks = windowed ? n_wgroups : (n_lines + kLinesPerChunk - 1) / kLinesPerChunk;
+    p.windowed = sorted && n_v <= 256 && 2.0 * width_kms / (2.0 * kCKms * c->delta) <= 15.0;
+    p.n_wgroups = (n_lines + kWinLines - 1) / kWinLines;   // one chunk of lines per block
+    p.n_chunks = p.windowed ? p.n_wgroups : (n_lines + kLinesPerChunk - 1) / kLinesPerChunk;
+    int sms = 0, dev = 0;
+    SOAP_CUDA(cudaGetDevice(&dev));
+    SOAP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     // register-tiled kernel (FP32, sorted mask): pixels a group of kTileVT velocities can reach
     // for one line, from the largest spread of kTileVT consecutive box positions
-    int tile_np = 0, tile_blocks = 0, tile_lines = 0;
     if (f32 && sorted && n_v >= kTileVT) {
         const double box = width_kms / (kCKms * c->delta);
         double spread = 0.0;
@@ -838,37 +860,30 @@ soap_status rv_ccf_run(soap_ctx* c, const void* spectra_dev, int f32, int n_spec
             sweep + np + 5 + 1 <= kTileWin) {
             // one full wave: as many blocks as fit on the GPU at once, split evenly over the lines
             // (a partial second wave would double the time of its SMs)
-            tile_np = std::max(np, 2);
+            p.tile_np = std::max(np, 2);
             const int tthreads = (groups * kTileLP + 31) / 32 * 32;
-            int sms = 0, dev = 0, per_sm = 0;
-            SOAP_CUDA(cudaGetDevice(&dev));
-            SOAP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+            int per_sm = 0;
             SOAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &per_sm, tile_np == 2 ? k_ccf_tile<2> : tile_np == 3 ? k_ccf_tile<3> : k_ccf_tile<4>,
+                &per_sm, p.tile_np == 2 ? k_ccf_tile<2> : p.tile_np == 3 ? k_ccf_tile<3> : k_ccf_tile<4>,
                 tthreads, 0));
             const int ys = (n_spec + kTileSB - 1) / kTileSB;
             const int wave = std::max(1, sms * std::max(per_sm, 1));
-            tile_blocks = std::max(1, std::min(wave >= ys ? wave / ys : 1, (n_lines + 7) / 8));
-            tile_lines = (n_lines + tile_blocks - 1) / tile_blocks;
-            tile_blocks = (n_lines + tile_lines - 1) / tile_lines;
-            n_chunks = tile_blocks;
+            p.tile_blocks = std::max(1, std::min(wave >= ys ? wave / ys : 1, (n_lines + 7) / 8));
+            p.tile_lines = (n_lines + p.tile_blocks - 1) / p.tile_blocks;
+            p.tile_blocks = (n_lines + p.tile_lines - 1) / p.tile_lines;
+            p.n_chunks = p.tile_blocks;
         }
     }
     // tensor-core form (FP32 spectra, sorted mask): pixel chunks of one wave of CTAs
-    int64_t tc_chunk = 0;
-    int tc_smin = 0, tc_smax = 0;
     if (tc && f32 && sorted && ccf_tc_fits(n_v)) {
-        int sms = 0, dev = 0;
-        SOAP_CUDA(cudaGetDevice(&dev));
-        SOAP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        tc_chunk = ccf_tc_chunk(c->n_px, n_spec, sms);
-        n_chunks = (int)((c->n_px + tc_chunk - 1) / tc_chunk);
+        p.tc_chunk = ccf_tc_chunk(c->n_px, n_spec, sms);
+        p.n_chunks = (int)((c->n_px + p.tc_chunk - 1) / p.tc_chunk);
         // range of the velocity shifts' integer parts S_k, one pixel of margin on each side
         double s_a = std::atanh(v_lo / kCKms) / c->delta;
         double s_b = std::atanh((v_lo + v_step * (n_v - 1)) / kCKms) / c->delta;
-        tc_smin = (int)std::floor(std::min(s_a, s_b)) - 1;
-        tc_smax = (int)std::floor(std::max(s_a, s_b)) + 1;
-        tile_np = 0;
+        p.tc_smin = (int)std::floor(std::min(s_a, s_b)) - 1;
+        p.tc_smax = (int)std::floor(std::max(s_a, s_b)) + 1;
+        p.tile_np = 0;
     }
     // table layout (8-byte aligned pieces, 256-byte aligned blocks) and per-call scratch
     auto al = [](size_t x) { return (x + 255) / 256 * 256; };
@@ -884,75 +899,85 @@ soap_status rv_ccf_run(soap_ctx* c, const void* spectra_dev, int f32, int n_spec
     size_t o_g32 = al(o_g64 + (size_t)n_v * 8);
     size_t tab_total = o_g32 + (size_t)n_v * 4;
     size_t o_part = 0;
-    size_t o_ccf = al(o_part + (size_t)n_chunks * n_spec * n_v * 8);
+    size_t o_ccf = al(o_part + (size_t)p.n_chunks * n_spec * n_v * 8);
     size_t o_y = al(o_ccf + (size_t)n_spec * n_v * 8);
     size_t total = o_y + (size_t)n_spec * n_v * 8;
-    SOAP_TRY(ensure(c->ccf_tmp, total));
-    SOAP_TRY(ensure(c->ccf_tab, tab_total));
-    char* tab = c->ccf_tab.as<char>();
-    char* base = c->ccf_tmp.as<char>();
-    double* d_lam = (double*)(tab + o_lam);
-    double* d_w = (double*)(tab + o_w);
-    int* d_U = (int*)(tab + o_U);
-    double* d_f64 = (double*)(tab + o_f64);
-    float* d_f32 = (float*)(tab + o_f32);
-    float* d_w32 = (float*)(tab + o_w32);
-    int* d_valid = (int*)(tab + o_valid);
-    int* d_S = (int*)(tab + o_S);
-    double* d_g64 = (double*)(tab + o_g64);
-    float* d_g32 = (float*)(tab + o_g32);
-    double* d_part = (double*)(base + o_part);
-    double* d_ccf = ccf_dev ? ccf_dev : (double*)(base + o_ccf);
-    double* d_y = (double*)(base + o_y);
-    cudaEvent_t tb = (c->profiling && !same_tab) ? timer_begin(c) : nullptr;
-    const double h = width_kms / (2.0 * kCKms * c->delta);
-    const double v_hi = v_lo + v_step * (n_v - 1);
+    SOAP_TRY(ensure(st.tmp, total));
     if (!same_tab) {
-        c->ccf_lines_ok = false;
-        c->ccf_m_ok = false;
-        SOAP_TRY(upload_small(c, d_lam, mask_lambda, (size_t)n_lines * 8));
-        SOAP_TRY(upload_small(c, d_w, mask_weight, (size_t)n_lines * 8));
-        k_ccf_lines<<<(n_lines + 255) / 256, 256, 0, c->stream>>>(
-            n_lines, d_lam, d_w, c->lam_s, c->delta, h, std::atanh(v_lo / kCKms) / c->delta,
-            std::atanh(v_hi / kCKms) / c->delta, c->n_px, d_U, d_f64, d_f32, d_w32, d_valid);
-        SOAP_LAUNCHED(c);
-        k_ccf_velocities<<<(n_v + 127) / 128, 128, 0, c->stream>>>(n_v, v_lo, v_step, c->delta, d_S,
-                                                                   d_g64, d_g32);
-        SOAP_LAUNCHED(c);
-        c->ccf_mask_key.assign(mask_lambda, mask_lambda + n_lines);
-        c->ccf_mask_key.insert(c->ccf_mask_key.end(), mask_weight, mask_weight + n_lines);
-        c->ccf_mask_key.push_back(width_kms);
-        c->ccf_vel_key[0] = v_lo;
-        c->ccf_vel_key[1] = v_step;
-        c->ccf_vel_key[2] = (double)n_v;
-        c->ccf_sorted = sorted;
-        c->ccf_lines_ok = true;
+        // a grown table buffer moves: the old tables (and the mask matrix) are gone with it
+        st.lines_ok = false;
+        st.m_ok = false;
+        SOAP_TRY(ensure(st.tab, tab_total));
     }
-    if (tb) timer_end(c, SOAP_TIMER_CCF_AUX, tb);
-    tb = c->profiling ? timer_begin(c) : nullptr;
+    char* tab = st.tab.as<char>();
+    char* base = st.tmp.as<char>();
+    double* d_lam = (double*)(tab + o_lam);
+    p.w64 = (double*)(tab + o_w);
+    p.U = (int*)(tab + o_U);
+    p.f64 = (double*)(tab + o_f64);
+    p.f32t = (float*)(tab + o_f32);
+    p.w32 = (float*)(tab + o_w32);
+    p.valid = (int*)(tab + o_valid);
+    p.S = (int*)(tab + o_S);
+    p.g64 = (double*)(tab + o_g64);
+    p.g32 = (float*)(tab + o_g32);
+    p.part = (double*)(base + o_part);
+    p.ccf = (double*)(base + o_ccf);
+    p.y = (double*)(base + o_y);
+    if (!same_tab) {
+        cudaEvent_t tb = c->profiling ? timer_begin(c) : nullptr;
+        const double v_hi = v_lo + v_step * (n_v - 1);
+        SOAP_TRY(upload_small(c, d_lam, mask_lambda, (size_t)n_lines * 8));
+        SOAP_TRY(upload_small(c, p.w64, mask_weight, (size_t)n_lines * 8));
+        k_ccf_lines<<<(n_lines + 255) / 256, 256, 0, c->stream>>>(
+            n_lines, d_lam, p.w64, c->lam_s, c->delta, p.h, std::atanh(v_lo / kCKms) / c->delta,
+            std::atanh(v_hi / kCKms) / c->delta, c->n_px, p.U, p.f64, p.f32t, p.w32, p.valid);
+        SOAP_LAUNCHED(c);
+        k_ccf_velocities<<<(n_v + 127) / 128, 128, 0, c->stream>>>(n_v, v_lo, v_step, c->delta, p.S,
+                                                                   p.g64, p.g32);
+        SOAP_LAUNCHED(c);
+        st.mask_key.assign(mask_lambda, mask_lambda + n_lines);
+        st.mask_key.insert(st.mask_key.end(), mask_weight, mask_weight + n_lines);
+        st.mask_key.push_back(width_kms);
+        st.vel_key[0] = v_lo;
+        st.vel_key[1] = v_step;
+        st.vel_key[2] = (double)n_v;
+        st.sorted = sorted;
+        st.lines_ok = true;
+        if (tb) timer_end(c, SOAP_TIMER_CCF_AUX, tb);
+    }
+    if (p.tc_chunk && !st.m_ok) SOAP_TRY(ccf_tc_build_m(c, st, p));
+    return SOAP_OK;
+}
+
+soap_status ccf_enqueue(soap_ctx* c, CcfState& st, const CcfPlan& p, const void* spectra_dev, double* rv_dev,
+                        double* fit_dev, double* ccf_dev, const int* win) {
+    const int n_spec = p.n_spec, n_v = p.n_v, n_lines = p.n_lines;
+    double* d_part = p.part;
+    double* d_ccf = ccf_dev ? ccf_dev : p.ccf;
+    cudaEvent_t tb = c->profiling ? timer_begin(c) : nullptr;
     const int threads = n_v >= 256 ? 256 : ((n_v + 31) / 32) * 32;
-    if (tc_chunk) {
-        SOAP_TRY(ccf_tc(c, n_lines, d_U, d_f32, d_valid, d_w32, n_v, d_S, d_g32, tc_smin, tc_smax, 2.0 * h,
-                        tc_chunk, n_spec, (const float*)spectra_dev, reinterpret_cast<float*>(d_part)));
-    } else if (tile_np) {
+    if (p.tc_chunk) {
+        SOAP_TRY(ccf_tc(c, st, p, (const float*)spectra_dev, reinterpret_cast<float*>(d_part)));
+    } else if (p.tile_np) {
         const int tthreads = ((n_v + kTileVT - 1) / kTileVT * kTileLP + 31) / 32 * 32;
-        dim3 grid((unsigned)tile_blocks, (unsigned)((n_spec + kTileSB - 1) / kTileSB));
-        const float box = (float)(2.0 * h);
+        dim3 grid((unsigned)p.tile_blocks, (unsigned)((n_spec + kTileSB - 1) / kTileSB));
+        const float box = (float)(2.0 * p.h);
 #define SOAP_TILE_LAUNCH(NP)                                                                       \
-        k_ccf_tile<NP><<<grid, tthreads, 0, c->stream>>>(n_lines, tile_lines, d_U, d_f32, d_valid,  \
-                                                         d_w32, n_v, d_S, d_g32, box, c->n_px,     \
+        k_ccf_tile<NP><<<grid, tthreads, 0, c->stream>>>(n_lines, p.tile_lines, p.U, p.f32t, p.valid, \
+                                                         p.w32, n_v, p.S, p.g32, box, c->n_px,     \
                                                          n_spec, (const float*)spectra_dev,        \
                                                          reinterpret_cast<float*>(d_part))
-        if (tile_np == 2) SOAP_TILE_LAUNCH(2);
-        else if (tile_np == 3) SOAP_TILE_LAUNCH(3);
+        if (p.tile_np == 2) SOAP_TILE_LAUNCH(2);
+        else if (p.tile_np == 3) SOAP_TILE_LAUNCH(3);
         else SOAP_TILE_LAUNCH(4);
 #undef SOAP_TILE_LAUNCH
-    } else if (windowed) {
+    } else if (p.windowed) {
         const int threads = ((n_v + 31) / 32) * 32;
-        const double box = 2.0 * h;
+        const double box = 2.0 * p.h;
         const bool small = box <= 1.0;                   // the box covers at most 2 pixels
-        dim3 grid32((unsigned)n_wgroups, (unsigned)((n_spec + 15) / 16));
-        dim3 grid64((unsigned)n_wgroups, (unsigned)((n_spec + 7) / 8));
+        dim3 grid32((unsigned)p.n_wgroups, (unsigned)((n_spec + 15) / 16));
+        dim3 grid64((unsigned)p.n_wgroups, (unsigned)((n_spec + 7) / 8));
         const size_t smem32 = (size_t)kWinMax * (16 + 4) * 4;
         const size_t smem64 = (size_t)kWinMax * (8 + 2) * 8;
 #define SOAP_CCF_LAUNCH(T, SB, NB, GRID, SMEM, F, WT, G, SPEC)                                    \
@@ -960,45 +985,57 @@ soap_status rv_ccf_run(soap_ctx* c, const void* spectra_dev, int f32, int n_spec
             SOAP_CUDA(cudaFuncSetAttribute(k_ccf_window<T, SB, NB>,                                \
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM)); \
             k_ccf_window<T, SB, NB><<<GRID, threads, SMEM, c->stream>>>(                          \
-                n_lines, d_U, F, d_valid, WT, n_v, d_S, G, box, c->n_px, n_spec,                   \
+                n_lines, p.U, F, p.valid, WT, n_v, p.S, G, box, c->n_px, n_spec,                   \
                 (const T*)SPEC, reinterpret_cast<T*>(d_part));                                     \
         } while (0)
-        if (f32) {
-            if (small) SOAP_CCF_LAUNCH(float, 16, 2, grid32, smem32, d_f32, d_w32, d_g32, spectra_dev);
-            else SOAP_CCF_LAUNCH(float, 16, 16, grid32, smem32, d_f32, d_w32, d_g32, spectra_dev);
+        if (p.f32) {
+            if (small) SOAP_CCF_LAUNCH(float, 16, 2, grid32, smem32, p.f32t, p.w32, p.g32, spectra_dev);
+            else SOAP_CCF_LAUNCH(float, 16, 16, grid32, smem32, p.f32t, p.w32, p.g32, spectra_dev);
         } else {
-            if (small) SOAP_CCF_LAUNCH(double, 8, 2, grid64, smem64, d_f64, d_w, d_g64, spectra_dev);
-            else SOAP_CCF_LAUNCH(double, 8, 16, grid64, smem64, d_f64, d_w, d_g64, spectra_dev);
+            if (small) SOAP_CCF_LAUNCH(double, 8, 2, grid64, smem64, p.f64, p.w64, p.g64, spectra_dev);
+            else SOAP_CCF_LAUNCH(double, 8, 16, grid64, smem64, p.f64, p.w64, p.g64, spectra_dev);
         }
 #undef SOAP_CCF_LAUNCH
-    } else if (f32) {
+    } else if (p.f32) {
         constexpr int SB = 16;
-        dim3 grid((unsigned)n_chunks, (unsigned)((n_spec + SB - 1) / SB));
+        dim3 grid((unsigned)p.n_chunks, (unsigned)((n_spec + SB - 1) / SB));
         k_ccf_partial<float, SB><<<grid, threads, 0, c->stream>>>(
-            n_lines, d_U, d_f32, d_valid, d_w, n_v, d_S, d_g32, 2.0 * h, c->n_px, n_spec,
+            n_lines, p.U, p.f32t, p.valid, p.w64, n_v, p.S, p.g32, 2.0 * p.h, c->n_px, n_spec,
             (const float*)spectra_dev, d_part);
     } else {
         constexpr int SB = 8;
-        dim3 grid((unsigned)n_chunks, (unsigned)((n_spec + SB - 1) / SB));
+        dim3 grid((unsigned)p.n_chunks, (unsigned)((n_spec + SB - 1) / SB));
         k_ccf_partial<double, SB><<<grid, threads, 0, c->stream>>>(
-            n_lines, d_U, d_f64, d_valid, d_w, n_v, d_S, d_g64, 2.0 * h, c->n_px, n_spec,
+            n_lines, p.U, p.f64, p.valid, p.w64, n_v, p.S, p.g64, 2.0 * p.h, c->n_px, n_spec,
             (const double*)spectra_dev, d_part);
     }
     SOAP_LAUNCHED(c);
     if (tb) timer_end(c, SOAP_TIMER_CCF, tb);
     tb = c->profiling ? timer_begin(c) : nullptr;
     int64_t tot = (int64_t)n_spec * n_v * kReduceSplit;
-    if ((windowed || tile_np || tc_chunk) && f32)      // FP32 partial sums (converted exactly to FP64 here)
+    if ((p.windowed || p.tile_np || p.tc_chunk) && p.f32)   // FP32 partial sums (converted exactly to FP64 here)
         k_ccf_reduce<float><<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(
-            n_chunks, n_spec, n_v, reinterpret_cast<const float*>(d_part), d_ccf);
+            p.n_chunks, n_spec, n_v, reinterpret_cast<const float*>(d_part), d_ccf);
     else
-        k_ccf_reduce<double><<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(n_chunks, n_spec, n_v, d_part, d_ccf);
+        k_ccf_reduce<double><<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(p.n_chunks, n_spec, n_v,
+                                                                                  d_part, d_ccf);
     SOAP_LAUNCHED(c);
     if (tb) timer_end(c, SOAP_TIMER_CCF_AUX, tb);
     SOAP_TIMED(c, SOAP_TIMER_FIT,
-               k_gauss_fit<<<n_spec, kFitThreads, 0, c->stream>>>(n_spec, n_v, v_lo, v_step, d_ccf, d_y, rv_dev, fit_dev);
+               k_gauss_fit<<<n_spec, kFitThreads, 0, c->stream>>>(n_spec, n_v, p.v_lo, p.v_step, d_ccf, p.y,
+                                                                  rv_dev, fit_dev, win);
                SOAP_LAUNCHED(c));
     return SOAP_OK;
+}
+
+soap_status rv_ccf_run(soap_ctx* c, const void* spectra_dev, int f32, int n_spec,
+                       const double* mask_lambda, const double* mask_weight, int n_lines,
+                       double width_kms, double v_lo, double v_step, int n_v, double* rv_dev,
+                       double* fit_dev, double* ccf_dev, int tc) {
+    CcfPlan p;
+    SOAP_TRY(ccf_prepare(c, c->ccf, mask_lambda, mask_weight, n_lines, width_kms, v_lo, v_step, n_v, n_spec,
+                         f32, tc, p));
+    return ccf_enqueue(c, c->ccf, p, spectra_dev, rv_dev, fit_dev, ccf_dev, nullptr);
 }
 
 }  // namespace soap
@@ -1018,11 +1055,13 @@ constexpr size_t kStaticScratchBytes = size_t(16) << 20;      // 16 MiB
 static __device__ __align__(256) unsigned char g_rv_scratch[kStaticScratchBytes];
 
 constexpr int kStaticMaxDevices = 64;
-static void* g_rv_scratch_ptr[kStaticMaxDevices];              // device address per device
-static bool g_rv_scratch_ready[kStaticMaxDevices];
+static std::atomic<void*> g_rv_scratch_ptr[kStaticMaxDevices];   // device address per device
+static std::mutex g_rv_scratch_mutex;                            // serialises first lookups
 
 // Device address of g_rv_scratch on the current device, looked up once per device.  In host
 // code g_rv_scratch is only a host-side handle, so the address must come from the runtime.
+// Threads making their first call at the same time take the lookup in turn; later calls read
+// the cached address without locking.
 static soap_status static_scratch(void** out) {
     int dev = 0;
     SOAP_CUDA(cudaGetDevice(&dev));
@@ -1030,17 +1069,20 @@ static soap_status static_scratch(void** out) {
         set_error("device %d beyond the %d devices soap_rv_ccf_static supports", dev, kStaticMaxDevices);
         return SOAP_ERANGE;
     }
-    if (!g_rv_scratch_ready[dev]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_rv_scratch);
-        if (e != cudaSuccess || !p) {
-            set_error("cudaGetSymbolAddress(g_rv_scratch) failed: %s", cudaGetErrorString(e));
-            return SOAP_ECUDA;
+    void* p = g_rv_scratch_ptr[dev].load(std::memory_order_acquire);
+    if (!p) {
+        std::lock_guard<std::mutex> lock(g_rv_scratch_mutex);
+        p = g_rv_scratch_ptr[dev].load(std::memory_order_acquire);
+        if (!p) {
+            cudaError_t e = cudaGetSymbolAddress(&p, g_rv_scratch);
+            if (e != cudaSuccess || !p) {
+                set_error("cudaGetSymbolAddress(g_rv_scratch) failed: %s", cudaGetErrorString(e));
+                return SOAP_ECUDA;
+            }
+            g_rv_scratch_ptr[dev].store(p, std::memory_order_release);
         }
-        g_rv_scratch_ptr[dev] = p;
-        g_rv_scratch_ready[dev] = true;
     }
-    *out = g_rv_scratch_ptr[dev];
+    *out = p;
     return SOAP_OK;
 }
 
@@ -1055,6 +1097,7 @@ extern "C" soap_status soap_rv_ccf_static(double lambda_start_A, double lambda_e
     using namespace soap;
     clear_error();
     if (!spectra || !mask_lambda || !mask_weight || !rv_kms) { set_error("NULL argument"); return SOAP_EINVAL; }
+    if (spectra_f32 != 0 && spectra_f32 != 1) { set_error("spectra_f32 must be 0 or 1"); return SOAP_EINVAL; }
     if (!(lambda_start_A > 0) || !(lambda_end_A > lambda_start_A) || !std::isfinite(lambda_end_A) ||
         n_px < 2 || n_px > (int64_t(1) << 28)) {
         set_error("invalid wavelength grid"); return SOAP_EINVAL;
@@ -1131,7 +1174,8 @@ extern "C" soap_status soap_rv_ccf_static(double lambda_start_A, double lambda_e
     int64_t tot = (int64_t)n_spec * n_v * kReduceSplit;
     k_ccf_reduce<double><<<(unsigned)((tot + 255) / 256), 256, 0, stream>>>(n_chunks, n_spec, n_v, d_part, d_ccf);
     SOAP_CUDA(cudaGetLastError());
-    k_gauss_fit<<<n_spec, kFitThreads, 0, stream>>>(n_spec, n_v, v_lo, v_step, d_ccf, d_y, rv_kms, fit_params);
+    k_gauss_fit<<<n_spec, kFitThreads, 0, stream>>>(n_spec, n_v, v_lo, v_step, d_ccf, d_y, rv_kms, fit_params,
+                                                    nullptr);
     SOAP_CUDA(cudaGetLastError());
     return SOAP_OK;
 }

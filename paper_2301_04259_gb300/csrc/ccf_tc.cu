@@ -323,51 +323,53 @@ int64_t ccf_tc_chunk(int64_t n_px, int n_spec, int sms) {
     return std::max<int64_t>(kCcK, std::min<int64_t>(chunk, kCcChunkMax));
 }
 
-soap_status ccf_tc(soap_ctx* c, int n_lines, const int* U, const float* f, const int* valid, const float* w,
-                   int n_v, const int* S, const float* g, int s_min, int s_max, double box, int64_t chunk,
-                   int n_spec, const float* spectra, float* partial) {
-    const int n_pad = (n_v + 15) / 16 * 16;
-    if (!c->ccf_m_ok) {
-        // the mask matrix of this mask and velocity grid (kept until either changes)
-        const int64_t n_kb = (c->n_px + kCcK - 1) / kCcK;
-        SOAP_TRY(ensure(c->ccf_m, (size_t)n_kb * 2 * cc_bb(n_pad)));
-        CcMArgs m{};
-        m.U = U;
-        m.f = f;
-        m.valid = valid;
-        m.w = w;
-        m.S = S;
-        m.g = g;
-        m.m = c->ccf_m.as<unsigned char>();
-        m.n_lines = n_lines;
-        m.n_v = n_v;
-        m.n_pad = n_pad;
-        // a line reaches pixels [p, p + 64) at velocity k only if U + S_k < p + 64 and
-        // U + S_k + 2 + box > p (box start U + S_k + f + g with f + g < 2); S_min, S_max carry a margin
-        m.lo_off = s_max + 2 + (int)std::ceil(box) + 1;
-        m.hi_off = kCcK - s_min + 1;
-        m.box = (float)box;
-        SOAP_TRY(fit_dynamic_smem(k_ccf_tc_m, cc_m_smem()));
-        k_ccf_tc_m<<<(unsigned)n_kb, kCcThreads, cc_m_smem(), c->stream>>>(m);
-        SOAP_LAUNCHED(c);
-        c->ccf_m_ok = true;
-    }
+soap_status ccf_tc_build_m(soap_ctx* c, CcfState& st, const CcfPlan& p) {
+    // the mask matrix of this mask and velocity grid (kept until either changes)
+    const int n_pad = (p.n_v + 15) / 16 * 16;
+    const int64_t n_kb = (c->n_px + kCcK - 1) / kCcK;
+    const double box = 2.0 * p.h;
+    SOAP_TRY(ensure(st.m, (size_t)n_kb * 2 * cc_bb(n_pad)));
+    CcMArgs m{};
+    m.U = p.U;
+    m.f = p.f32t;
+    m.valid = p.valid;
+    m.w = p.w32;
+    m.S = p.S;
+    m.g = p.g32;
+    m.m = st.m.as<unsigned char>();
+    m.n_lines = p.n_lines;
+    m.n_v = p.n_v;
+    m.n_pad = n_pad;
+    // a line reaches pixels [p, p + 64) at velocity k only if U + S_k < p + 64 and
+    // U + S_k + 2 + box > p (box start U + S_k + f + g with f + g < 2); S_min, S_max carry a margin
+    m.lo_off = p.tc_smax + 2 + (int)std::ceil(box) + 1;
+    m.hi_off = kCcK - p.tc_smin + 1;
+    m.box = (float)box;
+    SOAP_TRY(fit_dynamic_smem(k_ccf_tc_m, cc_m_smem()));
+    k_ccf_tc_m<<<(unsigned)n_kb, kCcThreads, cc_m_smem(), c->stream>>>(m);
+    SOAP_LAUNCHED(c);
+    st.m_ok = true;
+    return SOAP_OK;
+}
+
+soap_status ccf_tc(soap_ctx* c, const CcfState& st, const CcfPlan& p, const float* spectra, float* partial) {
+    const int n_pad = (p.n_v + 15) / 16 * 16;
     CcArgs a{};
-    a.m = c->ccf_m.as<unsigned char>();
+    a.m = st.m.as<unsigned char>();
     a.spectra = spectra;
     a.partial = partial;
     a.n_px = c->n_px;
-    a.chunk = chunk;
-    a.n_v = n_v;
+    a.chunk = p.tc_chunk;
+    a.n_v = p.n_v;
     a.n_pad = n_pad;
-    a.n_spec = n_spec;
+    a.n_spec = p.n_spec;
     a.vec4 = (reinterpret_cast<uintptr_t>(spectra) % 16 == 0 && c->n_px % 4 == 0) ? 1 : 0;
     uint32_t cols = 32;
     while ((int)cols < n_pad) cols <<= 1;
     a.tmem_cols = cols;
     const size_t smem = cc_smem(n_pad);
     SOAP_TRY(fit_dynamic_smem(k_ccf_tc, smem));
-    dim3 grid((unsigned)((c->n_px + chunk - 1) / chunk), (unsigned)((n_spec + kCcM - 1) / kCcM));
+    dim3 grid((unsigned)((c->n_px + p.tc_chunk - 1) / p.tc_chunk), (unsigned)((p.n_spec + kCcM - 1) / kCcM));
     k_ccf_tc<<<grid, kCcThreads, smem, c->stream>>>(a, c->flags);
     SOAP_LAUNCHED(c);
     return SOAP_OK;

@@ -105,6 +105,34 @@ enum DeviceFlag : unsigned int {
     kFlagTimeout = 16u         // a tensor-core kernel's bounded barrier wait gave up
 };
 
+// CCF state of one user of the CCF (the single-star calls, or the batched form): line and
+// velocity tables (kept while the mask and the velocity grid stay the same), the cached mask
+// matrix of the tensor-core form, and per-call scratch (partial sums, CCF, scaled CCF).
+struct CcfState {
+    DevBuf tab, tmp, m;
+    std::vector<double> mask_key;        // mask_lambda, mask_weight, then width
+    double vel_key[3] = {0, 0, -1};      // v_lo, v_step, n_v
+    bool lines_ok = false;
+    bool sorted = false;
+    bool m_ok = false;                   // tensor-core mask matrix built for the current tables
+};
+
+// How one CCF call runs (ccf_prepare), for n_spec spectra.
+struct CcfPlan {
+    int n_spec = 0, n_lines = 0, n_v = 0, f32 = 0;
+    double v_lo = 0, v_step = 0, h = 0;
+    bool windowed = false;
+    int n_wgroups = 0, n_chunks = 0;
+    int tile_np = 0, tile_blocks = 0, tile_lines = 0;
+    int64_t tc_chunk = 0;
+    int tc_smin = 0, tc_smax = 0;
+    // device tables (in CcfState::tab) and scratch (in CcfState::tmp)
+    int* U = nullptr; double* f64 = nullptr; float* f32t = nullptr; float* w32 = nullptr;
+    int* valid = nullptr; double* w64 = nullptr;
+    int* S = nullptr; double* g64 = nullptr; float* g32 = nullptr;
+    double* part = nullptr; double* ccf = nullptr; double* y = nullptr;
+};
+
 }  // namespace soap
 
 struct soap_ctx {
@@ -184,8 +212,7 @@ struct soap_ctx {
     soap::DevBuf phases;
     soap::DevBuf radii;         // per-(phase, region) radii of evolving regions
     soap::DevBuf out_stage;     // device output when the caller wants host output
-    soap::DevBuf partial;       // direct-form and CCF partial sums
-    soap::DevBuf ccf_tmp;       // CCF inputs / outputs
+    soap::DevBuf partial;       // direct-form partial sums
     soap::HostBuf host_stage;
     soap::PinnedRing ring;      // small uploads (see PinnedRing)
 
@@ -198,15 +225,8 @@ struct soap_ctx {
     soap::DevBuf bis_tab;       // bisector tables of the last injection
     soap::DevBuf tc_coef;       // tensor-core contraction: kernel rows (BF16 hi / lo) + block flags
 
-    // CCF line and velocity tables, kept while the mask and the velocity grid stay the same
-    soap::DevBuf ccf_tab;
-    std::vector<double> ccf_mask_key;    // mask_lambda, mask_weight, then width
-    double ccf_vel_key[3] = {0, 0, -1};  // v_lo, v_step, n_v
-    bool ccf_lines_ok = false;
-    bool ccf_sorted = false;
-    // tensor-core CCF: the mask matrix as BF16 hi / lo tiles (ccf_tc.cu), kept with the tables
-    soap::DevBuf ccf_m;
-    bool ccf_m_ok = false;
+    // CCF of the single-star calls (soap_rv_ccf, soap_active_rv)
+    soap::CcfState ccf;
 
     // host-transfer pipeline: uploads from host memory run on in_stream, downloads of host
     // results on out_stream, ordered against the compute stream by events.  up_* serve the
@@ -231,6 +251,13 @@ struct soap_ctx {
     std::vector<uint64_t> b_graph_key;
     uint64_t b_graph_kernels = 0;
     int b_variant = -1;             // chosen by soap_batch_set_variant / the autotuner; -1: default
+    // batched RVs (soap_batch_set_rv): mask and velocity grid, fit margin, CCF form, own CCF state
+    bool b_rv_set = false;
+    std::vector<double> b_rv_lambda, b_rv_weight;
+    double b_rv_width = 0, b_rv_v_lo = 0, b_rv_v_step = 0, b_rv_margin = 0;
+    int b_rv_n_v = 0, b_rv_tc = 0;
+    soap::CcfState b_ccf;
+    soap::DevBuf b_win;             // per phase: first point and length of its fit window
 
     // per-kernel timers
     bool profiling = false;
@@ -285,8 +312,8 @@ soap_status inject_bisectors(soap_ctx* c, const double* in, double* out, int n_r
 // ring (pageable sources are fine; the source may change once the call returns).
 soap_status upload_small(soap_ctx* c, void* dst, const void* src, size_t bytes);
 void ring_release(soap_ctx* c);
-// True when the context's CCF line tables were built from exactly this mask and width.
-bool ccf_mask_same(const soap_ctx* c, const double* mask_lambda, const double* mask_weight,
+// True when the CCF line tables of `st` were built from exactly this mask and width.
+bool ccf_mask_same(const CcfState& st, const double* mask_lambda, const double* mask_weight,
                    int n_lines, double width_kms);
 
 // Toeplitz quiet spectrum into dst (fp64 or fp32) on the context's stream.
@@ -313,24 +340,38 @@ soap_status toeplitz_active(soap_ctx* c, const RegionDev* regions_host, int n_re
 
 // Batched form (batch.cu); variant in 0 .. batch_num_variants() - 1, out [n_phases][n_px] FP32
 // (F, or F - F_q when residual).
+// rv (nullable): device [n_phases] RVs of the output rows (needs the RV mask of soap_batch_set_rv).
 soap_status batch_run(soap_ctx* c, const soap_batch_item* items, int n_items, const soap_region* regions,
-                      int n_regions, const double* phases, int n_phases, int variant, int residual, float* out);
+                      int n_regions, const double* phases, int n_phases, int variant, int residual, float* out,
+                      double* rv = nullptr);
 int batch_num_variants();
 int batch_default_variant(int max_phases_per_item);
 void batch_variant_info(int v, int* phases_per_block, int* px_per_thread);
 void batch_release(soap_ctx* c);
 
+// CCF + Gaussian RV fit (Sect. 4.1) in two steps.  ccf_prepare makes the host decisions for
+// n_spec spectra, sizes the scratch of `st` and, when the mask or the velocity grid changed,
+// uploads the mask and builds the line / velocity tables (and, for the tensor-core form, the mask
+// matrix) on the context's stream.  ccf_enqueue then only launches kernels (no allocation, no
+// host transfer: it may be captured into a graph): partial sums, their reduction and the fits.
 // tc: FP32 spectra whose CCF may run on the tensor cores (BF16 split, ccf_tc.cu) where that
-// form applies (mask sorted by wavelength, at most 240 velocities)
+// form applies (mask sorted by wavelength, at most 256 velocities).  win (nullable): per spectrum
+// the first velocity index and the number of points of its fit window ([n_spec][2]).
+soap_status ccf_prepare(soap_ctx* c, CcfState& st, const double* mask_lambda, const double* mask_weight,
+                        int n_lines, double width_kms, double v_lo, double v_step, int n_v, int n_spec,
+                        int f32, int tc, CcfPlan& p);
+soap_status ccf_enqueue(soap_ctx* c, CcfState& st, const CcfPlan& p, const void* spectra_dev, double* rv_dev,
+                        double* fit_dev, double* ccf_dev, const int* win);
+// Both steps, for the single-star calls (the context's own CCF state).
 soap_status rv_ccf_run(soap_ctx* c, const void* spectra_dev, int f32, int n_spec,
                        const double* mask_lambda, const double* mask_weight, int n_lines,
                        double width_kms, double v_lo, double v_step, int n_v, double* rv_dev,
                        double* fit_dev, double* ccf_dev, int tc = 0);
 bool ccf_tc_fits(int n_v);
 int64_t ccf_tc_chunk(int64_t n_px, int n_spec, int sms);
-soap_status ccf_tc(soap_ctx* c, int n_lines, const int* U, const float* f, const int* valid, const float* w,
-                   int n_v, const int* S, const float* g, int s_min, int s_max, double box, int64_t chunk,
-                   int n_spec, const float* spectra, float* partial);
+// Mask matrix of the tensor-core form for the tables of `st` (once per mask and grid).
+soap_status ccf_tc_build_m(soap_ctx* c, CcfState& st, const CcfPlan& p);
+soap_status ccf_tc(soap_ctx* c, const CcfState& st, const CcfPlan& p, const float* spectra, float* partial);
 
 }  // namespace soap
 

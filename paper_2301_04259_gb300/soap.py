@@ -112,9 +112,11 @@ def _load():
         "soap_active_phases": (i32, [P, ctypes.POINTER(soap_region), i32, P, i32, u32, i32, P, ctypes.c_int]),
         "soap_rv_ccf": (i32, [P, P, i32, i32, ctypes.c_int, P, P, i32, d, d, d, i32, P, P, P, ctypes.c_int]),
         "soap_get_launch_count": (i32, [P, ctypes.POINTER(ctypes.c_uint64)]),
+        "soap_debug_inject_timeout": (i32, [P]),
         "soap_rv_ccf_static": (i32, [d, d, i64, P, i32, i32, P, P, i32, d, d, d, i32, P, P, P, P]),
         "soap_active_batch": (i32, [P, ctypes.POINTER(soap_batch_item), i32, ctypes.POINTER(soap_region), i32,
-                                    P, i32, i32, P, ctypes.c_int]),
+                                    P, i32, i32, P, P, ctypes.c_int]),
+        "soap_batch_set_rv": (i32, [P, P, P, i32, d, d, d, i32, d, i32]),
         "soap_batch_num_variants": (i32, [ctypes.POINTER(i32)]),
         "soap_batch_variant_info": (i32, [i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
         "soap_batch_set_variant": (i32, [P, i32]),
@@ -430,16 +432,38 @@ def batch_items_array(items: Sequence) -> ctypes.Array:
     return arr
 
 
+def _batch_rv_ptr(out, rv_out):
+    if rv_out is None:
+        return None
+    rp, rdev = _ptr(rv_out)
+    if rdev != _ptr(out)[1]:
+        raise ValueError("out and rv_out must both be host or both device")
+    return rp
+
+
 def soap_active_batch(ctx, items: Sequence, regions: Sequence, phases, out,
-                      output: int = 0) -> None:
+                      output: int = 0, rv_out=None) -> None:
     """out: float32 [n_phases, n_px], host (numpy) or device (torch); output SOAP_BATCH_SPECTRUM
-    (F) or SOAP_BATCH_RESIDUAL (F - F_q)."""
+    (F) or SOAP_BATCH_RESIDUAL (F - F_q); rv_out: float64 [n_phases] RVs (km/s) of the spectra,
+    in the same memory space as out (needs soap_batch_set_rv)."""
     ia = batch_items_array(items)
     ra = regions_array(regions)
     ph = np.ascontiguousarray(phases, dtype=np.float64)
     ptr, dev = _ptr(out)
+    rp = _batch_rv_ptr(out, rv_out)
     _check(_lib.soap_active_batch(ctx, ia, len(items), ra, len(regions), ctypes.c_void_p(ph.ctypes.data),
-                                  ph.size, int(output), ptr, dev), "soap_active_batch")
+                                  ph.size, int(output), ptr, rp, dev), "soap_active_batch")
+
+
+def soap_batch_set_rv(ctx, mask_lambda, mask_weight, mask_width_kms: float, v_lo: float, v_step: float,
+                      n_v: int, fit_margin_kms: float = 20.0, tensor_cores: bool = False) -> None:
+    """Mask and common velocity grid of the batched RVs; each configuration fits the grid
+    velocities with |v| <= |vsini| + fit_margin_kms (the whole grid when fit_margin_kms <= 0)."""
+    ml = np.ascontiguousarray(mask_lambda, dtype=np.float64)
+    mw = np.ascontiguousarray(mask_weight, dtype=np.float64)
+    _check(_lib.soap_batch_set_rv(ctx, ctypes.c_void_p(ml.ctypes.data), ctypes.c_void_p(mw.ctypes.data), ml.size,
+                                  float(mask_width_kms), float(v_lo), float(v_step), int(n_v),
+                                  float(fit_margin_kms), int(bool(tensor_cores))), "soap_batch_set_rv")
 
 
 ITEM_DTYPE = np.dtype([("vsini_kms", "<f8"), ("incl_deg", "<f8"), ("first_region", "<i4"),
@@ -462,16 +486,17 @@ def batch_columns_arrays(cols):
     return it, rg, np.ascontiguousarray(cols["phases"], np.float64)
 
 
-def soap_active_batch_arrays(ctx, items, regions, phases, out, output: int = 0) -> None:
+def soap_active_batch_arrays(ctx, items, regions, phases, out, output: int = 0, rv_out=None) -> None:
     """soap_active_batch with items / regions given as ITEM_DTYPE / REGION_DTYPE arrays."""
     items = np.ascontiguousarray(items, ITEM_DTYPE)
     regions = np.ascontiguousarray(regions, REGION_DTYPE)
     ph = np.ascontiguousarray(phases, np.float64)
     ptr, dev = _ptr(out)
+    rvp = _batch_rv_ptr(out, rv_out)
     ip = ctypes.cast(ctypes.c_void_p(items.ctypes.data), ctypes.POINTER(soap_batch_item))
     rp = ctypes.cast(ctypes.c_void_p(regions.ctypes.data), ctypes.POINTER(soap_region))
     _check(_lib.soap_active_batch(ctx, ip, len(items), rp, len(regions), ctypes.c_void_p(ph.ctypes.data),
-                                  ph.size, int(output), ptr, dev), "soap_active_batch")
+                                  ph.size, int(output), ptr, rvp, dev), "soap_active_batch")
 
 
 def soap_batch_num_variants() -> int:
@@ -535,6 +560,12 @@ def soap_get_launch_count(ctx) -> int:
     n = ctypes.c_uint64()
     _check(_lib.soap_get_launch_count(ctx, ctypes.byref(n)), "soap_get_launch_count")
     return int(n.value)
+
+
+def soap_debug_inject_timeout(ctx) -> None:
+    """Mark the context's device status word as a timed-out tensor-core wait would (for testing
+    error reporting)."""
+    _check(_lib.soap_debug_inject_timeout(ctx), "soap_debug_inject_timeout")
 
 
 def soap_free(ctx) -> None:

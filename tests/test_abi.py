@@ -79,7 +79,9 @@ def test_null_arguments_are_rejected(lib):
 
 
 def test_batch_entry_points_without_a_gpu(lib):
-    assert lib._lib.soap_active_batch(None, None, 0, None, 0, None, 0, 0, None, 0) == lib.SOAP_EINVAL
+    assert lib._lib.soap_active_batch(None, None, 0, None, 0, None, 0, 0, None, None, 0) == lib.SOAP_EINVAL
+    assert lib._lib.soap_batch_set_rv(None, None, None, 0, 0.82, -30.0, 0.25, 241, 20.0, 0) == lib.SOAP_EINVAL
+    assert lib._lib.soap_debug_inject_timeout(None) == lib.SOAP_EINVAL
     n = lib.soap_batch_num_variants()
     assert n >= 2
     seen = set()

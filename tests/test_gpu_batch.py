@@ -92,6 +92,80 @@ def test_batch_matches_oracle_per_configuration(S, small):
         assert err <= TOL32, (cfg, err)
 
 
+def _oracle_batch_rvs(case, cfg, F, lo, step, nv, margin=20.0):
+    """RVs of oracle spectra F [n, n_px] the way the batched form defines them: the CCF on the
+    common velocity grid (line validity from that grid, Sect. 4.1), the least-squares Gaussian
+    fitted at the grid velocities with |v| <= |vsini| + margin."""
+    C = O.ccf(F, case.star, case.mask_lambda, case.mask_weight, case.mask_width_kms, lo, step, nv)
+    v = lo + step * np.arange(nv)
+    H = abs(cfg.vsini_kms) + margin
+    k0 = max(0, int(np.ceil((-H - lo) / step - 1e-9)))
+    k1 = min(nv - 1, int(np.floor((H - lo) / step + 1e-9)))
+    return np.array([O.fit_gaussian(v[k0:k1 + 1], row[k0:k1 + 1])[2] for row in C])
+
+
+@pytest.mark.parametrize("tensor_cores", [False, True])
+def test_batch_rvs_match_oracle_per_configuration(S, small, tensor_cores):
+    """soap_active_batch with rv_kms: each phase's RV (CCF on the common grid -30..30 km/s, fit in
+    its configuration's window |v| <= |vsini| + 20 km/s) against the oracle's spectra, CCF and
+    fit within the mixed path's 1 cm/s; the spectra are unchanged by asking for RVs."""
+    cfgs, items, regions, phases = _small_batch()
+    lo, step, nv = synth.velocity_grid(10.0)
+    with _disk(S, small) as d:
+        S.soap_batch_set_rv(d.ctx, small.mask_lambda, small.mask_weight, small.mask_width_kms, lo, step, nv,
+                            fit_margin_kms=20.0, tensor_cores=tensor_cores)
+        out = torch.empty((phases.size, small.star.n_px), dtype=torch.float32, device=DEV)
+        rv = torch.full((phases.size,), float("nan"), dtype=torch.float64, device=DEV)
+        S.soap_active_batch(d.ctx, items, regions, phases, out, rv_out=rv)
+        plain = torch.empty_like(out)
+        S.soap_active_batch(d.ctx, items, regions, phases, plain)
+        S.soap_synchronize(d.ctx)
+        g = rv.cpu().numpy()
+    assert torch.equal(out, plain)
+    assert np.isfinite(g).all()
+    for cfg, it in zip(cfgs, items):
+        fp, n = it[4], it[5]
+        ref = _oracle_batch_rvs(small, cfg, _oracle_rows(small, cfg, phases[fp:fp + n]), lo, step, nv)
+        err_cms = np.abs(g[fp:fp + n] - ref).max() * 1e5
+        assert err_cms <= 1.0, (cfg, err_cms)
+
+
+def test_batch_rvs_host_output_whole_grid_and_errors(S, small):
+    """Host outputs equal device outputs; fit_margin_kms <= 0 fits the whole grid (against the
+    oracle); RVs need soap_batch_set_rv and the spectrum output."""
+    cfgs, items, regions, phases = _small_batch()
+    lo, step, nv = synth.velocity_grid(10.0)
+    n_px = small.star.n_px
+    with _disk(S, small) as d:
+        out = torch.empty((phases.size, n_px), dtype=torch.float32, device=DEV)
+        rv = torch.empty(phases.size, dtype=torch.float64, device=DEV)
+        with pytest.raises(S.SoapError) as e:
+            S.soap_active_batch(d.ctx, items, regions, phases, out, rv_out=rv)
+        assert e.value.status == S.SOAP_ESTATE
+        S.soap_batch_set_rv(d.ctx, small.mask_lambda, small.mask_weight, small.mask_width_kms, lo, step, nv,
+                            fit_margin_kms=0.0)
+        with pytest.raises(S.SoapError) as e:
+            S.soap_active_batch(d.ctx, items, regions, phases, out, output=S.SOAP_BATCH_RESIDUAL, rv_out=rv)
+        assert e.value.status == S.SOAP_EINVAL
+        S.soap_active_batch(d.ctx, items, regions, phases, out, rv_out=rv)
+        host = np.empty((phases.size, n_px), dtype=np.float32)
+        rvh = np.empty(phases.size)
+        S.soap_active_batch(d.ctx, items, regions, phases, host, rv_out=rvh)
+        S.soap_synchronize(d.ctx)
+        g = rv.cpu().numpy()
+        S.soap_batch_set_rv(d.ctx, small.mask_lambda, small.mask_weight, small.mask_width_kms, lo, step, nv,
+                            fit_margin_kms=0.1)                  # vsini 0 item: 0.1 km/s holds < 5 points
+        with pytest.raises(S.SoapError) as e:
+            S.soap_active_batch(d.ctx, items, regions, phases, out, rv_out=rv)
+        assert e.value.status == S.SOAP_EINVAL
+    assert np.array_equal(out.cpu().numpy(), host) and np.array_equal(g, rvh)
+    for cfg, it in list(zip(cfgs, items))[1:4]:
+        fp, n = it[4], it[5]
+        ref = _oracle_batch_rvs(small, cfg, _oracle_rows(small, cfg, phases[fp:fp + n]), lo, step, nv,
+                                margin=1e9)
+        assert np.abs(g[fp:fp + n] - ref).max() * 1e5 <= 1.0, cfg
+
+
 def test_batch_variants_agree_bitwise(S, small):
     """Phases per block only widens tap ranges with exact zeros and pixels per thread does not
     touch the arithmetic: every variant gives the same bits."""
@@ -186,11 +260,17 @@ def test_batch_fullsize_sampled_pixels(S):
     cfgs = synth.batch_configs(1, 4096)
     items, regions, phases = synth.batch_layout(cfgs)
     n_px = case.star.n_px
+    lo, step, nv = synth.velocity_grid(10.0)
     with _disk(S, case) as d:
+        S.soap_batch_set_rv(d.ctx, case.mask_lambda, case.mask_weight, case.mask_width_kms, lo, step, nv,
+                            fit_margin_kms=20.0)
         out = torch.empty((phases.size, n_px), dtype=torch.float32, device=DEV)
-        S.soap_active_batch(d.ctx, items, regions, phases, out)
+        rv = torch.empty(phases.size, dtype=torch.float64, device=DEV)
+        S.soap_active_batch(d.ctx, items, regions, phases, out, rv_out=rv)
         S.soap_synchronize(d.ctx)
         assert bool(torch.isfinite(out).all())
+        rvg = rv.cpu().numpy()
+        assert np.isfinite(rvg).all()
         rng = np.random.default_rng(7)
         pick = sorted(set(rng.integers(0, len(cfgs), 6).tolist()) | {0, len(cfgs) - 1})
         pix = np.unique(np.concatenate([[0, 1, n_px - 2, n_px - 1], rng.integers(0, n_px, 24)]))
@@ -205,6 +285,11 @@ def test_batch_fullsize_sampled_pixels(S):
             g = out[fp + torch.from_numpy(ph).to(DEV)][:, torch.from_numpy(pix).to(DEV)].double().cpu().numpy()
             err = np.abs(g - ref).max() / scale
             assert err <= TOL32, (k, err)
+            if k in pick[:4]:
+                # RVs of two phases of the configuration: the oracle's whole spectra, CCF and fit
+                full = O.active(star, case.quiet, case.active, cfg.regions, phases[fp + ph[:2]], effects=1)[0]
+                ref_rv = _oracle_batch_rvs(case, cfg, full, lo, step, nv)
+                assert np.abs(rvg[fp + ph[:2]] - ref_rv).max() * 1e5 <= 1.0, k
         del out
 
 

@@ -69,7 +69,7 @@ def test_ccf_tc_matches_oracle_fullsize(S, cfg2, width, step, n_spec):
     c = cfg2
     half = c.star.vsini_kms + 20.0
     nv = int(np.floor(2 * half / step + 1e-9)) + 1
-    assert nv <= 240                                   # the tensor-core form applies
+    assert nv <= 256                                   # the tensor-core form applies
     lo = -half
     F = _spectra(c, n_spec)
     ccf_o = O.ccf(F.astype(np.float64), c.star, c.mask_lambda, c.mask_weight, width, lo, step, nv)
@@ -181,3 +181,52 @@ def test_rv_ccf_rejects_unknown_spectra_type(S):
                                 ctypes.c_void_p(mw.ctypes.data), ml.size, float(c.mask_width_kms), float(lo),
                                 float(step), int(nv), ctypes.c_void_p(rv.data_ptr()), None, None, 1)
     assert st == S.SOAP_EINVAL
+
+
+def test_ccf_tc_at_its_velocity_limit(S, cfg2):
+    """256 velocities, the most the tensor-core form takes (N = 256, shared memory ~193 KiB),
+    against the oracle; the mask-matrix tiles then fill the whole N range."""
+    c = cfg2
+    nv, step = 256, 0.2
+    lo = -0.5 * step * (nv - 1)
+    F = _spectra(c, 5)
+    ccf_o = O.ccf(F.astype(np.float64), c.star, c.mask_lambda, c.mask_weight, c.mask_width_kms, lo, step, nv)
+    _, ccf_g = _tc_ccf(S, c, F, c.mask_width_kms, lo, step, nv)
+    assert np.isfinite(ccf_g).all()
+    assert np.abs(ccf_g - ccf_o).max() <= TOL_CCF * np.abs(ccf_o).max()
+
+
+def test_rv_ccf_reports_a_timed_out_wait_with_host_outputs(S):
+    """A tensor-core wait that gave up is reported by soap_rv_ccf itself when its outputs are on
+    the host (the status word is marked as the kernel would mark it; no kernel is made to wait),
+    the status is cleared by that report, and the next call succeeds."""
+    c = synth.config1(0)
+    lo, step, nv = synth.velocity_grid(c.star.vsini_kms)
+    F = _spectra(c, 3)
+    with S.Disk(c.star, _t(c.quiet)) as d:
+        rv = np.empty(3)
+        S.soap_debug_inject_timeout(d.ctx)
+        with pytest.raises(S.SoapError) as e:
+            S.soap_rv_ccf(d.ctx, F, c.mask_lambda, c.mask_weight, c.mask_width_kms, lo, step, nv, rv,
+                          tensor_cores=True)
+        assert e.value.status == S.SOAP_ETIMEOUT
+        assert "timeout 1" in str(e.value)
+        S.soap_rv_ccf(d.ctx, F, c.mask_lambda, c.mask_weight, c.mask_width_kms, lo, step, nv, rv,
+                      tensor_cores=True)
+        assert np.isfinite(rv).all()
+
+
+def test_device_outputs_report_a_timed_out_wait_at_synchronize(S):
+    """With device outputs the call returns at once and soap_synchronize reports the timeout."""
+    c = synth.config1(0)
+    lo, step, nv = synth.velocity_grid(c.star.vsini_kms)
+    F = _t(_spectra(c, 3))
+    with S.Disk(c.star, _t(c.quiet)) as d:
+        rv = torch.empty(3, dtype=torch.float64, device=DEV)
+        S.soap_debug_inject_timeout(d.ctx)
+        S.soap_rv_ccf(d.ctx, F, c.mask_lambda, c.mask_weight, c.mask_width_kms, lo, step, nv, rv,
+                      tensor_cores=True)
+        with pytest.raises(S.SoapError) as e:
+            S.soap_synchronize(d.ctx)
+        assert e.value.status == S.SOAP_ETIMEOUT
+        S.soap_synchronize(d.ctx)
