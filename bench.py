@@ -221,6 +221,7 @@ def run_ours(args):
     value = world * P / (ms_step * 1e-3)
     value64 = world * P / (ms64 * 1e-3)
     rv_err = float((rv32 - rv64).abs().max().item() * 1e5)          # cm/s
+    rv_vs_oracle = oracle_rv_errors(case, args, rv32, rv64)
 
     # end to end through the C-ABI with host buffers (pinned), copies inside the timed region:
     # every step uploads the local spectra, computes the phases' spectra and RVs and brings both
@@ -343,10 +344,11 @@ def run_ours(args):
            "data": "synthetic (seeded 20k-line spectra, random-init regions)",
            "config": {"workload": case.name, "grid": st.grid_n, "n_px": n_px, "n_mu": n_mu,
                       "phases_per_step": P, "effects": "total (Eq. 3)",
-                      "precision": "FP32 local spectra, contraction and CCF; FP64 positions and weights; fit FP32 LM + FP64 Newton",
+                      "precision": "FP32 local spectra, contraction, CCF and fit; FP64 positions and weights",
                       "l2": "flushed between timed steps (256 MB write)",
                       "parallelism": f"replicas{world}"},
            "rv_err_cms_vs_fp64": rv_err,
+           "rv_err_cms_vs_oracle": rv_vs_oracle,
            "fp64_path": {"value": round(value64, 2), "unit": UNIT, "ms_per_step": round(ms64, 5),
                          "kernel_ms_per_step": {k: round(v[0] / K64, 5)
                                                 for k, v in timers64.items() if v[1]}},
@@ -366,6 +368,22 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as tdist
         tdist.destroy_process_group()
+
+
+def oracle_rv_errors(case, args, rv32, rv64):
+    """Max |RV - RV_oracle| (cm/s) of the FP32 and FP64 paths over the 100 phases, against the FP64
+    oracle's RVs of its own full-size spectra (tests/golden/cfg2_fullsize_oracle.json, written by
+    tests/golden/make_cfg2_fullsize.py for seed 0); None for any other workload."""
+    path = os.path.join(ROOT, "tests", "golden", "cfg2_fullsize_oracle.json")
+    if (args.seed, case.star.grid_n, case.star.n_px) != (0, 300, 205800) or not os.path.exists(path):
+        return None
+    g = json.load(open(path))
+    ref = np.asarray(g["rv_kms"])
+    if ref.size != rv32.numel():
+        return None
+    return {"fp32": round(float(np.abs(rv32.cpu().numpy() - ref).max() * 1e5), 6),
+            "fp64": float(np.abs(rv64.cpu().numpy() - ref).max() * 1e5),
+            "oracle": "FP64 oracle, all 205,800 px x 100 phases (tests/golden/cfg2_fullsize_oracle.json)"}
 
 
 def profiled_traffic(name):

@@ -220,7 +220,8 @@ static void free_ctx_memory(soap_ctx* c) {
         if (p) cudaFree(p);
     DevBuf* bufs[] = {&c->stage_in, &c->fq, &c->contrast, &c->kphase, &c->jobs, &c->coefs, &c->job_counters,
                       &c->regions, &c->region_geo, &c->phases, &c->out_stage, &c->partial, &c->ccf.tmp,
-                      &c->ccf.tab, &c->lsf_taps, &c->lsf_tmp, &c->bis_tab, &c->tc_coef, &c->ccf.m};
+                      &c->ccf.tab, &c->lsf_taps, &c->lsf_tmp, &c->bis_tab, &c->tc_coef, &c->ccf.m,
+                      &c->tm_planes, &c->tm_coef};
     for (DevBuf* b : bufs) release(*b);
     release_host(c->host_stage);
     ring_release(c);
@@ -258,6 +259,7 @@ static soap_status upload_spectra(soap_ctx* c, const void* src, int on_device, i
     }
     if (f32src) SOAP_TRY(pad_rows32(c, static_cast<const float*>(dsrc), dst32, c->n_mu));
     else SOAP_TRY(pad_rows(c, static_cast<const double*>(dsrc), dst64, dst32, c->n_mu));
+    c->rows_version++;                      // derived copies of the rows (BF16 planes) are stale
     if (!on_device && c->host_async) SOAP_CUDA(cudaEventRecord(c->up_free[slot], c->stream));
     return SOAP_OK;
 }

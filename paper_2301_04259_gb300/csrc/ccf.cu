@@ -802,6 +802,222 @@ __global__ void __launch_bounds__(kFitThreads) k_gauss_fit(int n_spec, int n_v_g
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// Gaussian fit of CCFs from float32 spectra: one warp per spectrum, FP32 throughout.
+// ---------------------------------------------------------------------------------------
+// Such a CCF carries FP32 rounding (~1e-7 relative) already, so the fit needs no FP64: the
+// FP32 residuals r = a + b e - y (|r| error ~1e-7 of the continuum) move the least-squares centre
+// by ~1e-8 of the width, far below the mixed path's 1 cm/s.  The start, the scaled variables and
+// the two phases are those of k_gauss_fit; the second phase is Newton on the exact Hessian in
+// FP32.  A warp's sums are xor butterflies (addition commutes, so every lane holds the same
+// bits and runs the same iteration); there is no shared memory and no block barrier, so a block
+// of 4 warps fits 4 spectra independently.  Points k = lane + 32 i, i < kFwCache, stay in
+// registers; further points (more than 256 velocities) are kept as floats in the scratch row.
+constexpr int kFwCache = 8;
+constexpr int kFwWarps = 4;
+constexpr int kFwPassesA = 80;          // FP32 Levenberg-Marquardt passes at most
+constexpr int kFwPassesB = 8;           // Newton passes at most
+constexpr float kFwTolA = 1e-4f;        // scaled step at which Levenberg-Marquardt hands over
+constexpr float kFwTolB = 2e-6f;        // scaled Newton step at FP32's resolution of the minimum
+
+template <int NF>
+__device__ __forceinline__ void warp_allsum(float (&f)[NF]) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int q = 0; q < NF; q++) f[q] += __shfl_xor_sync(0xffffffffu, f[q], o);
+}
+
+// One pass at scaled parameters p of a + b exp(-(u - m)^2 / (2 w^2)): J^T J (10, upper
+// triangle by rows), J^T r (4), r^2 (1) and, with HESS, R_j = sum r g d^j, j = 0..4 (g the
+// Gaussian, d = u - m) for the second-derivative part of the Hessian.  u_k = (k - kmin) du.
+template <bool HESS>
+__device__ __forceinline__ void fw_pass(const float p[4], int n_v, int lane, int kmin, float du,
+                                        const float (&yc)[kFwCache], const float* __restrict__ ys,
+                                        float (&acc)[HESS ? 20 : 15]) {
+    constexpr int NF = HESS ? 20 : 15;
+#pragma unroll
+    for (int q = 0; q < NF; q++) acc[q] = 0.0f;
+    const float iw = 1.0f / p[3];
+    const float iw2 = iw * iw;
+    auto point = [&](int k, float yk) {
+        const float d = (float)(k - kmin) * du - p[2];
+        const float e = expf(-0.5f * d * d * iw2);
+        const float r = fmaf(p[1], e, p[0]) - yk;
+        const float t = p[1] * e * d * iw2;
+        const float J[4] = {1.0f, e, t, t * d * iw};
+        int q = 0;
+#pragma unroll
+        for (int a = 0; a < 4; a++)
+#pragma unroll
+            for (int b = a; b < 4; b++) { acc[q] = fmaf(J[a], J[b], acc[q]); q++; }
+#pragma unroll
+        for (int a = 0; a < 4; a++) acc[10 + a] = fmaf(J[a], r, acc[10 + a]);
+        acc[14] = fmaf(r, r, acc[14]);
+        if constexpr (HESS) {
+            float w = r * e;
+#pragma unroll
+            for (int j = 0; j < 5; j++) { acc[15 + j] += w; w *= d; }
+        }
+    };
+#pragma unroll
+    for (int i = 0; i < kFwCache; i++)
+        if (lane + 32 * i < n_v) point(lane + 32 * i, yc[i]);
+    for (int k = lane + 32 * kFwCache; k < n_v; k += 32) point(k, ys[k]);
+    warp_allsum<NF>(acc);
+}
+
+__global__ void __launch_bounds__(32 * kFwWarps) k_gauss_fit_f32(int n_spec, int n_v_grid, double v_lo_grid,
+                                                                  double v_step,
+                                                                  const double* __restrict__ ccf,
+                                                                  float* scratch, double* rv, double* fit,
+                                                                  const int* __restrict__ win) {
+    const int spec = blockIdx.x * kFwWarps + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (spec >= n_spec) return;                           // the whole warp leaves together
+    int k0 = 0, n_v = n_v_grid;
+    if (win) {
+        k0 = win[2 * spec];
+        n_v = win[2 * spec + 1];
+    }
+    const double v_lo = win ? fma((double)k0, v_step, v_lo_grid) : v_lo_grid;
+    const double* c = ccf + (int64_t)spec * n_v_grid + k0;
+    float* ys = scratch + (int64_t)spec * n_v_grid + k0;
+    // the CCF in FP32; its largest value, and its smallest with the first index reaching it
+    float yc[kFwCache];
+    float mx = -INFINITY, mn = INFINITY;
+    int kmin = n_v;
+#pragma unroll
+    for (int i = 0; i < kFwCache; i++) {
+        const int k = lane + 32 * i;
+        yc[i] = k < n_v ? (float)c[k] : 0.0f;
+        if (k < n_v) {
+            mx = fmaxf(mx, yc[i]);
+            if (yc[i] < mn) { mn = yc[i]; kmin = k; }
+        }
+    }
+    for (int k = lane + 32 * kFwCache; k < n_v; k += 32) {
+        const float v = (float)c[k];
+        ys[k] = v;
+        mx = fmaxf(mx, v);
+        if (v < mn) { mn = v; kmin = k; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        const float mo = __shfl_xor_sync(0xffffffffu, mn, o);
+        const int ko = __shfl_xor_sync(0xffffffffu, kmin, o);
+        if (mo < mn || (mo == mn && ko < kmin)) { mn = mo; kmin = ko; }
+    }
+    // scaled CCF y = CCF / |max|; start a = max, b = min - max, m = 0 at the minimum, w = 1 in units
+    // of the starting width s0 = dip area / (|b| sqrt(2 pi)), at least one velocity step
+    const float scale = mx != 0.0f ? fabsf(mx) : 1.0f;
+    const float iscale = 1.0f / scale;
+    float area[1] = {0.0f};
+#pragma unroll
+    for (int i = 0; i < kFwCache; i++) {
+        yc[i] *= iscale;
+        if (lane + 32 * i < n_v) area[0] += mx * iscale - yc[i];
+    }
+    for (int k = lane + 32 * kFwCache; k < n_v; k += 32) {
+        const float v = ys[k] * iscale;
+        ys[k] = v;
+        area[0] += mx * iscale - v;
+    }
+    warp_allsum<1>(area);
+    const float b0 = (mn - mx) * iscale;
+    const double s0 = fmax(b0 != 0.0f ? (double)area[0] * v_step / ((double)fabsf(b0) * 2.5066282746310002) : v_step,
+                           v_step);
+    const double c0 = fma((double)kmin, v_step, v_lo);
+    const float du = (float)(v_step / s0);
+
+    // ---- phase 1: Levenberg-Marquardt ----
+    float p[4] = {mx * iscale, b0, 0.0f, 1.0f};
+    float pt[4] = {p[0], p[1], p[2], p[3]};
+    float acc[15], jtj[10], jtr[4], cost = 0.0f, lam = 1e-3f;
+    bool tiny = false;
+    fw_pass<false>(p, n_v, lane, kmin, du, yc, ys, acc);
+    for (int it = 0; it < kFwPassesA; it++) {
+        bool stop = false;
+        if (it == 0 || acc[14] <= cost) {            // keep the trial point
+            for (int a = 0; a < 4; a++) p[a] = pt[a];
+            for (int q = 0; q < 10; q++) jtj[q] = acc[q];
+            for (int a = 0; a < 4; a++) jtr[a] = acc[10 + a];
+            cost = acc[14];
+            if (it > 0) lam = fmaxf(lam * 0.1f, 1e-9f);
+            if (tiny) stop = true;
+        } else {
+            if (tiny) stop = true;
+            lam *= 10.0f;
+        }
+        while (!stop) {
+            if (lam > 1e8f) { stop = true; break; }
+            float M[4][4], b[4], dx[4];
+            for (int a = 0; a < 4; a++)
+                for (int bb = a; bb < 4; bb++) M[a][bb] = M[bb][a] = jtj[tri(a, bb)];
+            for (int a = 0; a < 4; a++) { M[a][a] *= 1.0f + lam; b[a] = -jtr[a]; }
+            if (!solve4f(M, b, dx)) { lam *= 10.0f; continue; }
+            tiny = fabsf(dx[2]) <= kFwTolA && fabsf(dx[3]) <= kFwTolA &&
+                   fabsf(dx[0]) <= kFwTolA * fabsf(p[0]) && fabsf(dx[1]) <= kFwTolA * fabsf(p[1]);
+            for (int a = 0; a < 4; a++) pt[a] = p[a] + dx[a];
+            break;
+        }
+        if (stop) break;
+        fw_pass<false>(pt, n_v, lane, kmin, du, yc, ys, acc);
+    }
+
+    // ---- phase 2: Newton on H = J^T J + sum r d2m ----
+    float prev[4] = {p[0], p[1], p[2], p[3]};
+    float cost_prev = INFINITY, last = INFINITY;
+    for (int it = 0; it < kFwPassesB; it++) {
+        float f[20];
+        fw_pass<true>(p, n_v, lane, kmin, du, yc, ys, f);
+        if (!(f[14] <= cost_prev * (1.0f + 1e-5f))) {   // the last step did not help: undo it
+            for (int a = 0; a < 4; a++) p[a] = prev[a];
+            break;
+        }
+        const float b = p[1], w = p[3];
+        const float iw = 1.0f / w, iw2 = iw * iw;
+        const float R0 = f[15], R1 = f[16], R2 = f[17], R3 = f[18], R4 = f[19];
+        float M[4][4], rhs[4], dx[4];
+        for (int a = 0; a < 4; a++)
+            for (int bb = a; bb < 4; bb++) M[a][bb] = M[bb][a] = f[tri(a, bb)];
+        M[1][2] += R1 * iw2;
+        M[1][3] += R2 * iw2 * iw;
+        M[2][2] += b * iw2 * (R2 * iw2 - R0);
+        M[2][3] += b * iw2 * iw * (R3 * iw2 - 2.0f * R1);
+        M[3][3] += b * iw2 * iw2 * (R4 * iw2 - 3.0f * R2);
+        M[2][1] = M[1][2];
+        M[3][1] = M[1][3];
+        M[3][2] = M[2][3];
+        for (int a = 0; a < 4; a++) rhs[a] = -f[10 + a];
+        if (!solve4f(M, rhs, dx)) break;
+        if (!(dx[0] * rhs[0] + dx[1] * rhs[1] + dx[2] * rhs[2] + dx[3] * rhs[3] > 0.0f)) break;
+        const float ref = fabsf(p[0]), wref = fabsf(w);
+        const float size = fmaxf(fmaxf(fabsf(dx[0]) / ref, fabsf(dx[1]) / ref),
+                                 fmaxf(fabsf(dx[2]) / wref, fabsf(dx[3]) / wref));
+        if (!(size < last)) break;
+        for (int a = 0; a < 4; a++) { prev[a] = p[a]; p[a] += dx[a]; }
+        cost_prev = f[14];
+        last = size;
+        if (size <= kFwTolB) break;
+    }
+
+    if (lane == 0) {
+        // a fit that leaves the velocity grid (no dip to fit) is reported as NaN
+        const double v_hi = fma((double)(n_v - 1), v_step, v_lo);
+        double mu = fma((double)p[2], s0, c0);
+        if (!(mu >= v_lo && mu <= v_hi) || !(fabs((double)p[3]) * s0 <= v_hi - v_lo)) mu = NAN;
+        rv[spec] = mu;
+        if (fit) {
+            fit[(int64_t)spec * 4 + 0] = (double)p[0] * scale;
+            fit[(int64_t)spec * 4 + 1] = (double)p[1] * scale;
+            fit[(int64_t)spec * 4 + 2] = mu;
+            fit[(int64_t)spec * 4 + 3] = fabs((double)p[3]) * s0;
+        }
+    }
+}
+
 bool ccf_mask_same(const CcfState& st, const double* mask_lambda, const double* mask_weight,
                    int n_lines, double width_kms) {
     const std::vector<double>& k = st.mask_key;
@@ -1021,10 +1237,16 @@ soap_status ccf_enqueue(soap_ctx* c, CcfState& st, const CcfPlan& p, const void*
                                                                                   d_part, d_ccf);
     SOAP_LAUNCHED(c);
     if (tb) timer_end(c, SOAP_TIMER_CCF_AUX, tb);
-    SOAP_TIMED(c, SOAP_TIMER_FIT,
-               k_gauss_fit<<<n_spec, kFitThreads, 0, c->stream>>>(n_spec, n_v, p.v_lo, p.v_step, d_ccf, p.y,
-                                                                  rv_dev, fit_dev, win);
-               SOAP_LAUNCHED(c));
+    if (p.f32)      // float32 spectra: FP32 fit, one warp per spectrum
+        SOAP_TIMED(c, SOAP_TIMER_FIT,
+                   k_gauss_fit_f32<<<(n_spec + kFwWarps - 1) / kFwWarps, 32 * kFwWarps, 0, c->stream>>>(
+                       n_spec, n_v, p.v_lo, p.v_step, d_ccf, reinterpret_cast<float*>(p.y), rv_dev, fit_dev, win);
+                   SOAP_LAUNCHED(c));
+    else            // float64 spectra: FP64 residuals, the least-squares minimum to FP64 rounding
+        SOAP_TIMED(c, SOAP_TIMER_FIT,
+                   k_gauss_fit<<<n_spec, kFitThreads, 0, c->stream>>>(n_spec, n_v, p.v_lo, p.v_step, d_ccf, p.y,
+                                                                      rv_dev, fit_dev, win);
+                   SOAP_LAUNCHED(c));
     return SOAP_OK;
 }
 
@@ -1174,8 +1396,12 @@ extern "C" soap_status soap_rv_ccf_static(double lambda_start_A, double lambda_e
     int64_t tot = (int64_t)n_spec * n_v * kReduceSplit;
     k_ccf_reduce<double><<<(unsigned)((tot + 255) / 256), 256, 0, stream>>>(n_chunks, n_spec, n_v, d_part, d_ccf);
     SOAP_CUDA(cudaGetLastError());
-    k_gauss_fit<<<n_spec, kFitThreads, 0, stream>>>(n_spec, n_v, v_lo, v_step, d_ccf, d_y, rv_kms, fit_params,
-                                                    nullptr);
+    if (spectra_f32)
+        k_gauss_fit_f32<<<(n_spec + kFwWarps - 1) / kFwWarps, 32 * kFwWarps, 0, stream>>>(
+            n_spec, n_v, v_lo, v_step, d_ccf, reinterpret_cast<float*>(d_y), rv_kms, fit_params, nullptr);
+    else
+        k_gauss_fit<<<n_spec, kFitThreads, 0, stream>>>(n_spec, n_v, v_lo, v_step, d_ccf, d_y, rv_kms, fit_params,
+                                                        nullptr);
     SOAP_CUDA(cudaGetLastError());
     return SOAP_OK;
 }

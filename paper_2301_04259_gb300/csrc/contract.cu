@@ -393,8 +393,13 @@ soap_status toeplitz_active(soap_ctx* c, const RegionDev* regions_host, int n_re
     const double* a64f = c->active_set[1] ? c->a64[1] : c->a64[0];
     const float* a32s = c->active_set[0] ? c->a32[0] : c->a32[1];
     const float* a32f = c->active_set[1] ? c->a32[1] : c->a32[0];
-    if (precision == SOAP_BF16X3)
+    if (precision == SOAP_BF16X3) {
+        // operand windows by TMA and one accumulator per class; a contrast row per mu bin (facula
+        // limb brightening) or a shape beyond that form's limits takes the operand-building kernel
+        if (!per_bin && toeplitz_tma_fits(c, ncl))
+            return toeplitz_tma(c, kfix, n_phases, ncl, class_type, a32s, a32f, con32, el.e, n_eff, (float*)dst);
         return toeplitz_tc(c, kfix, n_phases, ncl, class_type, a32s, a32f, con32, per_bin, el.e, n_eff, (float*)dst);
+    }
     if (f64)
         return launch_contract<double, kPB64, kR64, kT64>(c, nbk, G, mt, toff, gstart, c64, ct, con64,
                                                          c->fq.as<double>(), n_phases, el, n_eff,

@@ -224,6 +224,11 @@ struct soap_ctx {
     soap::DevBuf lsf_taps, lsf_tmp;
     soap::DevBuf bis_tab;       // bisector tables of the last injection
     soap::DevBuf tc_coef;       // tensor-core contraction: kernel rows (BF16 hi / lo) + block flags
+    // tensor-core contraction with TMA-loaded windows (toeplitz_tma.cu): the FP32 rows as BF16 hi / lo
+    // planes of 8 mu bins per pixel, rebuilt when the rows change (rows_version counts uploads)
+    soap::DevBuf tm_planes, tm_coef;
+    uint64_t rows_version = 0, tm_planes_version = ~0ull;
+    const float* tm_planes_src[3] = {nullptr, nullptr, nullptr};
 
     // CCF of the single-star calls (soap_rv_ccf, soap_active_rv)
     soap::CcfState ccf;
@@ -332,6 +337,13 @@ struct RegionDev {      // one region as the kernels see it
 soap_status toeplitz_tc(soap_ctx* c, const long long* kfix, int n_phases, int ncl, const int* class_type,
                         const float* a_spot, const float* a_fac, const float* con32, bool per_bin,
                         const int* effects, int n_eff, float* out);
+// The same contraction with the Toeplitz operand taken from TMA-loaded windows of BF16 planes and
+// one accumulator per class (contrast applied at readout); SOAP_ERANGE when a limit of that form is
+// exceeded (the caller then uses toeplitz_tc).
+soap_status toeplitz_tma(soap_ctx* c, const long long* kfix, int n_phases, int ncl, const int* class_type,
+                         const float* a_spot, const float* a_fac, const float* con32, const int* effects, int n_eff,
+                         float* out);
+bool toeplitz_tma_fits(const soap_ctx* c, int ncl);
 soap_status toeplitz_active(soap_ctx* c, const RegionDev* regions_host, int n_regions,
                             const double* class_temp, const int* class_type, int n_class,
                             const double* phases_host, int n_phases, uint32_t effects,

@@ -41,6 +41,30 @@ static soap_status make_map(CUtensorMap* map, const void* base, int64_t rows, in
     return SOAP_OK;
 }
 
+soap_status encode_map(CUtensorMap* map, int rank, const void* base, const uint64_t* dims,
+                       const uint64_t* strides, const uint32_t* box) {
+    auto fn = encode_fn();
+    if (!fn) { set_error("cuTensorMapEncodeTiled is not available from the driver"); return SOAP_ECUDA; }
+    if (rank < 1 || rank > 5 || (reinterpret_cast<uintptr_t>(base) & 15)) {
+        set_error("tensor map: rank 1..5 and a 16-byte aligned base needed");
+        return SOAP_EINVAL;
+    }
+    cuuint64_t d[5];
+    cuuint64_t st[4];
+    cuuint32_t bx[5], estr[5];
+    for (int i = 0; i < rank; i++) {
+        d[i] = (cuuint64_t)dims[i];
+        bx[i] = (cuuint32_t)box[i];
+        estr[i] = 1;
+        if (i + 1 < rank) st[i] = (cuuint64_t)strides[i];
+    }
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank, const_cast<void*>(base), d, st, bx, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) { set_error("cuTensorMapEncodeTiled failed (%d)", (int)r); return SOAP_ECUDA; }
+    return SOAP_OK;
+}
+
 template <int BN>
 static soap_status launch(const CUtensorMap& ma, const CUtensorMap& mb, int M, int N, int K, const Epilogue& ep,
                           cudaStream_t st, unsigned int* flags) {

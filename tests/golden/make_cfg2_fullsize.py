@@ -11,11 +11,20 @@ It stores
 Only the oracle computes anything here (the synthetic inputs come from synth.py, which holds
 none of the method's arithmetic).  It takes about 12 minutes on 8 cores:
 
-    python tests/golden/make_cfg2_fullsize.py
+    python tests/golden/make_cfg2_fullsize.py [--out PATH]
+
+The synthetic spectra depend on the platform's float64 exp at the 1e-12 level: numpy's
+vectorised exp rounds differently on x86-64 (AVX-512) and aarch64, and on a 6000 A grid a
+one-ulp change of a wavelength moves a line-flank value by ~1e-11 relative (the wavelength is
+~4e4 times the distance to the line centre in units of its own rounding).  The oracle's answer
+inherits that, so the stored values are written on the platform the GPU tests run on (aarch64)
+and the file records the platform.
 """
 from __future__ import annotations
 
+import argparse
 import json
+import platform
 import sys
 import time
 from pathlib import Path
@@ -35,6 +44,9 @@ SAMPLE_SEED = 20230110
 
 
 def main() -> None:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--out", default=str(OUT))
+    out = Path(ap.parse_args().out)
     O.build()
     t0 = time.time()
     case = synth.config2(SEED)
@@ -70,9 +82,10 @@ def main() -> None:
         "max_F_quiet_sampled": float(Fq.max()),
         "oracle_seconds": {"spectra": round(t1 - t0, 1), "rv": round(t2 - t1, 1)},
         "oracle_threads": O.num_threads(),
+        "platform": {"machine": platform.machine(), "numpy": np.__version__},
     }
-    OUT.write_text(json.dumps(doc, indent=1) + "\n")
-    print(f"wrote {OUT} ({t1 - t0:.0f} s spectra, {t2 - t1:.0f} s RVs)")
+    out.write_text(json.dumps(doc, indent=1) + "\n")
+    print(f"wrote {out} ({t1 - t0:.0f} s spectra, {t2 - t1:.0f} s RVs)")
 
 
 if __name__ == "__main__":

@@ -1,10 +1,10 @@
 """Active-phase contraction on the tensor cores (SOAP_BF16X3: Eqs. 1-4 as a GEMM over pixels x
 phases x (class, mu bin, tap), BF16 hi/lo operands, three products, FP32 accumulation) against
 the FP64 oracle at the mixed path's tolerances: 2e-6 of max F_quiet, 1 cm/s RV.  Cases: config 1
-(all effects), four region classes with differential rotation and wide kernels (K blocks that
-cross class and bin boundaries), per-bin facula contrast, the full-size configuration (two
-phase tiles, sampled pixels), no regions (every kernel block skipped), RVs through
-soap_active_rv, and the precision refused where it does not apply."""
+(all effects), four region classes with differential rotation and wide kernels, eight classes
+over 70 phases (five phase groups), per-bin facula contrast (the operand-building kernel), the
+full-size configuration (two phase groups, sampled pixels), no regions (every coefficient tile
+skipped), RVs through soap_active_rv, and the precision refused where it does not apply."""
 import numpy as np
 import pytest
 
@@ -126,6 +126,20 @@ def test_bf16x3_rv_matches_oracle(S):
                          c.mask_weight, c.mask_width_kms, lo, step, nv, spec, rv)
         torch.cuda.synchronize()
     assert np.abs(rv.cpu().numpy() - rv_ref).max() * 1e5 <= 1.0
+
+
+def test_bf16x3_eight_classes_many_phases(S):
+    """Eight region classes (every accumulator the tensor memory holds: groups of 16 phases) over 70
+    phases (five phase groups, the last ragged), all three effects, against the oracle."""
+    c = synth.config1(2)
+    regs = [Region(SPOT if k % 2 else FACULA, -40.0 + 11.0 * k, 45.0 * k, 0.08 + 0.02 * k, 4300.0 + 250.0 * k)
+            for k in range(8)]
+    phases = np.linspace(0.0, 1.0, 70, endpoint=False)
+    q = O.quiet(c.star, c.quiet)
+    ref = O.active(c.star, c.quiet, c.active, regs, phases, effects=7)
+    got = _active(S, c, regs, phases, 7)
+    assert np.isfinite(got).all()
+    assert _rel(got, ref, q.max()) <= TOL
 
 
 def test_bf16x3_only_for_active_phases(S):
