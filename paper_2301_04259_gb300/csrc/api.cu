@@ -221,7 +221,7 @@ static void free_ctx_memory(soap_ctx* c) {
     DevBuf* bufs[] = {&c->stage_in, &c->fq, &c->contrast, &c->kphase, &c->jobs, &c->coefs, &c->job_counters,
                       &c->regions, &c->region_geo, &c->phases, &c->out_stage, &c->partial, &c->ccf.tmp,
                       &c->ccf.tab, &c->lsf_taps, &c->lsf_tmp, &c->bis_tab, &c->tc_coef, &c->ccf.m,
-                      &c->tm_planes, &c->tm_coef};
+                      &c->tm_planes, &c->tm_coef, &c->dir_cells, &c->dir_count, &c->dir_rows};
     for (DevBuf* b : bufs) release(*b);
     release_host(c->host_stage);
     ring_release(c);
@@ -416,7 +416,9 @@ soap_status soap_init_star(const soap_star_desc* s, const double* quiet_local, i
     c->tap_min = (int)tmin;
     c->n_taps = (int)(tmax - tmin + 1);
     int64_t need = std::max<int64_t>(tmax, -tmin) + 1;
-    c->pad = round_up(need, 32);
+    // 32 more than the taps need: the direct form reads 16-byte vectors up to 20 values past a
+    // pixel and rounds its start down to a vector boundary
+    c->pad = round_up(need + 32, 32);
     // rows reach past the last tile of any contraction (tiles of up to 1024 pixels)
     c->row_len = round_up(round_up(c->n_px, 1024) + 2 * c->pad, 32);
 

@@ -305,6 +305,7 @@ soap_status geometry_init(soap_ctx* c) {
         SOAP_CUDA(cudaEventRecord(c->ev_geo, c->stream));
     }
     c->geo_pending = true;
+    c->geo_version++;
     return SOAP_OK;
 }
 

@@ -213,6 +213,12 @@ struct soap_ctx {
     soap::DevBuf radii;         // per-(phase, region) radii of evolving regions
     soap::DevBuf out_stage;     // device output when the caller wants host output
     soap::DevBuf partial;       // direct-form partial sums
+    // direct form: visible cells compacted once per geometry (direct.cu); geo_version counts
+    // geometry computations
+    soap::DevBuf dir_cells, dir_count, dir_rows;
+    uint64_t geo_version = 0, dir_version = ~0ull, dir_rows_version = ~0ull;
+    int dir_prec = -1;
+    const void* dir_rows_src = nullptr;          // the rows dir_rows was shifted from
     soap::HostBuf host_stage;
     soap::PinnedRing ring;      // small uploads (see PinnedRing)
 
