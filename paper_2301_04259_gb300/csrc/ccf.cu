@@ -260,12 +260,15 @@ constexpr int kTileRed = kTileVT * kTileSB + 1;                 // lane-sum row 
 constexpr int kTileMaxGroups = kTileWin * kTileRow / kTileRed;  // lane sums reuse the window
 static_assert(kTileLP == 2, "the lane sums below add exactly two lanes");
 
-template <int NP>
+template <int NP, int SB, bool SKIP0>
 __global__ void __launch_bounds__(256)
 k_ccf_tile(int n_lines, int lines_per_block, const int* __restrict__ U, const float* __restrict__ f,
            const int* __restrict__ valid, const float* __restrict__ wl_, int n_v,
            const int* __restrict__ S, const float* __restrict__ g, float box, int64_t n_px,
-           int n_spec, const float* __restrict__ spectra, float* __restrict__ partial) {
+           int n_spec, int s_base, const float* __restrict__ spectra, float* __restrict__ partial) {
+    static_assert(SB % 4 == 0 && SB <= kTileSB, "SB: a multiple of 4, at most kTileSB");
+    constexpr int ROW = SB + 4;                            // padded row (floats)
+    constexpr int RED = kTileVT * SB + 1;                  // lane-sum row (floats, padded)
     __shared__ __align__(16) float win[kTileWin * kTileRow];
     __shared__ int sB[kTileCL];
     __shared__ float sF[kTileCL];
@@ -275,8 +278,8 @@ k_ccf_tile(int n_lines, int lines_per_block, const int* __restrict__ U, const fl
     const int gi = threadIdx.x - lane * NG;
     const bool active = lane < kTileLP;
     const int k0 = gi * kTileVT;
-    const int s0 = blockIdx.y * kTileSB;
-    const int ns = min(kTileSB, n_spec - s0);
+    const int s0 = s_base + blockIdx.y * SB;
+    const int ns = min(SB, n_spec - s0);
     const int L0 = blockIdx.x * lines_per_block;
     const int L1 = min(n_lines, L0 + lines_per_block);
     int S0 = 0;
@@ -295,11 +298,11 @@ k_ccf_tile(int n_lines, int lines_per_block, const int* __restrict__ U, const fl
     }
     const int Smin = S[0], sweep = S[n_v - 1] - Smin;
     const int budget = kTileWin - sweep - NP - 5;           // >= 0 (checked by the host)
-    float acc[kTileVT][kTileSB];
+    float acc[kTileVT][SB];
 #pragma unroll
     for (int kk = 0; kk < kTileVT; kk++)
 #pragma unroll
-        for (int s = 0; s < kTileSB; s++) acc[kk][s] = 0.0f;
+        for (int s = 0; s < SB; s++) acc[kk][s] = 0.0f;
     const float* base = spectra + (int64_t)s0 * n_px;
     for (int j0 = L0; j0 < L1;) {
         // lines j0 .. j1-1 whose boxes fit one window
@@ -323,15 +326,15 @@ k_ccf_tile(int n_lines, int lines_per_block, const int* __restrict__ U, const fl
             const int64_t pix = n_lo + x;
             const bool on = pix >= 0 && pix < n_px;
             const float* col = base + pix;                  // spectrum s at col + s n_px (added, not multiplied)
-            float v[kTileSB];
+            float v[SB];
 #pragma unroll
-            for (int s = 0; s < kTileSB; s++) {
+            for (int s = 0; s < SB; s++) {
                 v[s] = (on && s < ns) ? __ldg(col) : 0.0f;
                 col += n_px;
             }
-            float4* dst = reinterpret_cast<float4*>(win + x * kTileRow);
+            float4* dst = reinterpret_cast<float4*>(win + x * ROW);
 #pragma unroll
-            for (int q = 0; q < kTileSB / 4; q++)
+            for (int q = 0; q < SB / 4; q++)
                 dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
         }
         __syncthreads();
@@ -350,21 +353,27 @@ k_ccf_tile(int n_lines, int lines_per_block, const int* __restrict__ U, const fl
                     const float e = a + box;
 #pragma unroll
                     for (int jj = 0; jj < NP; jj++)
-                        ov[kk][jj] = wl * fmaxf(fminf(e, (float)(jj + 1)) - fmaxf(a, (float)jj), 0.0f);
+                        ov[kk][jj] = (SKIP0 && kk == 0 && jj >= 2)
+                                         ? 0.0f
+                                         : wl * fmaxf(fminf(e, (float)(jj + 1)) - fmaxf(a, (float)jj), 0.0f);
                 }
 #pragma unroll
                 for (int jj = 0; jj < NP; jj++) {
-                    const float4* src = reinterpret_cast<const float4*>(win + (n0 + jj) * kTileRow);
-                    float t[kTileSB];
+                    const float4* src = reinterpret_cast<const float4*>(win + (n0 + jj) * ROW);
+                    float t[SB];
 #pragma unroll
-                    for (int q = 0; q < kTileSB / 4; q++) {
+                    for (int q = 0; q < SB / 4; q++) {
                         const float4 x = src[q];
                         t[4 * q] = x.x; t[4 * q + 1] = x.y; t[4 * q + 2] = x.z; t[4 * q + 3] = x.w;
                     }
 #pragma unroll
-                    for (int kk = 0; kk < kTileVT; kk++)
+                    for (int kk = 0; kk < kTileVT; kk++) {
+                        // the first velocity's box starts in pixel n0: one no wider than a pixel
+                        // ends before pixel n0 + 2
+                        if (SKIP0 && kk == 0 && jj >= 2) continue;
 #pragma unroll
-                        for (int s = 0; s < kTileSB; s++) acc[kk][s] = fmaf(ov[kk][jj], t[s], acc[kk][s]);
+                        for (int s = 0; s < SB; s++) acc[kk][s] = fmaf(ov[kk][jj], t[s], acc[kk][s]);
+                    }
                 }
             }
         }
@@ -376,7 +385,7 @@ k_ccf_tile(int n_lines, int lines_per_block, const int* __restrict__ U, const fl
 #pragma unroll
         for (int kk = 0; kk < kTileVT; kk++)
 #pragma unroll
-            for (int s = 0; s < kTileSB; s++) win[gi * kTileRed + kk * kTileSB + s] = acc[kk][s];
+            for (int s = 0; s < SB; s++) win[gi * RED + kk * SB + s] = acc[kk][s];
     __syncthreads();
     if (active && lane == 0) {
 #pragma unroll
@@ -384,10 +393,10 @@ k_ccf_tile(int n_lines, int lines_per_block, const int* __restrict__ U, const fl
             const int k = k0 + kk;
             if (k >= n_v) break;
 #pragma unroll
-            for (int s = 0; s < kTileSB; s++)
+            for (int s = 0; s < SB; s++)
                 if (s < ns)
                     partial[((int64_t)blockIdx.x * n_spec + s0 + s) * n_v + k] =
-                        acc[kk][s] + win[gi * kTileRed + kk * kTileSB + s];
+                        acc[kk][s] + win[gi * RED + kk * SB + s];
         }
     }
 }
@@ -1080,7 +1089,8 @@ soap_status ccf_prepare(soap_ctx* c, CcfState& st, const double* mask_lambda, co
             const int tthreads = (groups * kTileLP + 31) / 32 * 32;
             int per_sm = 0;
             SOAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &per_sm, p.tile_np == 2 ? k_ccf_tile<2> : p.tile_np == 3 ? k_ccf_tile<3> : k_ccf_tile<4>,
+                &per_sm, p.tile_np == 2 ? k_ccf_tile<2, kTileSB, false>
+                         : p.tile_np == 3 ? k_ccf_tile<3, kTileSB, false> : k_ccf_tile<4, kTileSB, false>,
                 tthreads, 0));
             const int ys = (n_spec + kTileSB - 1) / kTileSB;
             const int wave = std::max(1, sms * std::max(per_sm, 1));
@@ -1177,16 +1187,23 @@ soap_status ccf_enqueue(soap_ctx* c, CcfState& st, const CcfPlan& p, const void*
         SOAP_TRY(ccf_tc(c, st, p, (const float*)spectra_dev, reinterpret_cast<float*>(d_part)));
     } else if (p.tile_np) {
         const int tthreads = ((n_v + kTileVT - 1) / kTileVT * kTileLP + 31) / 32 * 32;
-        dim3 grid((unsigned)p.tile_blocks, (unsigned)((n_spec + kTileSB - 1) / kTileSB));
         const float box = (float)(2.0 * p.h);
-#define SOAP_TILE_LAUNCH(NP)                                                                       \
-        k_ccf_tile<NP><<<grid, tthreads, 0, c->stream>>>(n_lines, p.tile_lines, p.U, p.f32t, p.valid, \
-                                                         p.w32, n_v, p.S, p.g32, box, c->n_px,     \
-                                                         n_spec, (const float*)spectra_dev,        \
-                                                         reinterpret_cast<float*>(d_part))
-        if (p.tile_np == 2) SOAP_TILE_LAUNCH(2);
-        else if (p.tile_np == 3) SOAP_TILE_LAUNCH(3);
-        else SOAP_TILE_LAUNCH(4);
+        const bool skip0 = 2.0 * p.h <= 1.0;             // boxes no wider than a pixel
+        const int n16 = (n_spec + kTileSB - 1) / kTileSB;   // blocks of 16 spectra (the last ragged)
+#define SOAP_TILE_LAUNCH(NP, SB, SK, NB, SBASE)                                                    \
+        k_ccf_tile<NP, SB, SK><<<dim3((unsigned)p.tile_blocks, (unsigned)(NB)), tthreads, 0, c->stream>>>( \
+            n_lines, p.tile_lines, p.U, p.f32t, p.valid, p.w32, n_v, p.S, p.g32, box, c->n_px, n_spec,   \
+            SBASE, (const float*)spectra_dev, reinterpret_cast<float*>(d_part))
+#define SOAP_TILE_NP(SB, NB, SBASE)                                                                \
+        do {                                                                                       \
+            if (p.tile_np == 2) SOAP_TILE_LAUNCH(2, SB, false, NB, SBASE);                         \
+            else if (p.tile_np == 3 && skip0) SOAP_TILE_LAUNCH(3, SB, true, NB, SBASE);            \
+            else if (p.tile_np == 3) SOAP_TILE_LAUNCH(3, SB, false, NB, SBASE);                    \
+            else if (skip0) SOAP_TILE_LAUNCH(4, SB, true, NB, SBASE);                              \
+            else SOAP_TILE_LAUNCH(4, SB, false, NB, SBASE);                                        \
+        } while (0)
+        SOAP_TILE_NP(kTileSB, n16, 0);
+#undef SOAP_TILE_NP
 #undef SOAP_TILE_LAUNCH
     } else if (p.windowed) {
         const int threads = ((n_v + 31) / 32) * 32;
