@@ -1,10 +1,11 @@
 """What the trained surrogate gains over the plain method, checked by the plain method.
 
-A surrogate trained on residual spectra of the batched method answers part of the held-out
-queries; for those its RV must agree with the plain method's within 10 cm/s (up to the 1%
-calibration miss rate plus sampling slack).  Its gain is measured on the compressed answer (128
-PCA coefficients per query) against the plain method's spectra projected onto the same basis,
-and reported for full spectra against the plain method alone."""
+A surrogate trained on residual spectra of the batched method answers the queries it accepts;
+for those its RV must agree with the plain method's within 10 cm/s for all but at most 1% of them
+(the calibrated acceptance, checked here on held-out queries).  Its gain is measured on the
+answer that keeps that guarantee: 128 PCA coefficients per query from the network where it is
+accepted and from the plain method's spectra projected onto the basis elsewhere, against the
+plain method for every query.  Full residual spectra through the same hybrid are reported."""
 import time
 
 import numpy as np
@@ -31,7 +32,7 @@ def test_surrogate_gain_over_the_plain_method(S):
     case = synth.batch_spectra(0)
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
     with S.Disk(case.star, t(case.quiet), {k: t(v) for k, v in case.active.items()}) as d:
-        model = SP.train(d.ctx, case, n_train=300_000, epochs=100, n_err=98_304, err_epochs=60, seed=3)
+        model = SP.train(d.ctx, case, n_train=600_000, epochs=100, n_err=98_304, err_epochs=60, seed=3)
         try:
             xe = synth.surrogate_params(1234, 8192)
             err = SP.plain_rv_errors(d.ctx, case, model, xe)
@@ -39,12 +40,12 @@ def test_surrogate_gain_over_the_plain_method(S):
             S.soap_surrogate_predict(model.handle, t(xe), model.accept_thr_cms, accepted=acc)
             a = acc.cpu().numpy().astype(bool)
             assert a.mean() >= 0.05, a.mean()
-            assert (err[a] > SP.RV_ERR_MAX_CMS).mean() <= 0.03
+            assert (err[a] > SP.RV_ERR_MAX_CMS).mean() <= 0.01, (err[a] > SP.RV_ERR_MAX_CMS).mean()
             # 65536 queries, answered as 128 PCA coefficients of the residual spectrum: by the
-            # plain method (residual spectra, then the projection onto the basis) and by the
-            # network; and as full residual spectra, by the plain method alone and by the hybrid
-            # (surrogate where accepted).  Full spectra cost both sides the same output writes, so
-            # only the first comparison is asserted; the second is reported.
+            # plain method (residual spectra, then the projection onto the basis), by the network
+            # alone, and by the hybrid (network where accepted, plain method elsewhere); and as
+            # full residual spectra, by the plain method and by the hybrid.  Full spectra cost both
+            # sides the same output writes, so that gain is reported, not asserted.
             xq = synth.surrogate_params(4321, 65536)
             n_px = case.star.n_px
             spec = torch.empty((len(xq), n_px), dtype=torch.float32, device=DEV)
@@ -64,9 +65,15 @@ def test_surrogate_gain_over_the_plain_method(S):
             def hybrid_spec():
                 SP.query(d.ctx, model, xq)
 
+            hcoef = torch.empty_like(coef)
+
+            def hybrid_coef():
+                SP.query_coefficients(d.ctx, model, xq, hcoef)
+
             times = {}
             for name, fn in (("plain_coef", plain_coef), ("surrogate_coef", surrogate_coef),
-                             ("plain_spec", plain_spec), ("hybrid_spec", hybrid_spec)):
+                             ("hybrid_coef", hybrid_coef), ("plain_spec", plain_spec),
+                             ("hybrid_spec", hybrid_spec)):
                 fn()
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
@@ -75,12 +82,21 @@ def test_surrogate_gain_over_the_plain_method(S):
                 torch.cuda.synchronize()
                 times[name] = (time.perf_counter() - t0) / 3
             gain_coef = times["plain_coef"] / times["surrogate_coef"]
+            gain_hybrid = times["plain_coef"] / times["hybrid_coef"]
             gain_spec = times["plain_spec"] / times["hybrid_spec"]
+            # the hybrid's rows for rejected queries are the plain method's
+            plain_coef()
+            rej = torch.from_numpy(np.flatnonzero(~SP.query_coefficients(d.ctx, model, xq, hcoef))).to(DEV)
+            torch.cuda.synchronize()
+            hr, pr = hcoef.index_select(0, rej), coef.index_select(0, rej)
+            assert (hr - pr).abs().max().item() <= 1e-5 * pr.abs().max().item()
             print(f"accepted {a.mean():.3f}, accepted RV err p99 {np.percentile(err[a], 99):.2f} cm/s, "
                   f"coefficients: plain {times['plain_coef'] * 1e3:.2f} ms vs network "
-                  f"{times['surrogate_coef'] * 1e3:.2f} ms ({gain_coef:.1f}x); spectra: plain "
+                  f"{times['surrogate_coef'] * 1e3:.2f} ms ({gain_coef:.1f}x), hybrid "
+                  f"{times['hybrid_coef'] * 1e3:.2f} ms ({gain_hybrid:.2f}x); spectra: plain "
                   f"{times['plain_spec'] * 1e3:.2f} ms vs hybrid {times['hybrid_spec'] * 1e3:.2f} ms "
                   f"({gain_spec:.2f}x)")
             assert gain_coef > 5.0
+            assert gain_hybrid > 1.0, gain_hybrid
         finally:
             model.free()
