@@ -246,10 +246,30 @@ k_ccf_window(int n_lines, const int* __restrict__ U, const T* __restrict__ f,
 // pixels n0 .. n0 + NP - 1.  Each of those pixels is read once from the staged window (all
 // kTileSB spectra: four 16-byte loads) and applied to every velocity of the group with its
 // overlap (zero where a box misses the pixel): NP x VT x SB FMAs per line for 4 x NP loads,
-// against 2 x SB FMAs for 2 x 4 loads per velocity when a thread owns one velocity.  The line
+// against 2 x SB FMAs for 2 x 4 loads per velocity when a thread owns one velocity (the FMAs of
+// spectrum pairs as two-wide fma.rn.f32x2).  The line
 // lanes take alternate lines of each window; their sums are added in lane order at the end.
 // Lines are staged kTileCL at a time in windows of at most kTileWin pixels (a window closes
 // early where the lines spread out), so every line is handled in shared memory.
+// Two-wide FP32 arithmetic on 64-bit register pairs (sm_100 and later): fma.rn.f32x2 performs two
+// independent IEEE single-precision FMAs, so results equal those of two fmaf calls.
+__device__ __forceinline__ unsigned long long f32x2_dup(float x) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ unsigned long long f32x2_pack(float lo, float hi) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f32x2_unpack(unsigned long long v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ void f32x2_fma(unsigned long long& d, unsigned long long a, unsigned long long b) {
+    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(d) : "l"(a), "l"(b));
+}
+
 constexpr int kTileVT = 4;
 constexpr int kTileSB = 16;
 constexpr int kTileLP = 2;
@@ -298,11 +318,13 @@ k_ccf_tile(int n_lines, int lines_per_block, const int* __restrict__ U, const fl
     }
     const int Smin = S[0], sweep = S[n_v - 1] - Smin;
     const int budget = kTileWin - sweep - NP - 5;           // >= 0 (checked by the host)
-    float acc[kTileVT][SB];
+    // accumulators of spectrum pairs (2i, 2i+1) share a 64-bit register: one two-wide FMA
+    // (fma.rn.f32x2, two independent IEEE FMAs) per pair
+    unsigned long long acc[kTileVT][SB / 2];
 #pragma unroll
     for (int kk = 0; kk < kTileVT; kk++)
 #pragma unroll
-        for (int s = 0; s < SB; s++) acc[kk][s] = 0.0f;
+        for (int s = 0; s < SB / 2; s++) acc[kk][s] = 0ull;
     const float* base = spectra + (int64_t)s0 * n_px;
     for (int j0 = L0; j0 < L1;) {
         // lines j0 .. j1-1 whose boxes fit one window
@@ -346,25 +368,30 @@ k_ccf_tile(int n_lines, int lines_per_block, const int* __restrict__ U, const fl
                 const bool carry = fl + g0 >= 1.0f;
                 const float cf = carry ? 1.0f : 0.0f;
                 const int n0 = sB[j] + S0 + (carry ? 1 : 0);
-                float ov[kTileVT][NP];
+                // overlap of box [a, e) with pixel n0 + jj: sat(e - jj) - sat(a - jj) (sat: clamp
+                // to [0, 1]; x - jj is exact for the small box coordinates here), times w_l
+                unsigned long long ov[kTileVT][NP];
 #pragma unroll
                 for (int kk = 0; kk < kTileVT; kk++) {
                     const float a = (fl + rel[kk]) - cf;     // box start from pixel n0
                     const float e = a + box;
 #pragma unroll
-                    for (int jj = 0; jj < NP; jj++)
-                        ov[kk][jj] = (SKIP0 && kk == 0 && jj >= 2)
-                                         ? 0.0f
-                                         : wl * fmaxf(fminf(e, (float)(jj + 1)) - fmaxf(a, (float)jj), 0.0f);
+                    for (int jj = 0; jj < NP; jj++) {
+                        const float o = (SKIP0 && kk == 0 && jj >= 2)
+                                            ? 0.0f
+                                            : wl * (__saturatef(e - (float)jj) - __saturatef(a - (float)jj));
+                        ov[kk][jj] = f32x2_dup(o);
+                    }
                 }
 #pragma unroll
                 for (int jj = 0; jj < NP; jj++) {
                     const float4* src = reinterpret_cast<const float4*>(win + (n0 + jj) * ROW);
-                    float t[SB];
+                    unsigned long long t[SB / 2];
 #pragma unroll
                     for (int q = 0; q < SB / 4; q++) {
                         const float4 x = src[q];
-                        t[4 * q] = x.x; t[4 * q + 1] = x.y; t[4 * q + 2] = x.z; t[4 * q + 3] = x.w;
+                        t[2 * q] = f32x2_pack(x.x, x.y);
+                        t[2 * q + 1] = f32x2_pack(x.z, x.w);
                     }
 #pragma unroll
                     for (int kk = 0; kk < kTileVT; kk++) {
@@ -372,7 +399,7 @@ k_ccf_tile(int n_lines, int lines_per_block, const int* __restrict__ U, const fl
                         // ends before pixel n0 + 2
                         if (SKIP0 && kk == 0 && jj >= 2) continue;
 #pragma unroll
-                        for (int s = 0; s < SB; s++) acc[kk][s] = fmaf(ov[kk][jj], t[s], acc[kk][s]);
+                        for (int s = 0; s < SB / 2; s++) f32x2_fma(acc[kk][s], ov[kk][jj], t[s]);
                     }
                 }
             }
@@ -385,7 +412,8 @@ k_ccf_tile(int n_lines, int lines_per_block, const int* __restrict__ U, const fl
 #pragma unroll
         for (int kk = 0; kk < kTileVT; kk++)
 #pragma unroll
-            for (int s = 0; s < SB; s++) win[gi * RED + kk * SB + s] = acc[kk][s];
+            for (int s = 0; s < SB / 2; s++)
+                f32x2_unpack(acc[kk][s], win[gi * RED + kk * SB + 2 * s], win[gi * RED + kk * SB + 2 * s + 1]);
     __syncthreads();
     if (active && lane == 0) {
 #pragma unroll
@@ -393,10 +421,15 @@ k_ccf_tile(int n_lines, int lines_per_block, const int* __restrict__ U, const fl
             const int k = k0 + kk;
             if (k >= n_v) break;
 #pragma unroll
-            for (int s = 0; s < SB; s++)
-                if (s < ns)
-                    partial[((int64_t)blockIdx.x * n_spec + s0 + s) * n_v + k] =
-                        acc[kk][s] + win[gi * RED + kk * SB + s];
+            for (int s = 0; s < SB / 2; s++) {
+                float lo, hi;
+                f32x2_unpack(acc[kk][s], lo, hi);
+                if (2 * s < ns)
+                    partial[((int64_t)blockIdx.x * n_spec + s0 + 2 * s) * n_v + k] = lo + win[gi * RED + kk * SB + 2 * s];
+                if (2 * s + 1 < ns)
+                    partial[((int64_t)blockIdx.x * n_spec + s0 + 2 * s + 1) * n_v + k] =
+                        hi + win[gi * RED + kk * SB + 2 * s + 1];
+            }
         }
     }
 }
