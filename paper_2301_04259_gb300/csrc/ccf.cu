@@ -845,22 +845,28 @@ __global__ void __launch_bounds__(kFitThreads) k_gauss_fit(int n_spec, int n_v_g
 }
 
 // ---------------------------------------------------------------------------------------
-// Gaussian fit of CCFs from float32 spectra: one warp per spectrum, FP32 throughout.
+// Gaussian fit of CCFs from float32 spectra: one block of kFwSpan warps per spectrum, FP32.
 // ---------------------------------------------------------------------------------------
 // Such a CCF carries FP32 rounding (~1e-7 relative) already, so the fit needs no FP64: the
 // FP32 residuals r = a + b e - y (|r| error ~1e-7 of the continuum) move the least-squares centre
 // by ~1e-8 of the width, far below the mixed path's 1 cm/s.  The start, the scaled variables and
 // the two phases are those of k_gauss_fit; the second phase is Newton on the exact Hessian in
-// FP32.  A warp's sums are xor butterflies (addition commutes, so every lane holds the same
-// bits and runs the same iteration); there is no shared memory and no block barrier, so a block
-// of 4 warps fits 4 spectra independently.  Points k = lane + 32 i, i < kFwCache, stay in
-// registers; further points (more than 256 velocities) are kept as floats in the scratch row.
-constexpr int kFwCache = 8;
-constexpr int kFwWarps = 4;
+// FP32.  Thread t of the block takes the points k = t + 32 kFwSpan i; a pass's sums are warp xor
+// butterflies, then the warps' sums are added in warp order through shared memory, so every
+// thread holds the same bits and runs the same iteration (the block's barriers are reached by
+// all of its threads).  Points with i < kFwCache stay in registers; further ones (more than 256
+// velocities) are kept as floats in the scratch row.
+#ifndef SOAP_FIT_SPAN
+#define SOAP_FIT_SPAN 4
+#endif
+constexpr int kFwSpan = SOAP_FIT_SPAN;   // warps per spectrum
+constexpr int kFwThreads = 32 * kFwSpan;
+constexpr int kFwCache = (256 + kFwThreads - 1) / kFwThreads;
 constexpr int kFwPassesA = 80;          // FP32 Levenberg-Marquardt passes at most
 constexpr int kFwPassesB = 8;           // Newton passes at most
 constexpr float kFwTolA = 1e-4f;        // scaled step at which Levenberg-Marquardt hands over
 constexpr float kFwTolB = 2e-6f;        // scaled Newton step at FP32's resolution of the minimum
+constexpr int kFwMaxSums = 20;
 
 template <int NF>
 __device__ __forceinline__ void warp_allsum(float (&f)[NF]) {
@@ -870,13 +876,37 @@ __device__ __forceinline__ void warp_allsum(float (&f)[NF]) {
         for (int q = 0; q < NF; q++) f[q] += __shfl_xor_sync(0xffffffffu, f[q], o);
 }
 
+// Block-wide sums, identical in every thread: warp butterflies, then the kFwSpan warp sums added
+// in warp order.  buf: 2 x kFwSpan x kFwMaxSums floats, used alternately (a buffer is written
+// again only after the next call's barrier, when every thread has read it).
+template <int NF>
+__device__ __forceinline__ void block_allsum(float (&f)[NF], float* buf, int& parity) {
+    warp_allsum<NF>(f);
+    if constexpr (kFwSpan > 1) {
+        float* b = buf + parity * (kFwSpan * kFwMaxSums);
+        const int w = threadIdx.x >> 5;
+        if ((threadIdx.x & 31) == 0)
+#pragma unroll
+            for (int q = 0; q < NF; q++) b[w * kFwMaxSums + q] = f[q];
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < NF; q++) {
+            float t = b[q];
+#pragma unroll
+            for (int v = 1; v < kFwSpan; v++) t += b[v * kFwMaxSums + q];
+            f[q] = t;
+        }
+        parity ^= 1;
+    }
+}
+
 // One pass at scaled parameters p of a + b exp(-(u - m)^2 / (2 w^2)): J^T J (10, upper
 // triangle by rows), J^T r (4), r^2 (1) and, with HESS, R_j = sum r g d^j, j = 0..4 (g the
 // Gaussian, d = u - m) for the second-derivative part of the Hessian.  u_k = (k - kmin) du.
 template <bool HESS>
-__device__ __forceinline__ void fw_pass(const float p[4], int n_v, int lane, int kmin, float du,
+__device__ __forceinline__ void fw_pass(const float p[4], int n_v, int kmin, float du,
                                         const float (&yc)[kFwCache], const float* __restrict__ ys,
-                                        float (&acc)[HESS ? 20 : 15]) {
+                                        float (&acc)[HESS ? 20 : 15], float* buf, int& parity) {
     constexpr int NF = HESS ? 20 : 15;
 #pragma unroll
     for (int q = 0; q < NF; q++) acc[q] = 0.0f;
@@ -902,21 +932,25 @@ __device__ __forceinline__ void fw_pass(const float p[4], int n_v, int lane, int
             for (int j = 0; j < 5; j++) { acc[15 + j] += w; w *= d; }
         }
     };
+    const int t = threadIdx.x;
 #pragma unroll
     for (int i = 0; i < kFwCache; i++)
-        if (lane + 32 * i < n_v) point(lane + 32 * i, yc[i]);
-    for (int k = lane + 32 * kFwCache; k < n_v; k += 32) point(k, ys[k]);
-    warp_allsum<NF>(acc);
+        if (t + kFwThreads * i < n_v) point(t + kFwThreads * i, yc[i]);
+    for (int k = t + kFwThreads * kFwCache; k < n_v; k += kFwThreads) point(k, ys[k]);
+    block_allsum<NF>(acc, buf, parity);
 }
 
-__global__ void __launch_bounds__(32 * kFwWarps) k_gauss_fit_f32(int n_spec, int n_v_grid, double v_lo_grid,
-                                                                  double v_step,
-                                                                  const double* __restrict__ ccf,
-                                                                  float* scratch, double* rv, double* fit,
-                                                                  const int* __restrict__ win) {
-    const int spec = blockIdx.x * kFwWarps + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (spec >= n_spec) return;                           // the whole warp leaves together
+__global__ void __launch_bounds__(kFwThreads) k_gauss_fit_f32(int n_spec, int n_v_grid, double v_lo_grid,
+                                                               double v_step, const double* __restrict__ ccf,
+                                                               float* scratch, double* rv, double* fit,
+                                                               const int* __restrict__ win) {
+    __shared__ float buf[2 * kFwSpan * kFwMaxSums];
+    __shared__ float sx[3 * kFwSpan];
+    __shared__ int sk[kFwSpan];
+    int parity = 0;
+    const int spec = blockIdx.x;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    if (spec >= n_spec) return;                           // the whole block leaves together
     int k0 = 0, n_v = n_v_grid;
     if (win) {
         k0 = win[2 * spec];
@@ -931,14 +965,14 @@ __global__ void __launch_bounds__(32 * kFwWarps) k_gauss_fit_f32(int n_spec, int
     int kmin = n_v;
 #pragma unroll
     for (int i = 0; i < kFwCache; i++) {
-        const int k = lane + 32 * i;
+        const int k = t + kFwThreads * i;
         yc[i] = k < n_v ? (float)c[k] : 0.0f;
         if (k < n_v) {
             mx = fmaxf(mx, yc[i]);
             if (yc[i] < mn) { mn = yc[i]; kmin = k; }
         }
     }
-    for (int k = lane + 32 * kFwCache; k < n_v; k += 32) {
+    for (int k = t + kFwThreads * kFwCache; k < n_v; k += kFwThreads) {
         const float v = (float)c[k];
         ys[k] = v;
         mx = fmaxf(mx, v);
@@ -951,6 +985,18 @@ __global__ void __launch_bounds__(32 * kFwWarps) k_gauss_fit_f32(int n_spec, int
         const int ko = __shfl_xor_sync(0xffffffffu, kmin, o);
         if (mo < mn || (mo == mn && ko < kmin)) { mn = mo; kmin = ko; }
     }
+    if constexpr (kFwSpan > 1) {
+        if (lane == 0) { sx[w] = mx; sx[kFwSpan + w] = mn; sk[w] = kmin; }
+        __syncthreads();
+        mx = sx[0]; mn = sx[kFwSpan]; kmin = sk[0];
+#pragma unroll
+        for (int v = 1; v < kFwSpan; v++) {
+            mx = fmaxf(mx, sx[v]);
+            const float mo = sx[kFwSpan + v];
+            const int ko = sk[v];
+            if (mo < mn || (mo == mn && ko < kmin)) { mn = mo; kmin = ko; }
+        }
+    }
     // scaled CCF y = CCF / |max|; start a = max, b = min - max, m = 0 at the minimum, w = 1 in units
     // of the starting width s0 = dip area / (|b| sqrt(2 pi)), at least one velocity step
     const float scale = mx != 0.0f ? fabsf(mx) : 1.0f;
@@ -959,14 +1005,17 @@ __global__ void __launch_bounds__(32 * kFwWarps) k_gauss_fit_f32(int n_spec, int
 #pragma unroll
     for (int i = 0; i < kFwCache; i++) {
         yc[i] *= iscale;
-        if (lane + 32 * i < n_v) area[0] += mx * iscale - yc[i];
+        if (t + kFwThreads * i < n_v) area[0] += mx * iscale - yc[i];
     }
-    for (int k = lane + 32 * kFwCache; k < n_v; k += 32) {
-        const float v = ys[k] * iscale;
-        ys[k] = v;
-        area[0] += mx * iscale - v;
+    if (n_v > kFwThreads * kFwCache) {
+        __syncthreads();                                  // the scratch row written above is complete
+        for (int k = t + kFwThreads * kFwCache; k < n_v; k += kFwThreads) {
+            const float v = ys[k] * iscale;
+            ys[k] = v;
+            area[0] += mx * iscale - v;
+        }
     }
-    warp_allsum<1>(area);
+    block_allsum<1>(area, buf, parity);
     const float b0 = (mn - mx) * iscale;
     const double s0 = fmax(b0 != 0.0f ? (double)area[0] * v_step / ((double)fabsf(b0) * 2.5066282746310002) : v_step,
                            v_step);
@@ -978,7 +1027,7 @@ __global__ void __launch_bounds__(32 * kFwWarps) k_gauss_fit_f32(int n_spec, int
     float pt[4] = {p[0], p[1], p[2], p[3]};
     float acc[15], jtj[10], jtr[4], cost = 0.0f, lam = 1e-3f;
     bool tiny = false;
-    fw_pass<false>(p, n_v, lane, kmin, du, yc, ys, acc);
+    fw_pass<false>(p, n_v, kmin, du, yc, ys, acc, buf, parity);
     for (int it = 0; it < kFwPassesA; it++) {
         bool stop = false;
         if (it == 0 || acc[14] <= cost) {            // keep the trial point
@@ -1005,7 +1054,7 @@ __global__ void __launch_bounds__(32 * kFwWarps) k_gauss_fit_f32(int n_spec, int
             break;
         }
         if (stop) break;
-        fw_pass<false>(pt, n_v, lane, kmin, du, yc, ys, acc);
+        fw_pass<false>(pt, n_v, kmin, du, yc, ys, acc, buf, parity);
     }
 
     // ---- phase 2: Newton on H = J^T J + sum r d2m ----
@@ -1013,7 +1062,7 @@ __global__ void __launch_bounds__(32 * kFwWarps) k_gauss_fit_f32(int n_spec, int
     float cost_prev = INFINITY, last = INFINITY;
     for (int it = 0; it < kFwPassesB; it++) {
         float f[20];
-        fw_pass<true>(p, n_v, lane, kmin, du, yc, ys, f);
+        fw_pass<true>(p, n_v, kmin, du, yc, ys, f, buf, parity);
         if (!(f[14] <= cost_prev * (1.0f + 1e-5f))) {   // the last step did not help: undo it
             for (int a = 0; a < 4; a++) p[a] = prev[a];
             break;
@@ -1045,7 +1094,7 @@ __global__ void __launch_bounds__(32 * kFwWarps) k_gauss_fit_f32(int n_spec, int
         if (size <= kFwTolB) break;
     }
 
-    if (lane == 0) {
+    if (t == 0) {
         // a fit that leaves the velocity grid (no dip to fit) is reported as NaN
         const double v_hi = fma((double)(n_v - 1), v_step, v_lo);
         double mu = fma((double)p[2], s0, c0);
@@ -1289,7 +1338,7 @@ soap_status ccf_enqueue(soap_ctx* c, CcfState& st, const CcfPlan& p, const void*
     if (tb) timer_end(c, SOAP_TIMER_CCF_AUX, tb);
     if (p.f32)      // float32 spectra: FP32 fit, one warp per spectrum
         SOAP_TIMED(c, SOAP_TIMER_FIT,
-                   k_gauss_fit_f32<<<(n_spec + kFwWarps - 1) / kFwWarps, 32 * kFwWarps, 0, c->stream>>>(
+                   k_gauss_fit_f32<<<n_spec, kFwThreads, 0, c->stream>>>(
                        n_spec, n_v, p.v_lo, p.v_step, d_ccf, reinterpret_cast<float*>(p.y), rv_dev, fit_dev, win);
                    SOAP_LAUNCHED(c));
     else            // float64 spectra: FP64 residuals, the least-squares minimum to FP64 rounding
@@ -1447,7 +1496,7 @@ extern "C" soap_status soap_rv_ccf_static(double lambda_start_A, double lambda_e
     k_ccf_reduce<double><<<(unsigned)((tot + 255) / 256), 256, 0, stream>>>(n_chunks, n_spec, n_v, d_part, d_ccf);
     SOAP_CUDA(cudaGetLastError());
     if (spectra_f32)
-        k_gauss_fit_f32<<<(n_spec + kFwWarps - 1) / kFwWarps, 32 * kFwWarps, 0, stream>>>(
+        k_gauss_fit_f32<<<n_spec, kFwThreads, 0, stream>>>(
             n_spec, n_v, v_lo, v_step, d_ccf, reinterpret_cast<float*>(d_y), rv_kms, fit_params, nullptr);
     else
         k_gauss_fit<<<n_spec, kFitThreads, 0, stream>>>(n_spec, n_v, v_lo, v_step, d_ccf, d_y, rv_kms, fit_params,
