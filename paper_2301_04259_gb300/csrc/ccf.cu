@@ -275,7 +275,7 @@ constexpr int kTileSB = 16;
 constexpr int kTileLP = 2;
 constexpr int kTileCL = 16;
 constexpr int kTileWin = 320;
-constexpr int kTileRow = kTileSB + 4;                           // padded row (floats)
+constexpr int kTileRow = kTileSB + 2;                           // padded row (floats)
 constexpr int kTileRed = kTileVT * kTileSB + 1;                 // lane-sum row (floats, padded)
 constexpr int kTileMaxGroups = kTileWin * kTileRow / kTileRed;  // lane sums reuse the window
 static_assert(kTileLP == 2, "the lane sums below add exactly two lanes");
@@ -287,16 +287,21 @@ k_ccf_tile(int n_lines, int lines_per_block, const int* __restrict__ U, const fl
            const int* __restrict__ S, const float* __restrict__ g, float box, int64_t n_px,
            int n_spec, int s_base, const float* __restrict__ spectra, float* __restrict__ partial) {
     static_assert(SB % 4 == 0 && SB <= kTileSB, "SB: a multiple of 4, at most kTileSB");
-    constexpr int ROW = SB + 4;                            // padded row (floats)
+    // Row pitch SB + 2 floats, read as 8-byte pairs: for 16 spectra a row is 9 pairs, so the
+    // rows a half-warp reads (16 velocity groups, about 1.2 pixels apart) fall on distinct
+    // banks unless 16 rows apart
+    constexpr int ROW = SB + 2;
     constexpr int RED = kTileVT * SB + 1;                  // lane-sum row (floats, padded)
     __shared__ __align__(16) float win[kTileWin * kTileRow];
     __shared__ int sB[kTileCL];
     __shared__ float sF[kTileCL];
     __shared__ float sW[kTileCL];
+    // velocity groups padded to a multiple of 16, so no half-warp mixes the two line lanes
     const int NG = (n_v + kTileVT - 1) / kTileVT;
-    const int lane = threadIdx.x / NG;
-    const int gi = threadIdx.x - lane * NG;
-    const bool active = lane < kTileLP;
+    const int NGP = (NG + 15) & ~15;
+    const int lane = threadIdx.x / NGP;
+    const int gi = threadIdx.x - lane * NGP;
+    const bool active = lane < kTileLP && gi < NG;
     const int k0 = gi * kTileVT;
     const int s0 = s_base + blockIdx.y * SB;
     const int ns = min(SB, n_spec - s0);
@@ -354,10 +359,9 @@ k_ccf_tile(int n_lines, int lines_per_block, const int* __restrict__ U, const fl
                 v[s] = (on && s < ns) ? __ldg(col) : 0.0f;
                 col += n_px;
             }
-            float4* dst = reinterpret_cast<float4*>(win + x * ROW);
+            float2* dst = reinterpret_cast<float2*>(win + x * ROW);
 #pragma unroll
-            for (int q = 0; q < SB / 4; q++)
-                dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            for (int q = 0; q < SB / 2; q++) dst[q] = make_float2(v[2 * q], v[2 * q + 1]);
         }
         __syncthreads();
         if (active) {
@@ -385,13 +389,12 @@ k_ccf_tile(int n_lines, int lines_per_block, const int* __restrict__ U, const fl
                 }
 #pragma unroll
                 for (int jj = 0; jj < NP; jj++) {
-                    const float4* src = reinterpret_cast<const float4*>(win + (n0 + jj) * ROW);
+                    const float2* src = reinterpret_cast<const float2*>(win + (n0 + jj) * ROW);
                     unsigned long long t[SB / 2];
 #pragma unroll
-                    for (int q = 0; q < SB / 4; q++) {
-                        const float4 x = src[q];
-                        t[2 * q] = f32x2_pack(x.x, x.y);
-                        t[2 * q + 1] = f32x2_pack(x.z, x.w);
+                    for (int q = 0; q < SB / 2; q++) {
+                        const float2 x = src[q];
+                        t[q] = f32x2_pack(x.x, x.y);
                     }
 #pragma unroll
                     for (int kk = 0; kk < kTileVT; kk++) {
@@ -1163,12 +1166,12 @@ soap_status ccf_prepare(soap_ctx* c, CcfState& st, const double* mask_lambda, co
         const double sweep = (std::atanh((v_lo + (n_v - 1) * v_step) / kCKms) -
                               std::atanh(v_lo / kCKms)) / c->delta + 2.0;
         const int groups = (n_v + kTileVT - 1) / kTileVT;
-        if (np <= 4 && groups <= kTileMaxGroups && groups * kTileLP <= 256 &&
+        if (np <= 4 && groups <= kTileMaxGroups && (groups + 15) / 16 * 16 * kTileLP <= 256 &&
             sweep + np + 5 + 1 <= kTileWin) {
             // one full wave: as many blocks as fit on the GPU at once, split evenly over the lines
             // (a partial second wave would double the time of its SMs)
             p.tile_np = std::max(np, 2);
-            const int tthreads = (groups * kTileLP + 31) / 32 * 32;
+            const int tthreads = ((groups + 15) / 16 * 16 * kTileLP + 31) / 32 * 32;
             int per_sm = 0;
             SOAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
                 &per_sm, p.tile_np == 2 ? k_ccf_tile<2, kTileSB, false>
@@ -1268,7 +1271,7 @@ soap_status ccf_enqueue(soap_ctx* c, CcfState& st, const CcfPlan& p, const void*
     if (p.tc_chunk) {
         SOAP_TRY(ccf_tc(c, st, p, (const float*)spectra_dev, reinterpret_cast<float*>(d_part)));
     } else if (p.tile_np) {
-        const int tthreads = ((n_v + kTileVT - 1) / kTileVT * kTileLP + 31) / 32 * 32;
+        const int tthreads = (((n_v + kTileVT - 1) / kTileVT + 15) / 16 * 16 * kTileLP + 31) / 32 * 32;
         const float box = (float)(2.0 * p.h);
         const bool skip0 = 2.0 * p.h <= 1.0;             // boxes no wider than a pixel
         const int n16 = (n_spec + kTileSB - 1) / kTileSB;   // blocks of 16 spectra (the last ragged)
