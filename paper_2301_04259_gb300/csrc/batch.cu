@@ -245,8 +245,8 @@ k_batch_contract(int64_t n_px, Rows<float> rows, const long long* __restrict__ t
         float* orow = out + (int64_t)pb.first_phase * n_px;
         const PlanckContrast32 con{aq, fd, items[pb.item].cls_type, items[pb.item].cls_a};
         for (int tile = 0; tile < n_tiles; tile++)
-            contract_tile_fold<float, PB, R, THREADS>(n_px, rows, tt, gs, G, cb, con, fqi, SOAP_EFFECT_TOT, tile,
-                                                      pb.np, orow);
+            contract_tile_fold32<PB, R, THREADS, SOAP_EFFECT_TOT>(n_px, rows, tt, gs, G, cb, con, fqi, tile, pb.np,
+                                                                  orow);
     }
 }
 

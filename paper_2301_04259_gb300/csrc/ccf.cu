@@ -848,23 +848,28 @@ __global__ void __launch_bounds__(kFitThreads) k_gauss_fit(int n_spec, int n_v_g
 }
 
 // ---------------------------------------------------------------------------------------
-// Gaussian fit of CCFs from float32 spectra: one block of kFwSpan warps per spectrum, FP32.
+// Gaussian fit of CCFs from float32 spectra: SPAN warps per spectrum, FP32 throughout.
 // ---------------------------------------------------------------------------------------
 // Such a CCF carries FP32 rounding (~1e-7 relative) already, so the fit needs no FP64: the
 // FP32 residuals r = a + b e - y (|r| error ~1e-7 of the continuum) move the least-squares centre
 // by ~1e-8 of the width, far below the mixed path's 1 cm/s.  The start, the scaled variables and
 // the two phases are those of k_gauss_fit; the second phase is Newton on the exact Hessian in
-// FP32.  Thread t of the block takes the points k = t + 32 kFwSpan i; a pass's sums are warp xor
-// butterflies, then the warps' sums are added in warp order through shared memory, so every
-// thread holds the same bits and runs the same iteration (the block's barriers are reached by
-// all of its threads).  Points with i < kFwCache stay in registers; further ones (more than 256
-// velocities) are kept as floats in the scratch row.
-#ifndef SOAP_FIT_SPAN
-#define SOAP_FIT_SPAN 4
-#endif
-constexpr int kFwSpan = SOAP_FIT_SPAN;   // warps per spectrum
-constexpr int kFwThreads = 32 * kFwSpan;
-constexpr int kFwCache = (256 + kFwThreads - 1) / kFwThreads;
+// FP32.  A block has 4 warps: SPAN = 4 gives each spectrum the whole block (a short chain per
+// pass: few spectra finish sooner), SPAN = 1 one warp (every lane repeats the small solves once
+// per spectrum instead of four times: many spectra finish sooner).  Thread t of a spectrum takes
+// the points k = t + 32 SPAN i; a pass's sums are warp xor butterflies, then (SPAN = 4) the
+// warps' sums are added in warp order through shared memory, so every thread holds the same bits
+// and runs the same iteration (the block's barriers are reached by all of its threads).  Points
+// with i < Fw<SPAN>::cache stay in registers; further ones (more than 256 velocities) are kept as
+// floats in the scratch row, each read back by the thread that wrote it.
+template <int SPAN>
+struct Fw {
+    static_assert(SPAN == 1 || SPAN == 4, "one warp or the whole block per spectrum");
+    static constexpr int threads = 32 * SPAN;                  // per spectrum
+    static constexpr int cache = (256 + threads - 1) / threads;
+    static constexpr int per_block = 4 / SPAN;                 // spectra per block of 4 warps
+};
+constexpr int kFwBlock = 128;
 constexpr int kFwPassesA = 80;          // FP32 Levenberg-Marquardt passes at most
 constexpr int kFwPassesB = 8;           // Newton passes at most
 constexpr float kFwTolA = 1e-4f;        // scaled step at which Levenberg-Marquardt hands over
@@ -879,14 +884,14 @@ __device__ __forceinline__ void warp_allsum(float (&f)[NF]) {
         for (int q = 0; q < NF; q++) f[q] += __shfl_xor_sync(0xffffffffu, f[q], o);
 }
 
-// Block-wide sums, identical in every thread: warp butterflies, then the kFwSpan warp sums added
-// in warp order.  buf: 2 x kFwSpan x kFwMaxSums floats, used alternately (a buffer is written
+// Sums over a spectrum's threads, identical in every thread: warp butterflies, then the SPAN warp
+// sums added in warp order.  buf: 2 x SPAN x kFwMaxSums floats, used alternately (a buffer is written
 // again only after the next call's barrier, when every thread has read it).
-template <int NF>
+template <int SPAN, int NF>
 __device__ __forceinline__ void block_allsum(float (&f)[NF], float* buf, int& parity) {
     warp_allsum<NF>(f);
-    if constexpr (kFwSpan > 1) {
-        float* b = buf + parity * (kFwSpan * kFwMaxSums);
+    if constexpr (SPAN > 1) {
+        float* b = buf + parity * (SPAN * kFwMaxSums);
         const int w = threadIdx.x >> 5;
         if ((threadIdx.x & 31) == 0)
 #pragma unroll
@@ -896,7 +901,7 @@ __device__ __forceinline__ void block_allsum(float (&f)[NF], float* buf, int& pa
         for (int q = 0; q < NF; q++) {
             float t = b[q];
 #pragma unroll
-            for (int v = 1; v < kFwSpan; v++) t += b[v * kFwMaxSums + q];
+            for (int v = 1; v < SPAN; v++) t += b[v * kFwMaxSums + q];
             f[q] = t;
         }
         parity ^= 1;
@@ -906,10 +911,11 @@ __device__ __forceinline__ void block_allsum(float (&f)[NF], float* buf, int& pa
 // One pass at scaled parameters p of a + b exp(-(u - m)^2 / (2 w^2)): J^T J (10, upper
 // triangle by rows), J^T r (4), r^2 (1) and, with HESS, R_j = sum r g d^j, j = 0..4 (g the
 // Gaussian, d = u - m) for the second-derivative part of the Hessian.  u_k = (k - kmin) du.
-template <bool HESS>
-__device__ __forceinline__ void fw_pass(const float p[4], int n_v, int kmin, float du,
-                                        const float (&yc)[kFwCache], const float* __restrict__ ys,
+template <int SPAN, bool HESS>
+__device__ __forceinline__ void fw_pass(const float p[4], int n_v, int kmin, float du, int t,
+                                        const float (&yc)[Fw<SPAN>::cache], const float* __restrict__ ys,
                                         float (&acc)[HESS ? 20 : 15], float* buf, int& parity) {
+    constexpr int kFwThreads = Fw<SPAN>::threads, kFwCache = Fw<SPAN>::cache;
     constexpr int NF = HESS ? 20 : 15;
 #pragma unroll
     for (int q = 0; q < NF; q++) acc[q] = 0.0f;
@@ -935,25 +941,26 @@ __device__ __forceinline__ void fw_pass(const float p[4], int n_v, int kmin, flo
             for (int j = 0; j < 5; j++) { acc[15 + j] += w; w *= d; }
         }
     };
-    const int t = threadIdx.x;
 #pragma unroll
     for (int i = 0; i < kFwCache; i++)
         if (t + kFwThreads * i < n_v) point(t + kFwThreads * i, yc[i]);
     for (int k = t + kFwThreads * kFwCache; k < n_v; k += kFwThreads) point(k, ys[k]);
-    block_allsum<NF>(acc, buf, parity);
+    block_allsum<SPAN, NF>(acc, buf, parity);
 }
 
-__global__ void __launch_bounds__(kFwThreads) k_gauss_fit_f32(int n_spec, int n_v_grid, double v_lo_grid,
-                                                               double v_step, const double* __restrict__ ccf,
-                                                               float* scratch, double* rv, double* fit,
-                                                               const int* __restrict__ win) {
+template <int SPAN>
+__global__ void __launch_bounds__(kFwBlock) k_gauss_fit_f32(int n_spec, int n_v_grid, double v_lo_grid,
+                                                             double v_step, const double* __restrict__ ccf,
+                                                             float* scratch, double* rv, double* fit,
+                                                             const int* __restrict__ win) {
+    constexpr int kFwThreads = Fw<SPAN>::threads, kFwCache = Fw<SPAN>::cache, kFwSpan = SPAN;
     __shared__ float buf[2 * kFwSpan * kFwMaxSums];
     __shared__ float sx[3 * kFwSpan];
     __shared__ int sk[kFwSpan];
     int parity = 0;
-    const int spec = blockIdx.x;
-    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    if (spec >= n_spec) return;                           // the whole block leaves together
+    const int spec = blockIdx.x * Fw<SPAN>::per_block + (int)threadIdx.x / kFwThreads;
+    const int t = threadIdx.x % kFwThreads, lane = t & 31, w = t >> 5;
+    if (spec >= n_spec) return;                           // SPAN = 4: the whole block; 1: the warp
     int k0 = 0, n_v = n_v_grid;
     if (win) {
         k0 = win[2 * spec];
@@ -1010,15 +1017,12 @@ __global__ void __launch_bounds__(kFwThreads) k_gauss_fit_f32(int n_spec, int n_
         yc[i] *= iscale;
         if (t + kFwThreads * i < n_v) area[0] += mx * iscale - yc[i];
     }
-    if (n_v > kFwThreads * kFwCache) {
-        __syncthreads();                                  // the scratch row written above is complete
-        for (int k = t + kFwThreads * kFwCache; k < n_v; k += kFwThreads) {
-            const float v = ys[k] * iscale;
-            ys[k] = v;
-            area[0] += mx * iscale - v;
-        }
+    for (int k = t + kFwThreads * kFwCache; k < n_v; k += kFwThreads) {   // values this thread wrote
+        const float v = ys[k] * iscale;
+        ys[k] = v;
+        area[0] += mx * iscale - v;
     }
-    block_allsum<1>(area, buf, parity);
+    block_allsum<SPAN, 1>(area, buf, parity);
     const float b0 = (mn - mx) * iscale;
     const double s0 = fmax(b0 != 0.0f ? (double)area[0] * v_step / ((double)fabsf(b0) * 2.5066282746310002) : v_step,
                            v_step);
@@ -1030,7 +1034,7 @@ __global__ void __launch_bounds__(kFwThreads) k_gauss_fit_f32(int n_spec, int n_
     float pt[4] = {p[0], p[1], p[2], p[3]};
     float acc[15], jtj[10], jtr[4], cost = 0.0f, lam = 1e-3f;
     bool tiny = false;
-    fw_pass<false>(p, n_v, kmin, du, yc, ys, acc, buf, parity);
+    fw_pass<SPAN, false>(p, n_v, kmin, du, t, yc, ys, acc, buf, parity);
     for (int it = 0; it < kFwPassesA; it++) {
         bool stop = false;
         if (it == 0 || acc[14] <= cost) {            // keep the trial point
@@ -1057,7 +1061,7 @@ __global__ void __launch_bounds__(kFwThreads) k_gauss_fit_f32(int n_spec, int n_
             break;
         }
         if (stop) break;
-        fw_pass<false>(pt, n_v, kmin, du, yc, ys, acc, buf, parity);
+        fw_pass<SPAN, false>(pt, n_v, kmin, du, t, yc, ys, acc, buf, parity);
     }
 
     // ---- phase 2: Newton on H = J^T J + sum r d2m ----
@@ -1065,7 +1069,7 @@ __global__ void __launch_bounds__(kFwThreads) k_gauss_fit_f32(int n_spec, int n_
     float cost_prev = INFINITY, last = INFINITY;
     for (int it = 0; it < kFwPassesB; it++) {
         float f[20];
-        fw_pass<true>(p, n_v, kmin, du, yc, ys, f, buf, parity);
+        fw_pass<SPAN, true>(p, n_v, kmin, du, t, yc, ys, f, buf, parity);
         if (!(f[14] <= cost_prev * (1.0f + 1e-5f))) {   // the last step did not help: undo it
             for (int a = 0; a < 4; a++) p[a] = prev[a];
             break;
@@ -1110,6 +1114,19 @@ __global__ void __launch_bounds__(kFwThreads) k_gauss_fit_f32(int n_spec, int n_
             fit[(int64_t)spec * 4 + 3] = fabs((double)p[3]) * s0;
         }
     }
+}
+
+// Fits of the CCFs of FP32 spectra: a whole block per spectrum while the spectra are few (up to
+// two per SM: the latency of one fit is what the call waits for), one warp per spectrum beyond
+// (the throughput of many fits).
+constexpr int kFwWholeBlockMax = 2 * 152;
+
+static void fit_f32_launch(int n_spec, cudaStream_t st, int n, int n_v, double v_lo, double v_step,
+                           const double* ccf, float* scratch, double* rv, double* fit, const int* win) {
+    if (n_spec <= kFwWholeBlockMax)
+        k_gauss_fit_f32<4><<<n_spec, kFwBlock, 0, st>>>(n, n_v, v_lo, v_step, ccf, scratch, rv, fit, win);
+    else
+        k_gauss_fit_f32<1><<<(n_spec + 3) / 4, kFwBlock, 0, st>>>(n, n_v, v_lo, v_step, ccf, scratch, rv, fit, win);
 }
 
 bool ccf_mask_same(const CcfState& st, const double* mask_lambda, const double* mask_weight,
@@ -1341,7 +1358,7 @@ soap_status ccf_enqueue(soap_ctx* c, CcfState& st, const CcfPlan& p, const void*
     if (tb) timer_end(c, SOAP_TIMER_CCF_AUX, tb);
     if (p.f32)      // float32 spectra: FP32 fit, one warp per spectrum
         SOAP_TIMED(c, SOAP_TIMER_FIT,
-                   k_gauss_fit_f32<<<n_spec, kFwThreads, 0, c->stream>>>(
+                   fit_f32_launch(n_spec, c->stream,
                        n_spec, n_v, p.v_lo, p.v_step, d_ccf, reinterpret_cast<float*>(p.y), rv_dev, fit_dev, win);
                    SOAP_LAUNCHED(c));
     else            // float64 spectra: FP64 residuals, the least-squares minimum to FP64 rounding
@@ -1499,7 +1516,7 @@ extern "C" soap_status soap_rv_ccf_static(double lambda_start_A, double lambda_e
     k_ccf_reduce<double><<<(unsigned)((tot + 255) / 256), 256, 0, stream>>>(n_chunks, n_spec, n_v, d_part, d_ccf);
     SOAP_CUDA(cudaGetLastError());
     if (spectra_f32)
-        k_gauss_fit_f32<<<n_spec, kFwThreads, 0, stream>>>(
+        fit_f32_launch(n_spec, stream,
             n_spec, n_v, v_lo, v_step, d_ccf, reinterpret_cast<float*>(d_y), rv_kms, fit_params, nullptr);
     else
         k_gauss_fit<<<n_spec, kFitThreads, 0, stream>>>(n_spec, n_v, v_lo, v_step, d_ccf, d_y, rv_kms, fit_params,

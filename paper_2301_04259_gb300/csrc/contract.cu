@@ -149,9 +149,23 @@ k_contract(int64_t n_px, Rows<T> rows, const long long* __restrict__ toff, const
     T* out_rows = out + (int64_t)blockIdx.z * n_phases * n_px + (int64_t)pb * PB * n_px;
     const TableContrast<T> con{contrast, n_px, ctype};
     if (fold) {
-        contract_tile_fold<T, PB, R, THREADS>(n_px, rows, toff + (int64_t)pb * max_taps, gstart + (int64_t)pb * (G + 1),
-                                              G, coefs + (int64_t)pb * max_taps * PB, con, fq, effs.e[blockIdx.z],
-                                              blockIdx.x, np, out_rows);
+        const long long* tt = toff + (int64_t)pb * max_taps;
+        const int* gs = gstart + (int64_t)pb * (G + 1);
+        const T* cb = coefs + (int64_t)pb * max_taps * PB;
+        const int eff = effs.e[blockIdx.z];
+        if constexpr (sizeof(T) == 4 && R % 2 == 0) {
+            if (eff == SOAP_EFFECT_FLUX)
+                contract_tile_fold32<PB, R, THREADS, SOAP_EFFECT_FLUX>(n_px, rows, tt, gs, G, cb, con, fq, blockIdx.x, np,
+                                                                       out_rows);
+            else if (eff == SOAP_EFFECT_BCONV)
+                contract_tile_fold32<PB, R, THREADS, SOAP_EFFECT_BCONV>(n_px, rows, tt, gs, G, cb, con, fq, blockIdx.x, np,
+                                                                        out_rows);
+            else
+                contract_tile_fold32<PB, R, THREADS, SOAP_EFFECT_TOT>(n_px, rows, tt, gs, G, cb, con, fq, blockIdx.x, np,
+                                                                      out_rows);
+        } else {
+            contract_tile_fold<T, PB, R, THREADS>(n_px, rows, tt, gs, G, cb, con, fq, eff, blockIdx.x, np, out_rows);
+        }
         return;
     }
     contract_tile<T, PB, R, THREADS>(n_px, rows, toff + (int64_t)pb * max_taps, gstart + (int64_t)pb * (G + 1), G,
@@ -195,7 +209,7 @@ static soap_status launch_contract(soap_ctx* c, int n_blocks, int G, int max_tap
 #define SOAP_R32 4
 #endif
 #ifndef SOAP_QR32
-#define SOAP_QR32 2
+#define SOAP_QR32 4
 #endif
 constexpr int kPB64 = 4, kR64 = 2, kT64 = 128;
 constexpr int kPB32 = SOAP_PB32, kR32 = SOAP_R32, kT32 = 128;

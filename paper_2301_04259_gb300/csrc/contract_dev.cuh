@@ -257,6 +257,91 @@ __device__ __forceinline__ void contract_tile_fold(int64_t n_px, const Rows<T>& 
     }
 }
 
+// FP32 form of contract_tile_fold with the effect fixed at compile time: X = C S_a - S_q (TOT),
+// S_a - S_q (BCONV), (C - 1) S_q (FLUX, no active row read), the same roundings as the generic
+// form, and the accumulators of pixel pairs (r, r+1) in 64-bit registers updated by two-wide
+// FMAs (fma.rn.f32x2: two independent IEEE FMAs), so the results are the same.
+__device__ __forceinline__ unsigned long long ct_pack(float lo, float hi) {
+    unsigned long long v;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(v) : "f"(lo), "f"(hi));
+    return v;
+}
+__device__ __forceinline__ void ct_unpack(unsigned long long v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ void ct_fma2(unsigned long long& d, unsigned long long a, unsigned long long b) {
+    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(d) : "l"(a), "l"(b));
+}
+
+template <int PB, int R, int THREADS, int EFF, class Con>
+__device__ __forceinline__ void contract_tile_fold32(int64_t n_px, const Rows<float>& rows,
+                                                     const long long* __restrict__ toff,
+                                                     const int* __restrict__ gs, int G, const float* __restrict__ cb,
+                                                     const Con& con, const float* __restrict__ fq, int64_t tile,
+                                                     int np, float* __restrict__ out_rows) {
+    static_assert(R % 2 == 0, "pixel pairs");
+    const int64_t m0 = tile * THREADS * R + threadIdx.x;
+    int64_t mcl[R];
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+        const int64_t m = m0 + (int64_t)r * THREADS;
+        mcl[r] = m < n_px ? m : n_px - 1;
+    }
+    unsigned long long acc[PB][R / 2];
+#pragma unroll
+    for (int p = 0; p < PB; p++)
+#pragma unroll
+        for (int k = 0; k < R / 2; k++) acc[p][k] = 0ull;
+    const float* bq = rows.q + m0;
+    for (int g = 0; g < G; g++) {
+        const int t0 = gs[g], t1 = gs[g + 1];
+        if (t0 == t1) continue;
+        const float* ba = rows.a[con.type(g) == SOAP_FACULA ? 1 : 0] + m0;
+        float cc[R];                                       // C (TOT) or C - 1 (FLUX)
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            if constexpr (EFF == SOAP_EFFECT_BCONV) cc[r] = 1.0f;
+            else if constexpr (EFF == SOAP_EFFECT_FLUX) cc[r] = con.at(g, mcl[r]) - 1.0f;
+            else cc[r] = con.at(g, mcl[r]);
+        }
+#pragma unroll 4
+        for (int t = t0; t < t1; t++) {
+            const long long off = __ldg(toff + t);
+            float x[R];
+#pragma unroll
+            for (int r = 0; r < R; r++) {
+                const float q = __ldg(bq + off + r * THREADS);
+                if constexpr (EFF == SOAP_EFFECT_FLUX) x[r] = cc[r] * q;
+                else if constexpr (EFF == SOAP_EFFECT_BCONV) x[r] = __ldg(ba + off + r * THREADS) - q;
+                else x[r] = fmaf(cc[r], __ldg(ba + off + r * THREADS), -q);
+            }
+            unsigned long long x2[R / 2];
+#pragma unroll
+            for (int k = 0; k < R / 2; k++) x2[k] = ct_pack(x[2 * k], x[2 * k + 1]);
+            float cv[PB];
+            load_coefs<float, PB>(cb + (int64_t)t * PB, cv);
+#pragma unroll
+            for (int p = 0; p < PB; p++) {
+                const unsigned long long c2 = ct_pack(cv[p], cv[p]);
+#pragma unroll
+                for (int k = 0; k < R / 2; k++) ct_fma2(acc[p][k], c2, x2[k]);
+            }
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < PB; p++) {
+        if (p >= np) break;
+        float y[R];
+#pragma unroll
+        for (int k = 0; k < R / 2; k++) ct_unpack(acc[p][k], y[2 * k], y[2 * k + 1]);
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const int64_t m = m0 + (int64_t)r * THREADS;
+            if (m < n_px) out_rows[(int64_t)p * n_px + m] = fq ? fq[mcl[r]] + y[r] : y[r];
+        }
+    }
+}
+
 // Contrast rows from a device list of temperatures (one row per class and mu bin when facula
 // temperatures depend on mu): FP64 rows (and their FP32 copies).
 static __global__ void k_contrast_rows(int64_t n_px, double lam_s, double delta, double t_quiet, int n_rows,

@@ -307,6 +307,25 @@ def test_ccf_and_rv_config1(S, cfg1, cfg1_ref):
     assert np.abs(rv_32 - rv_o).max() * 1e5 <= 1.0
 
 
+def test_rv_fp32_many_spectra_against_the_oracle(S, cfg1, cfg1_ref):
+    """FP32 fits of few spectra take a block each, of many (more than 304) a warp each: 325 float32
+    spectra (the 25 phases at 13 brightness scales, which leave the RV unchanged) against the
+    oracle's RVs of the same spectra within 1 cm/s, and the 25 of the first scale fitted alone
+    (one block each) against the same spectra inside the large call within 0.1 cm/s."""
+    _, ref = cfg1_ref
+    lo, step, nv = synth.velocity_grid(cfg1.star.vsini_kms)
+    base = ref[0]
+    F = np.concatenate([base * (1.0 + 0.002 * k) for k in range(13)]).astype(np.float32)
+    assert F.shape[0] > 304
+    rv_o, _, _ = O.rv(F.astype(np.float64), cfg1.star, cfg1.mask_lambda, cfg1.mask_weight,
+                      cfg1.mask_width_kms, lo, step, nv)
+    rv_many, _, _ = _gpu_rv(S, cfg1, F, lo, step, nv)
+    assert np.isfinite(rv_many).all()
+    assert np.abs(rv_many - rv_o).max() * 1e5 <= 1.0
+    rv_few, _, _ = _gpu_rv(S, cfg1, F[:25], lo, step, nv)
+    assert np.abs(rv_few - rv_many[:25]).max() * 1e5 <= 0.1
+
+
 def _tile_np(c, width, step, nv, lo):
     """Pixels a group of 4 consecutive velocities can reach for one line (the tiled CCF kernel
     runs for 2..4): box width plus the largest spread of 4 box positions, + 2."""
