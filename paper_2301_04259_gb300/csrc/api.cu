@@ -215,7 +215,8 @@ static void free_ctx_memory(soap_ctx* c) {
     void* ptrs[] = {c->cell_I, c->cell_w, c->cell_mu, c->cell_j, c->cell_bin, c->cell_mu32,
                     c->cell_k0, c->cell_k1, c->flags, c->q64,
                     c->q32, c->a64[0], c->a32[0], c->a64[1], c->a32[1], c->kq_fixed,
-                    c->sum_I_fixed, c->qtoff, c->qgstart, c->qc64, c->qc32, c->geo_counter, c->cell_x};
+                    c->sum_I_fixed, c->qtoff, c->qgstart, c->qc64, c->qc32, c->geo_counter, c->cell_x,
+                    c->qgrp, c->qgrp_start};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     DevBuf* bufs[] = {&c->stage_in, &c->fq, &c->contrast, &c->kphase, &c->jobs, &c->coefs, &c->job_counters,
@@ -442,6 +443,8 @@ soap_status soap_init_star(const soap_star_desc* s, const double* quiet_local, i
     ALLOC(c->sum_I_fixed, 2 * sizeof(long long));
     ALLOC(c->qtoff, (size_t)c->n_mu * SOAP_MAX_TAPS * sizeof(long long));
     ALLOC(c->qgstart, 2 * sizeof(int));
+    ALLOC(c->qgrp, (size_t)c->n_mu * (SOAP_MAX_TAPS + 1) * sizeof(soap::TapGroup));
+    ALLOC(c->qgrp_start, 2 * sizeof(int));
     ALLOC(c->qc64, (size_t)c->n_mu * SOAP_MAX_TAPS * sizeof(double));
     ALLOC(c->qc32, (size_t)c->n_mu * SOAP_MAX_TAPS * sizeof(float));
     ALLOC(c->geo_counter, sizeof(int));

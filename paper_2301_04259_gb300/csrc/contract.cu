@@ -208,9 +208,6 @@ static soap_status launch_contract(soap_ctx* c, int n_blocks, int G, int max_tap
 #ifndef SOAP_R32
 #define SOAP_R32 4
 #endif
-#ifndef SOAP_QR32
-#define SOAP_QR32 4
-#endif
 constexpr int kPB64 = 4, kR64 = 2, kT64 = 128;
 constexpr int kPB32 = SOAP_PB32, kR32 = SOAP_R32, kT32 = 128;
 
@@ -238,6 +235,52 @@ static soap_status tap_buffers(soap_ctx* c, int n_phases, int n_class, int PB, i
     return SOAP_OK;
 }
 
+// Quiet integral (Alg. 1) in FP32 from the quiet taps as aligned groups (build_taps_dev): a thread
+// owns 4 consecutive pixels; the taps of a group sit at row offsets 4q + e, e < 4, so their row
+// values for the 4 pixels are 8 values from 4q + m0, two aligned 16-byte loads.  Groups are taken
+// 4 at a time (all their loads issued before the first is applied); per pixel the taps are added
+// in table order, as in contract_tile (same results).
+__global__ void __launch_bounds__(128)
+k_quiet_groups(int64_t n_px, const float* __restrict__ q, const TapGroup* __restrict__ grp,
+               const int* __restrict__ gstart, const float* __restrict__ coef, float* __restrict__ out) {
+    const int64_t m0 = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+    if (m0 >= n_px) return;
+    const int n = gstart[1];
+    const float* base = q + m0;
+    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    for (int i0 = 0; i0 < n; i0 += 4) {
+        TapGroup d[4];
+        float W[4][8];
+#pragma unroll
+        for (int j = 0; j < 4; j++) d[j] = grp[min(i0 + j, n - 1)];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const float4 a = __ldg(reinterpret_cast<const float4*>(base + d[j].off4));
+            const float4 b = __ldg(reinterpret_cast<const float4*>(base + d[j].off4) + 1);
+            W[j][0] = a.x; W[j][1] = a.y; W[j][2] = a.z; W[j][3] = a.w;
+            W[j][4] = b.x; W[j][5] = b.y; W[j][6] = b.z; W[j][7] = b.w;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            if (i0 + j >= n) break;
+#pragma unroll
+            for (int e = 3; e >= 0; e--) {                     // offsets falling: table order
+                if (!(d[j].mask & (1 << e))) continue;
+                const float cv = __ldg(coef + d[j].tap0 - e);
+#pragma unroll
+                for (int r = 0; r < 4; r++) acc[r] = fmaf(cv, W[j][e + r], acc[r]);
+            }
+        }
+    }
+    if ((n_px & 3) == 0 && (reinterpret_cast<uintptr_t>(out) & 15) == 0) {
+        *reinterpret_cast<float4*>(out + m0) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+    } else {
+#pragma unroll
+        for (int r = 0; r < 4; r++)
+            if (m0 + r < n_px) out[m0 + r] = acc[r];
+    }
+}
+
 soap_status toeplitz_quiet(soap_ctx* c, int precision, void* dst) {
     // tap table built by the geometry kernel
     SOAP_TRY(join_geometry(c));
@@ -247,8 +290,12 @@ soap_status toeplitz_quiet(soap_ctx* c, int precision, void* dst) {
     if (precision == SOAP_FP64)
         return launch_contract<double, 1, 1, 128>(c, nbk, G, mt, c->qtoff, c->qgstart, c->qc64, ct, nullptr,
                                                  nullptr, 1, el, 1, (double*)dst, c->q64, nullptr, nullptr);
-    return launch_contract<float, 1, SOAP_QR32, 128>(c, nbk, G, mt, c->qtoff, c->qgstart, c->qc32, ct, nullptr,
-                                            nullptr, 1, el, 1, (float*)dst, c->q32, nullptr, nullptr);
+    const unsigned blocks = (unsigned)((c->n_px + 4 * 128 - 1) / (4 * 128));
+    SOAP_TIMED(c, SOAP_TIMER_CONTRACT_QUIET,
+               k_quiet_groups<<<blocks, 128, 0, c->stream>>>(c->n_px, c->q32, c->qgrp, c->qgrp_start, c->qc32,
+                                                            (float*)dst);
+               SOAP_LAUNCHED(c));
+    return SOAP_OK;
 }
 
 soap_status toeplitz_active(soap_ctx* c, const RegionDev* regions_host, int n_regions,

@@ -62,7 +62,7 @@ k_geometry(int N, double vsini, double sin_i, double cos_i, double alpha, double
            int32_t* cell_bin, long long* cell_k0, long long* cell_k1, long long* kq_fixed,
            long long* sum2, long long* qtoff, int* qgstart, double* qc64, float* qc32, int q_max_taps,
            int64_t row_len, int64_t pad, int fx_bits, int* counter, unsigned int* flags,
-           const double* __restrict__ cell_x, double area) {
+           const double* __restrict__ cell_x, double area, TapGroup* qgrp, int* qgrp_start) {
     extern __shared__ long long hist[];                  // [n_mu][n_taps]
     const int nb = n_mu * n_taps;
     for (int t = threadIdx.x; t < nb; t += blockDim.x) hist[t] = 0;
@@ -129,7 +129,7 @@ k_geometry(int N, double vsini, double sin_i, double cos_i, double alpha, double
     if (s_last) {
         __threadfence();
         build_taps_dev(kq_fixed, 0, 1, 1, n_mu, n_taps, tap_min, 1, 0, 1.0 / scale, fx_bits, row_len, pad, qtoff,
-                       qgstart, qc64, qc32, q_max_taps, hist, flags);
+                       qgstart, qc64, qc32, q_max_taps, hist, flags, nullptr, qgrp, qgrp_start);
     }
 }
 
@@ -299,7 +299,7 @@ soap_status geometry_init(soap_ctx* c) {
             tap_max, c->n_taps, scale, c->cell_I, c->cell_w, c->cell_mu, c->cell_mu32, c->cell_j,
             c->cell_bin, c->cell_k0, c->cell_k1, c->kq_fixed, c->sum_I_fixed, c->qtoff, c->qgstart, c->qc64,
             c->qc32, c->n_mu * SOAP_MAX_TAPS, c->row_len, c->pad, c->fx_bits, c->geo_counter, c->flags,
-            c->cell_x, (2.0 / (double)c->N) * (2.0 / (double)c->N));
+            c->cell_x, (2.0 / (double)c->N) * (2.0 / (double)c->N), c->qgrp, c->qgrp_start);
         SOAP_LAUNCHED(c);
         if (c->profiling) timer_end(c, SOAP_TIMER_GEOMETRY, tb);
         SOAP_CUDA(cudaEventRecord(c->ev_geo, c->stream));

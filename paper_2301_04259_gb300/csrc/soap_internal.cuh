@@ -105,6 +105,13 @@ enum DeviceFlag : unsigned int {
     kFlagTimeout = 16u         // a tensor-core kernel's bounded barrier wait gave up
 };
 
+// The taps of one (group, mu bin) of a tap table at row offsets 4q .. 4q + 3 (build_taps_dev).
+struct TapGroup {
+    long long off4;    // 4q: row offset of the group's first value (a multiple of 4)
+    int tap0;          // tap index of offset 4q (offset 4q + e is tap tap0 - e)
+    int mask;          // bit e: offset 4q + e is one of the taps
+};
+
 // CCF state of one user of the CCF (the single-star calls, or the batched form): line and
 // velocity tables (kept while the mask and the velocity grid stay the same), the cached mask
 // matrix of the tensor-core form, and per-call scratch (partial sums, CCF, scaled CCF).
@@ -193,6 +200,8 @@ struct soap_ctx {
     // quiet tap table, rebuilt with the geometry: row offsets, group starts, coefficients
     long long* qtoff = nullptr;     // [n_mu * SOAP_MAX_TAPS]
     int* qgstart = nullptr;         // [2]
+    soap::TapGroup* qgrp = nullptr; // quiet taps as aligned groups [n_mu * (SOAP_MAX_TAPS + 1)]
+    int* qgrp_start = nullptr;      // [2]
     double* qc64 = nullptr;
     float* qc32 = nullptr;
     int* geo_counter = nullptr;
@@ -482,15 +491,24 @@ __device__ __forceinline__ float fixed_to_float(long long K, int bits) {
 // toff + pb*max_taps,
 // gstart + pb*(G+1) and coef + pb*max_taps*PB.  A table that would exceed max_taps is left
 // empty and flags kFlagJobOverflow.
+// agrp / agstart (optional): the same taps as aligned groups.  The taps of one (group, bin) are
+// consecutive shifts of one row, at offsets o_hi, o_hi - 1, .., o_lo; aligned group q holds those
+// of them in 4q .. 4q + 3 (TapGroup: off4 = 4q, the tap index of offset 4q, a bit per present
+// offset; groups listed from the highest q down, like the taps), so that a contraction can read the row values of four consecutive pixels for all of
+// a group's taps as two aligned 16-byte vectors.  agstart[g] is the first aligned group of
+// group g (G + 1 entries, last = total); block pb's groups start at agrp + pb * max_groups with
+// max_groups = max_taps + G n_mu (a (group, bin) with nk taps has at most nk + 1 groups).
 __device__ __forceinline__ void build_taps_dev(const long long* __restrict__ kfix, int pb, int n_phases,
                                                int n_class, int n_mu, int n_taps, int tap_min, int PB, int mode,
                                                double inv_scale, int fx_bits, int64_t row_len, int64_t pad,
                                                long long* toff,
                                                int* gstart, double* c64, float* c32, int max_taps,
-                                               long long* s_k, unsigned int* flags, int* bstart = nullptr) {
+                                               long long* s_k, unsigned int* flags, int* bstart = nullptr,
+                                               TapGroup* agrp = nullptr, int* agstart = nullptr) {
     __shared__ int s_lo[(1 + SOAP_MAX_CLASSES) * SOAP_MAX_MU];
     __shared__ int s_hi[(1 + SOAP_MAX_CLASSES) * SOAP_MAX_MU];
     __shared__ int s_off[(1 + SOAP_MAX_CLASSES) * SOAP_MAX_MU];
+    __shared__ int s_goff[(1 + SOAP_MAX_CLASSES) * SOAP_MAX_MU];
     __shared__ int s_warp[32];
     __shared__ int s_total;
     const int use_smem = s_k != nullptr;
@@ -548,44 +566,62 @@ __device__ __forceinline__ void build_taps_dev(const long long* __restrict__ kfi
         }
         s_lo[t] = lo; s_hi[t] = hi;
     }
-    // exclusive prefix sum of the tap counts (warp scans, chunks of blockDim.x)
+    // exclusive prefix sums (warp scans, chunks of blockDim.x) of the tap counts and of the
+    // aligned-group counts per (group, bin)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    if (threadIdx.x == 0) s_total = 0;
-    __syncthreads();
-    for (int c0 = 0; c0 < ngb; c0 += blockDim.x) {
-        const int t = c0 + threadIdx.x;
-        const int nk = (t < ngb && s_hi[t] >= s_lo[t]) ? s_hi[t] - s_lo[t] + 1 : 0;
-        int x = nk;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) s_warp[warp] = x;
+    const int64_t o_top = pad - tap_min;                       // offset of tap 0 in bin 0
+    auto scan = [&](auto count, int* dst) -> int {
+        if (threadIdx.x == 0) s_total = 0;
         __syncthreads();
-        if (warp == 0) {
-            int w = lane < nw ? s_warp[lane] : 0;
+        for (int c0 = 0; c0 < ngb; c0 += blockDim.x) {
+            const int t = c0 + threadIdx.x;
+            const int n = t < ngb ? count(t) : 0;
+            int x = n;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, w, o);
-                if (lane >= o) w += y;
+                const int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
             }
-            if (lane < nw) s_warp[lane] = w;
+            if (lane == 31) s_warp[warp] = x;
+            __syncthreads();
+            if (warp == 0) {
+                int w = lane < nw ? s_warp[lane] : 0;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, w, o);
+                    if (lane >= o) w += y;
+                }
+                if (lane < nw) s_warp[lane] = w;
+            }
+            __syncthreads();
+            if (t < ngb) dst[t] = s_total + (warp > 0 ? s_warp[warp - 1] : 0) + x - n;
+            __syncthreads();
+            if (threadIdx.x == 0) s_total += s_warp[nw - 1];
+            __syncthreads();
         }
-        __syncthreads();
-        if (t < ngb) s_off[t] = s_total + (warp > 0 ? s_warp[warp - 1] : 0) + x - nk;
-        __syncthreads();
-        if (threadIdx.x == 0) s_total += s_warp[nw - 1];
-        __syncthreads();
-    }
-    const int total = s_total;
+        return s_total;
+    };
+    auto n_groups = [&](int t) -> int {
+        if (s_hi[t] < s_lo[t]) return 0;
+        const int64_t ob = (int64_t)(t % n_mu) * row_len + o_top;
+        return (int)(((ob - s_lo[t]) >> 2) - ((ob - s_hi[t]) >> 2) + 1);
+    };
+    const int total_groups = agrp ? scan(n_groups, s_goff) : 0;
+    __syncthreads();
+    const int total = scan([&](int t) { return s_hi[t] >= s_lo[t] ? s_hi[t] - s_lo[t] + 1 : 0; }, s_off);
     int* gs = gstart + (int64_t)pb * (G + 1);
     if (total > max_taps) {
         if (threadIdx.x == 0) atomicOr(flags, kFlagJobOverflow);
         for (int g = threadIdx.x; g <= G; g += blockDim.x) gs[g] = 0;
+        if (agrp)
+            for (int g = threadIdx.x; g <= G; g += blockDim.x) agstart[(int64_t)pb * (G + 1) + g] = 0;
         return;
     }
     for (int g = threadIdx.x; g <= G; g += blockDim.x) gs[g] = g < G ? s_off[g * n_mu] : total;
+    if (agrp) {
+        int* ags = agstart + (int64_t)pb * (G + 1);
+        for (int g = threadIdx.x; g <= G; g += blockDim.x) ags[g] = g < G ? s_goff[g * n_mu] : total_groups;
+    }
     // per-(group, bin) tap starts, for contractions that fold each bin separately
     if (bstart) {
         int* bs = bstart + (int64_t)pb * (ngb + 1);
@@ -599,6 +635,24 @@ __device__ __forceinline__ void build_taps_dev(const long long* __restrict__ kfi
         const int64_t tap0 = (int64_t)pb * max_taps + s_off[t];
         for (int kk = lane; kk < nk; kk += 32)
             toff[tap0 + kk] = (int64_t)b * row_len + pad - (tap_min + s_lo[t] + kk);
+        if (agrp) {
+            // taps kk = 0 .. nk-1 at offsets o_hi - kk (tap index within the block: s_off[t] + kk)
+            const int64_t o_hi = (int64_t)b * row_len + o_top - s_lo[t], o_lo = o_hi - (nk - 1);
+            const int64_t q_hi = o_hi >> 2;
+            const int ng = (int)(q_hi - (o_lo >> 2) + 1);
+            TapGroup* dst = agrp + (int64_t)pb * (max_taps + ngb) + s_goff[t];
+            for (int i = lane; i < ng; i += 32) {               // table order: offsets falling
+                const int64_t off4 = 4 * (q_hi - i);
+                int mask = 0;
+                for (int e = 0; e < 4; e++)
+                    if (off4 + e >= o_lo && off4 + e <= o_hi) mask |= 1 << e;
+                TapGroup tg;
+                tg.off4 = off4;
+                tg.tap0 = s_off[t] + (int)(o_hi - off4);
+                tg.mask = mask;
+                dst[i] = tg;
+            }
+        }
         for (int e = lane; e < nk * PB; e += 32) {
             const int kk = e / PB, pl = e % PB;
             const long long K = value(g, b, pl, s_lo[t] + kk);
