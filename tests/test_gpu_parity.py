@@ -336,12 +336,13 @@ def _tile_np(c, width, step, nv, lo):
 
 
 @pytest.mark.parametrize("width,step,n_spec", [(0.82, 0.25, 17), (0.3, 0.15, 1), (1.6, 0.25, 33),
-                                               (0.82, 0.5, 16)])
+                                               (0.82, 0.5, 16), (0.82, 0.25, 22), (0.82, 0.25, 29)])
 def test_ccf_fp32_sorted_mask_matches_oracle(S, cfg2, width, step, n_spec):
     """FP32 spectra, mask sorted by wavelength, full-size grid (205,800 px, 12,946 lines): the
     CCF element by element against the oracle's on the same (FP32-rounded) spectra, for boxes
     of 0.35 / 0.94 / 1.84 px and velocity steps of 0.15 / 0.25 / 0.5 km/s (2, 3 and 4 pixels per
-    group of 4 velocities), with 1, 16, 17 and 33 spectra (ragged blocks of 16)."""
+    group of 4 velocities), with 1, 16, 17, 22, 29 and 33 spectra (full rows of 16, and a last
+    row of 1, 6 or 13 spectra computed as 4, 8 or 16 over its own line split)."""
     c = cfg2
     half = c.star.vsini_kms + 20.0
     nv = int(np.floor(2 * half / step + 1e-9)) + 1
