@@ -11,12 +11,12 @@
 // adds the overlaps of the few lines that reach those pixels (staged in shared memory) in a
 // private FP32 row and stores it split, x = hi + lo with hi = bf16(x), lo = bf16(x - hi), as the
 // 128-byte-swizzle K-major image of the block's shared-memory tile (hi tile, then lo tile).
-// k_ccf_tc: CTA = (chunk of pixels, tile of 128 spectra), 256 threads, one CTA per SM.  Per K
-// block the mask tiles are copied verbatim (cp.async, 16 bytes a thread and copy) and every
-// thread splits 32 pixels of one spectrum (its operand row) into the stage; the copies and loads
-// of block i+1 are issued before block i is split, and one thread issues the 12 MMAs of block i
-// (M = 128, N = velocities rounded up to 16, K = 16; F_hi M_hi + F_hi M_lo + F_lo M_hi) and
-// commits them to the stage's barrier (two stages).  The epilogue writes the chunk's FP32
+// k_ccf_tc: CTA = (chunk of pixels, tile of 128 spectra), one CTA per SM, warp-specialised (see
+// the kernel): one lane streams the mask tiles of each K block with a bulk copy into a ring of up
+// to four stages, eight warps split the spectra (loaded one block ahead into registers) into
+// their BF16 hi/lo stage, one lane issues the 12 MMAs of the block (M = 128, N = velocities
+// rounded up to 16, K = 16; F_hi M_hi + F_hi M_lo + F_lo M_hi) once both stages are full and
+// commits them to the barriers that free the stages.  The epilogue writes the chunk's FP32
 // partial CCF, which k_ccf_reduce adds over the chunks in a fixed order.  Every barrier wait is
 // bounded; a timeout sets kFlagTimeout and the CTA stops issuing work.
 #include <cuda_bf16.h>
@@ -29,17 +29,14 @@ namespace soap {
 
 constexpr int kCcM = 128;                  // spectra per CTA (TMEM lanes)
 constexpr int kCcK = 64;                   // pixels per K block: one 128-byte swizzle row of BF16
-constexpr int kCcThreads = 256;            // two threads per spectrum row
+constexpr int kCcThreads = 256;            // mask-matrix builder threads
 constexpr int kCcAB = kCcM * kCcK * 2;     // bytes of one half (hi or lo) of the spectra tile, 16 KB
-constexpr int kCcStages = 2;
 constexpr int kCcChunkMax = 2048;          // pixels per CTA at most (bounds the FP32 accumulation)
 // mask-matrix builder
 constexpr int kCcWin = 512;                // lines of a K block staged in shared memory (more: read directly)
 constexpr int kCcMaxV = 256;               // velocities at most (N <= 256)
 
 __host__ __device__ inline int cc_bb(int n_pad) { return n_pad * kCcK * 2; }       // one mask-tile half
-__host__ __device__ inline int cc_stage(int n_pad) { return 2 * kCcAB + 2 * cc_bb(n_pad); }
-__host__ __device__ inline size_t cc_smem(int n_pad) { return (size_t)kCcStages * cc_stage(n_pad) + 1024 + 64; }
 __host__ __device__ inline size_t cc_m_smem() {
     return (size_t)kCcThreads * 32 * 4 + (size_t)kCcWin * 12 + (size_t)kCcMaxV * 8;
 }
@@ -170,9 +167,6 @@ struct CcArgs {
     uint32_t tmem_cols;
 };
 
-__device__ __forceinline__ void cc_cp_async16(void* dst, const void* src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_u32(dst)), "l"(src) : "memory");
-}
 
 // 32 spectrum values of row frow at pixels pa .. pa+31, zero at and past P1 (or for no row)
 __device__ __forceinline__ void cc_load_row(float (&a)[32], const float* frow, bool row_on, int vec4,
@@ -190,109 +184,146 @@ __device__ __forceinline__ void cc_load_row(float (&a)[32], const float* frow, b
     }
 }
 
-__global__ void __launch_bounds__(kCcThreads, 1)
+// Warp-specialised form.  Warp 0, one lane: the mask tiles of K block kb, one bulk copy of both
+// halves into B stage kb mod SB (completion on fullB, transaction bytes).  Warps 2..9 (256
+// threads, two per spectrum row): the spectrum values of block kb split into the A stage
+// kb mod kCcSA (loaded one block ahead into registers), each thread then fences its writes for the
+// tensor cores and arrives on fullA.  Warp 1, one lane: when both stages are full, the 12 MMAs of
+// the block, committed to emptyA and emptyB, which free the stages for the copies and splits of
+// later blocks.  So the tensor cores, the copies and the splits of different K blocks overlap, the
+// mask tiles SB - 1 blocks ahead of the MMAs.
+constexpr int kCcWsThreads = 320;
+constexpr int kCcSA = 2;                   // A (spectra) stages
+constexpr int kCcSBMax = 4;                // B (mask) stages at most
+__host__ __device__ inline int cc_sb(int n_pad) {
+    const long avail = 227L * 1024 - 1024 - 256 - (long)kCcSA * 2 * kCcAB;
+    const long sb = avail / (2L * cc_bb(n_pad));
+    return (int)(sb < kCcSBMax ? sb : kCcSBMax);
+}
+__host__ __device__ inline size_t cc_ws_smem(int n_pad) {
+    return (size_t)kCcSA * 2 * kCcAB + (size_t)cc_sb(n_pad) * 2 * cc_bb(n_pad) + 1024 + 256;
+}
+
+__device__ __forceinline__ void cc_mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void cc_bulk(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(tc::smem_u32(dst)), "l"(src), "r"(bytes), "r"(tc::smem_u32(bar))
+                 : "memory");
+}
+
+__global__ void __launch_bounds__(kCcWsThreads, 1)
 k_ccf_tc(const __grid_constant__ CcArgs g, unsigned int* flags) {
     extern __shared__ unsigned char smem_raw[];
-    unsigned char* ring = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
-    const int stage_bytes = cc_stage(g.n_pad);
+    unsigned char* base = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
     const int bb = cc_bb(g.n_pad);
-    uint64_t* empty = reinterpret_cast<uint64_t*>(ring + kCcStages * stage_bytes);
-    uint64_t* accum = empty + kCcStages;
+    const int SB = cc_sb(g.n_pad);
+    unsigned char* ringA = base;                                   // [kCcSA][hi, lo][128 x 128 B]
+    unsigned char* ringB = ringA + kCcSA * 2 * kCcAB;              // [SB][hi, lo][n_pad x 128 B]
+    uint64_t* fullA = reinterpret_cast<uint64_t*>(ringB + (size_t)SB * 2 * bb);
+    uint64_t* emptyA = fullA + kCcSA;
+    uint64_t* fullB = emptyA + kCcSA;
+    uint64_t* emptyB = fullB + kCcSBMax;
+    uint64_t* accum = emptyB + kCcSBMax;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
-    const int t = threadIdx.x, warp = t >> 5;
-    const int r = t & (kCcM - 1), half = t >> 7;    // spectrum row and which 32 pixels of the block
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const int64_t P0 = (int64_t)blockIdx.x * g.chunk;
     const int64_t P1 = P0 + g.chunk < g.n_px ? P0 + g.chunk : g.n_px;
     const int n_kb = (int)((P1 - P0 + kCcK - 1) / kCcK);
     const int64_t kb0 = P0 / kCcK;                  // first K block of the chunk in the mask tiles
     const int s0 = blockIdx.y * kCcM;
-    const bool row_on = s0 + r < g.n_spec;
-    const float* frow = g.spectra + (int64_t)(row_on ? s0 + r : 0) * g.n_px;
-    const int n_copy = 2 * bb / 16;                 // 16-byte pieces of the two mask tiles
 
     if (t == 0) {
-        for (int s = 0; s < kCcStages; s++) tc::mbar_init(&empty[s], 1);
+        for (int s = 0; s < kCcSA; s++) { tc::mbar_init(&fullA[s], 256); tc::mbar_init(&emptyA[s], 1); }
+        for (int s = 0; s < SB; s++) { tc::mbar_init(&fullB[s], 1); tc::mbar_init(&emptyB[s], 1); }
         tc::mbar_init(accum, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                      ::"r"(tc::smem_u32(tmem_slot)), "r"(g.tmem_cols) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    // block 0: mask tiles in flight, spectrum values in registers
-    {
-        const unsigned char* src = g.m + (size_t)kb0 * 2 * bb;
-        for (int i = t; i < n_copy; i += kCcThreads) cc_cp_async16(ring + 2 * kCcAB + 16 * i, src + 16 * i);
-        asm volatile("cp.async.commit_group;" ::: "memory");
-    }
-    float a[32];
-    cc_load_row(a, frow, row_on, g.vec4, P0 + 32 * half, P1);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
 
-    // one K block; the spectrum values of block kb are in cur, those of block kb+1 go to nxt (the
-    // loop below alternates two register sets, so no copy waits for the loads in flight)
-    bool ok = true;
-    auto step = [&](int kb, float (&cur)[32], float (&nxt)[32]) -> bool {
-        const int s = kb & 1;
-        const bool next = kb + 1 < n_kb;
-        if (next) {
-            // block kb+1: its stage is free once the MMAs of block kb-1 are done
-            const int s1 = (kb + 1) & 1;
-            if (kb + 1 >= kCcStages) ok = tc::mbar_wait(&empty[s1], ((kb + 1 - kCcStages) / kCcStages) & 1, flags);
-            if (!__syncthreads_and(ok)) { ok = false; return false; }
-            const unsigned char* src = g.m + (size_t)(kb0 + kb + 1) * 2 * bb;
-            unsigned char* dst = ring + s1 * stage_bytes + 2 * kCcAB;
-            for (int i = t; i < n_copy; i += kCcThreads) cc_cp_async16(dst + 16 * i, src + 16 * i);
-            asm volatile("cp.async.commit_group;" ::: "memory");
-            cc_load_row(nxt, frow, row_on, g.vec4, P0 + (int64_t)(kb + 1) * kCcK + 32 * half, P1);
-        }
-        // block kb: spectrum row r, chunks 4 half .. 4 half + 3 (the stage's last reader, the
-        // MMAs of block kb-2, finished before its mask copies were issued)
-        unsigned char* st = ring + s * stage_bytes;
-#pragma unroll
-        for (int q = 0; q < 4; q++) cc_put8(st, st + kCcAB, cc_sw128(r, 4 * half + q), cur + 8 * q);
-        if (next) asm volatile("cp.async.wait_group 1;" ::: "memory");   // block kb's mask tiles landed
-        else asm volatile("cp.async.wait_group 0;" ::: "memory");
-        // the tensor cores read shared memory through the async proxy
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (t == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t ah = tc::smem_u32(st), al = ah + kCcAB, bh = al + kCcAB, bl = bh + (uint32_t)bb;
-            const uint32_t idesc = tc::idesc_bf16(g.n_pad);
-#pragma unroll
-            for (int k = 0; k < kCcK / 16; k++) {
-                tc::mma_bf16(tmem, tc::sdesc(ah + k * 32), tc::sdesc(bh + k * 32), idesc, (kb | k) != 0);
-                tc::mma_bf16(tmem, tc::sdesc(ah + k * 32), tc::sdesc(bl + k * 32), idesc, 1u);
-                tc::mma_bf16(tmem, tc::sdesc(al + k * 32), tc::sdesc(bh + k * 32), idesc, 1u);
+    if (warp == 0) {
+        if (lane == 0) {
+            // producer: mask tiles, SB - 1 blocks ahead of the MMAs
+            int armed = 0;
+            for (int kb = 0; kb < n_kb; kb++) {
+                const int s = kb % SB;
+                if (!tc::mbar_wait(&emptyB[s], ((kb / SB) & 1) ^ 1, flags)) break;
+                tc::mbar_expect_tx(&fullB[s], 2u * (uint32_t)bb);
+                cc_bulk(ringB + (size_t)s * 2 * bb, g.m + (size_t)(kb0 + kb) * 2 * bb, 2u * (uint32_t)bb, &fullB[s]);
+                armed = kb + 1;
             }
-            tc::mma_commit(&empty[s]);
+            // the last copies issued must land before the CTA may exit
+            for (int kb = armed - 1; kb >= 0 && kb >= armed - SB; kb--)
+                tc::mbar_wait(&fullB[kb % SB], (kb / SB) & 1, flags);
         }
-        return true;
-    };
-    float a1[32];
-    for (int kb = 0; kb < n_kb; kb += 2) {
-        if (!step(kb, a, a1)) break;
-        if (kb + 1 < n_kb && !step(kb + 1, a1, a)) break;
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // MMA issuer
+            const uint32_t idesc = tc::idesc_bf16(g.n_pad);
+            for (int kb = 0; kb < n_kb; kb++) {
+                const int sa = kb % kCcSA, sb = kb % SB;
+                if (!tc::mbar_wait(&fullA[sa], (kb / kCcSA) & 1, flags)) break;
+                if (!tc::mbar_wait(&fullB[sb], (kb / SB) & 1, flags)) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t ah = tc::smem_u32(ringA + (size_t)sa * 2 * kCcAB), al = ah + kCcAB;
+                const uint32_t bh = tc::smem_u32(ringB + (size_t)sb * 2 * bb), bl = bh + (uint32_t)bb;
+#pragma unroll
+                for (int k = 0; k < kCcK / 16; k++) {
+                    tc::mma_bf16(tmem, tc::sdesc(ah + k * 32), tc::sdesc(bh + k * 32), idesc, (kb | k) != 0);
+                    tc::mma_bf16(tmem, tc::sdesc(ah + k * 32), tc::sdesc(bl + k * 32), idesc, 1u);
+                    tc::mma_bf16(tmem, tc::sdesc(al + k * 32), tc::sdesc(bh + k * 32), idesc, 1u);
+                }
+                tc::mma_commit(&emptyA[sa]);
+                tc::mma_commit(&emptyB[sb]);
+            }
+            tc::mma_commit(accum);          // arrives once every MMA issued above has completed
+        }
+    } else {
+        // splitters: spectrum row r, pixels 32 h .. 32 h + 31 of each K block
+        const int u = t - 64;
+        const int r = u & (kCcM - 1), half = u >> 7;
+        const bool row_on = s0 + r < g.n_spec;
+        const float* frow = g.spectra + (int64_t)(row_on ? s0 + r : 0) * g.n_px;
+        float a[32], a1[32];
+        cc_load_row(a, frow, row_on, g.vec4, P0 + 32 * half, P1);
+        auto split = [&](int kb, float (&cur)[32], float (&nxt)[32]) -> bool {
+            if (kb + 1 < n_kb) cc_load_row(nxt, frow, row_on, g.vec4, P0 + (int64_t)(kb + 1) * kCcK + 32 * half, P1);
+            const int sa = kb % kCcSA;
+            if (!tc::mbar_wait(&emptyA[sa], ((kb / kCcSA) & 1) ^ 1, flags)) return false;
+            unsigned char* st = ringA + (size_t)sa * 2 * kCcAB;
+#pragma unroll
+            for (int q = 0; q < 4; q++) cc_put8(st, st + kCcAB, cc_sw128(r, 4 * half + q), cur + 8 * q);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");     // visible to the tensor cores
+            cc_mbar_arrive(&fullA[sa]);
+            return true;
+        };
+        for (int kb = 0; kb < n_kb; kb += 2) {
+            if (!split(kb, a, a1)) break;
+            if (kb + 1 < n_kb && !split(kb + 1, a1, a)) break;
+        }
     }
-    asm volatile("cp.async.wait_group 0;" ::: "memory");     // no copy outlives the CTA
 
-    // accumulator complete (every MMA issued above has finished) before it is read or released
-    if (t == 0) tc::mma_commit(accum);            // n_kb >= 1: at least one block was issued
-    bool done = tc::mbar_wait(accum, 0, flags) && ok;
-    done = __syncthreads_and(done);
+    // accumulator complete before it is read or released (every MMA issued has finished)
+    bool done = true;
+    if (warp >= 2) done = __all_sync(0xffffffffu, tc::mbar_wait(accum, 0, flags));
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (done) {
+    if (warp >= 2 && done) {
         // warp w: TMEM lanes 32 (w & 3) .. +31 (its spectra), column blocks of 32 alternating
-        // between the two warp groups (its velocities)
+        // between the two groups of four warps (its velocities)
         const int lg = warp & 3;
-        const int sp = s0 + 32 * lg + (t & 31);
+        const int sp = s0 + 32 * lg + lane;
+        const int grp = (warp - 2) >> 2;
 #pragma unroll 1
-        for (int c = 32 * (warp >> 2); c < g.n_pad; c += 64) {
+        for (int c = 32 * grp; c < g.n_pad; c += 64) {
             float v[32];
             tc::tmem_ld32(tmem + ((uint32_t)(32 * lg) << 16) + (uint32_t)c, v);
             if (sp < g.n_spec) {
@@ -305,7 +336,7 @@ k_ccf_tc(const __grid_constant__ CcArgs g, unsigned int* flags) {
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) {
+    if (warp == 1) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(g.tmem_cols) : "memory");
     }
@@ -313,7 +344,7 @@ k_ccf_tc(const __grid_constant__ CcArgs g, unsigned int* flags) {
 
 bool ccf_tc_fits(int n_v) {
     const int n_pad = (n_v + 15) / 16 * 16;
-    return n_v >= 1 && n_v <= kCcMaxV && cc_smem(n_pad) <= 227 * 1024;
+    return n_v >= 1 && n_v <= kCcMaxV && cc_sb(n_pad) >= 2 && cc_ws_smem(n_pad) <= 227 * 1024;
 }
 
 int64_t ccf_tc_chunk(int64_t n_px, int n_spec, int sms) {
@@ -367,10 +398,10 @@ soap_status ccf_tc(soap_ctx* c, const CcfState& st, const CcfPlan& p, const floa
     uint32_t cols = 32;
     while ((int)cols < n_pad) cols <<= 1;
     a.tmem_cols = cols;
-    const size_t smem = cc_smem(n_pad);
+    const size_t smem = cc_ws_smem(n_pad);
     SOAP_TRY(fit_dynamic_smem(k_ccf_tc, smem));
     dim3 grid((unsigned)((c->n_px + p.tc_chunk - 1) / p.tc_chunk), (unsigned)((p.n_spec + kCcM - 1) / kCcM));
-    k_ccf_tc<<<grid, kCcThreads, smem, c->stream>>>(a, c->flags);
+    k_ccf_tc<<<grid, kCcWsThreads, smem, c->stream>>>(a, c->flags);
     SOAP_LAUNCHED(c);
     return SOAP_OK;
 }
