@@ -13,8 +13,9 @@
 // 128-byte-swizzle K-major image of the block's shared-memory tile (hi tile, then lo tile).
 // k_ccf_tc: CTA = (chunk of pixels, tile of 128 spectra), one CTA per SM, warp-specialised (see
 // the kernel): one lane streams the mask tiles of each K block with a bulk copy into a ring of up
-// to four stages, eight warps split the spectra (loaded one block ahead into registers) into
-// their BF16 hi/lo stage, one lane issues the 12 MMAs of the block (M = 128, N = velocities
+// to four stages, another copies the block's FP32 spectra into the A stage with a TMA tensor copy
+// (16-byte aligned rows; otherwise they are loaded into registers), eight warps split them in
+// place into the BF16 hi/lo tiles, one lane issues the 12 MMAs of the block (M = 128, N = velocities
 // rounded up to 16, K = 16; F_hi M_hi + F_hi M_lo + F_lo M_hi) once both stages are full and
 // commits them to the barriers that free the stages.  The epilogue writes the chunk's FP32
 // partial CCF, which k_ccf_reduce adds over the chunks in a fixed order.  Every barrier wait is
@@ -30,7 +31,6 @@ namespace soap {
 constexpr int kCcM = 128;                  // spectra per CTA (TMEM lanes)
 constexpr int kCcK = 64;                   // pixels per K block: one 128-byte swizzle row of BF16
 constexpr int kCcThreads = 256;            // mask-matrix builder threads
-constexpr int kCcAB = kCcM * kCcK * 2;     // bytes of one half (hi or lo) of the spectra tile, 16 KB
 constexpr int kCcChunkMax = 2048;          // pixels per CTA at most (bounds the FP32 accumulation)
 // mask-matrix builder
 constexpr int kCcWin = 512;                // lines of a K block staged in shared memory (more: read directly)
@@ -164,6 +164,7 @@ struct CcArgs {
     int64_t chunk;            // pixels per chunk (a multiple of kCcK)
     int n_v, n_pad, n_spec;
     int vec4;                 // rows are 16-byte aligned: 16-byte loads
+    int ra;                   // spectrum rows an A stage holds (a multiple of 8, at most 128)
     uint32_t tmem_cols;
 };
 
@@ -186,22 +187,37 @@ __device__ __forceinline__ void cc_load_row(float (&a)[32], const float* frow, b
 
 // Warp-specialised form.  Warp 0, one lane: the mask tiles of K block kb, one bulk copy of both
 // halves into B stage kb mod SB (completion on fullB, transaction bytes).  Warps 2..9 (256
-// threads, two per spectrum row): the spectrum values of block kb split into the A stage
-// kb mod kCcSA (loaded one block ahead into registers), each thread then fences its writes for the
-// tensor cores and arrives on fullA.  Warp 1, one lane: when both stages are full, the 12 MMAs of
-// the block, committed to emptyA and emptyB, which free the stages for the copies and splits of
-// later blocks.  So the tensor cores, the copies and the splits of different K blocks overlap, the
-// mask tiles SB - 1 blocks ahead of the MMAs.
-constexpr int kCcWsThreads = 320;
-constexpr int kCcSA = 2;                   // A (spectra) stages
+// threads): the spectrum values of block kb split into the A stage kb mod SA, after which each
+// thread fences its writes for the tensor cores and arrives on fullA.  Warp 1, one lane: when both
+// stages are full, the 12 MMAs of the block, committed to emptyA and emptyB, which free the
+// stages for the copies and splits of later blocks.  So the tensor cores, the copies and the
+// splits of different K blocks overlap, the mask tiles SB - 1 blocks ahead of the MMAs.
+// The splitters take the spectrum values from one of two places:
+//  - TMA (16-byte aligned rows): warp 10, one lane, copies the FP32 block (128 rows x 64 px, rows
+//    past the last spectrum and pixels past the grid read as zero) into the A stage itself once
+//    the MMAs have released it (fullR); the splitters read it back (lanes along the pixels of two
+//    rows per warp access), agree on a named barrier that every value was read, and overwrite the
+//    stage with its BF16 hi/lo tiles.  No spectrum value passes through the load queues.
+//  - registers (any alignment): two threads per spectrum row load the row's values of block kb + 1
+//    while block kb is split, and write block kb once the MMAs have released its stage.
+constexpr int kCcWsThreads = 352;
+// A (spectra) stages: three when they are filled by TMA; two when the splitters load the values
+// through L1 themselves (the smaller ring leaves more of the SM's memory to L1)
+__host__ __device__ constexpr int cc_sa(bool tma) { return tma ? 3 : 2; }
+constexpr int kCcSAMax = 3;
 constexpr int kCcSBMax = 4;                // B (mask) stages at most
-__host__ __device__ inline int cc_sb(int n_pad) {
-    const long avail = 227L * 1024 - 1024 - 256 - (long)kCcSA * 2 * kCcAB;
+// An A stage holds ra rows (the spectra of the largest tile rounded up to 8, at most 128): the
+// hi tile's rows at 128 r, then the lo tile's at ra x 128 + 128 r.  The MMAs read 128 rows of
+// each; the rows from ra on hold other data (the lo tile, the next stage, the mask ring) and
+// only reach accumulator lanes of spectra the tile does not have, which are never read.
+__host__ __device__ inline int cc_ab(int ra) { return ra * kCcK * 2; }         // one half (hi or lo)
+__host__ __device__ inline int cc_sb(int n_pad, int ra, int sa) {
+    const long avail = 227L * 1024 - 1024 - 256 - (long)sa * 2 * cc_ab(ra);
     const long sb = avail / (2L * cc_bb(n_pad));
     return (int)(sb < kCcSBMax ? sb : kCcSBMax);
 }
-__host__ __device__ inline size_t cc_ws_smem(int n_pad) {
-    return (size_t)kCcSA * 2 * kCcAB + (size_t)cc_sb(n_pad) * 2 * cc_bb(n_pad) + 1024 + 256;
+__host__ __device__ inline size_t cc_ws_smem(int n_pad, int ra, int sa) {
+    return (size_t)sa * 2 * cc_ab(ra) + (size_t)cc_sb(n_pad, ra, sa) * 2 * cc_bb(n_pad) + 1024 + 256;
 }
 
 __device__ __forceinline__ void cc_mbar_arrive(uint64_t* bar) {
@@ -212,18 +228,30 @@ __device__ __forceinline__ void cc_bulk(void* dst, const void* src, uint32_t byt
                  ::"r"(tc::smem_u32(dst)), "l"(src), "r"(bytes), "r"(tc::smem_u32(bar))
                  : "memory");
 }
+// named barrier 1 over the 256 splitter threads: true when v holds in every one of them
+__device__ __forceinline__ bool cc_split_all(bool v) {
+    uint32_t r;
+    asm volatile("{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbarrier.red.and.pred q, 1, 256, p;\n\t"
+                 "selp.u32 %0, 1, 0, q;\n\t}"
+                 : "=r"(r) : "r"((uint32_t)v) : "memory");
+    return r != 0;
+}
 
+template <bool kTmaA>
 __global__ void __launch_bounds__(kCcWsThreads, 1)
-k_ccf_tc(const __grid_constant__ CcArgs g, unsigned int* flags) {
+k_ccf_tc(const __grid_constant__ CcArgs g, const __grid_constant__ CUtensorMap map_f, unsigned int* flags) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
     const int bb = cc_bb(g.n_pad);
-    const int SB = cc_sb(g.n_pad);
-    unsigned char* ringA = base;                                   // [kCcSA][hi, lo][128 x 128 B]
-    unsigned char* ringB = ringA + kCcSA * 2 * kCcAB;              // [SB][hi, lo][n_pad x 128 B]
+    const int ab = cc_ab(g.ra);
+    constexpr int SA = cc_sa(kTmaA);
+    const int SB = cc_sb(g.n_pad, g.ra, SA);
+    unsigned char* ringA = base;                                   // [SA][hi, lo][ra x 128 B]
+    unsigned char* ringB = ringA + SA * 2 * ab;                    // [SB][hi, lo][n_pad x 128 B]
     uint64_t* fullA = reinterpret_cast<uint64_t*>(ringB + (size_t)SB * 2 * bb);
-    uint64_t* emptyA = fullA + kCcSA;
-    uint64_t* fullB = emptyA + kCcSA;
+    uint64_t* emptyA = fullA + kCcSAMax;
+    uint64_t* fullR = emptyA + kCcSAMax;
+    uint64_t* fullB = fullR + kCcSAMax;
     uint64_t* emptyB = fullB + kCcSBMax;
     uint64_t* accum = emptyB + kCcSBMax;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
@@ -235,7 +263,11 @@ k_ccf_tc(const __grid_constant__ CcArgs g, unsigned int* flags) {
     const int s0 = blockIdx.y * kCcM;
 
     if (t == 0) {
-        for (int s = 0; s < kCcSA; s++) { tc::mbar_init(&fullA[s], 256); tc::mbar_init(&emptyA[s], 1); }
+        for (int s = 0; s < SA; s++) {
+            tc::mbar_init(&fullA[s], 256);
+            tc::mbar_init(&emptyA[s], 1);
+            tc::mbar_init(&fullR[s], 1);
+        }
         for (int s = 0; s < SB; s++) { tc::mbar_init(&fullB[s], 1); tc::mbar_init(&emptyB[s], 1); }
         tc::mbar_init(accum, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -265,16 +297,30 @@ k_ccf_tc(const __grid_constant__ CcArgs g, unsigned int* flags) {
             for (int kb = armed - 1; kb >= 0 && kb >= armed - SB; kb--)
                 tc::mbar_wait(&fullB[kb % SB], (kb / SB) & 1, flags);
         }
+    } else if (warp == 10) {
+        if (kTmaA && lane == 0) {
+            // producer: FP32 spectrum blocks (ra rows) into the A stages the MMAs have released
+            int armed = 0;
+            for (int kb = 0; kb < n_kb; kb++) {
+                const int s = kb % SA;
+                if (!tc::mbar_wait(&emptyA[s], ((kb / SA) & 1) ^ 1, flags)) break;
+                tc::mbar_expect_tx(&fullR[s], 2u * (uint32_t)ab);
+                tc::tma_load_2d(ringA + (size_t)s * 2 * ab, &map_f, (int)(P0 + (int64_t)kb * kCcK), s0, &fullR[s]);
+                armed = kb + 1;
+            }
+            for (int kb = armed - 1; kb >= 0 && kb >= armed - SA; kb--)
+                tc::mbar_wait(&fullR[kb % SA], (kb / SA) & 1, flags);
+        }
     } else if (warp == 1) {
         if (lane == 0) {
             // MMA issuer
             const uint32_t idesc = tc::idesc_bf16(g.n_pad);
             for (int kb = 0; kb < n_kb; kb++) {
-                const int sa = kb % kCcSA, sb = kb % SB;
-                if (!tc::mbar_wait(&fullA[sa], (kb / kCcSA) & 1, flags)) break;
+                const int sa = kb % SA, sb = kb % SB;
+                if (!tc::mbar_wait(&fullA[sa], (kb / SA) & 1, flags)) break;
                 if (!tc::mbar_wait(&fullB[sb], (kb / SB) & 1, flags)) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t ah = tc::smem_u32(ringA + (size_t)sa * 2 * kCcAB), al = ah + kCcAB;
+                const uint32_t ah = tc::smem_u32(ringA + (size_t)sa * 2 * ab), al = ah + (uint32_t)ab;
                 const uint32_t bh = tc::smem_u32(ringB + (size_t)sb * 2 * bb), bl = bh + (uint32_t)bb;
 #pragma unroll
                 for (int k = 0; k < kCcK / 16; k++) {
@@ -287,8 +333,37 @@ k_ccf_tc(const __grid_constant__ CcArgs g, unsigned int* flags) {
             }
             tc::mma_commit(accum);          // arrives once every MMA issued above has completed
         }
+    } else if (kTmaA) {
+        // splitters on the staged block: warp w' = warp - 2 takes rows 16 w' .. 16 w' + 15, two
+        // rows per access (lanes 0-15 and 16-31), four pixels per lane
+        const int w8 = warp - 2, j = lane & 15;
+        for (int kb = 0; kb < n_kb; kb++) {
+            const int sa = kb % SA;
+            const bool ok = tc::mbar_wait(&fullR[sa], (kb / SA) & 1, flags);
+            unsigned char* st = ringA + (size_t)sa * 2 * ab;
+            float4 v[8];
+#pragma unroll
+            for (int i = 0; i < 8; i++) {
+                const int r = 16 * w8 + 2 * i + (lane >> 4);
+                if (r < g.ra) v[i] = *reinterpret_cast<const float4*>(st + r * (kCcK * 4) + j * 16);
+            }
+            if (!cc_split_all(ok)) break;                  // every value of the stage read (or a wait gave up)
+#pragma unroll
+            for (int i = 0; i < 8; i++) {
+                const int r = 16 * w8 + 2 * i + (lane >> 4);
+                if (r >= g.ra) continue;
+                uint2 hw, lw;
+                cc_split2(v[i].x, v[i].y, hw.x, lw.x);
+                cc_split2(v[i].z, v[i].w, hw.y, lw.y);
+                const uint32_t off = cc_sw128(r, j >> 1) + (uint32_t)(j & 1) * 8;
+                *reinterpret_cast<uint2*>(st + off) = hw;
+                *reinterpret_cast<uint2*>(st + ab + off) = lw;
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");     // visible to the tensor cores
+            cc_mbar_arrive(&fullA[sa]);
+        }
     } else {
-        // splitters: spectrum row r, pixels 32 h .. 32 h + 31 of each K block
+        // splitters from registers: spectrum row r, pixels 32 h .. 32 h + 31 of each K block
         const int u = t - 64;
         const int r = u & (kCcM - 1), half = u >> 7;
         const bool row_on = s0 + r < g.n_spec;
@@ -297,11 +372,13 @@ k_ccf_tc(const __grid_constant__ CcArgs g, unsigned int* flags) {
         cc_load_row(a, frow, row_on, g.vec4, P0 + 32 * half, P1);
         auto split = [&](int kb, float (&cur)[32], float (&nxt)[32]) -> bool {
             if (kb + 1 < n_kb) cc_load_row(nxt, frow, row_on, g.vec4, P0 + (int64_t)(kb + 1) * kCcK + 32 * half, P1);
-            const int sa = kb % kCcSA;
-            if (!tc::mbar_wait(&emptyA[sa], ((kb / kCcSA) & 1) ^ 1, flags)) return false;
-            unsigned char* st = ringA + (size_t)sa * 2 * kCcAB;
+            const int sa = kb % SA;
+            if (!tc::mbar_wait(&emptyA[sa], ((kb / SA) & 1) ^ 1, flags)) return false;
+            unsigned char* st = ringA + (size_t)sa * 2 * ab;
+            if (r < g.ra) {
 #pragma unroll
-            for (int q = 0; q < 4; q++) cc_put8(st, st + kCcAB, cc_sw128(r, 4 * half + q), cur + 8 * q);
+                for (int q = 0; q < 4; q++) cc_put8(st, st + ab, cc_sw128(r, 4 * half + q), cur + 8 * q);
+            }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");     // visible to the tensor cores
             cc_mbar_arrive(&fullA[sa]);
             return true;
@@ -313,10 +390,11 @@ k_ccf_tc(const __grid_constant__ CcArgs g, unsigned int* flags) {
     }
 
     // accumulator complete before it is read or released (every MMA issued has finished)
+    const bool epi = warp >= 2 && warp < 10;
     bool done = true;
-    if (warp >= 2) done = __all_sync(0xffffffffu, tc::mbar_wait(accum, 0, flags));
+    if (epi) done = __all_sync(0xffffffffu, tc::mbar_wait(accum, 0, flags));
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (warp >= 2 && done) {
+    if (epi && done) {
         // warp w: TMEM lanes 32 (w & 3) .. +31 (its spectra), column blocks of 32 alternating
         // between the two groups of four warps (its velocities)
         const int lg = warp & 3;
@@ -344,7 +422,9 @@ k_ccf_tc(const __grid_constant__ CcArgs g, unsigned int* flags) {
 
 bool ccf_tc_fits(int n_v) {
     const int n_pad = (n_v + 15) / 16 * 16;
-    return n_v >= 1 && n_v <= kCcMaxV && cc_sb(n_pad) >= 2 && cc_ws_smem(n_pad) <= 227 * 1024;
+    for (int sa = 2; sa <= kCcSAMax; sa++)
+        if (cc_sb(n_pad, kCcM, sa) < 2 || cc_ws_smem(n_pad, kCcM, sa) > 227 * 1024) return false;
+    return n_v >= 1 && n_v <= kCcMaxV;
 }
 
 int64_t ccf_tc_chunk(int64_t n_px, int n_spec, int sms) {
@@ -398,10 +478,23 @@ soap_status ccf_tc(soap_ctx* c, const CcfState& st, const CcfPlan& p, const floa
     uint32_t cols = 32;
     while ((int)cols < n_pad) cols <<= 1;
     a.tmem_cols = cols;
-    const size_t smem = cc_ws_smem(n_pad);
-    SOAP_TRY(fit_dynamic_smem(k_ccf_tc, smem));
+    a.ra = (int)std::min<int64_t>(kCcM, ((int64_t)p.n_spec + 7) / 8 * 8);
     dim3 grid((unsigned)((c->n_px + p.tc_chunk - 1) / p.tc_chunk), (unsigned)((p.n_spec + kCcM - 1) / kCcM));
-    k_ccf_tc<<<grid, kCcWsThreads, smem, c->stream>>>(a, c->flags);
+    CUtensorMap map_f{};
+    if (a.vec4 && c->n_px < INT_MAX && p.n_spec < INT_MAX) {
+        // spectra [n_spec][n_px] FP32, boxes of ra rows x 64 pixels
+        const uint64_t dims[2] = {(uint64_t)c->n_px, (uint64_t)p.n_spec};
+        const uint64_t strides[1] = {(uint64_t)c->n_px * 4};
+        const uint32_t box[2] = {(uint32_t)kCcK, (uint32_t)a.ra};
+        SOAP_TRY(tc::encode_map(&map_f, 2, spectra, dims, strides, box, CU_TENSOR_MAP_DATA_TYPE_FLOAT32));
+        const size_t smem = cc_ws_smem(n_pad, a.ra, cc_sa(true));
+        SOAP_TRY(fit_dynamic_smem(k_ccf_tc<true>, smem));
+        k_ccf_tc<true><<<grid, kCcWsThreads, smem, c->stream>>>(a, map_f, c->flags);
+    } else {
+        const size_t smem = cc_ws_smem(n_pad, a.ra, cc_sa(false));
+        SOAP_TRY(fit_dynamic_smem(k_ccf_tc<false>, smem));
+        k_ccf_tc<false><<<grid, kCcWsThreads, smem, c->stream>>>(a, map_f, c->flags);
+    }
     SOAP_LAUNCHED(c);
     return SOAP_OK;
 }

@@ -42,7 +42,7 @@ static soap_status make_map(CUtensorMap* map, const void* base, int64_t rows, in
 }
 
 soap_status encode_map(CUtensorMap* map, int rank, const void* base, const uint64_t* dims,
-                       const uint64_t* strides, const uint32_t* box) {
+                       const uint64_t* strides, const uint32_t* box, CUtensorMapDataType dt) {
     auto fn = encode_fn();
     if (!fn) { set_error("cuTensorMapEncodeTiled is not available from the driver"); return SOAP_ECUDA; }
     if (rank < 1 || rank > 5 || (reinterpret_cast<uintptr_t>(base) & 15)) {
@@ -58,7 +58,7 @@ soap_status encode_map(CUtensorMap* map, int rank, const void* base, const uint6
         estr[i] = 1;
         if (i + 1 < rank) st[i] = (cuuint64_t)strides[i];
     }
-    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank, const_cast<void*>(base), d, st, bx, estr,
+    CUresult r = fn(map, dt, (cuuint32_t)rank, const_cast<void*>(base), d, st, bx, estr,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) { set_error("cuTensorMapEncodeTiled failed (%d)", (int)r); return SOAP_ECUDA; }

@@ -318,10 +318,11 @@ k_gemm_tn(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUt
     }
 }
 
-// Tiled tensor map of a BF16 tensor without swizzle: dims[0] innermost (elements), strides in bytes
-// of dims 1 .. rank-1, box in elements.  Zero fill outside the tensor.
+// Tiled tensor map without swizzle (BF16 elements unless dt says otherwise): dims[0] innermost
+// (elements), strides in bytes of dims 1 .. rank-1, box in elements.  Zero fill outside the tensor.
 soap_status encode_map(CUtensorMap* map, int rank, const void* base, const uint64_t* dims,
-                       const uint64_t* strides, const uint32_t* box);
+                       const uint64_t* strides, const uint32_t* box,
+                       CUtensorMapDataType dt = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
 
 // C = epilogue(A B^T): A [M][K] (row stride lda), B [N][K] (row stride ldb), BF16, device, with
 // 16-byte aligned bases and strides that are multiples of 8 elements.  Asynchronous on `st`.
