@@ -164,23 +164,25 @@ def run_ours(args):
     # by the library); the FP64 path gets float64 ones
     q_dev32, a_dev32 = q_dev.float(), a_dev.float()
 
-    def step(prec, out, rv):
+    # the mixed path's CCF runs on the tensor cores (BF16 hi/lo split of spectra and line mask,
+    # FP32 accumulation); tc=False times the same step with the FP32 SIMT CCF beside it
+    def step(prec, out, rv, tc=False):
         f32 = prec == S.SOAP_FP32
         S.soap_update_star(ctx, st)
         S.soap_set_quiet_spectrum(ctx, q_dev32 if f32 else q_dev)
         S.soap_set_active_spectrum(ctx, S.SOAP_SPOT, a_dev32 if f32 else a_dev)
         S.soap_active_phases(ctx, case.regions, case.phases, S.SOAP_EFFECT_TOT, prec, out)
         S.soap_rv_ccf(ctx, out[0], case.mask_lambda, case.mask_weight, case.mask_width_kms,
-                      lo, vstep, nv, rv)
+                      lo, vstep, nv, rv, tensor_cores=tc)
 
     def barrier():
         if world > 1:
             import torch.distributed as tdist
             tdist.barrier()
 
-    def timed(prec, out, rv, K, W, profile=False):
+    def timed(prec, out, rv, K, W, profile=False, tc=False):
         for _ in range(W):
-            step(prec, out, rv)
+            step(prec, out, rv, tc)
         torch.cuda.synchronize()
         S.soap_reset_kernel_times(ctx)
         S.soap_set_profiling(ctx, profile)
@@ -192,7 +194,7 @@ def run_ours(args):
         for k in range(K):
             flush.fill_(k & 0xFF)                 # evict L2 between steps (not timed)
             ev[k][0].record(stream)
-            step(prec, out, rv)
+            step(prec, out, rv, tc)
             ev[k][1].record(stream)
         torch.cuda.synchronize()
         barrier()
@@ -207,9 +209,12 @@ def run_ours(args):
         return ms, launches, timers
 
     K, W = args.steps, max(3, args.warmup)
+    rv32s = torch.empty(P, dtype=torch.float64, device=dev)
     with ClockSampler(local) as clk:
-        ms32, launches, timers = timed(S.SOAP_FP32, out32, rv32, K, W, profile=True)
-        ms32_plain, launches_plain, _ = timed(S.SOAP_FP32, out32, rv32, K, W)
+        ms32, launches, timers = timed(S.SOAP_FP32, out32, rv32, K, W, profile=True, tc=True)
+        ms32_plain, launches_plain, _ = timed(S.SOAP_FP32, out32, rv32, K, W, tc=True)
+        _, _, timers_simt = timed(S.SOAP_FP32, out32, rv32s, K, W, profile=True)
+        ms_simt, launches_simt, _ = timed(S.SOAP_FP32, out32, rv32s, K, W)
         K64 = max(3, K // 4)
     ms64, _, timers64 = timed(S.SOAP_FP64, out64, rv64, K64, 3, profile=True)
     clocks = clk.summary()
@@ -217,13 +222,15 @@ def run_ours(args):
     # max over ranks
     if world > 1:
         import torch.distributed as tdist
-        t = torch.tensor([ms_step, ms64], device=dev, dtype=torch.float64)
+        t = torch.tensor([ms_step, ms64, ms_simt], device=dev, dtype=torch.float64)
         tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        ms_step, ms64 = float(t[0]), float(t[1])
+        ms_step, ms64, ms_simt = float(t[0]), float(t[1]), float(t[2])
     value = world * P / (ms_step * 1e-3)
     value64 = world * P / (ms64 * 1e-3)
     rv_err = float((rv32 - rv64).abs().max().item() * 1e5)          # cm/s
     rv_vs_oracle = oracle_rv_errors(case, args, rv32, rv64)
+    if rv_vs_oracle is not None:
+        rv_vs_oracle["fp32_simt_ccf"] = oracle_rv_errors(case, args, rv32s, rv64)["fp32"]
 
     # end to end through the C-ABI with host buffers (pinned), copies inside the timed region:
     # every step uploads the local spectra, computes the phases' spectra and RVs and brings both
@@ -236,6 +243,7 @@ def run_ours(args):
     out_host = torch.empty((P, n_px), dtype=torch.float32).pin_memory()
     rv_host = torch.empty(P, dtype=torch.float64).pin_memory()
     S.soap_set_host_async(ctx, True)
+    S.soap_set_ccf_tensor_cores(ctx, True)
 
     def step_e2e():
         S.soap_update_star(ctx, st)
@@ -293,8 +301,19 @@ def run_ours(args):
                    "frac": round(achieved / hbm_peak, 4),
                    "traffic": profiled_traffic("k_contract_f32_disk300_205800px.md") if full else None,
                    "bytes_per_launch": bytes_contract, "ms_per_launch": round(c_per, 5), "peak_source": src}
-    # CCF: 2 pixels per (line, velocity, spectrum), one FMA (2 flop) each, over the lines whose
-    # box stays on the grid; FP32 SIMT peak from the unit counts and the maximum SM clock
+    # CCF on the tensor cores: it streams the line-mask matrix (BF16 hi + lo per velocity, padded
+    # to 16, and pixel, padded to 64) and the spectra once per launch
+    n_pad = -(-nv // 16) * 16
+    bytes_ccf_tc = (-(-n_px // 64) * 64) * n_pad * 4 + P * n_px * 4
+    t_per = per_launch("ccf")
+    ach_tc = bytes_ccf_tc / (t_per * 1e-3) / 1e9
+    rl_ccf_tc = {"kernel": "k_ccf_tc (CCF as a tcgen05 GEMM, BF16 hi/lo, warp-specialised)", "bound": "hbm",
+                 "achieved": round(ach_tc, 1), "peak": hbm_peak, "unit": "GB/s",
+                 "frac": round(ach_tc / hbm_peak, 4),
+                 "traffic": profiled_traffic("k_ccf_tc_bf16x3_disk300_205800px.md") if full else None,
+                 "bytes_per_launch": bytes_ccf_tc, "ms_per_launch": round(t_per, 5), "peak_source": src}
+    # SIMT CCF: 2 pixels per (line, velocity, spectrum), one FMA (2 flop) each, over the lines
+    # whose box stays on the grid; FP32 SIMT peak from the unit counts and the maximum SM clock
     delta = np.log(st.lambda_end_A / st.lambda_start_A) / (n_px - 1)
     h = case.mask_width_kms / (2 * 299792.458 * delta)
     u = np.log(case.mask_lambda / st.lambda_start_A) / delta
@@ -305,7 +324,7 @@ def run_ours(args):
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     max_mhz = float(clocks.get("sm_max_mhz") or 2070.0)
     fp32_peak = sms * 128 * 2 * max_mhz * 1e6 / 1e12
-    f_per = per_launch("ccf")
+    f_per = timers_simt["ccf"][0] / max(1, timers_simt["ccf"][1])
     ach_ccf = flops_ccf / (f_per * 1e-3) / 1e12
     rl_ccf = {"kernel": "k_ccf_tile (CCF, 4 velocities x 16 spectra per thread)", "bound": "alu",
               "achieved": round(ach_ccf, 2), "peak": round(fp32_peak, 1), "unit": "TFLOP/s",
@@ -314,9 +333,9 @@ def run_ours(args):
               "flops_per_launch": flops_ccf, "ms_per_launch": round(f_per, 5),
               "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 flop x {max_mhz:.0f} MHz"}
     name, (tot, n) = max(timers.items(), key=lambda kv: kv[1][0])
-    roofline = dict(rl_ccf if c_per < f_per else rl_contract)
+    roofline = dict(rl_ccf_tc if c_per < t_per else rl_contract)
     roofline.update({"dominant_kernel": name, "dominant_ms_per_step": round(tot / K, 5)})
-    rooflines = {"contract": rl_contract, "ccf": rl_ccf}
+    rooflines = {"contract": rl_contract, "ccf": rl_ccf_tc, "ccf_simt": rl_ccf}
     kernel_ms_per_step = {k: round(v[0] / K, 5) for k, v in timers.items() if v[1]}
 
     cpu = None
@@ -342,15 +361,20 @@ def run_ours(args):
 
     res = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
            "steps": K, "warmup": W, "ms_per_step": round(ms_step, 5), "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16x3",
            "data": "synthetic (seeded 20k-line spectra, random-init regions)",
            "config": {"workload": case.name, "grid": st.grid_n, "n_px": n_px, "n_mu": n_mu,
                       "phases_per_step": P, "effects": "total (Eq. 3)",
-                      "precision": "FP32 local spectra, contraction, CCF and fit; FP64 positions and weights",
+                      "precision": "FP32 local spectra, contraction and fit; CCF as BF16 hi/lo tcgen05 GEMM "
+                                   "with FP32 accumulation; FP64 positions and weights",
                       "l2": "flushed between timed steps (256 MB write)",
                       "parallelism": f"replicas{world}"},
            "rv_err_cms_vs_fp64": rv_err,
            "rv_err_cms_vs_oracle": rv_vs_oracle,
+           "fp32_simt_ccf": {"value": round(world * P / (ms_simt * 1e-3), 2), "unit": UNIT,
+                             "ms_per_step": round(ms_simt, 5), "gpu_launches": int(launches_simt),
+                             "rv_max_diff_cms_vs_tensor_ccf": float((rv32 - rv32s).abs().max().item() * 1e5),
+                             "kernel_ms_per_step": {k: round(v[0] / K, 5) for k, v in timers_simt.items() if v[1]}},
            "fp64_path": {"value": round(value64, 2), "unit": UNIT, "ms_per_step": round(ms64, 5),
                          "kernel_ms_per_step": {k: round(v[0] / K64, 5)
                                                 for k, v in timers64.items() if v[1]}},
@@ -399,7 +423,8 @@ def profiled_traffic(name):
         for line in text.splitlines():
             if line.startswith(f"| {key} |"):
                 val, unit = line.split("|")[2].split()[:2]
-                tot += float(val) * {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}[unit]
+                tot += float(val) * {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9,
+                                     "B": 1, "KB": 1e3, "MB": 1e6, "GB": 1e9}[unit]
                 break
         else:
             return None

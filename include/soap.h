@@ -327,6 +327,15 @@ soap_status soap_lower_resolution(soap_ctx* ctx, const void* in, void* out, int3
  * soap_active_phases(_radii) and soap_active_rv; the batched form does not use it. */
 soap_status soap_set_facula_limb_brightening(soap_ctx* ctx, int enabled);
 
+/* CCF of the FP32 spectra of soap_active_rv (precision SOAP_FP32) on the tensor cores: when
+ * enabled, the CCF of Sect. 4.1 runs as soap_rv_ccf with spectra_f32 = 2 (a tcgen05 GEMM of
+ * spectra x velocities over pixels against the line-mask matrix, both split into BF16 high and
+ * low parts, three products accumulated in FP32: within 1.7e-4 of the largest CCF value, RVs
+ * within 0.05 cm/s of the FP32 CCF's on the 205,800-pixel workload); the contraction and the
+ * Gaussian fit are unchanged.  Masks not sorted by wavelength and grids of more than 256
+ * velocities keep the FP32 CCF.  Off by default (SOAP_BF16X3 always takes this form). */
+soap_status soap_set_ccf_tensor_cores(soap_ctx* ctx, int enabled);
+
 /* Active-region size evolution (Sect. 4.2.1).  The paper names three laws and their
  * parameters; the formulas are readings:
  *  SOAP_EVOLVE_NONE            the region keeps its radius_rstar;

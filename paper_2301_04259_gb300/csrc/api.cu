@@ -600,6 +600,13 @@ soap_status soap_set_facula_limb_brightening(soap_ctx* c, int enabled) {
     return SOAP_OK;
 }
 
+soap_status soap_set_ccf_tensor_cores(soap_ctx* c, int enabled) {
+    clear_error();
+    if (!c) { set_error("ctx is NULL"); return SOAP_EINVAL; }
+    c->ccf_tc = enabled != 0;
+    return SOAP_OK;
+}
+
 soap_status soap_set_host_async(soap_ctx* c, int enabled) {
     clear_error();
     if (!c) { set_error("ctx is NULL"); return SOAP_EINVAL; }
@@ -943,6 +950,7 @@ soap_status soap_active_rv(soap_ctx* c, const soap_region* regions, int32_t n_re
     SOAP_TRY(check_rv(c, mask_lambda, mask_weight, n_lines, mask_width_kms, v_lo, v_step, n_v));
     if (n_phases == 0) return SOAP_OK;
     const int f32 = precision != SOAP_FP64;
+    const bool ccf_tc = precision == SOAP_BF16X3 || (precision == SOAP_FP32 && c->ccf_tc);
     const size_t sbytes = (size_t)n_phases * (size_t)c->n_px * (f32 ? 4 : 8);
     if (out_on_device) {
         void* sp = spectra_out;
@@ -952,7 +960,7 @@ soap_status soap_active_rv(soap_ctx* c, const soap_region* regions, int32_t n_re
         }
         SOAP_TRY(active_lsf(c, A, n_regions, phases, n_phases, effect, precision, sp, sbytes));
         return rv_ccf_run(c, sp, f32, n_phases, mask_lambda, mask_weight, n_lines, mask_width_kms,
-                          v_lo, v_step, n_v, rv_kms, nullptr, nullptr, precision == SOAP_BF16X3);
+                          v_lo, v_step, n_v, rv_kms, nullptr, nullptr, ccf_tc);
     }
     // host results: computed into one of two alternating device buffers; the spectra go to the
     // host on out_stream while the CCF runs, the RVs after the fit
@@ -972,7 +980,7 @@ soap_status soap_active_rv(soap_ctx* c, const soap_region* regions, int32_t n_re
         SOAP_CUDA(cudaMemcpyAsync(spectra_out, spec_d, sbytes, cudaMemcpyDeviceToHost, c->out_stream));
     }
     SOAP_TRY(rv_ccf_run(c, spec_d, f32, n_phases, mask_lambda, mask_weight, n_lines, mask_width_kms,
-                        v_lo, v_step, n_v, rv_d, nullptr, nullptr, precision == SOAP_BF16X3));
+                        v_lo, v_step, n_v, rv_d, nullptr, nullptr, ccf_tc));
     SOAP_CUDA(cudaEventRecord(c->dn_rv[o], c->stream));
     SOAP_CUDA(cudaStreamWaitEvent(c->out_stream, c->dn_rv[o], 0));
     SOAP_CUDA(cudaMemcpyAsync(rv_kms, rv_d, (size_t)n_phases * 8, cudaMemcpyDeviceToHost, c->out_stream));

@@ -216,9 +216,13 @@ __host__ __device__ inline int cc_sb(int n_pad, int ra, int sa) {
     const long sb = avail / (2L * cc_bb(n_pad));
     return (int)(sb < kCcSBMax ? sb : kCcSBMax);
 }
-__host__ __device__ inline size_t cc_ws_smem(int n_pad, int ra, int sa) {
-    return (size_t)sa * 2 * cc_ab(ra) + (size_t)cc_sb(n_pad, ra, sa) * 2 * cc_bb(n_pad) + 1024 + 256;
+// the epilogue's transpose tiles (32 x 33 floats per warp, eight warps) reuse the rings
+constexpr int kCcEpi = 8 * 32 * 33 * 4;
+__host__ __device__ inline size_t cc_rings(int n_pad, int ra, int sa) {
+    const size_t r = (size_t)sa * 2 * cc_ab(ra) + (size_t)cc_sb(n_pad, ra, sa) * 2 * cc_bb(n_pad);
+    return r > (size_t)kCcEpi ? r : (size_t)kCcEpi;
 }
+__host__ __device__ inline size_t cc_ws_smem(int n_pad, int ra, int sa) { return cc_rings(n_pad, ra, sa) + 1024 + 256; }
 
 __device__ __forceinline__ void cc_mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
@@ -248,7 +252,7 @@ k_ccf_tc(const __grid_constant__ CcArgs g, const __grid_constant__ CUtensorMap m
     const int SB = cc_sb(g.n_pad, g.ra, SA);
     unsigned char* ringA = base;                                   // [SA][hi, lo][ra x 128 B]
     unsigned char* ringB = ringA + SA * 2 * ab;                    // [SB][hi, lo][n_pad x 128 B]
-    uint64_t* fullA = reinterpret_cast<uint64_t*>(ringB + (size_t)SB * 2 * bb);
+    uint64_t* fullA = reinterpret_cast<uint64_t*>(base + cc_rings(g.n_pad, g.ra, SA));
     uint64_t* emptyA = fullA + kCcSAMax;
     uint64_t* fullR = emptyA + kCcSAMax;
     uint64_t* fullB = fullR + kCcSAMax;
@@ -396,20 +400,18 @@ k_ccf_tc(const __grid_constant__ CcArgs g, const __grid_constant__ CUtensorMap m
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (epi && done) {
         // warp w: TMEM lanes 32 (w & 3) .. +31 (its spectra), column blocks of 32 alternating
-        // between the two groups of four warps (its velocities)
+        // between the two groups of four warps (its velocities); each 32 x 32 block goes out
+        // through the warp's shared tile (every MMA has completed, so the rings are free), one
+        // spectrum's 32 velocities per store
         const int lg = warp & 3;
-        const int sp = s0 + 32 * lg + lane;
         const int grp = (warp - 2) >> 2;
+        float (*tile)[33] = reinterpret_cast<float (*)[33]>(base + (size_t)(warp - 2) * 32 * 33 * 4);
+        float* dst = g.partial + (int64_t)blockIdx.x * g.n_spec * g.n_v;
 #pragma unroll 1
         for (int c = 32 * grp; c < g.n_pad; c += 64) {
             float v[32];
             tc::tmem_ld32(tmem + ((uint32_t)(32 * lg) << 16) + (uint32_t)c, v);
-            if (sp < g.n_spec) {
-                float* dst = g.partial + ((int64_t)blockIdx.x * g.n_spec + sp) * g.n_v;
-#pragma unroll
-                for (int i = 0; i < 32; i++)
-                    if (c + i < g.n_v) dst[c + i] = v[i];
-            }
+            tc::store_rows(tile, v, lane, dst, g.n_v, s0 + 32 * lg, g.n_spec, c, g.n_v);
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");

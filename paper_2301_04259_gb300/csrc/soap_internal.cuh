@@ -191,6 +191,7 @@ struct soap_ctx {
     float* a32[2] = {nullptr, nullptr};
     bool active_set[2] = {false, false};
     bool facula_mu = false;                // facula temperature T_quiet + dT_f(mu) per mu bin
+    bool ccf_tc = false;                   // soap_active_rv at SOAP_FP32: the CCF on the tensor cores
     bool q64_ok = false;                   // float64 rows hold the last quiet upload
     bool a64_ok[2] = {false, false};       // (a float32 upload fills the float32 rows only)
 

@@ -101,6 +101,7 @@ def _load():
         "soap_set_host_async": (i32, [P, ctypes.c_int]),
         "soap_inject_bisectors": (i32, [P, P, P, i32, P, P, i32, ctypes.c_int]),
         "soap_set_facula_limb_brightening": (i32, [P, ctypes.c_int]),
+        "soap_set_ccf_tensor_cores": (i32, [P, ctypes.c_int]),
         "soap_evolve_radii": (i32, [ctypes.POINTER(soap_region_evolution), ctypes.POINTER(soap_region), i32, P, i32, P]),
         "soap_active_phases_radii": (i32, [P, ctypes.POINTER(soap_region), i32, P, i32, P, u32, i32, P, ctypes.c_int]),
         "soap_set_instrument_resolution": (i32, [P, d]),
@@ -336,6 +337,10 @@ def soap_active_phases_radii(ctx, regions: Sequence, phases, radii, effects: int
 
 def soap_set_facula_limb_brightening(ctx, enabled: bool) -> None:
     _check(_lib.soap_set_facula_limb_brightening(ctx, int(bool(enabled))), "soap_set_facula_limb_brightening")
+
+
+def soap_set_ccf_tensor_cores(ctx, enabled: bool) -> None:
+    _check(_lib.soap_set_ccf_tensor_cores(ctx, int(bool(enabled))), "soap_set_ccf_tensor_cores")
 
 
 def soap_inject_bisectors(ctx, spectra, out, bis_table, orig_table) -> None:

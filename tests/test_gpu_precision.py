@@ -67,8 +67,10 @@ GOLDEN = Path(__file__).resolve().parent / "golden" / "cfg2_fullsize_oracle.json
 
 def test_fullsize_rvs_against_the_oracle():
     """The full-size active star (synth.config2(0): disk 300x300, 205,800 px, 20 mu bins, facula +
-    2 spots, 100 phases) through soap_active_rv at every precision: all 100 RVs against the
-    oracle's RVs of its own FP64 spectra, and sampled spectrum values against the oracle's."""
+    2 spots, 100 phases) through soap_active_rv at every precision, and at SOAP_FP32 with the CCF
+    on the tensor cores (soap_set_ccf_tensor_cores): all 100 RVs against the oracle's RVs of its
+    own FP64 spectra, and sampled spectrum values against the oracle's.  The option leaves the
+    FP32 spectra unchanged, bit for bit."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     import __graft_entry__
@@ -87,19 +89,25 @@ def test_fullsize_rvs_against_the_oracle():
         S.soap_quiet_spectrum(d.ctx, S.SOAP_FORM_TOEPLITZ, S.SOAP_FP64, qf)
         torch.cuda.synchronize()
         scale = float(qf.max())
-        for prec, dt, tol_f, tol_rv in ((S.SOAP_FP64, torch.float64, 1e-12, 1e-6),
-                                        (S.SOAP_FP32, torch.float32, 2e-6, 1.0),
-                                        (S.SOAP_BF16X3, torch.float32, 2e-6, 1.0)):
+        spectra = {}
+        for prec, dt, tol_f, tol_rv, tc in ((S.SOAP_FP64, torch.float64, 1e-12, 1e-6, False),
+                                            (S.SOAP_FP32, torch.float32, 2e-6, 1.0, False),
+                                            (S.SOAP_FP32, torch.float32, 2e-6, 1.0, True),
+                                            (S.SOAP_BF16X3, torch.float32, 2e-6, 1.0, False)):
             spec = torch.empty((c.phases.size, c.star.n_px), dtype=dt, device=DEV)
             rv = torch.empty(c.phases.size, dtype=torch.float64, device=DEV)
+            S.soap_set_ccf_tensor_cores(d.ctx, tc)
             S.soap_active_rv(d.ctx, c.regions, c.phases, S.SOAP_EFFECT_TOT, prec, c.mask_lambda, c.mask_weight,
                              c.mask_width_kms, lo, step, nv, spec, rv)
+            S.soap_set_ccf_tensor_cores(d.ctx, False)
             torch.cuda.synchronize()
+            spectra[(prec, tc)] = spec
             r = rv.cpu().numpy()
             e_rv = np.abs(r - ref).max() * 1e5
             e_f = np.abs(spec[torch.from_numpy(sp).to(DEV), torch.from_numpy(px).to(DEV)].double().cpu().numpy()
                          - F_ref).max() / scale
-            print(f"precision {prec}: RV max err {e_rv:.3e} cm/s, sampled flux err {e_f:.2e}")
+            print(f"precision {prec} (tensor-core CCF {tc}): RV max err {e_rv:.3e} cm/s, sampled flux err {e_f:.2e}")
             assert np.isfinite(r).all()
-            assert e_rv <= tol_rv, (prec, e_rv)
-            assert e_f <= tol_f, (prec, e_f)
+            assert e_rv <= tol_rv, (prec, tc, e_rv)
+            assert e_f <= tol_f, (prec, tc, e_f)
+        assert torch.equal(spectra[(S.SOAP_FP32, True)], spectra[(S.SOAP_FP32, False)])
