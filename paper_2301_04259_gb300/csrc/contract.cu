@@ -238,9 +238,11 @@ static soap_status tap_buffers(soap_ctx* c, int n_phases, int n_class, int PB, i
 // Quiet integral (Alg. 1) in FP32 from the quiet taps as aligned groups (build_taps_dev): a thread
 // owns 4 consecutive pixels; the taps of a group sit at row offsets 4q + e, e < 4, so their row
 // values for the 4 pixels are 8 values from 4q + m0, two aligned 16-byte loads.  Groups are taken
-// 4 at a time (all their loads issued before the first is applied); per pixel the taps are added
-// in table order, as in contract_tile (same results).
-__global__ void __launch_bounds__(128)
+// kQG at a time (all their loads issued before the first is applied: with ~50 groups and one
+// thread per 4 pixels, ~10 warps per SM, the kernel is bound by the number of load round trips);
+// per pixel the taps are added in table order, as in contract_tile (same results).
+constexpr int kQG = 8;
+__global__ void __launch_bounds__(128, 4)
 k_quiet_groups(int64_t n_px, const float* __restrict__ q, const TapGroup* __restrict__ grp,
                const int* __restrict__ gstart, const float* __restrict__ coef, float* __restrict__ out) {
     const int64_t m0 = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
@@ -248,27 +250,31 @@ k_quiet_groups(int64_t n_px, const float* __restrict__ q, const TapGroup* __rest
     const int n = gstart[1];
     const float* base = q + m0;
     float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    for (int i0 = 0; i0 < n; i0 += 4) {
-        TapGroup d[4];
-        float W[4][8];
+    for (int i0 = 0; i0 < n; i0 += kQG) {
+        TapGroup d[kQG];
+        float W[kQG][8];
 #pragma unroll
-        for (int j = 0; j < 4; j++) d[j] = grp[min(i0 + j, n - 1)];
+        for (int j = 0; j < kQG; j++) d[j] = grp[min(i0 + j, n - 1)];
 #pragma unroll
-        for (int j = 0; j < 4; j++) {
+        for (int j = 0; j < kQG; j++) {
             const float4 a = __ldg(reinterpret_cast<const float4*>(base + d[j].off4));
             const float4 b = __ldg(reinterpret_cast<const float4*>(base + d[j].off4) + 1);
             W[j][0] = a.x; W[j][1] = a.y; W[j][2] = a.z; W[j][3] = a.w;
             W[j][4] = b.x; W[j][5] = b.y; W[j][6] = b.z; W[j][7] = b.w;
         }
+        // selects instead of branches, so that no load is deferred to its use
 #pragma unroll
-        for (int j = 0; j < 4; j++) {
-            if (i0 + j >= n) break;
+        for (int j = 0; j < kQG; j++) {
+            const int mk = i0 + j < n ? d[j].mask : 0;
 #pragma unroll
             for (int e = 3; e >= 0; e--) {                     // offsets falling: table order
-                if (!(d[j].mask & (1 << e))) continue;
-                const float cv = __ldg(coef + d[j].tap0 - e);
+                const bool on = (mk >> e) & 1;
+                const float cv = on ? __ldg(coef + d[j].tap0 - e) : 0.0f;
 #pragma unroll
-                for (int r = 0; r < 4; r++) acc[r] = fmaf(cv, W[j][e + r], acc[r]);
+                for (int r = 0; r < 4; r++) {
+                    const float t = fmaf(cv, W[j][e + r], acc[r]);
+                    acc[r] = on ? t : acc[r];
+                }
             }
         }
     }

@@ -45,6 +45,27 @@ __device__ __forceinline__ int nearest_mu(double mu, int n_mu, const MuTable& mu
     return best;
 }
 
+// hist[key] += v for every lane with on set.  Lanes of a warp with equal keys in consecutive
+// lanes (neighbouring cells of a row mostly share their mu bin and velocity offset) are summed
+// first by a segmented scan, and the last lane of each run adds the run's sum: one shared-memory
+// atomic per run instead of one per cell.  The sums are integers, so the result is exact in any
+// order.  Every lane of the warp must call it.
+__device__ __forceinline__ void hist_add_runs(long long* hist, int key, unsigned long long v, bool on) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int k = on ? key : -1;
+    const int kprev = __shfl_up_sync(full, k, 1);
+    const int knext = __shfl_down_sync(full, k, 1);
+    int start = (lane == 0 || kprev != k) ? lane : 0;          // first lane of this lane's run
+    for (int o = 1; o < 32; o <<= 1) start = max(start, __shfl_up_sync(full, start, o));
+    unsigned long long sum = on ? v : 0ull;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long t = __shfl_up_sync(full, sum, o);
+        if (lane - o >= start) sum += t;
+    }
+    if (on && (lane == 31 || knext != k)) atomicAdd((unsigned long long*)&hist[k], sum);
+}
+
 // One block per (row j, 128 columns).  Besides the geometry it stores, per cell, the two
 // fixed-point contributions fx(I (1-w)) and fx(I w) of its two-tap kernel (reused by every
 // phase), an FP32 copy of mu (for the FP32 membership pre-test), and adds the cell to the quiet
@@ -70,6 +91,9 @@ k_geometry(int N, double vsini, double sin_i, double cos_i, double alpha, double
     __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long sumI = 0, cnt = 0;
+    int hkey = 0;                                      // the cell's (bin, tap) entry and its two taps
+    unsigned long long hk0 = 0, hk1 = 0;
+    bool hon = false;
     if (i < N) {
         const int64_t c = (int64_t)j * N + i;
         const double x = cell_x[i];                                        // (2 i + 1 - N) / N
@@ -99,13 +123,16 @@ k_geometry(int N, double vsini, double sin_i, double cos_i, double alpha, double
             const long long k1 = __double2ll_rn(I * w * scale);
             cell_I[c] = I; cell_w[c] = w; cell_mu[c] = mu; cell_mu32[c] = (float)mu;
             cell_j[c] = jt; cell_bin[c] = best; cell_k0[c] = k0; cell_k1[c] = k1;
-            const int kk = jt - tap_min;
-            atomicAdd((unsigned long long*)&hist[best * n_taps + kk], (unsigned long long)k0);
-            atomicAdd((unsigned long long*)&hist[best * n_taps + kk - 1], (unsigned long long)k1);
+            hkey = best * n_taps + (jt - tap_min);
+            hk0 = (unsigned long long)k0;
+            hk1 = (unsigned long long)k1;
+            hon = true;
             sumI = (unsigned long long)__double2ll_rn(I * scale);
             cnt = 1;
         }
     }
+    hist_add_runs(hist, hkey, hk0, hon);
+    hist_add_runs(hist, hkey - 1, hk1, hon);
     for (int o = 16; o > 0; o >>= 1) {
         sumI += __shfl_down_sync(0xffffffffu, sumI, o);
         cnt += __shfl_down_sync(0xffffffffu, cnt, o);
