@@ -20,12 +20,29 @@ namespace soap {
 
 struct MuTable {
     double v[SOAP_MAX_MU];
+    float mid[SOAP_MAX_MU];   // (mu_b + mu_b+1) / 2 rounded to float (used when fast32 is set)
+    int fast32;               // strictly increasing, neighbours at least 1e-4 apart
 };
 
 // Nearest tabulated mu, ties to the lower index, as the first minimum of |mu - mu_b| in FP64.
 // For a strictly increasing table the minimum lies next to the insertion point, so only a
-// window around it is scanned (same answer as the full scan).
+// window around it is scanned (same answer as the full scan).  With fast32 the bin is first
+// read off the FP32 midpoints: mu and the midpoints are within 6e-8 of their float roundings,
+// so a float mu farther than 1e-6 from both midpoints around it lies on the same sides of the
+// exact midpoints, where the FP64 comparison decides the same bin (the FP64 pipe is the
+// geometry kernel's limit, the FP32 compares cost nothing); closer ones take the FP64 path.
 __device__ __forceinline__ int nearest_mu(double mu, int n_mu, const MuTable& mus, int sorted) {
+    if (mus.fast32) {
+        const float mf = __double2float_rn(mu);
+        int lo = 0, hi = n_mu - 1;              // number of midpoints below mf
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (mus.mid[mid] < mf) lo = mid + 1; else hi = mid;
+        }
+        const bool near = (lo > 0 && fabsf(mf - mus.mid[lo - 1]) < 1e-6f) ||
+                          (lo < n_mu - 1 && fabsf(mf - mus.mid[lo]) < 1e-6f);
+        if (!near) return lo;
+    }
     int b0 = 0, b1 = n_mu - 1;
     if (sorted) {
         int lo = 0, hi = n_mu;                  // first index with mu_b >= mu
@@ -108,7 +125,8 @@ k_geometry(int N, double vsini, double sin_i, double cos_i, double alpha, double
             const double om = 1.0 - mu;
             const double I = area * (1.0 - u1 * om - u2 * om * om);      // quadratic limb darkening
             const double slat = y * sin_i + mu * cos_i;                    // sin(latitude) of the cell
-            const double v = vsini * x * (1.0 + alpha * slat * slat);      // x > 0 recedes
+            // x > 0 recedes; rigid rotation (alpha = 0) skips the latitude term, 1 + 0 s^2 = 1 exactly
+            const double v = alpha != 0.0 ? vsini * x * (1.0 + alpha * slat * slat) : vsini * x;
             const double beta = v * inv_c;
             const double ab = SERIES ? atanh_small(beta) : atanh(beta);    // ln D
             const double jd = ceil(ab * inv_delta);                        // j = ceil(s), s = ln D / Delta
@@ -302,6 +320,11 @@ soap_status pad_rows32(soap_ctx* c, const float* src, float* dst32, int rows) {
 soap_status geometry_init(soap_ctx* c) {
     MuTable mus{};
     for (int b = 0; b < c->n_mu; b++) mus.v[b] = c->mu_values[b];
+    mus.fast32 = c->mu_sorted;
+    for (int b = 0; b + 1 < c->n_mu; b++) {
+        mus.mid[b] = (float)(0.5 * (c->mu_values[b] + c->mu_values[b + 1]));
+        if (!(c->mu_values[b + 1] - c->mu_values[b] >= 1e-4)) mus.fast32 = 0;
+    }
     double incl = c->incl_deg * (kPi / 180.0);
     int tap_max = c->tap_min + c->n_taps - 1;
     size_t nb = (size_t)c->n_mu * c->n_taps;

@@ -119,6 +119,29 @@ def test_quiet_library_atanh_and_expm1(S, lam0, lam1, n_px, vsini):
         assert rel(gpu_quiet(S, case, form, S.SOAP_FP32), ref, ref.max()) <= TOL32
 
 
+def test_quiet_cells_on_mu_bin_midpoints(S):
+    """Cells whose mu lies exactly on the midpoint of two tabulated mu values (a tie: the lower
+    bin, as the first minimum of |mu - mu_b|) or 1e-9 above one: the nearest-bin decision leaves
+    the float midpoints for the FP64 comparison there and agrees with the oracle's."""
+    N = 24
+    x = (2 * np.arange(N) + 1 - N) / N
+    r2 = x[:, None] * x[:, None] + x[None, :] * x[None, :]
+    mu = np.sqrt(1.0 - r2[r2 < 1.0])
+    d = 2.0 ** -6
+    a = mu[np.argmin(np.abs(mu - 0.35))]             # tie: midpoint of a - d and a + d is a
+    b = mu[np.argmin(np.abs(mu - 0.62))]             # just above the midpoint b - 1e-9
+    assert a - d >= 0.25 and a + d < 0.5
+    table = np.array([a - d, a + d, b - 1e-9 - d, b - 1e-9 + d, 1.0])
+    assert 0.5 * (table[0] + table[1]) == a and np.all(np.diff(table) > 1e-4)
+    case = synth.make_case(N + 400, name="q", grid_n=N, lambda_start=6000.0, lambda_end=6010.0,
+                           n_px=400, mu_values=table, n_lines=15, depth_law="uniform",
+                           sigma_law="angstrom", vsini_kms=2.0, incl_deg=90.0, diff_rot_alpha=0.0,
+                           regions=[], n_phases=1)
+    ref = O.quiet(case.star, case.quiet)
+    for form in (0, 1):
+        assert rel(gpu_quiet(S, case, form, S.SOAP_FP64), ref, ref.max()) <= TOL64
+
+
 # ------------------------------------------------------------------------------------------
 # active star
 # ------------------------------------------------------------------------------------------
