@@ -303,7 +303,9 @@ k_ccf_tc(const __grid_constant__ CcArgs g, const __grid_constant__ CUtensorMap m
         }
     } else if (warp == 10) {
         if (kTmaA && lane == 0) {
-            // producer: FP32 spectrum blocks (ra rows) into the A stages the MMAs have released
+            // producer: FP32 spectrum blocks (ra rows) into the A stages the MMAs have released,
+            // once the kernel that wrote them has finished (a no-op without an early start)
+            asm volatile("griddepcontrol.wait;" ::: "memory");
             int armed = 0;
             for (int kb = 0; kb < n_kb; kb++) {
                 const int s = kb % SA;
@@ -372,6 +374,7 @@ k_ccf_tc(const __grid_constant__ CcArgs g, const __grid_constant__ CUtensorMap m
         const int r = u & (kCcM - 1), half = u >> 7;
         const bool row_on = s0 + r < g.n_spec;
         const float* frow = g.spectra + (int64_t)(row_on ? s0 + r : 0) * g.n_px;
+        asm volatile("griddepcontrol.wait;" ::: "memory");     // the spectra's writer has finished
         float a[32], a1[32];
         cc_load_row(a, frow, row_on, g.vec4, P0 + 32 * half, P1);
         auto split = [&](int kb, float (&cur)[32], float (&nxt)[32]) -> bool {
@@ -462,10 +465,11 @@ soap_status ccf_tc_build_m(soap_ctx* c, CcfState& st, const CcfPlan& p) {
     k_ccf_tc_m<<<(unsigned)n_kb, kCcThreads, cc_m_smem(), c->stream>>>(m);
     SOAP_LAUNCHED(c);
     st.m_ok = true;
+    st.m_fresh = true;
     return SOAP_OK;
 }
 
-soap_status ccf_tc(soap_ctx* c, const CcfState& st, const CcfPlan& p, const float* spectra, float* partial) {
+soap_status ccf_tc(soap_ctx* c, CcfState& st, const CcfPlan& p, const float* spectra, float* partial) {
     const int n_pad = (p.n_v + 15) / 16 * 16;
     CcArgs a{};
     a.m = st.m.as<unsigned char>();
@@ -482,6 +486,20 @@ soap_status ccf_tc(soap_ctx* c, const CcfState& st, const CcfPlan& p, const floa
     a.tmem_cols = cols;
     a.ra = (int)std::min<int64_t>(kCcM, ((int64_t)p.n_spec + 7) / 8 * 8);
     dim3 grid((unsigned)((c->n_px + p.tc_chunk - 1) / p.tc_chunk), (unsigned)((p.n_spec + kCcM - 1) / kCcM));
+    // Programmatic dependent launch: the CTAs may start while the kernel queued before this one
+    // finishes (it lets them go once all its CTAs have started), set up their barriers and TMEM
+    // and stream the first mask tiles; whatever reads the spectra waits for that kernel first
+    // (griddepcontrol.wait).  Not when that kernel wrote the mask matrix itself.
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = st.m_fresh ? 0 : 1;
+    st.m_fresh = false;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(kCcWsThreads);
+    cfg.stream = c->stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
     CUtensorMap map_f{};
     if (a.vec4 && c->n_px < INT_MAX && p.n_spec < INT_MAX) {
         // spectra [n_spec][n_px] FP32, boxes of ra rows x 64 pixels
@@ -489,13 +507,13 @@ soap_status ccf_tc(soap_ctx* c, const CcfState& st, const CcfPlan& p, const floa
         const uint64_t strides[1] = {(uint64_t)c->n_px * 4};
         const uint32_t box[2] = {(uint32_t)kCcK, (uint32_t)a.ra};
         SOAP_TRY(tc::encode_map(&map_f, 2, spectra, dims, strides, box, CU_TENSOR_MAP_DATA_TYPE_FLOAT32));
-        const size_t smem = cc_ws_smem(n_pad, a.ra, cc_sa(true));
-        SOAP_TRY(fit_dynamic_smem(k_ccf_tc<true>, smem));
-        k_ccf_tc<true><<<grid, kCcWsThreads, smem, c->stream>>>(a, map_f, c->flags);
+        cfg.dynamicSmemBytes = cc_ws_smem(n_pad, a.ra, cc_sa(true));
+        SOAP_TRY(fit_dynamic_smem(k_ccf_tc<true>, cfg.dynamicSmemBytes));
+        SOAP_CUDA(cudaLaunchKernelEx(&cfg, k_ccf_tc<true>, a, map_f, c->flags));
     } else {
-        const size_t smem = cc_ws_smem(n_pad, a.ra, cc_sa(false));
-        SOAP_TRY(fit_dynamic_smem(k_ccf_tc<false>, smem));
-        k_ccf_tc<false><<<grid, kCcWsThreads, smem, c->stream>>>(a, map_f, c->flags);
+        cfg.dynamicSmemBytes = cc_ws_smem(n_pad, a.ra, cc_sa(false));
+        SOAP_TRY(fit_dynamic_smem(k_ccf_tc<false>, cfg.dynamicSmemBytes));
+        SOAP_CUDA(cudaLaunchKernelEx(&cfg, k_ccf_tc<false>, a, map_f, c->flags));
     }
     SOAP_LAUNCHED(c);
     return SOAP_OK;

@@ -144,6 +144,9 @@ k_contract(int64_t n_px, Rows<T> rows, const long long* __restrict__ toff, const
            int G, int max_taps, const T* __restrict__ coefs, ClassTypes ctype, const T* __restrict__ contrast,
            const T* __restrict__ fq, int n_phases, EffectList effs, T* __restrict__ out,
            const int* __restrict__ bstart, int n_mu, int fold) {
+    // a kernel launched after this one with an early start (the tensor-core CCF) may begin once
+    // every CTA here has started: it waits for this grid before it reads the output
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int pb = blockIdx.y;
     const int np = min(PB, n_phases - pb * PB);
     T* out_rows = out + (int64_t)blockIdx.z * n_phases * n_px + (int64_t)pb * PB * n_px;

@@ -122,6 +122,7 @@ struct CcfState {
     bool lines_ok = false;
     bool sorted = false;
     bool m_ok = false;                   // tensor-core mask matrix built for the current tables
+    bool m_fresh = false;                // ... by the last kernel queued (the CCF must not start early)
 };
 
 // How one CCF call runs (ccf_prepare), for n_spec spectra.
@@ -399,7 +400,7 @@ bool ccf_tc_fits(int n_v);
 int64_t ccf_tc_chunk(int64_t n_px, int n_spec, int sms);
 // Mask matrix of the tensor-core form for the tables of `st` (once per mask and grid).
 soap_status ccf_tc_build_m(soap_ctx* c, CcfState& st, const CcfPlan& p);
-soap_status ccf_tc(soap_ctx* c, const CcfState& st, const CcfPlan& p, const float* spectra, float* partial);
+soap_status ccf_tc(soap_ctx* c, CcfState& st, const CcfPlan& p, const float* spectra, float* partial);
 
 }  // namespace soap
 
