@@ -460,6 +460,9 @@ __device__ __forceinline__ void pair_add(float& hi, float& lo, float x) {
 template <typename TP>
 __global__ void k_ccf_reduce(int n_chunks, int n_spec, int n_v, const TP* __restrict__ partial,
                              double* __restrict__ ccf) {
+    // launched early after the tensor-core CCF: wait for its partials, then let the fit start early
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int64_t total = (int64_t)n_spec * n_v;
     const int sub = threadIdx.x % kReduceSplit;
     const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kReduceSplit;
@@ -957,6 +960,7 @@ __global__ void __launch_bounds__(kFwBlock) k_gauss_fit_f32(int n_spec, int n_v_
     __shared__ float buf[2 * kFwSpan * kFwMaxSums];
     __shared__ float sx[3 * kFwSpan];
     __shared__ int sk[kFwSpan];
+    asm volatile("griddepcontrol.wait;" ::: "memory");      // the CCF, when launched early after it
     int parity = 0;
     const int spec = blockIdx.x * Fw<SPAN>::per_block + (int)threadIdx.x / kFwThreads;
     const int t = threadIdx.x % kFwThreads, lane = t & 31, w = t >> 5;
@@ -1121,12 +1125,29 @@ __global__ void __launch_bounds__(kFwBlock) k_gauss_fit_f32(int n_spec, int n_v_
 // (the throughput of many fits).
 constexpr int kFwWholeBlockMax = 2 * 152;
 
-static void fit_f32_launch(int n_spec, cudaStream_t st, int n, int n_v, double v_lo, double v_step,
-                           const double* ccf, float* scratch, double* rv, double* fit, const int* win) {
-    if (n_spec <= kFwWholeBlockMax)
-        k_gauss_fit_f32<4><<<n_spec, kFwBlock, 0, st>>>(n, n_v, v_lo, v_step, ccf, scratch, rv, fit, win);
-    else
-        k_gauss_fit_f32<1><<<(n_spec + 3) / 4, kFwBlock, 0, st>>>(n, n_v, v_lo, v_step, ccf, scratch, rv, fit, win);
+// early: programmatic dependent launch (the kernel before it releases it; it waits for that
+// kernel before it reads anything)
+static cudaLaunchConfig_t pdl_config(dim3 grid, dim3 block, cudaStream_t st, bool early, cudaLaunchAttribute* attr) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.stream = st;
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = early ? 1 : 0;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+
+static cudaError_t fit_f32_launch(int n_spec, cudaStream_t st, bool early, int n, int n_v, double v_lo, double v_step,
+                                  const double* ccf, float* scratch, double* rv, double* fit, const int* win) {
+    cudaLaunchAttribute attr[1];
+    if (n_spec <= kFwWholeBlockMax) {
+        const cudaLaunchConfig_t cfg = pdl_config(dim3(n_spec), dim3(kFwBlock), st, early, attr);
+        return cudaLaunchKernelEx(&cfg, k_gauss_fit_f32<4>, n, n_v, v_lo, v_step, ccf, scratch, rv, fit, win);
+    }
+    const cudaLaunchConfig_t cfg = pdl_config(dim3((n_spec + 3) / 4), dim3(kFwBlock), st, early, attr);
+    return cudaLaunchKernelEx(&cfg, k_gauss_fit_f32<1>, n, n_v, v_lo, v_step, ccf, scratch, rv, fit, win);
 }
 
 bool ccf_mask_same(const CcfState& st, const double* mask_lambda, const double* mask_weight,
@@ -1348,18 +1369,23 @@ soap_status ccf_enqueue(soap_ctx* c, CcfState& st, const CcfPlan& p, const void*
     if (tb) timer_end(c, SOAP_TIMER_CCF, tb);
     tb = c->profiling ? timer_begin(c) : nullptr;
     int64_t tot = (int64_t)n_spec * n_v * kReduceSplit;
-    if ((p.windowed || p.tile_np || p.tc_chunk) && p.f32)   // FP32 partial sums (converted exactly to FP64 here)
-        k_ccf_reduce<float><<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(
-            p.n_chunks, n_spec, n_v, reinterpret_cast<const float*>(d_part), d_ccf);
-    else
+    // after the tensor-core CCF (which releases its dependents as it starts) the reduction and the
+    // fit are launched early, so that their launches overlap the kernel before them
+    const bool early = p.tc_chunk != 0;
+    if ((p.windowed || p.tile_np || p.tc_chunk) && p.f32) {  // FP32 partial sums (converted exactly to FP64 here)
+        cudaLaunchAttribute attr[1];
+        const cudaLaunchConfig_t cfg = pdl_config(dim3((unsigned)((tot + 255) / 256)), dim3(256), c->stream, early, attr);
+        SOAP_CUDA(cudaLaunchKernelEx(&cfg, k_ccf_reduce<float>, p.n_chunks, n_spec, n_v,
+                                     reinterpret_cast<const float*>(d_part), d_ccf));
+    } else
         k_ccf_reduce<double><<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(p.n_chunks, n_spec, n_v,
                                                                                   d_part, d_ccf);
     SOAP_LAUNCHED(c);
     if (tb) timer_end(c, SOAP_TIMER_CCF_AUX, tb);
     if (p.f32)      // float32 spectra: FP32 fit, one warp per spectrum
         SOAP_TIMED(c, SOAP_TIMER_FIT,
-                   fit_f32_launch(n_spec, c->stream,
-                       n_spec, n_v, p.v_lo, p.v_step, d_ccf, reinterpret_cast<float*>(p.y), rv_dev, fit_dev, win);
+                   SOAP_CUDA(fit_f32_launch(n_spec, c->stream, early,
+                       n_spec, n_v, p.v_lo, p.v_step, d_ccf, reinterpret_cast<float*>(p.y), rv_dev, fit_dev, win));
                    SOAP_LAUNCHED(c));
     else            // float64 spectra: FP64 residuals, the least-squares minimum to FP64 rounding
         SOAP_TIMED(c, SOAP_TIMER_FIT,
@@ -1516,8 +1542,8 @@ extern "C" soap_status soap_rv_ccf_static(double lambda_start_A, double lambda_e
     k_ccf_reduce<double><<<(unsigned)((tot + 255) / 256), 256, 0, stream>>>(n_chunks, n_spec, n_v, d_part, d_ccf);
     SOAP_CUDA(cudaGetLastError());
     if (spectra_f32)
-        fit_f32_launch(n_spec, stream,
-            n_spec, n_v, v_lo, v_step, d_ccf, reinterpret_cast<float*>(d_y), rv_kms, fit_params, nullptr);
+        SOAP_CUDA(fit_f32_launch(n_spec, stream, false,
+            n_spec, n_v, v_lo, v_step, d_ccf, reinterpret_cast<float*>(d_y), rv_kms, fit_params, nullptr));
     else
         k_gauss_fit<<<n_spec, kFitThreads, 0, stream>>>(n_spec, n_v, v_lo, v_step, d_ccf, d_y, rv_kms, fit_params,
                                                         nullptr);

@@ -245,6 +245,8 @@ template <bool kTmaA>
 __global__ void __launch_bounds__(kCcWsThreads, 1)
 k_ccf_tc(const __grid_constant__ CcArgs g, const __grid_constant__ CUtensorMap map_f, unsigned int* flags) {
     extern __shared__ unsigned char smem_raw[];
+    // the reduction after this kernel may launch now: it waits for this grid before reading
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     unsigned char* base = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
     const int bb = cc_bb(g.n_pad);
     const int ab = cc_ab(g.ra);
