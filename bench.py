@@ -551,7 +551,7 @@ def measure_surrogate(args, dev):
         xe = synth.surrogate_params(args.seed + 99, 8192)
         err = SP.plain_rv_errors(d.ctx, case, model, xe)
         acc = torch.empty(len(xe), dtype=torch.uint8, device=dev)
-        S.soap_surrogate_predict(model.handle, torch.from_numpy(xe).to(dev), model.accept_thr_cms, accepted=acc)
+        S.soap_surrogate_predict(model.handle, SP.encode_dev(xe), model.accept_thr_cms, accepted=acc)
         a = acc.cpu().numpy().astype(bool)
         res["heldout_vs_plain"] = {
             "queries": len(xe), "accepted_frac": round(float(a.mean()), 4),
@@ -565,7 +565,7 @@ def measure_surrogate(args, dev):
         # (plain; surrogate for every query; hybrid = surrogate where accepted, plain elsewhere)
         nq, ch = args.sur_queries, 65536
         xq = synth.surrogate_params(args.seed + 123, nq)
-        xqd = torch.from_numpy(xq).to(dev)
+        xqd = SP.encode_dev(xq)          # the network's inputs
         out = torch.empty((ch, n_px), dtype=torch.float32, device=dev)
         coef = torch.empty((nq, 128), dtype=torch.float32, device=dev)
         accq = torch.empty(nq, dtype=torch.uint8, device=dev)

@@ -613,6 +613,16 @@ soap_status soap_surrogate_query(soap_surrogate* s, const float* x, int64_t n, f
                                  float* pred_err_cms, uint8_t* accepted);
 void soap_surrogate_free(soap_surrogate* s);
 
+/* Network inputs of n surrogate queries (device float32 [n][8] -> device float32 [n][8],
+ * asynchronous on the stream).  Query parameters: latitude (deg), longitude (deg), radius (R*),
+ * spot temperature (K), phase, inclination (deg), vsini (km/s), facula filling.  Inputs: the
+ * region's centre at that phase in the observer frame of the disk integration (Sect. 2.1 and
+ * Alg. 5: star-frame (cos lat sin L, sin lat, cos lat cos L), L = lon + 360 phase, tilted so that
+ * the rotation axis is (0, sin i, cos i); x across the disk, y up, z toward the observer, rigid
+ * rotation) as (y, x, radius, temperature, z, vsini * x, vsini, filling): the spectrum depends on
+ * latitude, longitude, phase and inclination only through that point.  FP32 (sincosf). */
+soap_status soap_surrogate_encode(const float* params, int64_t n, float* x, void* cuda_stream);
+
 /* y[i] += alpha x[i] for device float arrays of n elements (asynchronous on the stream). */
 soap_status soap_axpy_f32(int64_t n, float alpha, const float* x, float* y, void* cuda_stream);
 

@@ -356,6 +356,30 @@ __global__ void k_axpy(int64_t n, float alpha, const float* __restrict__ x, floa
         y[e] = fmaf(alpha, x[e], y[e]);
 }
 
+// Network inputs of query parameters (soap_surrogate_encode): the region centre at the query's
+// phase in the observer frame (the frame and angles of region_geometry, rigid rotation) and the
+// parameters it does not fix.
+__global__ void k_surrogate_encode(int64_t n, const float* __restrict__ q, float* __restrict__ x) {
+    const float d2r = 0.017453292519943295f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float* p = q + 8 * i;
+        float* o = x + 8 * i;
+        float sl, cl, sL, cL, si, ci;
+        sincosf(p[0] * d2r, &sl, &cl);
+        sincosf((p[1] + 360.0f * p[4]) * d2r, &sL, &cL);
+        sincosf(p[5] * d2r, &si, &ci);
+        const float px = cl * sL, pc = cl * cL;
+        o[0] = sl * si - pc * ci;
+        o[1] = px;
+        o[2] = p[2];
+        o[3] = p[3];
+        o[4] = sl * ci + pc * si;
+        o[5] = p[6] * px;
+        o[6] = p[6];
+        o[7] = p[7];
+    }
+}
+
 // column means of X [n][p] (FP64 accumulation)
 __global__ void k_colmean(const float* __restrict__ X, int64_t n, int64_t p, float* __restrict__ mu) {
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < p; c += (int64_t)gridDim.x * blockDim.x) {
@@ -947,6 +971,16 @@ void soap_surrogate_free(soap_surrogate* s) {
     cudaStreamSynchronize(s->stream);
     free_all(s);
     delete s;
+}
+
+soap_status soap_surrogate_encode(const float* params, int64_t n, float* x, void* cuda_stream) {
+    clear_error();
+    if (n < 0) { set_error("invalid argument"); return SOAP_EINVAL; }
+    if (n == 0) return SOAP_OK;
+    if (!params || !x) { set_error("NULL argument"); return SOAP_EINVAL; }
+    k_surrogate_encode<<<grid1(n), 256, 0, (cudaStream_t)cuda_stream>>>(n, params, x);
+    SOAP_CUDA(cudaGetLastError());
+    return SOAP_OK;
 }
 
 soap_status soap_axpy_f32(int64_t n, float alpha, const float* x, float* y, void* cuda_stream) {

@@ -140,6 +140,7 @@ def _load():
         "soap_surrogate_free": (None, [P]),
         "soap_pca_fit": (i32, [P, i64, i64, P, i32, i32, i32, P, P, P, P]),
         "soap_axpy_f32": (i32, [i64, ctypes.c_float, P, P, P]),
+        "soap_surrogate_encode": (i32, [P, i64, P, P]),
         "soap_pca_project": (i32, [P, i64, i64, P, P, i32, P, P]),
         "soap_free": (None, [P]),
         "soap_last_error": (ctypes.c_char_p, []),
@@ -698,6 +699,14 @@ def soap_pca_fit(X, omega, k: int, n_power: int = 2, stream=None):
                              int(n_power), _dev(mean), _dev(basis), ctypes.c_void_p(sv.ctypes.data),
                              _stream_handle(stream)), "soap_pca_fit")
     return mean, basis, sv
+
+
+def soap_surrogate_encode(params, out, stream=None) -> None:
+    """Network inputs out [n, 8] of query parameters [n, 8] (CUDA float32 tensors)."""
+    if params.shape != out.shape or params.shape[-1] != 8:
+        raise ValueError("params and out must both be [n, 8]")
+    _check(_lib.soap_surrogate_encode(_dev(params, "torch.float32"), int(params.shape[0]), _dev(out, "torch.float32"),
+                                      _stream_handle(stream)), "soap_surrogate_encode")
 
 
 def soap_axpy_f32(alpha: float, x, y, stream=None) -> None:

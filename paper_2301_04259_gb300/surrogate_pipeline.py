@@ -27,6 +27,48 @@ from . import synth
 
 RV_ERR_MAX_CMS = 10.0
 
+# Network inputs: 8 numbers that fix the residual spectrum of a query, computed from its 8
+# parameters.  The region's centre at the query's phase, in the observer's frame (x across the
+# disk along the rotational velocity gradient, y up, z toward the observer: the same frame and
+# angles as the library's region geometry, rigid rotation), replaces latitude, longitude, phase
+# and inclination: the spectrum depends on them only through that point (the cells a region
+# covers and their velocities vsini * x follow from it), and periodically in longitude and phase.
+# Slots: (y, x, radius, spot temperature, z, vsini * x, vsini, facula filling).
+NET_LO = np.array([-1.0, -1.0, 0.01, 3800.0, -1.0, -10.0, 1.0, 0.0])
+NET_HI = np.array([1.0, 1.0, 0.2, 5600.0, 1.0, 10.0, 10.0, 3.0])
+
+
+def encode(params) -> np.ndarray:
+    """Network inputs (float32 [n, 8]) of query parameters [n, 8] (synth.SURROGATE_INPUTS order),
+    on the host in FP64: the statement soap_surrogate_encode (the device form the pipeline uses)
+    is tested against."""
+    q = np.asarray(params, np.float64)
+    lat = np.deg2rad(q[:, 0])
+    lon = np.deg2rad(q[:, 1] + 360.0 * q[:, 4])
+    inc = np.deg2rad(q[:, 5])
+    px = np.cos(lat) * np.sin(lon)
+    ps = np.sin(lat)
+    pc = np.cos(lat) * np.cos(lon)
+    x = np.empty_like(q)
+    x[:, 0] = ps * np.sin(inc) - pc * np.cos(inc)
+    x[:, 1] = px
+    x[:, 2] = q[:, 2]
+    x[:, 3] = q[:, 3]
+    x[:, 4] = ps * np.cos(inc) + pc * np.sin(inc)
+    x[:, 5] = q[:, 6] * px
+    x[:, 6] = q[:, 6]
+    x[:, 7] = q[:, 7]
+    return x.astype(np.float32)
+
+
+def encode_dev(params_host):
+    """Device network inputs [n, 8] of host query parameters (uploaded, then soap_surrogate_encode)."""
+    torch = _torch()
+    q = torch.from_numpy(np.ascontiguousarray(params_host, np.float32)).to("cuda:0")
+    x = torch.empty_like(q)
+    S.soap_surrogate_encode(q, x, torch.cuda.current_stream())
+    return x
+
 
 def _torch():
     import torch
@@ -142,7 +184,7 @@ def train(ctx, case, n_train=200_000, n_cal=32_768, n_err=65_536, epochs=200, er
     t = np.zeros((n_train, k + 1), np.float32)
     t[:, :k] = (c - cm) / cs
     del coef
-    h = S.soap_surrogate_create(synth.SURROGATE_LO, synth.SURROGATE_HI, batch)
+    h = S.soap_surrogate_create(NET_LO, NET_HI, batch)
     model = Surrogate(h, mean, basis, cm.astype(np.float32), cs.astype(np.float32), sv, log=log)
     S.soap_surrogate_set_params(h, synth.surrogate_init(seed + 2))
     S.soap_surrogate_set_scaling(h, model.coef_mean, model.coef_std)
@@ -159,7 +201,7 @@ def train(ctx, case, n_train=200_000, n_cal=32_768, n_err=65_536, epochs=200, er
     else:
         w0[:k] = 1.0 / k
     t0 = time.time()
-    xd = torch.from_numpy(x).to(dev)
+    xd = encode_dev(x)
     td = torch.from_numpy(t).to(dev)
     log["loss"] = S.soap_surrogate_train(h, xd, td, epochs, _cosine(epochs, lr, lr * 0.02), w0, stage=0,
                                          seed=seed + 3).tolist()
@@ -178,9 +220,9 @@ def train(ctx, case, n_train=200_000, n_cal=32_768, n_err=65_536, epochs=200, er
     tc[:, k] = np.log10(err + 0.1)
     w1 = np.zeros(k + 1, np.float32)
     w1[k] = 1.0
-    model.error_net = S.soap_surrogate_create(synth.SURROGATE_LO, synth.SURROGATE_HI, batch)
+    model.error_net = S.soap_surrogate_create(NET_LO, NET_HI, batch)
     S.soap_surrogate_set_params(model.error_net, synth.surrogate_init(seed + 7))
-    log["head_loss"] = S.soap_surrogate_train(model.error_net, torch.from_numpy(xc).to(dev),
+    log["head_loss"] = S.soap_surrogate_train(model.error_net, encode_dev(xc),
                                               torch.from_numpy(tc).to(dev), err_epochs,
                                               _cosine(err_epochs, lr, lr * 0.02), w1, stage=2,
                                               seed=seed + 5).tolist()
@@ -188,7 +230,7 @@ def train(ctx, case, n_train=200_000, n_cal=32_768, n_err=65_536, epochs=200, er
     xv = synth.surrogate_params(seed + 6, n_cal)
     err_v = plain_rv_errors(ctx, case, model, xv)
     pe = torch.empty(n_cal, dtype=torch.float32, device=dev)
-    S.soap_surrogate_predict(h, torch.from_numpy(xv).to(dev), RV_ERR_MAX_CMS, pred_err=pe)
+    S.soap_surrogate_predict(h, encode_dev(xv), RV_ERR_MAX_CMS, pred_err=pe)
     model.accept_thr_cms = calibrate_threshold(pe.cpu().numpy(), err_v)
     log["calib_s"] = time.time() - t0
     log["calib_err_cms_median"] = float(np.median(err))
@@ -211,7 +253,7 @@ def plain_rv_errors(ctx, case, model, x, chunk=8192):
         plain_residuals(ctx, xa, Rt, output=S.SOAP_BATCH_RESIDUAL)
         Rh = torch.empty_like(F)
         acc = torch.empty(m, dtype=torch.uint8, device=dev)
-        S.soap_surrogate_query(model.handle, torch.from_numpy(xa).to(dev), 1e30, Rh, acc)
+        S.soap_surrogate_query(model.handle, encode_dev(xa), 1e30, Rh, acc)
         S.soap_synchronize(ctx)
         Fh = F.clone()
         S.soap_axpy_f32(-1.0, Rt, Fh)
@@ -229,7 +271,7 @@ def query(ctx, model, x_host, sink=None, thr_cms=None, chunk=65536):
     dev = model.basis.device
     n = len(x_host)
     k, n_px = model.basis.shape
-    x_dev = torch.from_numpy(np.ascontiguousarray(x_host, np.float32)).to(dev)
+    x_dev = encode_dev(x_host)
     coef = torch.empty((n, k), dtype=torch.float32, device=dev)
     acc = torch.empty(n, dtype=torch.uint8, device=dev)
     thr = model.accept_thr_cms if thr_cms is None else thr_cms
@@ -261,7 +303,7 @@ def query_coefficients(ctx, model, x_host, coef_out, thr_cms=None, chunk=65536):
     dev = model.basis.device
     n = len(x_host)
     k, n_px = model.basis.shape
-    x_dev = torch.from_numpy(np.ascontiguousarray(x_host, np.float32)).to(dev)
+    x_dev = encode_dev(x_host)
     acc = torch.empty(n, dtype=torch.uint8, device=dev)
     thr = model.accept_thr_cms if thr_cms is None else thr_cms
     S.soap_surrogate_predict(model.handle, x_dev, thr, coef=coef_out, accepted=acc)

@@ -175,3 +175,19 @@ def test_split_bf16_reconstruction_and_query(S):
         assert int(acc.sum().item()) == 0
     finally:
         S.soap_surrogate_free(s)
+
+
+def test_surrogate_encode_matches_the_host_statement(S):
+    """soap_surrogate_encode (FP32, sincosf) against the FP64 host statement of the network
+    inputs (surrogate_pipeline.encode, pinned by test_host_logic): the region centre's y, x, z,
+    vsini * x, and the parameters passed through unchanged."""
+    from paper_2301_04259_gb300 import surrogate_pipeline as SP
+    q = synth.surrogate_params(11, 4099)
+    got = SP.encode_dev(q).cpu().numpy().astype(np.float64)
+    ref = SP.encode(q.astype(np.float64)).astype(np.float64)
+    for k in (2, 3, 6, 7):
+        np.testing.assert_array_equal(got[:, k], q[:, k].astype(np.float64))
+    np.testing.assert_allclose(got[:, [0, 1, 4]], ref[:, [0, 1, 4]], rtol=0, atol=5e-6)
+    np.testing.assert_allclose(got[:, 5], ref[:, 5], rtol=0, atol=5e-5)
+    empty = torch.empty((0, 8), dtype=torch.float32, device=DEV)
+    S.soap_surrogate_encode(empty, empty)

@@ -37,7 +37,7 @@ def test_surrogate_gain_over_the_plain_method(S):
             xe = synth.surrogate_params(1234, 8192)
             err = SP.plain_rv_errors(d.ctx, case, model, xe)
             acc = torch.empty(len(xe), dtype=torch.uint8, device=DEV)
-            S.soap_surrogate_predict(model.handle, t(xe), model.accept_thr_cms, accepted=acc)
+            S.soap_surrogate_predict(model.handle, SP.encode_dev(xe), model.accept_thr_cms, accepted=acc)
             a = acc.cpu().numpy().astype(bool)
             assert a.mean() >= 0.05, a.mean()
             assert (err[a] > SP.RV_ERR_MAX_CMS).mean() <= 0.01, (err[a] > SP.RV_ERR_MAX_CMS).mean()
@@ -50,7 +50,7 @@ def test_surrogate_gain_over_the_plain_method(S):
             n_px = case.star.n_px
             spec = torch.empty((len(xq), n_px), dtype=torch.float32, device=DEV)
             coef = torch.empty((len(xq), 128), dtype=torch.float32, device=DEV)
-            xqd = t(xq)
+            xqd = SP.encode_dev(xq)
 
             def plain_coef():
                 SP.plain_residuals(d.ctx, xq, spec)

@@ -117,6 +117,37 @@ def test_acceptance_threshold_calibration():
 
 
 
+def test_surrogate_inputs_are_the_region_centre_in_the_observer_frame():
+    """The network sees the region centre at the query's phase (a unit vector: y, x, z in slots
+    0, 1, 4; the library's convention: star-frame (cos lat sin L, sin lat, cos lat cos L), L = lon
+    + 360 phase, tilted so that the rotation axis is (0, sin i, cos i)), vsini * x in slot 5, and
+    radius, temperature, vsini and filling unchanged.  Queries with the same centre (a longitude
+    moved by -360 dphase, or by a whole turn) get the same inputs; a pole-on view (i = 0) puts
+    the centre's height at -cos lat cos L; every input lies inside the network's ranges."""
+    from paper_2301_04259_gb300 import synth
+    from paper_2301_04259_gb300.surrogate_pipeline import NET_HI, NET_LO, encode
+    q = synth.surrogate_params(7, 256).astype(np.float64)
+    x = encode(q).astype(np.float64)
+    np.testing.assert_allclose(x[:, 0] ** 2 + x[:, 1] ** 2 + x[:, 4] ** 2, 1.0, atol=1e-6)
+    np.testing.assert_allclose(x[:, 5], q[:, 6] * x[:, 1], rtol=1e-6, atol=1e-6)
+    for k in (2, 3, 6, 7):
+        np.testing.assert_array_equal(x[:, k], q[:, k].astype(np.float32))
+    lat, L = np.deg2rad(q[:, 0]), np.deg2rad(q[:, 1] + 360.0 * q[:, 4])
+    np.testing.assert_allclose(x[:, 1], np.cos(lat) * np.sin(L), atol=1e-6)
+    q0 = q.copy()
+    q0[:, 5] = 0.0
+    np.testing.assert_allclose(encode(q0)[:, 0], -np.cos(lat) * np.cos(L), atol=1e-6)
+    np.testing.assert_allclose(encode(q0)[:, 4], np.sin(lat), atol=1e-6)
+    q2 = q.copy()
+    q2[:, 4] = np.mod(q[:, 4] + 0.3, 1.0)
+    q2[:, 1] = q[:, 1] - 360.0 * (q2[:, 4] - q[:, 4])
+    np.testing.assert_allclose(encode(q2), x, atol=2e-5)
+    q3 = q.copy()
+    q3[:, 1] += 360.0
+    np.testing.assert_allclose(encode(q3), x, atol=2e-5)
+    assert np.all(x >= NET_LO - 1e-6) and np.all(x <= NET_HI + 1e-6)
+
+
 def test_library_evolution_radii_equal_the_oracle_laws():
     """soap_evolve_radii (host code of the library) against the oracle's laws (Sect. 4.2.1)."""
     from paper_2301_04259_gb300 import _build
