@@ -437,8 +437,8 @@ k_ccf_tile(int n_lines, int lines_per_block, const int* __restrict__ U, const fl
     }
 }
 
-// ccf[t] = sum over chunks of partial[c][t], in a fixed order: kReduceSplit lanes take
-// interleaved chunks, then a fixed shuffle tree adds the lanes.  FP64 partials are added in
+// ccf[t] = sum over chunks of partial[c][t], in a fixed order: kReduceSplit threads take
+// interleaved chunks, then a fixed tree adds their sums.  FP64 partials are added in
 // FP64.  FP32 partials are added as unevaluated pairs hi + lo of floats with the error-free
 // transformation TwoSum (Knuth): the pair carries ~48 bits, so the sum is as exact as an FP64
 // sum of the same floats while every operation stays on the FP32 pipe (FP64 and float->double
@@ -457,36 +457,54 @@ __device__ __forceinline__ void pair_add(float& hi, float& lo, float x) {
     lo += e;
 }
 
+// Block (32, kReduceSplit): lane x of warp y takes output t = 32 blockIdx.x + x and chunks y,
+// y + kReduceSplit, ..., so each load instruction reads 32 consecutive outputs of one chunk
+// (whole sectors; with the split across the lanes of a warp every load touched 32 sectors for 128
+// useful bytes); the kReduceSplit sums of an output are then combined through shared memory by
+// the fixed tree of the lane version (y += y + 4, y += y + 2, y += y + 1): the same results.
 template <typename TP>
-__global__ void k_ccf_reduce(int n_chunks, int n_spec, int n_v, const TP* __restrict__ partial,
-                             double* __restrict__ ccf) {
+__global__ void __launch_bounds__(32 * kReduceSplit)
+k_ccf_reduce(int n_chunks, int n_spec, int n_v, const TP* __restrict__ partial, double* __restrict__ ccf) {
     // launched early after the tensor-core CCF: wait for its partials, then let the fit start early
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int64_t total = (int64_t)n_spec * n_v;
-    const int sub = threadIdx.x % kReduceSplit;
-    const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kReduceSplit;
+    const int x = threadIdx.x, sub = threadIdx.y;
+    const int64_t t = (int64_t)blockIdx.x * 32 + x;
     if constexpr (sizeof(TP) == 8) {
+        __shared__ double sh[kReduceSplit][32];
         double s = 0.0;
         if (t < total) {
 #pragma unroll 4
             for (int c = sub; c < n_chunks; c += kReduceSplit) s += (double)partial[(int64_t)c * total + t];
         }
-        for (int o = kReduceSplit / 2; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, kReduceSplit);
-        if (sub == 0 && t < total) ccf[t] = s;
+        sh[sub][x] = s;
+        __syncthreads();
+        for (int o = kReduceSplit / 2; o > 0; o >>= 1) {
+            if (sub < o) sh[sub][x] += sh[sub + o][x];
+            __syncthreads();
+        }
+        if (sub == 0 && t < total) ccf[t] = sh[0][x];
     } else {
+        __shared__ float shh[kReduceSplit][32], shl[kReduceSplit][32];
         float hi = 0.0f, lo = 0.0f;
         if (t < total) {
 #pragma unroll 4
             for (int c = sub; c < n_chunks; c += kReduceSplit) pair_add(hi, lo, partial[(int64_t)c * total + t]);
         }
+        shh[sub][x] = hi;
+        shl[sub][x] = lo;
+        __syncthreads();
         for (int o = kReduceSplit / 2; o > 0; o >>= 1) {
-            const float h2 = __shfl_down_sync(0xffffffffu, hi, o, kReduceSplit);
-            const float l2 = __shfl_down_sync(0xffffffffu, lo, o, kReduceSplit);
-            pair_add(hi, lo, h2);
-            lo += l2;
+            if (sub < o) {
+                float h = shh[sub][x], l = shl[sub][x];
+                pair_add(h, l, shh[sub + o][x]);
+                shh[sub][x] = h;
+                shl[sub][x] = l + shl[sub + o][x];
+            }
+            __syncthreads();
         }
-        if (sub == 0 && t < total) ccf[t] = (double)hi + (double)lo;
+        if (sub == 0 && t < total) ccf[t] = (double)shh[0][x] + (double)shl[0][x];
     }
 }
 
@@ -1368,18 +1386,18 @@ soap_status ccf_enqueue(soap_ctx* c, CcfState& st, const CcfPlan& p, const void*
     SOAP_LAUNCHED(c);
     if (tb) timer_end(c, SOAP_TIMER_CCF, tb);
     tb = c->profiling ? timer_begin(c) : nullptr;
-    int64_t tot = (int64_t)n_spec * n_v * kReduceSplit;
+    const unsigned rblocks = (unsigned)(((int64_t)n_spec * n_v + 31) / 32);
     // after the tensor-core CCF (which releases its dependents as it starts) the reduction and the
     // fit are launched early, so that their launches overlap the kernel before them
     const bool early = p.tc_chunk != 0;
     if ((p.windowed || p.tile_np || p.tc_chunk) && p.f32) {  // FP32 partial sums (converted exactly to FP64 here)
         cudaLaunchAttribute attr[1];
-        const cudaLaunchConfig_t cfg = pdl_config(dim3((unsigned)((tot + 255) / 256)), dim3(256), c->stream, early, attr);
+        const cudaLaunchConfig_t cfg = pdl_config(dim3(rblocks), dim3(32, kReduceSplit), c->stream, early, attr);
         SOAP_CUDA(cudaLaunchKernelEx(&cfg, k_ccf_reduce<float>, p.n_chunks, n_spec, n_v,
                                      reinterpret_cast<const float*>(d_part), d_ccf));
     } else
-        k_ccf_reduce<double><<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(p.n_chunks, n_spec, n_v,
-                                                                                  d_part, d_ccf);
+        k_ccf_reduce<double><<<rblocks, dim3(32, kReduceSplit), 0, c->stream>>>(p.n_chunks, n_spec, n_v,
+                                                                                d_part, d_ccf);
     SOAP_LAUNCHED(c);
     if (tb) timer_end(c, SOAP_TIMER_CCF_AUX, tb);
     if (p.f32)      // float32 spectra: FP32 fit, one warp per spectrum
@@ -1538,8 +1556,8 @@ extern "C" soap_status soap_rv_ccf_static(double lambda_start_A, double lambda_e
             (const double*)spectra, d_part);
     }
     SOAP_CUDA(cudaGetLastError());
-    int64_t tot = (int64_t)n_spec * n_v * kReduceSplit;
-    k_ccf_reduce<double><<<(unsigned)((tot + 255) / 256), 256, 0, stream>>>(n_chunks, n_spec, n_v, d_part, d_ccf);
+    k_ccf_reduce<double><<<(unsigned)(((int64_t)n_spec * n_v + 31) / 32), dim3(32, kReduceSplit), 0, stream>>>(
+        n_chunks, n_spec, n_v, d_part, d_ccf);
     SOAP_CUDA(cudaGetLastError());
     if (spectra_f32)
         SOAP_CUDA(fit_f32_launch(n_spec, stream, false,
