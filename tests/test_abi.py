@@ -75,6 +75,10 @@ def test_null_arguments_are_rejected(lib):
     assert lib._lib.soap_active_rv(None, None, 0, None, 0, 1, 0, None, None, 0, 0.8, -20.0, 0.25, 161,
                                    None, None, 0) == lib.SOAP_EINVAL
     assert lib._lib.soap_set_host_async(None, 1) == lib.SOAP_EINVAL
+    assert lib._lib.soap_set_ccf_tensor_cores(None, 1) == lib.SOAP_EINVAL
+    assert lib._lib.soap_surrogate_encode(None, 4, None, None) == lib.SOAP_EINVAL
+    assert lib._lib.soap_surrogate_encode(None, -1, None, None) == lib.SOAP_EINVAL
+    assert lib._lib.soap_surrogate_encode(None, 0, None, None) == lib.SOAP_OK       # nothing to do
     lib._lib.soap_free(None)
 
 
