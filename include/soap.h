@@ -479,8 +479,9 @@ soap_status soap_batch_autotune(soap_ctx* ctx, const soap_batch_item* items, int
  * at least one velocity step: Levenberg-Marquardt in FP32 until its step is below 1e-4, then
  * Newton steps on the exact Hessian.  Float64 spectra: the Newton steps take FP64 residuals and
  * gradient, so that the result is the least-squares minimum to FP64 rounding.  Float32 spectra
- * (whose CCF carries FP32 rounding already): one warp per spectrum, FP32 throughout, which
- * places the centre within ~1e-8 of the Gaussian's width of that minimum.
+ * (whose CCF carries FP32 rounding already): FP32 throughout, a block of four warps per spectrum
+ * for at most 304 spectra and one warp per spectrum beyond, which places the centre within ~1e-8
+ * of the Gaussian's width of that minimum.
  *  rv_kms         [n_spec] fitted mu (km/s); NaN when the fit leaves the velocity grid (mu
  *                 outside it or a width larger than it: no dip to fit).
  *  fit_params     [n_spec][4] (A, B, mu, s), or NULL.
